@@ -1,0 +1,295 @@
+"""FP64 oracle for the visibility-based binned angular bispectrum (Sec. 2).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only users.  The product path never
+imports this package, and this package never imports the product.
+
+The heavy loops (gridding, brute-force triple sums) are plain C in
+``abs_oracle.c``; this module loads it with ctypes and adds the numpy glue.
+``fft_form`` is a second, independent route to the same sums through numpy's
+FFT (the identity the fast estimator of Sec. 2 relies on); the tests check
+the two against each other and against closed forms.
+
+Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
+
+* cell / ring thresholds / triplets: explicit worked cases, integer brute force
+* grid: single-visibility closed forms, Hermitian mirror, NGP exact sums
+* triple_bruteforce / triple_one: pure-Python enumeration on tiny grids,
+  FFT identity, constant-sky B = s^3, point-source phase closure,
+  ring-constant product, rotation/reflection invariance, permutation
+  symmetry of counts, Gaussian-sky zero mean, quadratic-sky closed form
+  (discrete Eq. bsana)
+* ellbar: direct closed form on a hand-built mask
+* normalise: closed forms above
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "abs_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle in place (gcc, FP contraction off, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    P = ctypes.c_void_p
+    i32, i64, f32, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
+    lib.orc_cell.argtypes = [f32, f32]
+    lib.orc_cell.restype = i32
+    lib.orc_ring_q.argtypes = [i32, P, f32, P]
+    lib.orc_ring_q.restype = None
+    lib.orc_triplets.argtypes = [i32, P, i32, P]
+    lib.orc_triplets.restype = i32
+    lib.orc_grid.argtypes = [i32, f32, i32, f64, i32, i64, P, P, P, P, P]
+    lib.orc_grid.restype = ctypes.c_int
+    lib.orc_mean_grid.argtypes = [i32, P, P, P, P, P]
+    lib.orc_mean_grid.restype = None
+    lib.orc_triple_bruteforce.argtypes = [i32, P, P, i32, P, i32, P, P, P, P]
+    lib.orc_triple_bruteforce.restype = ctypes.c_int
+    lib.orc_triple_one.argtypes = [i32, P, P, i32, P, i32, i32, i32, P, P, P]
+    lib.orc_triple_one.restype = ctypes.c_int
+    lib.orc_ellbar.argtypes = [i32, f32, P, i32, P, P]
+    lib.orc_ellbar.restype = None
+    lib.orc_normalise.argtypes = [i32, P, P, f64, P]
+    lib.orc_normalise.restype = None
+    _lib = lib
+    return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ------------------------------------------------------------------ small pieces
+
+
+def cell(u: float, du: float) -> int:
+    """Nearest grid index of one coordinate, binary32 rule floor(fl(fl(u/dU)+0.5))."""
+    return int(_load().orc_cell(float(np.float32(u)), float(np.float32(du))))
+
+
+def ring_q(ell_edges, du: float) -> np.ndarray:
+    e = np.ascontiguousarray(ell_edges, np.float64)
+    q = np.zeros(len(e), np.int64)
+    _load().orc_ring_q(len(e) - 1, _p(e), float(np.float32(du)), _p(q))
+    return q
+
+
+def triplets(q: np.ndarray) -> np.ndarray:
+    q = np.ascontiguousarray(q, np.int64)
+    nb = len(q) - 1
+    n = _load().orc_triplets(nb, _p(q), 0, None)
+    out = np.zeros((max(n, 1), 3), np.int32)
+    _load().orc_triplets(nb, _p(q), n, _p(out))
+    return out[:n]
+
+
+# ------------------------------------------------------------------ gridding
+
+
+@dataclass
+class Grid:
+    grid: np.ndarray      # complex128 [n, n] (FFT order), Eq. vg sums incl. mirror
+    wsum: np.ndarray      # float64 [n, n]
+    ncontrib: np.ndarray  # int64 [n, n]
+
+    @property
+    def n(self):
+        return self.grid.shape[0]
+
+
+def grid(n: int, du: float, uv: np.ndarray, vis: np.ndarray, kernel: str = "gauss",
+         sigma_cells: float = 1.0, radius_cells: int = 3) -> Grid:
+    uv = np.ascontiguousarray(uv, np.float32)
+    v2 = np.ascontiguousarray(np.asarray(vis, np.complex64)).view(np.float32)
+    g = np.zeros((n, n, 2), np.float64)
+    w = np.zeros((n, n), np.float64)
+    c = np.zeros((n, n), np.int64)
+    rc = _load().orc_grid(n, float(np.float32(du)), 0 if kernel == "ngp" else 1, float(sigma_cells),
+                          int(radius_cells), len(uv), _p(uv), _p(v2), _p(g), _p(w), _p(c))
+    if rc != 0:
+        raise ValueError(f"orc_grid rejected its arguments (code {rc})")
+    return Grid(g[..., 0] + 1j * g[..., 1], w, c)
+
+
+def mean_grid(gr: Grid):
+    """X_g = V_g / sum w on filled cells (complex128 [n,n]) and the filled mask (uint8)."""
+    n = gr.n
+    g2 = np.ascontiguousarray(np.stack([gr.grid.real, gr.grid.imag], -1))
+    X = np.zeros((n, n, 2), np.float64)
+    f = np.zeros((n, n), np.uint8)
+    _load().orc_mean_grid(n, _p(g2), _p(np.ascontiguousarray(gr.wsum)),
+                          _p(np.ascontiguousarray(gr.ncontrib)), _p(X), _p(f))
+    return X[..., 0] + 1j * X[..., 1], f
+
+
+# ------------------------------------------------------------------ triple sums
+
+
+def _x2(X):
+    return np.ascontiguousarray(np.stack([np.real(X), np.imag(X)], -1).astype(np.float64))
+
+
+def triple_bruteforce(X: np.ndarray, filled: np.ndarray, q: np.ndarray, ijk: np.ndarray):
+    """(S complex128 [t], |.|-sum float64 [t], T int64 [t]) over all closed grid triangles."""
+    n = X.shape[0]
+    ijk = np.ascontiguousarray(ijk, np.int32).reshape(-1, 3)
+    nt = len(ijk)
+    S = np.zeros((max(nt, 1), 2))
+    A = np.zeros(max(nt, 1))
+    T = np.zeros(max(nt, 1), np.int64)
+    rc = _load().orc_triple_bruteforce(n, _p(_x2(X)), _p(np.ascontiguousarray(filled, np.uint8)),
+                                       len(q) - 1, _p(np.ascontiguousarray(q, np.int64)), nt,
+                                       _p(ijk), _p(S), _p(A), _p(T))
+    if rc != 0:
+        raise MemoryError("orc_triple_bruteforce: allocation failed")
+    return (S[:nt, 0] + 1j * S[:nt, 1]), A[:nt], T[:nt]
+
+
+def triple_one(X, filled, q, i, j, k):
+    n = X.shape[0]
+    S = np.zeros(2)
+    A = np.zeros(1)
+    T = np.zeros(1, np.int64)
+    _load().orc_triple_one(n, _p(_x2(X)), _p(np.ascontiguousarray(filled, np.uint8)), len(q) - 1,
+                           _p(np.ascontiguousarray(q, np.int64)), int(i), int(j), int(k),
+                           _p(S), _p(A), _p(T))
+    return complex(S[0], S[1]), float(A[0]), int(T[0])
+
+
+def ellbar(filled: np.ndarray, q: np.ndarray, du: float) -> np.ndarray:
+    n = filled.shape[0]
+    out = np.zeros(len(q) - 1)
+    _load().orc_ellbar(n, float(np.float32(du)), _p(np.ascontiguousarray(filled, np.uint8)),
+                       len(q) - 1, _p(np.ascontiguousarray(q, np.int64)), _p(out))
+    return out
+
+
+def normalise(S: np.ndarray, T: np.ndarray, norm_A: float = 1.0) -> np.ndarray:
+    S = np.asarray(S)
+    nt = len(S)
+    s2 = np.ascontiguousarray(np.stack([S.real, S.imag], -1).reshape(-1, 2), np.float64)
+    B = np.zeros(max(nt, 1))
+    _load().orc_normalise(nt, _p(s2), _p(np.ascontiguousarray(T, np.int64)), float(norm_A), _p(B))
+    return B[:nt]
+
+
+# ------------------------------------------------------------------ FFT form
+
+
+def ring_fields(X: np.ndarray, filled: np.ndarray, q: np.ndarray, N: int, unit: bool = False):
+    """Real fields D_m(p) = sum_{g in a_m} X_g exp(-2 pi i g.p / N) (Eq. iFT) on an N x N
+    sky grid, via numpy's FFT; with unit=True the unit-mask fields (X = 1 on filled
+    ring cells).  Returns float64 [n_bins, N, N] (imaginary parts dropped) and the
+    largest |imaginary part| seen."""
+    n = X.shape[0]
+    half = n // 2 - 1
+    gy, gx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    gy = np.where(gy > n // 2, gy - n, gy)
+    gx = np.where(gx > n // 2, gx - n, gx)
+    r2 = gx.astype(np.int64) ** 2 + gy.astype(np.int64) ** 2
+    inside = (np.abs(gx) <= half) & (np.abs(gy) <= half) & (filled > 0)
+    nb = len(q) - 1
+    D = np.zeros((nb, N, N))
+    im = 0.0
+    for m in range(nb):
+        sel = inside & (r2 >= q[m]) & (r2 < q[m + 1])
+        Z = np.zeros((N, N), np.complex128)
+        vals = np.ones(sel.sum()) if unit else X[sel]
+        np.add.at(Z, (gy[sel] % N, gx[sel] % N), vals)
+        F = np.fft.fft2(Z)
+        im = max(im, float(np.abs(F.imag).max()) if F.size else 0.0)
+        D[m] = F.real
+    return D, im
+
+
+def fft_form(X, filled, q, ijk, N: int):
+    """S_ijk = N^-2 sum_p D_i D_j D_k and T_ijk = N^-2 sum_p I_i I_j I_k (rounded), Eq. estimator_t."""
+    D, _ = ring_fields(X, filled, q, N)
+    I, _ = ring_fields(X, filled, q, N, unit=True)
+    S = np.array([np.sum(D[i] * D[j] * D[k]) for i, j, k in ijk]) / (N * N)
+    T = np.array([np.sum(I[i] * I[j] * I[k]) for i, j, k in ijk]) / (N * N)
+    return S, np.rint(T).astype(np.int64), T
+
+
+def min_fft_size(q: np.ndarray) -> int:
+    """Smallest 2^a 3^b 5^c >= 3 R + 1, R the largest |g_x| of any ring cell."""
+    R = int(np.floor(np.sqrt(float(q[-1] - 1))))
+    while R * R > q[-1] - 1:
+        R -= 1
+    while (R + 1) * (R + 1) <= q[-1] - 1:
+        R += 1
+    N = 3 * R + 1
+    while True:
+        m = N
+        for p in (2, 3, 5):
+            while m % p == 0:
+                m //= p
+        if m == 1:
+            return N
+        N += 1
+
+
+# ------------------------------------------------------------------ whole estimate
+
+
+@dataclass
+class Estimate:
+    B: np.ndarray         # float64 [t]
+    S: np.ndarray         # complex128 [t]
+    absum: np.ndarray     # float64 [t]
+    T: np.ndarray         # int64 [t]
+    ellbar: np.ndarray    # float64 [n_bins]
+    ijk: np.ndarray       # int32 [t, 3]
+    q: np.ndarray         # int64 [n_bins + 1]
+    X: np.ndarray         # complex128 [n, n]
+    filled: np.ndarray    # uint8 [n, n]
+    grid: Grid
+
+
+def estimate(n, du, ell_edges, uv, vis, kernel="gauss", sigma_cells=1.0, radius_cells=3,
+             norm_A=1.0, ijk=None) -> Estimate:
+    """V -> B for one realisation: Eq. vg, ring membership, closed-triangle sums, Eq. estimator_t."""
+    q = ring_q(ell_edges, du)
+    if ijk is None:
+        ijk = triplets(q)
+    gr = grid(n, du, uv, vis, kernel, sigma_cells, radius_cells)
+    X, f = mean_grid(gr)
+    S, A, T = triple_bruteforce(X, f, q, ijk)
+    B = normalise(S, T, norm_A)
+    return Estimate(B, S, A, T, ellbar(f, q, du), np.asarray(ijk, np.int32), q, X, f, gr)
+
+
+# ------------------------------------------------------------------ paper constants
+
+
+def beam_constants(theta_f_deg: float = 24.68):
+    """theta_0 = 0.6 theta_F (Eq. A_G), dU_g = sqrt(ln 2)/(pi theta_0) and the
+    decorrelation exp(-pi^2 theta_0^2 dU^2/3) at dU^2 = dU_g^2/2 (Sec. 3), and the
+    normalisation A = pi theta_0^2 / 3 of Eq. estimator_t."""
+    th0 = 0.6 * np.deg2rad(theta_f_deg)
+    dug = np.sqrt(np.log(2.0)) / (np.pi * th0)
+    decor = np.exp(-np.pi ** 2 * th0 ** 2 * (dug ** 2 / 2.0) / 3.0)
+    A = np.pi * th0 ** 2 / 3.0
+    return {"theta0": th0, "du_g": dug, "decorrelation": decor, "A": A}

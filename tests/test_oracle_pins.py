@@ -1,0 +1,483 @@
+"""Pins for the FP64 oracle against what the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own code path: worked cases
+written out by hand, closed forms, pure-Python enumeration on tiny grids, the
+FFT identity through numpy's transform, and symmetries.  Each is chosen so
+that a plausible mistake (a dropped term, a wrong sign or index, a
+transposed operand) fails at least one of them.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_02246_gb300 import synth
+
+
+# ----------------------------------------------------------------- helpers
+
+
+def full_mask(n):
+    f = np.ones((n, n), np.uint8)
+    f[n // 2, :] = 0          # the row/column at index n/2 is off the grid (|g| <= n/2-1)
+    f[:, n // 2] = 0
+    return f
+
+
+def coords(n):
+    k = np.arange(n)
+    k = np.where(k > n // 2, k - n, k)
+    gy, gx = np.meshgrid(k, k, indexing="ij")
+    return gx, gy
+
+
+def random_hermitian_grid(n, rng):
+    """X with X(-g) = conj X(g) on the grid (|g| <= n/2-1), built by explicit mirroring."""
+    gx, gy = coords(n)
+    X = np.zeros((n, n), np.complex128)
+    half = n // 2 - 1
+    for y in range(-half, half + 1):
+        for x in range(-half, half + 1):
+            if (y, x) < (0, 0) or (y == 0 and x < 0):
+                continue
+            v = complex(rng.standard_normal(), rng.standard_normal())
+            if x == 0 and y == 0:
+                v = complex(v.real, 0.0)
+            X[y % n, x % n] = v
+            X[(-y) % n, (-x) % n] = np.conj(v)
+    return X
+
+
+# ----------------------------------------------------------------- cell index
+
+
+def test_cell_rule_worked_cases():
+    # nearest grid point, ties rounded up (floor(x + 1/2)), Eq. vg
+    assert oracle.cell(0.0, 1.0) == 0
+    assert oracle.cell(0.5, 1.0) == 1
+    assert oracle.cell(-0.5, 1.0) == 0
+    assert oracle.cell(1.49, 1.0) == 1
+    assert oracle.cell(-1.5, 1.0) == -1
+    assert oracle.cell(-1.51, 1.0) == -2
+    assert oracle.cell(7.0, 2.0) == 4          # 3.5 -> 4
+    assert oracle.cell(-7.0, 2.0) == -3        # -3.5 -> -3
+    assert oracle.cell(219.9, 2.3) == 96
+
+
+def test_cell_rule_is_binary32():
+    # 0.3/0.2: in binary32 the quotient rounds to exactly 1.5 and goes up to 2;
+    # in binary64 it is 1.4999999999999998 and would go to 1.  Masks (and hence
+    # counts) depend on taking the binary32 reading on both sides.
+    u, du = np.float32(0.3), np.float32(0.2)
+    assert np.float32(u / du) == np.float32(1.5)
+    assert float(u) / float(du) != 1.5
+    assert oracle.cell(0.3, 0.2) == 2
+
+
+# ----------------------------------------------------------------- rings, triplets
+
+
+def test_ring_thresholds_against_membership_definition():
+    # a_m holds the cells with l_m <= 2 pi |g| dU < l_{m+1}: Q_m is the smallest
+    # integer |g|^2 in ring m.  Checked by scanning the integers directly.
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        du = float(np.float32(rng.uniform(0.5, 3.0)))
+        edges = np.sort(rng.uniform(10.0, 900.0, 6))
+        q = oracle.ring_q(edges, du)
+        for m, e in enumerate(edges):
+            r2 = 0
+            while 2.0 * math.pi * du * math.sqrt(r2) < e:
+                r2 += 1
+            # r2 is the first integer with l(r2) >= e (up to the last ulp of sqrt)
+            assert abs(q[m] - r2) <= 1
+            if q[m] != r2:        # only possible at an exact tie in floating point
+                assert abs(2.0 * math.pi * du * math.sqrt(q[m]) - e) < 1e-9 * e
+
+
+def test_ring_thresholds_known_values():
+    # l = 2 pi dU r with r = 2.5 -> r^2 = 6.25 -> first integer 7; r = 4.1 -> 16.81 -> 17
+    q = oracle.ring_q([2 * math.pi * 2.5, 2 * math.pi * 4.1], 1.0)
+    assert list(q) == [7, 17]
+    q = oracle.ring_q([2 * math.pi * 2.0 * 2.5], 2.0)
+    assert list(q) == [7]
+
+
+def test_paper_ring_set_has_2024_combinations():
+    # Sec. 3: 22 rings in grid units ([1,5], nine in 5-50, five in 50-100, five
+    # in 100-200, two in 200-250), "every possible combination of three rings".
+    r = [1.0, 5.0] + list(np.linspace(5, 50, 10)[1:]) + list(np.linspace(50, 100, 6)[1:]) \
+        + list(np.linspace(100, 200, 6)[1:]) + list(np.linspace(200, 250, 3)[1:])
+    assert len(r) == 23
+    edges = 2 * np.pi * np.asarray(r)       # dU_g = 1
+    q = oracle.ring_q(edges, 1.0)
+    nb = len(q) - 1
+    assert nb == 22
+    assert len(list(itertools.combinations_with_replacement(range(nb), 3))) == 2024
+    t = oracle.triplets(q)
+    assert 0 < len(t) < 2024
+
+
+def test_triplets_are_a_superset_of_closing_rings():
+    # Every (i<=j<=k) that holds at least one closed triangle on a full grid
+    # must be listed; the list must be ordered i<=j<=k lexicographically.
+    n = 40
+    edges = np.array([6.0, 20.0, 37.0, 55.0, 80.0, 110.0])
+    du = 1.0
+    q = oracle.ring_q(edges, du)
+    t = oracle.triplets(q)
+    assert np.all(t[:, 0] <= t[:, 1]) and np.all(t[:, 1] <= t[:, 2])
+    assert [tuple(x) for x in t] == sorted(tuple(x) for x in t)
+    allc = np.array(list(itertools.combinations_with_replacement(range(len(q) - 1), 3)), np.int32)
+    X = np.ones((n, n), np.complex128)
+    _, _, T = oracle.triple_bruteforce(X, full_mask(n), q, allc)
+    listed = {tuple(x) for x in t}
+    for (i, j, k), cnt in zip(allc, T):
+        if cnt > 0:
+            assert (i, j, k) in listed
+    # and the test is tight enough to drop most non-closing combinations
+    assert len(t) < len(allc)
+
+
+# ----------------------------------------------------------------- gridding
+
+
+def test_grid_single_visibility_on_grid_point():
+    # Gaussian kernel sigma = 1 cell, r = 3: weights exp(-|d|^2/2) at c + d,
+    # mirrored with V* at -(c + d).  du = 1 so U_i is exactly the grid point.
+    n = 64
+    v = 0.75 - 0.5j
+    gr = oracle.grid(n, 1.0, np.array([[10.0, 5.0]], np.float32), np.array([v], np.complex64))
+    for dy in range(-3, 4):
+        for dx in range(-3, 4):
+            w = math.exp(-(dx * dx + dy * dy) / 2.0)
+            gx, gy = 10 + dx, 5 + dy
+            assert gr.wsum[gy % n, gx % n] == pytest.approx(w, rel=1e-15)
+            assert gr.grid[gy % n, gx % n] == pytest.approx(w * v, rel=1e-15)
+            assert gr.grid[(-gy) % n, (-gx) % n] == pytest.approx(w * np.conj(v), rel=1e-15)
+            assert gr.ncontrib[gy % n, gx % n] == 1
+    s1 = sum(math.exp(-k * k / 2.0) for k in range(-3, 4))
+    assert gr.wsum.sum() == pytest.approx(2 * s1 * s1, rel=1e-14)
+    assert gr.ncontrib.sum() == 2 * 49
+
+
+def test_grid_single_visibility_off_grid():
+    # U = (c + f) dU with f = (0.25, -0.375): w = exp(-((dx - fx)^2 + (dy - fy)^2)/2)
+    n, du = 64, 2.0
+    fx, fy = 0.25, -0.375
+    u = np.array([[(7 + fx) * du, (-9 + fy) * du]], np.float32)
+    gr = oracle.grid(n, du, u, np.array([1.0 + 0j], np.complex64))
+    for dy in range(-3, 4):
+        for dx in range(-3, 4):
+            w = math.exp(-((dx - fx) ** 2 + (dy - fy) ** 2) / 2.0)
+            assert gr.wsum[(-9 + dy) % n, (7 + dx) % n] == pytest.approx(w, rel=1e-14)
+
+
+def test_grid_sigma_and_radius():
+    n = 32
+    gr = oracle.grid(n, 1.0, np.array([[3.0, 4.0]], np.float32), np.array([1.0], np.complex64),
+                     sigma_cells=2.0, radius_cells=1)
+    assert gr.ncontrib.sum() == 2 * 9
+    assert gr.wsum[5 % n, 4 % n] == pytest.approx(math.exp(-2.0 / 8.0), rel=1e-15)
+
+
+def test_grid_ngp_sums_and_mirror():
+    # NGP: every visibility lands on its nearest cell with w = 1
+    n, du = 32, 1.0
+    uv = np.array([[2.2, 3.1], [1.8, 2.6], [-4.0, 0.4]], np.float32)
+    vis = np.array([1 + 2j, 3 - 1j, 0.5 + 0.5j], np.complex64)
+    gr = oracle.grid(n, du, uv, vis, kernel="ngp")
+    assert gr.grid[3, 2] == pytest.approx(complex(vis[0]) + complex(vis[1]))
+    assert gr.grid[(-3) % n, (-2) % n] == pytest.approx(np.conj(complex(vis[0]) + complex(vis[1])))
+    assert gr.ncontrib[3, 2] == 2 and gr.ncontrib[0, (-4) % n] == 1 and gr.ncontrib[0, 4] == 1
+    assert gr.ncontrib.sum() == 6
+
+
+def test_grid_edge_cells_dropped():
+    # cells with |g_x| or |g_y| > n/2 - 1 are not on the grid
+    n = 16
+    gr = oracle.grid(n, 1.0, np.array([[7.0, 0.0]], np.float32), np.array([1.0], np.complex64))
+    # footprint x in 4..10, only 4..7 kept: 4 columns x 7 rows, twice (mirror)
+    assert gr.ncontrib.sum() == 2 * 4 * 7
+    assert gr.ncontrib[:, n // 2].sum() == 0 and gr.ncontrib[n // 2, :].sum() == 0
+
+
+def test_grid_is_hermitian():
+    inp = synth.make_inputs(0)
+    gr = oracle.grid(64, inp.wl.du, inp.uv, inp.vis)
+    flip = lambda a: np.roll(a[::-1, ::-1], 1, axis=(0, 1))   # a(-g)
+    assert np.allclose(gr.grid, np.conj(flip(gr.grid)), rtol=0, atol=1e-12 * np.abs(gr.grid).max())
+    assert np.array_equal(gr.ncontrib, flip(gr.ncontrib))
+    X, f = oracle.mean_grid(gr)
+    assert np.array_equal(f, (gr.ncontrib > 0).astype(np.uint8))
+    sel = f > 0
+    assert np.allclose(X[sel] * gr.wsum[sel], gr.grid[sel], rtol=1e-14, atol=0)
+
+
+# ----------------------------------------------------------------- triple sums
+
+
+def python_enumeration(X, filled, q):
+    """All ordered triples (g1,g2,g3) of filled ring cells with g1+g2+g3 = 0: O(C^3)."""
+    n = X.shape[0]
+    half = n // 2 - 1
+    cells = []
+    for gy in range(-half, half + 1):
+        for gx in range(-half, half + 1):
+            if not filled[gy % n, gx % n]:
+                continue
+            r2 = gx * gx + gy * gy
+            m = [b for b in range(len(q) - 1) if q[b] <= r2 < q[b + 1]]
+            if m:
+                cells.append((gx, gy, m[0], X[gy % n, gx % n]))
+    S, T = {}, {}
+    for a in cells:
+        for b in cells:
+            for c in cells:
+                if a[0] + b[0] + c[0] == 0 and a[1] + b[1] + c[1] == 0:
+                    key = (a[2], b[2], c[2])
+                    S[key] = S.get(key, 0) + a[3] * b[3] * c[3]
+                    T[key] = T.get(key, 0) + 1
+    return S, T
+
+
+def test_bruteforce_matches_python_enumeration_tiny():
+    rng = np.random.default_rng(7)
+    n = 14
+    X = random_hermitian_grid(n, rng)
+    filled = full_mask(n)
+    gx, gy = coords(n)
+    drop = rng.random((n, n)) < 0.2
+    filled[drop] = 0
+    filled[(-gy[drop]) % n, (-gx[drop]) % n] = 0      # holes come in +-g pairs
+    edges = 2 * np.pi * np.array([1.2, 2.6, 4.0, 5.7])
+    q = oracle.ring_q(edges, 1.0)
+    allc = np.array(list(itertools.product(range(3), repeat=3)), np.int32)
+    S, _, T = oracle.triple_bruteforce(X, filled, q, allc)
+    Sp, Tp = python_enumeration(X, filled, q)
+    for t, (i, j, k) in enumerate(allc):
+        assert T[t] == Tp.get((i, j, k), 0)
+        assert S[t] == pytest.approx(Sp.get((i, j, k), 0), rel=1e-12, abs=1e-12)
+    assert T.sum() > 0
+    # triple_one agrees with the all-pairs route
+    for t in (0, 5, 13, 26):
+        s1, _, t1 = oracle.triple_one(X, filled, q, *allc[t])
+        assert t1 == T[t] and s1 == pytest.approx(S[t], rel=1e-12, abs=1e-12)
+
+
+def test_fft_identity_and_aliasing():
+    # Sec. 2: sum_theta D_i D_j D_k (Eq. iFT) equals N^2 times the sum over closed
+    # grid triangles when the sky grid is large enough (N >= 3R+1) to exclude
+    # wrapped triangles; smaller N aliases.
+    inp = synth.make_inputs(0)
+    wl = inp.wl
+    est = oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+    N = oracle.min_fft_size(est.q)
+    assert N == 90
+    S_fft, T_fft, T_raw = oracle.fft_form(est.X, est.filled, est.q, est.ijk, N)
+    assert np.max(np.abs(S_fft - est.S.real) / np.maximum(est.absum, 1e-300)) < 1e-12
+    assert np.array_equal(T_fft, est.T)
+    assert np.max(np.abs(T_raw - est.T)) < 1e-6
+    S_al, T_al, _ = oracle.fft_form(est.X, est.filled, est.q, est.ijk, 64)
+    assert np.sum(T_al != est.T) > 0
+
+
+def test_constant_visibilities_give_s_cubed():
+    # V = s (real) everywhere -> every filled X_g = s (the gridded mean of a constant,
+    # mirror included) -> B = s^3 on every triplet with T > 0, whatever the gridding
+    # kernel (a point source at the phase centre).
+    inp = synth.make_inputs(0)
+    wl = inp.wl
+    vis = np.full(len(inp.uv), 0.7, np.complex64)
+    s = float(np.float32(0.7))
+    for kernel in ("gauss", "ngp"):
+        est = oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, inp.uv, vis, kernel=kernel)
+        ok = est.T > 0
+        assert ok.sum() > 50
+        assert np.allclose(est.B[ok], s ** 3, rtol=1e-12)
+        assert np.all(np.isnan(est.B[~ok]))
+
+
+def test_point_source_phase_closure():
+    # X_g = s exp(-2 pi i g.p0 / M): the phases cancel on every closed triangle
+    # (g1+g2+g3 = 0), so S = s^3 T exactly; a wrong closure sign would not cancel.
+    n = 48
+    gx, gy = coords(n)
+    p0 = (5.0, -3.0)
+    s = 1.3
+    X = s * np.exp(-2j * np.pi * (gx * p0[0] + gy * p0[1]) / 37.0)
+    q = oracle.ring_q(2 * np.pi * np.array([2.0, 6.0, 10.0, 15.0, 21.0]), 1.0)
+    ijk = oracle.triplets(q)
+    S, _, T = oracle.triple_bruteforce(X, full_mask(n), q, ijk)
+    assert np.all(T > 0)
+    assert np.allclose(S, s ** 3 * T, rtol=1e-11)
+    B = oracle.normalise(S, T)
+    assert np.allclose(B, s ** 3, rtol=1e-11)
+
+
+def test_ring_constant_fields_give_products():
+    n = 40
+    gx, gy = coords(n)
+    edges = 2 * np.pi * np.array([2.0, 5.0, 8.0, 12.0, 17.0])
+    q = oracle.ring_q(edges, 1.0)
+    r2 = gx.astype(np.int64) ** 2 + gy.astype(np.int64) ** 2
+    xm = np.array([1.5, -0.5, 2.0, 0.25])
+    X = np.zeros((n, n), np.complex128)
+    for m in range(4):
+        X[(r2 >= q[m]) & (r2 < q[m + 1])] = xm[m]
+    ijk = oracle.triplets(q)
+    S, _, T = oracle.triple_bruteforce(X, full_mask(n), q, ijk)
+    B = oracle.normalise(S, T, norm_A=2.0)
+    for t, (i, j, k) in enumerate(ijk):
+        if T[t] > 0:
+            assert B[t] == pytest.approx(xm[i] * xm[j] * xm[k] / 2.0, rel=1e-13)
+        else:
+            assert np.isnan(B[t])
+
+
+def test_rotation_and_reflection_invariance():
+    rng = np.random.default_rng(3)
+    n = 32
+    X = random_hermitian_grid(n, rng)
+    q = oracle.ring_q(2 * np.pi * np.array([2.0, 4.5, 7.0, 10.0, 14.0]), 1.0)
+    ijk = oracle.triplets(q)
+    f = full_mask(n)
+    S0, _, T0 = oracle.triple_bruteforce(X, f, q, ijk)
+    gx, gy = coords(n)
+    rot = X[(gx % n), (-gy) % n]           # X'(gx, gy) = X(-gy, gx): 90 degree rotation
+    ref = X[(-gy) % n, gx % n]             # X'(gx, gy) = X(gx, -gy): reflection
+    for Y in (rot, ref):
+        S1, _, T1 = oracle.triple_bruteforce(Y, f, q, ijk)
+        assert np.array_equal(T1, T0)
+        assert np.allclose(S1, S0, rtol=1e-11, atol=1e-11 * np.abs(S0).max())
+
+
+def test_counts_permutation_symmetric_and_real_sums():
+    inp = synth.make_inputs(0)
+    wl = inp.wl
+    est = oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+    perms = []
+    for (i, j, k) in est.ijk[:30]:
+        perms += [(i, j, k), (k, j, i), (j, k, i), (i, k, j)]
+    perms = np.array(perms, np.int32)
+    S, A, T = oracle.triple_bruteforce(est.X, est.filled, est.q, perms)
+    T4, S4 = T.reshape(-1, 4), S.reshape(-1, 4)
+    assert np.all(T4 == T4[:, :1])
+    assert np.allclose(S4, S4[:, :1], rtol=1e-11, atol=1e-12 * np.abs(S4).max())
+    # Hermitian grid -> imaginary parts cancel to rounding
+    assert np.max(np.abs(est.S.imag) / np.maximum(est.absum, 1e-300)) < 1e-13
+    # sum over k of T_ijk is bounded by |a_i||a_j| (each pair closes at most once)
+    assert np.all(T >= 0)
+
+
+def test_ellbar_hand_mask():
+    n = 32
+    f = np.zeros((n, n), np.uint8)
+    for (x, y) in [(3, 4), (-3, -4), (5, 0), (-5, 0), (1, 1), (-1, -1)]:
+        f[y % n, x % n] = 1
+    du = 2.0
+    q = oracle.ring_q(2 * np.pi * du * np.array([1.0, 3.0, 6.0]), du)
+    e = oracle.ellbar(f, q, du)
+    assert e[0] == pytest.approx(2 * np.pi * du * math.sqrt(2.0), rel=1e-15)
+    assert e[1] == pytest.approx(2 * np.pi * du * 5.0, rel=1e-15)
+
+
+def test_normalise_nan_on_empty():
+    B = oracle.normalise(np.array([6.0 + 0j, 1.0, 0.0]), np.array([3, 0, 2]), norm_A=2.0)
+    assert B[0] == 1.0 and np.isnan(B[1]) and B[2] == 0.0
+
+
+# ----------------------------------------------------------------- statistics
+
+
+def _grid_direct_B(delta_modes, q, ijk):
+    """Estimator on X_g = map modes directly (no gridding), full mask."""
+    n = delta_modes.shape[0]
+    S, _, T = oracle.triple_bruteforce(delta_modes, full_mask(n), q, ijk)
+    return oracle.normalise(S, T), T
+
+
+def _closed_form_expectation(P, q, ijk, f, M):
+    """Discrete Eq. bsana: E[X1 X2 X3] = 2 f M^2 (P1P2 + P2P3 + P3P1) per closed
+    triangle (Wick's theorem on the quadratic field, App. B, with sums for
+    integrals), averaged over the closed triangles of each ring triplet."""
+    n = P.shape[0]
+    half = n // 2 - 1
+    gx, gy = coords(n)
+    r2 = gx.astype(np.int64) ** 2 + gy.astype(np.int64) ** 2
+    inside = (np.abs(gx) <= half) & (np.abs(gy) <= half)
+    binmap = np.full((n, n), -1)
+    for m in range(len(q) - 1):
+        binmap[inside & (r2 >= q[m]) & (r2 < q[m + 1])] = m
+    cy, cx = np.nonzero(binmap >= 0)
+    g = np.stack([gx[cy, cx], gy[cy, cx]], 1)
+    bm = binmap[cy, cx]
+    Pc = P[cy, cx]
+    nb = len(q) - 1
+    acc = np.zeros((nb, nb, nb))
+    cnt = np.zeros((nb, nb, nb))
+    for a in range(len(g)):
+        h = -(g[a] + g)
+        ok = (np.abs(h[:, 0]) <= half) & (np.abs(h[:, 1]) <= half)
+        hk = np.full(len(g), -1)
+        hk[ok] = binmap[h[ok, 1] % n, h[ok, 0] % n]
+        sel = hk >= 0
+        P3 = P[h[sel, 1] % n, h[sel, 0] % n]
+        val = Pc[a] * Pc[sel] + Pc[sel] * P3 + P3 * Pc[a]
+        np.add.at(acc, (bm[a], bm[sel], hk[sel]), val)
+        np.add.at(cnt, (bm[a], bm[sel], hk[sel]), 1)
+    out = np.array([acc[i, j, k] / cnt[i, j, k] if cnt[i, j, k] else np.nan for i, j, k in ijk])
+    return 2.0 * f * M * M * out
+
+
+@pytest.mark.slow
+def test_gaussian_sky_has_zero_mean_and_quadratic_sky_matches_closed_form():
+    M = 32
+    q = oracle.ring_q(2 * np.pi * np.array([2.0, 4.0, 6.5, 9.0, 13.0]), 1.0)
+    ijk = oracle.triplets(q)
+    P = synth.power_spectrum_model(M)
+    R = 300
+    rng = np.random.default_rng(2024)
+    res = {}
+    for f in (0.0, 0.05):
+        Bs = []
+        for _ in range(R):
+            g = synth.gaussian_field(M, rng)
+            modes = synth.sky_modes(synth.quadratic_sky(g, f))
+            B, T = _grid_direct_B(modes, q, ijk)
+            Bs.append(B)
+        Bs = np.array(Bs)
+        res[f] = (Bs.mean(0), Bs.std(0, ddof=1) / np.sqrt(R))
+    mean0, se0 = res[0.0]
+    z0 = mean0 / se0
+    assert np.all(np.abs(z0) < 5.0)
+    expect = _closed_form_expectation(P, q, ijk, 0.05, M)
+    mean1, se1 = res[0.05]
+    z1 = (mean1 - expect) / se1
+    assert np.all(np.abs(z1) < 5.0)
+    # the pin has teeth: the signal is detected, and a halved or doubled
+    # prediction (a dropped Wick pairing, a wrong factor 2) is rejected
+    assert np.max(np.abs(mean1 / se1)) > 10.0
+    assert np.max(np.abs((mean1 - 0.5 * expect) / se1)) > 5.0
+    assert np.max(np.abs((mean1 - 2.0 * expect) / se1)) > 5.0
+
+
+# ----------------------------------------------------------------- paper constants
+
+
+def test_paper_constants():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+    vals = {}
+    for line in open(path):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split("=")
+            vals[k.strip()] = float(v)
+    c = oracle.beam_constants(vals["theta_F_deg"])
+    # Sec. 3 prints dU_g ~ 1 and a decorrelation factor of 0.89
+    assert round(c["du_g"], 0) == vals["du_g_approx"]
+    assert round(c["decorrelation"], 2) == vals["decorrelation"]
+    assert c["A"] == pytest.approx(np.pi * (0.6 * np.deg2rad(vals["theta_F_deg"])) ** 2 / 3)
