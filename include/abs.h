@@ -1,0 +1,194 @@
+/*
+ * abs.h -- C ABI of the GB300 (sm_103a) visibility-based binned angular
+ * bispectrum (ABS) estimator of arXiv 2412.02246, Sec. 2.
+ *
+ * Problem statement (Sec. 2): measured visibilities V(U_i) at baselines U_i
+ * are gridded on a uv grid of spacing dU (Eq. vg); for every ring a_m of the
+ * uv plane the ring-restricted grid is Fourier transformed to a real sky-plane
+ * field (Eqs. iFT, iFT_I); for every combination of three rings the triple
+ * product of the fields is summed over the sky plane and divided by the same
+ * sum for unit-mask fields (Eq. estimator_t).  The result is the binned
+ * bispectrum B(l1, l2, l3) together with the exact number of closed grid
+ * triangles behind each value.
+ *
+ * Conventions used by every entry point:
+ *
+ *  - Grid cells g = (gx, gy) with |gx|, |gy| <= n/2 - 1; grids are n x n,
+ *    row-major [gy][gx] in FFT order (index gx mod n, gy mod n; the row and
+ *    column at index n/2 stay zero).
+ *  - dU is used as its IEEE binary32 rounding everywhere.  The nearest grid
+ *    point of a baseline coordinate u is floor(fl32(fl32(u / dU) + 0.5)).
+ *  - Ring m holds the cells with Q_m <= |g|^2 < Q_{m+1},
+ *    Q_m = ceil((l_m / (2 pi dU))^2) evaluated in binary64 on the host
+ *    (half-open bins [l_m, l_{m+1}) in l = 2 pi |U_g|).
+ *  - Every visibility is also entered at -U_i with V* (the sky is real), so
+ *    the gridded data are Hermitian and every field is real.
+ *  - A cell is "filled" if at least one visibility's footprint covers it;
+ *    the estimator uses the weighted mean X_g = V_g / sum w on filled cells
+ *    and unit-mask fields for the denominator, which makes the denominator
+ *    N^2 T_ijk with T_ijk the integer number of ordered closed triangles
+ *    (g1 in a_i, g2 in a_j, g3 in a_k, all filled, g1 + g2 + g3 = 0).
+ *  - Triplets are (i, j, k) with i <= j <= k, listed in lexicographic order.
+ *  - The sky grid side N (n_fft) must be at least 3 R + 1, R the largest
+ *    |gx| of any ring cell, so that no wrapped triangle enters the sums.
+ *
+ * Ownership and execution: the caller allocates every d_* buffer on the
+ * context's device and keeps it alive until the context's stream has
+ * finished the call.  The context owns its workspaces, tables and caches and
+ * frees them in abs_destroy.  All device work is enqueued asynchronously on
+ * the context's stream.  A call returns ABS_OK once its work is enqueued, an
+ * error code for bad arguments (nothing enqueued), or ABS_ERR_CUDA for a
+ * launch failure.  Data-dependent device errors (for instance an unsorted
+ * triplet list) are latched into the context and reported by abs_sync.
+ * Contexts are not thread-safe; use one per host thread.  abs_last_error
+ * describes the last non-OK status.
+ */
+#ifndef ABS_GB300_H
+#define ABS_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ABS_OK = 0,
+    ABS_ERR_INVALID_ARG = 1,  /* argument outside the documented domain; nothing enqueued */
+    ABS_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed */
+    ABS_ERR_OOM = 3,          /* workspace allocation failed */
+    ABS_ERR_TIMEOUT = 4,      /* a bounded device-side wait gave up */
+    ABS_ERR_UNSUPPORTED = 5,  /* valid request this build does not implement */
+    ABS_ERR_DEVICE = 6        /* device-side validation failed (see abs_last_error) */
+} abs_status;
+
+enum { ABS_KERNEL_NGP = 0, ABS_KERNEL_GAUSS = 1 };
+enum { ABS_FP32 = 0, ABS_SPLIT_BF16 = 1 };
+
+#define ABS_MAX_BINS 254      /* ring ids fit a byte with one code to spare */
+#define ABS_MAX_RADIUS 3      /* largest Gaussian footprint half-width (cells) */
+#define ABS_MAX_FFT 4096      /* largest sky-grid side N */
+
+typedef struct abs_config {
+    int32_t n_grid;           /* uv grid side n: even, 8 <= n <= 8192 */
+    double du;                /* grid spacing dU_g in wavelengths (> 0), used as binary32 */
+    int32_t kernel;           /* ABS_KERNEL_GAUSS (default) or ABS_KERNEL_NGP (Eq. vg) */
+    double sigma_cells;       /* Gaussian kernel width in cells (> 0.25), GAUSS only */
+    int32_t radius_cells;     /* footprint half-width r in cells, 0..ABS_MAX_RADIUS, GAUSS only */
+    int32_t n_bins;           /* number of rings, 1..ABS_MAX_BINS */
+    const double *ell_edges;  /* host: n_bins + 1 strictly ascending edges in l, edges[0] > 0 */
+    int32_t n_fft;            /* sky grid N: 0 = smallest 2^a 3^b 5^c >= 3R+1; else a
+                                 2^a 3^b 5^c value with 3R+1 <= N <= ABS_MAX_FFT */
+    int32_t precision;        /* triple sums: ABS_FP32 or ABS_SPLIT_BF16 */
+    double norm_A;            /* A of Eq. estimator_t (> 0; 1 leaves B in grid units) */
+} abs_config;
+
+typedef struct abs_ctx abs_ctx;
+
+/* Create a context on CUDA device `device`; all work goes to `cuda_stream`
+ * (a cudaStream_t, NULL = the legacy default stream).  *out is set to NULL on error. */
+abs_status abs_create(abs_ctx **out, int32_t device, void *cuda_stream);
+
+/* Release the context and everything it owns (synchronises its stream first). */
+abs_status abs_destroy(abs_ctx *ctx);
+
+/* Human-readable text for the context's last non-OK status ("" if none). */
+const char *abs_last_error(const abs_ctx *ctx);
+
+/* Wait for the context's stream, then report any latched device-side error
+ * (ABS_ERR_DEVICE or ABS_ERR_TIMEOUT) and clear it. */
+abs_status abs_sync(abs_ctx *ctx);
+
+/* Host-only helpers (no device work).
+ * abs_ring_q: the n_bins + 1 integer thresholds Q_m (ring definition above).
+ * abs_fft_size: the sky-grid side N the estimator uses for cfg (resolves n_fft = 0).
+ * abs_triplets: the closing triplets of cfg in canonical order: i <= j <= k with
+ *   sqrt(Q_k) <= sqrt(Q_{i+1} - 1) + sqrt(Q_{j+1} - 1) (integer test), i.e. every
+ *   ring combination that can hold a closed triangle ("every possible
+ *   combination of three annular rings", Sec. 3).  Writes min(cap, count)
+ *   triplets as [t][3] int32 to ijk (may be NULL) and the count to *n_trip. */
+abs_status abs_ring_q(const abs_config *cfg, int64_t *q);
+abs_status abs_fft_size(const abs_config *cfg, int32_t *n_fft);
+abs_status abs_triplets(const abs_config *cfg, int32_t cap, int32_t *n_trip, int32_t *ijk);
+
+/* Stage 1, Eq. vg.  Grid n_vis visibilities: d_uv [n_vis][2] float32 (u, v)
+ * in wavelengths, d_vis [n_vis][2] float32 (re, im).  Outputs (n x n, FFT
+ * order, fully overwritten): d_grid [n*n][2] float32 = sum_i w V (mirror
+ * included), d_wsum [n*n] float32 = sum_i w, d_mask [n*n] uint8 = 1 on
+ * filled cells.  Visibilities with a non-finite coordinate are skipped;
+ * n_vis may be 0.  Accumulation is compensated FP32 per cell run with FP64
+ * cross-run sums. */
+abs_status abs_grid(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis, const float *d_uv,
+                    const float *d_vis, float *d_grid, float *d_wsum, uint8_t *d_mask);
+
+/* Stage 2, Eqs. iFT / iFT_I.  For every ring m: X = d_grid / d_wsum on the
+ * filled cells of a_m, zero elsewhere; D_m(p) = sum_g X_g exp(-2 pi i g.p / N)
+ * on the N x N sky grid (unnormalised forward DFT, real by Hermitian
+ * symmetry).  d_fields [n_bins][N][N] float32, row-major [p_y][p_x]. */
+abs_status abs_filter_fft(abs_ctx *ctx, const abs_config *cfg, const float *d_grid,
+                          const float *d_wsum, const uint8_t *d_mask, float *d_fields);
+
+/* Stages 3-4, Eq. estimator_t numerator and denominator.
+ * d_sum [n_trip] float64 (may be NULL): S_ijk = N^-2 sum_p D_i D_j D_k over the
+ *   sky grid (equal to the sum of X1 X2 X3 over the closed triangles), in
+ *   cfg->precision.
+ * d_count [n_trip] int64 (may be NULL): T_ijk, exact integer triangle counts
+ *   from d_mask (= N^-2 sum_p I_i I_j I_k for unit-mask fields).
+ * d_ijk [n_trip][3] int32 device, canonical order (i <= j <= k, lexicographic,
+ *   k < n_bins); a list that breaks this is reported by abs_sync. */
+abs_status abs_triple(abs_ctx *ctx, const abs_config *cfg, const float *d_fields,
+                      const uint8_t *d_mask, int32_t n_trip, const int32_t *d_ijk,
+                      double *d_sum, int64_t *d_count);
+
+/* Stage 5.  d_B[t] = d_sum[t] / (norm_A * d_count[t]) in FP64, NaN where the
+ * count is 0.  d_ellbar [n_bins] (may be NULL): mean l = 2 pi |g| dU over the
+ * filled cells of each ring (NaN for an empty ring), from d_mask. */
+abs_status abs_normalise(abs_ctx *ctx, const abs_config *cfg, int32_t n_trip,
+                         const double *d_sum, const int64_t *d_count, double *d_B,
+                         const uint8_t *d_mask, double *d_ellbar);
+
+/* Whole estimate, V -> B: stages 1-5 with workspaces owned by the context.
+ * d_ijk NULL = the canonical closing list of abs_triplets (n_trip must then
+ * equal its length).  Outputs: d_B [n_trip] f64, d_count [n_trip] i64,
+ * d_ellbar [n_bins] f64 (each may be NULL). */
+abs_status abs_estimate(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis, const float *d_uv,
+                        const float *d_vis, int32_t n_trip, const int32_t *d_ijk, double *d_B,
+                        int64_t *d_count, double *d_ellbar);
+
+/* abs_estimate on n_real realisations observed with the same baselines (the
+ * ensemble of Sec. 3): d_vis [n_real][n_vis][2] float32, d_B [n_real][n_trip],
+ * d_count [n_trip] (counts depend on the baselines only), d_ellbar [n_bins].
+ * The baseline plan, the ring tables and the counts are built once. */
+abs_status abs_estimate_many(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis,
+                             const float *d_uv, int32_t n_real, const float *d_vis,
+                             int32_t n_trip, const int32_t *d_ijk, double *d_B,
+                             int64_t *d_count, double *d_ellbar);
+
+/* abs_estimate_many from HOST memory: copies h_uv, h_vis to the device,
+ * runs, copies h_B, h_count, h_ellbar back, and waits for completion.
+ * h_ijk NULL = canonical list.  Pinned host buffers make the copies
+ * asynchronous; pageable ones work too. */
+abs_status abs_estimate_host(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis,
+                             const float *h_uv, int32_t n_real, const float *h_vis,
+                             int32_t n_trip, const int32_t *h_ijk, double *h_B,
+                             int64_t *h_count, double *h_ellbar);
+
+/* Stage profiler (tracing).  When on, every kernel launch of the context is
+ * bracketed by CUDA events on the context's stream and its device time is
+ * accumulated under a stage name ("grid", "fft_rows", "count_pairs", ...).
+ * abs_profile(ctx, 1) turns it on and clears the totals, abs_profile(ctx, 0)
+ * turns it off.  abs_profile_read waits for the stream, then writes up to
+ * `cap` entries (name, total ms, launches) and the number of stages to *n. */
+typedef struct abs_stage_time {
+    char name[32];
+    double ms;
+    int64_t launches;
+} abs_stage_time;
+
+abs_status abs_profile(abs_ctx *ctx, int32_t on);
+abs_status abs_profile_read(abs_ctx *ctx, int32_t cap, int32_t *n, abs_stage_time *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ABS_GB300_H */

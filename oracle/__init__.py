@@ -233,14 +233,16 @@ def fft_form(X, filled, q, ijk, N: int):
     return S, np.rint(T).astype(np.int64), T
 
 
-def min_fft_size(q: np.ndarray) -> int:
-    """Smallest 2^a 3^b 5^c >= 3 R + 1, R the largest |g_x| of any ring cell."""
-    R = int(np.floor(np.sqrt(float(q[-1] - 1))))
-    while R * R > q[-1] - 1:
-        R -= 1
-    while (R + 1) * (R + 1) <= q[-1] - 1:
-        R += 1
-    N = 3 * R + 1
+def min_fft_size(q: np.ndarray, n: int | None = None) -> int:
+    """Smallest 2^a 3^b 5^c >= max(3 R + 1, 8), R the largest |g_x| of any ring cell
+    on an n x n grid (|g_x|, |g_y| <= n/2 - 1), found by scanning the cells."""
+    half = (n // 2 - 1) if n else int(np.sqrt(float(q[-1]))) + 1
+    k = np.arange(-half, half + 1)
+    gx, gy = np.meshgrid(k, k)
+    r2 = gx.astype(np.int64) ** 2 + gy.astype(np.int64) ** 2
+    inring = (r2 >= q[0]) & (r2 < q[-1])
+    R = int(np.abs(gx[inring]).max()) if inring.any() else 0
+    N = max(3 * R + 1, 8)
     while True:
         m = N
         for p in (2, 3, 5):

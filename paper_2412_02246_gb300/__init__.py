@@ -1,0 +1,260 @@
+"""GB300 (sm_103a) visibility-based binned angular bispectrum estimator (arXiv 2412.02246).
+
+Thin ctypes binding over the C ABI declared in ``include/abs.h`` (libabs.so).
+Every step of the estimator runs in the library's CUDA kernels; this module
+only marshals arguments (torch device tensors -> pointers, the current CUDA
+stream).  There is no CPU fallback: if libabs.so is missing or cannot load,
+every call raises.
+
+Names follow the C ABI: ``abs_grid``, ``abs_filter_fft``, ``abs_triple``,
+``abs_normalise``, ``abs_estimate``, ``abs_estimate_many``,
+``abs_estimate_host``, plus the host helpers ``abs_ring_q``,
+``abs_fft_size``, ``abs_triplets``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libabs.so")
+
+ABS_OK, ABS_ERR_INVALID_ARG, ABS_ERR_CUDA, ABS_ERR_OOM, ABS_ERR_TIMEOUT, ABS_ERR_UNSUPPORTED, \
+    ABS_ERR_DEVICE = range(7)
+ABS_KERNEL_NGP, ABS_KERNEL_GAUSS = 0, 1
+ABS_FP32, ABS_SPLIT_BF16 = 0, 1
+_STATUS = {0: "ABS_OK", 1: "ABS_ERR_INVALID_ARG", 2: "ABS_ERR_CUDA", 3: "ABS_ERR_OOM",
+           4: "ABS_ERR_TIMEOUT", 5: "ABS_ERR_UNSUPPORTED", 6: "ABS_ERR_DEVICE"}
+
+
+class AbsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class abs_stage_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("ms", ctypes.c_double), ("launches", ctypes.c_int64)]
+
+
+class abs_config(ctypes.Structure):
+    _fields_ = [("n_grid", ctypes.c_int32), ("du", ctypes.c_double), ("kernel", ctypes.c_int32),
+                ("sigma_cells", ctypes.c_double), ("radius_cells", ctypes.c_int32),
+                ("n_bins", ctypes.c_int32), ("ell_edges", ctypes.POINTER(ctypes.c_double)),
+                ("n_fft", ctypes.c_int32), ("precision", ctypes.c_int32), ("norm_A", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libabs.so (built by ``paper_2412_02246_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libabs.so not built ({p}); run paper_2412_02246_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    C = ctypes.POINTER(abs_config)
+    sig = {
+        "abs_create": ([ctypes.POINTER(P), i32, P], ctypes.c_int),
+        "abs_destroy": ([P], ctypes.c_int),
+        "abs_last_error": ([P], ctypes.c_char_p),
+        "abs_sync": ([P], ctypes.c_int),
+        "abs_ring_q": ([C, P], ctypes.c_int),
+        "abs_fft_size": ([C, P], ctypes.c_int),
+        "abs_triplets": ([C, i32, P, P], ctypes.c_int),
+        "abs_grid": ([P, C, i64, P, P, P, P, P], ctypes.c_int),
+        "abs_filter_fft": ([P, C, P, P, P, P], ctypes.c_int),
+        "abs_triple": ([P, C, P, P, i32, P, P, P], ctypes.c_int),
+        "abs_normalise": ([P, C, i32, P, P, P, P, P], ctypes.c_int),
+        "abs_estimate": ([P, C, i64, P, P, i32, P, P, P, P], ctypes.c_int),
+        "abs_estimate_many": ([P, C, i64, P, i32, P, i32, P, P, P, P], ctypes.c_int),
+        "abs_estimate_host": ([P, C, i64, P, i32, P, i32, P, P, P, P], ctypes.c_int),
+        "abs_profile": ([P, i32], ctypes.c_int),
+        "abs_profile_read": ([P, i32, P, P], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------------ config
+
+
+@dataclass
+class Config:
+    n_grid: int
+    du: float
+    ell_edges: np.ndarray
+    kernel: int = ABS_KERNEL_GAUSS
+    sigma_cells: float = 1.0
+    radius_cells: int = 3
+    n_fft: int = 0
+    precision: int = ABS_FP32
+    norm_A: float = 1.0
+
+    def __post_init__(self):
+        self.ell_edges = np.ascontiguousarray(self.ell_edges, np.float64)
+        self._c = abs_config(int(self.n_grid), float(self.du), int(self.kernel), float(self.sigma_cells),
+                             int(self.radius_cells), len(self.ell_edges) - 1,
+                             self.ell_edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             int(self.n_fft), int(self.precision), float(self.norm_A))
+
+    @property
+    def n_bins(self) -> int:
+        return len(self.ell_edges) - 1
+
+    def ref(self):
+        return ctypes.byref(self._c)
+
+    @classmethod
+    def from_workload(cls, wl, **kw):
+        prec = ABS_SPLIT_BF16 if getattr(wl, "precision", "fp32") == "split_bf16" else ABS_FP32
+        args = dict(n_grid=wl.n_grid, du=wl.du, ell_edges=wl.ell_edges,
+                    kernel=ABS_KERNEL_NGP if wl.kernel == "ngp" else ABS_KERNEL_GAUSS,
+                    sigma_cells=wl.sigma_cells, radius_cells=wl.radius_cells, precision=prec)
+        args.update(kw)
+        return cls(**args)
+
+
+def _check(st: int, ctx=None, what: str = ""):
+    if st != ABS_OK:
+        msg = load().abs_last_error(ctx).decode() if ctx else ""
+        raise AbsError(st, f"{what}: {msg}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ host helpers
+
+
+def abs_ring_q(cfg: Config) -> np.ndarray:
+    q = np.zeros(cfg.n_bins + 1, np.int64)
+    _check(load().abs_ring_q(cfg.ref(), q.ctypes.data_as(ctypes.c_void_p)), what="abs_ring_q")
+    return q
+
+
+def abs_fft_size(cfg: Config) -> int:
+    n = ctypes.c_int32(0)
+    _check(load().abs_fft_size(cfg.ref(), ctypes.byref(n)), what="abs_fft_size")
+    return n.value
+
+
+def abs_triplets(cfg: Config) -> np.ndarray:
+    n = ctypes.c_int32(0)
+    _check(load().abs_triplets(cfg.ref(), 0, ctypes.byref(n), None), what="abs_triplets")
+    out = np.zeros((max(n.value, 1), 3), np.int32)
+    _check(load().abs_triplets(cfg.ref(), n.value, ctypes.byref(n), out.ctypes.data_as(ctypes.c_void_p)),
+           what="abs_triplets")
+    return out[:n.value]
+
+
+# ------------------------------------------------------------------ context
+
+
+class Context:
+    """An abs_ctx on one device, bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(load().abs_create(ctypes.byref(h), int(device), ctypes.c_void_p(stream.cuda_stream)),
+               what="abs_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().abs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self):
+        _check(load().abs_sync(self.h), self.h, "abs_sync")
+
+    def profile(self, on: bool = True):
+        """Turn the per-kernel CUDA-event profiler on (clearing totals) or off."""
+        _check(load().abs_profile(self.h, 1 if on else 0), self.h, "abs_profile")
+
+    def profile_read(self) -> dict:
+        """{stage: (total ms, launches)} accumulated since profile(True); waits for the stream."""
+        n = ctypes.c_int32(0)
+        _check(load().abs_profile_read(self.h, 0, ctypes.byref(n), None), self.h, "abs_profile_read")
+        arr = (abs_stage_time * max(n.value, 1))()
+        _check(load().abs_profile_read(self.h, n.value, ctypes.byref(n), arr), self.h, "abs_profile_read")
+        return {arr[i].name.decode(): (arr[i].ms, arr[i].launches) for i in range(n.value)}
+
+    # ------------- stages (torch CUDA tensors in, torch CUDA tensors out)
+    def abs_grid(self, cfg: Config, uv, vis, grid, wsum, mask):
+        _check(load().abs_grid(self.h, cfg.ref(), uv.shape[0], _ptr(uv), _ptr(vis), _ptr(grid), _ptr(wsum),
+                               _ptr(mask)), self.h, "abs_grid")
+
+    def abs_filter_fft(self, cfg: Config, grid, wsum, mask, fields):
+        _check(load().abs_filter_fft(self.h, cfg.ref(), _ptr(grid), _ptr(wsum), _ptr(mask), _ptr(fields)),
+               self.h, "abs_filter_fft")
+
+    def abs_triple(self, cfg: Config, fields, mask, ijk, sums=None, counts=None):
+        _check(load().abs_triple(self.h, cfg.ref(), _ptr(fields), _ptr(mask), ijk.shape[0], _ptr(ijk),
+                                 _ptr(sums), _ptr(counts)), self.h, "abs_triple")
+
+    def abs_normalise(self, cfg: Config, sums, counts, B, mask=None, ellbar=None):
+        _check(load().abs_normalise(self.h, cfg.ref(), sums.shape[0], _ptr(sums), _ptr(counts), _ptr(B),
+                                    _ptr(mask), _ptr(ellbar)), self.h, "abs_normalise")
+
+    def abs_estimate(self, cfg: Config, uv, vis, n_trip, ijk=None, B=None, counts=None, ellbar=None):
+        _check(load().abs_estimate(self.h, cfg.ref(), uv.shape[0], _ptr(uv), _ptr(vis), int(n_trip), _ptr(ijk),
+                                   _ptr(B), _ptr(counts), _ptr(ellbar)), self.h, "abs_estimate")
+
+    def abs_estimate_many(self, cfg: Config, uv, vis, n_trip, ijk=None, B=None, counts=None, ellbar=None):
+        n_real = vis.shape[0]
+        _check(load().abs_estimate_many(self.h, cfg.ref(), uv.shape[0], _ptr(uv), n_real, _ptr(vis), int(n_trip),
+                                        _ptr(ijk), _ptr(B), _ptr(counts), _ptr(ellbar)), self.h,
+               "abs_estimate_many")
+
+    def abs_estimate_host(self, cfg: Config, uv: np.ndarray, vis: np.ndarray, n_trip: int, ijk=None,
+                          B=None, counts=None, ellbar=None):
+        """Host arrays in and out (numpy or pinned torch CPU tensors); blocks until done."""
+        def hp(a):
+            if a is None:
+                return None
+            if hasattr(a, "data_ptr"):
+                return ctypes.c_void_p(a.data_ptr())
+            return a.ctypes.data_as(ctypes.c_void_p)
+        n_real = vis.shape[0] if vis.ndim == 3 else 1
+        _check(load().abs_estimate_host(self.h, cfg.ref(), uv.shape[0], hp(uv), n_real, hp(vis), int(n_trip),
+                                        hp(ijk), hp(B), hp(counts), hp(ellbar)), self.h, "abs_estimate_host")
+
+
+def estimate(cfg: Config, uv, vis, ctx: Context | None = None):
+    """Convenience: one realisation V -> (B, counts, ellbar) as torch CUDA tensors."""
+    import torch
+    ctx = ctx or Context(uv.device.index or 0)
+    ijk = abs_triplets(cfg)
+    nt = len(ijk)
+    dev = uv.device
+    B = torch.empty(nt, dtype=torch.float64, device=dev)
+    T = torch.empty(nt, dtype=torch.int64, device=dev)
+    E = torch.empty(cfg.n_bins, dtype=torch.float64, device=dev)
+    ctx.abs_estimate(cfg, uv, vis, nt, None, B, T, E)
+    return B, T, E, ijk

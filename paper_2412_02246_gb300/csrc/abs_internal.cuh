@@ -1,0 +1,122 @@
+// Internal declarations shared by the CUDA translation units of libabs.
+// Nothing here is part of the C ABI (include/abs.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/abs.h"
+
+namespace absk {
+
+// --------------------------------------------------------------------------- setup
+// Everything derived on the host from an abs_config (validated), cached per
+// context.  Integer ring thresholds, sky-grid size and its radix plan, ring
+// list offsets, the canonical triplet list.
+struct Setup {
+    int n = 0, half = 0;          // uv grid side, largest |g| component on the grid
+    float du = 0.f;               // binary32 grid spacing
+    int kernel = 1, r = 3;        // gridding kernel, footprint half-width
+    float s_hi = 0.5f, s_lo = 0.f;  // 1/(2 sigma^2) as a float pair
+    int nb = 0;                   // rings
+    std::vector<int64_t> q;       // nb+1 thresholds in |g|^2
+    std::vector<int> Rm;          // per ring: largest |g_x| of its cells on the grid (-1 empty)
+    int R = 0;                    // max over rings
+    int N = 0;                    // sky-grid side
+    std::vector<int> radices;     // N = prod(radices)
+    std::vector<int64_t> lat;     // lattice cells per ring (full annulus, on the grid)
+    std::vector<int64_t> lat_off; // nb+1 prefix offsets of lat
+    std::vector<int32_t> ijk;     // canonical closing triplets [t][3]
+    int precision = ABS_FP32;
+    double norm_A = 1.0;
+    // device copies (owned by the context)
+    int64_t *d_q = nullptr;
+    int64_t *d_lat_off = nullptr;
+    int32_t *d_ijk = nullptr;
+    float2 *d_tw = nullptr;       // exp(-2 pi i t / N), t < N
+    int32_t *d_Rm = nullptr;
+};
+
+// Host-side validation + derivation.  Returns ABS_OK or an error with text in err.
+abs_status make_setup(const abs_config *cfg, Setup &s, std::string &err);
+// Canonical closing triplets for thresholds q (shared by abs_triplets and Setup).
+void closing_triplets(const std::vector<int64_t> &q, std::vector<int32_t> &ijk);
+int64_t ring_threshold(double ell, float du);
+
+// --------------------------------------------------------------------------- context
+struct Workspace {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace absk
+
+struct abs_ctx {
+    // stage profiler: pending (name, start, stop) event triples, totals by name
+    struct Pending { std::string name; cudaEvent_t a, b; };
+    bool profiling = false;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    std::map<std::string, std::pair<double, int64_t>> stage_totals;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string last_error;
+    int32_t *d_err = nullptr;  // latched device error word: 0 ok, else a code below
+    std::map<std::string, absk::Workspace> ws;
+    std::map<std::string, std::unique_ptr<absk::Setup>> setups;
+};
+
+namespace absk {
+
+// Device error codes latched into ctx->d_err (first one wins).
+enum : int32_t {
+    DERR_NONE = 0,
+    DERR_TRIPLET_ORDER = 1,   // triplet list not canonical / bin out of range
+    DERR_TRIPLET_BIN = 2,
+    DERR_TIMEOUT = 3,
+};
+
+// Grow-only named workspace.  Returns nullptr on allocation failure.
+void *workspace(abs_ctx *ctx, const char *name, size_t bytes);
+abs_status fail(abs_ctx *ctx, abs_status st, const std::string &msg);
+abs_status check_launch(abs_ctx *ctx, const char *what);
+const Setup *get_setup(abs_ctx *ctx, const abs_config *cfg, abs_status &st);
+
+// --------------------------------------------------------------------------- stage launchers
+// Each enqueues on ctx->stream and returns ABS_OK / an error status.
+// Gridding is split in a per-baseline-set plan (sort by uv tile and cell) and a
+// per-realisation accumulation that reuses it.
+abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv);
+abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_vis,
+                                  float *d_grid, float *d_wsum, uint8_t *d_mask);
+abs_status launch_filter_fft(abs_ctx *ctx, const Setup &s, const float *d_grid,
+                             const float *d_wsum, const uint8_t *d_mask, float *d_fields);
+abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_fields,
+                              int32_t n_trip, const int32_t *d_ijk, double *d_sum);
+abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, int32_t n_trip,
+                         const int32_t *d_ijk, int64_t *d_count);
+abs_status launch_normalise(abs_ctx *ctx, const Setup &s, int32_t n_trip, const double *d_sum,
+                            const int64_t *d_count, double *d_B);
+abs_status launch_ellbar(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, double *d_ellbar);
+abs_status launch_check_triplets(abs_ctx *ctx, const Setup &s, int32_t n_trip,
+                                 const int32_t *d_ijk);
+
+// Brackets the kernel launches of its scope with events when profiling is on.
+struct StageTimer {
+    abs_ctx *ctx;
+    const char *name;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageTimer(abs_ctx *c, const char *n);
+    ~StageTimer();
+};
+
+// --------------------------------------------------------------------------- helpers
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace absk

@@ -1,0 +1,619 @@
+// C ABI of libabs: context, argument validation, host-side setup, and the
+// orchestration of the stage kernels (grid.cu, fft.cu, counts.cu, triple.cu).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "abs_internal.cuh"
+
+namespace absk {
+
+// ------------------------------------------------------------------ host arithmetic
+
+// Q_m = ceil((l_m / (2 pi dU))^2): the smallest integer |g|^2 of ring m, whose
+// cells satisfy l_m <= 2 pi |g| dU (Eq. iFT, l_g = 2 pi U_g).
+int64_t ring_threshold(double ell, float du) {
+    const double t = ell / (2.0 * M_PI * (double)du);
+    return (int64_t)std::ceil(t * t);
+}
+
+static int64_t isqrt64(int64_t v) {
+    if (v <= 0) return 0;
+    int64_t r = (int64_t)std::sqrt((double)v);
+    while (r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
+}
+
+static int64_t ceil_sqrt64(int64_t v) {
+    if (v <= 0) return 0;
+    const int64_t r = isqrt64(v);
+    return r * r == v ? r : r + 1;
+}
+
+// i <= j <= k that can close: sqrt(Q_k) <= sqrt(Q_{i+1}-1) + sqrt(Q_{j+1}-1).
+void closing_triplets(const std::vector<int64_t> &q, std::vector<int32_t> &ijk) {
+    const int nb = (int)q.size() - 1;
+    ijk.clear();
+    for (int i = 0; i < nb; ++i)
+        for (int j = i; j < nb; ++j)
+            for (int k = j; k < nb; ++k) {
+                const int64_t a = q[i + 1] - 1, b = q[j + 1] - 1;
+                const int64_t l = q[k] - a - b;
+                const bool closes = a >= 0 && b >= 0 && (l <= 0 || l * l <= 4 * a * b);
+                if (!closes) continue;
+                ijk.push_back(i);
+                ijk.push_back(j);
+                ijk.push_back(k);
+            }
+}
+
+static bool smooth235(int v) {
+    if (v < 1) return false;
+    for (int p : {2, 3, 5})
+        while (v % p == 0) v /= p;
+    return v == 1;
+}
+
+static std::vector<int> radix_plan(int N) {
+    std::vector<int> r;
+    while (N % 4 == 0) { r.push_back(4); N /= 4; }
+    while (N % 2 == 0) { r.push_back(2); N /= 2; }
+    while (N % 3 == 0) { r.push_back(3); N /= 3; }
+    while (N % 5 == 0) { r.push_back(5); N /= 5; }
+    return r;
+}
+
+abs_status make_setup(const abs_config *cfg, Setup &s, std::string &err) {
+    if (!cfg) { err = "cfg is NULL"; return ABS_ERR_INVALID_ARG; }
+    if (cfg->n_grid < 8 || cfg->n_grid > 8192 || (cfg->n_grid & 1)) {
+        err = "n_grid must be even and in [8, 8192]";
+        return ABS_ERR_INVALID_ARG;
+    }
+    const float du = (float)cfg->du;
+    if (!(cfg->du > 0.0) || !std::isfinite(cfg->du) || !(du > 0.f) || !std::isfinite(du)) {
+        err = "du must be finite and > 0 in binary32";
+        return ABS_ERR_INVALID_ARG;
+    }
+    if (cfg->kernel != ABS_KERNEL_GAUSS && cfg->kernel != ABS_KERNEL_NGP) {
+        err = "kernel must be ABS_KERNEL_GAUSS or ABS_KERNEL_NGP";
+        return ABS_ERR_INVALID_ARG;
+    }
+    if (cfg->kernel == ABS_KERNEL_GAUSS) {
+        if (!(cfg->sigma_cells > 0.25) || !std::isfinite(cfg->sigma_cells)) {
+            err = "sigma_cells must be finite and > 0.25";
+            return ABS_ERR_INVALID_ARG;
+        }
+        if (cfg->radius_cells < 0 || cfg->radius_cells > ABS_MAX_RADIUS) {
+            err = "radius_cells must be in [0, 3]";
+            return ABS_ERR_INVALID_ARG;
+        }
+    }
+    if (cfg->n_bins < 1 || cfg->n_bins > ABS_MAX_BINS) { err = "n_bins must be in [1, 254]"; return ABS_ERR_INVALID_ARG; }
+    if (!cfg->ell_edges) { err = "ell_edges is NULL"; return ABS_ERR_INVALID_ARG; }
+    for (int m = 0; m <= cfg->n_bins; ++m) {
+        const double e = cfg->ell_edges[m];
+        if (!std::isfinite(e) || !(e > 0.0) || (m > 0 && !(e > cfg->ell_edges[m - 1]))) {
+            err = "ell_edges must be finite, > 0 and strictly ascending";
+            return ABS_ERR_INVALID_ARG;
+        }
+    }
+    if (cfg->precision != ABS_FP32 && cfg->precision != ABS_SPLIT_BF16) {
+        err = "precision must be ABS_FP32 or ABS_SPLIT_BF16";
+        return ABS_ERR_INVALID_ARG;
+    }
+    if (!(cfg->norm_A > 0.0) || !std::isfinite(cfg->norm_A)) { err = "norm_A must be finite and > 0"; return ABS_ERR_INVALID_ARG; }
+
+    s.n = cfg->n_grid;
+    s.half = s.n / 2 - 1;
+    s.du = du;
+    s.kernel = cfg->kernel;
+    s.r = cfg->kernel == ABS_KERNEL_NGP ? 0 : cfg->radius_cells;
+    if (cfg->kernel == ABS_KERNEL_GAUSS) {
+        const double sc = 1.0 / (2.0 * cfg->sigma_cells * cfg->sigma_cells);
+        s.s_hi = (float)sc;
+        s.s_lo = (float)(sc - (double)s.s_hi);
+    }
+    s.nb = cfg->n_bins;
+    s.q.resize(s.nb + 1);
+    for (int m = 0; m <= s.nb; ++m) s.q[m] = ring_threshold(cfg->ell_edges[m], du);
+    if (s.q[s.nb] > (int64_t)1 << 40) { err = "l range too large for the uv grid spacing"; return ABS_ERR_INVALID_ARG; }
+    // largest |g_x| of a ring cell on the grid, per ring
+    s.Rm.assign(s.nb, -1);
+    s.R = 0;
+    for (int m = 0; m < s.nb; ++m) {
+        const int64_t lo = s.q[m], hi = s.q[m + 1] - 1;
+        if (hi < lo) continue;
+        for (int64_t x = std::min<int64_t>(s.half, isqrt64(hi)); x >= 0; --x) {
+            const int64_t ylo = ceil_sqrt64(lo - x * x);
+            const int64_t yhi = std::min<int64_t>(s.half, isqrt64(hi - x * x));
+            if (hi - x * x >= 0 && ylo <= yhi) {
+                s.Rm[m] = (int)x;
+                break;
+            }
+        }
+        s.R = std::max(s.R, s.Rm[m]);
+    }
+    const int Nmin = std::max(3 * s.R + 1, 8);
+    if (cfg->n_fft == 0) {
+        int N = Nmin;
+        while (!smooth235(N)) ++N;
+        s.N = N;
+    } else {
+        if (!smooth235(cfg->n_fft) || cfg->n_fft < Nmin) {
+            err = "n_fft must be a 2^a 3^b 5^c value >= 3R+1 (R = " + std::to_string(s.R) + ")";
+            return ABS_ERR_INVALID_ARG;
+        }
+        s.N = cfg->n_fft;
+    }
+    if (s.N > ABS_MAX_FFT) { err = "sky grid side N exceeds 4096 (reduce the l range or coarsen du)"; return ABS_ERR_UNSUPPORTED; }
+    s.radices = radix_plan(s.N);
+    // lattice cells per ring on the grid (capacity of the ring lists)
+    s.lat.assign(s.nb, 0);
+    for (int y = -s.R; y <= s.R; ++y)
+        for (int x = -s.R; x <= s.R; ++x) {
+            const int64_t r2 = (int64_t)x * x + (int64_t)y * y;
+            if (r2 < s.q[0] || r2 >= s.q[s.nb]) continue;
+            int m = 0;
+            while (r2 >= s.q[m + 1]) ++m;
+            s.lat[m]++;
+        }
+    s.lat_off.assign(s.nb + 1, 0);
+    for (int m = 0; m < s.nb; ++m) s.lat_off[m + 1] = s.lat_off[m] + s.lat[m];
+    closing_triplets(s.q, s.ijk);
+    s.precision = cfg->precision;
+    s.norm_A = cfg->norm_A;
+    return ABS_OK;
+}
+
+// ------------------------------------------------------------------ context helpers
+
+abs_status fail(abs_ctx *ctx, abs_status st, const std::string &msg) {
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+abs_status check_launch(abs_ctx *ctx, const char *what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, ABS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return ABS_OK;
+}
+
+void *workspace(abs_ctx *ctx, const char *name, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    Workspace &w = ctx->ws[name];
+    if (w.bytes >= bytes) return w.p;
+    if (w.p) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(w.p);
+        w.p = nullptr;
+        w.bytes = 0;
+    }
+    const size_t want = bytes + bytes / 8;   // some headroom against regrowth
+    if (cudaMalloc(&w.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        w.p = nullptr;
+        return nullptr;
+    }
+    w.bytes = want;
+    return w.p;
+}
+
+static std::string setup_key(const abs_config *c) {
+    std::string k;
+    auto put = [&k](const void *p, size_t n) { k.append((const char *)p, n); };
+    put(&c->n_grid, sizeof c->n_grid);
+    put(&c->du, sizeof c->du);
+    put(&c->kernel, sizeof c->kernel);
+    put(&c->sigma_cells, sizeof c->sigma_cells);
+    put(&c->radius_cells, sizeof c->radius_cells);
+    put(&c->n_bins, sizeof c->n_bins);
+    put(c->ell_edges, sizeof(double) * (c->n_bins + 1));
+    put(&c->n_fft, sizeof c->n_fft);
+    put(&c->precision, sizeof c->precision);
+    put(&c->norm_A, sizeof c->norm_A);
+    return k;
+}
+
+template <class T>
+static T *upload(const std::vector<T> &v) {
+    T *d = nullptr;
+    const size_t bytes = sizeof(T) * std::max<size_t>(v.size(), 1);
+    if (cudaMalloc(&d, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    if (!v.empty() && cudaMemcpy(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(d);
+        return nullptr;
+    }
+    return d;
+}
+
+static void free_setup(Setup &s) {
+    cudaFree(s.d_q);
+    cudaFree(s.d_lat_off);
+    cudaFree(s.d_ijk);
+    cudaFree(s.d_tw);
+    cudaFree(s.d_Rm);
+    s.d_q = nullptr;
+    s.d_lat_off = nullptr;
+    s.d_ijk = nullptr;
+    s.d_tw = nullptr;
+    s.d_Rm = nullptr;
+}
+
+const Setup *get_setup(abs_ctx *ctx, const abs_config *cfg, abs_status &st) {
+    std::string err;
+    if (!cfg || !cfg->ell_edges || cfg->n_bins < 1 || cfg->n_bins > ABS_MAX_BINS) {
+        st = fail(ctx, ABS_ERR_INVALID_ARG, "invalid config (ell_edges / n_bins)");
+        return nullptr;
+    }
+    const std::string key = setup_key(cfg);
+    auto it = ctx->setups.find(key);
+    if (it != ctx->setups.end()) {
+        st = ABS_OK;
+        return it->second.get();
+    }
+    std::unique_ptr<Setup> s(new Setup);
+    st = make_setup(cfg, *s, err);
+    if (st != ABS_OK) {
+        fail(ctx, st, err);
+        return nullptr;
+    }
+    std::vector<float2> tw(s->N);
+    for (int t = 0; t < s->N; ++t) {
+        const double a = 2.0 * M_PI * (double)t / (double)s->N;
+        tw[t] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
+    }
+    s->d_q = upload(s->q);
+    s->d_lat_off = upload(s->lat_off);
+    s->d_ijk = upload(s->ijk);
+    s->d_tw = upload(tw);
+    s->d_Rm = upload(std::vector<int32_t>(s->Rm.begin(), s->Rm.end()));
+    if (!s->d_q || !s->d_lat_off || !s->d_ijk || !s->d_tw || !s->d_Rm) {
+        free_setup(*s);
+        st = fail(ctx, ABS_ERR_OOM, "setup tables");
+        return nullptr;
+    }
+    Setup *raw = s.get();
+    ctx->setups[key] = std::move(s);
+    st = ABS_OK;
+    return raw;
+}
+
+static cudaEvent_t pool_get(abs_ctx *ctx) {
+    if (!ctx->event_pool.empty()) {
+        cudaEvent_t e = ctx->event_pool.back();
+        ctx->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+StageTimer::StageTimer(abs_ctx *c, const char *n) : ctx(c), name(n) {
+    if (!ctx->profiling) return;
+    a = pool_get(ctx);
+    b = pool_get(ctx);
+    if (a) cudaEventRecord(a, ctx->stream);
+}
+
+StageTimer::~StageTimer() {
+    if (!a || !b) return;
+    cudaEventRecord(b, ctx->stream);
+    ctx->pending.push_back({name, a, b});
+}
+
+static void profile_drain(abs_ctx *ctx) {
+    for (auto &p : ctx->pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            auto &t = ctx->stage_totals[p.name];
+            t.first += ms;
+            t.second += 1;
+        }
+        cudaGetLastError();
+        ctx->event_pool.push_back(p.a);
+        ctx->event_pool.push_back(p.b);
+    }
+    ctx->pending.clear();
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace absk
+
+using namespace absk;
+
+#define ABS_CHECK(x)                      \
+    do {                                  \
+        const abs_status _st = (x);       \
+        if (_st != ABS_OK) return _st;    \
+    } while (0)
+
+extern "C" {
+
+abs_status abs_create(abs_ctx **out, int32_t device, void *cuda_stream) {
+    if (!out) return ABS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return ABS_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(device);
+    abs_ctx *ctx = new abs_ctx;
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&ctx->d_err, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(ctx->d_err, 0, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return ABS_ERR_OOM;
+    }
+    *out = ctx;
+    return ABS_OK;
+}
+
+abs_status abs_destroy(abs_ctx *ctx) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    {
+        DeviceGuard g(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        for (auto &kv : ctx->ws) cudaFree(kv.second.p);
+        for (auto &kv : ctx->setups) free_setup(*kv.second);
+        cudaFree(ctx->d_err);
+        for (auto &p : ctx->pending) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    }
+    delete ctx;
+    return ABS_OK;
+}
+
+const char *abs_last_error(const abs_ctx *ctx) { return ctx ? ctx->last_error.c_str() : "no context"; }
+
+abs_status abs_sync(abs_ctx *ctx) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        return fail(ctx, ABS_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(cudaGetLastError()));
+    int32_t e = 0;
+    if (cudaMemcpy(&e, ctx->d_err, sizeof e, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(ctx, ABS_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+    if (e == DERR_NONE) return ABS_OK;
+    cudaMemset(ctx->d_err, 0, sizeof(int32_t));
+    if (e == DERR_TIMEOUT) return fail(ctx, ABS_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (e == DERR_TRIPLET_ORDER) return fail(ctx, ABS_ERR_DEVICE, "triplet list is not in canonical order");
+    return fail(ctx, ABS_ERR_DEVICE, "triplet list holds a bin outside 0 <= i <= j <= k < n_bins");
+}
+
+abs_status abs_profile(abs_ctx *ctx, int32_t on) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    profile_drain(ctx);
+    ctx->stage_totals.clear();
+    ctx->profiling = on != 0;
+    return ABS_OK;
+}
+
+abs_status abs_profile_read(abs_ctx *ctx, int32_t cap, int32_t *n, abs_stage_time *out) {
+    if (!ctx || !n || cap < 0) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    profile_drain(ctx);
+    int32_t k = 0;
+    for (auto &kv : ctx->stage_totals) {
+        if (out && k < cap) {
+            std::memset(out[k].name, 0, sizeof out[k].name);
+            std::strncpy(out[k].name, kv.first.c_str(), sizeof out[k].name - 1);
+            out[k].ms = kv.second.first;
+            out[k].launches = kv.second.second;
+        }
+        ++k;
+    }
+    *n = k;
+    return ABS_OK;
+}
+
+abs_status abs_ring_q(const abs_config *cfg, int64_t *q) {
+    if (!q) return ABS_ERR_INVALID_ARG;
+    Setup s;
+    std::string err;
+    ABS_CHECK(make_setup(cfg, s, err));
+    for (int m = 0; m <= s.nb; ++m) q[m] = s.q[m];
+    return ABS_OK;
+}
+
+abs_status abs_fft_size(const abs_config *cfg, int32_t *n_fft) {
+    if (!n_fft) return ABS_ERR_INVALID_ARG;
+    Setup s;
+    std::string err;
+    ABS_CHECK(make_setup(cfg, s, err));
+    *n_fft = s.N;
+    return ABS_OK;
+}
+
+abs_status abs_triplets(const abs_config *cfg, int32_t cap, int32_t *n_trip, int32_t *ijk) {
+    if (!n_trip || cap < 0) return ABS_ERR_INVALID_ARG;
+    Setup s;
+    std::string err;
+    ABS_CHECK(make_setup(cfg, s, err));
+    const int32_t n = (int32_t)(s.ijk.size() / 3);
+    *n_trip = n;
+    if (ijk) std::memcpy(ijk, s.ijk.data(), sizeof(int32_t) * 3 * std::min(n, cap));
+    return ABS_OK;
+}
+
+abs_status abs_grid(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis, const float *d_uv,
+                    const float *d_vis, float *d_grid, float *d_wsum, uint8_t *d_mask) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    abs_status st;
+    const Setup *s = get_setup(ctx, cfg, st);
+    if (!s) return st;
+    if (n_vis < 0 || n_vis > 0x7fffffffLL) return fail(ctx, ABS_ERR_INVALID_ARG, "n_vis must be in [0, 2^31)");
+    if ((n_vis > 0 && (!d_uv || !d_vis)) || !d_grid || !d_wsum || !d_mask)
+        return fail(ctx, ABS_ERR_INVALID_ARG, "NULL buffer");
+    ABS_CHECK(launch_grid_plan(ctx, *s, n_vis, d_uv));
+    return launch_grid_accumulate(ctx, *s, n_vis, d_vis, d_grid, d_wsum, d_mask);
+}
+
+abs_status abs_filter_fft(abs_ctx *ctx, const abs_config *cfg, const float *d_grid, const float *d_wsum,
+                          const uint8_t *d_mask, float *d_fields) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    abs_status st;
+    const Setup *s = get_setup(ctx, cfg, st);
+    if (!s) return st;
+    if (!d_grid || !d_wsum || !d_mask || !d_fields) return fail(ctx, ABS_ERR_INVALID_ARG, "NULL buffer");
+    return launch_filter_fft(ctx, *s, d_grid, d_wsum, d_mask, d_fields);
+}
+
+abs_status abs_triple(abs_ctx *ctx, const abs_config *cfg, const float *d_fields, const uint8_t *d_mask,
+                      int32_t n_trip, const int32_t *d_ijk, double *d_sum, int64_t *d_count) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    abs_status st;
+    const Setup *s = get_setup(ctx, cfg, st);
+    if (!s) return st;
+    if (n_trip < 0) return fail(ctx, ABS_ERR_INVALID_ARG, "n_trip < 0");
+    if (n_trip > 0 && !d_ijk) return fail(ctx, ABS_ERR_INVALID_ARG, "d_ijk is NULL");
+    if (d_sum && !d_fields) return fail(ctx, ABS_ERR_INVALID_ARG, "d_fields is NULL");
+    if (d_count && !d_mask) return fail(ctx, ABS_ERR_INVALID_ARG, "d_mask is NULL");
+    ABS_CHECK(launch_check_triplets(ctx, *s, n_trip, d_ijk));
+    if (d_sum) ABS_CHECK(launch_triple_sums(ctx, *s, d_fields, n_trip, d_ijk, d_sum));
+    if (d_count) ABS_CHECK(launch_counts(ctx, *s, d_mask, n_trip, d_ijk, d_count));
+    return ABS_OK;
+}
+
+abs_status abs_normalise(abs_ctx *ctx, const abs_config *cfg, int32_t n_trip, const double *d_sum,
+                         const int64_t *d_count, double *d_B, const uint8_t *d_mask, double *d_ellbar) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    abs_status st;
+    const Setup *s = get_setup(ctx, cfg, st);
+    if (!s) return st;
+    if (n_trip < 0 || (n_trip > 0 && (!d_sum || !d_count || !d_B)))
+        return fail(ctx, ABS_ERR_INVALID_ARG, "NULL buffer or n_trip < 0");
+    if (d_ellbar && !d_mask) return fail(ctx, ABS_ERR_INVALID_ARG, "d_mask is NULL");
+    ABS_CHECK(launch_normalise(ctx, *s, n_trip, d_sum, d_count, d_B));
+    if (d_ellbar) ABS_CHECK(launch_ellbar(ctx, *s, d_mask, d_ellbar));
+    return ABS_OK;
+}
+
+static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv,
+                                int32_t n_real, const float *d_vis, int32_t n_trip,
+                                const int32_t *d_ijk, double *d_B, int64_t *d_count, double *d_ellbar) {
+    const int64_t cells = (int64_t)s.n * s.n;
+    const int64_t P = (int64_t)s.N * s.N;
+    float *grid = (float *)workspace(ctx, "est.grid", sizeof(float) * 2 * cells);
+    float *wsum = (float *)workspace(ctx, "est.wsum", sizeof(float) * cells);
+    uint8_t *mask = (uint8_t *)workspace(ctx, "est.mask", cells);
+    float *fields = (float *)workspace(ctx, "est.fields", sizeof(float) * (size_t)s.nb * P);
+    double *sum = (double *)workspace(ctx, "est.sum", sizeof(double) * std::max(n_trip, 1));
+    int64_t *count = d_count ? d_count : (int64_t *)workspace(ctx, "est.count", sizeof(int64_t) * std::max(n_trip, 1));
+    if (!grid || !wsum || !mask || !fields || !sum || !count) return fail(ctx, ABS_ERR_OOM, "estimate workspace");
+    ABS_CHECK(launch_check_triplets(ctx, s, n_trip, d_ijk));
+    ABS_CHECK(launch_grid_plan(ctx, s, n_vis, d_uv));
+    for (int32_t r = 0; r < n_real; ++r) {
+        ABS_CHECK(launch_grid_accumulate(ctx, s, n_vis, d_vis + (size_t)r * 2 * n_vis, grid, wsum, mask));
+        if (r == 0) {
+            // the filled mask depends on the baselines only: counts and mean l once
+            ABS_CHECK(launch_counts(ctx, s, mask, n_trip, d_ijk, count));
+            if (d_ellbar) ABS_CHECK(launch_ellbar(ctx, s, mask, d_ellbar));
+        }
+        ABS_CHECK(launch_filter_fft(ctx, s, grid, wsum, mask, fields));
+        ABS_CHECK(launch_triple_sums(ctx, s, fields, n_trip, d_ijk, sum));
+        if (d_B) ABS_CHECK(launch_normalise(ctx, s, n_trip, sum, count, d_B + (size_t)r * n_trip));
+    }
+    return ABS_OK;
+}
+
+static abs_status estimate_args(abs_ctx *ctx, const Setup &s, int64_t n_vis, const void *uv,
+                                int32_t n_real, const void *vis, int32_t n_trip, const int32_t *&ijk) {
+    if (n_vis < 0 || n_vis > 0x7fffffffLL) return fail(ctx, ABS_ERR_INVALID_ARG, "n_vis must be in [0, 2^31)");
+    if (n_real < 1) return fail(ctx, ABS_ERR_INVALID_ARG, "n_real must be >= 1");
+    if (n_vis > 0 && (!uv || !vis)) return fail(ctx, ABS_ERR_INVALID_ARG, "NULL visibility buffer");
+    if (n_trip < 0) return fail(ctx, ABS_ERR_INVALID_ARG, "n_trip < 0");
+    if (!ijk) {
+        if (n_trip != (int32_t)(s.ijk.size() / 3))
+            return fail(ctx, ABS_ERR_INVALID_ARG, "n_trip must equal the canonical triplet count when d_ijk is NULL");
+        ijk = s.d_ijk;
+    }
+    return ABS_OK;
+}
+
+abs_status abs_estimate_many(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis, const float *d_uv,
+                             int32_t n_real, const float *d_vis, int32_t n_trip, const int32_t *d_ijk,
+                             double *d_B, int64_t *d_count, double *d_ellbar) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    abs_status st;
+    const Setup *s = get_setup(ctx, cfg, st);
+    if (!s) return st;
+    ABS_CHECK(estimate_args(ctx, *s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk));
+    return estimate_many(ctx, *s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar);
+}
+
+abs_status abs_estimate(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis, const float *d_uv,
+                        const float *d_vis, int32_t n_trip, const int32_t *d_ijk, double *d_B,
+                        int64_t *d_count, double *d_ellbar) {
+    return abs_estimate_many(ctx, cfg, n_vis, d_uv, 1, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar);
+}
+
+abs_status abs_estimate_host(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis, const float *h_uv,
+                             int32_t n_real, const float *h_vis, int32_t n_trip, const int32_t *h_ijk,
+                             double *h_B, int64_t *h_count, double *h_ellbar) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    abs_status st;
+    const Setup *s = get_setup(ctx, cfg, st);
+    if (!s) return st;
+    const int32_t *probe = h_ijk;
+    ABS_CHECK(estimate_args(ctx, *s, n_vis, h_uv, n_real, h_vis, n_trip, probe));
+    const size_t uvb = sizeof(float) * 2 * (size_t)n_vis, visb = uvb * (size_t)n_real;
+    float *d_uv = (float *)workspace(ctx, "host.uv", uvb);
+    float *d_vis = (float *)workspace(ctx, "host.vis", visb);
+    double *d_B = (double *)workspace(ctx, "host.B", sizeof(double) * (size_t)std::max(n_trip, 1) * n_real);
+    int64_t *d_count = (int64_t *)workspace(ctx, "host.count", sizeof(int64_t) * std::max(n_trip, 1));
+    double *d_ellbar = (double *)workspace(ctx, "host.ellbar", sizeof(double) * s->nb);
+    const int32_t *d_ijk = s->d_ijk;
+    if (h_ijk) {
+        int32_t *p = (int32_t *)workspace(ctx, "host.ijk", sizeof(int32_t) * 3 * std::max(n_trip, 1));
+        if (!p) return fail(ctx, ABS_ERR_OOM, "host staging");
+        if (n_trip > 0) cudaMemcpyAsync(p, h_ijk, sizeof(int32_t) * 3 * n_trip, cudaMemcpyHostToDevice, ctx->stream);
+        d_ijk = p;
+    }
+    if (!d_uv || !d_vis || !d_B || !d_count || !d_ellbar) return fail(ctx, ABS_ERR_OOM, "host staging");
+    if (n_vis > 0) {
+        cudaMemcpyAsync(d_uv, h_uv, uvb, cudaMemcpyHostToDevice, ctx->stream);
+        cudaMemcpyAsync(d_vis, h_vis, visb, cudaMemcpyHostToDevice, ctx->stream);
+    }
+    ABS_CHECK(check_launch(ctx, "host to device copies"));
+    ABS_CHECK(estimate_many(ctx, *s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar));
+    if (h_B && n_trip > 0)
+        cudaMemcpyAsync(h_B, d_B, sizeof(double) * (size_t)n_trip * n_real, cudaMemcpyDeviceToHost, ctx->stream);
+    if (h_count && n_trip > 0)
+        cudaMemcpyAsync(h_count, d_count, sizeof(int64_t) * n_trip, cudaMemcpyDeviceToHost, ctx->stream);
+    if (h_ellbar) cudaMemcpyAsync(h_ellbar, d_ellbar, sizeof(double) * s->nb, cudaMemcpyDeviceToHost, ctx->stream);
+    ABS_CHECK(check_launch(ctx, "device to host copies"));
+    return abs_sync(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,378 @@
+// Stage 4: exact triangle counts, the denominator of Eq. estimator_t.
+//
+// With unit-mask fields I_m (X = 1 on the filled cells of a_m) the sum
+// N^-2 sum_p I_i I_j I_k is the number T_ijk of ordered closed triangles
+// (g1 in a_i, g2 in a_j, g3 in a_k, all filled, g1 + g2 + g3 = 0).  FP32 or
+// even FP64 pixel sums cannot return that integer exactly at these sizes, so
+// it is counted directly in integers:
+//
+//   T_ijk = 2 #{ (g1, g2) : g1 in F_i upper half plane, g2 in F_j, g1 + g2 in F_k }
+//
+// (F_m = filled cells of ring m.  F_k is symmetric under g -> -g, so the
+// third vertex -(g1+g2) is in F_k iff g1 + g2 is; negating a triangle maps
+// g1 to the other half plane, hence the factor 2; the origin is in no ring.)
+//
+// Ring lists are built row-major, so the upper half plane of each ring is
+// the second half of its list.  A byte map over [-2R, 2R]^2 holds 1 + ring
+// id of every filled ring cell (0 elsewhere), so a pair is classified by one
+// integer add and one byte load, with no bounds test.  One CTA per (i, j,
+// chunk of g1) streams all of F_j through shared memory; each thread keeps
+// run-length state for its g1 cells (consecutive g2 in row order usually
+// land in the same ring) and adds finished runs into a lane-private
+// shared-memory histogram over k, which is reduced into an int64 (i, j, k)
+// table at the end.
+#include "abs_internal.cuh"
+
+namespace absk {
+namespace {
+
+constexpr int G1 = 4;            // g1 cells per thread
+constexpr int CT = 256;          // threads per counting CTA (max)
+constexpr int STAGE = 2048;      // g2 cells staged per pass
+constexpr unsigned FULL = 0xffffffffu;
+
+struct CountGeom {
+    int n, half, nb, R, W;       // W = 4R + 1
+    int64_t base;                // 2R W + 2R
+};
+
+__device__ __forceinline__ int64_t cell_index(int n, int gx, int gy) {
+    return (int64_t)(gy < 0 ? gy + n : gy) * n + (gx < 0 ? gx + n : gx);
+}
+
+// One CTA per ring: compact the filled cells of a_m in row-major order.
+__global__ void __launch_bounds__(1024) k_ring_lists(CountGeom G, const int64_t *__restrict__ q,
+                                                     const int32_t *__restrict__ Rm,
+                                                     const int64_t *__restrict__ lat_off,
+                                                     const uint8_t *__restrict__ mask,
+                                                     short2 *__restrict__ lists,
+                                                     int32_t *__restrict__ counts,
+                                                     uint8_t *__restrict__ binmap) {
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t carry_s;
+    const int m = blockIdx.x;
+    const int Rr = Rm[m];
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    if (Rr < 0) {
+        if (threadIdx.x == 0) counts[m] = 0;
+        return;
+    }
+    const int side = 2 * Rr + 1;
+    const int64_t total = (int64_t)side * side;
+    const int64_t q0 = q[m], q1 = q[m + 1];
+    short2 *out = lists + lat_off[m];
+    const int64_t cap = lat_off[m + 1] - lat_off[m];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t b = 0; b < total; b += blockDim.x) {
+        const int64_t idx = b + threadIdx.x;
+        bool on = false;
+        int x = 0, y = 0;
+        if (idx < total) {
+            y = (int)(idx / side) - Rr;
+            x = (int)(idx % side) - Rr;
+            const int64_t r2 = (int64_t)x * x + (int64_t)y * y;
+            on = r2 >= q0 && r2 < q1 && x >= -G.half && x <= G.half && y >= -G.half &&
+                 y <= G.half && mask[cell_index(G.n, x, y)];
+        }
+        const unsigned bal = __ballot_sync(FULL, on);
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < warp) before += wsum[w];
+            tot += wsum[w];
+        }
+        const int pos = carry_s + before + __popc(bal & ((1u << lane) - 1u));
+        if (on && pos < cap) {
+            out[pos] = make_short2((short)x, (short)y);
+            binmap[(int64_t)(y + 2 * G.R) * G.W + (x + 2 * G.R)] = (uint8_t)(m + 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) counts[m] = (int32_t)min((int64_t)carry_s, cap);
+}
+
+// One block: the (i, j, first g1) work items for every distinct (i, j) row of
+// the triplet list.  A list that is not canonical latches an error.
+__global__ void __launch_bounds__(1024) k_count_items(int nb, int32_t n_trip,
+                                                      const int32_t *__restrict__ ijk,
+                                                      const int32_t *__restrict__ counts, int chunk,
+                                                      int4 *__restrict__ items, int cap,
+                                                      int *__restrict__ n_items,
+                                                      int32_t *__restrict__ err) {
+    __shared__ int32_t wsum[32];
+    __shared__ int32_t carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int b = 0; b < n_trip; b += blockDim.x) {
+        const int t = b + threadIdx.x;
+        int nchunks = 0, i = 0, j = 0;
+        if (t < n_trip) {
+            i = ijk[3 * t];
+            j = ijk[3 * t + 1];
+            const int k = ijk[3 * t + 2];
+            if (i < 0 || j < i || k < j || k >= nb) atomicCAS(err, 0, DERR_TRIPLET_BIN);
+            bool row_start = true;
+            if (t > 0) {
+                const int pi = ijk[3 * t - 3], pj = ijk[3 * t - 2], pk = ijk[3 * t - 1];
+                const bool same = pi == i && pj == j;
+                row_start = !same;
+                const bool ordered = pi < i || (pi == i && (pj < j || (pj == j && pk < k)));
+                if (!ordered) atomicCAS(err, 0, DERR_TRIPLET_ORDER);
+            }
+            if (row_start && i >= 0 && i < nb && j >= 0 && j < nb) {
+                const int half_i = counts[i] / 2;
+                nchunks = (half_i + chunk - 1) / chunk;
+            }
+        }
+        // block exclusive scan of nchunks (small values; warp-level then serial over warps)
+        int x = nchunks;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        int before = 0, tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            if (w < warp) before += wsum[w];
+            tot += wsum[w];
+        }
+        const int pos = carry_s + before + x - nchunks;
+        for (int c = 0; c < nchunks; ++c)
+            if (pos + c < cap) items[pos + c] = make_int4(i, j, c * chunk, 0);
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_items = min(carry_s, cap);
+}
+
+template <bool MAP_IN_SMEM>
+__global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__restrict__ items,
+                                                    const int *__restrict__ n_items,
+                                                    const short2 *__restrict__ lists,
+                                                    const int64_t *__restrict__ lat_off,
+                                                    const int32_t *__restrict__ counts,
+                                                    const uint8_t *__restrict__ binmap_g,
+                                                    unsigned long long *__restrict__ Td) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int hs = G.nb + 1;                       // histogram slots (0 = no ring)
+    uint32_t *hist = (uint32_t *)smem;             // [nwarps][hs][32]
+    int32_t *stage = (int32_t *)(hist + (size_t)nwarps * hs * 32);   // [STAGE]
+    uint8_t *map_s = (uint8_t *)(stage + STAGE);
+    const uint8_t *map = MAP_IN_SMEM ? map_s : binmap_g;
+    if (MAP_IN_SMEM) {
+        const int64_t mb = (int64_t)G.W * G.W;
+        const int64_t nv = mb / 16;
+        for (int64_t i = threadIdx.x; i < nv; i += blockDim.x)
+            ((uint4 *)map_s)[i] = ((const uint4 *)binmap_g)[i];
+        for (int64_t i = nv * 16 + threadIdx.x; i < mb; i += blockDim.x) map_s[i] = binmap_g[i];
+    }
+    for (int i = threadIdx.x; i < nwarps * hs * 32; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    uint32_t *myhist = hist + (size_t)warp * hs * 32 + lane;
+    const int ni = *n_items;
+    for (int it = blockIdx.x; it < ni; it += gridDim.x) {
+        const int4 I = items[it];
+        const int i = I.x, j = I.y;
+        const int ci = counts[i], cj = counts[j];
+        const short2 *Fi = lists + lat_off[i] + ci / 2;   // upper half plane of ring i
+        const short2 *Fj = lists + lat_off[j];
+        const int nh = ci / 2;
+        int lin1[G1];
+        bool v1[G1];
+#pragma unroll
+        for (int q = 0; q < G1; ++q) {
+            const int a = I.z + q * blockDim.x + threadIdx.x;
+            v1[q] = a < nh;
+            const short2 g = v1[q] ? Fi[a] : make_short2(0, 0);
+            lin1[q] = g.y * G.W + g.x + (int)G.base;
+        }
+        int cur[G1];
+        uint32_t cnt[G1];
+#pragma unroll
+        for (int q = 0; q < G1; ++q) {
+            cur[q] = 0;
+            cnt[q] = 0;
+        }
+        for (int s0 = 0; s0 < cj; s0 += STAGE) {
+            const int ns = min(STAGE, cj - s0);
+            __syncthreads();
+            for (int a = threadIdx.x; a < ns; a += blockDim.x) {
+                const short2 g = Fj[s0 + a];
+                stage[a] = g.y * G.W + g.x;
+            }
+            __syncthreads();
+            for (int a = 0; a < ns; ++a) {
+                const int l2 = stage[a];
+#pragma unroll
+                for (int q = 0; q < G1; ++q) {
+                    const int k = v1[q] ? (int)map[lin1[q] + l2] : 0;
+                    if (k != cur[q]) {
+                        myhist[(size_t)cur[q] * 32] += cnt[q];
+                        cur[q] = k;
+                        cnt[q] = 0;
+                    }
+                    ++cnt[q];
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < G1; ++q) myhist[(size_t)cur[q] * 32] += cnt[q];
+        __syncthreads();
+        // reduce lanes and warps; slot 0 (no ring) is dropped
+        for (int k = 1 + warp; k < hs; k += nwarps) {
+            uint64_t s = 0;
+            for (int w = 0; w < nwarps; ++w) s += hist[((size_t)w * hs + k) * 32 + lane];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+            if (lane == 0 && s)
+                atomicAdd(&Td[((size_t)i * G.nb + j) * G.nb + (k - 1)], (unsigned long long)s);
+        }
+        __syncthreads();
+        for (int a = threadIdx.x; a < nwarps * hs * 32; a += blockDim.x) hist[a] = 0u;
+        __syncthreads();
+    }
+}
+
+__global__ void k_count_gather(int nb, int32_t n_trip, const int32_t *__restrict__ ijk,
+                               const unsigned long long *__restrict__ Td, int64_t *__restrict__ T) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_trip) return;
+    const int i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
+    if (i < 0 || j < 0 || k < 0 || i >= nb || j >= nb || k >= nb) {
+        T[t] = 0;
+        return;
+    }
+    T[t] = 2 * (int64_t)Td[((size_t)i * nb + j) * nb + k];
+}
+
+// Mean l of each ring over its filled cells (FP64, fixed-order tree per ring).
+__global__ void __launch_bounds__(256) k_ellbar(int nb, float du, const short2 *__restrict__ lists,
+                                                const int64_t *__restrict__ lat_off,
+                                                const int32_t *__restrict__ counts,
+                                                double *__restrict__ ellbar) {
+    __shared__ double sh[256];
+    const int m = blockIdx.x;
+    const int c = counts[m];
+    const short2 *L = lists + lat_off[m];
+    double s = 0.0;
+    for (int a = threadIdx.x; a < c; a += blockDim.x) {
+        const short2 g = L[a];
+        s += sqrt((double)g.x * g.x + (double)g.y * g.y);
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        ellbar[m] = c > 0 ? 2.0 * 3.14159265358979323846 * (double)du * sh[0] / (double)c : nan("");
+}
+
+CountGeom cgeom(const Setup &s) {
+    CountGeom G;
+    G.n = s.n;
+    G.half = s.half;
+    G.nb = s.nb;
+    G.R = s.R;
+    G.W = 4 * s.R + 1;
+    G.base = (int64_t)2 * s.R * G.W + 2 * s.R;
+    return G;
+}
+
+struct RingBufs {
+    short2 *lists;
+    int32_t *counts;
+    uint8_t *binmap;
+};
+
+abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, RingBufs &rb) {
+    const CountGeom G = cgeom(s);
+    const int64_t ncell = std::max<int64_t>(s.lat_off.back(), 1);
+    rb.lists = (short2 *)workspace(ctx, "ring.lists", sizeof(short2) * ncell);
+    rb.counts = (int32_t *)workspace(ctx, "ring.counts", sizeof(int32_t) * s.nb);
+    const int64_t mb = (int64_t)G.W * G.W;
+    rb.binmap = (uint8_t *)workspace(ctx, "ring.binmap", (size_t)cdiv(mb, 16) * 16);
+    if (!rb.lists || !rb.counts || !rb.binmap) return fail(ctx, ABS_ERR_OOM, "ring table workspace");
+    StageTimer timer(ctx, "ring_lists");
+    cudaMemsetAsync(rb.binmap, 0, (size_t)cdiv(mb, 16) * 16, ctx->stream);
+    k_ring_lists<<<s.nb, 1024, 0, ctx->stream>>>(G, s.d_q, s.d_Rm, s.d_lat_off, d_mask, rb.lists,
+                                                 rb.counts, rb.binmap);
+    return check_launch(ctx, "ring lists");
+}
+
+}  // namespace
+
+abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, int32_t n_trip,
+                         const int32_t *d_ijk, int64_t *d_count) {
+    RingBufs rb;
+    abs_status st = ring_tables(ctx, s, d_mask, rb);
+    if (st != ABS_OK) return st;
+    if (n_trip == 0) return ABS_OK;
+    const CountGeom G = cgeom(s);
+    // threads per CTA: lane-private histograms must fit next to the map
+    const int hs = s.nb + 1;
+    const int64_t map_bytes = cdiv((int64_t)G.W * G.W, 16) * 16;
+    const size_t hist_budget = 96 * 1024;
+    int nwarps = (int)std::min<size_t>(CT / 32, hist_budget / ((size_t)hs * 32 * 4));
+    if (nwarps < 1) return fail(ctx, ABS_ERR_UNSUPPORTED, "too many rings for the count kernel");
+    const bool map_smem = map_bytes + (int64_t)nwarps * hs * 32 * 4 + STAGE * 4 <= 220 * 1024;
+    const int threads = nwarps * 32;
+    const int chunk = threads * G1;
+    const size_t smem = (size_t)nwarps * hs * 32 * 4 + STAGE * 4 + (map_smem ? map_bytes : 0);
+    // work items: one per (row, chunk of the upper half of ring i)
+    int64_t max_half = 0;
+    for (int m = 0; m < s.nb; ++m) max_half = std::max<int64_t>(max_half, s.lat[m] / 2);
+    const int cap = (int)std::min<int64_t>((int64_t)n_trip * cdiv(std::max<int64_t>(max_half, 1), chunk), 1 << 26);
+    int4 *items = (int4 *)workspace(ctx, "count.items", sizeof(int4) * cap);
+    int *n_items = (int *)workspace(ctx, "count.n_items", sizeof(int));
+    const size_t td_bytes = sizeof(unsigned long long) * (size_t)s.nb * s.nb * s.nb;
+    unsigned long long *Td = (unsigned long long *)workspace(ctx, "count.table", td_bytes);
+    if (!items || !n_items || !Td) return fail(ctx, ABS_ERR_OOM, "count workspace");
+    cudaStream_t stm = ctx->stream;
+    {
+        StageTimer timer(ctx, "count_items");
+        cudaMemsetAsync(Td, 0, td_bytes, stm);
+        k_count_items<<<1, 1024, 0, stm>>>(s.nb, n_trip, d_ijk, rb.counts, chunk, items, cap, n_items,
+                                           ctx->d_err);
+    }
+    {
+    StageTimer timer(ctx, "count_pairs");
+    const int blocks = ctx->sm_count * (map_smem ? 1 : 2);
+    if (map_smem) {
+        cudaFuncSetAttribute(k_count_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_count_pairs<true><<<blocks, threads, smem, stm>>>(G, items, n_items, rb.lists, s.d_lat_off,
+                                                            rb.counts, rb.binmap, Td);
+    } else {
+        cudaFuncSetAttribute(k_count_pairs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_count_pairs<false><<<blocks, threads, smem, stm>>>(G, items, n_items, rb.lists, s.d_lat_off,
+                                                             rb.counts, rb.binmap, Td);
+    }
+    }
+    {
+        StageTimer t2(ctx, "count_gather");
+        k_count_gather<<<(int)cdiv(n_trip, 256), 256, 0, stm>>>(s.nb, n_trip, d_ijk, Td, d_count);
+    }
+    return check_launch(ctx, "counts");
+}
+
+abs_status launch_ellbar(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, double *d_ellbar) {
+    RingBufs rb;
+    abs_status st = ring_tables(ctx, s, d_mask, rb);
+    if (st != ABS_OK) return st;
+    StageTimer timer(ctx, "ellbar");
+    k_ellbar<<<s.nb, 256, 0, ctx->stream>>>(s.nb, s.du, rb.lists, s.d_lat_off, rb.counts, d_ellbar);
+    return check_launch(ctx, "ellbar");
+}
+
+}  // namespace absk

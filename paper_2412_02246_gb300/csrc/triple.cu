@@ -1,0 +1,199 @@
+// Stage 3 (FP32 form) and stage 5: sky-plane triple sums, Eq. estimator_t.
+//
+// S_ijk = N^-2 sum_p D_i(p) D_j(p) D_k(p) for every listed triplet.  Triplets
+// sharing (i, j) form a row; the product D_i D_j is formed once per pixel and
+// row and multiplied into each D_k of the row (the contraction
+// C[(i,j), k] = sum_p (D_i D_j)(p) D_k(p)).
+//
+// A CTA owns a group of up to TG consecutive triplets and a contiguous range
+// of pixels.  It stages the fields of PC pixels at a time in shared memory
+// (all rings, coalesced float4 loads); each warp takes a row segment of the
+// group and accumulates 8 triplets at a time over the staged pixels (lane ->
+// pixel, FP32), reduces across the warp, and adds the result into an FP64
+// per-triplet accumulator in shared memory.  Per-CTA partial sums go to
+// [split][triplet] and a second kernel adds the splits in a fixed order (so
+// the result does not depend on scheduling) and applies N^-2 in FP64.
+//
+// B_ijk = S_ijk / (A T_ijk) is then formed in FP64 (NaN for T = 0).
+#include "abs_internal.cuh"
+
+namespace absk {
+namespace {
+
+constexpr int TG = 1024;       // triplets per CTA group
+constexpr int TT = 256;        // threads per CTA
+constexpr int KB = 8;          // triplets per warp pass
+constexpr unsigned FULL = 0xffffffffu;
+
+struct TripleGeom {
+    int nb;
+    int64_t P;                 // pixels
+    int PC;                    // pixels staged per pass (multiple of 128)
+    int64_t per_split;         // pixels per split (multiple of PC)
+    int n_trip;
+    int vec4;                  // fields rows are 16-byte aligned (P % 4 == 0, aligned base)
+};
+
+__global__ void __launch_bounds__(TT) k_triple_fp32(TripleGeom G, const float *__restrict__ fields,
+                                                    const int32_t *__restrict__ ijk,
+                                                    double *__restrict__ partial) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    float *F = (float *)smem;                                    // [nb][PC]
+    double *acc = (double *)(F + (size_t)G.nb * G.PC);           // [TG]
+    int *seg = (int *)(acc + TG);                                 // [TG + 1] row starts
+    int *kk = seg + TG + 1;                                       // [TG] k of each triplet
+    __shared__ int nseg_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int t0 = blockIdx.y * TG;
+    const int nt = min(TG, G.n_trip - t0);
+    const int64_t p_begin = (int64_t)blockIdx.x * G.per_split;
+    const int64_t p_end = min(G.P, p_begin + G.per_split);
+    // row segments of this group (serial; TG is small)
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        acc[t] = 0.0;
+        const int k = ijk[3 * (t0 + t) + 2];
+        kk[t] = (k >= 0 && k < G.nb) ? k : -1;   // out-of-range bins contribute nothing
+    }
+    if (threadIdx.x == 0) {
+        int ns = 0;
+        for (int t = 0; t < nt; ++t) {
+            const int i = ijk[3 * (t0 + t)], j = ijk[3 * (t0 + t) + 1];
+            if (t == 0 || i != ijk[3 * (t0 + t - 1)] || j != ijk[3 * (t0 + t - 1) + 1]) seg[ns++] = t;
+        }
+        seg[ns] = nt;
+        nseg_s = ns;
+    }
+    __syncthreads();
+    const int nseg = nseg_s;
+    for (int64_t pc = p_begin; pc < p_end; pc += G.PC) {
+        const int np = (int)min((int64_t)G.PC, p_end - pc);
+        __syncthreads();
+        // stage fields[m][pc .. pc+np) (np is a multiple of 4 except possibly at the very end)
+        const int nv4 = G.vec4 ? np / 4 : 0;
+        for (int e = threadIdx.x; e < G.nb * nv4; e += blockDim.x) {
+            const int m = e / nv4, v = e - m * nv4;
+            ((float4 *)(F + (size_t)m * G.PC))[v] =
+                __ldg((const float4 *)(fields + (size_t)m * G.P + pc) + v);
+        }
+        for (int e = threadIdx.x; e < G.nb * G.PC; e += blockDim.x) {
+            const int m = e / G.PC, v = e - m * G.PC;
+            if (v >= nv4 * 4) F[(size_t)m * G.PC + v] = v < np ? fields[(size_t)m * G.P + pc + v] : 0.f;
+        }
+        __syncthreads();
+        for (int sgi = warp; sgi < nseg; sgi += nwarps) {
+            const int ta = seg[sgi], tb = seg[sgi + 1];
+            const int i = ijk[3 * (t0 + ta)], j = ijk[3 * (t0 + ta) + 1];
+            if (i < 0 || i >= G.nb || j < 0 || j >= G.nb) continue;
+            const float *Fi = F + (size_t)i * G.PC, *Fj = F + (size_t)j * G.PC;
+            for (int tq = ta; tq < tb; tq += KB) {
+                const float *Fk[KB];
+                float a[KB];
+#pragma unroll
+                for (int b = 0; b < KB; ++b) {
+                    Fk[b] = F + (size_t)max(kk[min(tq + b, tb - 1)], 0) * G.PC;
+                    a[b] = 0.f;
+                }
+                for (int p = lane; p < G.PC; p += 32) {
+                    const float dij = Fi[p] * Fj[p];
+#pragma unroll
+                    for (int b = 0; b < KB; ++b) a[b] = fmaf(dij, Fk[b][p], a[b]);
+                }
+#pragma unroll
+                for (int b = 0; b < KB; ++b) {
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) a[b] += __shfl_xor_sync(FULL, a[b], o);
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int b = 0; b < KB; ++b)
+                        if (tq + b < tb && kk[tq + b] >= 0) acc[tq + b] += (double)a[b];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nt; t += blockDim.x)
+        partial[(size_t)blockIdx.x * G.n_trip + t0 + t] = acc[t];
+}
+
+__global__ void k_triple_reduce(int n_trip, int nsplit, double inv_p, const double *__restrict__ partial,
+                                double *__restrict__ S) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_trip) return;
+    double s = 0.0;
+    for (int k = 0; k < nsplit; ++k) s += partial[(size_t)k * n_trip + t];
+    S[t] = s * inv_p;
+}
+
+__global__ void k_normalise(int n_trip, double norm_A, const double *__restrict__ S,
+                            const int64_t *__restrict__ T, double *__restrict__ B) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_trip) return;
+    const int64_t c = T[t];
+    B[t] = c > 0 ? S[t] / (norm_A * (double)c) : nan("");
+}
+
+__global__ void k_check_triplets(int nb, int n_trip, const int32_t *__restrict__ ijk,
+                                 int32_t *__restrict__ err) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_trip) return;
+    const int i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
+    if (i < 0 || j < i || k < j || k >= nb) atomicCAS(err, 0, DERR_TRIPLET_BIN);
+    if (t > 0) {
+        const int pi = ijk[3 * t - 3], pj = ijk[3 * t - 2], pk = ijk[3 * t - 1];
+        const bool ordered = pi < i || (pi == i && (pj < j || (pj == j && pk < k)));
+        if (!ordered) atomicCAS(err, 0, DERR_TRIPLET_ORDER);
+    }
+}
+
+}  // namespace
+
+abs_status launch_check_triplets(abs_ctx *ctx, const Setup &s, int32_t n_trip, const int32_t *d_ijk) {
+    if (n_trip == 0) return ABS_OK;
+    StageTimer timer(ctx, "check_triplets");
+    k_check_triplets<<<(int)cdiv(n_trip, 256), 256, 0, ctx->stream>>>(s.nb, n_trip, d_ijk, ctx->d_err);
+    return check_launch(ctx, "triplet check");
+}
+
+abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_fields, int32_t n_trip,
+                              const int32_t *d_ijk, double *d_sum) {
+    if (n_trip == 0) return ABS_OK;
+    if (s.precision != ABS_FP32) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 triple sums not built");
+    TripleGeom G;
+    G.nb = s.nb;
+    G.P = (int64_t)s.N * s.N;
+    G.n_trip = n_trip;
+    // staged pixels: keep the field tile within ~96 KB
+    int PC = 1024;
+    while (PC > 128 && (size_t)G.nb * PC * 4 > 96 * 1024) PC >>= 1;
+    G.PC = PC;
+    G.vec4 = (G.P % 4 == 0) && (((uintptr_t)d_fields & 15) == 0);
+    const int groups = (int)cdiv(n_trip, TG);
+    // splits: about two CTAs per SM overall
+    const int64_t chunks = cdiv(G.P, PC);
+    int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(chunks, cdiv(2 * ctx->sm_count, groups)));
+    G.per_split = cdiv(chunks, nsplit) * PC;
+    nsplit = cdiv(G.P, G.per_split);
+    double *partial = (double *)workspace(ctx, "triple.partial", sizeof(double) * nsplit * n_trip);
+    if (!partial) return fail(ctx, ABS_ERR_OOM, "triple-sum workspace");
+    const size_t smem = (size_t)G.nb * PC * 4 + TG * 8 + (2 * TG + 1) * 4;
+    cudaFuncSetAttribute(k_triple_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        StageTimer timer(ctx, "triple_fp32");
+        k_triple_fp32<<<dim3((unsigned)nsplit, groups), TT, smem, ctx->stream>>>(G, d_fields, d_ijk, partial);
+    }
+    StageTimer timer(ctx, "triple_reduce");
+    k_triple_reduce<<<(int)cdiv(n_trip, 256), 256, 0, ctx->stream>>>(
+        n_trip, (int)nsplit, 1.0 / ((double)s.N * (double)s.N), partial, d_sum);
+    return check_launch(ctx, "triple sums");
+}
+
+abs_status launch_normalise(abs_ctx *ctx, const Setup &s, int32_t n_trip, const double *d_sum,
+                            const int64_t *d_count, double *d_B) {
+    if (n_trip == 0) return ABS_OK;
+    StageTimer timer(ctx, "normalise");
+    k_normalise<<<(int)cdiv(n_trip, 256), 256, 0, ctx->stream>>>(n_trip, s.norm_A, d_sum, d_count, d_B);
+    return check_launch(ctx, "normalise");
+}
+
+}  // namespace absk

@@ -1,0 +1,96 @@
+"""The C ABI library loads, exports every declared symbol, and its host-only
+helpers (ring thresholds, sky-grid size, closing triplets, argument checks)
+agree with the oracle.  No GPU needed: these entry points do no device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2412_02246_gb300 as absmod
+from paper_2412_02246_gb300 import build as absbuild
+from paper_2412_02246_gb300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    absbuild.build()
+    return absmod.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "abs.h")).read()
+    return sorted(set(re.findall(r"^(?:abs_status|const char \*)\s*(abs_\w+)\s*\(", src, re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+@pytest.mark.parametrize("cfg_id", [0, 1, 2])
+def test_ring_q_fft_size_triplets_match_oracle(lib, cfg_id):
+    wl = synth.workload(cfg_id)
+    cfg = absmod.Config.from_workload(wl)
+    q = absmod.abs_ring_q(cfg)
+    assert np.array_equal(q, oracle.ring_q(wl.ell_edges, wl.du))
+    assert absmod.abs_fft_size(cfg) == oracle.min_fft_size(q, wl.n_grid)
+    assert np.array_equal(absmod.abs_triplets(cfg), oracle.triplets(q))
+
+
+def test_known_sizes(lib):
+    # N = smallest 2^a 3^b 5^c >= 3R + 1 for the three workload shapes
+    sizes = [absmod.abs_fft_size(absmod.Config.from_workload(synth.workload(c))) for c in (0, 1, 2)]
+    assert sizes == [90, 288, 576]
+    assert len(absmod.abs_triplets(absmod.Config.from_workload(synth.workload(1)))) == 689
+
+
+def test_random_edges_match_oracle(lib):
+    rng = np.random.default_rng(5)
+    for _ in range(30):
+        n = int(rng.choice([16, 32, 64, 128]))
+        du = float(rng.uniform(0.5, 3.0))
+        nb = int(rng.integers(1, 12))
+        edges = np.sort(rng.uniform(5.0, 2 * np.pi * du * n / 2, nb + 1))
+        if np.any(np.diff(edges) <= 0):
+            continue
+        cfg = absmod.Config(n_grid=n, du=du, ell_edges=edges)
+        q = absmod.abs_ring_q(cfg)
+        assert np.array_equal(q, oracle.ring_q(edges, du))
+        assert np.array_equal(absmod.abs_triplets(cfg), oracle.triplets(q))
+        assert absmod.abs_fft_size(cfg) == oracle.min_fft_size(q, n)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n_grid=7), dict(n_grid=0), dict(n_grid=16386), dict(du=0.0), dict(du=-1.0),
+    dict(du=float("nan")), dict(kernel=5), dict(sigma_cells=0.1), dict(radius_cells=4),
+    dict(radius_cells=-1), dict(precision=3), dict(norm_A=0.0), dict(n_fft=7), dict(n_fft=80), dict(n_fft=91),
+    dict(ell_edges=[10.0, 5.0]), dict(ell_edges=[0.0, 5.0]), dict(ell_edges=[5.0, float("inf")]),
+])
+def test_invalid_configs_rejected(lib, bad):
+    base = dict(n_grid=64, du=2.0, ell_edges=np.linspace(25, 375, 9))
+    base.update(bad)
+    cfg = absmod.Config(**base)
+    with pytest.raises(absmod.AbsError) as ei:
+        absmod.abs_ring_q(cfg) if "n_fft" not in bad else absmod.abs_fft_size(cfg)
+    assert ei.value.status == absmod.ABS_ERR_INVALID_ARG
+
+
+def test_fft_size_user_value(lib):
+    cfg = absmod.Config(n_grid=64, du=2.0, ell_edges=np.linspace(25, 375, 9), n_fft=128)
+    assert absmod.abs_fft_size(cfg) == 128
+    cfg = absmod.Config(n_grid=64, du=2.0, ell_edges=np.linspace(25, 375, 9), n_fft=90)
+    assert absmod.abs_fft_size(cfg) == 90
+
+
+def test_product_path_has_no_cpu_fallback(monkeypatch, tmp_path):
+    # with the library absent the binding raises instead of computing anything
+    monkeypatch.setattr(absmod, "_lib", None)
+    with pytest.raises(RuntimeError):
+        absmod.load(str(tmp_path / "missing.so"))

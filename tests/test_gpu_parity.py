@@ -1,0 +1,336 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (stated by the method's accuracy requirements):
+  * masks and triangle counts: bit-exact;
+  * gridded sums: |dV_g| <= 1e-6 sum_i w |V_i| per cell (normwise: the
+    componentwise error of a sum that cancels is unbounded), weights 1e-6;
+  * fields: |dD_m(p)| <= 1e-5 sum_g |X_m(g)| (the DFT bound |D| <= sum |X|);
+  * FP32 triple sums and B: relative 1e-5 on every triplet with
+    |B| >= 1e-3 max |B|; the remaining triplets within 1e-5 of max |B|;
+  * mean l per ring: relative 1e-12.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2412_02246_gb300 as absmod
+from paper_2412_02246_gb300 import build as absbuild
+from paper_2412_02246_gb300 import synth
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+GRID_TOL = 1e-6
+FIELD_TOL = 1e-5
+SUM_TOL = 1e-5
+_cache = {}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    absbuild.build()
+    c = absmod.Context(0)
+    yield c
+    c.close()
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def oracle_run(key, n, du, edges, uv, vis, kernel="gauss", sigma=1.0, radius=3):
+    if key not in _cache:
+        _cache[key] = oracle.estimate(n, du, edges, uv, vis, kernel, sigma, radius)
+    return _cache[key]
+
+
+def inputs(cfg_id, realisation=0):
+    k = ("inp", cfg_id, realisation)
+    if k not in _cache:
+        _cache[k] = synth.make_inputs(cfg_id, realisation)
+    return _cache[k]
+
+
+def to_dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(dev())
+
+
+def gpu_grid(ctx, cfg, uv, vis):
+    n = cfg.n_grid
+    g = torch.empty((n, n, 2), dtype=torch.float32, device=dev())
+    w = torch.empty((n, n), dtype=torch.float32, device=dev())
+    m = torch.empty((n, n), dtype=torch.uint8, device=dev())
+    ctx.abs_grid(cfg, to_dev(uv), to_dev(synth.vis_as_float2(vis)), g, w, m)
+    ctx.sync()
+    G = g.cpu().numpy().astype(np.float64)
+    return G[..., 0] + 1j * G[..., 1], w.cpu().numpy(), m.cpu().numpy(), (g, w, m)
+
+
+def grid_abs_bound(n, du, uv, vis, kernel="gauss", sigma=1.0, radius=3):
+    return oracle.grid(n, du, uv, np.abs(vis).astype(np.complex64), kernel, sigma, radius).grid.real
+
+
+def assert_grid_parity(G, W, M, est, bound):
+    assert np.array_equal(M, (est.grid.ncontrib > 0).astype(np.uint8))
+    sel = bound > 0
+    err = np.abs(G - est.grid.grid)[sel] / bound[sel]
+    assert err.max() <= GRID_TOL, f"grid normwise error {err.max():.3e}"
+    wsel = est.grid.wsum > 0
+    werr = np.abs(W[wsel] - est.grid.wsum[wsel]) / est.grid.wsum[wsel]
+    assert werr.max() <= GRID_TOL, f"weight error {werr.max():.3e}"
+    assert np.all(G[~sel] == 0) and np.all(W[~wsel] == 0)
+
+
+@pytest.mark.parametrize("cfg_id", [0, 1])
+def test_grid_parity(ctx, cfg_id):
+    inp = inputs(cfg_id)
+    wl = inp.wl
+    cfg = absmod.Config.from_workload(wl)
+    est = oracle_run(("est", cfg_id), wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+    G, W, M, _ = gpu_grid(ctx, cfg, inp.uv, inp.vis)
+    assert_grid_parity(G, W, M, est, grid_abs_bound(wl.n_grid, wl.du, inp.uv, inp.vis))
+
+
+@pytest.mark.parametrize("kernel,sigma,radius", [("ngp", 1.0, 3), ("gauss", 2.0, 1), ("gauss", 0.7, 0),
+                                                 ("gauss", 1.5, 2)])
+def test_grid_kernel_variants(ctx, kernel, sigma, radius):
+    inp = inputs(0)
+    wl = inp.wl
+    cfg = absmod.Config.from_workload(wl, kernel=absmod.ABS_KERNEL_NGP if kernel == "ngp" else
+                                      absmod.ABS_KERNEL_GAUSS, sigma_cells=sigma, radius_cells=radius)
+    est = oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis, kernel, sigma, radius)
+    G, W, M, _ = gpu_grid(ctx, cfg, inp.uv, inp.vis)
+    assert_grid_parity(G, W, M, est, grid_abs_bound(wl.n_grid, wl.du, inp.uv, inp.vis, kernel, sigma, radius))
+
+
+def test_grid_skips_nonfinite_and_far_baselines(ctx):
+    inp = inputs(0)
+    wl = inp.wl
+    uv = inp.uv.copy()
+    uv[::7, 0] = np.nan
+    uv[3::11, 1] = np.inf
+    uv[5::13] = 1e6        # far outside the grid: no footprint cell on it
+    keep = np.isfinite(uv).all(1)
+    cfg = absmod.Config.from_workload(wl)
+    est = oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, uv[keep], inp.vis[keep])
+    G, W, M, _ = gpu_grid(ctx, cfg, uv, inp.vis)
+    assert_grid_parity(G, W, M, est, grid_abs_bound(wl.n_grid, wl.du, uv[keep], inp.vis[keep]))
+
+
+def test_grid_empty(ctx):
+    wl = synth.workload(0)
+    cfg = absmod.Config.from_workload(wl)
+    n = wl.n_grid
+    g = torch.full((n, n, 2), 7.0, device=dev())
+    w = torch.full((n, n), 7.0, device=dev())
+    m = torch.full((n, n), 7, dtype=torch.uint8, device=dev())
+    uv = torch.empty((0, 2), device=dev())
+    ctx.abs_grid(cfg, uv, torch.empty((0, 2), device=dev()), g, w, m)
+    ctx.sync()
+    assert g.abs().sum().item() == 0 and w.abs().sum().item() == 0 and m.sum().item() == 0
+
+
+def gpu_fields(ctx, cfg, gwm):
+    g, w, m = gwm
+    N = absmod.abs_fft_size(cfg)
+    f = torch.empty((cfg.n_bins, N, N), dtype=torch.float32, device=dev())
+    ctx.abs_filter_fft(cfg, g, w, m, f)
+    ctx.sync()
+    return f
+
+
+@pytest.mark.parametrize("cfg_id,n_fft", [(0, 0), (0, 96), (0, 135), (1, 0)])
+def test_fields_parity(ctx, cfg_id, n_fft):
+    inp = inputs(cfg_id)
+    wl = inp.wl
+    cfg = absmod.Config.from_workload(wl, n_fft=n_fft)
+    est = oracle_run(("est", cfg_id), wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+    _, _, _, gwm = gpu_grid(ctx, cfg, inp.uv, inp.vis)
+    f = gpu_fields(ctx, cfg, gwm).cpu().numpy().astype(np.float64)
+    N = f.shape[-1]
+    D, imag = oracle.ring_fields(est.X, est.filled, est.q, N)
+    for m in range(cfg.n_bins):
+        r2 = _r2(wl.n_grid)
+        sel = (est.filled > 0) & (r2 >= est.q[m]) & (r2 < est.q[m + 1])
+        bound = np.abs(est.X[sel]).sum()
+        if bound == 0:
+            assert np.all(f[m] == 0)
+            continue
+        err = np.abs(f[m] - D[m]).max() / bound
+        assert err <= FIELD_TOL, f"ring {m}: field error {err:.3e}"
+
+
+def _r2(n):
+    k = np.arange(n)
+    k = np.where(k > n // 2, k - n, k)
+    gy, gx = np.meshgrid(k, k, indexing="ij")
+    return gx.astype(np.int64) ** 2 + gy.astype(np.int64) ** 2
+
+
+def check_sums(S, est, tol=SUM_TOL):
+    B = est.B
+    big = np.abs(B) >= 1e-3 * np.nanmax(np.abs(B))
+    ok = est.T > 0
+    rel = np.abs(S[big & ok] - est.S.real[big & ok]) / np.abs(est.S.real[big & ok])
+    assert rel.max() <= tol, f"triple-sum relative error {rel.max():.3e}"
+    # small ones: absolute, scaled by the largest sum of the set
+    scale = np.abs(est.S.real[ok]).max()
+    assert np.all(np.abs(S[ok] - est.S.real[ok]) <= tol * scale)
+
+
+@pytest.mark.parametrize("cfg_id", [0, 1])
+def test_triple_sums_and_counts(ctx, cfg_id):
+    inp = inputs(cfg_id)
+    wl = inp.wl
+    cfg = absmod.Config.from_workload(wl, precision=absmod.ABS_FP32)
+    est = oracle_run(("est", cfg_id), wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+    _, _, M, gwm = gpu_grid(ctx, cfg, inp.uv, inp.vis)
+    assert np.array_equal(M, est.filled)
+    f = gpu_fields(ctx, cfg, gwm)
+    ijk = to_dev(est.ijk)
+    nt = len(est.ijk)
+    S = torch.empty(nt, dtype=torch.float64, device=dev())
+    T = torch.empty(nt, dtype=torch.int64, device=dev())
+    ctx.abs_triple(cfg, f, gwm[2], ijk, S, T)
+    ctx.sync()
+    assert np.array_equal(T.cpu().numpy(), est.T), "counts differ"
+    check_sums(S.cpu().numpy(), est)
+    # normalisation and mean l
+    B = torch.empty(nt, dtype=torch.float64, device=dev())
+    E = torch.empty(cfg.n_bins, dtype=torch.float64, device=dev())
+    ctx.abs_normalise(cfg, S, T, B, gwm[2], E)
+    ctx.sync()
+    Bn = B.cpu().numpy()
+    assert np.array_equal(np.isnan(Bn), np.isnan(est.B))
+    assert np.allclose(E.cpu().numpy(), est.ellbar, rtol=1e-12, equal_nan=True)
+
+
+@pytest.mark.parametrize("cfg_id", [0, 1])
+def test_estimate_end_to_end(ctx, cfg_id):
+    inp = inputs(cfg_id)
+    wl = inp.wl
+    cfg = absmod.Config.from_workload(wl, precision=absmod.ABS_FP32)
+    est = oracle_run(("est", cfg_id), wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+    B, T, E, ijk = absmod.estimate(cfg, to_dev(inp.uv), to_dev(synth.vis_as_float2(inp.vis)), ctx)
+    ctx.sync()
+    assert np.array_equal(ijk, est.ijk)
+    assert np.array_equal(T.cpu().numpy(), est.T)
+    Bg = B.cpu().numpy()
+    assert np.array_equal(np.isnan(Bg), np.isnan(est.B))
+    ok = ~np.isnan(est.B)
+    big = ok & (np.abs(est.B) >= 1e-3 * np.nanmax(np.abs(est.B)))
+    rel = np.abs(Bg[big] - est.B[big]) / np.abs(est.B[big])
+    assert rel.max() <= SUM_TOL, f"B relative error {rel.max():.3e}"
+    assert np.allclose(E.cpu().numpy(), est.ellbar, rtol=1e-12, equal_nan=True)
+
+
+def test_estimate_many_and_host(ctx):
+    wl = synth.workload(0)
+    cfg = absmod.Config.from_workload(wl)
+    ins = [inputs(0, r) for r in range(3)]
+    uv = ins[0].uv
+    vis = np.stack([synth.vis_as_float2(i.vis) for i in ins])
+    ijk = absmod.abs_triplets(cfg)
+    nt = len(ijk)
+    B = torch.empty((3, nt), dtype=torch.float64, device=dev())
+    T = torch.empty(nt, dtype=torch.int64, device=dev())
+    E = torch.empty(cfg.n_bins, dtype=torch.float64, device=dev())
+    ctx.abs_estimate_many(cfg, to_dev(uv), to_dev(vis), nt, None, B, T, E)
+    ctx.sync()
+    Bm = B.cpu().numpy()
+    for r in range(3):
+        est = oracle_run(("est0r", r), wl.n_grid, wl.du, wl.ell_edges, uv, ins[r].vis)
+        assert np.array_equal(T.cpu().numpy(), est.T)
+        ok = ~np.isnan(est.B)
+        big = ok & (np.abs(est.B) >= 1e-3 * np.nanmax(np.abs(est.B)))
+        assert (np.abs(Bm[r][big] - est.B[big]) / np.abs(est.B[big])).max() <= SUM_TOL
+    # host entry point: same numbers
+    hB = np.zeros((3, nt))
+    hT = np.zeros(nt, np.int64)
+    hE = np.zeros(cfg.n_bins)
+    ctx.abs_estimate_host(cfg, np.ascontiguousarray(uv), np.ascontiguousarray(vis), nt, None, hB, hT, hE)
+    assert np.array_equal(hT, T.cpu().numpy())
+    assert np.allclose(hB, Bm, rtol=1e-12, equal_nan=True)
+    assert np.allclose(hE, E.cpu().numpy(), rtol=0, equal_nan=True)
+
+
+def test_counts_deterministic(ctx):
+    inp = inputs(1)
+    wl = inp.wl
+    cfg = absmod.Config.from_workload(wl, precision=absmod.ABS_FP32)
+    outs = []
+    for _ in range(2):
+        B, T, E, _ = absmod.estimate(cfg, to_dev(inp.uv), to_dev(synth.vis_as_float2(inp.vis)), ctx)
+        ctx.sync()
+        outs.append((T.cpu().numpy(), B.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    ok = ~np.isnan(outs[0][1])
+    assert np.allclose(outs[0][1][ok], outs[1][1][ok], rtol=1e-9)
+
+
+@pytest.mark.parametrize("case", ["odd_bins_small_grid", "empty_rings", "constant_sky", "one_bin"])
+def test_edge_cases(ctx, case):
+    rng = np.random.default_rng(11)
+    if case == "odd_bins_small_grid":
+        n, du, edges = 16, 1.0, 2 * np.pi * np.array([1.0, 2.0, 3.2, 4.4])
+        uv = rng.uniform(-7.0, 7.0, (300, 2)).astype(np.float32)
+        vis = (rng.standard_normal(300) + 1j * rng.standard_normal(300)).astype(np.complex64)
+    elif case == "empty_rings":
+        n, du = 64, 2.0
+        edges = np.array([25.0, 25.5, 26.0, 120.0, 121.0, 300.0])   # two rings hold no cell
+        inp = inputs(0)
+        uv, vis = inp.uv, inp.vis
+    elif case == "constant_sky":
+        inp = inputs(0)
+        n, du, edges = 64, 2.0, inp.wl.ell_edges
+        uv, vis = inp.uv, np.full(len(inp.uv), 0.7, np.complex64)
+    else:
+        n, du, edges = 32, 1.0, np.array([2 * np.pi * 2.0, 2 * np.pi * 6.0])
+        uv = rng.uniform(-10.0, 10.0, (500, 2)).astype(np.float32)
+        vis = (rng.standard_normal(500) + 1j * rng.standard_normal(500)).astype(np.complex64)
+    cfg = absmod.Config(n_grid=n, du=du, ell_edges=edges)
+    est = oracle.estimate(n, du, edges, uv, vis)
+    B, T, E, ijk = absmod.estimate(cfg, to_dev(uv), to_dev(synth.vis_as_float2(vis)), ctx)
+    ctx.sync()
+    assert np.array_equal(T.cpu().numpy(), est.T)
+    Bg = B.cpu().numpy()
+    assert np.array_equal(np.isnan(Bg), np.isnan(est.B))
+    ok = ~np.isnan(est.B)
+    if ok.any():
+        scale = np.abs(est.B[ok]).max()
+        assert np.all(np.abs(Bg[ok] - est.B[ok]) <= SUM_TOL * scale)
+    if case == "constant_sky":
+        assert np.allclose(Bg[ok], np.float32(0.7) ** 3, rtol=1e-5)
+    assert np.allclose(E.cpu().numpy(), est.ellbar, rtol=1e-12, equal_nan=True)
+
+
+def test_bad_triplet_lists_are_reported(ctx):
+    wl = synth.workload(0)
+    cfg = absmod.Config.from_workload(wl)
+    inp = inputs(0)
+    _, _, _, gwm = gpu_grid(ctx, cfg, inp.uv, inp.vis)
+    f = gpu_fields(ctx, cfg, gwm)
+    for bad in (np.array([[0, 1, 2], [0, 0, 1]], np.int32),      # not sorted
+                np.array([[0, 0, 1], [2, 1, 3]], np.int32),      # j < i
+                np.array([[0, 0, 1], [0, 1, 99]], np.int32)):    # bin out of range
+        S = torch.zeros(len(bad), dtype=torch.float64, device=dev())
+        T = torch.zeros(len(bad), dtype=torch.int64, device=dev())
+        ctx.abs_triple(cfg, f, gwm[2], to_dev(bad), S, T)
+        with pytest.raises(absmod.AbsError) as ei:
+            ctx.sync()
+        assert ei.value.status == absmod.ABS_ERR_DEVICE
+    ctx.sync()   # the error is cleared once reported
+
+
+def test_invalid_arguments(ctx):
+    wl = synth.workload(0)
+    cfg = absmod.Config.from_workload(wl)
+    with pytest.raises(absmod.AbsError) as ei:
+        ctx.abs_estimate(cfg, torch.zeros((10, 2), device=dev()), torch.zeros((10, 2), device=dev()), 5)
+    assert ei.value.status == absmod.ABS_ERR_INVALID_ARG
