@@ -38,7 +38,7 @@ struct Setup {
     int64_t *d_q = nullptr;
     int64_t *d_lat_off = nullptr;
     int32_t *d_ijk = nullptr;
-    float2 *d_tw = nullptr;       // exp(-2 pi i t / N), t < N
+    float4 *d_tw = nullptr;       // exp(-2 pi i t / N), t < N, as double-float (re hi, lo, im hi, lo)
     int32_t *d_Rm = nullptr;
 };
 
@@ -97,10 +97,21 @@ abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, c
                                   float *d_grid, float *d_wsum, uint8_t *d_mask);
 abs_status launch_filter_fft(abs_ctx *ctx, const Setup &s, const float *d_grid,
                              const float *d_wsum, const uint8_t *d_mask, float *d_fields);
+// The same transform fed directly from the FP64 gridding accumulators (mirror
+// applied on the fly), as abs_estimate uses it.
+abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc, const uint8_t *hit,
+                                 float *d_fields);
+// FP64 accumulators [3][n*n] (re, im, w before the mirror) and hit flags of the
+// last launch_grid_accumulate on this context.
+void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc, uint8_t **hit);
 abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_fields,
                               int32_t n_trip, const int32_t *d_ijk, double *d_sum);
+// Ring tables (cell lists, byte map) from d_mask, then exact counts (d_count may be
+// NULL) and, if d_ellbar is not NULL, the mean l of every ring.
 abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, int32_t n_trip,
-                         const int32_t *d_ijk, int64_t *d_count);
+                         const int32_t *d_ijk, int64_t *d_count, double *d_ellbar);
+// Exclusive scan of len uint32 values; bsum holds cdiv(len, 4096) + 1 entries.
+void scan_u32(cudaStream_t st, const uint32_t *in, int64_t len, uint32_t *out, uint32_t *bsum);
 abs_status launch_normalise(abs_ctx *ctx, const Setup &s, int32_t n_trip, const double *d_sum,
                             const int64_t *d_count, double *d_B);
 abs_status launch_ellbar(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, double *d_ellbar);

@@ -259,10 +259,12 @@ const Setup *get_setup(abs_ctx *ctx, const abs_config *cfg, abs_status &st) {
         fail(ctx, st, err);
         return nullptr;
     }
-    std::vector<float2> tw(s->N);
+    std::vector<float4> tw(s->N);
     for (int t = 0; t < s->N; ++t) {
         const double a = 2.0 * M_PI * (double)t / (double)s->N;
-        tw[t] = make_float2((float)std::cos(a), (float)(-std::sin(a)));
+        const double c = std::cos(a), sn = -std::sin(a);
+        const float ch = (float)c, sh = (float)sn;
+        tw[t] = make_float4(ch, (float)(c - (double)ch), sh, (float)(sn - (double)sh));
     }
     s->d_q = upload(s->q);
     s->d_lat_off = upload(s->lat_off);
@@ -498,7 +500,7 @@ abs_status abs_triple(abs_ctx *ctx, const abs_config *cfg, const float *d_fields
     if (d_count && !d_mask) return fail(ctx, ABS_ERR_INVALID_ARG, "d_mask is NULL");
     ABS_CHECK(launch_check_triplets(ctx, *s, n_trip, d_ijk));
     if (d_sum) ABS_CHECK(launch_triple_sums(ctx, *s, d_fields, n_trip, d_ijk, d_sum));
-    if (d_count) ABS_CHECK(launch_counts(ctx, *s, d_mask, n_trip, d_ijk, d_count));
+    if (d_count) ABS_CHECK(launch_counts(ctx, *s, d_mask, n_trip, d_ijk, d_count, nullptr));
     return ABS_OK;
 }
 
@@ -535,10 +537,12 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
         ABS_CHECK(launch_grid_accumulate(ctx, s, n_vis, d_vis + (size_t)r * 2 * n_vis, grid, wsum, mask));
         if (r == 0) {
             // the filled mask depends on the baselines only: counts and mean l once
-            ABS_CHECK(launch_counts(ctx, s, mask, n_trip, d_ijk, count));
-            if (d_ellbar) ABS_CHECK(launch_ellbar(ctx, s, mask, d_ellbar));
+            ABS_CHECK(launch_counts(ctx, s, mask, n_trip, d_ijk, count, d_ellbar));
         }
-        ABS_CHECK(launch_filter_fft(ctx, s, grid, wsum, mask, fields));
+        double *acc;
+        uint8_t *hit;
+        grid_acc_buffers(ctx, s, &acc, &hit);
+        ABS_CHECK(launch_filter_fft_acc(ctx, s, acc, hit, fields));
         ABS_CHECK(launch_triple_sums(ctx, s, fields, n_trip, d_ijk, sum));
         if (d_B) ABS_CHECK(launch_normalise(ctx, s, n_trip, sum, count, d_B + (size_t)r * n_trip));
     }

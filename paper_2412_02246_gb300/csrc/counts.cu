@@ -20,7 +20,9 @@
 // run-length state for its g1 cells (consecutive g2 in row order usually
 // land in the same ring) and adds finished runs into a lane-private
 // shared-memory histogram over k, which is reduced into an int64 (i, j, k)
-// table at the end.
+// table at the end.  Of the two sets of a pair (upper half of F_i, all of
+// F_j) the larger is spread over the threads and the smaller is streamed, so
+// that no thread idles through a pass over a large ring.
 #include "abs_internal.cuh"
 
 namespace absk {
@@ -40,59 +42,99 @@ __device__ __forceinline__ int64_t cell_index(int n, int gx, int gy) {
     return (int64_t)(gy < 0 ? gy + n : gy) * n + (gx < 0 ? gx + n : gx);
 }
 
-// One CTA per ring: compact the filled cells of a_m in row-major order.
-__global__ void __launch_bounds__(1024) k_ring_lists(CountGeom G, const int64_t *__restrict__ q,
-                                                     const int32_t *__restrict__ Rm,
-                                                     const int64_t *__restrict__ lat_off,
-                                                     const uint8_t *__restrict__ mask,
-                                                     short2 *__restrict__ lists,
-                                                     int32_t *__restrict__ counts,
-                                                     uint8_t *__restrict__ binmap) {
-    __shared__ int32_t wsum[32];
-    __shared__ int32_t carry_s;
-    const int m = blockIdx.x;
-    const int Rr = Rm[m];
-    if (threadIdx.x == 0) carry_s = 0;
-    __syncthreads();
-    if (Rr < 0) {
-        if (threadIdx.x == 0) counts[m] = 0;
-        return;
+__device__ __forceinline__ int64_t isqrt_dev(int64_t v) {
+    if (v <= 0) return 0;
+    int64_t r = (int64_t)sqrt((double)v);
+    while (r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
+}
+
+// Cells of ring m in row y (|y| <= R): x in [-x1, -x0] and [x0, x1] clipped to
+// the grid (x0 = 0 contributes the single column x = 0 once).
+struct RowSpan {
+    int x0, x1;
+    bool ok;
+};
+__device__ __forceinline__ RowSpan row_span(const CountGeom &G, int64_t q0, int64_t q1, int y) {
+    RowSpan r{0, -1, false};
+    if (y < -G.half || y > G.half) return r;
+    const int64_t y2 = (int64_t)y * y;
+    const int64_t hi = q1 - 1 - y2;
+    if (hi < 0) return r;
+    const int64_t lo = q0 - y2;
+    int64_t x0 = lo <= 0 ? 0 : isqrt_dev(lo - 1) + 1;   // smallest x >= 0 with x^2 >= lo
+    int64_t x1 = isqrt_dev(hi);
+    if (x1 > G.half) x1 = G.half;
+    if (x0 > x1) return r;
+    r.x0 = (int)x0;
+    r.x1 = (int)x1;
+    r.ok = true;
+    return r;
+}
+
+// Pass 1: filled cells per (ring, row), FP64 sum of |g| per (ring, row).
+__global__ void k_ring_rows(CountGeom G, const int64_t *__restrict__ q, const uint8_t *__restrict__ mask,
+                            uint32_t *__restrict__ rowcnt, double *__restrict__ rowlen) {
+    const int rows = 2 * G.R + 1;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= G.nb * rows) return;
+    const int m = e / rows, y = e - m * rows - G.R;
+    const RowSpan sp = row_span(G, q[m], q[m + 1], y);
+    uint32_t c = 0;
+    double len = 0.0;
+    if (sp.ok) {
+        for (int x = -sp.x1; x <= sp.x1; ++x) {
+            if (x > -sp.x0 && x < sp.x0) x = sp.x0;   // skip the hole of the annulus
+            if (mask[cell_index(G.n, x, y)]) {
+                ++c;
+                len += sqrt((double)x * x + (double)y * y);
+            }
+        }
     }
-    const int side = 2 * Rr + 1;
-    const int64_t total = (int64_t)side * side;
-    const int64_t q0 = q[m], q1 = q[m + 1];
-    short2 *out = lists + lat_off[m];
-    const int64_t cap = lat_off[m + 1] - lat_off[m];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t b = 0; b < total; b += blockDim.x) {
-        const int64_t idx = b + threadIdx.x;
-        bool on = false;
-        int x = 0, y = 0;
-        if (idx < total) {
-            y = (int)(idx / side) - Rr;
-            x = (int)(idx % side) - Rr;
-            const int64_t r2 = (int64_t)x * x + (int64_t)y * y;
-            on = r2 >= q0 && r2 < q1 && x >= -G.half && x <= G.half && y >= -G.half &&
-                 y <= G.half && mask[cell_index(G.n, x, y)];
-        }
-        const unsigned bal = __ballot_sync(FULL, on);
-        if (lane == 0) wsum[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, tot = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            if (w < warp) before += wsum[w];
-            tot += wsum[w];
-        }
-        const int pos = carry_s + before + __popc(bal & ((1u << lane) - 1u));
-        if (on && pos < cap) {
-            out[pos] = make_short2((short)x, (short)y);
+    rowcnt[e] = c;
+    rowlen[e] = len;
+}
+
+// Pass 2: write the cells (row-major within each ring) and the byte ring map.
+__global__ void k_ring_write(CountGeom G, const int64_t *__restrict__ q, const uint8_t *__restrict__ mask,
+                             const uint32_t *__restrict__ rowoff, short2 *__restrict__ lists,
+                             uint8_t *__restrict__ binmap) {
+    const int rows = 2 * G.R + 1;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= G.nb * rows) return;
+    const int m = e / rows, y = e - m * rows - G.R;
+    const RowSpan sp = row_span(G, q[m], q[m + 1], y);
+    if (!sp.ok) return;
+    uint32_t pos = rowoff[e];
+    for (int x = -sp.x1; x <= sp.x1; ++x) {
+        if (x > -sp.x0 && x < sp.x0) x = sp.x0;
+        if (mask[cell_index(G.n, x, y)]) {
+            lists[pos++] = make_short2((short)x, (short)y);
             binmap[(int64_t)(y + 2 * G.R) * G.W + (x + 2 * G.R)] = (uint8_t)(m + 1);
         }
-        __syncthreads();
-        if (threadIdx.x == 0) carry_s += tot;
-        __syncthreads();
     }
-    if (threadIdx.x == 0) counts[m] = (int32_t)min((int64_t)carry_s, cap);
+}
+
+// Pass 3 (one thread per ring): ring offsets, counts and mean l (rows summed in order).
+__global__ void k_ring_finish(CountGeom G, float du, const uint32_t *__restrict__ rowoff,
+                              const uint32_t *__restrict__ rowcnt, const double *__restrict__ rowlen,
+                              int64_t *__restrict__ ring_off, int32_t *__restrict__ counts,
+                              double *__restrict__ ellbar) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= G.nb) return;
+    const int rows = 2 * G.R + 1;
+    const int64_t e0 = (int64_t)m * rows, e1 = e0 + rows;
+    const uint32_t start = rowoff[e0];
+    const uint32_t c = rowoff[e1 - 1] + rowcnt[e1 - 1] - start;
+    ring_off[m] = start;
+    counts[m] = (int32_t)c;
+    if (m == G.nb - 1) ring_off[G.nb] = start + c;
+    if (ellbar) {
+        double len = 0.0;
+        for (int64_t e = e0; e < e1; ++e) len += rowlen[e];
+        ellbar[m] = c > 0 ? 2.0 * 3.14159265358979323846 * (double)du * len / (double)c : nan("");
+    }
 }
 
 // One block: the (i, j, first g1) work items for every distinct (i, j) row of
@@ -111,6 +153,7 @@ __global__ void __launch_bounds__(1024) k_count_items(int nb, int32_t n_trip,
     for (int b = 0; b < n_trip; b += blockDim.x) {
         const int t = b + threadIdx.x;
         int nchunks = 0, i = 0, j = 0;
+        bool outer_i = false;
         if (t < n_trip) {
             i = ijk[3 * t];
             j = ijk[3 * t + 1];
@@ -125,8 +168,9 @@ __global__ void __launch_bounds__(1024) k_count_items(int nb, int32_t n_trip,
                 if (!ordered) atomicCAS(err, 0, DERR_TRIPLET_ORDER);
             }
             if (row_start && i >= 0 && i < nb && j >= 0 && j < nb) {
-                const int half_i = counts[i] / 2;
-                nchunks = (half_i + chunk - 1) / chunk;
+                const int half_i = counts[i] / 2, cj = counts[j];
+                outer_i = half_i >= cj;
+                nchunks = ((outer_i ? half_i : cj) + chunk - 1) / chunk;
             }
         }
         // block exclusive scan of nchunks (small values; warp-level then serial over warps)
@@ -145,7 +189,7 @@ __global__ void __launch_bounds__(1024) k_count_items(int nb, int32_t n_trip,
         }
         const int pos = carry_s + before + x - nchunks;
         for (int c = 0; c < nchunks; ++c)
-            if (pos + c < cap) items[pos + c] = make_int4(i, j, c * chunk, 0);
+            if (pos + c < cap) items[pos + c] = make_int4(i, j, c * chunk, outer_i ? 1 : 0);
         __syncthreads();
         if (threadIdx.x == 0) carry_s += tot;
         __syncthreads();
@@ -157,7 +201,7 @@ template <bool MAP_IN_SMEM>
 __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__restrict__ items,
                                                     const int *__restrict__ n_items,
                                                     const short2 *__restrict__ lists,
-                                                    const int64_t *__restrict__ lat_off,
+                                                    const int64_t *__restrict__ ring_off,
                                                     const int32_t *__restrict__ counts,
                                                     const uint8_t *__restrict__ binmap_g,
                                                     unsigned long long *__restrict__ Td) {
@@ -184,16 +228,19 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
         const int4 I = items[it];
         const int i = I.x, j = I.y;
         const int ci = counts[i], cj = counts[j];
-        const short2 *Fi = lists + lat_off[i] + ci / 2;   // upper half plane of ring i
-        const short2 *Fj = lists + lat_off[j];
+        const short2 *Fi = lists + ring_off[i] + ci / 2;   // upper half plane of ring i
+        const short2 *Fj = lists + ring_off[j];
         const int nh = ci / 2;
+        // outer set: spread over the threads; inner set: streamed through shared memory
+        const short2 *Fo = I.w ? Fi : Fj, *Fin = I.w ? Fj : Fi;
+        const int no = I.w ? nh : cj, nin = I.w ? cj : nh;
         int lin1[G1];
         bool v1[G1];
 #pragma unroll
         for (int q = 0; q < G1; ++q) {
             const int a = I.z + q * blockDim.x + threadIdx.x;
-            v1[q] = a < nh;
-            const short2 g = v1[q] ? Fi[a] : make_short2(0, 0);
+            v1[q] = a < no;
+            const short2 g = v1[q] ? Fo[a] : make_short2(0, 0);
             lin1[q] = g.y * G.W + g.x + (int)G.base;
         }
         int cur[G1];
@@ -203,11 +250,11 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
             cur[q] = 0;
             cnt[q] = 0;
         }
-        for (int s0 = 0; s0 < cj; s0 += STAGE) {
-            const int ns = min(STAGE, cj - s0);
+        for (int s0 = 0; s0 < nin; s0 += STAGE) {
+            const int ns = min(STAGE, nin - s0);
             __syncthreads();
             for (int a = threadIdx.x; a < ns; a += blockDim.x) {
-                const short2 g = Fj[s0 + a];
+                const short2 g = Fin[s0 + a];
                 stage[a] = g.y * G.W + g.x;
             }
             __syncthreads();
@@ -255,30 +302,6 @@ __global__ void k_count_gather(int nb, int32_t n_trip, const int32_t *__restrict
     T[t] = 2 * (int64_t)Td[((size_t)i * nb + j) * nb + k];
 }
 
-// Mean l of each ring over its filled cells (FP64, fixed-order tree per ring).
-__global__ void __launch_bounds__(256) k_ellbar(int nb, float du, const short2 *__restrict__ lists,
-                                                const int64_t *__restrict__ lat_off,
-                                                const int32_t *__restrict__ counts,
-                                                double *__restrict__ ellbar) {
-    __shared__ double sh[256];
-    const int m = blockIdx.x;
-    const int c = counts[m];
-    const short2 *L = lists + lat_off[m];
-    double s = 0.0;
-    for (int a = threadIdx.x; a < c; a += blockDim.x) {
-        const short2 g = L[a];
-        s += sqrt((double)g.x * g.x + (double)g.y * g.y);
-    }
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0)
-        ellbar[m] = c > 0 ? 2.0 * 3.14159265358979323846 * (double)du * sh[0] / (double)c : nan("");
-}
-
 CountGeom cgeom(const Setup &s) {
     CountGeom G;
     G.n = s.n;
@@ -293,32 +316,46 @@ CountGeom cgeom(const Setup &s) {
 struct RingBufs {
     short2 *lists;
     int32_t *counts;
+    int64_t *ring_off;
     uint8_t *binmap;
 };
 
-abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, RingBufs &rb) {
+abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, RingBufs &rb,
+                       double *d_ellbar) {
     const CountGeom G = cgeom(s);
     const int64_t ncell = std::max<int64_t>(s.lat_off.back(), 1);
+    const int64_t nrow = (int64_t)s.nb * (2 * s.R + 1);
     rb.lists = (short2 *)workspace(ctx, "ring.lists", sizeof(short2) * ncell);
     rb.counts = (int32_t *)workspace(ctx, "ring.counts", sizeof(int32_t) * s.nb);
+    rb.ring_off = (int64_t *)workspace(ctx, "ring.off", sizeof(int64_t) * (s.nb + 1));
     const int64_t mb = (int64_t)G.W * G.W;
     rb.binmap = (uint8_t *)workspace(ctx, "ring.binmap", (size_t)cdiv(mb, 16) * 16);
-    if (!rb.lists || !rb.counts || !rb.binmap) return fail(ctx, ABS_ERR_OOM, "ring table workspace");
+    uint32_t *rowcnt = (uint32_t *)workspace(ctx, "ring.rowcnt", sizeof(uint32_t) * nrow);
+    uint32_t *rowoff = (uint32_t *)workspace(ctx, "ring.rowoff", sizeof(uint32_t) * nrow);
+    double *rowlen = (double *)workspace(ctx, "ring.rowlen", sizeof(double) * nrow);
+    uint32_t *bsum = (uint32_t *)workspace(ctx, "ring.bsum", sizeof(uint32_t) * (cdiv(nrow, 4096) + 1));
+    if (!rb.lists || !rb.counts || !rb.ring_off || !rb.binmap || !rowcnt || !rowoff || !rowlen || !bsum)
+        return fail(ctx, ABS_ERR_OOM, "ring table workspace");
     StageTimer timer(ctx, "ring_lists");
-    cudaMemsetAsync(rb.binmap, 0, (size_t)cdiv(mb, 16) * 16, ctx->stream);
-    k_ring_lists<<<s.nb, 1024, 0, ctx->stream>>>(G, s.d_q, s.d_Rm, s.d_lat_off, d_mask, rb.lists,
-                                                 rb.counts, rb.binmap);
+    cudaStream_t st = ctx->stream;
+    cudaMemsetAsync(rb.binmap, 0, (size_t)cdiv(mb, 16) * 16, st);
+    const int nbk = (int)cdiv(nrow, 128);
+    k_ring_rows<<<nbk, 128, 0, st>>>(G, s.d_q, d_mask, rowcnt, rowlen);
+    scan_u32(st, rowcnt, nrow, rowoff, bsum);
+    k_ring_write<<<nbk, 128, 0, st>>>(G, s.d_q, d_mask, rowoff, rb.lists, rb.binmap);
+    k_ring_finish<<<(int)cdiv(s.nb, 128), 128, 0, st>>>(G, s.du, rowoff, rowcnt, rowlen, rb.ring_off,
+                                                        rb.counts, d_ellbar);
     return check_launch(ctx, "ring lists");
 }
 
 }  // namespace
 
 abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, int32_t n_trip,
-                         const int32_t *d_ijk, int64_t *d_count) {
+                         const int32_t *d_ijk, int64_t *d_count, double *d_ellbar) {
     RingBufs rb;
-    abs_status st = ring_tables(ctx, s, d_mask, rb);
+    abs_status st = ring_tables(ctx, s, d_mask, rb, d_ellbar);
     if (st != ABS_OK) return st;
-    if (n_trip == 0) return ABS_OK;
+    if (n_trip == 0 || !d_count) return ABS_OK;
     const CountGeom G = cgeom(s);
     // threads per CTA: lane-private histograms must fit next to the map
     const int hs = s.nb + 1;
@@ -331,9 +368,9 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     const int chunk = threads * G1;
     const size_t smem = (size_t)nwarps * hs * 32 * 4 + STAGE * 4 + (map_smem ? map_bytes : 0);
     // work items: one per (row, chunk of the upper half of ring i)
-    int64_t max_half = 0;
-    for (int m = 0; m < s.nb; ++m) max_half = std::max<int64_t>(max_half, s.lat[m] / 2);
-    const int cap = (int)std::min<int64_t>((int64_t)n_trip * cdiv(std::max<int64_t>(max_half, 1), chunk), 1 << 26);
+    int64_t max_ring = 0;
+    for (int m = 0; m < s.nb; ++m) max_ring = std::max<int64_t>(max_ring, s.lat[m]);
+    const int cap = (int)std::min<int64_t>((int64_t)n_trip * cdiv(std::max<int64_t>(max_ring, 1), chunk), 1 << 26);
     int4 *items = (int4 *)workspace(ctx, "count.items", sizeof(int4) * cap);
     int *n_items = (int *)workspace(ctx, "count.n_items", sizeof(int));
     const size_t td_bytes = sizeof(unsigned long long) * (size_t)s.nb * s.nb * s.nb;
@@ -351,11 +388,11 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     const int blocks = ctx->sm_count * (map_smem ? 1 : 2);
     if (map_smem) {
         cudaFuncSetAttribute(k_count_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_count_pairs<true><<<blocks, threads, smem, stm>>>(G, items, n_items, rb.lists, s.d_lat_off,
+        k_count_pairs<true><<<blocks, threads, smem, stm>>>(G, items, n_items, rb.lists, rb.ring_off,
                                                             rb.counts, rb.binmap, Td);
     } else {
         cudaFuncSetAttribute(k_count_pairs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_count_pairs<false><<<blocks, threads, smem, stm>>>(G, items, n_items, rb.lists, s.d_lat_off,
+        k_count_pairs<false><<<blocks, threads, smem, stm>>>(G, items, n_items, rb.lists, rb.ring_off,
                                                              rb.counts, rb.binmap, Td);
     }
     }
@@ -368,11 +405,7 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
 
 abs_status launch_ellbar(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, double *d_ellbar) {
     RingBufs rb;
-    abs_status st = ring_tables(ctx, s, d_mask, rb);
-    if (st != ABS_OK) return st;
-    StageTimer timer(ctx, "ellbar");
-    k_ellbar<<<s.nb, 256, 0, ctx->stream>>>(s.nb, s.du, rb.lists, s.d_lat_off, rb.counts, d_ellbar);
-    return check_launch(ctx, "ellbar");
+    return ring_tables(ctx, s, d_mask, rb, d_ellbar);
 }
 
 }  // namespace absk

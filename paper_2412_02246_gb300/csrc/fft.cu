@@ -7,15 +7,23 @@
 //
 // The 2D transform is a row pass then a column pass.  Only the rows
 // |g_y| <= R_b of a ring pair are nonzero, so the row pass transforms just
-// those (2 R_b + 1 of N) rows into a compact intermediate [2R_b+1][N]; the
-// column pass reads CW adjacent columns of it (coalesced), expands each to
-// length N with the zero rows, and writes CW columns of both fields.
+// those rows into a compact intermediate [2R+1][N]; the column pass reads CW
+// adjacent columns of it, expands each to length N with the zero rows, and
+// writes CW columns of both fields.
 //
-// Both passes are radix-2/3/4/5 Stockham transforms in shared memory (the
-// autosort form: pass with span p and radix R reads x[i + q N/R], applies
-// the twiddle exp(-2 pi i q (i mod p) / (p R)), and writes the R outputs at
-// (i div p) p R + (i mod p) + s p).  Twiddles come from a table of
-// exp(-2 pi i t / N) evaluated in double on the host.
+// Arithmetic.  Rounding inside an FP32 FFT leaves an error of order
+// eps log N ||X|| on every output, independent of the output's size, and
+// the triple sums amplify it by their cancellation; rounding the exact
+// field to FP32 once costs far less.  The butterflies therefore run in
+// double-float: every real is an unevaluated sum hi + lo of two FP32 values
+// (Dekker/Knuth two-sum and FMA two-product), twiddles and radix constants
+// carry their own low parts, and only the output is rounded to FP32.
+//
+// Both passes are radix-2/3/4/5 Stockham transforms in shared memory (pass
+// with span p and radix R reads x[i + q N/R], applies the twiddle
+// exp(-2 pi i q (i mod p) / (p R)), and writes the R outputs at
+// (i div p) p R + (i mod p) + s p); divisions by runtime constants use
+// precomputed multiply-high magic numbers.
 #include "abs_internal.cuh"
 
 namespace absk {
@@ -23,88 +31,134 @@ namespace {
 
 constexpr int MAXRAD = 16;
 
+struct FftPass {
+    int R, p, T, tstep;
+    uint32_t mag_p, mag_T;   // floor(x / p) = umulhi(x, mag_p) for x < 2^16
+};
+
 struct FftPlan {
     int N, nrad;
-    int rad[MAXRAD];
+    FftPass pass[MAXRAD];
 };
 
 struct RingGeom {
     int n, half, nb, N, Rmax;
 };
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+// ------------------------------------------------------------------ double-float
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fsub_rn(s, a.hi);
+    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    const float hi = __fadd_rn(s, e);
+    return {hi, __fsub_rn(e, __fsub_rn(hi, s))};
 }
-__device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }  // a * (-i)
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float hi = __fadd_rn(p, e);
+    return {hi, __fsub_rn(e, __fsub_rn(hi, p))};
+}
+__device__ __forceinline__ df df_scale_half(df a) { return {0.5f * a.hi, 0.5f * a.lo}; }
+
+// complex double-float, stored as float4 (re.hi, re.lo, im.hi, im.lo)
+struct cdf {
+    df re, im;
+};
+__device__ __forceinline__ cdf ld(const float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+__device__ __forceinline__ float4 st(cdf a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+__device__ __forceinline__ cdf c_add(cdf a, cdf b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ cdf c_sub(cdf a, cdf b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+__device__ __forceinline__ cdf c_mul(cdf a, cdf w) {
+    return {df_sub(df_mul(a.re, w.re), df_mul(a.im, w.im)), df_add(df_mul(a.re, w.im), df_mul(a.im, w.re))};
+}
+__device__ __forceinline__ cdf c_mi(cdf a) { return {a.im, df_neg(a.re)}; }  // a * (-i)
+__device__ __forceinline__ cdf c_scale(cdf a, df s) { return {df_mul(a.re, s), df_mul(a.im, s)}; }
+
+// radix constants as double-float pairs
+constexpr double kS3 = 0.86602540378443864676372317075294;   // sin(2 pi / 3)
+constexpr double kC1 = 0.30901699437494742410229341718282;   // cos(2 pi / 5)
+constexpr double kC2 = -0.80901699437494742410229341718282;  // cos(4 pi / 5)
+constexpr double kS1 = 0.95105651629515357211643933337938;   // sin(2 pi / 5)
+constexpr double kS2 = 0.58778525229247312916870595463907;   // sin(4 pi / 5)
+__device__ __forceinline__ df dfc(double v) {
+    const float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
 
 // One Stockham pass over `lines` transforms of length N stored line-major.
-__device__ __forceinline__ void stockham_pass(const float2 *__restrict__ in, float2 *__restrict__ out,
-                                              int N, int R, int p, int lines,
-                                              const float2 *__restrict__ tw) {
-    const int T = N / R;
-    const int tstep = N / (p * R);
-    const int nb = lines * T;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const int l = b / T, i = b - l * T;
-        const int k = i % p;
-        const float2 *src = in + (size_t)l * N + i;
-        float2 *dst = out + (size_t)l * N + (i - k) * R + k;
-        float2 x[5];
-        x[0] = src[0];
-        for (int q = 1; q < R; ++q) {
-            const float2 v = src[q * T];
-            x[q] = k ? cmul(v, __ldg(&tw[q * k * tstep])) : v;
+__device__ __forceinline__ void stockham_pass(const float4 *__restrict__ in, float4 *__restrict__ out,
+                                              int N, const FftPass &P, int lines,
+                                              const float4 *__restrict__ tw) {
+    const int R = P.R, p = P.p, T = P.T;
+    const int nbf = lines * T;
+    for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
+        const int l = (int)__umulhi((uint32_t)b, P.mag_T);
+        const int i = b - l * T;
+        const int ip = p == 1 ? i : (int)__umulhi((uint32_t)i, P.mag_p);
+        const int k = i - ip * p;
+        const float4 *src = in + (size_t)l * N + i;
+        float4 *dst = out + (size_t)l * N + ip * p * R + k;
+        cdf x[5];
+        x[0] = ld(src[0]);
+#pragma unroll
+        for (int q = 1; q < 5; ++q) {
+            if (q < R) {
+                const cdf v = ld(src[q * T]);
+                x[q] = k ? c_mul(v, ld(tw[q * k * P.tstep])) : v;
+            }
         }
         if (R == 4) {
-            const float2 a0 = cadd(x[0], x[2]), a1 = csub(x[0], x[2]);
-            const float2 b0 = cadd(x[1], x[3]), b1 = cmul_mi(csub(x[1], x[3]));
-            dst[0] = cadd(a0, b0);
-            dst[p] = cadd(a1, b1);
-            dst[2 * p] = csub(a0, b0);
-            dst[3 * p] = csub(a1, b1);
+            const cdf a0 = c_add(x[0], x[2]), a1 = c_sub(x[0], x[2]);
+            const cdf b0 = c_add(x[1], x[3]), b1 = c_mi(c_sub(x[1], x[3]));
+            dst[0] = st(c_add(a0, b0));
+            dst[p] = st(c_add(a1, b1));
+            dst[2 * p] = st(c_sub(a0, b0));
+            dst[3 * p] = st(c_sub(a1, b1));
         } else if (R == 2) {
-            dst[0] = cadd(x[0], x[1]);
-            dst[p] = csub(x[0], x[1]);
+            dst[0] = st(c_add(x[0], x[1]));
+            dst[p] = st(c_sub(x[0], x[1]));
         } else if (R == 3) {
-            const float s3 = 0.866025403784438646763723f;  // sin(2 pi / 3)
-            const float2 t = cadd(x[1], x[2]);
-            const float2 m = make_float2(x[0].x - 0.5f * t.x, x[0].y - 0.5f * t.y);
-            const float2 dd = cscale(cmul_mi(csub(x[1], x[2])), s3);
-            dst[0] = cadd(x[0], t);
-            dst[p] = cadd(m, dd);
-            dst[2 * p] = csub(m, dd);
+            const cdf t = c_add(x[1], x[2]);
+            const cdf m = c_sub(x[0], {df_scale_half(t.re), df_scale_half(t.im)});
+            const cdf d = c_scale(c_mi(c_sub(x[1], x[2])), dfc(kS3));
+            dst[0] = st(c_add(x[0], t));
+            dst[p] = st(c_add(m, d));
+            dst[2 * p] = st(c_sub(m, d));
         } else {  // R == 5
-            const float c1 = 0.309016994374947424102293f;   // cos(2 pi / 5)
-            const float c2 = -0.809016994374947424102293f;  // cos(4 pi / 5)
-            const float s1 = 0.951056516295153572116439f;   // sin(2 pi / 5)
-            const float s2 = 0.587785252292473129168706f;   // sin(4 pi / 5)
-            const float2 t1 = cadd(x[1], x[4]), t2 = cadd(x[2], x[3]);
-            const float2 t3 = csub(x[1], x[4]), t4 = csub(x[2], x[3]);
-            const float2 a1 = make_float2(x[0].x + c1 * t1.x + c2 * t2.x, x[0].y + c1 * t1.y + c2 * t2.y);
-            const float2 a2 = make_float2(x[0].x + c2 * t1.x + c1 * t2.x, x[0].y + c2 * t1.y + c1 * t2.y);
-            const float2 b1 = make_float2(s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y);
-            const float2 b2 = make_float2(s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y);
-            dst[0] = cadd(x[0], cadd(t1, t2));
-            dst[p] = cadd(a1, cmul_mi(b1));
-            dst[4 * p] = csub(a1, cmul_mi(b1));
-            dst[2 * p] = cadd(a2, cmul_mi(b2));
-            dst[3 * p] = csub(a2, cmul_mi(b2));
+            const df c1 = dfc(kC1), c2 = dfc(kC2), s1 = dfc(kS1), s2 = dfc(kS2);
+            const cdf t1 = c_add(x[1], x[4]), t2 = c_add(x[2], x[3]);
+            const cdf t3 = c_sub(x[1], x[4]), t4 = c_sub(x[2], x[3]);
+            const cdf a1 = c_add(x[0], c_add(c_scale(t1, c1), c_scale(t2, c2)));
+            const cdf a2 = c_add(x[0], c_add(c_scale(t1, c2), c_scale(t2, c1)));
+            const cdf b1 = c_mi(c_add(c_scale(t3, s1), c_scale(t4, s2)));
+            const cdf b2 = c_mi(c_sub(c_scale(t3, s2), c_scale(t4, s1)));
+            dst[0] = st(c_add(x[0], c_add(t1, t2)));
+            dst[p] = st(c_add(a1, b1));
+            dst[4 * p] = st(c_sub(a1, b1));
+            dst[2 * p] = st(c_add(a2, b2));
+            dst[3 * p] = st(c_sub(a2, b2));
         }
     }
 }
 
 // Transforms `lines` lines in buffer a (scratch b); returns the buffer holding the result.
-__device__ float2 *fft_lines(float2 *a, float2 *b, int lines, const FftPlan &P,
-                             const float2 *__restrict__ tw) {
-    int p = 1;
+__device__ float4 *fft_lines(float4 *a, float4 *b, int lines, const FftPlan &P,
+                             const float4 *__restrict__ tw) {
     for (int s = 0; s < P.nrad; ++s) {
         __syncthreads();
-        stockham_pass(a, b, P.N, P.rad[s], p, lines, tw);
-        p *= P.rad[s];
-        float2 *t = a;
+        stockham_pass(a, b, P.N, P.pass[s], lines, tw);
+        float4 *t = a;
         a = b;
         b = t;
     }
@@ -112,57 +166,84 @@ __device__ float2 *fft_lines(float2 *a, float2 *b, int lines, const FftPlan &P,
     return a;
 }
 
-__device__ __forceinline__ int bin_lookup(int64_t r2, int a, int b, const int64_t *__restrict__ q) {
-    // 0: ring a, 1: ring b, -1: neither
-    if (r2 >= q[a] && r2 < q[a + 1]) return 0;
-    if (b >= 0 && r2 >= q[b] && r2 < q[b + 1]) return 1;
-    return -1;
+__device__ __forceinline__ float4 cdf_from_double(double re, double im) {
+    const float rh = (float)re, ih = (float)im;
+    return make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
 }
 
-// Row pass: one CTA per (row y, ring pair).  W[pair][y + Rmax][N].
-__global__ void __launch_bounds__(256) k_fft_rows(RingGeom G, FftPlan P, const int64_t *__restrict__ q,
-                                                  const int32_t *__restrict__ Rm,
-                                                  const float2 *__restrict__ grid,
-                                                  const float *__restrict__ wsum,
-                                                  const uint8_t *__restrict__ mask,
-                                                  const float2 *__restrict__ tw,
-                                                  float2 *__restrict__ W) {
-    extern __shared__ float2 sbuf[];
+// Gridded data as the transform reads it: the weighted mean on a filled cell.
+struct GridF32 {   // abs_grid outputs (FP32)
+    const float2 *grid;
+    const float *wsum;
+    const uint8_t *mask;
+    __device__ bool value(int64_t cell, int64_t mcell, double &re, double &im) const {
+        if (!mask[cell]) return false;
+        const float2 g = grid[cell];
+        const double w = (double)wsum[cell];
+        re = (double)g.x / w;
+        im = (double)g.y / w;
+        return true;
+    }
+};
+struct GridF64 {   // FP64 accumulators before the mirror (inside abs_estimate)
+    const double *re, *im, *w;
+    const uint8_t *hit;
+    __device__ bool value(int64_t cell, int64_t mcell, double &vr, double &vi) const {
+        if (!(hit[cell] | hit[mcell])) return false;
+        const double ww = w[cell] + w[mcell];
+        vr = (re[cell] + re[mcell]) / ww;
+        vi = (im[cell] - im[mcell]) / ww;
+        return true;
+    }
+};
+
+// Row pass: one CTA per (block of RB rows, ring pair).  W[pair][y + Rmax][N].
+template <class Src>
+__global__ void __launch_bounds__(256) k_fft_rows(RingGeom G, FftPlan P, int RB, const int64_t *__restrict__ q,
+                                                  const int32_t *__restrict__ Rm, Src src,
+                                                  const float4 *__restrict__ tw_g,
+                                                  float4 *__restrict__ W) {
+    extern __shared__ float4 sbuf[];
     const int pair = blockIdx.y;
     const int a = 2 * pair, b = a + 1 < G.nb ? a + 1 : -1;
     const int Rp = max(Rm[a], b >= 0 ? Rm[b] : -1);
-    const int y = (int)blockIdx.x - G.Rmax;
-    if (Rp < 0 || y < -Rp || y > Rp) return;
-    float2 *l0 = sbuf, *l1 = sbuf + G.N;
-    for (int i = threadIdx.x; i < G.N; i += blockDim.x) l0[i] = make_float2(0.f, 0.f);
+    const int y0 = (int)blockIdx.x * RB - G.Rmax;
+    if (Rp < 0 || y0 > Rp || y0 + RB - 1 < -Rp) return;
+    float4 *tw = sbuf;
+    float4 *l0 = sbuf + G.N, *l1 = l0 + (size_t)RB * G.N;
+    for (int i = threadIdx.x; i < G.N; i += blockDim.x) tw[i] = tw_g[i];
+    for (int i = threadIdx.x; i < RB * G.N; i += blockDim.x) l0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
-    if (y >= -G.half && y <= G.half) {
-        for (int x = -Rp + (int)threadIdx.x; x <= Rp; x += blockDim.x) {
-            if (x < -G.half || x > G.half) continue;
-            const int64_t r2 = (int64_t)x * x + (int64_t)y * y;
-            const int which = bin_lookup(r2, a, b, q);
-            if (which < 0) continue;
-            const int64_t cell = (int64_t)(y < 0 ? y + G.n : y) * G.n + (x < 0 ? x + G.n : x);
-            if (!mask[cell]) continue;
-            const float2 g = grid[cell];
-            const float w = wsum[cell];
-            const float2 v = make_float2(__fdiv_rn(g.x, w), __fdiv_rn(g.y, w));
-            // Z = X_a + i X_b
-            l0[x < 0 ? x + G.N : x] = which == 0 ? v : make_float2(-v.y, v.x);
-        }
+    const int span = 2 * Rp + 1;
+    const int64_t qa0 = q[a], qa1 = q[a + 1], qb0 = b >= 0 ? q[b] : 0, qb1 = b >= 0 ? q[b + 1] : 0;
+    for (int e = threadIdx.x; e < RB * span; e += blockDim.x) {
+        const int r = e / span, x = e - r * span - Rp, y = y0 + r;
+        if (y < -Rp || y > Rp || y < -G.half || y > G.half || x < -G.half || x > G.half) continue;
+        const int64_t r2 = (int64_t)x * x + (int64_t)y * y;
+        const bool in_a = r2 >= qa0 && r2 < qa1, in_b = b >= 0 && r2 >= qb0 && r2 < qb1;
+        if (!in_a && !in_b) continue;
+        const int64_t cell = (int64_t)(y < 0 ? y + G.n : y) * G.n + (x < 0 ? x + G.n : x);
+        const int64_t mcell = (int64_t)(y > 0 ? G.n - y : -y) * G.n + (x > 0 ? G.n - x : -x);
+        double vr, vi;
+        if (!src.value(cell, mcell, vr, vi)) continue;
+        // Z = X_a + i X_b
+        l0[(size_t)r * G.N + (x < 0 ? x + G.N : x)] = in_a ? cdf_from_double(vr, vi) : cdf_from_double(-vi, vr);
     }
-    float2 *res = fft_lines(l0, l1, 1, P, tw);
-    float2 *dst = W + ((size_t)pair * (2 * G.Rmax + 1) + (y + G.Rmax)) * G.N;
-    for (int i = threadIdx.x; i < G.N; i += blockDim.x) dst[i] = res[i];
+    float4 *res = fft_lines(l0, l1, RB, P, tw);
+    for (int e = threadIdx.x; e < RB * G.N; e += blockDim.x) {
+        const int r = e / G.N, y = y0 + r;
+        if (y < -Rp || y > Rp) continue;
+        W[((size_t)pair * (2 * G.Rmax + 1) + (y + G.Rmax)) * G.N + (e - r * G.N)] = res[e];
+    }
 }
 
 // Column pass: one CTA per (CW-column tile, ring pair).
 __global__ void __launch_bounds__(256) k_fft_cols(RingGeom G, FftPlan P, int CW,
                                                   const int32_t *__restrict__ Rm,
-                                                  const float2 *__restrict__ W,
-                                                  const float2 *__restrict__ tw,
+                                                  const float4 *__restrict__ W,
+                                                  const float4 *__restrict__ tw_g,
                                                   float *__restrict__ fields) {
-    extern __shared__ float2 sbuf[];
+    extern __shared__ float4 sbuf[];
     const int pair = blockIdx.y;
     const int a = 2 * pair, b = a + 1 < G.nb ? a + 1 : -1;
     const int Rp = max(Rm[a], b >= 0 ? Rm[b] : -1);
@@ -177,66 +258,105 @@ __global__ void __launch_bounds__(256) k_fft_cols(RingGeom G, FftPlan P, int CW,
         }
         return;
     }
-    float2 *l0 = sbuf, *l1 = sbuf + (size_t)CW * G.N;
-    for (int i = threadIdx.x; i < CW * G.N; i += blockDim.x) l0[i] = make_float2(0.f, 0.f);
+    float4 *tw = sbuf;
+    float4 *l0 = sbuf + G.N, *l1 = l0 + (size_t)CW * G.N;
+    for (int i = threadIdx.x; i < G.N; i += blockDim.x) tw[i] = tw_g[i];
+    for (int i = threadIdx.x; i < CW * G.N; i += blockDim.x) l0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     const int rows = 2 * Rp + 1;
-    const float2 *src = W + (size_t)pair * (2 * G.Rmax + 1) * G.N;
+    const float4 *src = W + (size_t)pair * (2 * G.Rmax + 1) * G.N;
     for (int i = threadIdx.x; i < rows * cw; i += blockDim.x) {
         const int row = i / cw, c = i - row * cw;
         const int y = row - Rp;
         l0[(size_t)c * G.N + (y < 0 ? y + G.N : y)] = src[(size_t)(y + G.Rmax) * G.N + x0 + c];
     }
-    float2 *res = fft_lines(l0, l1, CW, P, tw);
+    float4 *res = fft_lines(l0, l1, CW, P, tw);
     for (int i = threadIdx.x; i < G.N * cw; i += blockDim.x) {
         const int py = i / cw, c = i - py * cw;
-        const float2 v = res[(size_t)c * G.N + py];
-        fields[(size_t)a * P2 + (size_t)py * G.N + x0 + c] = v.x;
-        if (b >= 0) fields[(size_t)b * P2 + (size_t)py * G.N + x0 + c] = v.y;
+        const float4 v = res[(size_t)c * G.N + py];
+        fields[(size_t)a * P2 + (size_t)py * G.N + x0 + c] = __fadd_rn(v.x, v.y);
+        if (b >= 0) fields[(size_t)b * P2 + (size_t)py * G.N + x0 + c] = __fadd_rn(v.z, v.w);
     }
+}
+
+uint32_t magic(int d) {  // floor(x / d) == umulhi(x, magic(d)) for 0 <= x < 2^16, 2 <= d < 2^16
+    return d < 2 ? 0u : (uint32_t)(((uint64_t)1 << 32) / (uint64_t)d + 1);
 }
 
 FftPlan make_plan(const Setup &s) {
     FftPlan P;
     P.N = s.N;
     P.nrad = (int)s.radices.size();
-    for (int i = 0; i < P.nrad && i < MAXRAD; ++i) P.rad[i] = s.radices[i];
+    int p = 1;
+    for (int i = 0; i < P.nrad && i < MAXRAD; ++i) {
+        FftPass &q = P.pass[i];
+        q.R = s.radices[i];
+        q.p = p;
+        q.T = s.N / q.R;
+        q.tstep = s.N / (p * q.R);
+        q.mag_p = magic(p);
+        q.mag_T = magic(q.T);
+        p *= q.R;
+    }
     return P;
+}
+
+struct FftLaunch {
+    int RB, CW;
+    size_t row_smem, col_smem;
+};
+
+FftLaunch fft_launch(const Setup &s) {
+    FftLaunch L;
+    const size_t line = sizeof(float4) * (size_t)s.N;
+    L.RB = 8;
+    while (L.RB > 1 && line * (2 * L.RB + 1) > 96 * 1024) L.RB >>= 1;
+    L.CW = 16;
+    while (L.CW > 1 && line * (2 * L.CW + 1) > 96 * 1024) L.CW >>= 1;
+    L.row_smem = line * (2 * L.RB + 1);
+    L.col_smem = line * (2 * L.CW + 1);
+    return L;
+}
+
+template <class Src>
+abs_status run_fft(abs_ctx *ctx, const Setup &s, const Src &src, float *d_fields) {
+    if ((int)s.radices.size() > MAXRAD) return fail(ctx, ABS_ERR_UNSUPPORTED, "FFT radix plan too long");
+    RingGeom G{s.n, s.half, s.nb, s.N, s.R};
+    const FftPlan P = make_plan(s);
+    const FftLaunch L = fft_launch(s);
+    const int npairs = (s.nb + 1) / 2;
+    const size_t wbytes = sizeof(float4) * (size_t)npairs * (2 * s.R + 1) * s.N;
+    float4 *W = (float4 *)workspace(ctx, "fft.rows", wbytes);
+    if (!W) return fail(ctx, ABS_ERR_OOM, "FFT row workspace");
+    cudaStream_t st = ctx->stream;
+    cudaFuncSetAttribute(k_fft_rows<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.row_smem);
+    cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.col_smem);
+    {
+        StageTimer timer(ctx, "fft_rows");
+        k_fft_rows<Src><<<dim3((unsigned)cdiv(2 * s.R + 1, L.RB), npairs), 256, L.row_smem, st>>>(
+            G, P, L.RB, s.d_q, s.d_Rm, src, (const float4 *)s.d_tw, W);
+    }
+    {
+        StageTimer timer(ctx, "fft_cols");
+        k_fft_cols<<<dim3((unsigned)cdiv(s.N, L.CW), npairs), 256, L.col_smem, st>>>(
+            G, P, L.CW, s.d_Rm, W, (const float4 *)s.d_tw, d_fields);
+    }
+    return check_launch(ctx, "filter+FFT");
 }
 
 }  // namespace
 
 abs_status launch_filter_fft(abs_ctx *ctx, const Setup &s, const float *d_grid, const float *d_wsum,
                              const uint8_t *d_mask, float *d_fields) {
-    if ((int)s.radices.size() > MAXRAD) return fail(ctx, ABS_ERR_UNSUPPORTED, "FFT radix plan too long");
-    RingGeom G{s.n, s.half, s.nb, s.N, s.R};
-    const FftPlan P = make_plan(s);
-    const int npairs = (s.nb + 1) / 2;
-    const size_t wbytes = sizeof(float2) * (size_t)npairs * (2 * s.R + 1) * s.N;
-    float2 *W = (float2 *)workspace(ctx, "fft.rows", wbytes);
-    if (!W) return fail(ctx, ABS_ERR_OOM, "FFT row workspace");
-    cudaStream_t st = ctx->stream;
-    const size_t row_smem = sizeof(float2) * 2 * s.N;
-    int CW = 32;
-    while (CW > 1 && sizeof(float2) * 2 * (size_t)CW * s.N > 96 * 1024) CW >>= 1;
-    const size_t col_smem = sizeof(float2) * 2 * (size_t)CW * s.N;
-    static bool attr_set[64] = {};
-    if (ctx->device < 64 && !attr_set[ctx->device]) {
-        cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr_set[ctx->device] = true;
-    }
-    {
-        StageTimer timer(ctx, "fft_rows");
-        k_fft_rows<<<dim3(2 * s.R + 1, npairs), 256, row_smem, st>>>(
-            G, P, s.d_q, s.d_Rm, (const float2 *)d_grid, d_wsum, d_mask, s.d_tw, W);
-    }
-    {
-        StageTimer timer(ctx, "fft_cols");
-        k_fft_cols<<<dim3((unsigned)cdiv(s.N, CW), npairs), 256, col_smem, st>>>(G, P, CW, s.d_Rm, W,
-                                                                               s.d_tw, d_fields);
-    }
-    return check_launch(ctx, "filter+FFT");
+    GridF32 src{(const float2 *)d_grid, d_wsum, d_mask};
+    return run_fft(ctx, s, src, d_fields);
+}
+
+abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc, const uint8_t *hit,
+                                 float *d_fields) {
+    const int64_t cells = (int64_t)s.n * s.n;
+    GridF64 src{acc, acc + cells, acc + 2 * cells, hit};
+    return run_fft(ctx, s, src, d_fields);
 }
 
 }  // namespace absk

@@ -36,7 +36,6 @@ constexpr int HS_MAX = TS + 2 * ABS_MAX_RADIUS;
 constexpr int HC = HS_MAX * HS_MAX;          // halo-tile cells
 constexpr int FWMAX = 2 * ABS_MAX_RADIUS + 1;
 constexpr unsigned FULL = 0xffffffffu;
-constexpr uint32_t KEY_NONE = 0xffffffffu;
 
 struct GridGeom {
     int n, half, r, ks, tt, off, kernel;
@@ -89,11 +88,12 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 // ------------------------------------------------------------------ plan kernels
 
 __global__ void k_plan_keys(GridGeom G, int64_t n_vis, const float2 *__restrict__ uv,
-                            uint32_t *__restrict__ keys, uint32_t *__restrict__ hist) {
+                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                            uint32_t *__restrict__ hist, uint32_t key_none) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_vis;
          i += (int64_t)gridDim.x * blockDim.x) {
         const float2 p = uv[i];
-        uint32_t key = KEY_NONE;
+        uint32_t key = key_none;
         if (isfinite(p.x) && isfinite(p.y)) {
             const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
             if (fabsf(qx) < 1.0e7f && fabsf(qy) < 1.0e7f) {
@@ -109,6 +109,7 @@ __global__ void k_plan_keys(GridGeom G, int64_t n_vis, const float2 *__restrict_
             }
         }
         keys[i] = key;
+        vals[i] = (uint32_t)i;
     }
 }
 
@@ -182,28 +183,88 @@ __global__ void k_scan_add(uint32_t *__restrict__ out, int64_t len,
     if (i < len) out[i] += block_sums[i / 4096];
 }
 
-__global__ void k_plan_scatter(int64_t n_vis, const float2 *__restrict__ uv,
-                               const uint32_t *__restrict__ keys, uint32_t *__restrict__ cursor,
-                               float2 *__restrict__ s_uv, uint32_t *__restrict__ s_idx,
-                               uint32_t *__restrict__ s_key) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_vis;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t key = keys[i];
-        if (key == KEY_NONE) continue;
-        const uint32_t pos = atomicAdd(&cursor[key], 1u);
-        s_uv[pos] = uv[i];
-        s_idx[pos] = (uint32_t)i;
-        s_key[pos] = key;
+// Stable LSD radix sort of (key, original index) pairs, 8-bit digits, so
+// that every cell's visibilities keep their input order and the gridded sums
+// are reproducible run to run.  Pass = per-tile digit histograms (digit-major)
+// -> exclusive scan -> order-preserving scatter.
+constexpr int RTILE = 2048;            // items per tile (256 threads x 8 rounds)
+
+__global__ void __launch_bounds__(256) k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
+                                                    int ntiles, uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t t0 = (int64_t)blockIdx.x * RTILE;
+    for (int r = 0; r < RTILE / 256; ++r) {
+        const int64_t e = t0 + r * 256 + threadIdx.x;
+        if (e < n) atomicAdd(&h[(keys[e] >> shift) & 255u], 1u);
     }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t *__restrict__ kin,
+                                                       const uint32_t *__restrict__ vin, int64_t n,
+                                                       int shift, int ntiles,
+                                                       const uint32_t *__restrict__ offs,
+                                                       uint32_t *__restrict__ kout,
+                                                       uint32_t *__restrict__ vout) {
+    __shared__ uint32_t wcount[8][256];
+    __shared__ uint32_t wbase[8][256];
+    __shared__ uint32_t base[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    base[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+    for (int w = 0; w < 8; ++w) wcount[w][threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t t0 = (int64_t)blockIdx.x * RTILE;
+    for (int r = 0; r < RTILE / 256; ++r) {
+        const int64_t e = t0 + r * 256 + threadIdx.x;
+        const bool on = e < n;
+        const uint32_t key = on ? kin[e] : 0u;
+        const uint32_t val = on ? vin[e] : 0u;
+        const uint32_t d = on ? ((key >> shift) & 255u) : 256u + lane;   // unique for idle lanes
+        const unsigned peers = __match_any_sync(FULL, d);
+        const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+        if (on && rank == 0) wcount[warp][d] = __popc(peers);
+        __syncthreads();
+        {   // digit threadIdx.x: prefix over warps in order
+            uint32_t run = base[threadIdx.x];
+            for (int w = 0; w < 8; ++w) {
+                const uint32_t c = wcount[w][threadIdx.x];
+                wbase[w][threadIdx.x] = run;
+                run += c;
+                wcount[w][threadIdx.x] = 0;
+            }
+            base[threadIdx.x] = run;
+        }
+        __syncthreads();
+        if (on) {
+            const uint32_t pos = wbase[warp][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_plan_gather(int64_t n_valid_max, const uint32_t *__restrict__ n_valid_p,
+                              const float2 *__restrict__ uv, const uint32_t *__restrict__ s_idx,
+                              float2 *__restrict__ s_uv) {
+    const uint32_t nv = *n_valid_p;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv && i < n_valid_max;
+         i += (int64_t)gridDim.x * blockDim.x)
+        s_uv[i] = uv[s_idx[i]];
 }
 
 // One block: cut every tile's run of sorted visibilities into units of <= UMAX.
 __global__ void __launch_bounds__(1024) k_units(const uint32_t *__restrict__ offs,
                                                 const uint32_t *__restrict__ hist, int64_t nkeys,
                                                 int ntiles, int4 *__restrict__ units,
-                                                int *__restrict__ n_units, int cap) {
+                                                int *__restrict__ n_units, int cap,
+                                                uint32_t *__restrict__ n_valid_out) {
     __shared__ uint32_t sh[32];
     const uint32_t n_valid = offs[nkeys - 1] + hist[nkeys - 1];
+    if (threadIdx.x == 0) *n_valid_out = n_valid;
     uint32_t carry = 0;
     for (int b = 0; b < ntiles; b += 1024) {
         const int t = b + threadIdx.x;
@@ -399,10 +460,11 @@ struct PlanBufs {
     uint32_t *keys, *hist, *offs, *bsum;
     float2 *s_uv;
     uint32_t *s_idx, *s_key;
+    uint32_t *k2, *v2, *vals, *rhist, *roffs, *n_valid;
     int4 *units;
     int *n_units;
     int64_t nkeys, n_vis;
-    int ntiles, units_cap;
+    int ntiles, units_cap, rtiles;
 };
 
 bool plan_bufs(abs_ctx *ctx, const GridGeom &G, int64_t n_vis, PlanBufs &b) {
@@ -420,33 +482,78 @@ bool plan_bufs(abs_ctx *ctx, const GridGeom &G, int64_t n_vis, PlanBufs &b) {
     b.s_key = (uint32_t *)workspace(ctx, "plan.s_key", sizeof(uint32_t) * nv);
     b.units = (int4 *)workspace(ctx, "plan.units", sizeof(int4) * b.units_cap);
     b.n_units = (int *)workspace(ctx, "plan.n_units", sizeof(int));
+    b.rtiles = (int)cdiv(nv, RTILE);
+    b.k2 = (uint32_t *)workspace(ctx, "plan.k2", sizeof(uint32_t) * nv);
+    b.v2 = (uint32_t *)workspace(ctx, "plan.v2", sizeof(uint32_t) * nv);
+    b.vals = (uint32_t *)workspace(ctx, "plan.vals", sizeof(uint32_t) * nv);
+    b.rhist = (uint32_t *)workspace(ctx, "plan.rhist", sizeof(uint32_t) * 256 * b.rtiles);
+    b.roffs = (uint32_t *)workspace(ctx, "plan.roffs", sizeof(uint32_t) * 256 * b.rtiles);
+    b.n_valid = (uint32_t *)workspace(ctx, "plan.n_valid", sizeof(uint32_t));
     return b.keys && b.hist && b.offs && b.bsum && b.s_uv && b.s_idx && b.s_key && b.units &&
-           b.n_units;
+           b.n_units && b.k2 && b.v2 && b.vals && b.rhist && b.roffs && b.n_valid;
 }
 
 }  // namespace
+
+// Exclusive scan of len uint32 values (3 kernels; bsum needs cdiv(len, 4096) + 1 entries).
+void scan_u32(cudaStream_t st, const uint32_t *in, int64_t len, uint32_t *out, uint32_t *bsum) {
+    const int nblk = (int)cdiv(len, 4096);
+    k_scan_local<<<nblk, 1024, 0, st>>>(in, len, out, bsum);
+    k_scan_top<<<1, 1024, 0, st>>>(bsum, nblk);
+    k_scan_add<<<(int)cdiv(len, 256), 256, 0, st>>>(out, len, bsum);
+}
 
 abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv) {
     const GridGeom G = geom(s);
     PlanBufs b;
     if (!plan_bufs(ctx, G, n_vis, b)) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
+    const int64_t rlen = (int64_t)256 * b.rtiles;
+    const int64_t scan_len = std::max<int64_t>(b.nkeys, rlen);
+    uint32_t *bsum = (uint32_t *)workspace(ctx, "plan.bsum2", sizeof(uint32_t) * (cdiv(scan_len, 4096) + 1));
+    if (!bsum) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
     cudaStream_t st = ctx->stream;
     StageTimer timer(ctx, "grid_plan");
     cudaMemsetAsync(b.hist, 0, sizeof(uint32_t) * b.nkeys, st);
     const int grid_v = (int)std::min<int64_t>(cdiv(std::max<int64_t>(n_vis, 1), 256), ctx->sm_count * 16);
+    const uint32_t key_none = (uint32_t)b.nkeys;     // invalid visibilities sort last
     if (n_vis > 0)
-        k_plan_keys<<<grid_v, 256, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, b.hist);
-    const int nblk = (int)cdiv(b.nkeys, 4096);
-    k_scan_local<<<nblk, 1024, 0, st>>>(b.hist, b.nkeys, b.offs, b.bsum);
-    k_scan_top<<<1, 1024, 0, st>>>(b.bsum, nblk);
-    k_scan_add<<<(int)cdiv(b.nkeys, 256), 256, 0, st>>>(b.offs, b.nkeys, b.bsum);
-    // cursor = offsets (reuse hist as cursor after units are cut)
-    k_units<<<1, 1024, 0, st>>>(b.offs, b.hist, b.nkeys, b.ntiles, b.units, b.n_units, b.units_cap);
-    cudaMemcpyAsync(b.hist, b.offs, sizeof(uint32_t) * b.nkeys, cudaMemcpyDeviceToDevice, st);
-    if (n_vis > 0)
-        k_plan_scatter<<<grid_v, 256, 0, st>>>(n_vis, (const float2 *)d_uv, b.keys, b.hist, b.s_uv,
-                                               b.s_idx, b.s_key);
+        k_plan_keys<<<grid_v, 256, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, b.vals, b.hist, key_none);
+    scan_u32(st, b.hist, b.nkeys, b.offs, bsum);
+    k_units<<<1, 1024, 0, st>>>(b.offs, b.hist, b.nkeys, b.ntiles, b.units, b.n_units, b.units_cap,
+                                b.n_valid);
+    if (n_vis > 0) {
+        // stable sort of (key, index); ping-pong keys/vals <-> k2/v2, result in s_key/s_idx
+        int bits = 1;
+        while (((uint64_t)1 << bits) <= (uint64_t)key_none) ++bits;
+        const int passes = (bits + 7) / 8;
+        uint32_t *ki = b.keys, *vi = b.vals, *ko = b.k2, *vo = b.v2;
+        for (int ps = 0; ps < passes; ++ps) {
+            if (ps == passes - 1) {
+                ko = b.s_key;
+                vo = b.s_idx;
+            }
+            k_radix_hist<<<b.rtiles, 256, 0, st>>>(ki, n_vis, 8 * ps, b.rtiles, b.rhist);
+            scan_u32(st, b.rhist, rlen, b.roffs, bsum);
+            k_radix_scatter<<<b.rtiles, 256, 0, st>>>(ki, vi, n_vis, 8 * ps, b.rtiles, b.roffs, ko, vo);
+            if (ps == 0) {
+                ki = b.k2;
+                vi = b.v2;
+                ko = b.keys;
+                vo = b.vals;
+            } else {
+                std::swap(ki, ko);
+                std::swap(vi, vo);
+            }
+        }
+        k_plan_gather<<<grid_v, 256, 0, st>>>(n_vis, b.n_valid, (const float2 *)d_uv, b.s_idx, b.s_uv);
+    }
     return check_launch(ctx, "grid plan");
+}
+
+void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc, uint8_t **hit) {
+    const int64_t cells = (int64_t)s.n * s.n;
+    *acc = (double *)workspace(ctx, "grid.acc", sizeof(double) * 3 * cells);
+    *hit = (uint8_t *)workspace(ctx, "grid.hit", cells);
 }
 
 abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_vis,

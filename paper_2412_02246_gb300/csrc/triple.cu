@@ -21,7 +21,7 @@ namespace absk {
 namespace {
 
 constexpr int TG = 1024;       // triplets per CTA group
-constexpr int TT = 256;        // threads per CTA
+constexpr int TT = 512;        // threads per CTA
 constexpr int KB = 8;          // triplets per warp pass
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -42,26 +42,43 @@ __global__ void __launch_bounds__(TT) k_triple_fp32(TripleGeom G, const float *_
     double *acc = (double *)(F + (size_t)G.nb * G.PC);           // [TG]
     int *seg = (int *)(acc + TG);                                 // [TG + 1] row starts
     int *kk = seg + TG + 1;                                       // [TG] k of each triplet
+    uint8_t *flag = (uint8_t *)(kk + TG);                         // [TG] row-start flags
     __shared__ int nseg_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int t0 = blockIdx.y * TG;
     const int nt = min(TG, G.n_trip - t0);
     const int64_t p_begin = (int64_t)blockIdx.x * G.per_split;
     const int64_t p_end = min(G.P, p_begin + G.per_split);
-    // row segments of this group (serial; TG is small)
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-        acc[t] = 0.0;
-        const int k = ijk[3 * (t0 + t) + 2];
-        kk[t] = (k >= 0 && k < G.nb) ? k : -1;   // out-of-range bins contribute nothing
-    }
-    if (threadIdx.x == 0) {
-        int ns = 0;
-        for (int t = 0; t < nt; ++t) {
+    // row segments of this group: flag row starts, then compact with one warp
+    for (int t = threadIdx.x; t < TG; t += blockDim.x) {
+        uint8_t f = 0;
+        if (t < nt) {
+            acc[t] = 0.0;
+            const int k = ijk[3 * (t0 + t) + 2];
+            kk[t] = (k >= 0 && k < G.nb) ? k : -1;   // out-of-range bins contribute nothing
             const int i = ijk[3 * (t0 + t)], j = ijk[3 * (t0 + t) + 1];
-            if (t == 0 || i != ijk[3 * (t0 + t - 1)] || j != ijk[3 * (t0 + t - 1) + 1]) seg[ns++] = t;
+            f = (t == 0 || i != ijk[3 * (t0 + t - 1)] || j != ijk[3 * (t0 + t - 1) + 1]) ? 1 : 0;
         }
-        seg[ns] = nt;
-        nseg_s = ns;
+        flag[t] = f;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int base = lane * (TG / 32);
+        int c = 0;
+        for (int e = 0; e < TG / 32; ++e) c += flag[base + e];
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int pos = incl - c;
+        for (int e = 0; e < TG / 32; ++e)
+            if (flag[base + e]) seg[pos++] = base + e;
+        if (lane == 31) {
+            seg[incl] = nt;
+            nseg_s = incl;
+        }
     }
     __syncthreads();
     const int nseg = nseg_s;
@@ -163,20 +180,22 @@ abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_field
     G.nb = s.nb;
     G.P = (int64_t)s.N * s.N;
     G.n_trip = n_trip;
-    // staged pixels: keep the field tile within ~96 KB
-    int PC = 1024;
-    while (PC > 128 && (size_t)G.nb * PC * 4 > 96 * 1024) PC >>= 1;
+    // staged pixels: keep the field tile within ~96 KB, and make enough
+    // chunks for about four CTAs per SM
+    // one pixel range per CTA, about two CTAs per SM overall; each range is
+    // staged in chunks of PC pixels (a multiple of 32 whose fields fit ~96 KB)
+    const int groups = (int)cdiv(n_trip, TG);
+    const int64_t target = std::max<int64_t>(1, cdiv(2 * ctx->sm_count, groups));
+    const int64_t per = cdiv(cdiv(G.P, target), 32) * 32;
+    const int64_t pc_max = std::max<int64_t>(32, ((96 * 1024) / (4 * (int64_t)G.nb)) / 32 * 32);
+    const int PC = (int)std::min<int64_t>(per, pc_max);
     G.PC = PC;
     G.vec4 = (G.P % 4 == 0) && (((uintptr_t)d_fields & 15) == 0);
-    const int groups = (int)cdiv(n_trip, TG);
-    // splits: about two CTAs per SM overall
-    const int64_t chunks = cdiv(G.P, PC);
-    int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>(chunks, cdiv(2 * ctx->sm_count, groups)));
-    G.per_split = cdiv(chunks, nsplit) * PC;
-    nsplit = cdiv(G.P, G.per_split);
+    G.per_split = cdiv(per, PC) * PC;
+    const int64_t nsplit = cdiv(G.P, G.per_split);
     double *partial = (double *)workspace(ctx, "triple.partial", sizeof(double) * nsplit * n_trip);
     if (!partial) return fail(ctx, ABS_ERR_OOM, "triple-sum workspace");
-    const size_t smem = (size_t)G.nb * PC * 4 + TG * 8 + (2 * TG + 1) * 4;
+    const size_t smem = (size_t)G.nb * PC * 4 + TG * 8 + (2 * TG + 1) * 4 + TG;
     cudaFuncSetAttribute(k_triple_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     {
         StageTimer timer(ctx, "triple_fp32");
