@@ -106,6 +106,9 @@ abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc
 void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc, uint8_t **hit);
 abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_fields,
                               int32_t n_trip, const int32_t *d_ijk, double *d_sum);
+// Split-BF16 tcgen05 form of the same sums (precision == ABS_SPLIT_BF16).
+abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
+                            int32_t n_trip, const int32_t *d_ijk, double *d_sum);
 // Ring tables (cell lists, byte map) from d_mask, then exact counts (d_count may be
 // NULL) and, if d_ellbar is not NULL, the mean l of every ring.
 abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, int32_t n_trip,

@@ -13,9 +13,13 @@
 // g1 to the other half plane, hence the factor 2; the origin is in no ring.)
 //
 // Ring lists are built row-major, so the upper half plane of each ring is
-// the second half of its list.  A byte map over [-2R, 2R]^2 holds 1 + ring
-// id of every filled ring cell (0 elsewhere), so a pair is classified by one
-// integer add and one byte load, with no bounds test.  One CTA per (i, j,
+// the second half of its list.  A byte map holds 1 + ring id of every filled
+// ring cell (0 elsewhere), indexed by |lin(h)| with lin(g) = g_y W + g_x,
+// W = 4R + 1: lin is linear and odd, so lin(g1 + g2) = lin(g1) + lin(g2) and
+// |lin(h)| = lin(+-h) picks the upper-half-plane representative of h, whose
+// ring and filled state are those of h.  A pair is then classified by one
+// add, one abs and one byte load, with no bounds test, from a map half the
+// size of [-2R, 2R]^2.  One CTA per (i, j,
 // chunk of g1) streams all of F_j through shared memory; each thread keeps
 // run-length state for its g1 cells (consecutive g2 in row order usually
 // land in the same ring) and adds finished runs into a lane-private
@@ -73,67 +77,96 @@ __device__ __forceinline__ RowSpan row_span(const CountGeom &G, int64_t q0, int6
     return r;
 }
 
-// Pass 1: filled cells per (ring, row), FP64 sum of |g| per (ring, row).
+// x of the t-th cell of the row span (left part -x1..-x0, then x0..x1).
+__device__ __forceinline__ int span_x(const RowSpan &sp, int t) {
+    if (sp.x0 == 0) return -sp.x1 + t;
+    const int n1 = sp.x1 - sp.x0 + 1;
+    return t < n1 ? -sp.x1 + t : sp.x0 + (t - n1);
+}
+__device__ __forceinline__ int span_len(const RowSpan &sp) {
+    if (!sp.ok) return 0;
+    return sp.x0 == 0 ? 2 * sp.x1 + 1 : 2 * (sp.x1 - sp.x0 + 1);
+}
+
+// Pass 1 (one warp per (ring, row)): filled cells and FP64 sum of |g|.
 __global__ void k_ring_rows(CountGeom G, const int64_t *__restrict__ q, const uint8_t *__restrict__ mask,
                             uint32_t *__restrict__ rowcnt, double *__restrict__ rowlen) {
     const int rows = 2 * G.R + 1;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= G.nb * rows) return;
     const int m = e / rows, y = e - m * rows - G.R;
     const RowSpan sp = row_span(G, q[m], q[m + 1], y);
+    const int len = span_len(sp);
     uint32_t c = 0;
-    double len = 0.0;
-    if (sp.ok) {
-        for (int x = -sp.x1; x <= sp.x1; ++x) {
-            if (x > -sp.x0 && x < sp.x0) x = sp.x0;   // skip the hole of the annulus
-            if (mask[cell_index(G.n, x, y)]) {
-                ++c;
-                len += sqrt((double)x * x + (double)y * y);
-            }
+    double sum = 0.0;
+    for (int t0 = 0; t0 < len; t0 += 32) {
+        const int t = t0 + lane;
+        bool on = false;
+        int x = 0;
+        if (t < len) {
+            x = span_x(sp, t);
+            on = mask[cell_index(G.n, x, y)] != 0;
         }
+        c += __popc(__ballot_sync(FULL, on));
+        if (on) sum += sqrt((double)x * x + (double)y * y);
     }
-    rowcnt[e] = c;
-    rowlen[e] = len;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+    if (lane == 0) {
+        rowcnt[e] = c;
+        rowlen[e] = sum;
+    }
 }
 
-// Pass 2: write the cells (row-major within each ring) and the byte ring map.
+// Pass 2 (one warp per (ring, row)): write the cells in x order and the byte map.
 __global__ void k_ring_write(CountGeom G, const int64_t *__restrict__ q, const uint8_t *__restrict__ mask,
                              const uint32_t *__restrict__ rowoff, short2 *__restrict__ lists,
                              uint8_t *__restrict__ binmap) {
     const int rows = 2 * G.R + 1;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= G.nb * rows) return;
     const int m = e / rows, y = e - m * rows - G.R;
     const RowSpan sp = row_span(G, q[m], q[m + 1], y);
-    if (!sp.ok) return;
+    const int len = span_len(sp);
     uint32_t pos = rowoff[e];
-    for (int x = -sp.x1; x <= sp.x1; ++x) {
-        if (x > -sp.x0 && x < sp.x0) x = sp.x0;
-        if (mask[cell_index(G.n, x, y)]) {
-            lists[pos++] = make_short2((short)x, (short)y);
-            binmap[(int64_t)(y + 2 * G.R) * G.W + (x + 2 * G.R)] = (uint8_t)(m + 1);
+    for (int t0 = 0; t0 < len; t0 += 32) {
+        const int t = t0 + lane;
+        bool on = false;
+        int x = 0;
+        if (t < len) {
+            x = span_x(sp, t);
+            on = mask[cell_index(G.n, x, y)] != 0;
         }
+        const unsigned bal = __ballot_sync(FULL, on);
+        if (on) {
+            lists[pos + __popc(bal & ((1u << lane) - 1u))] = make_short2((short)x, (short)y);
+            const int lin = y * G.W + x;
+            if (lin > 0) binmap[lin] = (uint8_t)(m + 1);
+        }
+        pos += __popc(bal);
     }
 }
 
-// Pass 3 (one thread per ring): ring offsets, counts and mean l (rows summed in order).
+// Pass 3 (one warp per ring): ring offsets, counts and mean l (fixed-order sums).
 __global__ void k_ring_finish(CountGeom G, float du, const uint32_t *__restrict__ rowoff,
                               const uint32_t *__restrict__ rowcnt, const double *__restrict__ rowlen,
                               int64_t *__restrict__ ring_off, int32_t *__restrict__ counts,
                               double *__restrict__ ellbar) {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (m >= G.nb) return;
     const int rows = 2 * G.R + 1;
     const int64_t e0 = (int64_t)m * rows, e1 = e0 + rows;
     const uint32_t start = rowoff[e0];
     const uint32_t c = rowoff[e1 - 1] + rowcnt[e1 - 1] - start;
-    ring_off[m] = start;
-    counts[m] = (int32_t)c;
-    if (m == G.nb - 1) ring_off[G.nb] = start + c;
-    if (ellbar) {
-        double len = 0.0;
-        for (int64_t e = e0; e < e1; ++e) len += rowlen[e];
-        ellbar[m] = c > 0 ? 2.0 * 3.14159265358979323846 * (double)du * len / (double)c : nan("");
+    double len = 0.0;
+    for (int64_t e = e0 + lane; e < e1; e += 32) len += rowlen[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(FULL, len, o);
+    if (lane == 0) {
+        ring_off[m] = start;
+        counts[m] = (int32_t)c;
+        if (m == G.nb - 1) ring_off[G.nb] = start + c;
+        if (ellbar) ellbar[m] = c > 0 ? 2.0 * 3.14159265358979323846 * (double)du * len / (double)c : nan("");
     }
 }
 
@@ -214,7 +247,7 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
     uint8_t *map_s = (uint8_t *)(stage + STAGE);
     const uint8_t *map = MAP_IN_SMEM ? map_s : binmap_g;
     if (MAP_IN_SMEM) {
-        const int64_t mb = (int64_t)G.W * G.W;
+        const int64_t mb = G.base + 1;
         const int64_t nv = mb / 16;
         for (int64_t i = threadIdx.x; i < nv; i += blockDim.x)
             ((uint4 *)map_s)[i] = ((const uint4 *)binmap_g)[i];
@@ -241,7 +274,7 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
             const int a = I.z + q * blockDim.x + threadIdx.x;
             v1[q] = a < no;
             const short2 g = v1[q] ? Fo[a] : make_short2(0, 0);
-            lin1[q] = g.y * G.W + g.x + (int)G.base;
+            lin1[q] = g.y * G.W + g.x;
         }
         int cur[G1];
         uint32_t cnt[G1];
@@ -262,7 +295,7 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
                 const int l2 = stage[a];
 #pragma unroll
                 for (int q = 0; q < G1; ++q) {
-                    const int k = v1[q] ? (int)map[lin1[q] + l2] : 0;
+                    const int k = v1[q] ? (int)map[abs(lin1[q] + l2)] : 0;
                     if (k != cur[q]) {
                         myhist[(size_t)cur[q] * 32] += cnt[q];
                         cur[q] = k;
@@ -309,7 +342,7 @@ CountGeom cgeom(const Setup &s) {
     G.nb = s.nb;
     G.R = s.R;
     G.W = 4 * s.R + 1;
-    G.base = (int64_t)2 * s.R * G.W + 2 * s.R;
+    G.base = (int64_t)2 * s.R * G.W + 2 * s.R;   // largest |lin| of a pair sum
     return G;
 }
 
@@ -328,7 +361,7 @@ abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, Ring
     rb.lists = (short2 *)workspace(ctx, "ring.lists", sizeof(short2) * ncell);
     rb.counts = (int32_t *)workspace(ctx, "ring.counts", sizeof(int32_t) * s.nb);
     rb.ring_off = (int64_t *)workspace(ctx, "ring.off", sizeof(int64_t) * (s.nb + 1));
-    const int64_t mb = (int64_t)G.W * G.W;
+    const int64_t mb = G.base + 1;
     rb.binmap = (uint8_t *)workspace(ctx, "ring.binmap", (size_t)cdiv(mb, 16) * 16);
     uint32_t *rowcnt = (uint32_t *)workspace(ctx, "ring.rowcnt", sizeof(uint32_t) * nrow);
     uint32_t *rowoff = (uint32_t *)workspace(ctx, "ring.rowoff", sizeof(uint32_t) * nrow);
@@ -339,12 +372,12 @@ abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, Ring
     StageTimer timer(ctx, "ring_lists");
     cudaStream_t st = ctx->stream;
     cudaMemsetAsync(rb.binmap, 0, (size_t)cdiv(mb, 16) * 16, st);
-    const int nbk = (int)cdiv(nrow, 128);
-    k_ring_rows<<<nbk, 128, 0, st>>>(G, s.d_q, d_mask, rowcnt, rowlen);
+    const int nbk = (int)cdiv(nrow * 32, 256);
+    k_ring_rows<<<nbk, 256, 0, st>>>(G, s.d_q, d_mask, rowcnt, rowlen);
     scan_u32(st, rowcnt, nrow, rowoff, bsum);
-    k_ring_write<<<nbk, 128, 0, st>>>(G, s.d_q, d_mask, rowoff, rb.lists, rb.binmap);
-    k_ring_finish<<<(int)cdiv(s.nb, 128), 128, 0, st>>>(G, s.du, rowoff, rowcnt, rowlen, rb.ring_off,
-                                                        rb.counts, d_ellbar);
+    k_ring_write<<<nbk, 256, 0, st>>>(G, s.d_q, d_mask, rowoff, rb.lists, rb.binmap);
+    k_ring_finish<<<(int)cdiv((int64_t)s.nb * 32, 256), 256, 0, st>>>(G, s.du, rowoff, rowcnt, rowlen,
+                                                                       rb.ring_off, rb.counts, d_ellbar);
     return check_launch(ctx, "ring lists");
 }
 
@@ -359,11 +392,13 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     const CountGeom G = cgeom(s);
     // threads per CTA: lane-private histograms must fit next to the map
     const int hs = s.nb + 1;
-    const int64_t map_bytes = cdiv((int64_t)G.W * G.W, 16) * 16;
+    const int64_t map_bytes = cdiv(G.base + 1, 16) * 16;
     const size_t hist_budget = 96 * 1024;
     int nwarps = (int)std::min<size_t>(CT / 32, hist_budget / ((size_t)hs * 32 * 4));
     if (nwarps < 1) return fail(ctx, ABS_ERR_UNSUPPORTED, "too many rings for the count kernel");
-    const bool map_smem = map_bytes + (int64_t)nwarps * hs * 32 * 4 + STAGE * 4 <= 220 * 1024;
+    const int64_t cta_bytes = map_bytes + (int64_t)nwarps * hs * 32 * 4 + STAGE * 4;
+    const bool map_smem = cta_bytes <= 220 * 1024;
+    const int per_sm = map_smem ? std::max<int>(1, (int)std::min<int64_t>(4, (226 * 1024) / (cta_bytes + 1024))) : 2;
     const int threads = nwarps * 32;
     const int chunk = threads * G1;
     const size_t smem = (size_t)nwarps * hs * 32 * 4 + STAGE * 4 + (map_smem ? map_bytes : 0);
@@ -385,7 +420,7 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     }
     {
     StageTimer timer(ctx, "count_pairs");
-    const int blocks = ctx->sm_count * (map_smem ? 1 : 2);
+    const int blocks = ctx->sm_count * per_sm;
     if (map_smem) {
         cudaFuncSetAttribute(k_count_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_count_pairs<true><<<blocks, threads, smem, stm>>>(G, items, n_items, rb.lists, rb.ring_off,

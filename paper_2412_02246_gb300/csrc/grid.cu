@@ -104,11 +104,16 @@ __global__ void k_plan_keys(GridGeom G, int64_t n_vis, const float2 *__restrict_
                     const int tx = kx / TS, ty = ky / TS;
                     key = (uint32_t)((ty * G.tt + tx) * (TS * TS) + (ky - ty * TS) * TS +
                                      (kx - tx * TS));
-                    atomicAdd(&hist[key], 1u);
                 }
             }
         }
         keys[i] = key;
+        // one atomic per distinct key in the warp (consecutive visibilities of a
+        // baseline usually share a cell)
+        const unsigned active = __activemask();
+        const unsigned peers = __match_any_sync(active, key);
+        const int lane = threadIdx.x & 31;
+        if (key != key_none && lane == __ffs(peers) - 1) atomicAdd(&hist[key], (uint32_t)__popc(peers));
         vals[i] = (uint32_t)i;
     }
 }

@@ -133,13 +133,24 @@ __global__ void __launch_bounds__(TT) k_triple_fp32(TripleGeom G, const float *_
         partial[(size_t)blockIdx.x * G.n_trip + t0 + t] = acc[t];
 }
 
-__global__ void k_triple_reduce(int n_trip, int nsplit, double inv_p, const double *__restrict__ partial,
-                                double *__restrict__ S) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_trip) return;
+// S[t] = inv_p * sum over splits of partial[split][t]: 32 triplets per block,
+// 8 lanes of splits per triplet, summed in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) k_triple_reduce(int n_trip, int nsplit, double inv_p,
+                                                       const double *__restrict__ partial,
+                                                       double *__restrict__ S) {
+    __shared__ double sh[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int t = blockIdx.x * 32 + tx;
     double s = 0.0;
-    for (int k = 0; k < nsplit; ++k) s += partial[(size_t)k * n_trip + t];
-    S[t] = s * inv_p;
+    if (t < n_trip)
+        for (int k = ty; k < nsplit; k += 8) s += partial[(size_t)k * n_trip + t];
+    sh[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && t < n_trip) {
+        double a = 0.0;
+        for (int k = 0; k < 8; ++k) a += sh[k][tx];
+        S[t] = a * inv_p;
+    }
 }
 
 __global__ void k_normalise(int n_trip, double norm_A, const double *__restrict__ S,
@@ -175,7 +186,7 @@ abs_status launch_check_triplets(abs_ctx *ctx, const Setup &s, int32_t n_trip, c
 abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_fields, int32_t n_trip,
                               const int32_t *d_ijk, double *d_sum) {
     if (n_trip == 0) return ABS_OK;
-    if (s.precision != ABS_FP32) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 triple sums not built");
+    if (s.precision == ABS_SPLIT_BF16) return launch_triple_tc(ctx, s, d_fields, n_trip, d_ijk, d_sum);
     TripleGeom G;
     G.nb = s.nb;
     G.P = (int64_t)s.N * s.N;
@@ -202,7 +213,7 @@ abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_field
         k_triple_fp32<<<dim3((unsigned)nsplit, groups), TT, smem, ctx->stream>>>(G, d_fields, d_ijk, partial);
     }
     StageTimer timer(ctx, "triple_reduce");
-    k_triple_reduce<<<(int)cdiv(n_trip, 256), 256, 0, ctx->stream>>>(
+    k_triple_reduce<<<(int)cdiv(n_trip, 32), 256, 0, ctx->stream>>>(
         n_trip, (int)nsplit, 1.0 / ((double)s.N * (double)s.N), partial, d_sum);
     return check_launch(ctx, "triple sums");
 }

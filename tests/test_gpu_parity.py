@@ -334,3 +334,61 @@ def test_invalid_arguments(ctx):
     with pytest.raises(absmod.AbsError) as ei:
         ctx.abs_estimate(cfg, torch.zeros((10, 2), device=dev()), torch.zeros((10, 2), device=dev()), 5)
     assert ei.value.status == absmod.ABS_ERR_INVALID_ARG
+
+
+# ----------------------------------------------------------------- split-BF16 (tcgen05) form
+
+BF16_TOL = 3e-4
+
+
+@pytest.mark.parametrize("cfg_id", [0, 1])
+def test_split_bf16_triple_sums(ctx, cfg_id):
+    inp = inputs(cfg_id)
+    wl = inp.wl
+    cfg = absmod.Config.from_workload(wl, precision=absmod.ABS_SPLIT_BF16)
+    est = oracle_run(("est", cfg_id), wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+    _, _, M, gwm = gpu_grid(ctx, cfg, inp.uv, inp.vis)
+    f = gpu_fields(ctx, cfg, gwm)
+    nt = len(est.ijk)
+    S = torch.empty(nt, dtype=torch.float64, device=dev())
+    T = torch.empty(nt, dtype=torch.int64, device=dev())
+    ctx.abs_triple(cfg, f, gwm[2], to_dev(est.ijk), S, T)
+    ctx.sync()
+    assert np.array_equal(T.cpu().numpy(), est.T)
+    check_sums(S.cpu().numpy(), est, tol=BF16_TOL)
+
+
+@pytest.mark.parametrize("cfg_id", [0, 1])
+def test_split_bf16_estimate(ctx, cfg_id):
+    inp = inputs(cfg_id)
+    wl = inp.wl
+    cfg = absmod.Config.from_workload(wl, precision=absmod.ABS_SPLIT_BF16)
+    est = oracle_run(("est", cfg_id), wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+    B, T, E, ijk = absmod.estimate(cfg, to_dev(inp.uv), to_dev(synth.vis_as_float2(inp.vis)), ctx)
+    ctx.sync()
+    assert np.array_equal(T.cpu().numpy(), est.T)
+    Bg = B.cpu().numpy()
+    ok = ~np.isnan(est.B)
+    assert np.array_equal(np.isnan(Bg), ~ok)
+    big = ok & (np.abs(est.B) >= 1e-3 * np.nanmax(np.abs(est.B)))
+    rel = np.abs(Bg[big] - est.B[big]) / np.abs(est.B[big])
+    assert rel.max() <= BF16_TOL, f"split-BF16 B relative error {rel.max():.3e}"
+
+
+def test_split_bf16_odd_shapes(ctx):
+    # rings not a multiple of 16 (MMA N padding), one pixel range ending mid-chunk
+    rng = np.random.default_rng(3)
+    n, du = 48, 1.0
+    edges = 2 * np.pi * np.linspace(1.5, 15.0, 38)       # 37 rings -> N = 48 columns
+    uv = rng.uniform(-15.0, 15.0, (4000, 2)).astype(np.float32)
+    vis = (rng.standard_normal(4000) + 1j * rng.standard_normal(4000)).astype(np.complex64)
+    est = oracle.estimate(n, du, edges, uv, vis)
+    for prec, tol in ((absmod.ABS_FP32, SUM_TOL), (absmod.ABS_SPLIT_BF16, BF16_TOL)):
+        cfg = absmod.Config(n_grid=n, du=du, ell_edges=edges, precision=prec)
+        B, T, E, ijk = absmod.estimate(cfg, to_dev(uv), to_dev(synth.vis_as_float2(vis)), ctx)
+        ctx.sync()
+        assert np.array_equal(T.cpu().numpy(), est.T)
+        Bg = B.cpu().numpy()
+        ok = ~np.isnan(est.B)
+        big = ok & (np.abs(est.B) >= 1e-3 * np.nanmax(np.abs(est.B)))
+        assert (np.abs(Bg[big] - est.B[big]) / np.abs(est.B[big])).max() <= tol
