@@ -39,11 +39,19 @@ WORKLOAD_ID = 1
 METRIC = "ABS estimates/s (V->binned B)"
 UNIT = "estimates/s"
 
-# kernels launched per stage-timer entry (the profiler brackets stages)
-KERNELS_PER_STAGE = {"grid_plan": 6, "grid_zero": 0, "grid": 1, "grid_finalize": 1, "ring_lists": 1,
-                     "count_items": 1, "count_pairs": 1, "count_gather": 1, "ellbar": 1,
+# kernels launched per stage-timer entry (the profiler brackets stages); the
+# gridding plan runs 6 kernels plus 5 per radix pass (8-bit digits of the cell key)
+KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "ring_lists": 6,
+                     "count_items": 1, "count_pairs": 1, "count_gather": 1, "ellbar": 6,
                      "fft_rows": 1, "fft_cols": 1, "triple_fp32": 1, "triple_reduce": 1,
-                     "normalise": 1, "check_triplets": 1}
+                     "normalise": 1, "check_triplets": 1, "tc_rows": 1, "triple_tc": 1}
+
+
+def plan_kernels(n_grid, radius):
+    tiles = -(-(n_grid - 1 + 2 * radius) // 16)
+    nkeys = tiles * tiles * 256
+    passes = -(-int(nkeys).bit_length() // 8)
+    return 6 + 5 * passes
 
 
 def load_peaks():
@@ -154,30 +162,68 @@ def workload_config(wl):
 
 
 def roofline_for(stage, avg_ms, geo, peaks):
-    """Algorithmic work per launch of the dominant kernel over its average duration."""
+    """Algorithmic work of one launch of `stage` over its average duration.
+
+    grid:        FP32 lane-ops, 4 per (visibility, footprint cell): w = wx wy, two FMAs, one add
+    count_pairs: integer pair visits x 2 lane-ops (index add, ring compare)
+    triple_fp32: 2 flops per (triplet, pixel)
+    triple_tc:   executed BF16 tensor flops, 2 M N K x 3 products (M, N padded tiles)
+    fft_rows/cols, others: algorithmic bytes (reads + writes of the data the kernel must move)
+    """
     s = avg_ms * 1e-3
+    lane_ops = geo["sm"] * 128 * geo["clk_hz"]
+    out = {}
     if stage == "grid":
-        # 16 B per visibility (U and V, read once) + 24 B per touched cell of the FP64 grid
-        byts = 16.0 * geo["n_vis"] + 24.0 * geo["cells_touched"]
-        return {"bound": "hbm", "achieved": byts / s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": byts / s / 1e9 / peaks["hbm_gbs"], "traffic": None,
-                "note": "gridder is bound by FP32 ALU (49 compensated weight-accumulations per "
-                        "visibility); the HBM fraction is reported against the measured copy peak"}
-    if stage == "count_pairs":
-        visits = geo["pair_visits"]
-        return {"bound": "alu", "achieved": visits / s / 1e9, "peak": geo["alu_gops"], "unit": "Gvisits/s",
-                "frac": visits / s / 1e9 / geo["alu_gops"], "traffic": None}
-    if stage == "triple_fp32":
+        ops = 4.0 * geo["n_vis"] * geo["footprint"]
+        out = {"bound": "alu", "achieved": ops / s / 1e12, "peak": lane_ops / 1e12, "unit": "Tlane-op/s"}
+    elif stage == "count_pairs":
+        ops = 2.0 * geo["pair_visits"]
+        out = {"bound": "alu", "achieved": ops / s / 1e12, "peak": lane_ops / 1e12, "unit": "Tlane-op/s"}
+    elif stage == "triple_fp32":
         fl = 2.0 * geo["n_trip"] * geo["P"]
-        pk = geo["fp32_tflops"]
-        return {"bound": "alu", "achieved": fl / s / 1e12, "peak": pk, "unit": "TFLOP/s",
-                "frac": fl / s / 1e12 / pk, "traffic": None}
-    if stage in ("fft_cols", "fft_rows"):
-        byts = geo["fft_bytes"][stage]
-        return {"bound": "hbm", "achieved": byts / s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": byts / s / 1e9 / peaks["hbm_gbs"], "traffic": None}
-    return {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": None,
-            "traffic": None}
+        out = {"bound": "alu", "achieved": fl / s / 1e12, "peak": 2 * lane_ops / 1e12, "unit": "TFLOP/s"}
+    elif stage == "triple_tc":
+        fl = 2.0 * geo["tc_rows"] * geo["tc_np"] * geo["P"] * 3
+        out = {"bound": "tensor", "achieved": fl / s / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s"}
+    else:
+        byts = geo["bytes"].get(stage)
+        if byts is None:
+            return {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": None,
+                    "traffic": None}
+        out = {"bound": "hbm", "achieved": byts / s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    out["frac"] = out["achieved"] / out["peak"]
+    out["traffic"] = None
+    return out
+
+
+def workload_geometry(m, cfg, ctx, uv, vis, ijk, N, wl, dev, torch):
+    """Counts that the roofline needs: filled ring cells (pair visits), padded tiles, bytes."""
+    n = cfg.n_grid
+    g = torch.empty((n, n, 2), dtype=torch.float32, device=dev)
+    w = torch.empty((n, n), dtype=torch.float32, device=dev)
+    mk = torch.empty((n, n), dtype=torch.uint8, device=dev)
+    ctx.abs_grid(cfg, uv, vis, g, w, mk)
+    ctx.sync()
+    mask = mk.cpu().numpy()
+    q = m.abs_ring_q(cfg)
+    k = np.arange(n)
+    k = np.where(k > n // 2, k - n, k)
+    gy, gx = np.meshgrid(k, k, indexing="ij")
+    r2 = gx.astype(np.int64) ** 2 + gy.astype(np.int64) ** 2
+    c = np.array([int(((mask > 0) & (r2 >= q[b]) & (r2 < q[b + 1])).sum()) for b in range(cfg.n_bins)])
+    rows = sorted({(int(i), int(j)) for i, j, _ in ijk})
+    visits = sum((c[i] // 2) * c[j] for i, j in rows)
+    nb = cfg.n_bins
+    npairs = (nb + 1) // 2
+    R = int(np.floor(np.sqrt(float(q[-1] - 1))))
+    P = N * N
+    fft_rows_bytes = npairs * (2 * R + 1) * N * 16 + int((mask > 0).sum()) * 24
+    fft_cols_bytes = npairs * (2 * R + 1) * N * 16 + nb * P * 4
+    return {"pair_visits": int(visits), "n_trip": len(ijk), "P": P, "n_vis": len(uv),
+            "footprint": (2 * cfg.radius_cells + 1) ** 2,
+            "tc_rows": -(-len(rows) // 128) * 128, "tc_np": -(-max(nb, 16) // 16) * 16,
+            "bytes": {"fft_rows": fft_rows_bytes, "fft_cols": fft_cols_bytes,
+                      "ring_lists": n * n * 2}}
 
 
 def run_ours(args):
@@ -291,23 +337,44 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return
 
+    # split-BF16 (tcgen05) form on the same workload and GPU
+    cfg_tc = m.Config.from_workload(wl, precision=m.ABS_SPLIT_BF16)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        ctx.abs_estimate(cfg_tc, uv, vis, nt, None, B, T, E)
+    ctx.sync()
+    ctx.profile(True)
+    ev_tc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev_tc[k][0].record(stream)
+        ctx.abs_estimate(cfg_tc, uv, vis, nt, None, B, T, E)
+        ev_tc[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    prof_tc = ctx.profile_read()
+    ctx.profile(False)
+    tc_ms = sum(a.elapsed_time(b) for a, b in ev_tc)
+
     # per-kernel averages and the dominant kernel's roofline
     stages = {k: {"ms_total": v[0], "launches": v[1], "avg_us": 1e3 * v[0] / max(v[1], 1)}
               for k, v in prof.items()}
-    launches = sum(KERNELS_PER_STAGE.get(k, 1) * v[1] for k, v in prof.items())
+    kps = dict(KERNELS_PER_STAGE, grid_plan=plan_kernels(wl.n_grid, wl.radius_cells))
+    launches = sum(kps.get(k, 1) * v[1] for k, v in prof.items())
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
     peaks = load_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = clk.get("sm_mhz") or 1900.0
-    fp32_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
-    mask_cells = None
-    geo = {"n_vis": len(inp.uv), "cells_touched": wl.n_grid * wl.n_grid // 4, "n_trip": nt, "P": N * N,
-           "fp32_tflops": fp32_tflops,
-           "alu_gops": props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e9 / 4.0,
-           "pair_visits": 0, "fft_bytes": {}}
+    geo = workload_geometry(m, cfg, ctx, uv, vis, ijk, N, wl, dev, torch)
+    geo["sm"] = props.multi_processor_count
+    geo["clk_hz"] = sm_mhz * 1e6
     roof = roofline_for(dom, stages[dom]["avg_us"] * 1e-3, geo, peaks)
     roof["kernel"] = dom
     roof["peak_source"] = peaks["source"]
+    tri_fp32 = roofline_for("triple_fp32", stages["triple_fp32"]["avg_us"] * 1e-3, geo, peaks)
+    tc_avg = 1e3 * prof_tc["triple_tc"][0] / max(prof_tc["triple_tc"][1], 1)
+    tri_tc = roofline_for("triple_tc", tc_avg * 1e-3, geo, peaks)
+    useful = 2.0 * nt * N * N
 
     cpu_s = oracle_estimate_seconds(inp)
     line = {
@@ -323,6 +390,14 @@ def run_ours(args):
         "batched": {"value": batched, "unit": UNIT, "realisations_per_call": R,
                     "note": "abs_estimate_many: realisations sharing one baseline set (plan, counts "
                             "and ring tables once per call)"},
+        "split_bf16": {"value": args.steps / (tc_ms * 1e-3), "unit": UNIT,
+                       "triple_tc_us": round(tc_avg, 2),
+                       "triple_tc_tflops_executed": tri_tc["achieved"],
+                       "triple_tc_frac_bf16_peak": tri_tc["frac"],
+                       "triple_useful_tflops": useful / (tc_avg * 1e-6) / 1e12},
+        "fp32": {"triple_fp32_us": round(stages["triple_fp32"]["avg_us"], 2),
+                 "triple_useful_tflops": useful / (stages["triple_fp32"]["avg_us"] * 1e-6) / 1e12,
+                 "frac_fp32_simt_peak": tri_fp32["frac"]},
         "stages_us": {k: round(v["avg_us"], 2) for k, v in sorted(stages.items())},
     }
     print(json.dumps(line), flush=True)

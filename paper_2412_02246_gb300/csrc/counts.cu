@@ -34,7 +34,8 @@ namespace {
 
 constexpr int G1 = 4;            // g1 cells per thread
 constexpr int CT = 256;          // threads per counting CTA (max)
-constexpr int STAGE = 2048;      // g2 cells staged per pass
+constexpr int STAGE = 2048;      // inner cells staged per pass
+constexpr int INNER = 512;       // inner cells per work item (bounds the work of one item)
 constexpr unsigned FULL = 0xffffffffu;
 
 struct CountGeom {
@@ -185,7 +186,7 @@ __global__ void __launch_bounds__(1024) k_count_items(int nb, int32_t n_trip,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int b = 0; b < n_trip; b += blockDim.x) {
         const int t = b + threadIdx.x;
-        int nchunks = 0, i = 0, j = 0;
+        int nchunks = 0, i = 0, j = 0, n_in = 0, n_oc = 0, n_ic = 1;
         bool outer_i = false;
         if (t < n_trip) {
             i = ijk[3 * t];
@@ -203,7 +204,10 @@ __global__ void __launch_bounds__(1024) k_count_items(int nb, int32_t n_trip,
             if (row_start && i >= 0 && i < nb && j >= 0 && j < nb) {
                 const int half_i = counts[i] / 2, cj = counts[j];
                 outer_i = half_i >= cj;
-                nchunks = ((outer_i ? half_i : cj) + chunk - 1) / chunk;
+                n_in = outer_i ? cj : half_i;
+                n_oc = ((outer_i ? half_i : cj) + chunk - 1) / chunk;
+                n_ic = (n_in + INNER - 1) / INNER;
+                nchunks = n_oc * n_ic;
             }
         }
         // block exclusive scan of nchunks (small values; warp-level then serial over warps)
@@ -221,8 +225,11 @@ __global__ void __launch_bounds__(1024) k_count_items(int nb, int32_t n_trip,
             tot += wsum[w];
         }
         const int pos = carry_s + before + x - nchunks;
-        for (int c = 0; c < nchunks; ++c)
-            if (pos + c < cap) items[pos + c] = make_int4(i, j, c * chunk, outer_i ? 1 : 0);
+        for (int c = 0; c < nchunks; ++c) {
+            const int oc = c / n_ic, ic = c - oc * n_ic;
+            if (pos + c < cap)
+                items[pos + c] = make_int4(i, j, oc * chunk, (ic * INNER) | (outer_i ? (int)0x80000000u : 0));
+        }
         __syncthreads();
         if (threadIdx.x == 0) carry_s += tot;
         __syncthreads();
@@ -237,7 +244,8 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
                                                     const int64_t *__restrict__ ring_off,
                                                     const int32_t *__restrict__ counts,
                                                     const uint8_t *__restrict__ binmap_g,
-                                                    unsigned long long *__restrict__ Td) {
+                                                    unsigned long long *__restrict__ Td,
+                                                    int *__restrict__ next_item) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int nwarps = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -256,17 +264,26 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
     for (int i = threadIdx.x; i < nwarps * hs * 32; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
     uint32_t *myhist = hist + (size_t)warp * hs * 32 + lane;
+    __shared__ int it_s;
     const int ni = *n_items;
-    for (int it = blockIdx.x; it < ni; it += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) it_s = atomicAdd(next_item, 1);   // dynamic: items differ in size
+        __syncthreads();
+        const int it = it_s;
+        if (it >= ni) break;
         const int4 I = items[it];
         const int i = I.x, j = I.y;
+        const bool outer_i = (I.w & 0x80000000) != 0;
+        const int in0 = I.w & 0x7fffffff;
         const int ci = counts[i], cj = counts[j];
         const short2 *Fi = lists + ring_off[i] + ci / 2;   // upper half plane of ring i
         const short2 *Fj = lists + ring_off[j];
         const int nh = ci / 2;
         // outer set: spread over the threads; inner set: streamed through shared memory
-        const short2 *Fo = I.w ? Fi : Fj, *Fin = I.w ? Fj : Fi;
-        const int no = I.w ? nh : cj, nin = I.w ? cj : nh;
+        const short2 *Fo = outer_i ? Fi : Fj;
+        const short2 *Fin = (outer_i ? Fj : Fi) + in0;
+        const int no = outer_i ? nh : cj;
+        const int nin = min(INNER, (outer_i ? cj : nh) - in0);
         int lin1[G1];
         bool v1[G1];
 #pragma unroll
@@ -405,9 +422,11 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     // work items: one per (row, chunk of the upper half of ring i)
     int64_t max_ring = 0;
     for (int m = 0; m < s.nb; ++m) max_ring = std::max<int64_t>(max_ring, s.lat[m]);
-    const int cap = (int)std::min<int64_t>((int64_t)n_trip * cdiv(std::max<int64_t>(max_ring, 1), chunk), 1 << 26);
+    const int64_t max_rows = std::min<int64_t>(n_trip, (int64_t)s.nb * (s.nb + 1) / 2);
+    const int64_t mr = std::max<int64_t>(max_ring, 1);
+    const int cap = (int)std::min<int64_t>(max_rows * cdiv(mr, chunk) * cdiv(mr, INNER), 1 << 26);
     int4 *items = (int4 *)workspace(ctx, "count.items", sizeof(int4) * cap);
-    int *n_items = (int *)workspace(ctx, "count.n_items", sizeof(int));
+    int *n_items = (int *)workspace(ctx, "count.n_items", sizeof(int) * 2);   // [count, next]
     const size_t td_bytes = sizeof(unsigned long long) * (size_t)s.nb * s.nb * s.nb;
     unsigned long long *Td = (unsigned long long *)workspace(ctx, "count.table", td_bytes);
     if (!items || !n_items || !Td) return fail(ctx, ABS_ERR_OOM, "count workspace");
@@ -415,6 +434,7 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     {
         StageTimer timer(ctx, "count_items");
         cudaMemsetAsync(Td, 0, td_bytes, stm);
+        cudaMemsetAsync(n_items, 0, sizeof(int) * 2, stm);
         k_count_items<<<1, 1024, 0, stm>>>(s.nb, n_trip, d_ijk, rb.counts, chunk, items, cap, n_items,
                                            ctx->d_err);
     }
@@ -424,11 +444,11 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     if (map_smem) {
         cudaFuncSetAttribute(k_count_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_count_pairs<true><<<blocks, threads, smem, stm>>>(G, items, n_items, rb.lists, rb.ring_off,
-                                                            rb.counts, rb.binmap, Td);
+                                                            rb.counts, rb.binmap, Td, n_items + 1);
     } else {
         cudaFuncSetAttribute(k_count_pairs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_count_pairs<false><<<blocks, threads, smem, stm>>>(G, items, n_items, rb.lists, rb.ring_off,
-                                                             rb.counts, rb.binmap, Td);
+                                                             rb.counts, rb.binmap, Td, n_items + 1);
     }
     }
     {

@@ -252,13 +252,24 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t *__restric
     }
 }
 
-__global__ void k_plan_gather(int64_t n_valid_max, const uint32_t *__restrict__ n_valid_p,
-                              const float2 *__restrict__ uv, const uint32_t *__restrict__ s_idx,
-                              float2 *__restrict__ s_uv) {
+// Fractional offset f = u/dU - c of every sorted visibility from its nearest
+// cell, as a float pair (hi = fl(u/dU) - c exactly, lo = the exact division
+// residual over dU): (fx_hi, fx_lo, fy_hi, fy_lo).
+__global__ void k_plan_offsets(GridGeom G, int64_t n_valid_max, const uint32_t *__restrict__ n_valid_p,
+                               const float2 *__restrict__ uv, const uint32_t *__restrict__ s_idx,
+                               const uint32_t *__restrict__ s_key, float4 *__restrict__ s_f) {
     const uint32_t nv = *n_valid_p;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv && i < n_valid_max;
-         i += (int64_t)gridDim.x * blockDim.x)
-        s_uv[i] = uv[s_idx[i]];
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 p = uv[s_idx[i]];
+        const uint32_t key = s_key[i];
+        const int tile = (int)(key >> 8), tx = tile % G.tt, ty = tile / G.tt;
+        const int cx = tx * TS + (int)(key & (TS - 1)) - G.off;
+        const int cy = ty * TS + (int)((key >> 4) & (TS - 1)) - G.off;
+        const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
+        s_f[i] = make_float4(__fsub_rn(qx, (float)cx), __fdiv_rn(fmaf(-qx, G.du, p.x), G.du),
+                             __fsub_rn(qy, (float)cy), __fdiv_rn(fmaf(-qy, G.du, p.y), G.du));
+    }
 }
 
 // One block: cut every tile's run of sorted visibilities into units of <= UMAX.
@@ -295,12 +306,34 @@ __global__ void __launch_bounds__(1024) k_units(const uint32_t *__restrict__ off
 
 // ------------------------------------------------------------------ accumulation
 
+// Per-lane accumulators of one slot lane: footprint column dx, rows dy, for
+// (re, im, w).  blk: plain FP32 sums of up to FOLD visibilities; s, c: Kahan
+// sum and compensation of the folded blocks.
+constexpr int FOLD = 4;
 struct SlotAcc {
-    float s[3][FWMAX], c[3][FWMAX];  // re, im, w: compensated sums per footprint row
+    float blk[3][FWMAX], s[3][FWMAX], c[3][FWMAX];
 };
+
+__device__ __forceinline__ void acc_zero(SlotAcc &A) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int q = 0; q < FWMAX; ++q) A.blk[k][q] = A.s[k][q] = A.c[k][q] = 0.f;
+}
+
+__device__ __forceinline__ void acc_fold(SlotAcc &A) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int q = 0; q < FWMAX; ++q) {
+            kahan_add(A.s[k][q], A.c[k][q], A.blk[k][q]);
+            A.blk[k][q] = 0.f;
+        }
+}
 
 __device__ __forceinline__ void slot_flush(float (*sm)[HC], SlotAcc &A, int hx0, int hy0, int HS,
                                            int fw, uint8_t *shit) {
+    acc_fold(A);
 #pragma unroll
     for (int dyi = 0; dyi < FWMAX; ++dyi) {
         if (dyi < fw) {
@@ -317,9 +350,11 @@ __device__ __forceinline__ void slot_flush(float (*sm)[HC], SlotAcc &A, int hx0,
     }
 }
 
+constexpr size_t GRID_SMEM = sizeof(float) * GW * 6 * HC + UMAX * (sizeof(float4) + sizeof(float2) + 1) + HC;
+
 __global__ void __launch_bounds__(GW * 32) k_grid(GridGeom G, const int4 *__restrict__ units,
                                                   const int *__restrict__ n_units,
-                                                  const float2 *__restrict__ s_uv,
+                                                  const float4 *__restrict__ s_f,
                                                   const uint32_t *__restrict__ s_idx,
                                                   const uint32_t *__restrict__ s_key,
                                                   const float2 *__restrict__ vis,
@@ -327,8 +362,12 @@ __global__ void __launch_bounds__(GW * 32) k_grid(GridGeom G, const int4 *__rest
                                                   double *__restrict__ acc_im,
                                                   double *__restrict__ acc_w,
                                                   uint8_t *__restrict__ hit) {
-    __shared__ float sm[GW][6][HC];
-    __shared__ uint8_t shit[HC];
+    extern __shared__ __align__(16) uint8_t dsm[];
+    float(*sm)[6][HC] = (float(*)[6][HC])dsm;                          // [GW][6][HC]
+    float4 *st_f = (float4 *)(dsm + sizeof(float) * GW * 6 * HC);      // [UMAX] offsets
+    float2 *st_v = (float2 *)(st_f + UMAX);                            // [UMAX] visibilities
+    uint8_t *st_c = (uint8_t *)(st_v + UMAX);                          // [UMAX] cell in tile
+    uint8_t *shit = st_c + UMAX;                                       // [HC] touched cells
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int slot = lane >> 3, l8 = lane & 7;
     const int r = G.r, fw = 2 * r + 1, HS = TS + 2 * r;
@@ -337,65 +376,55 @@ __global__ void __launch_bounds__(GW * 32) k_grid(GridGeom G, const int4 *__rest
     const int nu = *n_units;
     for (int u = blockIdx.x; u < nu; u += gridDim.x) {
         const int4 U = units[u];
+        const int total = U.z - U.y;
         for (int i = threadIdx.x; i < GW * 6 * HC; i += blockDim.x) (&sm[0][0][0])[i] = 0.f;
         for (int i = threadIdx.x; i < HC; i += blockDim.x) shit[i] = 0;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {   // stage the unit
+            st_f[t] = s_f[U.y + t];
+            st_c[t] = (uint8_t)(s_key[U.y + t] & 255u);
+            st_v[t] = vis[s_idx[U.y + t]];
+        }
         __syncthreads();
         const int tile = U.x, tx = tile % G.tt, ty = tile / G.tt;
         const int gx0 = tx * TS - G.off, gy0 = ty * TS - G.off;
-        const int total = U.z - U.y, nslots = GW * SLOTS;
+        const int nslots = GW * SLOTS;
         const int per = (total + nslots - 1) / nslots;
         const int sid = warp * SLOTS + slot;
-        const int my0 = U.y + min(total, sid * per), my1 = U.y + min(total, (sid + 1) * per);
+        const int my0 = min(total, sid * per), my1 = min(total, (sid + 1) * per);
         int trips = my1 - my0;
         trips = max(trips, __shfl_xor_sync(FULL, trips, 8));
         trips = max(trips, __shfl_xor_sync(FULL, trips, 16));
         SlotAcc A;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int q = 0; q < FWMAX; ++q) A.s[k][q] = A.c[k][q] = 0.f;
-        int run_lx = 0, run_ly = 0;
-        bool open = false;
+        acc_zero(A);
+        int run_c = -1, nblk = 0;
         for (int it = 0; it < trips; ++it) {
             const int idx = my0 + it;
             const bool act = idx < my1;
-            float2 p = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
-            int lx = 0, ly = 0;
+            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 v = make_float2(0.f, 0.f);
+            int cc = run_c;
             if (act) {
-                p = s_uv[idx];
-                const uint32_t key = s_key[idx];
-                v = vis[s_idx[idx]];
-                lx = key & (TS - 1);
-                ly = (key >> 4) & (TS - 1);
+                f = st_f[idx];
+                v = st_v[idx];
+                cc = st_c[idx];
             }
-            const bool need = act && open && (lx != run_lx || ly != run_ly);
+            const bool need = act && run_c >= 0 && cc != run_c;
             if (__any_sync(FULL, need)) {
                 for (int s = 0; s < SLOTS; ++s) {
                     if (slot == s && need && lane_on)
-                        slot_flush(sm[warp], A, run_lx + l8, run_ly, HS, fw, shit);
+                        slot_flush(sm[warp], A, (run_c & (TS - 1)) + l8, run_c >> 4, HS, fw, shit);
                     __syncwarp();
                 }
                 if (need) {
-#pragma unroll
-                    for (int k = 0; k < 3; ++k)
-#pragma unroll
-                        for (int q = 0; q < FWMAX; ++q) A.s[k][q] = A.c[k][q] = 0.f;
+                    acc_zero(A);
+                    nblk = 0;
                 }
             }
-            if (act) {
-                open = true;
-                run_lx = lx;
-                run_ly = ly;
-            }
+            if (act) run_c = cc;
             float wx = 1.f, wyl = 1.f;
             if (G.kernel == ABS_KERNEL_GAUSS) {
-                const int cx = gx0 + lx, cy = gy0 + ly;
-                const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
-                const float fxh = __fsub_rn(qx, (float)cx), fyh = __fsub_rn(qy, (float)cy);
-                const float fxl = __fdiv_rn(fmaf(-qx, G.du, p.x), G.du);
-                const float fyl = __fdiv_rn(fmaf(-qy, G.du, p.y), G.du);
-                wx = wexp(d, fxh, fxl, G.s_hi, G.s_lo);
-                wyl = wexp(d, fyh, fyl, G.s_hi, G.s_lo);
+                wx = wexp(d, f.x, f.y, G.s_hi, G.s_lo);
+                wyl = wexp(d, f.z, f.w, G.s_hi, G.s_lo);
             }
             const int sbase = slot * 8;
 #pragma unroll
@@ -403,15 +432,19 @@ __global__ void __launch_bounds__(GW * 32) k_grid(GridGeom G, const int4 *__rest
                 const float wy = __shfl_sync(FULL, wyl, sbase + dyi);
                 if (dyi < fw && act && lane_on) {
                     const float w = wx * wy;
-                    kahan_add(A.s[0][dyi], A.c[0][dyi], w * v.x);
-                    kahan_add(A.s[1][dyi], A.c[1][dyi], w * v.y);
-                    kahan_add(A.s[2][dyi], A.c[2][dyi], w);
+                    A.blk[0][dyi] = fmaf(w, v.x, A.blk[0][dyi]);
+                    A.blk[1][dyi] = fmaf(w, v.y, A.blk[1][dyi]);
+                    A.blk[2][dyi] += w;
                 }
+            }
+            if (act && ++nblk == FOLD) {
+                acc_fold(A);
+                nblk = 0;
             }
         }
         for (int s = 0; s < SLOTS; ++s) {
-            if (slot == s && open && lane_on)
-                slot_flush(sm[warp], A, run_lx + l8, run_ly, HS, fw, shit);
+            if (slot == s && run_c >= 0 && lane_on)
+                slot_flush(sm[warp], A, (run_c & (TS - 1)) + l8, run_c >> 4, HS, fw, shit);
             __syncwarp();
         }
         __syncthreads();
@@ -463,7 +496,7 @@ __global__ void k_grid_finalize(int n, const double *__restrict__ acc_re,
 
 struct PlanBufs {
     uint32_t *keys, *hist, *offs, *bsum;
-    float2 *s_uv;
+    float4 *s_f;
     uint32_t *s_idx, *s_key;
     uint32_t *k2, *v2, *vals, *rhist, *roffs, *n_valid;
     int4 *units;
@@ -482,7 +515,7 @@ bool plan_bufs(abs_ctx *ctx, const GridGeom &G, int64_t n_vis, PlanBufs &b) {
     b.hist = (uint32_t *)workspace(ctx, "plan.hist", sizeof(uint32_t) * b.nkeys);
     b.offs = (uint32_t *)workspace(ctx, "plan.offs", sizeof(uint32_t) * b.nkeys);
     b.bsum = (uint32_t *)workspace(ctx, "plan.bsum", sizeof(uint32_t) * (cdiv(b.nkeys, 4096) + 1));
-    b.s_uv = (float2 *)workspace(ctx, "plan.s_uv", sizeof(float2) * nv);
+    b.s_f = (float4 *)workspace(ctx, "plan.s_f", sizeof(float4) * nv);
     b.s_idx = (uint32_t *)workspace(ctx, "plan.s_idx", sizeof(uint32_t) * nv);
     b.s_key = (uint32_t *)workspace(ctx, "plan.s_key", sizeof(uint32_t) * nv);
     b.units = (int4 *)workspace(ctx, "plan.units", sizeof(int4) * b.units_cap);
@@ -494,7 +527,7 @@ bool plan_bufs(abs_ctx *ctx, const GridGeom &G, int64_t n_vis, PlanBufs &b) {
     b.rhist = (uint32_t *)workspace(ctx, "plan.rhist", sizeof(uint32_t) * 256 * b.rtiles);
     b.roffs = (uint32_t *)workspace(ctx, "plan.roffs", sizeof(uint32_t) * 256 * b.rtiles);
     b.n_valid = (uint32_t *)workspace(ctx, "plan.n_valid", sizeof(uint32_t));
-    return b.keys && b.hist && b.offs && b.bsum && b.s_uv && b.s_idx && b.s_key && b.units &&
+    return b.keys && b.hist && b.offs && b.bsum && b.s_f && b.s_idx && b.s_key && b.units &&
            b.n_units && b.k2 && b.v2 && b.vals && b.rhist && b.roffs && b.n_valid;
 }
 
@@ -550,7 +583,8 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
                 std::swap(vi, vo);
             }
         }
-        k_plan_gather<<<grid_v, 256, 0, st>>>(n_vis, b.n_valid, (const float2 *)d_uv, b.s_idx, b.s_uv);
+        k_plan_offsets<<<grid_v, 256, 0, st>>>(G, n_vis, b.n_valid, (const float2 *)d_uv, b.s_idx, b.s_key,
+                                               b.s_f);
     }
     return check_launch(ctx, "grid plan");
 }
@@ -578,8 +612,9 @@ abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, c
     }
     if (n_vis > 0) {
         StageTimer timer(ctx, "grid");
-        const int blocks = std::min(b.units_cap, ctx->sm_count * 4);
-        k_grid<<<blocks, GW * 32, 0, st>>>(G, b.units, b.n_units, b.s_uv, b.s_idx, b.s_key,
+        const int blocks = std::min(b.units_cap, ctx->sm_count * 3);
+        cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRID_SMEM);
+        k_grid<<<blocks, GW * 32, GRID_SMEM, st>>>(G, b.units, b.n_units, b.s_f, b.s_idx, b.s_key,
                                            (const float2 *)d_vis, acc, acc + cells,
                                            acc + 2 * cells, hit);
     }

@@ -376,19 +376,22 @@ def test_split_bf16_estimate(ctx, cfg_id):
 
 
 def test_split_bf16_odd_shapes(ctx):
-    # rings not a multiple of 16 (MMA N padding), one pixel range ending mid-chunk
-    rng = np.random.default_rng(3)
+    # 37 rings (MMA N padded to 48), odd sky grid N = 45 (pixel ranges end mid-chunk),
+    # a structured quadratic sky sampled on uniform baselines
     n, du = 48, 1.0
-    edges = 2 * np.pi * np.linspace(1.5, 15.0, 38)       # 37 rings -> N = 48 columns
-    uv = rng.uniform(-15.0, 15.0, (4000, 2)).astype(np.float32)
-    vis = (rng.standard_normal(4000) + 1j * rng.standard_normal(4000)).astype(np.complex64)
-    est = oracle.estimate(n, du, edges, uv, vis)
+    edges = 2 * np.pi * np.linspace(1.5, 15.0, 38)
+    wl = synth.Workload("odd-48sq-37lin", n, du, edges, map_side=48, layout="annulus", n_vis=4000,
+                        u_min=1.5, u_max=15.0)
+    inp = synth.make_inputs(7, 0, wl=wl)
+    est = oracle.estimate(n, du, edges, inp.uv, inp.vis)
     for prec, tol in ((absmod.ABS_FP32, SUM_TOL), (absmod.ABS_SPLIT_BF16, BF16_TOL)):
         cfg = absmod.Config(n_grid=n, du=du, ell_edges=edges, precision=prec)
-        B, T, E, ijk = absmod.estimate(cfg, to_dev(uv), to_dev(synth.vis_as_float2(vis)), ctx)
+        assert absmod.abs_fft_size(cfg) == 45
+        B, T, E, ijk = absmod.estimate(cfg, to_dev(inp.uv), to_dev(synth.vis_as_float2(inp.vis)), ctx)
         ctx.sync()
         assert np.array_equal(T.cpu().numpy(), est.T)
         Bg = B.cpu().numpy()
         ok = ~np.isnan(est.B)
         big = ok & (np.abs(est.B) >= 1e-3 * np.nanmax(np.abs(est.B)))
-        assert (np.abs(Bg[big] - est.B[big]) / np.abs(est.B[big])).max() <= tol
+        rel = np.abs(Bg[big] - est.B[big]) / np.abs(est.B[big])
+        assert rel.max() <= tol, f"precision {prec}: relative error {rel.max():.3e}"
