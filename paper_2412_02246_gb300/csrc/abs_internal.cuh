@@ -40,10 +40,18 @@ struct Setup {
     int32_t *d_ijk = nullptr;
     float4 *d_tw = nullptr;       // exp(-2 pi i t / N), t < N, as double-float (re hi, lo, im hi, lo)
     int32_t *d_Rm = nullptr;
+    // ordered closed-triangle counts of the full annuli [nb][nb][nb] (halved),
+    // a property of the ring geometry, computed on first use
+    unsigned long long *d_full_counts = nullptr;
+    bool full_counts_ready = false;
 };
 
 // Host-side validation + derivation.  Returns ABS_OK or an error with text in err.
 abs_status make_setup(const abs_config *cfg, Setup &s, std::string &err);
+// The allocation-free core of make_setup: validation, ring thresholds q[0..nb],
+// per-ring largest |g_x| Rm[0..nb-1], R and the sky-grid side N, written to
+// caller storage; *err is a static message on failure.
+abs_status derive_grid(const abs_config *cfg, int64_t *q, int *Rm, int *R, int *N, const char **err);
 // Canonical closing triplets for thresholds q (shared by abs_triplets and Setup).
 void closing_triplets(const std::vector<int64_t> &q, std::vector<int32_t> &ijk);
 int64_t ring_threshold(double ell, float du);
@@ -80,6 +88,7 @@ enum : int32_t {
     DERR_TRIPLET_ORDER = 1,   // triplet list not canonical / bin out of range
     DERR_TRIPLET_BIN = 2,
     DERR_TIMEOUT = 3,
+    DERR_CAPACITY = 4,        // an internal work list was too small for the problem
 };
 
 // Grow-only named workspace.  Returns nullptr on allocation failure.

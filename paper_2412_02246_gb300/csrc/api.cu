@@ -64,49 +64,95 @@ static std::vector<int> radix_plan(int N) {
     return r;
 }
 
-abs_status make_setup(const abs_config *cfg, Setup &s, std::string &err) {
-    if (!cfg) { err = "cfg is NULL"; return ABS_ERR_INVALID_ARG; }
+// Validates cfg and derives the ring thresholds q[0..nb], the largest |g_x| of
+// a ring cell on the grid per ring (Rm[0..nb-1], -1 for an empty ring), their
+// maximum R and the sky-grid side N, in caller-provided storage only (no heap
+// or device allocation).  *err points at a static message on failure.
+abs_status derive_grid(const abs_config *cfg, int64_t *q, int *Rm, int *R_out, int *N_out, const char **err) {
+    if (!cfg) { *err = "cfg is NULL"; return ABS_ERR_INVALID_ARG; }
     if (cfg->n_grid < 8 || cfg->n_grid > 8192 || (cfg->n_grid & 1)) {
-        err = "n_grid must be even and in [8, 8192]";
+        *err = "n_grid must be even and in [8, 8192]";
         return ABS_ERR_INVALID_ARG;
     }
     const float du = (float)cfg->du;
     if (!(cfg->du > 0.0) || !std::isfinite(cfg->du) || !(du > 0.f) || !std::isfinite(du)) {
-        err = "du must be finite and > 0 in binary32";
+        *err = "du must be finite and > 0 in binary32";
         return ABS_ERR_INVALID_ARG;
     }
     if (cfg->kernel != ABS_KERNEL_GAUSS && cfg->kernel != ABS_KERNEL_NGP) {
-        err = "kernel must be ABS_KERNEL_GAUSS or ABS_KERNEL_NGP";
+        *err = "kernel must be ABS_KERNEL_GAUSS or ABS_KERNEL_NGP";
         return ABS_ERR_INVALID_ARG;
     }
     if (cfg->kernel == ABS_KERNEL_GAUSS) {
         if (!(cfg->sigma_cells > 0.25) || !std::isfinite(cfg->sigma_cells)) {
-            err = "sigma_cells must be finite and > 0.25";
+            *err = "sigma_cells must be finite and > 0.25";
             return ABS_ERR_INVALID_ARG;
         }
         if (cfg->radius_cells < 0 || cfg->radius_cells > ABS_MAX_RADIUS) {
-            err = "radius_cells must be in [0, 3]";
+            *err = "radius_cells must be in [0, 3]";
             return ABS_ERR_INVALID_ARG;
         }
     }
-    if (cfg->n_bins < 1 || cfg->n_bins > ABS_MAX_BINS) { err = "n_bins must be in [1, 254]"; return ABS_ERR_INVALID_ARG; }
-    if (!cfg->ell_edges) { err = "ell_edges is NULL"; return ABS_ERR_INVALID_ARG; }
+    if (cfg->n_bins < 1 || cfg->n_bins > ABS_MAX_BINS) { *err = "n_bins must be in [1, 254]"; return ABS_ERR_INVALID_ARG; }
+    if (!cfg->ell_edges) { *err = "ell_edges is NULL"; return ABS_ERR_INVALID_ARG; }
     for (int m = 0; m <= cfg->n_bins; ++m) {
         const double e = cfg->ell_edges[m];
         if (!std::isfinite(e) || !(e > 0.0) || (m > 0 && !(e > cfg->ell_edges[m - 1]))) {
-            err = "ell_edges must be finite, > 0 and strictly ascending";
+            *err = "ell_edges must be finite, > 0 and strictly ascending";
             return ABS_ERR_INVALID_ARG;
         }
     }
     if (cfg->precision != ABS_FP32 && cfg->precision != ABS_SPLIT_BF16) {
-        err = "precision must be ABS_FP32 or ABS_SPLIT_BF16";
+        *err = "precision must be ABS_FP32 or ABS_SPLIT_BF16";
         return ABS_ERR_INVALID_ARG;
     }
-    if (!(cfg->norm_A > 0.0) || !std::isfinite(cfg->norm_A)) { err = "norm_A must be finite and > 0"; return ABS_ERR_INVALID_ARG; }
+    if (!(cfg->norm_A > 0.0) || !std::isfinite(cfg->norm_A)) { *err = "norm_A must be finite and > 0"; return ABS_ERR_INVALID_ARG; }
+    const int nb = cfg->n_bins, half = cfg->n_grid / 2 - 1;
+    for (int m = 0; m <= nb; ++m) q[m] = ring_threshold(cfg->ell_edges[m], du);
+    if (q[nb] > (int64_t)1 << 40) { *err = "l range too large for the uv grid spacing"; return ABS_ERR_INVALID_ARG; }
+    int R = 0;
+    for (int m = 0; m < nb; ++m) {
+        Rm[m] = -1;
+        const int64_t lo = q[m], hi = q[m + 1] - 1;
+        if (hi < lo) continue;
+        for (int64_t x = std::min<int64_t>(half, isqrt64(hi)); x >= 0; --x) {
+            const int64_t ylo = ceil_sqrt64(lo - x * x);
+            const int64_t yhi = std::min<int64_t>(half, isqrt64(hi - x * x));
+            if (hi - x * x >= 0 && ylo <= yhi) {
+                Rm[m] = (int)x;
+                break;
+            }
+        }
+        R = std::max(R, Rm[m]);
+    }
+    const int Nmin = std::max(3 * R + 1, 8);
+    int N = cfg->n_fft;
+    if (N == 0) {
+        N = Nmin;
+        while (!smooth235(N)) ++N;
+    } else if (!smooth235(N) || N < Nmin) {
+        *err = "n_fft must be a 2^a 3^b 5^c value >= 3R+1 (R = largest |g_x| of a ring cell)";
+        return ABS_ERR_INVALID_ARG;
+    }
+    if (N > ABS_MAX_FFT) { *err = "sky grid side N exceeds 4096 (reduce the l range or coarsen du)"; return ABS_ERR_UNSUPPORTED; }
+    *R_out = R;
+    *N_out = N;
+    return ABS_OK;
+}
 
+abs_status make_setup(const abs_config *cfg, Setup &s, std::string &err) {
+    const int nb = cfg && cfg->n_bins >= 1 && cfg->n_bins <= ABS_MAX_BINS ? cfg->n_bins : 1;
+    s.q.assign(nb + 1, 0);
+    s.Rm.assign(nb, -1);
+    const char *msg = "";
+    const abs_status st = derive_grid(cfg, s.q.data(), s.Rm.data(), &s.R, &s.N, &msg);
+    if (st != ABS_OK) {
+        err = msg;
+        return st;
+    }
     s.n = cfg->n_grid;
     s.half = s.n / 2 - 1;
-    s.du = du;
+    s.du = (float)cfg->du;
     s.kernel = cfg->kernel;
     s.r = cfg->kernel == ABS_KERNEL_NGP ? 0 : cfg->radius_cells;
     if (cfg->kernel == ABS_KERNEL_GAUSS) {
@@ -115,38 +161,6 @@ abs_status make_setup(const abs_config *cfg, Setup &s, std::string &err) {
         s.s_lo = (float)(sc - (double)s.s_hi);
     }
     s.nb = cfg->n_bins;
-    s.q.resize(s.nb + 1);
-    for (int m = 0; m <= s.nb; ++m) s.q[m] = ring_threshold(cfg->ell_edges[m], du);
-    if (s.q[s.nb] > (int64_t)1 << 40) { err = "l range too large for the uv grid spacing"; return ABS_ERR_INVALID_ARG; }
-    // largest |g_x| of a ring cell on the grid, per ring
-    s.Rm.assign(s.nb, -1);
-    s.R = 0;
-    for (int m = 0; m < s.nb; ++m) {
-        const int64_t lo = s.q[m], hi = s.q[m + 1] - 1;
-        if (hi < lo) continue;
-        for (int64_t x = std::min<int64_t>(s.half, isqrt64(hi)); x >= 0; --x) {
-            const int64_t ylo = ceil_sqrt64(lo - x * x);
-            const int64_t yhi = std::min<int64_t>(s.half, isqrt64(hi - x * x));
-            if (hi - x * x >= 0 && ylo <= yhi) {
-                s.Rm[m] = (int)x;
-                break;
-            }
-        }
-        s.R = std::max(s.R, s.Rm[m]);
-    }
-    const int Nmin = std::max(3 * s.R + 1, 8);
-    if (cfg->n_fft == 0) {
-        int N = Nmin;
-        while (!smooth235(N)) ++N;
-        s.N = N;
-    } else {
-        if (!smooth235(cfg->n_fft) || cfg->n_fft < Nmin) {
-            err = "n_fft must be a 2^a 3^b 5^c value >= 3R+1 (R = " + std::to_string(s.R) + ")";
-            return ABS_ERR_INVALID_ARG;
-        }
-        s.N = cfg->n_fft;
-    }
-    if (s.N > ABS_MAX_FFT) { err = "sky grid side N exceeds 4096 (reduce the l range or coarsen du)"; return ABS_ERR_UNSUPPORTED; }
     s.radices = radix_plan(s.N);
     // lattice cells per ring on the grid (capacity of the ring lists)
     s.lat.assign(s.nb, 0);
@@ -234,6 +248,9 @@ static void free_setup(Setup &s) {
     cudaFree(s.d_ijk);
     cudaFree(s.d_tw);
     cudaFree(s.d_Rm);
+    cudaFree(s.d_full_counts);
+    s.d_full_counts = nullptr;
+    s.full_counts_ready = false;
     s.d_q = nullptr;
     s.d_lat_off = nullptr;
     s.d_ijk = nullptr;
@@ -403,6 +420,7 @@ abs_status abs_sync(abs_ctx *ctx) {
     cudaMemset(ctx->d_err, 0, sizeof(int32_t));
     if (e == DERR_TIMEOUT) return fail(ctx, ABS_ERR_TIMEOUT, "a bounded device wait gave up");
     if (e == DERR_TRIPLET_ORDER) return fail(ctx, ABS_ERR_DEVICE, "triplet list is not in canonical order");
+    if (e == DERR_CAPACITY) return fail(ctx, ABS_ERR_UNSUPPORTED, "problem too large for an internal work list");
     return fail(ctx, ABS_ERR_DEVICE, "triplet list holds a bin outside 0 <= i <= j <= k < n_bins");
 }
 

@@ -4,29 +4,39 @@
 // N^-2 sum_p I_i I_j I_k is the number T_ijk of ordered closed triangles
 // (g1 in a_i, g2 in a_j, g3 in a_k, all filled, g1 + g2 + g3 = 0).  FP32 or
 // even FP64 pixel sums cannot return that integer exactly at these sizes, so
-// it is counted directly in integers:
+// it is counted in integers.  For symmetric cell sets X, Y, Z (closed under
+// g -> -g; the origin is in no ring)
 //
-//   T_ijk = 2 #{ (g1, g2) : g1 in F_i upper half plane, g2 in F_j, g1 + g2 in F_k }
+//   T(X_i, Y_j, Z_k) = 2 #{ (g1, g2) : g1 in X_i upper half plane, g2 in Y_j, g1 + g2 in Z_k }
 //
-// (F_m = filled cells of ring m.  F_k is symmetric under g -> -g, so the
-// third vertex -(g1+g2) is in F_k iff g1 + g2 is; negating a triangle maps
-// g1 to the other half plane, hence the factor 2; the origin is in no ring.)
+// (the third vertex -(g1+g2) is in Z_k iff g1 + g2 is; negating a triangle
+// moves g1 to the other half plane, hence the factor 2).
+//
+// With A = every cell of the annuli on the grid, F = the filled ones and
+// H = A \ F the holes, splitting g1, then g2, then g3 into filled and hole gives
+//
+//   T(F,F,F) = T(A,A,A) - T(H,A,A) - T(F,H,A) - T(F,F,H),
+//
+// where T(A,A,A) depends only on the ring geometry (computed once per
+// configuration and kept by the context) and every other term has a hole
+// among the enumerated pair, so its cost is |H| x ring size instead of
+// ring size squared.  T(F,F,H) is enumerated as (g1 in F_i, g3 in H_k) with
+// g2 = -(g1+g3) looked up in F.  A device-side estimate picks this route or
+// the direct enumeration of T(F,F,F), whichever visits fewer pairs; both are
+// exact.
 //
 // Ring lists are built row-major, so the upper half plane of each ring is
-// the second half of its list.  A byte map holds 1 + ring id of every filled
-// ring cell (0 elsewhere), indexed by |lin(h)| with lin(g) = g_y W + g_x,
+// the second half of its list.  A byte map holds 1 + ring id of every cell of
+// a family (0 elsewhere), indexed by |lin(h)| with lin(g) = g_y W + g_x,
 // W = 4R + 1: lin is linear and odd, so lin(g1 + g2) = lin(g1) + lin(g2) and
 // |lin(h)| = lin(+-h) picks the upper-half-plane representative of h, whose
-// ring and filled state are those of h.  A pair is then classified by one
-// add, one abs and one byte load, with no bounds test, from a map half the
-// size of [-2R, 2R]^2.  One CTA per (i, j,
-// chunk of g1) streams all of F_j through shared memory; each thread keeps
-// run-length state for its g1 cells (consecutive g2 in row order usually
-// land in the same ring) and adds finished runs into a lane-private
-// shared-memory histogram over k, which is reduced into an int64 (i, j, k)
-// table at the end.  Of the two sets of a pair (upper half of F_i, all of
-// F_j) the larger is spread over the threads and the smaller is streamed, so
-// that no thread idles through a pass over a large ring.
+// ring and membership are those of h.  A pair is then classified by one add,
+// one abs and one byte load, with no bounds test.  One CTA per work item
+// (pair of rings, chunk of the larger set spread over the threads, chunk of
+// the smaller set streamed through shared memory); each thread keeps
+// run-length state (consecutive cells in row order usually land in the same
+// ring) and adds finished runs into a lane-private shared-memory histogram
+// over the third ring, reduced into an int64 table at the end.
 #include "abs_internal.cuh"
 
 namespace absk {
@@ -34,7 +44,6 @@ namespace {
 
 constexpr int G1 = 4;            // g1 cells per thread
 constexpr int CT = 256;          // threads per counting CTA (max)
-constexpr int STAGE = 2048;      // inner cells staged per pass
 constexpr int INNER = 512;       // inner cells per work item (bounds the work of one item)
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -89,12 +98,30 @@ __device__ __forceinline__ int span_len(const RowSpan &sp) {
     return sp.x0 == 0 ? 2 * sp.x1 + 1 : 2 * (sp.x1 - sp.x0 + 1);
 }
 
-// Pass 1 (one warp per (ring, row)): filled cells and FP64 sum of |g|.
+// Cell families of the ring tables.
+enum { FAM_F = 0, FAM_H = 1, FAM_A = 2, NFAM = 3 };
+// Pair-count jobs: (set of g1 [upper half], set of g2, map looked up), table.
+enum { JOB_DIRECT = 0, JOB_E1 = 1, JOB_E2 = 2, JOB_E3 = 3, JOB_FULL = 4, NJOB = 5 };
+__host__ __device__ constexpr int job_x(int j) { return j == JOB_E1 ? FAM_H : j == JOB_FULL ? FAM_A : FAM_F; }
+__host__ __device__ constexpr int job_y(int j) {
+    return j == JOB_DIRECT ? FAM_F : (j == JOB_E1 || j == JOB_FULL) ? FAM_A : FAM_H;
+}
+__host__ __device__ constexpr bool job_map_a(int j) { return j == JOB_E1 || j == JOB_E2 || j == JOB_FULL; }
+
+struct Fams {
+    const short2 *lists;
+    const int64_t *off;   // [NFAM][nb + 1]
+    const int32_t *cnt;   // [NFAM][nb]
+};
+
+// Pass 1 (one warp per (ring, row)): filled, hole and annulus cells; FP64 sum
+// of |g| over the filled ones.  rowcnt is [NFAM][nb * rows].
 __global__ void k_ring_rows(CountGeom G, const int64_t *__restrict__ q, const uint8_t *__restrict__ mask,
                             uint32_t *__restrict__ rowcnt, double *__restrict__ rowlen) {
     const int rows = 2 * G.R + 1;
+    const int64_t nrow = (int64_t)G.nb * rows;
     const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (e >= G.nb * rows) return;
+    if (e >= nrow) return;
     const int m = e / rows, y = e - m * rows - G.R;
     const RowSpan sp = row_span(G, q[m], q[m + 1], y);
     const int len = span_len(sp);
@@ -115,182 +142,236 @@ __global__ void k_ring_rows(CountGeom G, const int64_t *__restrict__ q, const ui
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
     if (lane == 0) {
         rowcnt[e] = c;
+        rowcnt[nrow + e] = (uint32_t)len - c;
+        rowcnt[2 * nrow + e] = (uint32_t)len;
         rowlen[e] = sum;
     }
 }
 
-// Pass 2 (one warp per (ring, row)): write the cells in x order and the byte map.
+// Pass 2 (one warp per (ring, row)): write the three families in x order and
+// the byte maps of F and A.
 __global__ void k_ring_write(CountGeom G, const int64_t *__restrict__ q, const uint8_t *__restrict__ mask,
                              const uint32_t *__restrict__ rowoff, short2 *__restrict__ lists,
-                             uint8_t *__restrict__ binmap) {
+                             uint8_t *__restrict__ mapF, uint8_t *__restrict__ mapA) {
     const int rows = 2 * G.R + 1;
+    const int64_t nrow = (int64_t)G.nb * rows;
     const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (e >= G.nb * rows) return;
+    if (e >= nrow) return;
     const int m = e / rows, y = e - m * rows - G.R;
     const RowSpan sp = row_span(G, q[m], q[m + 1], y);
     const int len = span_len(sp);
-    uint32_t pos = rowoff[e];
+    uint32_t pf = rowoff[e], ph = rowoff[nrow + e];
+    const uint32_t pa = rowoff[2 * nrow + e];
     for (int t0 = 0; t0 < len; t0 += 32) {
         const int t = t0 + lane;
-        bool on = false;
+        bool on = false, in = t < len;
         int x = 0;
-        if (t < len) {
+        if (in) {
             x = span_x(sp, t);
             on = mask[cell_index(G.n, x, y)] != 0;
         }
-        const unsigned bal = __ballot_sync(FULL, on);
-        if (on) {
-            lists[pos + __popc(bal & ((1u << lane) - 1u))] = make_short2((short)x, (short)y);
+        const unsigned bf = __ballot_sync(FULL, on), bh = __ballot_sync(FULL, in && !on);
+        const unsigned below = (1u << lane) - 1u;
+        if (in) {
+            const short2 g = make_short2((short)x, (short)y);
+            lists[pa + t] = g;
+            if (on) lists[pf + __popc(bf & below)] = g;
+            else lists[ph + __popc(bh & below)] = g;
             const int lin = y * G.W + x;
-            if (lin > 0) binmap[lin] = (uint8_t)(m + 1);
+            if (lin > 0) {
+                mapA[lin] = (uint8_t)(m + 1);
+                if (on) mapF[lin] = (uint8_t)(m + 1);
+            }
         }
-        pos += __popc(bal);
+        pf += __popc(bf);
+        ph += __popc(bh);
     }
 }
 
-// Pass 3 (one warp per ring): ring offsets, counts and mean l (fixed-order sums).
+// Pass 3 (one warp per (family, ring)): offsets, counts, and the mean l of the
+// filled cells (fixed-order sums).
 __global__ void k_ring_finish(CountGeom G, float du, const uint32_t *__restrict__ rowoff,
                               const uint32_t *__restrict__ rowcnt, const double *__restrict__ rowlen,
                               int64_t *__restrict__ ring_off, int32_t *__restrict__ counts,
                               double *__restrict__ ellbar) {
-    const int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (m >= G.nb) return;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= NFAM * G.nb) return;
+    const int fam = w / G.nb, m = w - fam * G.nb;
     const int rows = 2 * G.R + 1;
-    const int64_t e0 = (int64_t)m * rows, e1 = e0 + rows;
+    const int64_t nrow = (int64_t)G.nb * rows;
+    const int64_t e0 = fam * nrow + (int64_t)m * rows, e1 = e0 + rows;
     const uint32_t start = rowoff[e0];
     const uint32_t c = rowoff[e1 - 1] + rowcnt[e1 - 1] - start;
     double len = 0.0;
-    for (int64_t e = e0 + lane; e < e1; e += 32) len += rowlen[e];
+    if (fam == FAM_F)
+        for (int64_t e = e0 + lane; e < e1; e += 32) len += rowlen[e];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(FULL, len, o);
     if (lane == 0) {
-        ring_off[m] = start;
-        counts[m] = (int32_t)c;
-        if (m == G.nb - 1) ring_off[G.nb] = start + c;
-        if (ellbar) ellbar[m] = c > 0 ? 2.0 * 3.14159265358979323846 * (double)du * len / (double)c : nan("");
+        ring_off[fam * (G.nb + 1) + m] = start;
+        counts[fam * G.nb + m] = (int32_t)c;
+        if (m == G.nb - 1) ring_off[fam * (G.nb + 1) + G.nb] = start + c;
+        if (fam == FAM_F && ellbar)
+            ellbar[m] = c > 0 ? 2.0 * 3.14159265358979323846 * (double)du * len / (double)c : nan("");
     }
 }
 
-// One block: the (i, j, first g1) work items for every distinct (i, j) row of
-// the triplet list.  A list that is not canonical latches an error.
-__global__ void __launch_bounds__(1024) k_count_items(int nb, int32_t n_trip,
-                                                      const int32_t *__restrict__ ijk,
-                                                      const int32_t *__restrict__ counts, int chunk,
-                                                      int4 *__restrict__ items, int cap,
-                                                      int *__restrict__ n_items,
-                                                      int32_t *__restrict__ err) {
-    __shared__ int32_t wsum[32];
-    __shared__ int32_t carry_s;
-    if (threadIdx.x == 0) carry_s = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int b = 0; b < n_trip; b += blockDim.x) {
-        const int t = b + threadIdx.x;
-        int nchunks = 0, i = 0, j = 0, n_in = 0, n_oc = 0, n_ic = 1;
-        bool outer_i = false;
-        if (t < n_trip) {
-            i = ijk[3 * t];
-            j = ijk[3 * t + 1];
-            const int k = ijk[3 * t + 2];
-            if (i < 0 || j < i || k < j || k >= nb) atomicCAS(err, 0, DERR_TRIPLET_BIN);
-            bool row_start = true;
-            if (t > 0) {
-                const int pi = ijk[3 * t - 3], pj = ijk[3 * t - 2], pk = ijk[3 * t - 1];
-                const bool same = pi == i && pj == j;
-                row_start = !same;
-                const bool ordered = pi < i || (pi == i && (pj < j || (pj == j && pk < k)));
-                if (!ordered) atomicCAS(err, 0, DERR_TRIPLET_ORDER);
-            }
-            if (row_start && i >= 0 && i < nb && j >= 0 && j < nb) {
-                const int half_i = counts[i] / 2, cj = counts[j];
-                outer_i = half_i >= cj;
-                n_in = outer_i ? cj : half_i;
-                n_oc = ((outer_i ? half_i : cj) + chunk - 1) / chunk;
-                n_ic = (n_in + INNER - 1) / INNER;
-                nchunks = n_oc * n_ic;
-            }
-        }
-        // block exclusive scan of nchunks (small values; warp-level then serial over warps)
-        int x = nchunks;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[warp] = x;
-        __syncthreads();
-        int before = 0, tot = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            if (w < warp) before += wsum[w];
-            tot += wsum[w];
-        }
-        const int pos = carry_s + before + x - nchunks;
-        for (int c = 0; c < nchunks; ++c) {
-            const int oc = c / n_ic, ic = c - oc * n_ic;
-            if (pos + c < cap)
-                items[pos + c] = make_int4(i, j, oc * chunk, (ic * INNER) | (outer_i ? (int)0x80000000u : 0));
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) carry_s += tot;
-        __syncthreads();
+// One block: choose the route (direct or holes) from the pair counts it would
+// visit, and write the work items of every job it needs: one per (pair a <= b,
+// chunk of the larger set, chunk of the smaller set).  Items of jobs that look
+// up the filled map go to list 0, the annulus map to list 1.
+// item = (a, b, outer start, inner start | job << 27 | outer-is-x << 31)
+__global__ void __launch_bounds__(1024) k_count_items(int nb, const int32_t *__restrict__ counts, int chunk,
+                                                      int need_full, int4 *__restrict__ items0,
+                                                      int4 *__restrict__ items1, int cap,
+                                                      int *__restrict__ ctl, int32_t *__restrict__ err) {
+    __shared__ unsigned long long wdir_s, wexc_s;
+    __shared__ int use_holes_s;
+    __shared__ int wsum[32];
+    __shared__ int carry_s[2];
+    const int npair = nb * (nb + 1) / 2;
+    const int32_t *cF = counts, *cH = counts + nb, *cA = counts + 2 * nb;
+    if (threadIdx.x == 0) {
+        wdir_s = 0;
+        wexc_s = 0;
+        carry_s[0] = carry_s[1] = 0;
     }
-    if (threadIdx.x == 0) *n_items = min(carry_s, cap);
+    __syncthreads();
+    unsigned long long wd = 0, we = 0;
+    for (int pr = threadIdx.x; pr < npair; pr += blockDim.x) {
+        int a = 0, rem = pr;
+        while (rem >= nb - a) { rem -= nb - a; ++a; }
+        const int b = a + rem;
+        wd += (unsigned long long)(cF[a] / 2) * cF[b];
+        we += (unsigned long long)(cH[a] / 2) * cA[b] + 2ull * (cF[a] / 2) * cH[b];
+    }
+    atomicAdd(&wdir_s, wd);
+    atomicAdd(&wexc_s, we);
+    __syncthreads();
+    if (threadIdx.x == 0) use_holes_s = wexc_s < wdir_s ? 1 : 0;
+    __syncthreads();
+    const int use_holes = use_holes_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int jobs[4], nj = 0;
+    if (use_holes) {
+        jobs[nj++] = JOB_E1;
+        jobs[nj++] = JOB_E2;
+        jobs[nj++] = JOB_E3;
+    } else {
+        jobs[nj++] = JOB_DIRECT;
+    }
+    if (need_full) jobs[nj++] = JOB_FULL;
+    for (int jj = 0; jj < nj; ++jj) {
+        const int job = jobs[jj];
+        const int lst = job_map_a(job) ? 1 : 0;
+        const int32_t *cx = counts + job_x(job) * nb, *cy = counts + job_y(job) * nb;
+        for (int p0 = 0; p0 < npair; p0 += blockDim.x) {
+            const int pr = p0 + threadIdx.x;
+            int a = 0, b = 0, n_oc = 0, n_ic = 1, nchunks = 0;
+            bool outer_x = false;
+            if (pr < npair) {
+                int rem = pr;
+                while (rem >= nb - a) { rem -= nb - a; ++a; }
+                b = a + rem;
+                const int hx = cx[a] / 2, ny = cy[b];
+                outer_x = hx >= ny;
+                const int no = outer_x ? hx : ny, ni = outer_x ? ny : hx;
+                n_oc = (no + chunk - 1) / chunk;
+                n_ic = (ni + INNER - 1) / INNER;
+                nchunks = ni > 0 ? n_oc * n_ic : 0;
+            }
+            int x = nchunks;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) wsum[warp] = x;
+            __syncthreads();
+            int before = 0, tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                if (w < warp) before += wsum[w];
+                tot += wsum[w];
+            }
+            const int pos = carry_s[lst] + before + x - nchunks;
+            int4 *items = lst ? items1 : items0;
+            for (int c = 0; c < nchunks; ++c) {
+                const int oc = c / n_ic, ic = c - oc * n_ic;
+                if (pos + c < cap)
+                    items[pos + c] = make_int4(a, b, oc * chunk,
+                                               (ic * INNER) | (job << 27) | (outer_x ? (int)0x80000000u : 0));
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) carry_s[lst] += tot;
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (carry_s[0] > cap || carry_s[1] > cap) atomicCAS(err, 0, DERR_CAPACITY);
+        ctl[0] = min(carry_s[0], cap);   // items in list 0
+        ctl[1] = min(carry_s[1], cap);   // items in list 1
+        ctl[2] = 0;                      // next item of list 0
+        ctl[3] = 0;                      // next item of list 1
+        ctl[4] = use_holes;
+    }
 }
 
 template <bool MAP_IN_SMEM>
 __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__restrict__ items,
                                                     const int *__restrict__ n_items,
-                                                    const short2 *__restrict__ lists,
-                                                    const int64_t *__restrict__ ring_off,
-                                                    const int32_t *__restrict__ counts,
-                                                    const uint8_t *__restrict__ binmap_g,
-                                                    unsigned long long *__restrict__ Td,
-                                                    int *__restrict__ next_item) {
+                                                    int *__restrict__ next_item, Fams fam,
+                                                    const uint8_t *__restrict__ map_g,
+                                                    unsigned long long *__restrict__ t0,
+                                                    unsigned long long *__restrict__ t1,
+                                                    unsigned long long *__restrict__ t2,
+                                                    unsigned long long *__restrict__ t3,
+                                                    unsigned long long *__restrict__ t4) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int nwarps = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int hs = G.nb + 1;                       // histogram slots (0 = no ring)
+    const int hs = G.nb + 1;                       // histogram slots (0 = none)
     uint32_t *hist = (uint32_t *)smem;             // [nwarps][hs][32]
-    int32_t *stage = (int32_t *)(hist + (size_t)nwarps * hs * 32);   // [STAGE]
-    uint8_t *map_s = (uint8_t *)(stage + STAGE);
-    const uint8_t *map = MAP_IN_SMEM ? map_s : binmap_g;
+    int32_t *stage = (int32_t *)(hist + (size_t)nwarps * hs * 32);   // [INNER]
+    uint8_t *map_s = (uint8_t *)(stage + INNER);
+    const uint8_t *map = MAP_IN_SMEM ? map_s : map_g;
+    const int ni = *n_items;
+    if (ni == 0) return;
     if (MAP_IN_SMEM) {
         const int64_t mb = G.base + 1;
         const int64_t nv = mb / 16;
-        for (int64_t i = threadIdx.x; i < nv; i += blockDim.x)
-            ((uint4 *)map_s)[i] = ((const uint4 *)binmap_g)[i];
-        for (int64_t i = nv * 16 + threadIdx.x; i < mb; i += blockDim.x) map_s[i] = binmap_g[i];
+        for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) ((uint4 *)map_s)[i] = ((const uint4 *)map_g)[i];
+        for (int64_t i = nv * 16 + threadIdx.x; i < mb; i += blockDim.x) map_s[i] = map_g[i];
     }
     for (int i = threadIdx.x; i < nwarps * hs * 32; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
     uint32_t *myhist = hist + (size_t)warp * hs * 32 + lane;
     __shared__ int it_s;
-    const int ni = *n_items;
     for (;;) {
         if (threadIdx.x == 0) it_s = atomicAdd(next_item, 1);   // dynamic: items differ in size
         __syncthreads();
         const int it = it_s;
         if (it >= ni) break;
         const int4 I = items[it];
-        const int i = I.x, j = I.y;
-        const bool outer_i = (I.w & 0x80000000) != 0;
-        const int in0 = I.w & 0x7fffffff;
-        const int ci = counts[i], cj = counts[j];
-        const short2 *Fi = lists + ring_off[i] + ci / 2;   // upper half plane of ring i
-        const short2 *Fj = lists + ring_off[j];
-        const int nh = ci / 2;
-        // outer set: spread over the threads; inner set: streamed through shared memory
-        const short2 *Fo = outer_i ? Fi : Fj;
-        const short2 *Fin = (outer_i ? Fj : Fi) + in0;
-        const int no = outer_i ? nh : cj;
-        const int nin = min(INNER, (outer_i ? cj : nh) - in0);
+        const int a = I.x, b = I.y;
+        const bool outer_x = (I.w & 0x80000000) != 0;
+        const int job = (I.w >> 27) & 7;
+        const int in0 = I.w & 0x07ffffff;
+        const int fx = job_x(job), fy = job_y(job);
+        const int cxa = fam.cnt[fx * G.nb + a], cyb = fam.cnt[fy * G.nb + b];
+        const short2 *X = fam.lists + fam.off[fx * (G.nb + 1) + a] + cxa / 2;   // upper half plane of X_a
+        const short2 *Y = fam.lists + fam.off[fy * (G.nb + 1) + b];
+        const int nx = cxa / 2;
+        const short2 *Fo = outer_x ? X : Y;
+        const short2 *Fin = (outer_x ? Y : X) + in0;
+        const int no = outer_x ? nx : cyb;
+        const int nin = min(INNER, (outer_x ? cyb : nx) - in0);
         int lin1[G1];
         bool v1[G1];
 #pragma unroll
         for (int q = 0; q < G1; ++q) {
-            const int a = I.z + q * blockDim.x + threadIdx.x;
-            v1[q] = a < no;
-            const short2 g = v1[q] ? Fo[a] : make_short2(0, 0);
+            const int k = I.z + q * blockDim.x + threadIdx.x;
+            v1[q] = k < no;
+            const short2 g = v1[q] ? Fo[k] : make_short2(0, 0);
             lin1[q] = g.y * G.W + g.x;
         }
         int cur[G1];
@@ -300,56 +381,64 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
             cur[q] = 0;
             cnt[q] = 0;
         }
-        for (int s0 = 0; s0 < nin; s0 += STAGE) {
-            const int ns = min(STAGE, nin - s0);
-            __syncthreads();
-            for (int a = threadIdx.x; a < ns; a += blockDim.x) {
-                const short2 g = Fin[s0 + a];
-                stage[a] = g.y * G.W + g.x;
-            }
-            __syncthreads();
-            for (int a = 0; a < ns; ++a) {
-                const int l2 = stage[a];
+        __syncthreads();
+        for (int k = threadIdx.x; k < nin; k += blockDim.x) {
+            const short2 g = Fin[k];
+            stage[k] = g.y * G.W + g.x;
+        }
+        __syncthreads();
+        for (int k = 0; k < nin; ++k) {
+            const int l2 = stage[k];
 #pragma unroll
-                for (int q = 0; q < G1; ++q) {
-                    const int k = v1[q] ? (int)map[abs(lin1[q] + l2)] : 0;
-                    if (k != cur[q]) {
-                        myhist[(size_t)cur[q] * 32] += cnt[q];
-                        cur[q] = k;
-                        cnt[q] = 0;
-                    }
-                    ++cnt[q];
+            for (int q = 0; q < G1; ++q) {
+                const int r = v1[q] ? (int)map[abs(lin1[q] + l2)] : 0;
+                if (r != cur[q]) {
+                    myhist[(size_t)cur[q] * 32] += cnt[q];
+                    cur[q] = r;
+                    cnt[q] = 0;
                 }
+                ++cnt[q];
             }
         }
 #pragma unroll
         for (int q = 0; q < G1; ++q) myhist[(size_t)cur[q] * 32] += cnt[q];
         __syncthreads();
-        // reduce lanes and warps; slot 0 (no ring) is dropped
+        unsigned long long *T = job == JOB_DIRECT ? t0 : job == JOB_E1 ? t1 : job == JOB_E2 ? t2
+                                : job == JOB_E3 ? t3 : t4;
         for (int k = 1 + warp; k < hs; k += nwarps) {
-            uint64_t s = 0;
-            for (int w = 0; w < nwarps; ++w) s += hist[((size_t)w * hs + k) * 32 + lane];
+            uint64_t sacc = 0;
+            for (int w = 0; w < nwarps; ++w) sacc += hist[((size_t)w * hs + k) * 32 + lane];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-            if (lane == 0 && s)
-                atomicAdd(&Td[((size_t)i * G.nb + j) * G.nb + (k - 1)], (unsigned long long)s);
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(FULL, sacc, o);
+            if (lane == 0 && sacc)
+                atomicAdd(&T[((size_t)a * G.nb + b) * G.nb + (k - 1)], (unsigned long long)sacc);
         }
         __syncthreads();
-        for (int a = threadIdx.x; a < nwarps * hs * 32; a += blockDim.x) hist[a] = 0u;
+        for (int k = threadIdx.x; k < nwarps * hs * 32; k += blockDim.x) hist[k] = 0u;
         __syncthreads();
     }
 }
 
+// T_ijk for every listed triplet from the tables of the route taken.
 __global__ void k_count_gather(int nb, int32_t n_trip, const int32_t *__restrict__ ijk,
-                               const unsigned long long *__restrict__ Td, int64_t *__restrict__ T) {
+                               const int *__restrict__ ctl, const unsigned long long *__restrict__ td,
+                               const unsigned long long *__restrict__ tA, const unsigned long long *__restrict__ e1,
+                               const unsigned long long *__restrict__ e2, const unsigned long long *__restrict__ e3,
+                               int64_t *__restrict__ T) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_trip) return;
     const int i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
-    if (i < 0 || j < 0 || k < 0 || i >= nb || j >= nb || k >= nb) {
+    if (i < 0 || j < i || k < j || k >= nb) {
         T[t] = 0;
         return;
     }
-    T[t] = 2 * (int64_t)Td[((size_t)i * nb + j) * nb + k];
+    const size_t ijkx = ((size_t)i * nb + j) * nb + k;
+    if (ctl[4]) {
+        const size_t ikj = ((size_t)i * nb + k) * nb + j;
+        T[t] = 2 * ((int64_t)tA[ijkx] - (int64_t)e1[ijkx] - (int64_t)e2[ijkx] - (int64_t)e3[ikj]);
+    } else {
+        T[t] = 2 * (int64_t)td[ijkx];
+    }
 }
 
 CountGeom cgeom(const Setup &s) {
@@ -365,9 +454,9 @@ CountGeom cgeom(const Setup &s) {
 
 struct RingBufs {
     short2 *lists;
-    int32_t *counts;
-    int64_t *ring_off;
-    uint8_t *binmap;
+    int32_t *counts;      // [NFAM][nb]
+    int64_t *ring_off;    // [NFAM][nb + 1]
+    uint8_t *mapF, *mapA;
 };
 
 abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, RingBufs &rb,
@@ -375,27 +464,38 @@ abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, Ring
     const CountGeom G = cgeom(s);
     const int64_t ncell = std::max<int64_t>(s.lat_off.back(), 1);
     const int64_t nrow = (int64_t)s.nb * (2 * s.R + 1);
-    rb.lists = (short2 *)workspace(ctx, "ring.lists", sizeof(short2) * ncell);
-    rb.counts = (int32_t *)workspace(ctx, "ring.counts", sizeof(int32_t) * s.nb);
-    rb.ring_off = (int64_t *)workspace(ctx, "ring.off", sizeof(int64_t) * (s.nb + 1));
-    const int64_t mb = G.base + 1;
-    rb.binmap = (uint8_t *)workspace(ctx, "ring.binmap", (size_t)cdiv(mb, 16) * 16);
-    uint32_t *rowcnt = (uint32_t *)workspace(ctx, "ring.rowcnt", sizeof(uint32_t) * nrow);
-    uint32_t *rowoff = (uint32_t *)workspace(ctx, "ring.rowoff", sizeof(uint32_t) * nrow);
+    rb.lists = (short2 *)workspace(ctx, "ring.lists", sizeof(short2) * 3 * ncell);
+    rb.counts = (int32_t *)workspace(ctx, "ring.counts", sizeof(int32_t) * NFAM * s.nb);
+    rb.ring_off = (int64_t *)workspace(ctx, "ring.off", sizeof(int64_t) * NFAM * (s.nb + 1));
+    const int64_t mb = cdiv(G.base + 1, 16) * 16;
+    uint8_t *maps = (uint8_t *)workspace(ctx, "ring.maps", (size_t)2 * mb);
+    uint32_t *rowcnt = (uint32_t *)workspace(ctx, "ring.rowcnt", sizeof(uint32_t) * NFAM * nrow);
+    uint32_t *rowoff = (uint32_t *)workspace(ctx, "ring.rowoff", sizeof(uint32_t) * NFAM * nrow);
     double *rowlen = (double *)workspace(ctx, "ring.rowlen", sizeof(double) * nrow);
-    uint32_t *bsum = (uint32_t *)workspace(ctx, "ring.bsum", sizeof(uint32_t) * (cdiv(nrow, 4096) + 1));
-    if (!rb.lists || !rb.counts || !rb.ring_off || !rb.binmap || !rowcnt || !rowoff || !rowlen || !bsum)
+    uint32_t *bsum = (uint32_t *)workspace(ctx, "ring.bsum", sizeof(uint32_t) * (cdiv(NFAM * nrow, 4096) + 1));
+    if (!rb.lists || !rb.counts || !rb.ring_off || !maps || !rowcnt || !rowoff || !rowlen || !bsum)
         return fail(ctx, ABS_ERR_OOM, "ring table workspace");
+    rb.mapF = maps;
+    rb.mapA = maps + mb;
     StageTimer timer(ctx, "ring_lists");
     cudaStream_t st = ctx->stream;
-    cudaMemsetAsync(rb.binmap, 0, (size_t)cdiv(mb, 16) * 16, st);
+    cudaMemsetAsync(maps, 0, (size_t)2 * mb, st);
     const int nbk = (int)cdiv(nrow * 32, 256);
     k_ring_rows<<<nbk, 256, 0, st>>>(G, s.d_q, d_mask, rowcnt, rowlen);
-    scan_u32(st, rowcnt, nrow, rowoff, bsum);
-    k_ring_write<<<nbk, 256, 0, st>>>(G, s.d_q, d_mask, rowoff, rb.lists, rb.binmap);
-    k_ring_finish<<<(int)cdiv((int64_t)s.nb * 32, 256), 256, 0, st>>>(G, s.du, rowoff, rowcnt, rowlen,
-                                                                       rb.ring_off, rb.counts, d_ellbar);
+    scan_u32(st, rowcnt, NFAM * nrow, rowoff, bsum);
+    k_ring_write<<<nbk, 256, 0, st>>>(G, s.d_q, d_mask, rowoff, rb.lists, rb.mapF, rb.mapA);
+    k_ring_finish<<<(int)cdiv((int64_t)NFAM * s.nb * 32, 256), 256, 0, st>>>(
+        G, s.du, rowoff, rowcnt, rowlen, rb.ring_off, rb.counts, d_ellbar);
     return check_launch(ctx, "ring lists");
+}
+
+template <bool SMEM>
+void launch_pairs(abs_ctx *ctx, const CountGeom &G, int blocks, int threads, size_t smem, const int4 *items,
+                  const int *n_items, int *next, const Fams &fam, const uint8_t *map,
+                  unsigned long long *const *tab) {
+    cudaFuncSetAttribute(k_count_pairs<SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_count_pairs<SMEM><<<blocks, threads, smem, ctx->stream>>>(G, items, n_items, next, fam, map, tab[0], tab[1],
+                                                               tab[2], tab[3], tab[4]);
 }
 
 }  // namespace
@@ -407,53 +507,64 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     if (st != ABS_OK) return st;
     if (n_trip == 0 || !d_count) return ABS_OK;
     const CountGeom G = cgeom(s);
-    // threads per CTA: lane-private histograms must fit next to the map
     const int hs = s.nb + 1;
     const int64_t map_bytes = cdiv(G.base + 1, 16) * 16;
     const size_t hist_budget = 96 * 1024;
     int nwarps = (int)std::min<size_t>(CT / 32, hist_budget / ((size_t)hs * 32 * 4));
     if (nwarps < 1) return fail(ctx, ABS_ERR_UNSUPPORTED, "too many rings for the count kernel");
-    const int64_t cta_bytes = map_bytes + (int64_t)nwarps * hs * 32 * 4 + STAGE * 4;
-    const bool map_smem = cta_bytes <= 220 * 1024;
-    const int per_sm = map_smem ? std::max<int>(1, (int)std::min<int64_t>(4, (226 * 1024) / (cta_bytes + 1024))) : 2;
     const int threads = nwarps * 32;
     const int chunk = threads * G1;
-    const size_t smem = (size_t)nwarps * hs * 32 * 4 + STAGE * 4 + (map_smem ? map_bytes : 0);
-    // work items: one per (row, chunk of the upper half of ring i)
+    const int64_t cta_bytes = map_bytes + (int64_t)nwarps * hs * 32 * 4 + INNER * 4;
+    const bool map_smem = cta_bytes <= 220 * 1024;
+    const int per_sm = map_smem ? std::max<int>(1, (int)std::min<int64_t>(4, (226 * 1024) / (cta_bytes + 1024))) : 2;
+    const size_t smem = (size_t)nwarps * hs * 32 * 4 + INNER * 4 + (map_smem ? map_bytes : 0);
     int64_t max_ring = 0;
     for (int m = 0; m < s.nb; ++m) max_ring = std::max<int64_t>(max_ring, s.lat[m]);
-    const int64_t max_rows = std::min<int64_t>(n_trip, (int64_t)s.nb * (s.nb + 1) / 2);
+    const int64_t npair = (int64_t)s.nb * (s.nb + 1) / 2;
     const int64_t mr = std::max<int64_t>(max_ring, 1);
-    const int cap = (int)std::min<int64_t>(max_rows * cdiv(mr, chunk) * cdiv(mr, INNER), 1 << 26);
-    int4 *items = (int4 *)workspace(ctx, "count.items", sizeof(int4) * cap);
-    int *n_items = (int *)workspace(ctx, "count.n_items", sizeof(int) * 2);   // [count, next]
-    const size_t td_bytes = sizeof(unsigned long long) * (size_t)s.nb * s.nb * s.nb;
-    unsigned long long *Td = (unsigned long long *)workspace(ctx, "count.table", td_bytes);
-    if (!items || !n_items || !Td) return fail(ctx, ABS_ERR_OOM, "count workspace");
+    const int cap = (int)std::min<int64_t>(4 * npair * cdiv(mr, chunk) * cdiv(mr, INNER), 1 << 26);
+    int4 *items0 = (int4 *)workspace(ctx, "count.items0", sizeof(int4) * cap);
+    int4 *items1 = (int4 *)workspace(ctx, "count.items1", sizeof(int4) * cap);
+    int *ctl = (int *)workspace(ctx, "count.ctl", sizeof(int) * 8);
+    const size_t tb = sizeof(unsigned long long) * (size_t)s.nb * s.nb * s.nb;
+    unsigned long long *tabs = (unsigned long long *)workspace(ctx, "count.tables", 4 * tb);
+    // full-annulus counts: a property of the ring geometry, kept per configuration
+    Setup &ms = const_cast<Setup &>(s);
+    if (!ms.d_full_counts) {
+        if (cudaMalloc(&ms.d_full_counts, tb) != cudaSuccess) {
+            cudaGetLastError();
+            ms.d_full_counts = nullptr;
+        }
+    }
+    if (!items0 || !items1 || !ctl || !tabs || !ms.d_full_counts) return fail(ctx, ABS_ERR_OOM, "count workspace");
+    const int need_full = ms.full_counts_ready ? 0 : 1;
+    unsigned long long *tab[NJOB] = {tabs, tabs + tb / 8, tabs + 2 * (tb / 8), tabs + 3 * (tb / 8), ms.d_full_counts};
     cudaStream_t stm = ctx->stream;
     {
         StageTimer timer(ctx, "count_items");
-        cudaMemsetAsync(Td, 0, td_bytes, stm);
-        cudaMemsetAsync(n_items, 0, sizeof(int) * 2, stm);
-        k_count_items<<<1, 1024, 0, stm>>>(s.nb, n_trip, d_ijk, rb.counts, chunk, items, cap, n_items,
+        cudaMemsetAsync(tabs, 0, 4 * tb, stm);
+        if (need_full) cudaMemsetAsync(ms.d_full_counts, 0, tb, stm);
+        k_count_items<<<1, 1024, 0, stm>>>(s.nb, rb.counts, chunk, need_full, items0, items1, cap, ctl,
                                            ctx->d_err);
     }
+    Fams fam{rb.lists, rb.ring_off, rb.counts};
     {
-    StageTimer timer(ctx, "count_pairs");
-    const int blocks = ctx->sm_count * per_sm;
-    if (map_smem) {
-        cudaFuncSetAttribute(k_count_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_count_pairs<true><<<blocks, threads, smem, stm>>>(G, items, n_items, rb.lists, rb.ring_off,
-                                                            rb.counts, rb.binmap, Td, n_items + 1);
-    } else {
-        cudaFuncSetAttribute(k_count_pairs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_count_pairs<false><<<blocks, threads, smem, stm>>>(G, items, n_items, rb.lists, rb.ring_off,
-                                                             rb.counts, rb.binmap, Td, n_items + 1);
+        StageTimer timer(ctx, "count_pairs");
+        const int blocks = ctx->sm_count * per_sm;
+        if (map_smem) {
+            launch_pairs<true>(ctx, G, blocks, threads, smem, items0, ctl + 0, ctl + 2, fam, rb.mapF, tab);
+            launch_pairs<true>(ctx, G, blocks, threads, smem, items1, ctl + 1, ctl + 3, fam, rb.mapA, tab);
+        } else {
+            launch_pairs<false>(ctx, G, blocks, threads, smem, items0, ctl + 0, ctl + 2, fam, rb.mapF, tab);
+            launch_pairs<false>(ctx, G, blocks, threads, smem, items1, ctl + 1, ctl + 3, fam, rb.mapA, tab);
+        }
     }
-    }
+    ms.full_counts_ready = true;
     {
         StageTimer t2(ctx, "count_gather");
-        k_count_gather<<<(int)cdiv(n_trip, 256), 256, 0, stm>>>(s.nb, n_trip, d_ijk, Td, d_count);
+        k_count_gather<<<(int)cdiv(n_trip, 256), 256, 0, stm>>>(s.nb, n_trip, d_ijk, ctl, tab[JOB_DIRECT],
+                                                                tab[JOB_FULL], tab[JOB_E1], tab[JOB_E2],
+                                                                tab[JOB_E3], d_count);
     }
     return check_launch(ctx, "counts");
 }

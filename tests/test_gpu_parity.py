@@ -395,3 +395,32 @@ def test_split_bf16_odd_shapes(ctx):
         big = ok & (np.abs(est.B) >= 1e-3 * np.nanmax(np.abs(est.B)))
         rel = np.abs(Bg[big] - est.B[big]) / np.abs(est.B[big])
         assert rel.max() <= tol, f"precision {prec}: relative error {rel.max():.3e}"
+
+
+# ----------------------------------------------------------------- counts with holes in the coverage
+
+
+@pytest.mark.parametrize("n_vis", [150, 800, 2000, 3500, 5000])
+def test_counts_with_holes(ctx, n_vis):
+    # NGP gridding of few visibilities leaves holes inside the rings: the count
+    # takes either the hole (inclusion-exclusion) route or the direct one
+    # depending on the fill fraction; both must be exact.  The same context is
+    # reused across fill fractions, so the cached full-annulus counts are reused.
+    inp = inputs(0)
+    wl = inp.wl
+    uv, vis = inp.uv[:n_vis], inp.vis[:n_vis]
+    cfg = absmod.Config.from_workload(wl, kernel=absmod.ABS_KERNEL_NGP)
+    est = oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, uv, vis, kernel="ngp")
+    q = est.q
+    r2 = _r2(wl.n_grid)
+    half = wl.n_grid // 2 - 1
+    k = np.arange(wl.n_grid)
+    k = np.where(k > wl.n_grid // 2, k - wl.n_grid, k)
+    gy, gx = np.meshgrid(k, k, indexing="ij")
+    annulus = (r2 >= q[0]) & (r2 < q[-1]) & (np.abs(gx) <= half) & (np.abs(gy) <= half)
+    holes = int((annulus & (est.filled == 0)).sum())
+    assert holes > 0
+    B, T, E, ijk = absmod.estimate(cfg, to_dev(uv), to_dev(synth.vis_as_float2(vis)), ctx)
+    ctx.sync()
+    assert np.array_equal(T.cpu().numpy(), est.T)
+    assert np.allclose(E.cpu().numpy(), est.ellbar, rtol=1e-12, equal_nan=True)
