@@ -173,6 +173,34 @@ abs_status abs_estimate_host(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis,
                              int32_t n_trip, const int32_t *h_ijk, double *h_B,
                              int64_t *h_count, double *h_ellbar);
 
+/* Triple sums of the FP32 path that allocate nothing.
+ *
+ * Some callers cannot allocate device memory at the point where they need the
+ * sums: code running inside CUDA stream capture (cudaMalloc is not allowed
+ * there), host code of a framework whose device allocator is the only one
+ * permitted to call cudaMalloc, or latency-critical loops that must never hit
+ * the allocator.  This entry point computes exactly what abs_triple computes
+ * for d_sum (cfg->precision is ignored; the FP32 form is used) without a
+ * context and without any allocation: its per-split partial sums live in one
+ * fixed device array of ABS_STATIC_SCRATCH_BYTES inside the library, which
+ * every GPU that loads libabs holds until the process exits.
+ *
+ * d_fields [n_bins][N][N] float32 and d_ijk [n_trip][3] int32 (canonical
+ * order, as for abs_triple) are inputs, d_sum [n_trip] float64 the output; all
+ * on the current CUDA device; work is enqueued on cuda_stream (a
+ * cudaStream_t, NULL = legacy default stream).  n_trip above
+ * ABS_STATIC_SCRATCH_BYTES / 8 is rejected with ABS_ERR_INVALID_ARG (the
+ * scratch holds at least one partial per triplet; larger problems use fewer
+ * pixel splits).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents: calls whose work overlaps on the GPU (different
+ * streams, or host threads) race on it and give wrong sums, so serialise them.
+ * The paper has no counterpart to this entry point; it is a deployment aid. */
+#define ABS_STATIC_SCRATCH_BYTES (8u << 20)
+abs_status abs_triple_sums_static(const abs_config *cfg, const float *d_fields, int32_t n_trip,
+                                  const int32_t *d_ijk, double *d_sum, void *cuda_stream);
+
 /* Stage profiler (tracing).  When on, every kernel launch of the context is
  * bracketed by CUDA events on the context's stream and its device time is
  * accumulated under a stage name ("grid", "fft_rows", "count_pairs", ...).

@@ -76,6 +76,7 @@ def load(path: str | None = None):
         "abs_estimate": ([P, C, i64, P, P, i32, P, P, P, P], ctypes.c_int),
         "abs_estimate_many": ([P, C, i64, P, i32, P, i32, P, P, P, P], ctypes.c_int),
         "abs_estimate_host": ([P, C, i64, P, i32, P, i32, P, P, P, P], ctypes.c_int),
+        "abs_triple_sums_static": ([C, P, i32, P, P, P], ctypes.c_int),
         "abs_profile": ([P, i32], ctypes.c_int),
         "abs_profile_read": ([P, i32, P, P], ctypes.c_int),
     }
@@ -244,6 +245,21 @@ class Context:
         n_real = vis.shape[0] if vis.ndim == 3 else 1
         _check(load().abs_estimate_host(self.h, cfg.ref(), uv.shape[0], hp(uv), n_real, hp(vis), int(n_trip),
                                         hp(ijk), hp(B), hp(counts), hp(ellbar)), self.h, "abs_estimate_host")
+
+
+def abs_triple_sums_static(cfg: Config, fields, ijk, sums, stream=None):
+    """FP32 triple sums without a context or any device allocation (see include/abs.h).
+
+    fields, ijk, sums: torch CUDA tensors on the current device; the work is
+    enqueued on `stream` (default: torch's current stream).  Calls share one
+    fixed scratch array inside the library, so calls that overlap on the GPU
+    must be serialised by the caller."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = load().abs_triple_sums_static(cfg.ref(), _ptr(fields), int(ijk.shape[0]), _ptr(ijk), _ptr(sums),
+                                       ctypes.c_void_p(stream.cuda_stream))
+    _check(st, None, "abs_triple_sums_static")
 
 
 def estimate(cfg: Config, uv, vis, ctx: Context | None = None):

@@ -15,6 +15,8 @@
 // the result does not depend on scheduling) and applies N^-2 in FP64.
 //
 // B_ijk = S_ijk / (A T_ijk) is then formed in FP64 (NaN for T = 0).
+#include <mutex>
+
 #include "abs_internal.cuh"
 
 namespace absk {
@@ -218,6 +220,28 @@ abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_field
     return check_launch(ctx, "triple sums");
 }
 
+// ------------------------------------------------------------------ allocation-free variant
+// Partial sums of abs_triple_sums_static: one fixed array per device, looked up
+// once per device with that device current.
+static __device__ __align__(256) double g_static_partial[ABS_STATIC_SCRATCH_BYTES / sizeof(double)];
+static double *g_static_ptr[64];
+static std::mutex g_static_mu;
+
+static abs_status static_scratch(int dev, double **out) {
+    if (dev < 0 || dev >= 64) return ABS_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_partial) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return ABS_ERR_CUDA;
+        }
+        g_static_ptr[dev] = (double *)p;
+    }
+    *out = g_static_ptr[dev];
+    return ABS_OK;
+}
+
 abs_status launch_normalise(abs_ctx *ctx, const Setup &s, int32_t n_trip, const double *d_sum,
                             const int64_t *d_count, double *d_B) {
     if (n_trip == 0) return ABS_OK;
@@ -227,3 +251,55 @@ abs_status launch_normalise(abs_ctx *ctx, const Setup &s, int32_t n_trip, const 
 }
 
 }  // namespace absk
+
+extern "C" abs_status abs_triple_sums_static(const abs_config *cfg, const float *d_fields, int32_t n_trip,
+                                             const int32_t *d_ijk, double *d_sum, void *cuda_stream) {
+    using namespace absk;
+    int64_t q[ABS_MAX_BINS + 1];
+    int Rm[ABS_MAX_BINS];
+    int R = 0, N = 0;
+    const char *msg = "";
+    const abs_status st = derive_grid(cfg, q, Rm, &R, &N, &msg);
+    if (st != ABS_OK) return st;
+    const int64_t cap = ABS_STATIC_SCRATCH_BYTES / sizeof(double);
+    if (n_trip < 0 || n_trip > cap) return ABS_ERR_INVALID_ARG;
+    if (n_trip == 0) return ABS_OK;
+    if (!d_fields || !d_ijk || !d_sum) return ABS_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return ABS_ERR_CUDA;
+    }
+    double *partial = nullptr;
+    const abs_status ss = static_scratch(dev, &partial);
+    if (ss != ABS_OK) return ss;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    // same tiling as launch_triple_sums, with the number of pixel splits capped
+    // so that [split][triplet] fits the fixed array
+    TripleGeom G;
+    G.nb = cfg->n_bins;
+    G.P = (int64_t)N * N;
+    G.n_trip = n_trip;
+    const int groups = (int)cdiv(n_trip, TG);
+    int64_t target = std::max<int64_t>(1, cdiv(2 * sms, groups));
+    target = std::min<int64_t>(target, std::max<int64_t>(1, cap / n_trip));
+    int64_t per = cdiv(cdiv(G.P, target), 32) * 32;
+    const int64_t pc_max = std::max<int64_t>(32, ((96 * 1024) / (4 * (int64_t)G.nb)) / 32 * 32);
+    const int PC = (int)std::min<int64_t>(per, pc_max);
+    G.PC = PC;
+    G.vec4 = (G.P % 4 == 0) && (((uintptr_t)d_fields & 15) == 0);
+    G.per_split = cdiv(per, PC) * PC;
+    int64_t nsplit = cdiv(G.P, G.per_split);
+    while (nsplit * n_trip > cap) {   // rounding can leave one split too many
+        per += PC;
+        G.per_split = cdiv(per, PC) * PC;
+        nsplit = cdiv(G.P, G.per_split);
+    }
+    const size_t smem = (size_t)G.nb * PC * 4 + TG * 8 + (2 * TG + 1) * 4 + TG;
+    cudaFuncSetAttribute(k_triple_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_triple_fp32<<<dim3((unsigned)nsplit, groups), TT, smem, stream>>>(G, d_fields, d_ijk, partial);
+    k_triple_reduce<<<(int)cdiv(n_trip, 32), 256, 0, stream>>>(n_trip, (int)nsplit,
+                                                               1.0 / ((double)N * (double)N), partial, d_sum);
+    return cudaGetLastError() == cudaSuccess ? ABS_OK : ABS_ERR_CUDA;
+}
