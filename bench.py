@@ -40,7 +40,7 @@ METRIC = "ABS estimates/s (V->binned B)"
 UNIT = "estimates/s"
 
 # kernels launched per stage-timer entry (the profiler brackets stages); the
-# gridding plan runs 6 kernels plus 5 per radix pass (8-bit digits of the cell key)
+# gridding plan runs 3 kernels plus 5 per radix pass (8-bit digits of the uv tile id)
 KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "ring_lists": 6,
                      "count_items": 1, "count_pairs": 1, "count_gather": 1, "ellbar": 6,
                      "fft_rows": 1, "fft_cols": 1, "triple_fp32": 1, "triple_reduce": 1,
@@ -49,9 +49,8 @@ KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "ring_lists"
 
 def plan_kernels(n_grid, radius):
     tiles = -(-(n_grid - 1 + 2 * radius) // 16)
-    nkeys = tiles * tiles * 256
-    passes = -(-int(nkeys).bit_length() // 8)
-    return 6 + 5 * passes
+    passes = -(-int(tiles * tiles).bit_length() // 8)
+    return 3 + 5 * passes
 
 
 def load_peaks():

@@ -5,19 +5,16 @@
 // V*.  The mirror is applied after accumulation (G(g) + conj G(-g)), which is
 // the same sum.
 //
-// Plan (per baseline set): key every visibility by (16x16-cell uv tile, cell
-// within the tile), counting-sort by key, and cut every tile's run into work
-// units of at most UMAX visibilities.
+// Plan (per baseline set): key every visibility by its 16x16-cell uv tile,
+// stable-sort by tile (LSD radix), cut every tile's run into work units of at
+// most UMAX visibilities, sort each unit by cell (stable) and form the 1-D
+// Gaussian weights of every visibility once.
 //
-// Accumulation (per realisation): a persistent kernel takes one unit per CTA
-// pass.  Each warp has 4 slots of 8 lanes; a slot walks a contiguous run of
-// the sorted visibilities, lane dx of the slot owning footprint column dx and
-// keeping the 2r+1 cells of that column in registers (Kahan-compensated FP32)
-// for as long as consecutive visibilities share a nearest cell.  When the cell
-// changes the run is added into the warp's shared-memory halo tile
-// (compensated FP32); at the end of the unit the warps' tiles are summed in
-// FP64 and added to an FP64 grid with one atomic per touched cell.  A final
-// pass applies the Hermitian mirror and writes the FP32 outputs.
+// Accumulation (per realisation): one CTA per unit stages the unit in shared
+// memory and cuts it into runs of visibilities that share a cell; a warp sums
+// the (2r+1)^2 footprint cells of a run (lane per footprint cell, compensated
+// FP32, fixed order) and adds them to an FP64 grid.  A final pass applies the
+// Hermitian mirror and writes the FP32 outputs.
 //
 // Weights: w = exp(-(dx - fx)^2 s) exp(-(dy - fy)^2 s), s = 1/(2 sigma^2),
 // with the fractional offset f = u/dU - c carried as a float pair (the exact
@@ -29,11 +26,7 @@ namespace absk {
 namespace {
 
 constexpr int TS = 16;                       // tile side in cells
-constexpr int SLOTS = 4;                     // slots per warp, 8 lanes each
-constexpr int GW = 4;                        // warps per CTA
-constexpr int UMAX = 1024;                   // visibilities per work unit
-constexpr int HS_MAX = TS + 2 * ABS_MAX_RADIUS;
-constexpr int HC = HS_MAX * HS_MAX;          // halo-tile cells
+constexpr int UMAX = 512;                    // visibilities per work unit
 constexpr int FWMAX = 2 * ABS_MAX_RADIUS + 1;
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -100,16 +93,13 @@ __global__ void k_plan_keys(GridGeom G, int64_t n_vis, const float2 *__restrict_
                 const int cx = (int)floorf(__fadd_rn(qx, 0.5f));
                 const int cy = (int)floorf(__fadd_rn(qy, 0.5f));
                 const int kx = cx + G.off, ky = cy + G.off;
-                if (kx >= 0 && kx < G.ks && ky >= 0 && ky < G.ks) {
-                    const int tx = kx / TS, ty = ky / TS;
-                    key = (uint32_t)((ty * G.tt + tx) * (TS * TS) + (ky - ty * TS) * TS +
-                                     (kx - tx * TS));
-                }
+                if (kx >= 0 && kx < G.ks && ky >= 0 && ky < G.ks)
+                    key = (uint32_t)((ky / TS) * G.tt + kx / TS);   // 16x16-cell uv tile
             }
         }
         keys[i] = key;
-        // one atomic per distinct key in the warp (consecutive visibilities of a
-        // baseline usually share a cell)
+        // one atomic per distinct tile in the warp (consecutive visibilities of a
+        // baseline usually share a tile)
         const unsigned active = __activemask();
         const unsigned peers = __match_any_sync(active, key);
         const int lane = threadIdx.x & 31;
@@ -252,221 +242,300 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t *__restric
     }
 }
 
-// Fractional offset f = u/dU - c of every sorted visibility from its nearest
-// cell, as a float pair (hi = fl(u/dU) - c exactly, lo = the exact division
-// residual over dU): (fx_hi, fx_lo, fy_hi, fy_lo).
-__global__ void k_plan_offsets(GridGeom G, int64_t n_valid_max, const uint32_t *__restrict__ n_valid_p,
-                               const float2 *__restrict__ uv, const uint32_t *__restrict__ s_idx,
-                               const uint32_t *__restrict__ s_key, float4 *__restrict__ s_f) {
-    const uint32_t nv = *n_valid_p;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv && i < n_valid_max;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 p = uv[s_idx[i]];
-        const uint32_t key = s_key[i];
-        const int tile = (int)(key >> 8), tx = tile % G.tt, ty = tile / G.tt;
-        const int cx = tx * TS + (int)(key & (TS - 1)) - G.off;
-        const int cy = ty * TS + (int)((key >> 4) & (TS - 1)) - G.off;
-        const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
-        s_f[i] = make_float4(__fsub_rn(qx, (float)cx), __fdiv_rn(fmaf(-qx, G.du, p.x), G.du),
-                             __fsub_rn(qy, (float)cy), __fdiv_rn(fmaf(-qy, G.du, p.y), G.du));
+// Per work unit (<= UMAX visibilities of one uv tile, in input order after the
+// stable tile sort): stable sort by cell within the tile, and the 2 x (2r+1)
+// one-dimensional weights of every visibility, w(d) = exp(-s (d - f)^2) with
+// f = u/dU - c carried as a float pair (the exact division residual).  Writes
+// s_key = tile << 8 | cell in tile, s_idx and s_w [16] = (wx[0..6], -, wy[0..6], -)
+// in cell order.  One CTA per unit, 128 threads.
+constexpr int PT = 128;
+constexpr int WREC = 16;   // floats per weight record
+
+__global__ void __launch_bounds__(PT) k_plan_units(GridGeom G, const int4 *__restrict__ units,
+                                                   const int *__restrict__ n_units,
+                                                   const float2 *__restrict__ uv,
+                                                   const uint32_t *__restrict__ t_idx,
+                                                   uint32_t *__restrict__ s_key,
+                                                   uint32_t *__restrict__ s_idx,
+                                                   float4 *__restrict__ s_w) {
+    __shared__ float4 wst[UMAX][WREC / 4];
+    __shared__ uint32_t ist[UMAX];
+    __shared__ uint8_t cst[UMAX];
+    __shared__ uint32_t cnt[256], base[256];
+    __shared__ uint32_t wcnt[PT / 32][256], wpre[PT / 32][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = G.r, fw = 2 * r + 1;
+    const int nu = *n_units;
+    for (int u = blockIdx.x; u < nu; u += gridDim.x) {
+        const int4 U = units[u];
+        const int total = U.z - U.y;
+        const uint32_t tile = (uint32_t)U.x;
+        for (int c = threadIdx.x; c < 256; c += PT) cnt[c] = 0;
+        __syncthreads();
+        for (int t = threadIdx.x; t < total; t += PT) {
+            const uint32_t idx = t_idx[U.y + t];
+            const float2 p = uv[idx];
+            const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
+            const int cx = (int)floorf(__fadd_rn(qx, 0.5f)), cy = (int)floorf(__fadd_rn(qy, 0.5f));
+            const int kx = cx + G.off, ky = cy + G.off;
+            const int lc = (ky % TS) * TS + kx % TS;
+            const float fxh = __fsub_rn(qx, (float)cx), fyh = __fsub_rn(qy, (float)cy);
+            const float fxl = __fdiv_rn(fmaf(-qx, G.du, p.x), G.du);
+            const float fyl = __fdiv_rn(fmaf(-qy, G.du, p.y), G.du);
+            float w[WREC];
+#pragma unroll
+            for (int k = 0; k < WREC; ++k) w[k] = 0.f;
+#pragma unroll
+            for (int k = 0; k < FWMAX; ++k) {
+                if (k < fw) {
+                    const float d = (float)(k - r);
+                    w[k] = G.kernel == ABS_KERNEL_GAUSS ? wexp(d, fxh, fxl, G.s_hi, G.s_lo) : 1.f;
+                    w[8 + k] = G.kernel == ABS_KERNEL_GAUSS ? wexp(d, fyh, fyl, G.s_hi, G.s_lo) : 1.f;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < WREC / 4; ++k) wst[t][k] = make_float4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+            ist[t] = idx;
+            cst[t] = (uint8_t)lc;
+            atomicAdd(&cnt[lc], 1u);
+        }
+        __syncthreads();
+        if (warp == 0) {   // exclusive scan of the 256 cell counts
+            uint32_t v[8], run = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                v[k] = cnt[lane * 8 + k];
+                run += v[k];
+            }
+            uint32_t incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            uint32_t b0 = incl - run;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                base[lane * 8 + k] = b0;
+                b0 += v[k];
+            }
+        }
+        __syncthreads();
+        // stable placement: items in input order, rounds of PT
+        for (int r0 = 0; r0 < total; r0 += PT) {
+            const int t = r0 + threadIdx.x;
+            const bool on = t < total;
+            const uint32_t c = on ? cst[t] : 256u + lane;
+            const unsigned peers = __match_any_sync(FULL, c);
+            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+            for (int w = 0; w < PT / 32; ++w) wcnt[w][threadIdx.x] = 0;   // PT >= ... 256 cells: loop below
+            for (int cc = threadIdx.x + PT; cc < 256; cc += PT)
+                for (int w = 0; w < PT / 32; ++w) wcnt[w][cc] = 0;
+            __syncthreads();
+            if (on && rank == 0) wcnt[warp][c] = __popc(peers);
+            __syncthreads();
+            for (int cc = threadIdx.x; cc < 256; cc += PT) {
+                uint32_t run = base[cc];
+                for (int w = 0; w < PT / 32; ++w) {
+                    wpre[w][cc] = run;
+                    run += wcnt[w][cc];
+                }
+                base[cc] = run;
+            }
+            __syncthreads();
+            if (on) {
+                const int pos = U.y + (int)(wpre[warp][c] + rank);
+                s_key[pos] = tile << 8 | c;
+                s_idx[pos] = ist[t];
+#pragma unroll
+                for (int k = 0; k < WREC / 4; ++k) s_w[(size_t)pos * (WREC / 4) + k] = wst[t][k];
+            }
+            __syncthreads();
+        }
     }
 }
 
 // One block: cut every tile's run of sorted visibilities into units of <= UMAX.
-__global__ void __launch_bounds__(1024) k_units(const uint32_t *__restrict__ offs,
-                                                const uint32_t *__restrict__ hist, int64_t nkeys,
-                                                int ntiles, int4 *__restrict__ units,
-                                                int *__restrict__ n_units, int cap,
-                                                uint32_t *__restrict__ n_valid_out) {
+__global__ void __launch_bounds__(1024) k_units(const uint32_t *__restrict__ hist, int ntiles,
+                                                int4 *__restrict__ units, int *__restrict__ n_units,
+                                                int cap, uint32_t *__restrict__ n_valid_out) {
     __shared__ uint32_t sh[32];
-    const uint32_t n_valid = offs[nkeys - 1] + hist[nkeys - 1];
-    if (threadIdx.x == 0) *n_valid_out = n_valid;
-    uint32_t carry = 0;
+    uint32_t carry = 0, base = 0;
     for (int b = 0; b < ntiles; b += 1024) {
         const int t = b + threadIdx.x;
-        uint32_t start = 0, end = 0, nu = 0;
-        if (t < ntiles) {
-            start = offs[(int64_t)t * (TS * TS)];
-            end = t + 1 < ntiles ? offs[(int64_t)(t + 1) * (TS * TS)] : n_valid;
-            nu = (end - start + UMAX - 1) / UMAX;
-        }
+        const uint32_t c = t < ntiles ? hist[t] : 0u;
+        uint32_t ctot;
+        const uint32_t start = base + block_exclusive_scan(c, sh, ctot);   // tile offset in sorted order
+        const uint32_t nu = (c + UMAX - 1) / UMAX;
         uint32_t total;
         const uint32_t pre = block_exclusive_scan(nu, sh, total);
         for (uint32_t k = 0; k < nu; ++k) {
             const uint32_t u = carry + pre + k;
             if ((int)u < cap) {
                 const uint32_t s0 = start + k * UMAX;
-                units[u] = make_int4(t, (int)s0, (int)min(end, s0 + UMAX), 0);
+                units[u] = make_int4(t, (int)s0, (int)min(start + c, s0 + UMAX), 0);
             }
         }
         carry += total;
+        base += ctot;
     }
-    if (threadIdx.x == 0) *n_units = min((int)carry, cap);
+    if (threadIdx.x == 0) {
+        *n_units = min((int)carry, cap);
+        *n_valid_out = base;
+    }
 }
 
 // ------------------------------------------------------------------ accumulation
 
-// Per-lane accumulators of one slot lane: footprint column dx, rows dy, for
-// (re, im, w).  blk: plain FP32 sums of up to FOLD visibilities; s, c: Kahan
-// sum and compensation of the folded blocks.
-constexpr int FOLD = 4;
-struct SlotAcc {
-    float blk[3][FWMAX], s[3][FWMAX], c[3][FWMAX];
-};
+// ------------------------------------------------------------------ accumulation
+// One CTA per work unit (<= UMAX visibilities of one 16x16-cell tile, sorted by
+// cell).  The unit is staged in shared memory (1-D weights from the plan, the
+// visibilities gathered) and cut into tasks: runs of at most CHUNK
+// visibilities that share a cell.  A warp takes a task; lane k owns footprint
+// cells k and k + 32 of the (2r+1)^2 around the run's cell and sums
+// w = wx[dx] wy[dy] times V over the run (plain FP32 blocks of 8 folded into
+// Kahan sums, fixed order), then adds its cells to the FP64 grid.  No shared
+// accumulators: runs never wait on one another, whether the tile is dense
+// (long runs) or sparse (short ones).
+constexpr int WST = 17;          // floats per staged weight record (odd: spreads banks)
+constexpr int GT = 256;          // threads per gridding CTA
+constexpr int GFOLD = 8;
+constexpr int CHUNK = 64;        // visibilities per task at most
+constexpr int MAXTASK = UMAX + 256;
+constexpr size_t GRID_SMEM = UMAX * (sizeof(float) * WST + sizeof(float2) + 1) + sizeof(uint32_t) * 257 +
+                             sizeof(int2) * MAXTASK;
 
-__device__ __forceinline__ void acc_zero(SlotAcc &A) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int q = 0; q < FWMAX; ++q) A.blk[k][q] = A.s[k][q] = A.c[k][q] = 0.f;
-}
-
-__device__ __forceinline__ void acc_fold(SlotAcc &A) {
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int q = 0; q < FWMAX; ++q) {
-            kahan_add(A.s[k][q], A.c[k][q], A.blk[k][q]);
-            A.blk[k][q] = 0.f;
-        }
-}
-
-__device__ __forceinline__ void slot_flush(float (*sm)[HC], SlotAcc &A, int hx0, int hy0, int HS,
-                                           int fw, uint8_t *shit) {
-    acc_fold(A);
-#pragma unroll
-    for (int dyi = 0; dyi < FWMAX; ++dyi) {
-        if (dyi < fw) {
-            const int ci = (hy0 + dyi) * HS + hx0;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                float ss = sm[2 * k][ci], cc = sm[2 * k + 1][ci];
-                kahan_add(ss, cc, A.s[k][dyi] - A.c[k][dyi]);
-                sm[2 * k][ci] = ss;
-                sm[2 * k + 1][ci] = cc;
-            }
-            shit[ci] = 1;
-        }
-    }
-}
-
-constexpr size_t GRID_SMEM = sizeof(float) * GW * 6 * HC + UMAX * (sizeof(float4) + sizeof(float2) + 1) + HC;
-
-__global__ void __launch_bounds__(GW * 32) k_grid(GridGeom G, const int4 *__restrict__ units,
-                                                  const int *__restrict__ n_units,
-                                                  const float4 *__restrict__ s_f,
-                                                  const uint32_t *__restrict__ s_idx,
-                                                  const uint32_t *__restrict__ s_key,
-                                                  const float2 *__restrict__ vis,
-                                                  double *__restrict__ acc_re,
-                                                  double *__restrict__ acc_im,
-                                                  double *__restrict__ acc_w,
-                                                  uint8_t *__restrict__ hit) {
+__global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict__ units,
+                                             const int *__restrict__ n_units,
+                                             const float4 *__restrict__ s_w,
+                                             const uint32_t *__restrict__ s_idx,
+                                             const uint32_t *__restrict__ s_key,
+                                             const float2 *__restrict__ vis,
+                                             double *__restrict__ acc_re,
+                                             double *__restrict__ acc_im,
+                                             double *__restrict__ acc_w,
+                                             uint8_t *__restrict__ hit) {
     extern __shared__ __align__(16) uint8_t dsm[];
-    float(*sm)[6][HC] = (float(*)[6][HC])dsm;                          // [GW][6][HC]
-    float4 *st_f = (float4 *)(dsm + sizeof(float) * GW * 6 * HC);      // [UMAX] offsets
-    float2 *st_v = (float2 *)(st_f + UMAX);                            // [UMAX] visibilities
-    uint8_t *st_c = (uint8_t *)(st_v + UMAX);                          // [UMAX] cell in tile
-    uint8_t *shit = st_c + UMAX;                                       // [HC] touched cells
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int slot = lane >> 3, l8 = lane & 7;
-    const int r = G.r, fw = 2 * r + 1, HS = TS + 2 * r;
-    const bool lane_on = l8 < fw;
-    const float d = (float)(l8 - r);
+    float *st_w = (float *)dsm;                                        // [UMAX][WST] 1-D weights
+    float2 *st_v = (float2 *)(st_w + UMAX * WST);                      // [UMAX] visibilities
+    int2 *task = (int2 *)(st_v + UMAX);                                // [MAXTASK] (first, end)
+    uint32_t *cstart = (uint32_t *)(task + MAXTASK);                   // [257] first item of each cell
+    uint8_t *st_c = (uint8_t *)(cstart + 257);                         // [UMAX] cell in tile
+    __shared__ int ntask_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = GT / 32;
+    const int r = G.r, fw = 2 * r + 1, nfp = fw * fw;
+    // this lane's two footprint cells
+    const int k1 = lane, k2 = lane + 32;
+    const bool on1 = k1 < nfp, on2 = k2 < nfp;
+    const int dx1 = on1 ? k1 % fw : 0, dy1 = on1 ? k1 / fw : 0;
+    const int dx2 = on2 ? k2 % fw : 0, dy2 = on2 ? k2 / fw : 0;
     const int nu = *n_units;
     for (int u = blockIdx.x; u < nu; u += gridDim.x) {
         const int4 U = units[u];
         const int total = U.z - U.y;
-        for (int i = threadIdx.x; i < GW * 6 * HC; i += blockDim.x) (&sm[0][0][0])[i] = 0.f;
-        for (int i = threadIdx.x; i < HC; i += blockDim.x) shit[i] = 0;
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {   // stage the unit
-            st_f[t] = s_f[U.y + t];
+        __syncthreads();   // previous unit done with the staging buffers
+        for (int e = threadIdx.x; e < total * (WREC / 4); e += GT) {
+            const int t = e >> 2, k = e & 3;
+            const float4 q = s_w[(size_t)(U.y + t) * (WREC / 4) + k];
+            float *d = st_w + t * WST + 4 * k;
+            d[0] = q.x;
+            d[1] = q.y;
+            d[2] = q.z;
+            d[3] = q.w;
+        }
+        for (int t = threadIdx.x; t < total; t += GT) {
             st_c[t] = (uint8_t)(s_key[U.y + t] & 255u);
             st_v[t] = vis[s_idx[U.y + t]];
         }
         __syncthreads();
+        for (int c = threadIdx.x; c <= 256; c += GT) {   // first item of each cell (unit is cell-sorted)
+            int lo = 0, hi = total;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((int)st_c[mid] < c) lo = mid + 1;
+                else hi = mid;
+            }
+            cstart[c] = (uint32_t)lo;
+        }
+        __syncthreads();
+        if (warp == 0) {   // tasks: every cell's run cut into chunks of <= CHUNK
+            uint32_t nt[8], run = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int c = lane * 8 + k;
+                const uint32_t n = cstart[c + 1] - cstart[c];
+                nt[k] = (n + CHUNK - 1) / CHUNK;
+                run += nt[k];
+            }
+            uint32_t incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            uint32_t pos = incl - run;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int c = lane * 8 + k;
+                const int j0 = (int)cstart[c], j1 = (int)cstart[c + 1];
+                for (uint32_t q = 0; q < nt[k]; ++q, ++pos) {
+                    const int a = j0 + (int)q * CHUNK;
+                    task[pos] = make_int2(a, min(j1, a + CHUNK));
+                }
+            }
+            if (lane == 31) ntask_s = (int)incl;
+        }
+        __syncthreads();
+        const int ntask = ntask_s;
         const int tile = U.x, tx = tile % G.tt, ty = tile / G.tt;
         const int gx0 = tx * TS - G.off, gy0 = ty * TS - G.off;
-        const int nslots = GW * SLOTS;
-        const int per = (total + nslots - 1) / nslots;
-        const int sid = warp * SLOTS + slot;
-        const int my0 = min(total, sid * per), my1 = min(total, (sid + 1) * per);
-        int trips = my1 - my0;
-        trips = max(trips, __shfl_xor_sync(FULL, trips, 8));
-        trips = max(trips, __shfl_xor_sync(FULL, trips, 16));
-        SlotAcc A;
-        acc_zero(A);
-        int run_c = -1, nblk = 0;
-        for (int it = 0; it < trips; ++it) {
-            const int idx = my0 + it;
-            const bool act = idx < my1;
-            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-            float2 v = make_float2(0.f, 0.f);
-            int cc = run_c;
-            if (act) {
-                f = st_f[idx];
-                v = st_v[idx];
-                cc = st_c[idx];
-            }
-            const bool need = act && run_c >= 0 && cc != run_c;
-            if (__any_sync(FULL, need)) {
-                for (int s = 0; s < SLOTS; ++s) {
-                    if (slot == s && need && lane_on)
-                        slot_flush(sm[warp], A, (run_c & (TS - 1)) + l8, run_c >> 4, HS, fw, shit);
-                    __syncwarp();
-                }
-                if (need) {
-                    acc_zero(A);
+        for (int tk = warp; tk < ntask; tk += nwarps) {
+            const int2 T = task[tk];
+            float b1[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f}, c1[3] = {0.f, 0.f, 0.f};
+            float b2[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f}, c2[3] = {0.f, 0.f, 0.f};
+            int nblk = 0;
+            for (int j = T.x; j < T.y; ++j) {
+                const float *w = st_w + j * WST;
+                const float2 v = st_v[j];
+                const float wa = w[dx1] * w[8 + dy1];
+                const float wb = w[dx2] * w[8 + dy2];
+                b1[0] = fmaf(wa, v.x, b1[0]);
+                b1[1] = fmaf(wa, v.y, b1[1]);
+                b1[2] += wa;
+                b2[0] = fmaf(wb, v.x, b2[0]);
+                b2[1] = fmaf(wb, v.y, b2[1]);
+                b2[2] += wb;
+                if (++nblk == GFOLD) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        kahan_add(s1[k], c1[k], b1[k]);
+                        kahan_add(s2[k], c2[k], b2[k]);
+                        b1[k] = b2[k] = 0.f;
+                    }
                     nblk = 0;
                 }
             }
-            if (act) run_c = cc;
-            float wx = 1.f, wyl = 1.f;
-            if (G.kernel == ABS_KERNEL_GAUSS) {
-                wx = wexp(d, f.x, f.y, G.s_hi, G.s_lo);
-                wyl = wexp(d, f.z, f.w, G.s_hi, G.s_lo);
-            }
-            const int sbase = slot * 8;
 #pragma unroll
-            for (int dyi = 0; dyi < FWMAX; ++dyi) {
-                const float wy = __shfl_sync(FULL, wyl, sbase + dyi);
-                if (dyi < fw && act && lane_on) {
-                    const float w = wx * wy;
-                    A.blk[0][dyi] = fmaf(w, v.x, A.blk[0][dyi]);
-                    A.blk[1][dyi] = fmaf(w, v.y, A.blk[1][dyi]);
-                    A.blk[2][dyi] += w;
-                }
+            for (int k = 0; k < 3; ++k) {
+                kahan_add(s1[k], c1[k], b1[k]);
+                kahan_add(s2[k], c2[k], b2[k]);
             }
-            if (act && ++nblk == FOLD) {
-                acc_fold(A);
-                nblk = 0;
-            }
-        }
-        for (int s = 0; s < SLOTS; ++s) {
-            if (slot == s && run_c >= 0 && lane_on)
-                slot_flush(sm[warp], A, (run_c & (TS - 1)) + l8, run_c >> 4, HS, fw, shit);
-            __syncwarp();
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < HS * HS; i += blockDim.x) {
-            if (!shit[i]) continue;
-            const int hx = i % HS, hy = i / HS;
-            const int gx = gx0 - r + hx, gy = gy0 - r + hy;
-            if (gx < -G.half || gx > G.half || gy < -G.half || gy > G.half) continue;
-            double re = 0.0, im = 0.0, w = 0.0;
+            const int cell = st_c[T.x];
+            const int cx = gx0 + (cell & (TS - 1)), cy = gy0 + (cell >> 4);
 #pragma unroll
-            for (int wv = 0; wv < GW; ++wv) {
-                re += (double)sm[wv][0][i] - (double)sm[wv][1][i];
-                im += (double)sm[wv][2][i] - (double)sm[wv][3][i];
-                w += (double)sm[wv][4][i] - (double)sm[wv][5][i];
+            for (int h = 0; h < 2; ++h) {
+                if (h == 0 ? !on1 : !on2) continue;
+                const int gx = cx + (h == 0 ? dx1 : dx2) - r, gy = cy + (h == 0 ? dy1 : dy2) - r;
+                if (gx < -G.half || gx > G.half || gy < -G.half || gy > G.half) continue;
+                const float *S = h == 0 ? s1 : s2;
+                const float *C = h == 0 ? c1 : c2;
+                const int64_t pidx = cell_index(G.n, gx, gy);
+                atomicAdd(&acc_re[pidx], (double)S[0] - (double)C[0]);
+                atomicAdd(&acc_im[pidx], (double)S[1] - (double)C[1]);
+                atomicAdd(&acc_w[pidx], (double)S[2] - (double)C[2]);
+                hit[pidx] = 1;
             }
-            const int64_t pidx = cell_index(G.n, gx, gy);
-            atomicAdd(&acc_re[pidx], re);
-            atomicAdd(&acc_im[pidx], im);
-            atomicAdd(&acc_w[pidx], w);
-            hit[pidx] = 1;
         }
-        __syncthreads();
     }
 }
 
@@ -496,7 +565,7 @@ __global__ void k_grid_finalize(int n, const double *__restrict__ acc_re,
 
 struct PlanBufs {
     uint32_t *keys, *hist, *offs, *bsum;
-    float4 *s_f;
+    float4 *s_w;          // [n][4] weight records
     uint32_t *s_idx, *s_key;
     uint32_t *k2, *v2, *vals, *rhist, *roffs, *n_valid;
     int4 *units;
@@ -507,7 +576,7 @@ struct PlanBufs {
 
 bool plan_bufs(abs_ctx *ctx, const GridGeom &G, int64_t n_vis, PlanBufs &b) {
     b.ntiles = G.tt * G.tt;
-    b.nkeys = (int64_t)b.ntiles * TS * TS;
+    b.nkeys = b.ntiles;
     b.n_vis = n_vis;
     b.units_cap = (int)(b.ntiles + cdiv(n_vis, UMAX) + 1);
     const int64_t nv = n_vis > 0 ? n_vis : 1;
@@ -515,7 +584,7 @@ bool plan_bufs(abs_ctx *ctx, const GridGeom &G, int64_t n_vis, PlanBufs &b) {
     b.hist = (uint32_t *)workspace(ctx, "plan.hist", sizeof(uint32_t) * b.nkeys);
     b.offs = (uint32_t *)workspace(ctx, "plan.offs", sizeof(uint32_t) * b.nkeys);
     b.bsum = (uint32_t *)workspace(ctx, "plan.bsum", sizeof(uint32_t) * (cdiv(b.nkeys, 4096) + 1));
-    b.s_f = (float4 *)workspace(ctx, "plan.s_f", sizeof(float4) * nv);
+    b.s_w = (float4 *)workspace(ctx, "plan.s_w", sizeof(float4) * 4 * nv);
     b.s_idx = (uint32_t *)workspace(ctx, "plan.s_idx", sizeof(uint32_t) * nv);
     b.s_key = (uint32_t *)workspace(ctx, "plan.s_key", sizeof(uint32_t) * nv);
     b.units = (int4 *)workspace(ctx, "plan.units", sizeof(int4) * b.units_cap);
@@ -527,7 +596,7 @@ bool plan_bufs(abs_ctx *ctx, const GridGeom &G, int64_t n_vis, PlanBufs &b) {
     b.rhist = (uint32_t *)workspace(ctx, "plan.rhist", sizeof(uint32_t) * 256 * b.rtiles);
     b.roffs = (uint32_t *)workspace(ctx, "plan.roffs", sizeof(uint32_t) * 256 * b.rtiles);
     b.n_valid = (uint32_t *)workspace(ctx, "plan.n_valid", sizeof(uint32_t));
-    return b.keys && b.hist && b.offs && b.bsum && b.s_f && b.s_idx && b.s_key && b.units &&
+    return b.keys && b.hist && b.offs && b.bsum && b.s_w && b.s_idx && b.s_key && b.units &&
            b.n_units && b.k2 && b.v2 && b.vals && b.rhist && b.roffs && b.n_valid;
 }
 
@@ -556,20 +625,15 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
     const uint32_t key_none = (uint32_t)b.nkeys;     // invalid visibilities sort last
     if (n_vis > 0)
         k_plan_keys<<<grid_v, 256, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, b.vals, b.hist, key_none);
-    scan_u32(st, b.hist, b.nkeys, b.offs, bsum);
-    k_units<<<1, 1024, 0, st>>>(b.offs, b.hist, b.nkeys, b.ntiles, b.units, b.n_units, b.units_cap,
-                                b.n_valid);
+    k_units<<<1, 1024, 0, st>>>(b.hist, b.ntiles, b.units, b.n_units, b.units_cap, b.n_valid);
     if (n_vis > 0) {
-        // stable sort of (key, index); ping-pong keys/vals <-> k2/v2, result in s_key/s_idx
+        // stable sort of (tile, index); ping-pong keys/vals <-> k2/v2, result in k2/v2
+        // or keys/vals; k_plan_units then sorts each unit by cell into s_key/s_idx
         int bits = 1;
         while (((uint64_t)1 << bits) <= (uint64_t)key_none) ++bits;
         const int passes = (bits + 7) / 8;
         uint32_t *ki = b.keys, *vi = b.vals, *ko = b.k2, *vo = b.v2;
         for (int ps = 0; ps < passes; ++ps) {
-            if (ps == passes - 1) {
-                ko = b.s_key;
-                vo = b.s_idx;
-            }
             k_radix_hist<<<b.rtiles, 256, 0, st>>>(ki, n_vis, 8 * ps, b.rtiles, b.rhist);
             scan_u32(st, b.rhist, rlen, b.roffs, bsum);
             k_radix_scatter<<<b.rtiles, 256, 0, st>>>(ki, vi, n_vis, 8 * ps, b.rtiles, b.roffs, ko, vo);
@@ -583,8 +647,9 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
                 std::swap(vi, vo);
             }
         }
-        k_plan_offsets<<<grid_v, 256, 0, st>>>(G, n_vis, b.n_valid, (const float2 *)d_uv, b.s_idx, b.s_key,
-                                               b.s_f);
+        // ki/vi now hold the tile-sorted (tile, index) pairs
+        const int ub = std::min(b.units_cap, ctx->sm_count * 8);
+        k_plan_units<<<ub, PT, 0, st>>>(G, b.units, b.n_units, (const float2 *)d_uv, vi, b.s_key, b.s_idx, b.s_w);
     }
     return check_launch(ctx, "grid plan");
 }
@@ -612,9 +677,8 @@ abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, c
     }
     if (n_vis > 0) {
         StageTimer timer(ctx, "grid");
-        const int blocks = std::min(b.units_cap, ctx->sm_count * 3);
-        cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRID_SMEM);
-        k_grid<<<blocks, GW * 32, GRID_SMEM, st>>>(G, b.units, b.n_units, b.s_f, b.s_idx, b.s_key,
+        const int blocks = std::min(b.units_cap, ctx->sm_count * 4);
+        k_grid<<<blocks, GT, GRID_SMEM, st>>>(G, b.units, b.n_units, b.s_w, b.s_idx, b.s_key,
                                            (const float2 *)d_vis, acc, acc + cells,
                                            acc + 2 * cells, hit);
     }
