@@ -40,7 +40,9 @@ METRIC = "ABS estimates/s (V->binned B)"
 UNIT = "estimates/s"
 
 # kernels launched per stage-timer entry (the profiler brackets stages); the
-# gridding plan runs 3 kernels plus 5 per radix pass (8-bit digits of the uv tile id)
+# gridding plan runs the key kernel, the unit cutter and, per radix pass of up
+# to 11-bit digits of the uv tile id, a 3-kernel scan and a scatter (plus a
+# histogram kernel on passes after the first)
 KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "ring_lists": 6,
                      "count_items": 1, "count_pairs": 1, "count_gather": 1, "ellbar": 6,
                      "fft_rows": 1, "fft_cols": 1, "triple_fp32": 1, "triple_reduce": 1,
@@ -49,8 +51,8 @@ KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "ring_lists"
 
 def plan_kernels(n_grid, radius):
     tiles = -(-(n_grid - 1 + 2 * radius) // 16)
-    passes = -(-int(tiles * tiles).bit_length() // 8)
-    return 3 + 5 * passes
+    passes = -(-int(tiles * tiles).bit_length() // 11)
+    return 2 + 4 * passes + (passes - 1)
 
 
 def load_peaks():
@@ -60,6 +62,24 @@ def load_peaks():
         return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "bf16_tflops": d.get("bf16_tflops", 1900.0),
                 "source": "measured"}
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# DRAM traffic of one launch (dram__bytes_read.sum + dram__bytes_write.sum)
+# from the ncu captures summarised under profiles/, with the SHA-256 of the
+# source file the kernel was built from when it was captured.  A kernel whose
+# source has changed since then reports null.
+MEASURED_TRAFFIC = {}
+
+
+def measured_traffic(stage):
+    e = MEASURED_TRAFFIC.get(stage)
+    if e is None:
+        return None
+    import hashlib
+    path = os.path.join(ROOT, e["source"])
+    if not os.path.exists(path) or hashlib.sha256(open(path, "rb").read()).hexdigest() != e["sha256"]:
+        return None
+    return e["bytes"]
 
 
 class ClockSampler:
@@ -188,10 +208,10 @@ def roofline_for(stage, avg_ms, geo, peaks):
         byts = geo["bytes"].get(stage)
         if byts is None:
             return {"bound": "hbm", "achieved": None, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": None,
-                    "traffic": None}
+                    "traffic": measured_traffic(stage)}
         out = {"bound": "hbm", "achieved": byts / s / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
     out["frac"] = out["achieved"] / out["peak"]
-    out["traffic"] = None
+    out["traffic"] = measured_traffic(stage)
     return out
 
 
@@ -360,7 +380,8 @@ def run_ours(args):
               for k, v in prof.items()}
     kps = dict(KERNELS_PER_STAGE, grid_plan=plan_kernels(wl.n_grid, wl.radius_cells))
     launches = sum(kps.get(k, 1) * v[1] for k, v in prof.items())
-    dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    # the dominant kernel: the single-kernel stage with the most device time
+    dom = max(((k, v) for k, v in prof.items() if kps.get(k, 1) == 1), key=lambda kv: kv[1][0])[0]
     peaks = load_peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_mhz = clk.get("sm_mhz") or 1900.0
@@ -370,6 +391,11 @@ def run_ours(args):
     roof = roofline_for(dom, stages[dom]["avg_us"] * 1e-3, geo, peaks)
     roof["kernel"] = dom
     roof["peak_source"] = peaks["source"]
+    other_roofs = {}
+    for k in ("grid", "fft_rows", "fft_cols", "count_pairs", "triple_fp32"):
+        if k in stages and k != dom:
+            rr = roofline_for(k, stages[k]["avg_us"] * 1e-3, geo, peaks)
+            other_roofs[k] = {kk: rr[kk] for kk in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
     tri_fp32 = roofline_for("triple_fp32", stages["triple_fp32"]["avg_us"] * 1e-3, geo, peaks)
     tc_avg = 1e3 * prof_tc["triple_tc"][0] / max(prof_tc["triple_tc"][1], 1)
     tri_tc = roofline_for("triple_tc", tc_avg * 1e-3, geo, peaks)
@@ -382,7 +408,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(wl), "clocks": clk,
         "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches), "roofline": roof,
+        "gpu_launches": int(launches), "roofline": roof, "stage_rooflines": other_roofs,
         "cpu_baseline": {"value": 1.0 / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "one full realisation of the workload (plain C FP64, brute-force "
                                    "closed-triangle sums)"},

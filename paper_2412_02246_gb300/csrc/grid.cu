@@ -6,15 +6,17 @@
 // the same sum.
 //
 // Plan (per baseline set): key every visibility by its 16x16-cell uv tile,
-// stable-sort by tile (LSD radix), cut every tile's run into work units of at
-// most UMAX visibilities, sort each unit by cell (stable) and form the 1-D
-// Gaussian weights of every visibility once.
+// stable-sort by tile (one radix pass while there are fewer than 2048 tiles,
+// about 700 cells a side; two beyond), write the sorted positions and original
+// indices, and cut every tile's run into work units of at most UMAX
+// visibilities.
 //
 // Accumulation (per realisation): one CTA per unit stages the unit in shared
-// memory and cuts it into runs of visibilities that share a cell; a warp sums
-// the (2r+1)^2 footprint cells of a run (lane per footprint cell, compensated
-// FP32, fixed order) and adds them to an FP64 grid.  A final pass applies the
-// Hermitian mirror and writes the FP32 outputs.
+// memory, sorts it by cell (stable), forms the 1-D Gaussian weights and cuts
+// it into runs of visibilities that share a cell; a warp sums the (2r+1)^2
+// footprint cells of a run (lane per footprint cell, compensated FP32, input
+// order) and adds them to an FP64 grid.  A final pass applies the Hermitian
+// mirror and writes the FP32 outputs.
 //
 // Weights: w = exp(-(dx - fx)^2 s) exp(-(dy - fy)^2 s), s = 1/(2 sigma^2),
 // with the fractional offset f = u/dU - c carried as a float pair (the exact
@@ -79,34 +81,140 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
 }
 
 // ------------------------------------------------------------------ plan kernels
+// The plan is a stable counting sort of the visibilities by uv tile: LSD radix
+// with digits of up to DMAX bits (one pass while the tile count fits 2^DMAX,
+// two for the largest grids), so every tile's visibilities keep their input
+// order and the gridded sums are reproducible run to run.  A pass is per-chunk
+// digit histograms (digit-major) -> exclusive scan -> order-preserving scatter.
+constexpr int RT = 4096;               // visibilities per sort chunk (256 threads x 16)
+constexpr int DMAX = 11;               // widest digit: 2048 bins
 
-__global__ void k_plan_keys(GridGeom G, int64_t n_vis, const float2 *__restrict__ uv,
-                            uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                            uint32_t *__restrict__ hist, uint32_t key_none) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_vis;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 p = uv[i];
-        uint32_t key = key_none;
-        if (isfinite(p.x) && isfinite(p.y)) {
-            const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
-            if (fabsf(qx) < 1.0e7f && fabsf(qy) < 1.0e7f) {
-                const int cx = (int)floorf(__fadd_rn(qx, 0.5f));
-                const int cy = (int)floorf(__fadd_rn(qy, 0.5f));
-                const int kx = cx + G.off, ky = cy + G.off;
-                if (kx >= 0 && kx < G.ks && ky >= 0 && ky < G.ks)
-                    key = (uint32_t)((ky / TS) * G.tt + kx / TS);   // 16x16-cell uv tile
-            }
+__device__ __forceinline__ uint32_t tile_key(const GridGeom &G, float2 p, uint32_t key_none) {
+    if (!(isfinite(p.x) && isfinite(p.y))) return key_none;
+    const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
+    if (!(fabsf(qx) < 1.0e7f && fabsf(qy) < 1.0e7f)) return key_none;
+    const int cx = (int)floorf(__fadd_rn(qx, 0.5f));
+    const int cy = (int)floorf(__fadd_rn(qy, 0.5f));
+    const int kx = cx + G.off, ky = cy + G.off;
+    if (kx < 0 || kx >= G.ks || ky < 0 || ky >= G.ks) return key_none;
+    return (uint32_t)((ky / TS) * G.tt + kx / TS);
+}
+
+// One CTA per chunk: the tile key of every visibility (key_none for non-finite
+// or off-grid positions), per-tile totals and the chunk's histogram of the
+// first digit.  Counts are added once per distinct key in a warp
+// (consecutive visibilities of a baseline usually share a tile).
+__global__ void __launch_bounds__(256) k_plan_keys(GridGeom G, int64_t n_vis, const float2 *__restrict__ uv,
+                                                   uint32_t *__restrict__ keys,
+                                                   uint32_t *__restrict__ tile_hist, uint32_t key_none,
+                                                   int dw, int nchunks, uint32_t *__restrict__ rhist) {
+    __shared__ uint32_t h[1 << DMAX];
+    const int nb = 1 << dw, lane = threadIdx.x & 31;
+    for (int d = threadIdx.x; d < nb; d += 256) h[d] = 0;
+    __syncthreads();
+    const int64_t c0 = (int64_t)blockIdx.x * RT;
+    for (int k = 0; k < RT / 256; ++k) {
+        const int64_t i = c0 + k * 256 + threadIdx.x;
+        const bool on = i < n_vis;
+        uint32_t key = 0xffffffffu;
+        if (on) {
+            key = tile_key(G, uv[i], key_none);
+            keys[i] = key;
         }
-        keys[i] = key;
-        // one atomic per distinct tile in the warp (consecutive visibilities of a
-        // baseline usually share a tile)
-        const unsigned active = __activemask();
-        const unsigned peers = __match_any_sync(active, key);
-        const int lane = threadIdx.x & 31;
-        if (key != key_none && lane == __ffs(peers) - 1) atomicAdd(&hist[key], (uint32_t)__popc(peers));
-        vals[i] = (uint32_t)i;
+        const unsigned peers = __match_any_sync(FULL, key);
+        if (on && lane == __ffs(peers) - 1) {
+            const uint32_t c = (uint32_t)__popc(peers);
+            if (key != key_none) atomicAdd(&tile_hist[key], c);
+            atomicAdd(&h[key & (uint32_t)(nb - 1)], c);
+        }
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += 256) rhist[(int64_t)d * nchunks + blockIdx.x] = h[d];
+}
+
+// Digit histogram of one chunk for the passes after the first.
+__global__ void __launch_bounds__(256) k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
+                                                    int dw, int nchunks, uint32_t *__restrict__ rhist) {
+    __shared__ uint32_t h[1 << DMAX];
+    const int nb = 1 << dw, lane = threadIdx.x & 31;
+    for (int d = threadIdx.x; d < nb; d += 256) h[d] = 0;
+    __syncthreads();
+    const int64_t c0 = (int64_t)blockIdx.x * RT;
+    for (int k = 0; k < RT / 256; ++k) {
+        const int64_t i = c0 + k * 256 + threadIdx.x;
+        const bool on = i < n;
+        const uint32_t d = on ? (keys[i] >> shift) & (uint32_t)(nb - 1) : 0x10000u + lane;
+        const unsigned peers = __match_any_sync(FULL, d);
+        if (on && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += 256) rhist[(int64_t)d * nchunks + blockIdx.x] = h[d];
+}
+
+// Order-preserving scatter of one chunk.  Warp w owns the contiguous eighth
+// [w RT/8, (w+1) RT/8) of the chunk: a first sweep counts its digits, a
+// prefix over warps gives every warp its place inside the chunk's run of each
+// digit, and a second sweep places the items (rank among equal digits from
+// __match_any_sync, lower lanes first).  vin == nullptr means the identity
+// (first pass); on the last pass (uv_out != nullptr) the sorted original
+// indices and positions are written instead of keys.
+__global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t *__restrict__ kin,
+                                                       const uint32_t *__restrict__ vin, int64_t n,
+                                                       int shift, int dw, int nchunks,
+                                                       const uint32_t *__restrict__ offs,
+                                                       uint32_t *__restrict__ kout,
+                                                       uint32_t *__restrict__ vout,
+                                                       const float2 *__restrict__ uv,
+                                                       float2 *__restrict__ uv_out) {
+    __shared__ uint16_t wloc[8][1 << DMAX];
+    __shared__ uint32_t base[1 << DMAX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nb = 1 << dw;
+    const uint32_t dmask = (uint32_t)(nb - 1);
+    for (int d = threadIdx.x; d < nb; d += 256) {
+        base[d] = offs[(int64_t)d * nchunks + blockIdx.x];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) wloc[w][d] = 0;
+    }
+    __syncthreads();
+    const int64_t w0 = (int64_t)blockIdx.x * RT + warp * (RT / 8);
+    for (int k = 0; k < RT / 8 / 32; ++k) {
+        const int64_t e = w0 + k * 32 + lane;
+        const bool on = e < n;
+        const uint32_t d = on ? (kin[e] >> shift) & dmask : 0x10000u + lane;
+        const unsigned peers = __match_any_sync(FULL, d);
+        if (on && lane == __ffs(peers) - 1) wloc[warp][d] += (uint16_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nb; d += 256) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t c = wloc[w][d];
+            wloc[w][d] = (uint16_t)run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < RT / 8 / 32; ++k) {
+        const int64_t e = w0 + k * 32 + lane;
+        const bool on = e < n;
+        const uint32_t key = on ? kin[e] : 0u;
+        const uint32_t d = on ? (key >> shift) & dmask : 0x10000u + lane;
+        const unsigned peers = __match_any_sync(FULL, d);
+        if (on) {
+            const uint32_t pos = base[d] + wloc[warp][d] + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+            const uint32_t val = vin ? vin[e] : (uint32_t)e;
+            vout[pos] = val;
+            if (uv_out) uv_out[pos] = uv[val];
+            else kout[pos] = key;
+        }
+        __syncwarp();
+        if (on && lane == __ffs(peers) - 1) wloc[warp][d] += (uint16_t)__popc(peers);
+        __syncwarp();
     }
 }
+
 
 // Block-wide exclusive scan of one value per thread (blockDim.x == 1024).
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *sh, uint32_t &total) {
@@ -178,182 +286,6 @@ __global__ void k_scan_add(uint32_t *__restrict__ out, int64_t len,
     if (i < len) out[i] += block_sums[i / 4096];
 }
 
-// Stable LSD radix sort of (key, original index) pairs, 8-bit digits, so
-// that every cell's visibilities keep their input order and the gridded sums
-// are reproducible run to run.  Pass = per-tile digit histograms (digit-major)
-// -> exclusive scan -> order-preserving scatter.
-constexpr int RTILE = 2048;            // items per tile (256 threads x 8 rounds)
-
-__global__ void __launch_bounds__(256) k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
-                                                    int ntiles, uint32_t *__restrict__ hist) {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t t0 = (int64_t)blockIdx.x * RTILE;
-    for (int r = 0; r < RTILE / 256; ++r) {
-        const int64_t e = t0 + r * 256 + threadIdx.x;
-        if (e < n) atomicAdd(&h[(keys[e] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
-}
-
-__global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t *__restrict__ kin,
-                                                       const uint32_t *__restrict__ vin, int64_t n,
-                                                       int shift, int ntiles,
-                                                       const uint32_t *__restrict__ offs,
-                                                       uint32_t *__restrict__ kout,
-                                                       uint32_t *__restrict__ vout) {
-    __shared__ uint32_t wcount[8][256];
-    __shared__ uint32_t wbase[8][256];
-    __shared__ uint32_t base[256];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    base[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
-    for (int w = 0; w < 8; ++w) wcount[w][threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t t0 = (int64_t)blockIdx.x * RTILE;
-    for (int r = 0; r < RTILE / 256; ++r) {
-        const int64_t e = t0 + r * 256 + threadIdx.x;
-        const bool on = e < n;
-        const uint32_t key = on ? kin[e] : 0u;
-        const uint32_t val = on ? vin[e] : 0u;
-        const uint32_t d = on ? ((key >> shift) & 255u) : 256u + lane;   // unique for idle lanes
-        const unsigned peers = __match_any_sync(FULL, d);
-        const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-        if (on && rank == 0) wcount[warp][d] = __popc(peers);
-        __syncthreads();
-        {   // digit threadIdx.x: prefix over warps in order
-            uint32_t run = base[threadIdx.x];
-            for (int w = 0; w < 8; ++w) {
-                const uint32_t c = wcount[w][threadIdx.x];
-                wbase[w][threadIdx.x] = run;
-                run += c;
-                wcount[w][threadIdx.x] = 0;
-            }
-            base[threadIdx.x] = run;
-        }
-        __syncthreads();
-        if (on) {
-            const uint32_t pos = wbase[warp][d] + rank;
-            kout[pos] = key;
-            vout[pos] = val;
-        }
-        __syncthreads();
-    }
-}
-
-// Per work unit (<= UMAX visibilities of one uv tile, in input order after the
-// stable tile sort): stable sort by cell within the tile, and the 2 x (2r+1)
-// one-dimensional weights of every visibility, w(d) = exp(-s (d - f)^2) with
-// f = u/dU - c carried as a float pair (the exact division residual).  Writes
-// s_key = tile << 8 | cell in tile, s_idx and s_w [16] = (wx[0..6], -, wy[0..6], -)
-// in cell order.  One CTA per unit, 128 threads.
-constexpr int PT = 128;
-constexpr int WREC = 16;   // floats per weight record
-
-__global__ void __launch_bounds__(PT) k_plan_units(GridGeom G, const int4 *__restrict__ units,
-                                                   const int *__restrict__ n_units,
-                                                   const float2 *__restrict__ uv,
-                                                   const uint32_t *__restrict__ t_idx,
-                                                   uint32_t *__restrict__ s_key,
-                                                   uint32_t *__restrict__ s_idx,
-                                                   float4 *__restrict__ s_w) {
-    __shared__ float4 wst[UMAX][WREC / 4];
-    __shared__ uint32_t ist[UMAX];
-    __shared__ uint8_t cst[UMAX];
-    __shared__ uint32_t cnt[256], base[256];
-    __shared__ uint32_t wcnt[PT / 32][256], wpre[PT / 32][256];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r = G.r, fw = 2 * r + 1;
-    const int nu = *n_units;
-    for (int u = blockIdx.x; u < nu; u += gridDim.x) {
-        const int4 U = units[u];
-        const int total = U.z - U.y;
-        const uint32_t tile = (uint32_t)U.x;
-        for (int c = threadIdx.x; c < 256; c += PT) cnt[c] = 0;
-        __syncthreads();
-        for (int t = threadIdx.x; t < total; t += PT) {
-            const uint32_t idx = t_idx[U.y + t];
-            const float2 p = uv[idx];
-            const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
-            const int cx = (int)floorf(__fadd_rn(qx, 0.5f)), cy = (int)floorf(__fadd_rn(qy, 0.5f));
-            const int kx = cx + G.off, ky = cy + G.off;
-            const int lc = (ky % TS) * TS + kx % TS;
-            const float fxh = __fsub_rn(qx, (float)cx), fyh = __fsub_rn(qy, (float)cy);
-            const float fxl = __fdiv_rn(fmaf(-qx, G.du, p.x), G.du);
-            const float fyl = __fdiv_rn(fmaf(-qy, G.du, p.y), G.du);
-            float w[WREC];
-#pragma unroll
-            for (int k = 0; k < WREC; ++k) w[k] = 0.f;
-#pragma unroll
-            for (int k = 0; k < FWMAX; ++k) {
-                if (k < fw) {
-                    const float d = (float)(k - r);
-                    w[k] = G.kernel == ABS_KERNEL_GAUSS ? wexp(d, fxh, fxl, G.s_hi, G.s_lo) : 1.f;
-                    w[8 + k] = G.kernel == ABS_KERNEL_GAUSS ? wexp(d, fyh, fyl, G.s_hi, G.s_lo) : 1.f;
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < WREC / 4; ++k) wst[t][k] = make_float4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
-            ist[t] = idx;
-            cst[t] = (uint8_t)lc;
-            atomicAdd(&cnt[lc], 1u);
-        }
-        __syncthreads();
-        if (warp == 0) {   // exclusive scan of the 256 cell counts
-            uint32_t v[8], run = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                v[k] = cnt[lane * 8 + k];
-                run += v[k];
-            }
-            uint32_t incl = run;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += y;
-            }
-            uint32_t b0 = incl - run;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                base[lane * 8 + k] = b0;
-                b0 += v[k];
-            }
-        }
-        __syncthreads();
-        // stable placement: items in input order, rounds of PT
-        for (int r0 = 0; r0 < total; r0 += PT) {
-            const int t = r0 + threadIdx.x;
-            const bool on = t < total;
-            const uint32_t c = on ? cst[t] : 256u + lane;
-            const unsigned peers = __match_any_sync(FULL, c);
-            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-            for (int w = 0; w < PT / 32; ++w) wcnt[w][threadIdx.x] = 0;   // PT >= ... 256 cells: loop below
-            for (int cc = threadIdx.x + PT; cc < 256; cc += PT)
-                for (int w = 0; w < PT / 32; ++w) wcnt[w][cc] = 0;
-            __syncthreads();
-            if (on && rank == 0) wcnt[warp][c] = __popc(peers);
-            __syncthreads();
-            for (int cc = threadIdx.x; cc < 256; cc += PT) {
-                uint32_t run = base[cc];
-                for (int w = 0; w < PT / 32; ++w) {
-                    wpre[w][cc] = run;
-                    run += wcnt[w][cc];
-                }
-                base[cc] = run;
-            }
-            __syncthreads();
-            if (on) {
-                const int pos = U.y + (int)(wpre[warp][c] + rank);
-                s_key[pos] = tile << 8 | c;
-                s_idx[pos] = ist[t];
-#pragma unroll
-                for (int k = 0; k < WREC / 4; ++k) s_w[(size_t)pos * (WREC / 4) + k] = wst[t][k];
-            }
-            __syncthreads();
-        }
-    }
-}
 
 // One block: cut every tile's run of sorted visibilities into units of <= UMAX.
 __global__ void __launch_bounds__(1024) k_units(const uint32_t *__restrict__ hist, int ntiles,
@@ -386,30 +318,29 @@ __global__ void __launch_bounds__(1024) k_units(const uint32_t *__restrict__ his
 }
 
 // ------------------------------------------------------------------ accumulation
-
-// ------------------------------------------------------------------ accumulation
-// One CTA per work unit (<= UMAX visibilities of one 16x16-cell tile, sorted by
-// cell).  The unit is staged in shared memory (1-D weights from the plan, the
-// visibilities gathered) and cut into tasks: runs of at most CHUNK
-// visibilities that share a cell.  A warp takes a task; lane k owns footprint
-// cells k and k + 32 of the (2r+1)^2 around the run's cell and sums
-// w = wx[dx] wy[dy] times V over the run (plain FP32 blocks of 8 folded into
-// Kahan sums, fixed order), then adds its cells to the FP64 grid.  No shared
-// accumulators: runs never wait on one another, whether the tile is dense
-// (long runs) or sparse (short ones).
+// One CTA per work unit (<= UMAX visibilities of one 16x16-cell tile, in input
+// order).  The unit is staged in shared memory and stably sorted by cell
+// (per-warp counts, prefix over (cell, warp), ranked placement), each
+// visibility's 2 (2r+1) one-dimensional weights are formed once, and the
+// unit is cut into tasks: runs of at most CHUNK visibilities that share a
+// cell.  A warp takes a task; lane k owns footprint cells k and k + 32 of the
+// (2r+1)^2 around the run's cell and sums w = wx[dx] wy[dy] times V over the
+// run (plain FP32 blocks of GFOLD folded into Kahan sums, in input order),
+// then adds its cells to the FP64 grid.  No shared accumulators: runs never
+// wait on one another, whether the tile is dense (long runs) or sparse.
+constexpr int GT = 256;          // threads per gridding CTA (8 warps x UMAX/8 items)
 constexpr int WST = 17;          // floats per staged weight record (odd: spreads banks)
-constexpr int GT = 256;          // threads per gridding CTA
 constexpr int GFOLD = 8;
 constexpr int CHUNK = 64;        // visibilities per task at most
-constexpr int MAXTASK = UMAX + 256;
-constexpr size_t GRID_SMEM = UMAX * (sizeof(float) * WST + sizeof(float2) + 1) + sizeof(uint32_t) * 257 +
-                             sizeof(int2) * MAXTASK;
+constexpr int MAXTASK = UMAX / CHUNK + 256;   // sum over cells of ceil(run / CHUNK)
+static_assert(UMAX == 8 * 64, "the in-unit sort gives each of 8 warps two rounds of 32 items");
+constexpr size_t GRID_SMEM = UMAX * (sizeof(float) * WST + sizeof(float2)) + sizeof(int2) * MAXTASK +
+                             sizeof(uint16_t) * 8 * 256 + sizeof(uint32_t) * 260 + 2 * UMAX;
 
 __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict__ units,
                                              const int *__restrict__ n_units,
-                                             const float4 *__restrict__ s_w,
+                                             const float2 *__restrict__ s_uv,
                                              const uint32_t *__restrict__ s_idx,
-                                             const uint32_t *__restrict__ s_key,
                                              const float2 *__restrict__ vis,
                                              double *__restrict__ acc_re,
                                              double *__restrict__ acc_im,
@@ -419,11 +350,15 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
     float *st_w = (float *)dsm;                                        // [UMAX][WST] 1-D weights
     float2 *st_v = (float2 *)(st_w + UMAX * WST);                      // [UMAX] visibilities
     int2 *task = (int2 *)(st_v + UMAX);                                // [MAXTASK] (first, end)
-    uint32_t *cstart = (uint32_t *)(task + MAXTASK);                   // [257] first item of each cell
-    uint8_t *st_c = (uint8_t *)(cstart + 257);                         // [UMAX] cell in tile
+    uint16_t *wloc = (uint16_t *)(task + MAXTASK);                     // [8][256] per-warp cell counts
+    uint32_t *cstart = (uint32_t *)(wloc + 8 * 256);                   // [257] first item of each cell
+    uint8_t *in_c = (uint8_t *)(cstart + 260);                         // [UMAX] cell, input order
+    uint8_t *st_c = in_c + UMAX;                                       // [UMAX] cell, sorted order
+    __shared__ uint32_t sh_scan[32];
     __shared__ int ntask_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = GT / 32;
     const int r = G.r, fw = 2 * r + 1, nfp = fw * fw;
+    const bool gauss = G.kernel == ABS_KERNEL_GAUSS;
     // this lane's two footprint cells
     const int k1 = lane, k2 = lane + 32;
     const bool on1 = k1 < nfp, on2 = k2 < nfp;
@@ -433,29 +368,77 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
     for (int u = blockIdx.x; u < nu; u += gridDim.x) {
         const int4 U = units[u];
         const int total = U.z - U.y;
+        const int tile = U.x, tx = tile % G.tt, ty = tile / G.tt;
         __syncthreads();   // previous unit done with the staging buffers
-        for (int e = threadIdx.x; e < total * (WREC / 4); e += GT) {
-            const int t = e >> 2, k = e & 3;
-            const float4 q = s_w[(size_t)(U.y + t) * (WREC / 4) + k];
-            float *d = st_w + t * WST + 4 * k;
-            d[0] = q.x;
-            d[1] = q.y;
-            d[2] = q.z;
-            d[3] = q.w;
-        }
-        for (int t = threadIdx.x; t < total; t += GT) {
-            st_c[t] = (uint8_t)(s_key[U.y + t] & 255u);
-            st_v[t] = vis[s_idx[U.y + t]];
+        // cells, and per-warp counts over the warp's 64 items (input order)
+        for (int k = lane; k < 256; k += 32) wloc[warp * 256 + k] = 0;
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = warp * 64 + h * 32 + lane;
+            const bool on = t < total;
+            uint32_t c = 0x10000u + lane;
+            if (on) {
+                const float2 p = s_uv[U.y + t];
+                const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
+                const int kx = (int)floorf(__fadd_rn(qx, 0.5f)) + G.off;
+                const int ky = (int)floorf(__fadd_rn(qy, 0.5f)) + G.off;
+                c = (uint32_t)((ky - ty * TS) * TS + (kx - tx * TS));
+                in_c[t] = (uint8_t)c;
+            }
+            const unsigned peers = __match_any_sync(FULL, c);
+            if (on && lane == __ffs(peers) - 1) wloc[warp * 256 + c] += (uint16_t)__popc(peers);
+            __syncwarp();
         }
         __syncthreads();
-        for (int c = threadIdx.x; c <= 256; c += GT) {   // first item of each cell (unit is cell-sorted)
-            int lo = 0, hi = total;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if ((int)st_c[mid] < c) lo = mid + 1;
-                else hi = mid;
+        {   // cell threadIdx.x: its start, and each warp's place inside its run
+            const int c = threadIdx.x;
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) cnt += wloc[w * 256 + c];
+            uint32_t tot;
+            const uint32_t start = block_exclusive_scan(cnt, sh_scan, tot);
+            cstart[c] = start;
+            if (c == 255) cstart[256] = start + cnt;
+            uint32_t run = start;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                const uint32_t x = wloc[w * 256 + c];
+                wloc[w * 256 + c] = (uint16_t)run;
+                run += x;
             }
-            cstart[c] = (uint32_t)lo;
+        }
+        __syncthreads();
+        // placement in cell order: weights, visibility and cell of every item
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = warp * 64 + h * 32 + lane;
+            const bool on = t < total;
+            const uint32_t c = on ? (uint32_t)in_c[t] : 0x10000u + lane;
+            const unsigned peers = __match_any_sync(FULL, c);
+            if (on) {
+                const int pos = (int)wloc[warp * 256 + c] + __popc(peers & ((1u << lane) - 1u));
+                const float2 p = s_uv[U.y + t];
+                const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
+                const float cxf = floorf(__fadd_rn(qx, 0.5f)), cyf = floorf(__fadd_rn(qy, 0.5f));
+                const float fxh = __fsub_rn(qx, cxf), fyh = __fsub_rn(qy, cyf);
+                const float fxl = __fdiv_rn(fmaf(-qx, G.du, p.x), G.du);
+                const float fyl = __fdiv_rn(fmaf(-qy, G.du, p.y), G.du);
+                float *w = st_w + pos * WST;
+#pragma unroll
+                for (int k = 0; k < FWMAX; ++k) {
+                    if (k < fw) {
+                        const float d = (float)(k - r);
+                        w[k] = gauss ? wexp(d, fxh, fxl, G.s_hi, G.s_lo) : 1.f;
+                        w[8 + k] = gauss ? wexp(d, fyh, fyl, G.s_hi, G.s_lo) : 1.f;
+                    }
+                }
+                st_v[pos] = vis[s_idx[U.y + t]];
+                st_c[pos] = (uint8_t)c;
+            }
+            __syncwarp();
+            if (on && lane == __ffs(peers) - 1) wloc[warp * 256 + c] += (uint16_t)__popc(peers);
+            __syncwarp();
         }
         __syncthreads();
         if (warp == 0) {   // tasks: every cell's run cut into chunks of <= CHUNK
@@ -487,38 +470,31 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
         }
         __syncthreads();
         const int ntask = ntask_s;
-        const int tile = U.x, tx = tile % G.tt, ty = tile / G.tt;
         const int gx0 = tx * TS - G.off, gy0 = ty * TS - G.off;
         for (int tk = warp; tk < ntask; tk += nwarps) {
             const int2 T = task[tk];
             float b1[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f}, c1[3] = {0.f, 0.f, 0.f};
             float b2[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f}, c2[3] = {0.f, 0.f, 0.f};
-            int nblk = 0;
-            for (int j = T.x; j < T.y; ++j) {
-                const float *w = st_w + j * WST;
-                const float2 v = st_v[j];
-                const float wa = w[dx1] * w[8 + dy1];
-                const float wb = w[dx2] * w[8 + dy2];
-                b1[0] = fmaf(wa, v.x, b1[0]);
-                b1[1] = fmaf(wa, v.y, b1[1]);
-                b1[2] += wa;
-                b2[0] = fmaf(wb, v.x, b2[0]);
-                b2[1] = fmaf(wb, v.y, b2[1]);
-                b2[2] += wb;
-                if (++nblk == GFOLD) {
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        kahan_add(s1[k], c1[k], b1[k]);
-                        kahan_add(s2[k], c2[k], b2[k]);
-                        b1[k] = b2[k] = 0.f;
-                    }
-                    nblk = 0;
+            for (int j0 = T.x; j0 < T.y; j0 += GFOLD) {   // plain blocks of GFOLD, folded into Kahan sums
+                const int je = min(j0 + GFOLD, T.y);
+                for (int j = j0; j < je; ++j) {
+                    const float *w = st_w + j * WST;
+                    const float2 v = st_v[j];
+                    const float wa = w[dx1] * w[8 + dy1];
+                    const float wb = w[dx2] * w[8 + dy2];
+                    b1[0] = fmaf(wa, v.x, b1[0]);
+                    b1[1] = fmaf(wa, v.y, b1[1]);
+                    b1[2] += wa;
+                    b2[0] = fmaf(wb, v.x, b2[0]);
+                    b2[1] = fmaf(wb, v.y, b2[1]);
+                    b2[2] += wb;
                 }
-            }
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                kahan_add(s1[k], c1[k], b1[k]);
-                kahan_add(s2[k], c2[k], b2[k]);
+                for (int k = 0; k < 3; ++k) {
+                    kahan_add(s1[k], c1[k], b1[k]);
+                    kahan_add(s2[k], c2[k], b2[k]);
+                    b1[k] = b2[k] = 0.f;
+                }
             }
             const int cell = st_c[T.x];
             const int cx = gx0 + (cell & (TS - 1)), cy = gy0 + (cell >> 4);
@@ -538,6 +514,7 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
         }
     }
 }
+
 
 // Hermitian mirror and FP32 outputs: G(g) + conj G(-g), W(g) + W(-g).
 __global__ void k_grid_finalize(int n, const double *__restrict__ acc_re,
@@ -563,41 +540,36 @@ __global__ void k_grid_finalize(int n, const double *__restrict__ acc_re,
     }
 }
 
+
 struct PlanBufs {
-    uint32_t *keys, *hist, *offs, *bsum;
-    float4 *s_w;          // [n][4] weight records
-    uint32_t *s_idx, *s_key;
-    uint32_t *k2, *v2, *vals, *rhist, *roffs, *n_valid;
+    uint32_t *keys, *tile_hist, *k2, *v2, *rhist, *roffs, *n_valid;
+    uint32_t *s_idx;      // sorted original indices
+    float2 *s_uv;         // sorted positions
     int4 *units;
     int *n_units;
-    int64_t nkeys, n_vis;
-    int ntiles, units_cap, rtiles;
+    int64_t n_vis;
+    int ntiles, units_cap, nchunks;
 };
 
 bool plan_bufs(abs_ctx *ctx, const GridGeom &G, int64_t n_vis, PlanBufs &b) {
     b.ntiles = G.tt * G.tt;
-    b.nkeys = b.ntiles;
     b.n_vis = n_vis;
     b.units_cap = (int)(b.ntiles + cdiv(n_vis, UMAX) + 1);
     const int64_t nv = n_vis > 0 ? n_vis : 1;
+    b.nchunks = (int)cdiv(nv, RT);
     b.keys = (uint32_t *)workspace(ctx, "plan.keys", sizeof(uint32_t) * nv);
-    b.hist = (uint32_t *)workspace(ctx, "plan.hist", sizeof(uint32_t) * b.nkeys);
-    b.offs = (uint32_t *)workspace(ctx, "plan.offs", sizeof(uint32_t) * b.nkeys);
-    b.bsum = (uint32_t *)workspace(ctx, "plan.bsum", sizeof(uint32_t) * (cdiv(b.nkeys, 4096) + 1));
-    b.s_w = (float4 *)workspace(ctx, "plan.s_w", sizeof(float4) * 4 * nv);
-    b.s_idx = (uint32_t *)workspace(ctx, "plan.s_idx", sizeof(uint32_t) * nv);
-    b.s_key = (uint32_t *)workspace(ctx, "plan.s_key", sizeof(uint32_t) * nv);
-    b.units = (int4 *)workspace(ctx, "plan.units", sizeof(int4) * b.units_cap);
-    b.n_units = (int *)workspace(ctx, "plan.n_units", sizeof(int));
-    b.rtiles = (int)cdiv(nv, RTILE);
+    b.tile_hist = (uint32_t *)workspace(ctx, "plan.tile_hist", sizeof(uint32_t) * b.ntiles);
     b.k2 = (uint32_t *)workspace(ctx, "plan.k2", sizeof(uint32_t) * nv);
     b.v2 = (uint32_t *)workspace(ctx, "plan.v2", sizeof(uint32_t) * nv);
-    b.vals = (uint32_t *)workspace(ctx, "plan.vals", sizeof(uint32_t) * nv);
-    b.rhist = (uint32_t *)workspace(ctx, "plan.rhist", sizeof(uint32_t) * 256 * b.rtiles);
-    b.roffs = (uint32_t *)workspace(ctx, "plan.roffs", sizeof(uint32_t) * 256 * b.rtiles);
+    b.rhist = (uint32_t *)workspace(ctx, "plan.rhist", sizeof(uint32_t) * ((size_t)1 << DMAX) * b.nchunks);
+    b.roffs = (uint32_t *)workspace(ctx, "plan.roffs", sizeof(uint32_t) * ((size_t)1 << DMAX) * b.nchunks);
     b.n_valid = (uint32_t *)workspace(ctx, "plan.n_valid", sizeof(uint32_t));
-    return b.keys && b.hist && b.offs && b.bsum && b.s_w && b.s_idx && b.s_key && b.units &&
-           b.n_units && b.k2 && b.v2 && b.vals && b.rhist && b.roffs && b.n_valid;
+    b.s_idx = (uint32_t *)workspace(ctx, "plan.s_idx", sizeof(uint32_t) * nv);
+    b.s_uv = (float2 *)workspace(ctx, "plan.s_uv", sizeof(float2) * nv);
+    b.units = (int4 *)workspace(ctx, "plan.units", sizeof(int4) * b.units_cap);
+    b.n_units = (int *)workspace(ctx, "plan.n_units", sizeof(int));
+    return b.keys && b.tile_hist && b.k2 && b.v2 && b.rhist && b.roffs && b.n_valid && b.s_idx &&
+           b.s_uv && b.units && b.n_units;
 }
 
 }  // namespace
@@ -614,42 +586,39 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
     const GridGeom G = geom(s);
     PlanBufs b;
     if (!plan_bufs(ctx, G, n_vis, b)) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
-    const int64_t rlen = (int64_t)256 * b.rtiles;
-    const int64_t scan_len = std::max<int64_t>(b.nkeys, rlen);
-    uint32_t *bsum = (uint32_t *)workspace(ctx, "plan.bsum2", sizeof(uint32_t) * (cdiv(scan_len, 4096) + 1));
+    const uint32_t key_none = (uint32_t)b.ntiles;     // invalid visibilities sort last
+    int bits = 1;
+    while (((uint64_t)1 << bits) <= (uint64_t)key_none) ++bits;
+    const int passes = (bits + DMAX - 1) / DMAX;
+    if (passes > 2) return fail(ctx, ABS_ERR_UNSUPPORTED, "uv tile count beyond two radix passes");
+    const int dw = (bits + passes - 1) / passes;
+    const int64_t rlen = ((int64_t)1 << dw) * b.nchunks;
+    uint32_t *bsum = (uint32_t *)workspace(ctx, "plan.bsum", sizeof(uint32_t) * (cdiv(rlen, 4096) + 1));
     if (!bsum) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
     cudaStream_t st = ctx->stream;
     StageTimer timer(ctx, "grid_plan");
-    cudaMemsetAsync(b.hist, 0, sizeof(uint32_t) * b.nkeys, st);
-    const int grid_v = (int)std::min<int64_t>(cdiv(std::max<int64_t>(n_vis, 1), 256), ctx->sm_count * 16);
-    const uint32_t key_none = (uint32_t)b.nkeys;     // invalid visibilities sort last
+    cudaMemsetAsync(b.tile_hist, 0, sizeof(uint32_t) * b.ntiles, st);
     if (n_vis > 0)
-        k_plan_keys<<<grid_v, 256, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, b.vals, b.hist, key_none);
-    k_units<<<1, 1024, 0, st>>>(b.hist, b.ntiles, b.units, b.n_units, b.units_cap, b.n_valid);
+        k_plan_keys<<<b.nchunks, 256, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, b.tile_hist, key_none, dw,
+                                               b.nchunks, b.rhist);
+    k_units<<<1, 1024, 0, st>>>(b.tile_hist, b.ntiles, b.units, b.n_units, b.units_cap, b.n_valid);
     if (n_vis > 0) {
-        // stable sort of (tile, index); ping-pong keys/vals <-> k2/v2, result in k2/v2
-        // or keys/vals; k_plan_units then sorts each unit by cell into s_key/s_idx
-        int bits = 1;
-        while (((uint64_t)1 << bits) <= (uint64_t)key_none) ++bits;
-        const int passes = (bits + 7) / 8;
-        uint32_t *ki = b.keys, *vi = b.vals, *ko = b.k2, *vo = b.v2;
+        // stable sort of (tile, index): keys -> (k2, v2) -> ... -> (s_idx, s_uv)
+        const uint32_t *ki = b.keys, *vi = nullptr;
+        uint32_t *ko = b.k2, *vo = b.v2;
+        uint32_t *kalt = b.keys, *valt = b.s_idx;   // ping-pong partners after the first pass
         for (int ps = 0; ps < passes; ++ps) {
-            k_radix_hist<<<b.rtiles, 256, 0, st>>>(ki, n_vis, 8 * ps, b.rtiles, b.rhist);
+            const bool last = ps == passes - 1;
+            if (ps > 0) k_radix_hist<<<b.nchunks, 256, 0, st>>>(ki, n_vis, dw * ps, dw, b.nchunks, b.rhist);
             scan_u32(st, b.rhist, rlen, b.roffs, bsum);
-            k_radix_scatter<<<b.rtiles, 256, 0, st>>>(ki, vi, n_vis, 8 * ps, b.rtiles, b.roffs, ko, vo);
-            if (ps == 0) {
-                ki = b.k2;
-                vi = b.v2;
-                ko = b.keys;
-                vo = b.vals;
-            } else {
-                std::swap(ki, ko);
-                std::swap(vi, vo);
-            }
+            k_radix_scatter<<<b.nchunks, 256, 0, st>>>(ki, vi, n_vis, dw * ps, dw, b.nchunks, b.roffs,
+                                                       last ? nullptr : ko, last ? b.s_idx : vo,
+                                                       (const float2 *)d_uv, last ? b.s_uv : nullptr);
+            ki = ko;
+            vi = vo;
+            std::swap(ko, kalt);
+            std::swap(vo, valt);
         }
-        // ki/vi now hold the tile-sorted (tile, index) pairs
-        const int ub = std::min(b.units_cap, ctx->sm_count * 8);
-        k_plan_units<<<ub, PT, 0, st>>>(G, b.units, b.n_units, (const float2 *)d_uv, vi, b.s_key, b.s_idx, b.s_w);
     }
     return check_launch(ctx, "grid plan");
 }
@@ -678,9 +647,8 @@ abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, c
     if (n_vis > 0) {
         StageTimer timer(ctx, "grid");
         const int blocks = std::min(b.units_cap, ctx->sm_count * 4);
-        k_grid<<<blocks, GT, GRID_SMEM, st>>>(G, b.units, b.n_units, b.s_w, b.s_idx, b.s_key,
-                                           (const float2 *)d_vis, acc, acc + cells,
-                                           acc + 2 * cells, hit);
+        k_grid<<<blocks, GT, GRID_SMEM, st>>>(G, b.units, b.n_units, b.s_uv, b.s_idx, (const float2 *)d_vis, acc,
+                                           acc + cells, acc + 2 * cells, hit);
     }
     {
         StageTimer timer(ctx, "grid_finalize");

@@ -109,6 +109,38 @@ def test_grid_kernel_variants(ctx, kernel, sigma, radius):
     assert_grid_parity(G, W, M, est, grid_abs_bound(wl.n_grid, wl.du, inp.uv, inp.vis, kernel, sigma, radius))
 
 
+def test_grid_parity_two_radix_passes(ctx):
+    """The 2048^2 grid of the 4M-visibility workload: 16,641 uv tiles, so the
+    tile sort takes two radix passes."""
+    inp = inputs(2)
+    wl = inp.wl
+    cfg = absmod.Config.from_workload(wl)
+    gr = oracle.grid(wl.n_grid, wl.du, inp.uv, inp.vis)
+    G, W, M, _ = gpu_grid(ctx, cfg, inp.uv, inp.vis)
+
+    class _E:
+        grid = gr
+    assert_grid_parity(G, W, M, _E, grid_abs_bound(wl.n_grid, wl.du, inp.uv, inp.vis))
+
+
+def test_grid_dense_cells(ctx):
+    """Thousands of visibilities inside one cell and one tile (runs longer
+    than a task, tiles longer than a work unit), next to sparse ones."""
+    inp = inputs(0)
+    wl = inp.wl
+    rng = np.random.default_rng(7)
+    c0 = np.array([9.0, -4.0]) * wl.du
+    pile = c0 + rng.uniform(-0.49, 0.49, (3000, 2)) * wl.du
+    near = c0 + rng.uniform(-7.5, 7.5, (2500, 2)) * wl.du
+    uv = np.concatenate([inp.uv, pile, near]).astype(np.float32)
+    vis = np.concatenate([inp.vis, (rng.standard_normal(5500) + 1j * rng.standard_normal(5500))
+                          .astype(np.complex64)])
+    cfg = absmod.Config.from_workload(wl)
+    est = oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, uv, vis)
+    G, W, M, _ = gpu_grid(ctx, cfg, uv, vis)
+    assert_grid_parity(G, W, M, est, grid_abs_bound(wl.n_grid, wl.du, uv, vis))
+
+
 def test_grid_skips_nonfinite_and_far_baselines(ctx):
     inp = inputs(0)
     wl = inp.wl
