@@ -116,6 +116,34 @@ struct Fams {
 
 // Pass 1 (one warp per (ring, row)): filled, hole and annulus cells; FP64 sum
 // of |g| over the filled ones.  rowcnt is [NFAM][nb * rows].
+// sqrt(v) of a non-negative integer v < 2^31 as a double-float pair h + l
+// (relative error about 2^-46), with 32-bit arithmetic only: GB300's FP64 pipe
+// (which also converts 64-bit integers) is too narrow for a square root per
+// cell.  v = vf + vr exactly; h is the correctly rounded sqrtf(vf), whose
+// residual vf - h^2 one FMA gives exactly; l = (v - h^2) / (2h) is the
+// first-order (Newton) correction.
+__device__ __forceinline__ void df_sqrt_int(int32_t v, float &h, float &l) {
+    const float vf = (float)v;
+    const float vr = (float)(v - (int32_t)vf);     // exact: |v - vf| <= ulp(vf) / 2 <= 64
+    h = sqrtf(vf);
+    if (h == 0.f) {
+        l = 0.f;
+        return;
+    }
+    const float r = __fadd_rn(fmaf(-h, h, vf), vr);
+    l = __fdiv_rn(r, __fmul_rn(2.f, h));
+}
+
+// (sh, sl) += (h, l) in double-float (TwoSum of the high parts, then the low parts).
+__device__ __forceinline__ void df_add(float &sh, float &sl, float h, float l) {
+    const float t = __fadd_rn(sh, h);
+    const float bp = __fsub_rn(t, sh);
+    const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(h, bp));
+    const float lo = __fadd_rn(e, __fadd_rn(sl, l));
+    sh = __fadd_rn(t, lo);                          // Fast2Sum renormalisation (|t| >= |lo|)
+    sl = __fsub_rn(lo, __fsub_rn(sh, t));
+}
+
 __global__ void k_ring_rows(CountGeom G, const int64_t *__restrict__ q, const uint8_t *__restrict__ mask,
                             uint32_t *__restrict__ rowcnt, double *__restrict__ rowlen) {
     const int rows = 2 * G.R + 1;
@@ -126,7 +154,7 @@ __global__ void k_ring_rows(CountGeom G, const int64_t *__restrict__ q, const ui
     const RowSpan sp = row_span(G, q[m], q[m + 1], y);
     const int len = span_len(sp);
     uint32_t c = 0;
-    double sum = 0.0;
+    float sh = 0.f, sl = 0.f;   // sum of |g| as a double-float pair
     for (int t0 = 0; t0 < len; t0 += 32) {
         const int t = t0 + lane;
         bool on = false;
@@ -136,15 +164,22 @@ __global__ void k_ring_rows(CountGeom G, const int64_t *__restrict__ q, const ui
             on = mask[cell_index(G.n, x, y)] != 0;
         }
         c += __popc(__ballot_sync(FULL, on));
-        if (on) sum += sqrt((double)x * x + (double)y * y);
+        if (on) {
+            float h, l;
+            df_sqrt_int(x * x + y * y, h, l);   // |x|, |y| <= n/2 <= 4096
+            df_add(sh, sl, h, l);
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(FULL, sh, o), ol = __shfl_xor_sync(FULL, sl, o);
+        df_add(sh, sl, oh, ol);
+    }
     if (lane == 0) {
         rowcnt[e] = c;
         rowcnt[nrow + e] = (uint32_t)len - c;
         rowcnt[2 * nrow + e] = (uint32_t)len;
-        rowlen[e] = sum;
+        rowlen[e] = (double)sh + (double)sl;
     }
 }
 
@@ -245,8 +280,15 @@ __global__ void __launch_bounds__(1024) k_count_items(int nb, const int32_t *__r
         wd += (unsigned long long)(cF[a] / 2) * cF[b];
         we += (unsigned long long)(cH[a] / 2) * cA[b] + 2ull * (cF[a] / 2) * cH[b];
     }
-    atomicAdd(&wdir_s, wd);
-    atomicAdd(&wexc_s, we);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {   // one shared-memory add per warp, not per thread
+        wd += __shfl_xor_sync(FULL, wd, o);
+        we += __shfl_xor_sync(FULL, we, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&wdir_s, wd);
+        atomicAdd(&wexc_s, we);
+    }
     __syncthreads();
     if (threadIdx.x == 0) use_holes_s = wexc_s < wdir_s ? 1 : 0;
     __syncthreads();
@@ -261,13 +303,17 @@ __global__ void __launch_bounds__(1024) k_count_items(int nb, const int32_t *__r
         jobs[nj++] = JOB_DIRECT;
     }
     if (need_full) jobs[nj++] = JOB_FULL;
+    // per batch of 1024 pairs: chunk counts, their prefix, then every thread
+    // writes items of the batch (pair found by binary search over the prefix)
+    __shared__ int b_pos[1025];
+    __shared__ int b_ab[1024], b_nic[1024];
     for (int jj = 0; jj < nj; ++jj) {
         const int job = jobs[jj];
         const int lst = job_map_a(job) ? 1 : 0;
         const int32_t *cx = counts + job_x(job) * nb, *cy = counts + job_y(job) * nb;
         for (int p0 = 0; p0 < npair; p0 += blockDim.x) {
             const int pr = p0 + threadIdx.x;
-            int a = 0, b = 0, n_oc = 0, n_ic = 1, nchunks = 0;
+            int a = 0, b = 0, n_ic = 1, nchunks = 0;
             bool outer_x = false;
             if (pr < npair) {
                 int rem = pr;
@@ -276,7 +322,7 @@ __global__ void __launch_bounds__(1024) k_count_items(int nb, const int32_t *__r
                 const int hx = cx[a] / 2, ny = cy[b];
                 outer_x = hx >= ny;
                 const int no = outer_x ? hx : ny, ni = outer_x ? ny : hx;
-                n_oc = (no + chunk - 1) / chunk;
+                const int n_oc = (no + chunk - 1) / chunk;
                 n_ic = (ni + INNER - 1) / INNER;
                 nchunks = ni > 0 ? n_oc * n_ic : 0;
             }
@@ -293,13 +339,25 @@ __global__ void __launch_bounds__(1024) k_count_items(int nb, const int32_t *__r
                 if (w < warp) before += wsum[w];
                 tot += wsum[w];
             }
-            const int pos = carry_s[lst] + before + x - nchunks;
+            b_pos[threadIdx.x] = before + x - nchunks;
+            if (threadIdx.x == 0) b_pos[blockDim.x] = tot;
+            b_ab[threadIdx.x] = a | b << 8 | (outer_x ? 1 << 16 : 0);
+            b_nic[threadIdx.x] = n_ic;
+            __syncthreads();
+            const int base = carry_s[lst];
             int4 *items = lst ? items1 : items0;
-            for (int c = 0; c < nchunks; ++c) {
-                const int oc = c / n_ic, ic = c - oc * n_ic;
-                if (pos + c < cap)
-                    items[pos + c] = make_int4(a, b, oc * chunk,
-                                               (ic * INNER) | (job << 27) | (outer_x ? (int)0x80000000u : 0));
+            for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+                int lo = 0, hi = (int)blockDim.x - 1;   // last pair q with b_pos[q] <= t
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (b_pos[mid] <= t) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int c = t - b_pos[lo], nic = b_nic[lo], ab = b_ab[lo];
+                const int oc = c / nic, ic = c - oc * nic;
+                if (base + t < cap)
+                    items[base + t] = make_int4(ab & 255, (ab >> 8) & 255, oc * chunk,
+                                                (ic * INNER) | (job << 27) | ((ab >> 16) ? (int)0x80000000u : 0));
             }
             __syncthreads();
             if (threadIdx.x == 0) carry_s[lst] += tot;

@@ -34,7 +34,7 @@ constexpr unsigned FULL = 0xffffffffu;
 
 struct GridGeom {
     int n, half, r, ks, tt, off, kernel;
-    float du, s_hi, s_lo;
+    float du, inv_du, s_hi, s_lo;
 };
 
 GridGeom geom(const Setup &s) {
@@ -47,6 +47,7 @@ GridGeom geom(const Setup &s) {
     g.off = s.half + g.r;
     g.kernel = s.kernel;
     g.du = s.du;
+    g.inv_du = (float)(1.0 / (double)s.du);
     g.s_hi = s.s_hi;
     g.s_lo = s.s_lo;
     return g;
@@ -113,12 +114,19 @@ __global__ void __launch_bounds__(256) k_plan_keys(GridGeom G, int64_t n_vis, co
     for (int d = threadIdx.x; d < nb; d += 256) h[d] = 0;
     __syncthreads();
     const int64_t c0 = (int64_t)blockIdx.x * RT;
+    float2 pv[RT / 256];   // all loads of the chunk in flight at once
+#pragma unroll
+    for (int k = 0; k < RT / 256; ++k) {
+        const int64_t i = c0 + k * 256 + threadIdx.x;
+        pv[k] = i < n_vis ? uv[i] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
     for (int k = 0; k < RT / 256; ++k) {
         const int64_t i = c0 + k * 256 + threadIdx.x;
         const bool on = i < n_vis;
         uint32_t key = 0xffffffffu;
         if (on) {
-            key = tile_key(G, uv[i], key_none);
+            key = tile_key(G, pv[k], key_none);
             keys[i] = key;
         }
         const unsigned peers = __match_any_sync(FULL, key);
@@ -176,11 +184,19 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t *__restric
         for (int w = 0; w < 8; ++w) wloc[w][d] = 0;
     }
     __syncthreads();
+    constexpr int NR = RT / 8 / 32;   // rounds per warp
     const int64_t w0 = (int64_t)blockIdx.x * RT + warp * (RT / 8);
-    for (int k = 0; k < RT / 8 / 32; ++k) {
+    uint32_t kv[NR];                  // the warp's keys, loaded once with all loads in flight
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int64_t e = w0 + k * 32 + lane;
+        kv[k] = e < n ? kin[e] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
         const int64_t e = w0 + k * 32 + lane;
         const bool on = e < n;
-        const uint32_t d = on ? (kin[e] >> shift) & dmask : 0x10000u + lane;
+        const uint32_t d = on ? (kv[k] >> shift) & dmask : 0x10000u + lane;
         const unsigned peers = __match_any_sync(FULL, d);
         if (on && lane == __ffs(peers) - 1) wloc[warp][d] += (uint16_t)__popc(peers);
         __syncwarp();
@@ -196,17 +212,28 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t *__restric
         }
     }
     __syncthreads();
-    for (int k = 0; k < RT / 8 / 32; ++k) {
+    uint32_t vv[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int64_t e = w0 + k * 32 + lane;
+        vv[k] = vin ? (e < n ? vin[e] : 0u) : (uint32_t)e;
+    }
+    float2 pv[NR];
+    if (uv_out) {
+#pragma unroll
+        for (int k = 0; k < NR; ++k) pv[k] = w0 + k * 32 + lane < n ? uv[vv[k]] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
         const int64_t e = w0 + k * 32 + lane;
         const bool on = e < n;
-        const uint32_t key = on ? kin[e] : 0u;
+        const uint32_t key = kv[k];
         const uint32_t d = on ? (key >> shift) & dmask : 0x10000u + lane;
         const unsigned peers = __match_any_sync(FULL, d);
         if (on) {
             const uint32_t pos = base[d] + wloc[warp][d] + (uint32_t)__popc(peers & ((1u << lane) - 1u));
-            const uint32_t val = vin ? vin[e] : (uint32_t)e;
-            vout[pos] = val;
-            if (uv_out) uv_out[pos] = uv[val];
+            vout[pos] = vv[k];
+            if (uv_out) uv_out[pos] = pv[k];
             else kout[pos] = key;
         }
         __syncwarp();
@@ -323,19 +350,46 @@ __global__ void __launch_bounds__(1024) k_units(const uint32_t *__restrict__ his
 // (per-warp counts, prefix over (cell, warp), ranked placement), each
 // visibility's 2 (2r+1) one-dimensional weights are formed once, and the
 // unit is cut into tasks: runs of at most CHUNK visibilities that share a
-// cell.  A warp takes a task; lane k owns footprint cells k and k + 32 of the
-// (2r+1)^2 around the run's cell and sums w = wx[dx] wy[dy] times V over the
-// run (plain FP32 blocks of GFOLD folded into Kahan sums, in input order),
-// then adds its cells to the FP64 grid.  No shared accumulators: runs never
-// wait on one another, whether the tile is dense (long runs) or sparse.
+// cell.  A warp takes a task; lane (dy, q) owns the footprint cells
+// (2q, dy) and (2q+1, dy) of the (2r+1)^2 around the run's cell and sums
+// w = wx wy, w Re V, w Im V over the run with packed FP32x2 arithmetic
+// (plain blocks of GFOLD folded into Kahan sums, input order), then adds its
+// cells to the FP64 grid.  No shared accumulators: runs never wait on one
+// another, whether the tile is dense (long runs) or sparse.
+//
+// Staged record of a visibility (RS floats): wx[0..7] (zero beyond 2r),
+// (wy[d], wy[d]) for d = 0..6, two pad floats, (Re V, Re V, Im V, Im V).
 constexpr int GT = 256;          // threads per gridding CTA (8 warps x UMAX/8 items)
-constexpr int WST = 17;          // floats per staged weight record (odd: spreads banks)
+constexpr int RS = 28;           // floats per staged record
+constexpr int R_WY = 8, R_V = 24;
 constexpr int GFOLD = 8;
 constexpr int CHUNK = 64;        // visibilities per task at most
 constexpr int MAXTASK = UMAX / CHUNK + 256;   // sum over cells of ceil(run / CHUNK)
 static_assert(UMAX == 8 * 64, "the in-unit sort gives each of 8 warps two rounds of 32 items");
-constexpr size_t GRID_SMEM = UMAX * (sizeof(float) * WST + sizeof(float2)) + sizeof(int2) * MAXTASK +
+constexpr size_t GRID_SMEM = UMAX * (sizeof(float) * RS + sizeof(float2)) + sizeof(int2) * MAXTASK +
                              sizeof(uint16_t) * 8 * 256 + sizeof(uint32_t) * 260 + 2 * UMAX;
+
+// The double with the value of x, built with integer operations only (GB300's
+// FP64 pipe is narrow: one hardware conversion per flushed value is what kept
+// it busy).  Exact for normal, infinite and NaN x; subnormal x (|x| < 2^-126)
+// become a zero of the same sign.
+__device__ __forceinline__ double widen(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t e = (b >> 23) & 255u;
+    const uint32_t sign = b & 0x80000000u;
+    const uint32_t eh = e == 255u ? 2047u : e + (1023u - 127u);
+    const uint32_t hi = e == 0u ? sign : sign | (eh << 20) | ((b >> 3) & 0xFFFFFu);
+    const uint32_t lo = e == 0u ? 0u : b << 29;
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+__device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 x) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    const float2 y = __ffma2_rn(c, m1, x);                   // x - c
+    const float2 t = __fadd2_rn(s, y);
+    c = __ffma2_rn(y, m1, __ffma2_rn(s, m1, t));             // (t - s) - y
+    s = t;
+}
 
 __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict__ units,
                                              const int *__restrict__ n_units,
@@ -347,9 +401,9 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
                                              double *__restrict__ acc_w,
                                              uint8_t *__restrict__ hit) {
     extern __shared__ __align__(16) uint8_t dsm[];
-    float *st_w = (float *)dsm;                                        // [UMAX][WST] 1-D weights
-    float2 *st_v = (float2 *)(st_w + UMAX * WST);                      // [UMAX] visibilities
-    int2 *task = (int2 *)(st_v + UMAX);                                // [MAXTASK] (first, end)
+    float *st = (float *)dsm;                                          // [UMAX][RS] staged records
+    float2 *in_q = (float2 *)(st + UMAX * RS);                         // [UMAX] u/dU, v/dU, input order
+    int2 *task = (int2 *)(in_q + UMAX);                                // [MAXTASK] (first, end)
     uint16_t *wloc = (uint16_t *)(task + MAXTASK);                     // [8][256] per-warp cell counts
     uint32_t *cstart = (uint32_t *)(wloc + 8 * 256);                   // [257] first item of each cell
     uint8_t *in_c = (uint8_t *)(cstart + 260);                         // [UMAX] cell, input order
@@ -357,13 +411,11 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
     __shared__ uint32_t sh_scan[32];
     __shared__ int ntask_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = GT / 32;
-    const int r = G.r, fw = 2 * r + 1, nfp = fw * fw;
+    const int r = G.r, fw = 2 * r + 1;
     const bool gauss = G.kernel == ABS_KERNEL_GAUSS;
-    // this lane's two footprint cells
-    const int k1 = lane, k2 = lane + 32;
-    const bool on1 = k1 < nfp, on2 = k2 < nfp;
-    const int dx1 = on1 ? k1 % fw : 0, dy1 = on1 ? k1 / fw : 0;
-    const int dx2 = on2 ? k2 % fw : 0, dy2 = on2 ? k2 / fw : 0;
+    // this lane's footprint cells: (2q, dy) and (2q + 1, dy)
+    const int dy = lane >> 2, q2 = 2 * (lane & 3);
+    const bool on_a = lane < 28 && dy < fw && q2 < fw, on_b = on_a && q2 + 1 < fw;
     const int nu = *n_units;
     for (int u = blockIdx.x; u < nu; u += gridDim.x) {
         const int4 U = units[u];
@@ -385,6 +437,7 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
                 const int ky = (int)floorf(__fadd_rn(qy, 0.5f)) + G.off;
                 c = (uint32_t)((ky - ty * TS) * TS + (kx - tx * TS));
                 in_c[t] = (uint8_t)c;
+                in_q[t] = make_float2(qx, qy);
             }
             const unsigned peers = __match_any_sync(FULL, c);
             if (on && lane == __ffs(peers) - 1) wloc[warp * 256 + c] += (uint16_t)__popc(peers);
@@ -419,21 +472,32 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
             if (on) {
                 const int pos = (int)wloc[warp * 256 + c] + __popc(peers & ((1u << lane) - 1u));
                 const float2 p = s_uv[U.y + t];
-                const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
-                const float cxf = floorf(__fadd_rn(qx, 0.5f)), cyf = floorf(__fadd_rn(qy, 0.5f));
-                const float fxh = __fsub_rn(qx, cxf), fyh = __fsub_rn(qy, cyf);
-                const float fxl = __fdiv_rn(fmaf(-qx, G.du, p.x), G.du);
-                const float fyl = __fdiv_rn(fmaf(-qy, G.du, p.y), G.du);
-                float *w = st_w + pos * WST;
+                const float2 qq = in_q[t];
+                const float cxf = floorf(__fadd_rn(qq.x, 0.5f)), cyf = floorf(__fadd_rn(qq.y, 0.5f));
+                const float fxh = __fsub_rn(qq.x, cxf), fyh = __fsub_rn(qq.y, cyf);
+                // the division residual (exact by FMA) over dU: a correction of
+                // relative size 2^-24, so one rounding of its own does not matter
+                const float fxl = __fmul_rn(fmaf(-qq.x, G.du, p.x), G.inv_du);
+                const float fyl = __fmul_rn(fmaf(-qq.y, G.du, p.y), G.inv_du);
+                float *rec = st + pos * RS;
+                float wx[8], wy[8];
 #pragma unroll
-                for (int k = 0; k < FWMAX; ++k) {
+                for (int k = 0; k < 8; ++k) {
+                    wx[k] = wy[k] = 0.f;
                     if (k < fw) {
                         const float d = (float)(k - r);
-                        w[k] = gauss ? wexp(d, fxh, fxl, G.s_hi, G.s_lo) : 1.f;
-                        w[8 + k] = gauss ? wexp(d, fyh, fyl, G.s_hi, G.s_lo) : 1.f;
+                        wx[k] = gauss ? wexp(d, fxh, fxl, G.s_hi, G.s_lo) : 1.f;
+                        wy[k] = gauss ? wexp(d, fyh, fyl, G.s_hi, G.s_lo) : 1.f;
                     }
                 }
-                st_v[pos] = vis[s_idx[U.y + t]];
+                ((float4 *)rec)[0] = make_float4(wx[0], wx[1], wx[2], wx[3]);
+                ((float4 *)rec)[1] = make_float4(wx[4], wx[5], wx[6], wx[7]);
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    ((float4 *)(rec + R_WY))[k] = make_float4(wy[2 * k], wy[2 * k], wy[2 * k + 1], wy[2 * k + 1]);
+                ((float2 *)(rec + R_WY))[6] = make_float2(wy[6], wy[6]);
+                const float2 v = vis[s_idx[U.y + t]];
+                ((float4 *)(rec + R_V))[0] = make_float4(v.x, v.x, v.y, v.y);
                 st_c[pos] = (uint8_t)c;
             }
             __syncwarp();
@@ -471,50 +535,54 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
         __syncthreads();
         const int ntask = ntask_s;
         const int gx0 = tx * TS - G.off, gy0 = ty * TS - G.off;
-        for (int tk = warp; tk < ntask; tk += nwarps) {
-            const int2 T = task[tk];
-            float b1[3] = {0.f, 0.f, 0.f}, s1[3] = {0.f, 0.f, 0.f}, c1[3] = {0.f, 0.f, 0.f};
-            float b2[3] = {0.f, 0.f, 0.f}, s2[3] = {0.f, 0.f, 0.f}, c2[3] = {0.f, 0.f, 0.f};
-            for (int j0 = T.x; j0 < T.y; j0 += GFOLD) {   // plain blocks of GFOLD, folded into Kahan sums
-                const int je = min(j0 + GFOLD, T.y);
-                for (int j = j0; j < je; ++j) {
-                    const float *w = st_w + j * WST;
-                    const float2 v = st_v[j];
-                    const float wa = w[dx1] * w[8 + dy1];
-                    const float wb = w[dx2] * w[8 + dy2];
-                    b1[0] = fmaf(wa, v.x, b1[0]);
-                    b1[1] = fmaf(wa, v.y, b1[1]);
-                    b1[2] += wa;
-                    b2[0] = fmaf(wb, v.x, b2[0]);
-                    b2[1] = fmaf(wb, v.y, b2[1]);
-                    b2[2] += wb;
+        if (on_a) {   // lanes without a footprint cell take no part in the sums
+            for (int tk = warp; tk < ntask; tk += nwarps) {
+                const int2 T = task[tk];
+                const float2 z = make_float2(0.f, 0.f);
+                float2 sre = z, cre = z, sim = z, cim = z, sw = z, cw = z;
+                for (int j0 = T.x; j0 < T.y; j0 += GFOLD) {   // plain blocks of GFOLD, folded into Kahan sums
+                    const int je = min(j0 + GFOLD, T.y);
+                    float2 bre = z, bim = z, bw = z;
+                    for (int j = j0; j < je; ++j) {
+                        const float *rec = st + j * RS;
+                        const float2 wxp = *(const float2 *)(rec + q2);
+                        const float2 wyy = *(const float2 *)(rec + R_WY + 2 * dy);
+                        const float4 vv = *(const float4 *)(rec + R_V);
+                        const float2 w = __fmul2_rn(wxp, wyy);
+                        bre = __ffma2_rn(w, make_float2(vv.x, vv.y), bre);
+                        bim = __ffma2_rn(w, make_float2(vv.z, vv.w), bim);
+                        bw = __fadd2_rn(w, bw);
+                    }
+                    kahan_add2(sre, cre, bre);
+                    kahan_add2(sim, cim, bim);
+                    kahan_add2(sw, cw, bw);
                 }
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    kahan_add(s1[k], c1[k], b1[k]);
-                    kahan_add(s2[k], c2[k], b2[k]);
-                    b1[k] = b2[k] = 0.f;
+                const int cell = st_c[T.x];
+                const int gy = gy0 + (cell >> 4) + dy - r;
+                const int gxa = gx0 + (cell & (TS - 1)) + q2 - r;
+                if (gy < -G.half || gy > G.half) continue;
+                // the run's sums s - c, rounded once to FP32 (relative 2^-24 of the run)
+                const float2 m1 = make_float2(-1.f, -1.f);
+                const float2 vre = __ffma2_rn(cre, m1, sre), vim = __ffma2_rn(cim, m1, sim);
+                const float2 vw = __ffma2_rn(cw, m1, sw);
+                if (gxa >= -G.half && gxa <= G.half) {
+                    const int64_t pidx = cell_index(G.n, gxa, gy);
+                    atomicAdd(&acc_re[pidx], widen(vre.x));
+                    atomicAdd(&acc_im[pidx], widen(vim.x));
+                    atomicAdd(&acc_w[pidx], widen(vw.x));
+                    hit[pidx] = 1;
                 }
-            }
-            const int cell = st_c[T.x];
-            const int cx = gx0 + (cell & (TS - 1)), cy = gy0 + (cell >> 4);
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                if (h == 0 ? !on1 : !on2) continue;
-                const int gx = cx + (h == 0 ? dx1 : dx2) - r, gy = cy + (h == 0 ? dy1 : dy2) - r;
-                if (gx < -G.half || gx > G.half || gy < -G.half || gy > G.half) continue;
-                const float *S = h == 0 ? s1 : s2;
-                const float *C = h == 0 ? c1 : c2;
-                const int64_t pidx = cell_index(G.n, gx, gy);
-                atomicAdd(&acc_re[pidx], (double)S[0] - (double)C[0]);
-                atomicAdd(&acc_im[pidx], (double)S[1] - (double)C[1]);
-                atomicAdd(&acc_w[pidx], (double)S[2] - (double)C[2]);
-                hit[pidx] = 1;
+                if (on_b && gxa + 1 >= -G.half && gxa + 1 <= G.half) {
+                    const int64_t pidx = cell_index(G.n, gxa + 1, gy);
+                    atomicAdd(&acc_re[pidx], widen(vre.y));
+                    atomicAdd(&acc_im[pidx], widen(vim.y));
+                    atomicAdd(&acc_w[pidx], widen(vw.y));
+                    hit[pidx] = 1;
+                }
             }
         }
     }
 }
-
 
 // Hermitian mirror and FP32 outputs: G(g) + conj G(-g), W(g) + W(-g).
 __global__ void k_grid_finalize(int n, const double *__restrict__ acc_re,
@@ -646,7 +714,8 @@ abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, c
     }
     if (n_vis > 0) {
         StageTimer timer(ctx, "grid");
-        const int blocks = std::min(b.units_cap, ctx->sm_count * 4);
+        const int blocks = std::min(b.units_cap, ctx->sm_count * 3);
+        cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRID_SMEM);
         k_grid<<<blocks, GT, GRID_SMEM, st>>>(G, b.units, b.n_units, b.s_uv, b.s_idx, (const float2 *)d_vis, acc,
                                            acc + cells, acc + 2 * cells, hit);
     }

@@ -5,12 +5,14 @@
 // row and multiplied into each D_k of the row (the contraction
 // C[(i,j), k] = sum_p (D_i D_j)(p) D_k(p)).
 //
-// A CTA owns a group of up to TG consecutive triplets and a contiguous range
-// of pixels.  It stages the fields of PC pixels at a time in shared memory
-// (all rings, coalesced float4 loads); each warp takes a row segment of the
-// group and accumulates 8 triplets at a time over the staged pixels (lane ->
-// pixel, FP32), reduces across the warp, and adds the result into an FP64
-// per-triplet accumulator in shared memory.  Per-CTA partial sums go to
+// A CTA owns a contiguous range of pixels, staged in shared memory for all
+// rings (coalesced loads, rows padded so that lanes on different rings read
+// different banks).  Lane <-> triplet: each warp takes 32 consecutive
+// triplets and every lane walks the staged pixels four at a time, forming
+// (D_i D_j) D_k with packed FP32x2 multiplies and fused multiply-adds into a
+// float2 partial sum, folded every FOLD steps into a double-float (FP32
+// pair, TwoSum) accumulator.  No
+// cross-lane reduction is needed.  Per-CTA partial sums go to
 // [split][triplet] and a second kernel adds the splits in a fixed order (so
 // the result does not depend on scheduling) and applies N^-2 in FP64.
 //
@@ -22,137 +24,148 @@
 namespace absk {
 namespace {
 
-constexpr int TG = 1024;       // triplets per CTA group
-constexpr int TT = 512;        // threads per CTA
-constexpr int KB = 8;          // triplets per warp pass
+constexpr int FOLD = 8;        // 4-pixel steps per FP32 block before the FP64 fold
 constexpr unsigned FULL = 0xffffffffu;
 
 struct TripleGeom {
     int nb;
     int64_t P;                 // pixels
-    int PC;                    // pixels staged per pass (multiple of 128)
+    int PC;                    // pixels staged per pass (multiple of 4)
+    int stride;                // staged row stride in floats (odd number of float4s)
     int64_t per_split;         // pixels per split (multiple of PC)
     int n_trip;
+    int rounds;                // triplet rounds per CTA (<= 4): blockDim.x triplets each
     int vec4;                  // fields rows are 16-byte aligned (P % 4 == 0, aligned base)
 };
 
-__global__ void __launch_bounds__(TT) k_triple_fp32(TripleGeom G, const float *__restrict__ fields,
-                                                    const int32_t *__restrict__ ijk,
-                                                    double *__restrict__ partial) {
-    extern __shared__ __align__(16) uint8_t smem[];
-    float *F = (float *)smem;                                    // [nb][PC]
-    double *acc = (double *)(F + (size_t)G.nb * G.PC);           // [TG]
-    int *seg = (int *)(acc + TG);                                 // [TG + 1] row starts
-    int *kk = seg + TG + 1;                                       // [TG] k of each triplet
-    uint8_t *flag = (uint8_t *)(kk + TG);                         // [TG] row-start flags
-    __shared__ int nseg_s;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int t0 = blockIdx.y * TG;
-    const int nt = min(TG, G.n_trip - t0);
-    const int64_t p_begin = (int64_t)blockIdx.x * G.per_split;
-    const int64_t p_end = min(G.P, p_begin + G.per_split);
-    // row segments of this group: flag row starts, then compact with one warp
-    for (int t = threadIdx.x; t < TG; t += blockDim.x) {
-        uint8_t f = 0;
-        if (t < nt) {
-            acc[t] = 0.0;
-            const int k = ijk[3 * (t0 + t) + 2];
-            kk[t] = (k >= 0 && k < G.nb) ? k : -1;   // out-of-range bins contribute nothing
-            const int i = ijk[3 * (t0 + t)], j = ijk[3 * (t0 + t) + 1];
-            f = (t == 0 || i != ijk[3 * (t0 + t - 1)] || j != ijk[3 * (t0 + t - 1) + 1]) ? 1 : 0;
-        }
-        flag[t] = f;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int base = lane * (TG / 32);
-        int c = 0;
-        for (int e = 0; e < TG / 32; ++e) c += flag[base + e];
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += y;
-        }
-        int pos = incl - c;
-        for (int e = 0; e < TG / 32; ++e)
-            if (flag[base + e]) seg[pos++] = base + e;
-        if (lane == 31) {
-            seg[incl] = nt;
-            nseg_s = incl;
-        }
-    }
-    __syncthreads();
-    const int nseg = nseg_s;
-    for (int64_t pc = p_begin; pc < p_end; pc += G.PC) {
-        const int np = (int)min((int64_t)G.PC, p_end - pc);
-        __syncthreads();
-        // stage fields[m][pc .. pc+np) (np is a multiple of 4 except possibly at the very end)
-        const int nv4 = G.vec4 ? np / 4 : 0;
-        for (int e = threadIdx.x; e < G.nb * nv4; e += blockDim.x) {
-            const int m = e / nv4, v = e - m * nv4;
-            ((float4 *)(F + (size_t)m * G.PC))[v] =
-                __ldg((const float4 *)(fields + (size_t)m * G.P + pc) + v);
-        }
-        for (int e = threadIdx.x; e < G.nb * G.PC; e += blockDim.x) {
-            const int m = e / G.PC, v = e - m * G.PC;
-            if (v >= nv4 * 4) F[(size_t)m * G.PC + v] = v < np ? fields[(size_t)m * G.P + pc + v] : 0.f;
-        }
-        __syncthreads();
-        for (int sgi = warp; sgi < nseg; sgi += nwarps) {
-            const int ta = seg[sgi], tb = seg[sgi + 1];
-            const int i = ijk[3 * (t0 + ta)], j = ijk[3 * (t0 + ta) + 1];
-            if (i < 0 || i >= G.nb || j < 0 || j >= G.nb) continue;
-            const float *Fi = F + (size_t)i * G.PC, *Fj = F + (size_t)j * G.PC;
-            for (int tq = ta; tq < tb; tq += KB) {
-                const float *Fk[KB];
-                float a[KB];
-#pragma unroll
-                for (int b = 0; b < KB; ++b) {
-                    Fk[b] = F + (size_t)max(kk[min(tq + b, tb - 1)], 0) * G.PC;
-                    a[b] = 0.f;
-                }
-                for (int p = lane; p < G.PC; p += 32) {
-                    const float dij = Fi[p] * Fj[p];
-#pragma unroll
-                    for (int b = 0; b < KB; ++b) a[b] = fmaf(dij, Fk[b][p], a[b]);
-                }
-#pragma unroll
-                for (int b = 0; b < KB; ++b) {
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) a[b] += __shfl_xor_sync(FULL, a[b], o);
-                }
-                if (lane == 0) {
-#pragma unroll
-                    for (int b = 0; b < KB; ++b)
-                        if (tq + b < tb && kk[tq + b] >= 0) acc[tq + b] += (double)a[b];
-                }
-            }
-        }
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < nt; t += blockDim.x)
-        partial[(size_t)blockIdx.x * G.n_trip + t0 + t] = acc[t];
+// a += (x y) z over four pixels, with packed FP32x2 arithmetic.
+__device__ __forceinline__ void step4(float4 x, float4 y, float4 z, float2 &a) {
+    const float2 p01 = __fmul2_rn(make_float2(x.x, x.y), make_float2(y.x, y.y));
+    const float2 p23 = __fmul2_rn(make_float2(x.z, x.w), make_float2(y.z, y.w));
+    a = __ffma2_rn(p01, make_float2(z.x, z.y), a);
+    a = __ffma2_rn(p23, make_float2(z.z, z.w), a);
 }
 
-// S[t] = inv_p * sum over splits of partial[split][t]: 32 triplets per block,
-// 8 lanes of splits per triplet, summed in a fixed order (deterministic).
+__global__ void k_triple_fp32(TripleGeom G, const float *__restrict__ fields, const int32_t *__restrict__ ijk,
+                              double *__restrict__ partial) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    float *F = (float *)smem;                                    // [nb][stride]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t p_begin = (int64_t)blockIdx.x * G.per_split;
+    const int64_t p_end = min(G.P, p_begin + G.per_split);
+    // this CTA's triplets: [t_base, t_base + rounds * blockDim.x)
+    const int t_base = blockIdx.y * G.rounds * blockDim.x;
+    const int rounds = G.rounds;
+    // this lane's triplet in each round (at most 4 rounds), as double-float
+    // sums hi + lo: GB300's FP64 pipe is too narrow for a per-block FP64 add
+    float Sh[4] = {0.f, 0.f, 0.f, 0.f}, Sl[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int64_t pc = p_begin; pc < p_end; pc += G.PC) {
+        const int np = (int)min((int64_t)G.PC, p_end - pc);
+        const int np4 = (np + 3) >> 2;
+        __syncthreads();
+        // stage fields[m][pc .. pc+np), zero-padded to a multiple of 4
+        if (G.vec4 && (np & 3) == 0) {
+            for (int e = threadIdx.x; e < G.nb * np4; e += blockDim.x) {
+                const int m = e / np4, v = e - m * np4;
+                ((float4 *)(F + (size_t)m * G.stride))[v] =
+                    __ldg((const float4 *)(fields + (size_t)m * G.P + pc) + v);
+            }
+        } else {
+            for (int e = threadIdx.x; e < G.nb * np4 * 4; e += blockDim.x) {
+                const int m = e / (np4 * 4), v = e - m * (np4 * 4);
+                F[(size_t)m * G.stride + v] = v < np ? fields[(size_t)m * G.P + pc + v] : 0.f;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rd = 0; rd < 4; ++rd) {
+            if (rd >= rounds) break;
+            const int t = t_base + ((rd * nwarps + warp) << 5) + lane;
+            if (t >= G.n_trip) continue;
+            const int i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
+            if (i < 0 || i >= G.nb || j < 0 || j >= G.nb || k < 0 || k >= G.nb) continue;   // contributes nothing
+            const float4 *Fi = (const float4 *)(F + (size_t)i * G.stride);
+            const float4 *Fj = (const float4 *)(F + (size_t)j * G.stride);
+            const float4 *Fk = (const float4 *)(F + (size_t)k * G.stride);
+            float sh = Sh[rd], sl = Sl[rd];
+            for (int q0 = 0; q0 < np4; q0 += FOLD) {
+                float2 a = make_float2(0.f, 0.f);
+                if (q0 + FOLD <= np4) {   // full block: all loads issued back to back
+#pragma unroll
+                    for (int u = 0; u < FOLD; ++u) step4(Fi[q0 + u], Fj[q0 + u], Fk[q0 + u], a);
+                } else {
+                    for (int q = q0; q < np4; ++q) step4(Fi[q], Fj[q], Fk[q], a);
+                }
+                const float v = __fadd_rn(a.x, a.y);
+                const float t = __fadd_rn(sh, v);             // TwoSum(sh, v)
+                const float bp = __fsub_rn(t, sh);
+                sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(v, bp)));
+                sh = t;
+            }
+            Sh[rd] = sh;
+            Sl[rd] = sl;
+        }
+    }
+#pragma unroll
+    for (int rd = 0; rd < 4; ++rd) {
+        const int t = t_base + ((rd * nwarps + warp) << 5) + lane;
+        if (rd < rounds && t < G.n_trip) partial[(size_t)blockIdx.x * G.n_trip + t] = (double)Sh[rd] + (double)Sl[rd];
+    }
+}
+
+// Launch shape of k_triple_fp32: pixel splits (about two CTAs per SM, or
+// fewer when max_split caps them) x triplet groups of up to 4096 (one warp per
+// 32 triplets, at most 1024 threads, walked in at most four rounds), and the
+// staged chunk.
+struct TriplePlan {
+    TripleGeom G;
+    int64_t nsplit;
+    int tgroups;
+    int threads;
+    size_t smem;
+};
+
+bool triple_plan(int nb, int N, int n_trip, int sms, int64_t max_split, const float *d_fields, TriplePlan &tp) {
+    TripleGeom &G = tp.G;
+    G.nb = nb;
+    G.P = (int64_t)N * N;
+    G.n_trip = n_trip;
+    const int ngroups = (int)cdiv(n_trip, 32);
+    const int warps = std::min(32, ngroups);
+    tp.threads = 32 * warps;
+    G.rounds = (int)std::min<int64_t>(4, cdiv(ngroups, warps));
+    tp.tgroups = (int)cdiv(n_trip, (int64_t)G.rounds * tp.threads);
+    int64_t target = std::max<int64_t>(1, std::min<int64_t>(cdiv(2 * (int64_t)sms, tp.tgroups), max_split));
+    int64_t per = cdiv(cdiv(G.P, target), 4) * 4;
+    const int64_t pc_max = std::max<int64_t>(4, ((96 * 1024) / (4 * (int64_t)nb) - 4) / 4 * 4);
+    G.PC = (int)std::min<int64_t>(per, pc_max);
+    G.stride = 4 * ((G.PC / 4) | 1);   // an odd number of float4: rows start on different banks
+    G.vec4 = (G.P % 4 == 0) && (((uintptr_t)d_fields & 15) == 0);
+    G.per_split = cdiv(per, G.PC) * G.PC;
+    tp.nsplit = cdiv(G.P, G.per_split);
+    while (tp.nsplit > max_split) {   // rounding can leave one split too many
+        per += G.PC;
+        G.per_split = cdiv(per, G.PC) * G.PC;
+        tp.nsplit = cdiv(G.P, G.per_split);
+    }
+    tp.smem = (size_t)nb * G.stride * 4;
+    return true;
+}
+
+// S[t] = inv_p * sum over splits of partial[split][t]: one warp per triplet,
+// lane l adds splits l, l + 32, ... and a fixed butterfly combines the lanes
+// (the order never depends on scheduling, so results are reproducible).
 __global__ void __launch_bounds__(256) k_triple_reduce(int n_trip, int nsplit, double inv_p,
                                                        const double *__restrict__ partial,
                                                        double *__restrict__ S) {
-    __shared__ double sh[8][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int t = blockIdx.x * 32 + tx;
+    const int lane = threadIdx.x & 31;
+    const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (t >= n_trip) return;
     double s = 0.0;
-    if (t < n_trip)
-        for (int k = ty; k < nsplit; k += 8) s += partial[(size_t)k * n_trip + t];
-    sh[ty][tx] = s;
-    __syncthreads();
-    if (ty == 0 && t < n_trip) {
-        double a = 0.0;
-        for (int k = 0; k < 8; ++k) a += sh[k][tx];
-        S[t] = a * inv_p;
-    }
+    for (int k = lane; k < nsplit; k += 32) s += partial[(size_t)k * n_trip + t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if (lane == 0) S[t] = s * inv_p;
 }
 
 __global__ void k_normalise(int n_trip, double norm_A, const double *__restrict__ S,
@@ -189,33 +202,20 @@ abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_field
                               const int32_t *d_ijk, double *d_sum) {
     if (n_trip == 0) return ABS_OK;
     if (s.precision == ABS_SPLIT_BF16) return launch_triple_tc(ctx, s, d_fields, n_trip, d_ijk, d_sum);
-    TripleGeom G;
-    G.nb = s.nb;
-    G.P = (int64_t)s.N * s.N;
-    G.n_trip = n_trip;
-    // staged pixels: keep the field tile within ~96 KB, and make enough
-    // chunks for about four CTAs per SM
-    // one pixel range per CTA, about two CTAs per SM overall; each range is
-    // staged in chunks of PC pixels (a multiple of 32 whose fields fit ~96 KB)
-    const int groups = (int)cdiv(n_trip, TG);
-    const int64_t target = std::max<int64_t>(1, cdiv(2 * ctx->sm_count, groups));
-    const int64_t per = cdiv(cdiv(G.P, target), 32) * 32;
-    const int64_t pc_max = std::max<int64_t>(32, ((96 * 1024) / (4 * (int64_t)G.nb)) / 32 * 32);
-    const int PC = (int)std::min<int64_t>(per, pc_max);
-    G.PC = PC;
-    G.vec4 = (G.P % 4 == 0) && (((uintptr_t)d_fields & 15) == 0);
-    G.per_split = cdiv(per, PC) * PC;
-    const int64_t nsplit = cdiv(G.P, G.per_split);
+    TriplePlan tp;
+    if (!triple_plan(s.nb, s.N, n_trip, ctx->sm_count, INT64_MAX, d_fields, tp))
+        return fail(ctx, ABS_ERR_UNSUPPORTED, "FP32 triple-sum tiling");
+    const int64_t nsplit = tp.nsplit;
     double *partial = (double *)workspace(ctx, "triple.partial", sizeof(double) * nsplit * n_trip);
     if (!partial) return fail(ctx, ABS_ERR_OOM, "triple-sum workspace");
-    const size_t smem = (size_t)G.nb * PC * 4 + TG * 8 + (2 * TG + 1) * 4 + TG;
-    cudaFuncSetAttribute(k_triple_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_triple_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem);
     {
         StageTimer timer(ctx, "triple_fp32");
-        k_triple_fp32<<<dim3((unsigned)nsplit, groups), TT, smem, ctx->stream>>>(G, d_fields, d_ijk, partial);
+        k_triple_fp32<<<dim3((unsigned)nsplit, tp.tgroups), tp.threads, tp.smem, ctx->stream>>>(tp.G, d_fields,
+                                                                                             d_ijk, partial);
     }
     StageTimer timer(ctx, "triple_reduce");
-    k_triple_reduce<<<(int)cdiv(n_trip, 32), 256, 0, ctx->stream>>>(
+    k_triple_reduce<<<(int)cdiv(n_trip, 8), 256, 0, ctx->stream>>>(
         n_trip, (int)nsplit, 1.0 / ((double)s.N * (double)s.N), partial, d_sum);
     return check_launch(ctx, "triple sums");
 }
@@ -277,29 +277,14 @@ extern "C" abs_status abs_triple_sums_static(const abs_config *cfg, const float 
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     // same tiling as launch_triple_sums, with the number of pixel splits capped
     // so that [split][triplet] fits the fixed array
-    TripleGeom G;
-    G.nb = cfg->n_bins;
-    G.P = (int64_t)N * N;
-    G.n_trip = n_trip;
-    const int groups = (int)cdiv(n_trip, TG);
-    int64_t target = std::max<int64_t>(1, cdiv(2 * sms, groups));
-    target = std::min<int64_t>(target, std::max<int64_t>(1, cap / n_trip));
-    int64_t per = cdiv(cdiv(G.P, target), 32) * 32;
-    const int64_t pc_max = std::max<int64_t>(32, ((96 * 1024) / (4 * (int64_t)G.nb)) / 32 * 32);
-    const int PC = (int)std::min<int64_t>(per, pc_max);
-    G.PC = PC;
-    G.vec4 = (G.P % 4 == 0) && (((uintptr_t)d_fields & 15) == 0);
-    G.per_split = cdiv(per, PC) * PC;
-    int64_t nsplit = cdiv(G.P, G.per_split);
-    while (nsplit * n_trip > cap) {   // rounding can leave one split too many
-        per += PC;
-        G.per_split = cdiv(per, PC) * PC;
-        nsplit = cdiv(G.P, G.per_split);
-    }
-    const size_t smem = (size_t)G.nb * PC * 4 + TG * 8 + (2 * TG + 1) * 4 + TG;
-    cudaFuncSetAttribute(k_triple_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_triple_fp32<<<dim3((unsigned)nsplit, groups), TT, smem, stream>>>(G, d_fields, d_ijk, partial);
-    k_triple_reduce<<<(int)cdiv(n_trip, 32), 256, 0, stream>>>(n_trip, (int)nsplit,
+    TriplePlan tp;
+    if (!triple_plan(cfg->n_bins, N, n_trip, sms, std::max<int64_t>(1, cap / n_trip), d_fields, tp))
+        return ABS_ERR_UNSUPPORTED;
+    const int64_t nsplit = tp.nsplit;
+    cudaFuncSetAttribute(k_triple_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem);
+    k_triple_fp32<<<dim3((unsigned)nsplit, tp.tgroups), tp.threads, tp.smem, stream>>>(tp.G, d_fields, d_ijk,
+                                                                                        partial);
+    k_triple_reduce<<<(int)cdiv(n_trip, 8), 256, 0, stream>>>(n_trip, (int)nsplit,
                                                                1.0 / ((double)N * (double)N), partial, d_sum);
     return cudaGetLastError() == cudaSuccess ? ABS_OK : ABS_ERR_CUDA;
 }
