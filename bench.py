@@ -68,7 +68,20 @@ def load_peaks():
 # from the ncu captures summarised under profiles/, with the SHA-256 of the
 # source file the kernel was built from when it was captured.  A kernel whose
 # source has changed since then reports null.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    "grid": {"bytes": 20373504, "source": "paper_2412_02246_gb300/csrc/grid.cu",
+              "sha256": "0ffc897d49b66e0ec51f76e7f9fb8e93d11dc36bd5a2d1dc24b64431189844b1",
+              "profile": "profiles/k_grid_mwa975k.md"},
+    "fft_rows": {"bytes": 731392, "source": "paper_2412_02246_gb300/csrc/fft.cu",
+                  "sha256": "f1c59431dcc1c05974dbe1e119c5a3df1f210e395416a1bbcf0b2dd2439c316c",
+                  "profile": "profiles/k_fft_rows_mwa975k.md"},
+    "fft_cols": {"bytes": 2887424, "source": "paper_2412_02246_gb300/csrc/fft.cu",
+                  "sha256": "f1c59431dcc1c05974dbe1e119c5a3df1f210e395416a1bbcf0b2dd2439c316c",
+                  "profile": "profiles/k_fft_cols_mwa975k.md"},
+    "triple_fp32": {"bytes": 6663424, "source": "paper_2412_02246_gb300/csrc/triple.cu",
+                     "sha256": "8fe8e2f9a56451dcf08f57598393d8c39c95e7bc3989490a4d3d75e67a289f4c",
+                     "profile": "profiles/k_triple_fp32_mwa975k.md"},
+}
 
 
 def measured_traffic(stage):

@@ -73,7 +73,10 @@ typedef struct abs_config {
     int32_t n_grid;           /* uv grid side n: even, 8 <= n <= 8192 */
     double du;                /* grid spacing dU_g in wavelengths (> 0), used as binary32 */
     int32_t kernel;           /* ABS_KERNEL_GAUSS (default) or ABS_KERNEL_NGP (Eq. vg) */
-    double sigma_cells;       /* Gaussian kernel width in cells (> 0.25), GAUSS only */
+    double sigma_cells;       /* Gaussian kernel width in cells, GAUSS only: > 0.25 and
+                                 > (radius_cells + 0.5) / 9, so that every footprint weight
+                                 (at most (r + 1/2)^2 / sigma^2 = 81 e-folds down) is a
+                                 normal FP32 number and a filled cell has weight sum > 0 */
     int32_t radius_cells;     /* footprint half-width r in cells, 0..ABS_MAX_RADIUS, GAUSS only */
     int32_t n_bins;           /* number of rings, 1..ABS_MAX_BINS */
     const double *ell_edges;  /* host: n_bins + 1 strictly ascending edges in l, edges[0] > 0 */

@@ -108,11 +108,13 @@ abs_status launch_filter_fft(abs_ctx *ctx, const Setup &s, const float *d_grid,
                              const float *d_wsum, const uint8_t *d_mask, float *d_fields);
 // The same transform fed directly from the FP64 gridding accumulators (mirror
 // applied on the fly), as abs_estimate uses it.
-abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc, const uint8_t *hit,
+abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc,
                                  float *d_fields);
-// FP64 accumulators [3][n*n] (re, im, w before the mirror) and hit flags of the
-// last launch_grid_accumulate on this context.
-void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc, uint8_t **hit);
+// FP64 accumulators [3][n*n] (re, im, w before the mirror) of the last
+// launch_grid_accumulate on this context.  A cell received a contribution
+// exactly when its weight sum is > 0 (every footprint weight is a normal,
+// positive FP32 number, which the sigma_cells bound guarantees).
+void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc);
 abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_fields,
                               int32_t n_trip, const int32_t *d_ijk, double *d_sum);
 // Split-BF16 tcgen05 form of the same sums (precision == ABS_SPLIT_BF16).

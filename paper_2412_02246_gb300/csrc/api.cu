@@ -92,6 +92,10 @@ abs_status derive_grid(const abs_config *cfg, int64_t *q, int *Rm, int *R_out, i
             *err = "radius_cells must be in [0, 3]";
             return ABS_ERR_INVALID_ARG;
         }
+        if (!(cfg->radius_cells + 0.5 < 9.0 * cfg->sigma_cells)) {
+            *err = "sigma_cells must exceed (radius_cells + 0.5) / 9 (footprint weights stay normal FP32)";
+            return ABS_ERR_INVALID_ARG;
+        }
     }
     if (cfg->n_bins < 1 || cfg->n_bins > ABS_MAX_BINS) { *err = "n_bins must be in [1, 254]"; return ABS_ERR_INVALID_ARG; }
     if (!cfg->ell_edges) { *err = "ell_edges is NULL"; return ABS_ERR_INVALID_ARG; }
@@ -558,9 +562,8 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
             ABS_CHECK(launch_counts(ctx, s, mask, n_trip, d_ijk, count, d_ellbar));
         }
         double *acc;
-        uint8_t *hit;
-        grid_acc_buffers(ctx, s, &acc, &hit);
-        ABS_CHECK(launch_filter_fft_acc(ctx, s, acc, hit, fields));
+        grid_acc_buffers(ctx, s, &acc);
+        ABS_CHECK(launch_filter_fft_acc(ctx, s, acc, fields));
         ABS_CHECK(launch_triple_sums(ctx, s, fields, n_trip, d_ijk, sum));
         if (d_B) ABS_CHECK(launch_normalise(ctx, s, n_trip, sum, count, d_B + (size_t)r * n_trip));
     }

@@ -187,10 +187,9 @@ struct GridF32 {   // abs_grid outputs (FP32)
 };
 struct GridF64 {   // FP64 accumulators before the mirror (inside abs_estimate)
     const double *re, *im, *w;
-    const uint8_t *hit;
     __device__ bool value(int64_t cell, int64_t mcell, double &vr, double &vi) const {
-        if (!(hit[cell] | hit[mcell])) return false;
-        const double ww = w[cell] + w[mcell];
+        const double ww = w[cell] + w[mcell];   // > 0 exactly on filled cells
+        if (!(ww > 0.0)) return false;
         vr = (re[cell] + re[mcell]) / ww;
         vi = (im[cell] - im[mcell]) / ww;
         return true;
@@ -352,10 +351,9 @@ abs_status launch_filter_fft(abs_ctx *ctx, const Setup &s, const float *d_grid, 
     return run_fft(ctx, s, src, d_fields);
 }
 
-abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc, const uint8_t *hit,
-                                 float *d_fields) {
+abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc, float *d_fields) {
     const int64_t cells = (int64_t)s.n * s.n;
-    GridF64 src{acc, acc + cells, acc + 2 * cells, hit};
+    GridF64 src{acc, acc + cells, acc + 2 * cells};
     return run_fft(ctx, s, src, d_fields);
 }
 

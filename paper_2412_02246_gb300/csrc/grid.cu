@@ -366,8 +366,8 @@ constexpr int GFOLD = 8;
 constexpr int CHUNK = 64;        // visibilities per task at most
 constexpr int MAXTASK = UMAX / CHUNK + 256;   // sum over cells of ceil(run / CHUNK)
 static_assert(UMAX == 8 * 64, "the in-unit sort gives each of 8 warps two rounds of 32 items");
-constexpr size_t GRID_SMEM = UMAX * (sizeof(float) * RS + sizeof(float2)) + sizeof(int2) * MAXTASK +
-                             sizeof(uint16_t) * 8 * 256 + sizeof(uint32_t) * 260 + 2 * UMAX;
+constexpr size_t GRID_SMEM = UMAX * sizeof(float) * RS + sizeof(int2) * MAXTASK + sizeof(uint16_t) * 8 * 256 +
+                             sizeof(uint32_t) * 260 + 2 * UMAX;
 
 // The double with the value of x, built with integer operations only (GB300's
 // FP64 pipe is narrow: one hardware conversion per flushed value is what kept
@@ -391,6 +391,29 @@ __device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 x) {
     s = t;
 }
 
+// Inputs of one unit as thread (warp, lane) sees them: items t = 64 warp +
+// 32 h + lane, h = 0, 1, in input order.
+struct UnitIn {
+    int4 U;
+    float2 p[2];
+    uint32_t idx[2];
+};
+
+__device__ __forceinline__ void load_unit(UnitIn &in, int u, int nu, const int4 *__restrict__ units,
+                                          const float2 *__restrict__ s_uv, const uint32_t *__restrict__ s_idx,
+                                          int warp, int lane) {
+    if (u >= nu) return;
+    in.U = units[u];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int t = warp * 64 + h * 32 + lane;
+        if (t < in.U.z - in.U.y) {
+            in.p[h] = s_uv[in.U.y + t];
+            in.idx[h] = s_idx[in.U.y + t];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict__ units,
                                              const int *__restrict__ n_units,
                                              const float2 *__restrict__ s_uv,
@@ -398,12 +421,10 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
                                              const float2 *__restrict__ vis,
                                              double *__restrict__ acc_re,
                                              double *__restrict__ acc_im,
-                                             double *__restrict__ acc_w,
-                                             uint8_t *__restrict__ hit) {
+                                             double *__restrict__ acc_w) {
     extern __shared__ __align__(16) uint8_t dsm[];
     float *st = (float *)dsm;                                          // [UMAX][RS] staged records
-    float2 *in_q = (float2 *)(st + UMAX * RS);                         // [UMAX] u/dU, v/dU, input order
-    int2 *task = (int2 *)(in_q + UMAX);                                // [MAXTASK] (first, end)
+    int2 *task = (int2 *)(st + UMAX * RS);                             // [MAXTASK] (first, end)
     uint16_t *wloc = (uint16_t *)(task + MAXTASK);                     // [8][256] per-warp cell counts
     uint32_t *cstart = (uint32_t *)(wloc + 8 * 256);                   // [257] first item of each cell
     uint8_t *in_c = (uint8_t *)(cstart + 260);                         // [UMAX] cell, input order
@@ -417,27 +438,34 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
     const int dy = lane >> 2, q2 = 2 * (lane & 3);
     const bool on_a = lane < 28 && dy < fw && q2 < fw, on_b = on_a && q2 + 1 < fw;
     const int nu = *n_units;
+    UnitIn nxt;
+    load_unit(nxt, blockIdx.x, nu, units, s_uv, s_idx, warp, lane);
     for (int u = blockIdx.x; u < nu; u += gridDim.x) {
-        const int4 U = units[u];
+        const UnitIn cur = nxt;
+        const int4 U = cur.U;
         const int total = U.z - U.y;
         const int tile = U.x, tx = tile % G.tt, ty = tile / G.tt;
+        float2 v[2];   // this unit's visibilities: gathered now, used at placement
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (warp * 64 + h * 32 + lane < total) v[h] = vis[cur.idx[h]];
+        load_unit(nxt, u + gridDim.x, nu, units, s_uv, s_idx, warp, lane);   // in flight during this unit
         __syncthreads();   // previous unit done with the staging buffers
         // cells, and per-warp counts over the warp's 64 items (input order)
         for (int k = lane; k < 256; k += 32) wloc[warp * 256 + k] = 0;
         __syncwarp();
+        float2 q[2];   // u/dU, v/dU of this thread's items
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int t = warp * 64 + h * 32 + lane;
             const bool on = t < total;
             uint32_t c = 0x10000u + lane;
             if (on) {
-                const float2 p = s_uv[U.y + t];
-                const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
-                const int kx = (int)floorf(__fadd_rn(qx, 0.5f)) + G.off;
-                const int ky = (int)floorf(__fadd_rn(qy, 0.5f)) + G.off;
+                q[h] = make_float2(__fdiv_rn(cur.p[h].x, G.du), __fdiv_rn(cur.p[h].y, G.du));
+                const int kx = (int)floorf(__fadd_rn(q[h].x, 0.5f)) + G.off;
+                const int ky = (int)floorf(__fadd_rn(q[h].y, 0.5f)) + G.off;
                 c = (uint32_t)((ky - ty * TS) * TS + (kx - tx * TS));
                 in_c[t] = (uint8_t)c;
-                in_q[t] = make_float2(qx, qy);
             }
             const unsigned peers = __match_any_sync(FULL, c);
             if (on && lane == __ffs(peers) - 1) wloc[warp * 256 + c] += (uint16_t)__popc(peers);
@@ -471,8 +499,7 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
             const unsigned peers = __match_any_sync(FULL, c);
             if (on) {
                 const int pos = (int)wloc[warp * 256 + c] + __popc(peers & ((1u << lane) - 1u));
-                const float2 p = s_uv[U.y + t];
-                const float2 qq = in_q[t];
+                const float2 p = cur.p[h], qq = q[h];
                 const float cxf = floorf(__fadd_rn(qq.x, 0.5f)), cyf = floorf(__fadd_rn(qq.y, 0.5f));
                 const float fxh = __fsub_rn(qq.x, cxf), fyh = __fsub_rn(qq.y, cyf);
                 // the division residual (exact by FMA) over dU: a correction of
@@ -496,8 +523,7 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
                 for (int k = 0; k < 3; ++k)
                     ((float4 *)(rec + R_WY))[k] = make_float4(wy[2 * k], wy[2 * k], wy[2 * k + 1], wy[2 * k + 1]);
                 ((float2 *)(rec + R_WY))[6] = make_float2(wy[6], wy[6]);
-                const float2 v = vis[s_idx[U.y + t]];
-                ((float4 *)(rec + R_V))[0] = make_float4(v.x, v.x, v.y, v.y);
+                ((float4 *)(rec + R_V))[0] = make_float4(v[h].x, v[h].x, v[h].y, v[h].y);
                 st_c[pos] = (uint8_t)c;
             }
             __syncwarp();
@@ -525,8 +551,8 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
             for (int k = 0; k < 8; ++k) {
                 const int c = lane * 8 + k;
                 const int j0 = (int)cstart[c], j1 = (int)cstart[c + 1];
-                for (uint32_t q = 0; q < nt[k]; ++q, ++pos) {
-                    const int a = j0 + (int)q * CHUNK;
+                for (uint32_t qn = 0; qn < nt[k]; ++qn, ++pos) {
+                    const int a = j0 + (int)qn * CHUNK;
                     task[pos] = make_int2(a, min(j1, a + CHUNK));
                 }
             }
@@ -570,14 +596,12 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
                     atomicAdd(&acc_re[pidx], widen(vre.x));
                     atomicAdd(&acc_im[pidx], widen(vim.x));
                     atomicAdd(&acc_w[pidx], widen(vw.x));
-                    hit[pidx] = 1;
                 }
                 if (on_b && gxa + 1 >= -G.half && gxa + 1 <= G.half) {
                     const int64_t pidx = cell_index(G.n, gxa + 1, gy);
                     atomicAdd(&acc_re[pidx], widen(vre.y));
                     atomicAdd(&acc_im[pidx], widen(vim.y));
                     atomicAdd(&acc_w[pidx], widen(vw.y));
-                    hit[pidx] = 1;
                 }
             }
         }
@@ -587,7 +611,7 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
 // Hermitian mirror and FP32 outputs: G(g) + conj G(-g), W(g) + W(-g).
 __global__ void k_grid_finalize(int n, const double *__restrict__ acc_re,
                                 const double *__restrict__ acc_im,
-                                const double *__restrict__ acc_w, const uint8_t *__restrict__ hit,
+                                const double *__restrict__ acc_w,
                                 float2 *__restrict__ grid, float *__restrict__ wsum,
                                 uint8_t *__restrict__ mask) {
     const int64_t cells = (int64_t)n * n;
@@ -604,7 +628,7 @@ __global__ void k_grid_finalize(int n, const double *__restrict__ acc_re,
         const int64_t pm = (int64_t)my * n + mx;
         grid[p] = make_float2((float)(acc_re[p] + acc_re[pm]), (float)(acc_im[p] - acc_im[pm]));
         wsum[p] = (float)(acc_w[p] + acc_w[pm]);
-        mask[p] = (hit[p] | hit[pm]) ? 1 : 0;
+        mask[p] = (acc_w[p] > 0.0 || acc_w[pm] > 0.0) ? 1 : 0;   // a filled cell has weight > 0
     }
 }
 
@@ -691,10 +715,9 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
     return check_launch(ctx, "grid plan");
 }
 
-void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc, uint8_t **hit) {
+void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc) {
     const int64_t cells = (int64_t)s.n * s.n;
     *acc = (double *)workspace(ctx, "grid.acc", sizeof(double) * 3 * cells);
-    *hit = (uint8_t *)workspace(ctx, "grid.hit", cells);
 }
 
 abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_vis,
@@ -704,25 +727,23 @@ abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, c
     if (!plan_bufs(ctx, G, n_vis, b)) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
     const int64_t cells = (int64_t)s.n * s.n;
     double *acc = (double *)workspace(ctx, "grid.acc", sizeof(double) * 3 * cells);
-    uint8_t *hit = (uint8_t *)workspace(ctx, "grid.hit", cells);
-    if (!acc || !hit) return fail(ctx, ABS_ERR_OOM, "grid accumulation workspace");
+    if (!acc) return fail(ctx, ABS_ERR_OOM, "grid accumulation workspace");
     cudaStream_t st = ctx->stream;
     {
         StageTimer timer(ctx, "grid_zero");
         cudaMemsetAsync(acc, 0, sizeof(double) * 3 * cells, st);
-        cudaMemsetAsync(hit, 0, cells, st);
     }
     if (n_vis > 0) {
         StageTimer timer(ctx, "grid");
         const int blocks = std::min(b.units_cap, ctx->sm_count * 3);
         cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRID_SMEM);
         k_grid<<<blocks, GT, GRID_SMEM, st>>>(G, b.units, b.n_units, b.s_uv, b.s_idx, (const float2 *)d_vis, acc,
-                                           acc + cells, acc + 2 * cells, hit);
+                                           acc + cells, acc + 2 * cells);
     }
     {
         StageTimer timer(ctx, "grid_finalize");
         const int fb = (int)std::min<int64_t>(cdiv(cells, 256), ctx->sm_count * 8);
-        k_grid_finalize<<<fb, 256, 0, st>>>(s.n, acc, acc + cells, acc + 2 * cells, hit,
+        k_grid_finalize<<<fb, 256, 0, st>>>(s.n, acc, acc + cells, acc + 2 * cells,
                                             (float2 *)d_grid, d_wsum, d_mask);
     }
     return check_launch(ctx, "grid accumulate");

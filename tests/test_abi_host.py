@@ -69,7 +69,7 @@ def test_random_edges_match_oracle(lib):
 
 @pytest.mark.parametrize("bad", [
     dict(n_grid=7), dict(n_grid=0), dict(n_grid=16386), dict(du=0.0), dict(du=-1.0),
-    dict(du=float("nan")), dict(kernel=5), dict(sigma_cells=0.1), dict(radius_cells=4),
+    dict(du=float("nan")), dict(kernel=5), dict(sigma_cells=0.1), dict(sigma_cells=0.38), dict(radius_cells=4),
     dict(radius_cells=-1), dict(precision=3), dict(norm_A=0.0), dict(n_fft=7), dict(n_fft=80), dict(n_fft=91),
     dict(ell_edges=[10.0, 5.0]), dict(ell_edges=[0.0, 5.0]), dict(ell_edges=[5.0, float("inf")]),
 ])
