@@ -40,11 +40,12 @@ METRIC = "ABS estimates/s (V->binned B)"
 UNIT = "estimates/s"
 
 # kernels launched per stage-timer entry (the profiler brackets stages); the
-# gridding plan runs the key kernel, the unit cutter and, per radix pass of up
-# to 11-bit digits of the uv tile id, a 3-kernel scan and a scatter (plus a
-# histogram kernel on passes after the first)
-KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "ring_lists": 6,
-                     "count_items": 1, "count_pairs": 1, "count_gather": 1, "ellbar": 6,
+# gridding plan runs the key kernel and, per radix pass of up to 11-bit digits
+# of the uv tile id, a fused scan and a scatter (plus a histogram kernel on
+# passes after the first); the ring lists run rows, a 2-kernel scan, write and
+# finish
+KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "ring_lists": 5,
+                     "count_items": 1, "count_pairs": 1, "count_gather": 1, "ellbar": 5,
                      "fft_rows": 1, "fft_cols": 1, "triple_fp32": 1, "triple_reduce": 1,
                      "normalise": 1, "check_triplets": 1, "tc_rows": 1, "triple_tc": 1}
 
@@ -52,7 +53,7 @@ KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "ring_lists"
 def plan_kernels(n_grid, radius):
     tiles = -(-(n_grid - 1 + 2 * radius) // 16)
     passes = -(-int(tiles * tiles).bit_length() // 11)
-    return 2 + 4 * passes + (passes - 1)
+    return 3 * passes
 
 
 def load_peaks():

@@ -93,6 +93,9 @@ enum : int32_t {
 
 // Grow-only named workspace.  Returns nullptr on allocation failure.
 void *workspace(abs_ctx *ctx, const char *name, size_t bytes);
+// The same, zero-filled (on the context's stream) whenever it is (re)allocated;
+// for counters that kernels re-arm themselves after use.
+void *workspace_zeroed(abs_ctx *ctx, const char *name, size_t bytes);
 abs_status fail(abs_ctx *ctx, abs_status st, const std::string &msg);
 abs_status check_launch(abs_ctx *ctx, const char *what);
 const Setup *get_setup(abs_ctx *ctx, const abs_config *cfg, abs_status &st);
@@ -124,8 +127,9 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
 // NULL) and, if d_ellbar is not NULL, the mean l of every ring.
 abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, int32_t n_trip,
                          const int32_t *d_ijk, int64_t *d_count, double *d_ellbar);
-// Exclusive scan of len uint32 values; bsum holds cdiv(len, 4096) + 1 entries.
-void scan_u32(cudaStream_t st, const uint32_t *in, int64_t len, uint32_t *out, uint32_t *bsum);
+// Exclusive scan of len uint32 values on the context's stream (2 kernels);
+// bsum holds cdiv(len, 4096) + 1 entries.  False if its counter cannot be allocated.
+bool scan_u32(abs_ctx *ctx, const uint32_t *in, int64_t len, uint32_t *out, uint32_t *bsum);
 abs_status launch_normalise(abs_ctx *ctx, const Setup &s, int32_t n_trip, const double *d_sum,
                             const int64_t *d_count, double *d_B);
 abs_status launch_ellbar(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, double *d_ellbar);

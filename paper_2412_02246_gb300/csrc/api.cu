@@ -217,6 +217,14 @@ void *workspace(abs_ctx *ctx, const char *name, size_t bytes) {
     return w.p;
 }
 
+void *workspace_zeroed(abs_ctx *ctx, const char *name, size_t bytes) {
+    Workspace &w = ctx->ws[name];
+    const bool fresh = w.bytes < (bytes == 0 ? 16 : bytes);
+    void *p = workspace(ctx, name, bytes);
+    if (p && fresh) cudaMemsetAsync(p, 0, ctx->ws[name].bytes, ctx->stream);
+    return p;
+}
+
 static std::string setup_key(const abs_config *c) {
     std::string k;
     auto put = [&k](const void *p, size_t n) { k.append((const char *)p, n); };

@@ -540,7 +540,7 @@ abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, Ring
     cudaMemsetAsync(maps, 0, (size_t)2 * mb, st);
     const int nbk = (int)cdiv(nrow * 32, 256);
     k_ring_rows<<<nbk, 256, 0, st>>>(G, s.d_q, d_mask, rowcnt, rowlen);
-    scan_u32(st, rowcnt, NFAM * nrow, rowoff, bsum);
+    if (!scan_u32(ctx, rowcnt, NFAM * nrow, rowoff, bsum)) return fail(ctx, ABS_ERR_OOM, "scan counter");
     k_ring_write<<<nbk, 256, 0, st>>>(G, s.d_q, d_mask, rowoff, rb.lists, rb.mapF, rb.mapA);
     k_ring_finish<<<(int)cdiv((int64_t)NFAM * s.nb * 32, 256), 256, 0, st>>>(
         G, s.du, rowoff, rowcnt, rowlen, rb.ring_off, rb.counts, d_ellbar);

@@ -103,26 +103,29 @@ __device__ __forceinline__ uint32_t tile_key(const GridGeom &G, float2 p, uint32
 
 // One CTA per chunk: the tile key of every visibility (key_none for non-finite
 // or off-grid positions), per-tile totals and the chunk's histogram of the
-// first digit.  Counts are added once per distinct key in a warp
-// (consecutive visibilities of a baseline usually share a tile).
-__global__ void __launch_bounds__(256) k_plan_keys(GridGeom G, int64_t n_vis, const float2 *__restrict__ uv,
-                                                   uint32_t *__restrict__ keys,
-                                                   uint32_t *__restrict__ tile_hist, uint32_t key_none,
-                                                   int dw, int nchunks, uint32_t *__restrict__ rhist) {
+// first digit (nbins bins; digit = key & dmask).  Counts are added once per
+// distinct key in a warp (consecutive visibilities of a baseline usually share
+// a tile).  1024 threads, RT / 1024 visibilities each, all loads in flight.
+constexpr int KT = 1024;
+__global__ void __launch_bounds__(KT) k_plan_keys(GridGeom G, int64_t n_vis, const float2 *__restrict__ uv,
+                                                  uint32_t *__restrict__ keys,
+                                                  uint32_t *__restrict__ tile_hist, uint32_t key_none,
+                                                  int nbins, uint32_t dmask, int nchunks,
+                                                  uint32_t *__restrict__ rhist) {
     __shared__ uint32_t h[1 << DMAX];
-    const int nb = 1 << dw, lane = threadIdx.x & 31;
-    for (int d = threadIdx.x; d < nb; d += 256) h[d] = 0;
+    const int lane = threadIdx.x & 31;
+    for (int d = threadIdx.x; d < nbins; d += KT) h[d] = 0;
     __syncthreads();
     const int64_t c0 = (int64_t)blockIdx.x * RT;
-    float2 pv[RT / 256];   // all loads of the chunk in flight at once
+    float2 pv[RT / KT];
 #pragma unroll
-    for (int k = 0; k < RT / 256; ++k) {
-        const int64_t i = c0 + k * 256 + threadIdx.x;
+    for (int k = 0; k < RT / KT; ++k) {
+        const int64_t i = c0 + k * KT + threadIdx.x;
         pv[k] = i < n_vis ? uv[i] : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int k = 0; k < RT / 256; ++k) {
-        const int64_t i = c0 + k * 256 + threadIdx.x;
+    for (int k = 0; k < RT / KT; ++k) {
+        const int64_t i = c0 + k * KT + threadIdx.x;
         const bool on = i < n_vis;
         uint32_t key = 0xffffffffu;
         if (on) {
@@ -133,18 +136,18 @@ __global__ void __launch_bounds__(256) k_plan_keys(GridGeom G, int64_t n_vis, co
         if (on && lane == __ffs(peers) - 1) {
             const uint32_t c = (uint32_t)__popc(peers);
             if (key != key_none) atomicAdd(&tile_hist[key], c);
-            atomicAdd(&h[key & (uint32_t)(nb - 1)], c);
+            atomicAdd(&h[key & dmask], c);
         }
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < nb; d += 256) rhist[(int64_t)d * nchunks + blockIdx.x] = h[d];
+    for (int d = threadIdx.x; d < nbins; d += KT) rhist[(int64_t)d * nchunks + blockIdx.x] = h[d];
 }
 
 // Digit histogram of one chunk for the passes after the first.
 __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
                                                     int dw, int nchunks, uint32_t *__restrict__ rhist) {
     __shared__ uint32_t h[1 << DMAX];
-    const int nb = 1 << dw, lane = threadIdx.x & 31;
+    const int nb = 1 << dw, lane = threadIdx.x & 31;   // passes after the first use full dw-bit digits
     for (int d = threadIdx.x; d < nb; d += 256) h[d] = 0;
     __syncthreads();
     const int64_t c0 = (int64_t)blockIdx.x * RT;
@@ -159,89 +162,92 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint32_t *__restrict__
     for (int d = threadIdx.x; d < nb; d += 256) rhist[(int64_t)d * nchunks + blockIdx.x] = h[d];
 }
 
-// Order-preserving scatter of one chunk.  Warp w owns the contiguous eighth
-// [w RT/8, (w+1) RT/8) of the chunk: a first sweep counts its digits, a
+// Order-preserving scatter of one chunk.  Warp w owns the contiguous
+// [w RT/ST_W, (w+1) RT/ST_W) of the chunk: a first sweep counts its digits, a
 // prefix over warps gives every warp its place inside the chunk's run of each
 // digit, and a second sweep places the items (rank among equal digits from
-// __match_any_sync, lower lanes first).  vin == nullptr means the identity
-// (first pass); on the last pass (uv_out != nullptr) the sorted original
-// indices and positions are written instead of keys.
-__global__ void __launch_bounds__(256) k_radix_scatter(const uint32_t *__restrict__ kin,
-                                                       const uint32_t *__restrict__ vin, int64_t n,
-                                                       int shift, int dw, int nchunks,
-                                                       const uint32_t *__restrict__ offs,
-                                                       uint32_t *__restrict__ kout,
-                                                       uint32_t *__restrict__ vout,
-                                                       const float2 *__restrict__ uv,
-                                                       float2 *__restrict__ uv_out) {
-    __shared__ uint16_t wloc[8][1 << DMAX];
-    __shared__ uint32_t base[1 << DMAX];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nb = 1 << dw;
-    const uint32_t dmask = (uint32_t)(nb - 1);
-    for (int d = threadIdx.x; d < nb; d += 256) {
-        base[d] = offs[(int64_t)d * nchunks + blockIdx.x];
+// __match_any_sync, lower lanes first).  The chunk's start of each digit is
+// the scanned histogram (local scan + its block's offset).  vin == nullptr
+// means the identity (first pass); on the last pass (uv_out != nullptr) the
+// sorted original indices and positions are written instead of keys.
+constexpr int ST_W = 16;                 // warps per scatter CTA
+constexpr int ST_R = RT / ST_W / 32;     // rounds per warp
+__global__ void __launch_bounds__(ST_W * 32) k_radix_scatter(const uint32_t *__restrict__ kin,
+                                                             const uint32_t *__restrict__ vin, int64_t n,
+                                                             int shift, int nbins, uint32_t dmask, int nchunks,
+                                                             const uint32_t *__restrict__ offs,
+                                                             const uint32_t *__restrict__ bsum,
+                                                             uint32_t *__restrict__ kout,
+                                                             uint32_t *__restrict__ vout,
+                                                             const float2 *__restrict__ uv,
+                                                             float2 *__restrict__ uv_out) {
+    extern __shared__ __align__(16) uint8_t ssm[];
+    uint32_t *base = (uint32_t *)ssm;                    // [nbins]
+    uint16_t *wloc = (uint16_t *)(base + nbins);         // [ST_W][nbins]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int d = threadIdx.x; d < nbins; d += blockDim.x) {
+        const int64_t e = (int64_t)d * nchunks + blockIdx.x;
+        base[d] = offs[e] + bsum[e / 4096];
 #pragma unroll
-        for (int w = 0; w < 8; ++w) wloc[w][d] = 0;
+        for (int w = 0; w < ST_W; ++w) wloc[w * nbins + d] = 0;
     }
     __syncthreads();
-    constexpr int NR = RT / 8 / 32;   // rounds per warp
-    const int64_t w0 = (int64_t)blockIdx.x * RT + warp * (RT / 8);
-    uint32_t kv[NR];                  // the warp's keys, loaded once with all loads in flight
+    const int64_t w0 = (int64_t)blockIdx.x * RT + warp * (RT / ST_W);
+    uint32_t kv[ST_R];                // the warp's keys, loaded once with all loads in flight
 #pragma unroll
-    for (int k = 0; k < NR; ++k) {
+    for (int k = 0; k < ST_R; ++k) {
         const int64_t e = w0 + k * 32 + lane;
         kv[k] = e < n ? kin[e] : 0u;
     }
 #pragma unroll
-    for (int k = 0; k < NR; ++k) {
+    for (int k = 0; k < ST_R; ++k) {
         const int64_t e = w0 + k * 32 + lane;
         const bool on = e < n;
         const uint32_t d = on ? (kv[k] >> shift) & dmask : 0x10000u + lane;
         const unsigned peers = __match_any_sync(FULL, d);
-        if (on && lane == __ffs(peers) - 1) wloc[warp][d] += (uint16_t)__popc(peers);
+        if (on && lane == __ffs(peers) - 1) wloc[warp * nbins + d] += (uint16_t)__popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < nb; d += 256) {
+    for (int d = threadIdx.x; d < nbins; d += blockDim.x) {
         uint32_t run = 0;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
-            const uint32_t c = wloc[w][d];
-            wloc[w][d] = (uint16_t)run;
+        for (int w = 0; w < ST_W; ++w) {
+            const uint32_t c = wloc[w * nbins + d];
+            wloc[w * nbins + d] = (uint16_t)run;
             run += c;
         }
     }
     __syncthreads();
-    uint32_t vv[NR];
+    uint32_t vv[ST_R];
 #pragma unroll
-    for (int k = 0; k < NR; ++k) {
+    for (int k = 0; k < ST_R; ++k) {
         const int64_t e = w0 + k * 32 + lane;
         vv[k] = vin ? (e < n ? vin[e] : 0u) : (uint32_t)e;
     }
-    float2 pv[NR];
+    float2 pv[ST_R];
     if (uv_out) {
 #pragma unroll
-        for (int k = 0; k < NR; ++k) pv[k] = w0 + k * 32 + lane < n ? uv[vv[k]] : make_float2(0.f, 0.f);
+        for (int k = 0; k < ST_R; ++k) pv[k] = w0 + k * 32 + lane < n ? uv[vv[k]] : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int k = 0; k < NR; ++k) {
+    for (int k = 0; k < ST_R; ++k) {
         const int64_t e = w0 + k * 32 + lane;
         const bool on = e < n;
         const uint32_t key = kv[k];
         const uint32_t d = on ? (key >> shift) & dmask : 0x10000u + lane;
         const unsigned peers = __match_any_sync(FULL, d);
         if (on) {
-            const uint32_t pos = base[d] + wloc[warp][d] + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+            const uint32_t pos = base[d] + wloc[warp * nbins + d] + (uint32_t)__popc(peers & ((1u << lane) - 1u));
             vout[pos] = vv[k];
             if (uv_out) uv_out[pos] = pv[k];
             else kout[pos] = key;
         }
         __syncwarp();
-        if (on && lane == __ffs(peers) - 1) wloc[warp][d] += (uint16_t)__popc(peers);
+        if (on && lane == __ffs(peers) - 1) wloc[warp * nbins + d] += (uint16_t)__popc(peers);
         __syncwarp();
     }
 }
-
 
 // Block-wide exclusive scan of one value per thread (blockDim.x == 1024).
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *sh, uint32_t &total) {
@@ -270,59 +276,14 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     return warp_base + x - v;
 }
 
-// Exclusive scan, level 1: 4096 elements per 1024-thread block.
-__global__ void __launch_bounds__(1024) k_scan_local(const uint32_t *__restrict__ in, int64_t len,
-                                                     uint32_t *__restrict__ out,
-                                                     uint32_t *__restrict__ block_sums) {
-    __shared__ uint32_t sh[32];
-    const int64_t base = (int64_t)blockIdx.x * 4096 + threadIdx.x * 4;
-    uint32_t v[4];
-    uint32_t s = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        v[k] = base + k < len ? in[base + k] : 0u;
-        s += v[k];
-    }
-    uint32_t total;
-    uint32_t pre = block_exclusive_scan(s, sh, total);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (base + k < len) out[base + k] = pre;
-        pre += v[k];
-    }
-    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
-}
-
-// Level 2: one block scans the block sums in place (any length).
-__global__ void __launch_bounds__(1024) k_scan_top(uint32_t *__restrict__ sums, int64_t len) {
-    __shared__ uint32_t sh[32];
-    uint32_t carry = 0;
-    for (int64_t b = 0; b < len; b += 1024) {
-        const int64_t i = b + threadIdx.x;
-        const uint32_t v = i < len ? sums[i] : 0u;
-        uint32_t total;
-        const uint32_t pre = block_exclusive_scan(v, sh, total);
-        if (i < len) sums[i] = carry + pre;
-        carry += total;
-    }
-}
-
-__global__ void k_scan_add(uint32_t *__restrict__ out, int64_t len,
-                           const uint32_t *__restrict__ block_sums) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < len) out[i] += block_sums[i / 4096];
-}
-
-
-// One block: cut every tile's run of sorted visibilities into units of <= UMAX.
-__global__ void __launch_bounds__(1024) k_units(const uint32_t *__restrict__ hist, int ntiles,
-                                                int4 *__restrict__ units, int *__restrict__ n_units,
-                                                int cap, uint32_t *__restrict__ n_valid_out) {
-    __shared__ uint32_t sh[32];
+// Cut every tile's run of sorted visibilities into units of <= UMAX (one
+// block of 1024 threads; tile totals in hist).
+__device__ void cut_units(const uint32_t *__restrict__ hist, int ntiles, int4 *__restrict__ units,
+                          int *__restrict__ n_units, int cap, uint32_t *__restrict__ n_valid_out, uint32_t *sh) {
     uint32_t carry = 0, base = 0;
-    for (int b = 0; b < ntiles; b += 1024) {
+    for (int b = 0; b < ntiles; b += blockDim.x) {
         const int t = b + threadIdx.x;
-        const uint32_t c = t < ntiles ? hist[t] : 0u;
+        const uint32_t c = t < ntiles ? __ldcg(hist + t) : 0u;
         uint32_t ctot;
         const uint32_t start = base + block_exclusive_scan(c, sh, ctot);   // tile offset in sorted order
         const uint32_t nu = (c + UMAX - 1) / UMAX;
@@ -342,6 +303,61 @@ __global__ void __launch_bounds__(1024) k_units(const uint32_t *__restrict__ his
         *n_units = min((int)carry, cap);
         *n_valid_out = base;
     }
+}
+
+// Exclusive scan of len values, 4096 per 1024-thread block: every block scans
+// its part into out and writes its total; the last block to finish (ticket)
+// scans the totals in place into block offsets (so element e's exclusive
+// prefix is out[e] + bsum[e / 4096]), optionally cuts the gridding units from
+// the tile totals, and re-arms the ticket.
+__global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ in, int64_t len,
+                                               uint32_t *__restrict__ out, uint32_t *__restrict__ bsum,
+                                               unsigned *__restrict__ ticket,
+                                               const uint32_t *__restrict__ tile_hist, int ntiles,
+                                               int4 *__restrict__ units, int *__restrict__ n_units, int cap,
+                                               uint32_t *__restrict__ n_valid_out) {
+    __shared__ uint32_t sh[32];
+    __shared__ bool last;
+    const int64_t base = (int64_t)blockIdx.x * 4096 + threadIdx.x * 4;
+    uint32_t v[4];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[k] = base + k < len ? in[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t total;
+    uint32_t pre = block_exclusive_scan(s, sh, total);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (base + k < len) out[base + k] = pre;
+        pre += v[k];
+    }
+    if (threadIdx.x == 0) {
+        bsum[blockIdx.x] = total;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    uint32_t carry = 0;
+    for (int64_t b = 0; b < gridDim.x; b += 1024) {
+        const int64_t i = b + threadIdx.x;
+        const uint32_t x = i < gridDim.x ? __ldcg(bsum + i) : 0u;
+        uint32_t t;
+        const uint32_t p = block_exclusive_scan(x, sh, t);
+        if (i < gridDim.x) bsum[i] = carry + p;
+        carry += t;
+    }
+    if (tile_hist) cut_units(tile_hist, ntiles, units, n_units, cap, n_valid_out, sh);
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+__global__ void k_scan_add(uint32_t *__restrict__ out, int64_t len,
+                           const uint32_t *__restrict__ block_sums) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) out[i] += block_sums[i / 4096];
 }
 
 // ------------------------------------------------------------------ accumulation
@@ -666,12 +682,15 @@ bool plan_bufs(abs_ctx *ctx, const GridGeom &G, int64_t n_vis, PlanBufs &b) {
 
 }  // namespace
 
-// Exclusive scan of len uint32 values (3 kernels; bsum needs cdiv(len, 4096) + 1 entries).
-void scan_u32(cudaStream_t st, const uint32_t *in, int64_t len, uint32_t *out, uint32_t *bsum) {
+// Exclusive scan of len uint32 values (2 kernels; bsum needs cdiv(len, 4096) + 1 entries).
+bool scan_u32(abs_ctx *ctx, const uint32_t *in, int64_t len, uint32_t *out, uint32_t *bsum) {
+    unsigned *ticket = (unsigned *)workspace_zeroed(ctx, "scan.ticket", sizeof(unsigned));
+    if (!ticket) return false;
     const int nblk = (int)cdiv(len, 4096);
-    k_scan_local<<<nblk, 1024, 0, st>>>(in, len, out, bsum);
-    k_scan_top<<<1, 1024, 0, st>>>(bsum, nblk);
-    k_scan_add<<<(int)cdiv(len, 256), 256, 0, st>>>(out, len, bsum);
+    if (nblk == 0) return true;
+    k_scan<<<nblk, 1024, 0, ctx->stream>>>(in, len, out, bsum, ticket, nullptr, 0, nullptr, nullptr, 0, nullptr);
+    k_scan_add<<<(int)cdiv(len, 256), 256, 0, ctx->stream>>>(out, len, bsum);
+    return true;
 }
 
 abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv) {
@@ -684,33 +703,44 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
     const int passes = (bits + DMAX - 1) / DMAX;
     if (passes > 2) return fail(ctx, ABS_ERR_UNSUPPORTED, "uv tile count beyond two radix passes");
     const int dw = (bits + passes - 1) / passes;
-    const int64_t rlen = ((int64_t)1 << dw) * b.nchunks;
+    // one pass: the digit is the key itself, so exactly ntiles + 1 bins
+    const int nbins0 = passes == 1 ? b.ntiles + 1 : 1 << dw;
+    const int64_t rlen = (int64_t)(1 << dw) * b.nchunks;
     uint32_t *bsum = (uint32_t *)workspace(ctx, "plan.bsum", sizeof(uint32_t) * (cdiv(rlen, 4096) + 1));
-    if (!bsum) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
+    unsigned *ticket = (unsigned *)workspace_zeroed(ctx, "scan.ticket", sizeof(unsigned));
+    if (!bsum || !ticket) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
     cudaStream_t st = ctx->stream;
     StageTimer timer(ctx, "grid_plan");
     cudaMemsetAsync(b.tile_hist, 0, sizeof(uint32_t) * b.ntiles, st);
-    if (n_vis > 0)
-        k_plan_keys<<<b.nchunks, 256, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, b.tile_hist, key_none, dw,
-                                               b.nchunks, b.rhist);
-    k_units<<<1, 1024, 0, st>>>(b.tile_hist, b.ntiles, b.units, b.n_units, b.units_cap, b.n_valid);
-    if (n_vis > 0) {
-        // stable sort of (tile, index): keys -> (k2, v2) -> ... -> (s_idx, s_uv)
-        const uint32_t *ki = b.keys, *vi = nullptr;
-        uint32_t *ko = b.k2, *vo = b.v2;
-        uint32_t *kalt = b.keys, *valt = b.s_idx;   // ping-pong partners after the first pass
-        for (int ps = 0; ps < passes; ++ps) {
-            const bool last = ps == passes - 1;
-            if (ps > 0) k_radix_hist<<<b.nchunks, 256, 0, st>>>(ki, n_vis, dw * ps, dw, b.nchunks, b.rhist);
-            scan_u32(st, b.rhist, rlen, b.roffs, bsum);
-            k_radix_scatter<<<b.nchunks, 256, 0, st>>>(ki, vi, n_vis, dw * ps, dw, b.nchunks, b.roffs,
-                                                       last ? nullptr : ko, last ? b.s_idx : vo,
-                                                       (const float2 *)d_uv, last ? b.s_uv : nullptr);
-            ki = ko;
-            vi = vo;
-            std::swap(ko, kalt);
-            std::swap(vo, valt);
-        }
+    if (n_vis == 0) {
+        // no visibilities: no units
+        k_scan<<<1, 1024, 0, st>>>(b.rhist, 0, b.roffs, bsum, ticket, b.tile_hist, b.ntiles, b.units, b.n_units,
+                                   b.units_cap, b.n_valid);
+        return check_launch(ctx, "grid plan");
+    }
+    const size_t ssmem0 = (size_t)nbins0 * (4 + 2 * ST_W), ssmem = (size_t)(1 << dw) * (4 + 2 * ST_W);
+    cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)std::max(ssmem0, ssmem));
+    k_plan_keys<<<b.nchunks, KT, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, b.tile_hist, key_none, nbins0,
+                                          passes == 1 ? 0xffffffffu : (uint32_t)((1 << dw) - 1), b.nchunks,
+                                          b.rhist);
+    // stable sort of (tile, index): keys -> (k2, v2) -> (s_idx, s_uv); the first
+    // scan also cuts the units from the tile totals
+    const uint32_t *ki = b.keys, *vi = nullptr;
+    for (int ps = 0; ps < passes; ++ps) {
+        const bool last = ps == passes - 1;
+        const int nbins = ps == 0 ? nbins0 : 1 << dw;
+        const uint32_t dmask = passes == 1 ? 0xffffffffu : (uint32_t)((1 << dw) - 1);
+        if (ps > 0) k_radix_hist<<<b.nchunks, 256, 0, st>>>(ki, n_vis, dw * ps, dw, b.nchunks, b.rhist);
+        const int64_t len = (int64_t)nbins * b.nchunks;
+        k_scan<<<(int)cdiv(len, 4096), 1024, 0, st>>>(b.rhist, len, b.roffs, bsum, ticket,
+                                                      ps == 0 ? b.tile_hist : nullptr, b.ntiles, b.units,
+                                                      b.n_units, b.units_cap, b.n_valid);
+        k_radix_scatter<<<b.nchunks, ST_W * 32, ps == 0 ? ssmem0 : ssmem, st>>>(
+            ki, vi, n_vis, dw * ps, nbins, dmask, b.nchunks, b.roffs, bsum, last ? nullptr : b.k2,
+            last ? b.s_idx : b.v2, (const float2 *)d_uv, last ? b.s_uv : nullptr);
+        ki = b.k2;
+        vi = b.v2;
     }
     return check_launch(ctx, "grid plan");
 }
