@@ -42,10 +42,10 @@ UNIT = "estimates/s"
 # kernels launched per stage-timer entry (the profiler brackets stages); the
 # gridding plan runs the key kernel and, per radix pass of up to 11-bit digits
 # of the uv tile id, a fused scan and a scatter (plus a histogram kernel on
-# passes after the first); the ring lists run rows, a 2-kernel scan, write and
-# finish
-KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "ring_lists": 5,
-                     "count_items": 1, "count_pairs": 1, "count_gather": 1, "ellbar": 5,
+# passes after the first); the ring lists run cells and finish; the pair
+# counts run once per byte map (filled, annulus)
+KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "grid_mask": 1, "ring_lists": 2,
+                     "count_items": 1, "count_pairs": 2, "count_gather": 1, "ellbar": 2,
                      "fft_rows": 1, "fft_cols": 1, "triple_fp32": 1, "triple_reduce": 1,
                      "normalise": 1, "check_triplets": 1, "tc_rows": 1, "triple_tc": 1}
 

@@ -31,14 +31,17 @@ struct Setup {
     std::vector<int> radices;     // N = prod(radices)
     std::vector<int64_t> lat;     // lattice cells per ring (full annulus, on the grid)
     std::vector<int64_t> lat_off; // nb+1 prefix offsets of lat
+    std::vector<int64_t> up_off;  // nb+1 prefix offsets of lat/2 (upper half plane of each ring)
     std::vector<int32_t> ijk;     // canonical closing triplets [t][3]
     int precision = ABS_FP32;
     double norm_A = 1.0;
     // device copies (owned by the context)
     int64_t *d_q = nullptr;
     int64_t *d_lat_off = nullptr;
+    int64_t *d_ring_off = nullptr;  // [3][nb+1] family f, ring m: f * up_off[nb] + up_off[m]
     int32_t *d_ijk = nullptr;
-    float4 *d_tw = nullptr;       // exp(-2 pi i t / N), t < N, as double-float (re hi, lo, im hi, lo)
+    float4 *d_tw = nullptr;       // exp(-2 pi i t / N) = c + i s, t < N, as packed double-float pairs:
+                                  // [2t] = (c.hi, c.hi, c.lo, c.lo), [2t+1] = (-s.hi, s.hi, -s.lo, s.lo)
     int32_t *d_Rm = nullptr;
     // ordered closed-triangle counts of the full annuli [nb][nb][nb] (halved),
     // a property of the ring geometry, computed on first use
@@ -105,6 +108,8 @@ const Setup *get_setup(abs_ctx *ctx, const abs_config *cfg, abs_status &st);
 // Gridding is split in a per-baseline-set plan (sort by uv tile and cell) and a
 // per-realisation accumulation that reuses it.
 abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv);
+// With d_grid == d_wsum == nullptr only the FP64 accumulators (and, if d_mask,
+// the filled mask) are produced.
 abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_vis,
                                   float *d_grid, float *d_wsum, uint8_t *d_mask);
 abs_status launch_filter_fft(abs_ctx *ctx, const Setup &s, const float *d_grid,
@@ -118,8 +123,11 @@ abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc
 // exactly when its weight sum is > 0 (every footprint weight is a normal,
 // positive FP32 number, which the sigma_cells bound guarantees).
 void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc);
+// With d_count and d_B also given, B = S / (A T) is written as well (fused
+// into the final reduction on the FP32 path).
 abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_fields,
-                              int32_t n_trip, const int32_t *d_ijk, double *d_sum);
+                              int32_t n_trip, const int32_t *d_ijk, double *d_sum,
+                              const int64_t *d_count = nullptr, double *d_B = nullptr);
 // Split-BF16 tcgen05 form of the same sums (precision == ABS_SPLIT_BF16).
 abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
                             int32_t n_trip, const int32_t *d_ijk, double *d_sum);

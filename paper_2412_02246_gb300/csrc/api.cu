@@ -178,6 +178,9 @@ abs_status make_setup(const abs_config *cfg, Setup &s, std::string &err) {
         }
     s.lat_off.assign(s.nb + 1, 0);
     for (int m = 0; m < s.nb; ++m) s.lat_off[m + 1] = s.lat_off[m] + s.lat[m];
+    // the lattice is closed under g -> -g and misses the origin: lat is even
+    s.up_off.assign(s.nb + 1, 0);
+    for (int m = 0; m < s.nb; ++m) s.up_off[m + 1] = s.up_off[m] + s.lat[m] / 2;
     closing_triplets(s.q, s.ijk);
     s.precision = cfg->precision;
     s.norm_A = cfg->norm_A;
@@ -257,6 +260,8 @@ static T *upload(const std::vector<T> &v) {
 static void free_setup(Setup &s) {
     cudaFree(s.d_q);
     cudaFree(s.d_lat_off);
+    cudaFree(s.d_ring_off);
+    s.d_ring_off = nullptr;
     cudaFree(s.d_ijk);
     cudaFree(s.d_tw);
     cudaFree(s.d_Rm);
@@ -288,19 +293,28 @@ const Setup *get_setup(abs_ctx *ctx, const abs_config *cfg, abs_status &st) {
         fail(ctx, st, err);
         return nullptr;
     }
-    std::vector<float4> tw(s->N);
+    // twiddles laid out for the packed (re, im) complex multiply of the transforms
+    std::vector<float4> tw(2 * (size_t)s->N);
     for (int t = 0; t < s->N; ++t) {
         const double a = 2.0 * M_PI * (double)t / (double)s->N;
         const double c = std::cos(a), sn = -std::sin(a);
         const float ch = (float)c, sh = (float)sn;
-        tw[t] = make_float4(ch, (float)(c - (double)ch), sh, (float)(sn - (double)sh));
+        const float cl = (float)(c - (double)ch), sl = (float)(sn - (double)sh);
+        tw[2 * t] = make_float4(ch, ch, cl, cl);
+        tw[2 * t + 1] = make_float4(-sh, sh, -sl, sl);
     }
     s->d_q = upload(s->q);
     s->d_lat_off = upload(s->lat_off);
+    {
+        std::vector<int64_t> ro(3 * (size_t)(s->nb + 1));
+        for (int f = 0; f < 3; ++f)
+            for (int m = 0; m <= s->nb; ++m) ro[(size_t)f * (s->nb + 1) + m] = f * s->up_off[s->nb] + s->up_off[m];
+        s->d_ring_off = upload(ro);
+    }
     s->d_ijk = upload(s->ijk);
     s->d_tw = upload(tw);
     s->d_Rm = upload(std::vector<int32_t>(s->Rm.begin(), s->Rm.end()));
-    if (!s->d_q || !s->d_lat_off || !s->d_ijk || !s->d_tw || !s->d_Rm) {
+    if (!s->d_q || !s->d_lat_off || !s->d_ring_off || !s->d_ijk || !s->d_tw || !s->d_Rm) {
         free_setup(*s);
         st = fail(ctx, ABS_ERR_OOM, "setup tables");
         return nullptr;
@@ -554,17 +568,18 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
                                 const int32_t *d_ijk, double *d_B, int64_t *d_count, double *d_ellbar) {
     const int64_t cells = (int64_t)s.n * s.n;
     const int64_t P = (int64_t)s.N * s.N;
-    float *grid = (float *)workspace(ctx, "est.grid", sizeof(float) * 2 * cells);
-    float *wsum = (float *)workspace(ctx, "est.wsum", sizeof(float) * cells);
     uint8_t *mask = (uint8_t *)workspace(ctx, "est.mask", cells);
     float *fields = (float *)workspace(ctx, "est.fields", sizeof(float) * (size_t)s.nb * P);
     double *sum = (double *)workspace(ctx, "est.sum", sizeof(double) * std::max(n_trip, 1));
     int64_t *count = d_count ? d_count : (int64_t *)workspace(ctx, "est.count", sizeof(int64_t) * std::max(n_trip, 1));
-    if (!grid || !wsum || !mask || !fields || !sum || !count) return fail(ctx, ABS_ERR_OOM, "estimate workspace");
-    ABS_CHECK(launch_check_triplets(ctx, s, n_trip, d_ijk));
+    if (!mask || !fields || !sum || !count) return fail(ctx, ABS_ERR_OOM, "estimate workspace");
+    // the canonical list (d_ijk == NULL at the ABI) was built and checked with the setup
+    if (d_ijk != s.d_ijk) ABS_CHECK(launch_check_triplets(ctx, s, n_trip, d_ijk));
     ABS_CHECK(launch_grid_plan(ctx, s, n_vis, d_uv));
     for (int32_t r = 0; r < n_real; ++r) {
-        ABS_CHECK(launch_grid_accumulate(ctx, s, n_vis, d_vis + (size_t)r * 2 * n_vis, grid, wsum, mask));
+        // the transform reads the FP64 accumulators; the mask is needed once
+        ABS_CHECK(launch_grid_accumulate(ctx, s, n_vis, d_vis + (size_t)r * 2 * n_vis, nullptr, nullptr,
+                                         r == 0 ? mask : nullptr));
         if (r == 0) {
             // the filled mask depends on the baselines only: counts and mean l once
             ABS_CHECK(launch_counts(ctx, s, mask, n_trip, d_ijk, count, d_ellbar));
@@ -572,8 +587,8 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
         double *acc;
         grid_acc_buffers(ctx, s, &acc);
         ABS_CHECK(launch_filter_fft_acc(ctx, s, acc, fields));
-        ABS_CHECK(launch_triple_sums(ctx, s, fields, n_trip, d_ijk, sum));
-        if (d_B) ABS_CHECK(launch_normalise(ctx, s, n_trip, sum, count, d_B + (size_t)r * n_trip));
+        ABS_CHECK(launch_triple_sums(ctx, s, fields, n_trip, d_ijk, sum, count,
+                                     d_B ? d_B + (size_t)r * n_trip : nullptr));
     }
     return ABS_OK;
 }

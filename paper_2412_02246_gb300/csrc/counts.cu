@@ -56,9 +56,11 @@ __device__ __forceinline__ int64_t cell_index(int n, int gx, int gy) {
     return (int64_t)(gy < 0 ? gy + n : gy) * n + (gx < 0 ? gx + n : gx);
 }
 
+// floor(sqrt(v)) for 0 <= v < 2^53: an FP32 estimate corrected in integers
+// (v here is below 2^26, where the estimate is off by at most one).
 __device__ __forceinline__ int64_t isqrt_dev(int64_t v) {
     if (v <= 0) return 0;
-    int64_t r = (int64_t)sqrt((double)v);
+    int64_t r = (int64_t)sqrtf((float)v);
     while (r * r > v) --r;
     while ((r + 1) * (r + 1) <= v) ++r;
     return r;
@@ -114,8 +116,6 @@ struct Fams {
     const int32_t *cnt;   // [NFAM][nb]
 };
 
-// Pass 1 (one warp per (ring, row)): filled, hole and annulus cells; FP64 sum
-// of |g| over the filled ones.  rowcnt is [NFAM][nb * rows].
 // sqrt(v) of a non-negative integer v < 2^31 as a double-float pair h + l
 // (relative error about 2^-46), with 32-bit arithmetic only: GB300's FP64 pipe
 // (which also converts 64-bit integers) is too narrow for a square root per
@@ -144,26 +144,60 @@ __device__ __forceinline__ void df_add(float &sh, float &sl, float h, float l) {
     sl = __fsub_rn(lo, __fsub_rn(sh, t));
 }
 
-__global__ void k_ring_rows(CountGeom G, const int64_t *__restrict__ q, const uint8_t *__restrict__ mask,
-                            uint32_t *__restrict__ rowcnt, double *__restrict__ rowlen) {
-    const int rows = 2 * G.R + 1;
+// One warp per (ring, row y >= 0): the ring's cells of the upper half plane
+// (y > 0, or y = 0 and x > 0) in that row, split into filled (F), hole (H)
+// and annulus (A) cells.  Each family list of a ring holds only its upper
+// half plane (its lower half is the negation, since every family is closed
+// under g -> -g), at a static offset with room for the whole upper half of the
+// ring's lattice; a warp reserves its place with one atomic per family and
+// batch of 32 cells, so rows land in any order (the counts do not depend on
+// it).  Also writes the byte maps of F and A (at lin > 0) and the row's sum of
+// |g| over filled cells in double-float.
+__global__ void k_ring_cells(CountGeom G, const int64_t *__restrict__ q, const uint8_t *__restrict__ mask,
+                             const int64_t *__restrict__ ring_off, int32_t *__restrict__ cnt_up,
+                             short2 *__restrict__ lists, uint8_t *__restrict__ mapF, uint8_t *__restrict__ mapA,
+                             double *__restrict__ rowlen) {
+    const int rows = G.R + 1;
     const int64_t nrow = (int64_t)G.nb * rows;
     const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (e >= nrow) return;
-    const int m = e / rows, y = e - m * rows - G.R;
+    const int m = e / rows, y = e - m * rows;
     const RowSpan sp = row_span(G, q[m], q[m + 1], y);
     const int len = span_len(sp);
-    uint32_t c = 0;
-    float sh = 0.f, sl = 0.f;   // sum of |g| as a double-float pair
+    const unsigned below = (1u << lane) - 1u;
+    short2 *LF = lists + ring_off[FAM_F * (G.nb + 1) + m];
+    short2 *LH = lists + ring_off[FAM_H * (G.nb + 1) + m];
+    short2 *LA = lists + ring_off[FAM_A * (G.nb + 1) + m];
+    float sh = 0.f, sl = 0.f;
     for (int t0 = 0; t0 < len; t0 += 32) {
         const int t = t0 + lane;
-        bool on = false;
         int x = 0;
-        if (t < len) {
+        bool in = t < len;
+        if (in) {
             x = span_x(sp, t);
-            on = mask[cell_index(G.n, x, y)] != 0;
+            in = y > 0 || x > 0;
         }
-        c += __popc(__ballot_sync(FULL, on));
+        const bool on = in && mask[cell_index(G.n, x, y)] != 0;
+        const unsigned bf = __ballot_sync(FULL, on), bh = __ballot_sync(FULL, in && !on);
+        const unsigned ba = __ballot_sync(FULL, in);
+        int pf = 0, ph = 0, pa = 0;
+        if (lane == 0) {
+            if (bf) pf = atomicAdd(&cnt_up[FAM_F * G.nb + m], __popc(bf));
+            if (bh) ph = atomicAdd(&cnt_up[FAM_H * G.nb + m], __popc(bh));
+            if (ba) pa = atomicAdd(&cnt_up[FAM_A * G.nb + m], __popc(ba));
+        }
+        pf = __shfl_sync(FULL, pf, 0);
+        ph = __shfl_sync(FULL, ph, 0);
+        pa = __shfl_sync(FULL, pa, 0);
+        if (in) {
+            const short2 g = make_short2((short)x, (short)y);
+            LA[pa + __popc(ba & below)] = g;
+            if (on) LF[pf + __popc(bf & below)] = g;
+            else LH[ph + __popc(bh & below)] = g;
+            const int lin = y * G.W + x;   // > 0 in the upper half plane
+            mapA[lin] = (uint8_t)(m + 1);
+            if (on) mapF[lin] = (uint8_t)(m + 1);
+        }
         if (on) {
             float h, l;
             df_sqrt_int(x * x + y * y, h, l);   // |x|, |y| <= n/2 <= 4096
@@ -175,77 +209,27 @@ __global__ void k_ring_rows(CountGeom G, const int64_t *__restrict__ q, const ui
         const float oh = __shfl_xor_sync(FULL, sh, o), ol = __shfl_xor_sync(FULL, sl, o);
         df_add(sh, sl, oh, ol);
     }
-    if (lane == 0) {
-        rowcnt[e] = c;
-        rowcnt[nrow + e] = (uint32_t)len - c;
-        rowcnt[2 * nrow + e] = (uint32_t)len;
-        rowlen[e] = (double)sh + (double)sl;
-    }
+    if (lane == 0) rowlen[e] = (double)sh + (double)sl;
 }
 
-// Pass 2 (one warp per (ring, row)): write the three families in x order and
-// the byte maps of F and A.
-__global__ void k_ring_write(CountGeom G, const int64_t *__restrict__ q, const uint8_t *__restrict__ mask,
-                             const uint32_t *__restrict__ rowoff, short2 *__restrict__ lists,
-                             uint8_t *__restrict__ mapF, uint8_t *__restrict__ mapA) {
-    const int rows = 2 * G.R + 1;
-    const int64_t nrow = (int64_t)G.nb * rows;
-    const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (e >= nrow) return;
-    const int m = e / rows, y = e - m * rows - G.R;
-    const RowSpan sp = row_span(G, q[m], q[m + 1], y);
-    const int len = span_len(sp);
-    uint32_t pf = rowoff[e], ph = rowoff[nrow + e];
-    const uint32_t pa = rowoff[2 * nrow + e];
-    for (int t0 = 0; t0 < len; t0 += 32) {
-        const int t = t0 + lane;
-        bool on = false, in = t < len;
-        int x = 0;
-        if (in) {
-            x = span_x(sp, t);
-            on = mask[cell_index(G.n, x, y)] != 0;
-        }
-        const unsigned bf = __ballot_sync(FULL, on), bh = __ballot_sync(FULL, in && !on);
-        const unsigned below = (1u << lane) - 1u;
-        if (in) {
-            const short2 g = make_short2((short)x, (short)y);
-            lists[pa + t] = g;
-            if (on) lists[pf + __popc(bf & below)] = g;
-            else lists[ph + __popc(bh & below)] = g;
-            const int lin = y * G.W + x;
-            if (lin > 0) {
-                mapA[lin] = (uint8_t)(m + 1);
-                if (on) mapF[lin] = (uint8_t)(m + 1);
-            }
-        }
-        pf += __popc(bf);
-        ph += __popc(bh);
-    }
-}
-
-// Pass 3 (one warp per (family, ring)): offsets, counts, and the mean l of the
-// filled cells (fixed-order sums).
-__global__ void k_ring_finish(CountGeom G, float du, const uint32_t *__restrict__ rowoff,
-                              const uint32_t *__restrict__ rowcnt, const double *__restrict__ rowlen,
-                              int64_t *__restrict__ ring_off, int32_t *__restrict__ counts,
+// One warp per (family, ring): full counts (twice the upper half plane) and
+// the mean l of the filled cells (the upper half plane has the same mean;
+// fixed-order sums over the rows).
+__global__ void k_ring_finish(CountGeom G, float du, const int32_t *__restrict__ cnt_up,
+                              const double *__restrict__ rowlen, int32_t *__restrict__ counts,
                               double *__restrict__ ellbar) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (w >= NFAM * G.nb) return;
     const int fam = w / G.nb, m = w - fam * G.nb;
-    const int rows = 2 * G.R + 1;
-    const int64_t nrow = (int64_t)G.nb * rows;
-    const int64_t e0 = fam * nrow + (int64_t)m * rows, e1 = e0 + rows;
-    const uint32_t start = rowoff[e0];
-    const uint32_t c = rowoff[e1 - 1] + rowcnt[e1 - 1] - start;
+    const int rows = G.R + 1;
+    const int32_t c = cnt_up[fam * G.nb + m];
     double len = 0.0;
     if (fam == FAM_F)
-        for (int64_t e = e0 + lane; e < e1; e += 32) len += rowlen[e];
+        for (int y = lane; y < rows; y += 32) len += rowlen[(int64_t)m * rows + y];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(FULL, len, o);
     if (lane == 0) {
-        ring_off[fam * (G.nb + 1) + m] = start;
-        counts[fam * G.nb + m] = (int32_t)c;
-        if (m == G.nb - 1) ring_off[fam * (G.nb + 1) + G.nb] = start + c;
+        counts[fam * G.nb + m] = 2 * c;
         if (fam == FAM_F && ellbar)
             ellbar[m] = c > 0 ? 2.0 * 3.14159265358979323846 * (double)du * len / (double)c : nan("");
     }
@@ -416,11 +400,10 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
         const int in0 = I.w & 0x07ffffff;
         const int fx = job_x(job), fy = job_y(job);
         const int cxa = fam.cnt[fx * G.nb + a], cyb = fam.cnt[fy * G.nb + b];
-        const short2 *X = fam.lists + fam.off[fx * (G.nb + 1) + a] + cxa / 2;   // upper half plane of X_a
-        const short2 *Y = fam.lists + fam.off[fy * (G.nb + 1) + b];
-        const int nx = cxa / 2;
-        const short2 *Fo = outer_x ? X : Y;
-        const short2 *Fin = (outer_x ? Y : X) + in0;
+        // X_a: its upper half plane; Y_b: whole, as its upper half then its negation
+        const short2 *X = fam.lists + fam.off[fx * (G.nb + 1) + a];
+        const short2 *Yu = fam.lists + fam.off[fy * (G.nb + 1) + b];
+        const int nx = cxa / 2, hy = cyb / 2;
         const int no = outer_x ? nx : cyb;
         const int nin = min(INNER, (outer_x ? cyb : nx) - in0);
         int lin1[G1];
@@ -429,8 +412,13 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
         for (int q = 0; q < G1; ++q) {
             const int k = I.z + q * blockDim.x + threadIdx.x;
             v1[q] = k < no;
-            const short2 g = v1[q] ? Fo[k] : make_short2(0, 0);
-            lin1[q] = g.y * G.W + g.x;
+            int l = 0;
+            if (v1[q]) {
+                const short2 g = outer_x ? X[k] : Yu[k < hy ? k : k - hy];
+                l = g.y * G.W + g.x;
+                if (!outer_x && k >= hy) l = -l;
+            }
+            lin1[q] = l;
         }
         int cur[G1];
         uint32_t cnt[G1];
@@ -441,8 +429,17 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
         }
         __syncthreads();
         for (int k = threadIdx.x; k < nin; k += blockDim.x) {
-            const short2 g = Fin[k];
-            stage[k] = g.y * G.W + g.x;
+            const int kk = in0 + k;
+            int l;
+            if (outer_x) {
+                const short2 g = Yu[kk < hy ? kk : kk - hy];
+                l = g.y * G.W + g.x;
+                if (kk >= hy) l = -l;
+            } else {
+                const short2 g = X[kk];
+                l = g.y * G.W + g.x;
+            }
+            stage[k] = l;
         }
         __syncthreads();
         for (int k = 0; k < nin; ++k) {
@@ -520,30 +517,26 @@ struct RingBufs {
 abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, RingBufs &rb,
                        double *d_ellbar) {
     const CountGeom G = cgeom(s);
-    const int64_t ncell = std::max<int64_t>(s.lat_off.back(), 1);
-    const int64_t nrow = (int64_t)s.nb * (2 * s.R + 1);
-    rb.lists = (short2 *)workspace(ctx, "ring.lists", sizeof(short2) * 3 * ncell);
+    const int64_t U = std::max<int64_t>(s.up_off.back(), 1);   // upper-half lattice cells, all rings
+    const int64_t nrow = (int64_t)s.nb * (s.R + 1);
+    rb.lists = (short2 *)workspace(ctx, "ring.lists", sizeof(short2) * NFAM * U);
     rb.counts = (int32_t *)workspace(ctx, "ring.counts", sizeof(int32_t) * NFAM * s.nb);
-    rb.ring_off = (int64_t *)workspace(ctx, "ring.off", sizeof(int64_t) * NFAM * (s.nb + 1));
+    rb.ring_off = s.d_ring_off;
     const int64_t mb = cdiv(G.base + 1, 16) * 16;
-    uint8_t *maps = (uint8_t *)workspace(ctx, "ring.maps", (size_t)2 * mb);
-    uint32_t *rowcnt = (uint32_t *)workspace(ctx, "ring.rowcnt", sizeof(uint32_t) * NFAM * nrow);
-    uint32_t *rowoff = (uint32_t *)workspace(ctx, "ring.rowoff", sizeof(uint32_t) * NFAM * nrow);
+    // byte maps of F and A, then the upper-half-plane counters: cleared together
+    uint8_t *maps = (uint8_t *)workspace(ctx, "ring.maps", (size_t)2 * mb + sizeof(int32_t) * NFAM * s.nb);
     double *rowlen = (double *)workspace(ctx, "ring.rowlen", sizeof(double) * nrow);
-    uint32_t *bsum = (uint32_t *)workspace(ctx, "ring.bsum", sizeof(uint32_t) * (cdiv(NFAM * nrow, 4096) + 1));
-    if (!rb.lists || !rb.counts || !rb.ring_off || !maps || !rowcnt || !rowoff || !rowlen || !bsum)
-        return fail(ctx, ABS_ERR_OOM, "ring table workspace");
+    if (!rb.lists || !rb.counts || !maps || !rowlen) return fail(ctx, ABS_ERR_OOM, "ring table workspace");
     rb.mapF = maps;
     rb.mapA = maps + mb;
+    int32_t *cnt_up = (int32_t *)(maps + 2 * mb);
     StageTimer timer(ctx, "ring_lists");
     cudaStream_t st = ctx->stream;
-    cudaMemsetAsync(maps, 0, (size_t)2 * mb, st);
-    const int nbk = (int)cdiv(nrow * 32, 256);
-    k_ring_rows<<<nbk, 256, 0, st>>>(G, s.d_q, d_mask, rowcnt, rowlen);
-    if (!scan_u32(ctx, rowcnt, NFAM * nrow, rowoff, bsum)) return fail(ctx, ABS_ERR_OOM, "scan counter");
-    k_ring_write<<<nbk, 256, 0, st>>>(G, s.d_q, d_mask, rowoff, rb.lists, rb.mapF, rb.mapA);
-    k_ring_finish<<<(int)cdiv((int64_t)NFAM * s.nb * 32, 256), 256, 0, st>>>(
-        G, s.du, rowoff, rowcnt, rowlen, rb.ring_off, rb.counts, d_ellbar);
+    cudaMemsetAsync(maps, 0, (size_t)2 * mb + sizeof(int32_t) * NFAM * s.nb, st);
+    k_ring_cells<<<(int)cdiv(nrow * 32, 256), 256, 0, st>>>(G, s.d_q, d_mask, rb.ring_off, cnt_up, rb.lists,
+                                                            rb.mapF, rb.mapA, rowlen);
+    k_ring_finish<<<(int)cdiv((int64_t)NFAM * s.nb * 32, 256), 256, 0, st>>>(G, s.du, cnt_up, rowlen, rb.counts,
+                                                                           d_ellbar);
     return check_launch(ctx, "ring lists");
 }
 

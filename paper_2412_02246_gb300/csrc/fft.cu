@@ -46,54 +46,59 @@ struct RingGeom {
 };
 
 // ------------------------------------------------------------------ double-float
+// A complex double-float value is held as two float2 registers, hi = (re.hi,
+// im.hi) and lo = (re.lo, im.lo), so that the real and imaginary parts go
+// through the same packed FP32x2 instruction (FADD2 / FMUL2 / FFMA2): every
+// complex addition or real scaling costs what one real double-float operation
+// costs in scalar code.  Stored as float4 (re.hi, im.hi, re.lo, im.lo).
 
-struct df {
-    float hi, lo;
+struct pdf {
+    float2 hi, lo;
 };
 
-__device__ __forceinline__ df df_add(df a, df b) {
-    const float s = __fadd_rn(a.hi, b.hi);
-    const float bb = __fsub_rn(s, a.hi);
-    float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
-    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
-    const float hi = __fadd_rn(s, e);
-    return {hi, __fsub_rn(e, __fsub_rn(hi, s))};
-}
-__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
-__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
-__device__ __forceinline__ df df_mul(df a, df b) {
-    const float p = __fmul_rn(a.hi, b.hi);
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    const float hi = __fadd_rn(p, e);
-    return {hi, __fsub_rn(e, __fsub_rn(hi, p))};
-}
-__device__ __forceinline__ df df_scale_half(df a) { return {0.5f * a.hi, 0.5f * a.lo}; }
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }  // a - b
 
-// complex double-float, stored as float4 (re.hi, re.lo, im.hi, im.lo)
-struct cdf {
-    df re, im;
-};
-__device__ __forceinline__ cdf ld(const float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
-__device__ __forceinline__ float4 st(cdf a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
-__device__ __forceinline__ cdf c_add(cdf a, cdf b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
-__device__ __forceinline__ cdf c_sub(cdf a, cdf b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
-__device__ __forceinline__ cdf c_mul(cdf a, cdf w) {
-    return {df_sub(df_mul(a.re, w.re), df_mul(a.im, w.im)), df_add(df_mul(a.re, w.im), df_mul(a.im, w.re))};
+// TwoSum of the high parts, low parts added, then Fast2Sum renormalisation.
+__device__ __forceinline__ pdf p_add(pdf a, pdf b) {
+    const float2 s = __fadd2_rn(a.hi, b.hi);
+    const float2 bb = f2sub(s, a.hi);
+    float2 e = __fadd2_rn(f2sub(a.hi, f2sub(s, bb)), f2sub(b.hi, bb));
+    e = __fadd2_rn(e, __fadd2_rn(a.lo, b.lo));
+    const float2 hi = __fadd2_rn(s, e);
+    return {hi, f2sub(e, f2sub(hi, s))};
 }
-__device__ __forceinline__ cdf c_mi(cdf a) { return {a.im, df_neg(a.re)}; }  // a * (-i)
-__device__ __forceinline__ cdf c_scale(cdf a, df s) { return {df_mul(a.re, s), df_mul(a.im, s)}; }
+__device__ __forceinline__ pdf p_neg(pdf a) { return {f2(-a.hi.x, -a.hi.y), f2(-a.lo.x, -a.lo.y)}; }
+__device__ __forceinline__ pdf p_sub(pdf a, pdf b) { return p_add(a, p_neg(b)); }
+// TwoProduct of the high parts (FMA), cross terms added, renormalised.
+__device__ __forceinline__ pdf p_mul(pdf a, pdf b) {
+    const float2 p = __fmul2_rn(a.hi, b.hi);
+    float2 e = __ffma2_rn(a.hi, b.hi, f2(-p.x, -p.y));
+    e = __ffma2_rn(a.hi, b.lo, e);
+    e = __ffma2_rn(a.lo, b.hi, e);
+    const float2 hi = __fadd2_rn(p, e);
+    return {hi, f2sub(e, f2sub(hi, p))};
+}
+__device__ __forceinline__ pdf p_half(pdf a) { return {__fmul2_rn(a.hi, f2(0.5f, 0.5f)), __fmul2_rn(a.lo, f2(0.5f, 0.5f))}; }
+__device__ __forceinline__ pdf ld(const float4 v) { return {f2(v.x, v.y), f2(v.z, v.w)}; }
+__device__ __forceinline__ float4 st(pdf a) { return make_float4(a.hi.x, a.hi.y, a.lo.x, a.lo.y); }
+// a * (-i) = (im, -re)
+__device__ __forceinline__ pdf c_mi(pdf a) { return {f2(a.hi.y, -a.hi.x), f2(a.lo.y, -a.lo.x)}; }
+// a * w with w = c + i s given as wr = (c, c), wi = (-s, s): a wr + swap(a) wi
+__device__ __forceinline__ pdf c_mul_tw(pdf a, pdf wr, pdf wi) {
+    const pdf sw = {f2(a.hi.y, a.hi.x), f2(a.lo.y, a.lo.x)};
+    return p_add(p_mul(a, wr), p_mul(sw, wi));
+}
 
-// radix constants as double-float pairs
+// radix constants as double-float pairs, broadcast to (re, im)
 constexpr double kS3 = 0.86602540378443864676372317075294;   // sin(2 pi / 3)
 constexpr double kC1 = 0.30901699437494742410229341718282;   // cos(2 pi / 5)
 constexpr double kC2 = -0.80901699437494742410229341718282;  // cos(4 pi / 5)
 constexpr double kS1 = 0.95105651629515357211643933337938;   // sin(2 pi / 5)
 constexpr double kS2 = 0.58778525229247312916870595463907;   // sin(4 pi / 5)
-__device__ __forceinline__ df dfc(double v) {
-    const float h = (float)v;
-    return {h, (float)(v - (double)h)};
+__device__ __forceinline__ pdf pconst(double v) {
+    const float h = (float)v, l = (float)(v - (double)h);
+    return {f2(h, h), f2(l, l)};
 }
 
 // One Stockham pass over `lines` transforms of length N stored line-major.
@@ -109,45 +114,46 @@ __device__ __forceinline__ void stockham_pass(const float4 *__restrict__ in, flo
         const int k = i - ip * p;
         const float4 *src = in + (size_t)l * N + i;
         float4 *dst = out + (size_t)l * N + ip * p * R + k;
-        cdf x[5];
+        pdf x[5];
         x[0] = ld(src[0]);
 #pragma unroll
         for (int q = 1; q < 5; ++q) {
             if (q < R) {
-                const cdf v = ld(src[q * T]);
-                x[q] = k ? c_mul(v, ld(tw[q * k * P.tstep])) : v;
+                const pdf v = ld(src[q * T]);
+                const int ti = 2 * q * k * P.tstep;
+                x[q] = k ? c_mul_tw(v, ld(tw[ti]), ld(tw[ti + 1])) : v;
             }
         }
         if (R == 4) {
-            const cdf a0 = c_add(x[0], x[2]), a1 = c_sub(x[0], x[2]);
-            const cdf b0 = c_add(x[1], x[3]), b1 = c_mi(c_sub(x[1], x[3]));
-            dst[0] = st(c_add(a0, b0));
-            dst[p] = st(c_add(a1, b1));
-            dst[2 * p] = st(c_sub(a0, b0));
-            dst[3 * p] = st(c_sub(a1, b1));
+            const pdf a0 = p_add(x[0], x[2]), a1 = p_sub(x[0], x[2]);
+            const pdf b0 = p_add(x[1], x[3]), b1 = c_mi(p_sub(x[1], x[3]));
+            dst[0] = st(p_add(a0, b0));
+            dst[p] = st(p_add(a1, b1));
+            dst[2 * p] = st(p_sub(a0, b0));
+            dst[3 * p] = st(p_sub(a1, b1));
         } else if (R == 2) {
-            dst[0] = st(c_add(x[0], x[1]));
-            dst[p] = st(c_sub(x[0], x[1]));
+            dst[0] = st(p_add(x[0], x[1]));
+            dst[p] = st(p_sub(x[0], x[1]));
         } else if (R == 3) {
-            const cdf t = c_add(x[1], x[2]);
-            const cdf m = c_sub(x[0], {df_scale_half(t.re), df_scale_half(t.im)});
-            const cdf d = c_scale(c_mi(c_sub(x[1], x[2])), dfc(kS3));
-            dst[0] = st(c_add(x[0], t));
-            dst[p] = st(c_add(m, d));
-            dst[2 * p] = st(c_sub(m, d));
+            const pdf t = p_add(x[1], x[2]);
+            const pdf m = p_sub(x[0], p_half(t));
+            const pdf d = p_mul(c_mi(p_sub(x[1], x[2])), pconst(kS3));
+            dst[0] = st(p_add(x[0], t));
+            dst[p] = st(p_add(m, d));
+            dst[2 * p] = st(p_sub(m, d));
         } else {  // R == 5
-            const df c1 = dfc(kC1), c2 = dfc(kC2), s1 = dfc(kS1), s2 = dfc(kS2);
-            const cdf t1 = c_add(x[1], x[4]), t2 = c_add(x[2], x[3]);
-            const cdf t3 = c_sub(x[1], x[4]), t4 = c_sub(x[2], x[3]);
-            const cdf a1 = c_add(x[0], c_add(c_scale(t1, c1), c_scale(t2, c2)));
-            const cdf a2 = c_add(x[0], c_add(c_scale(t1, c2), c_scale(t2, c1)));
-            const cdf b1 = c_mi(c_add(c_scale(t3, s1), c_scale(t4, s2)));
-            const cdf b2 = c_mi(c_sub(c_scale(t3, s2), c_scale(t4, s1)));
-            dst[0] = st(c_add(x[0], c_add(t1, t2)));
-            dst[p] = st(c_add(a1, b1));
-            dst[4 * p] = st(c_sub(a1, b1));
-            dst[2 * p] = st(c_add(a2, b2));
-            dst[3 * p] = st(c_sub(a2, b2));
+            const pdf c1 = pconst(kC1), c2 = pconst(kC2), s1 = pconst(kS1), s2 = pconst(kS2);
+            const pdf t1 = p_add(x[1], x[4]), t2 = p_add(x[2], x[3]);
+            const pdf t3 = p_sub(x[1], x[4]), t4 = p_sub(x[2], x[3]);
+            const pdf a1 = p_add(x[0], p_add(p_mul(t1, c1), p_mul(t2, c2)));
+            const pdf a2 = p_add(x[0], p_add(p_mul(t1, c2), p_mul(t2, c1)));
+            const pdf b1 = c_mi(p_add(p_mul(t3, s1), p_mul(t4, s2)));
+            const pdf b2 = c_mi(p_sub(p_mul(t3, s2), p_mul(t4, s1)));
+            dst[0] = st(p_add(x[0], p_add(t1, t2)));
+            dst[p] = st(p_add(a1, b1));
+            dst[4 * p] = st(p_sub(a1, b1));
+            dst[2 * p] = st(p_add(a2, b2));
+            dst[3 * p] = st(p_sub(a2, b2));
         }
     }
 }
@@ -166,9 +172,9 @@ __device__ float4 *fft_lines(float4 *a, float4 *b, int lines, const FftPlan &P,
     return a;
 }
 
-__device__ __forceinline__ float4 cdf_from_double(double re, double im) {
+__device__ __forceinline__ float4 cdf_from_double(double re, double im) {   // (re.hi, im.hi, re.lo, im.lo)
     const float rh = (float)re, ih = (float)im;
-    return make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+    return make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
 }
 
 // Gridded data as the transform reads it: the weighted mean on a filled cell.
@@ -209,8 +215,8 @@ __global__ void __launch_bounds__(256) k_fft_rows(RingGeom G, FftPlan P, int RB,
     const int y0 = (int)blockIdx.x * RB - G.Rmax;
     if (Rp < 0 || y0 > Rp || y0 + RB - 1 < -Rp) return;
     float4 *tw = sbuf;
-    float4 *l0 = sbuf + G.N, *l1 = l0 + (size_t)RB * G.N;
-    for (int i = threadIdx.x; i < G.N; i += blockDim.x) tw[i] = tw_g[i];
+    float4 *l0 = sbuf + 2 * G.N, *l1 = l0 + (size_t)RB * G.N;
+    for (int i = threadIdx.x; i < 2 * G.N; i += blockDim.x) tw[i] = tw_g[i];
     for (int i = threadIdx.x; i < RB * G.N; i += blockDim.x) l0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     const int span = 2 * Rp + 1;
@@ -258,8 +264,8 @@ __global__ void __launch_bounds__(256) k_fft_cols(RingGeom G, FftPlan P, int CW,
         return;
     }
     float4 *tw = sbuf;
-    float4 *l0 = sbuf + G.N, *l1 = l0 + (size_t)CW * G.N;
-    for (int i = threadIdx.x; i < G.N; i += blockDim.x) tw[i] = tw_g[i];
+    float4 *l0 = sbuf + 2 * G.N, *l1 = l0 + (size_t)CW * G.N;
+    for (int i = threadIdx.x; i < 2 * G.N; i += blockDim.x) tw[i] = tw_g[i];
     for (int i = threadIdx.x; i < CW * G.N; i += blockDim.x) l0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     const int rows = 2 * Rp + 1;
@@ -273,8 +279,8 @@ __global__ void __launch_bounds__(256) k_fft_cols(RingGeom G, FftPlan P, int CW,
     for (int i = threadIdx.x; i < G.N * cw; i += blockDim.x) {
         const int py = i / cw, c = i - py * cw;
         const float4 v = res[(size_t)c * G.N + py];
-        fields[(size_t)a * P2 + (size_t)py * G.N + x0 + c] = __fadd_rn(v.x, v.y);
-        if (b >= 0) fields[(size_t)b * P2 + (size_t)py * G.N + x0 + c] = __fadd_rn(v.z, v.w);
+        fields[(size_t)a * P2 + (size_t)py * G.N + x0 + c] = __fadd_rn(v.x, v.z);
+        if (b >= 0) fields[(size_t)b * P2 + (size_t)py * G.N + x0 + c] = __fadd_rn(v.y, v.w);
     }
 }
 
@@ -308,12 +314,14 @@ struct FftLaunch {
 FftLaunch fft_launch(const Setup &s) {
     FftLaunch L;
     const size_t line = sizeof(float4) * (size_t)s.N;
+    // lines per CTA: as many as keep the CTA within 48 KB of shared memory, so
+    // that four CTAs share an SM (both passes are latency-bound at moderate N)
     L.RB = 8;
-    while (L.RB > 1 && line * (2 * L.RB + 1) > 96 * 1024) L.RB >>= 1;
+    while (L.RB > 1 && line * (2 * L.RB + 2) > 48 * 1024) L.RB >>= 1;
     L.CW = 16;
-    while (L.CW > 1 && line * (2 * L.CW + 1) > 96 * 1024) L.CW >>= 1;
-    L.row_smem = line * (2 * L.RB + 1);
-    L.col_smem = line * (2 * L.CW + 1);
+    while (L.CW > 1 && line * (2 * L.CW + 2) > 48 * 1024) L.CW >>= 1;
+    L.row_smem = line * (2 * L.RB + 2);   // two line buffers + the packed twiddles (2N float4)
+    L.col_smem = line * (2 * L.CW + 2);
     return L;
 }
 

@@ -29,7 +29,6 @@ namespace {
 
 constexpr int TS = 16;                       // tile side in cells
 constexpr int UMAX = 512;                    // visibilities per work unit
-constexpr int FWMAX = 2 * ABS_MAX_RADIUS + 1;
 constexpr unsigned FULL = 0xffffffffu;
 
 struct GridGeom {
@@ -72,13 +71,6 @@ __device__ __forceinline__ float wexp(float d, float f_hi, float f_lo, float s_h
     const float arg_e = fmaf(-s_hi, p, -arg_hi);        // exact product error
     const float arg_lo = arg_e - s_hi * qq - s_lo * p;
     return expf(arg_hi) * (1.0f + arg_lo);
-}
-
-__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
-    const float y = __fsub_rn(x, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
 }
 
 // ------------------------------------------------------------------ plan kernels
@@ -649,6 +641,21 @@ __global__ void k_grid_finalize(int n, const double *__restrict__ acc_re,
 }
 
 
+// Filled mask only, for the estimate path (which transforms straight from the
+// FP64 accumulators): a cell is filled when it or its mirror has a nonzero
+// weight sum (sums of positive weights, never -0), tested on the bits.
+__global__ void k_grid_mask(int n, const double *__restrict__ acc_w, uint8_t *__restrict__ mask) {
+    const int64_t cells = (int64_t)n * n;
+    const unsigned long long *wb = (const unsigned long long *)acc_w;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < cells;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(p % n), iy = (int)(p / n);
+        const int mx = ix == 0 ? 0 : n - ix, my = iy == 0 ? 0 : n - iy;
+        const int64_t pm = (int64_t)my * n + mx;
+        mask[p] = (ix != n / 2 && iy != n / 2 && (wb[p] != 0ull || wb[pm] != 0ull)) ? 1 : 0;
+    }
+}
+
 struct PlanBufs {
     uint32_t *keys, *tile_hist, *k2, *v2, *rhist, *roffs, *n_valid;
     uint32_t *s_idx;      // sorted original indices
@@ -769,6 +776,14 @@ abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, c
         cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRID_SMEM);
         k_grid<<<blocks, GT, GRID_SMEM, st>>>(G, b.units, b.n_units, b.s_uv, b.s_idx, (const float2 *)d_vis, acc,
                                            acc + cells, acc + 2 * cells);
+    }
+    if (!d_grid && !d_wsum) {   // estimate path: the mask alone, if asked for
+        if (d_mask) {
+            StageTimer timer(ctx, "grid_mask");
+            const int fb = (int)std::min<int64_t>(cdiv(cells, 256), ctx->sm_count * 8);
+            k_grid_mask<<<fb, 256, 0, st>>>(s.n, acc + 2 * cells, d_mask);
+        }
+        return check_launch(ctx, "grid accumulate");
     }
     {
         StageTimer timer(ctx, "grid_finalize");

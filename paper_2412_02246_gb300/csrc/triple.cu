@@ -155,9 +155,11 @@ bool triple_plan(int nb, int N, int n_trip, int sms, int64_t max_split, const fl
 // S[t] = inv_p * sum over splits of partial[split][t]: one warp per triplet,
 // lane l adds splits l, l + 32, ... and a fixed butterfly combines the lanes
 // (the order never depends on scheduling, so results are reproducible).
+// With B != nullptr also B[t] = S[t] / (A T[t]) (NaN for T = 0).
 __global__ void __launch_bounds__(256) k_triple_reduce(int n_trip, int nsplit, double inv_p,
                                                        const double *__restrict__ partial,
-                                                       double *__restrict__ S) {
+                                                       double *__restrict__ S, const int64_t *__restrict__ T,
+                                                       double norm_A, double *__restrict__ B) {
     const int lane = threadIdx.x & 31;
     const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (t >= n_trip) return;
@@ -165,7 +167,14 @@ __global__ void __launch_bounds__(256) k_triple_reduce(int n_trip, int nsplit, d
     for (int k = lane; k < nsplit; k += 32) s += partial[(size_t)k * n_trip + t];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-    if (lane == 0) S[t] = s * inv_p;
+    if (lane == 0) {
+        const double v = s * inv_p;
+        S[t] = v;
+        if (B) {
+            const int64_t c = T[t];
+            B[t] = c > 0 ? v / (norm_A * (double)c) : nan("");
+        }
+    }
 }
 
 __global__ void k_normalise(int n_trip, double norm_A, const double *__restrict__ S,
@@ -199,9 +208,13 @@ abs_status launch_check_triplets(abs_ctx *ctx, const Setup &s, int32_t n_trip, c
 }
 
 abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_fields, int32_t n_trip,
-                              const int32_t *d_ijk, double *d_sum) {
+                              const int32_t *d_ijk, double *d_sum, const int64_t *d_count, double *d_B) {
     if (n_trip == 0) return ABS_OK;
-    if (s.precision == ABS_SPLIT_BF16) return launch_triple_tc(ctx, s, d_fields, n_trip, d_ijk, d_sum);
+    if (s.precision == ABS_SPLIT_BF16) {
+        const abs_status st = launch_triple_tc(ctx, s, d_fields, n_trip, d_ijk, d_sum);
+        if (st != ABS_OK || !d_B) return st;
+        return launch_normalise(ctx, s, n_trip, d_sum, d_count, d_B);
+    }
     TriplePlan tp;
     if (!triple_plan(s.nb, s.N, n_trip, ctx->sm_count, INT64_MAX, d_fields, tp))
         return fail(ctx, ABS_ERR_UNSUPPORTED, "FP32 triple-sum tiling");
@@ -216,7 +229,8 @@ abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_field
     }
     StageTimer timer(ctx, "triple_reduce");
     k_triple_reduce<<<(int)cdiv(n_trip, 8), 256, 0, ctx->stream>>>(
-        n_trip, (int)nsplit, 1.0 / ((double)s.N * (double)s.N), partial, d_sum);
+        n_trip, (int)nsplit, 1.0 / ((double)s.N * (double)s.N), partial, d_sum, d_count, s.norm_A,
+        d_B && d_count ? d_B : nullptr);
     return check_launch(ctx, "triple sums");
 }
 
@@ -285,6 +299,7 @@ extern "C" abs_status abs_triple_sums_static(const abs_config *cfg, const float 
     k_triple_fp32<<<dim3((unsigned)nsplit, tp.tgroups), tp.threads, tp.smem, stream>>>(tp.G, d_fields, d_ijk,
                                                                                         partial);
     k_triple_reduce<<<(int)cdiv(n_trip, 8), 256, 0, stream>>>(n_trip, (int)nsplit,
-                                                               1.0 / ((double)N * (double)N), partial, d_sum);
+                                                               1.0 / ((double)N * (double)N), partial, d_sum,
+                                                               nullptr, 1.0, nullptr);
     return cudaGetLastError() == cudaSuccess ? ABS_OK : ABS_ERR_CUDA;
 }
