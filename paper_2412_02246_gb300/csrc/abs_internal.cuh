@@ -81,6 +81,12 @@ struct abs_ctx {
     int32_t *d_err = nullptr;  // latched device error word: 0 ok, else a code below
     std::map<std::string, absk::Workspace> ws;
     std::map<std::string, std::unique_ptr<absk::Setup>> setups;
+    // CUDA graphs of abs_estimate(_many) calls, keyed by their arguments: the
+    // first call with a key runs eagerly (sizing workspaces, caching per-config
+    // tables), the second is captured and replayed from then on.  Dropped
+    // whenever a workspace is reallocated (the graphs hold its old address).
+    struct Graph { cudaGraphExec_t exec = nullptr; int seen = 0; bool failed = false; };
+    std::map<std::string, Graph> graphs;
 };
 
 namespace absk {

@@ -200,12 +200,19 @@ abs_status check_launch(abs_ctx *ctx, const char *what) {
     return ABS_OK;
 }
 
+void drop_graphs(abs_ctx *ctx) {
+    for (auto &kv : ctx->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    ctx->graphs.clear();
+}
+
 void *workspace(abs_ctx *ctx, const char *name, size_t bytes) {
     if (bytes == 0) bytes = 16;
     Workspace &w = ctx->ws[name];
     if (w.bytes >= bytes) return w.p;
     if (w.p) {
         cudaStreamSynchronize(ctx->stream);
+        drop_graphs(ctx);   // they refer to the buffer freed here
         cudaFree(w.p);
         w.p = nullptr;
         w.bytes = 0;
@@ -419,6 +426,7 @@ abs_status abs_destroy(abs_ctx *ctx) {
     {
         DeviceGuard g(ctx->device);
         cudaStreamSynchronize(ctx->stream);
+        drop_graphs(ctx);
         for (auto &kv : ctx->ws) cudaFree(kv.second.p);
         for (auto &kv : ctx->setups) free_setup(*kv.second);
         cudaFree(ctx->d_err);
@@ -593,6 +601,58 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
     return ABS_OK;
 }
 
+// estimate_many through the context's graph cache (see abs_ctx::graphs).  Not
+// used while the stage profiler runs or on the legacy default stream.
+static abs_status estimate_graphed(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv,
+                                   int32_t n_real, const float *d_vis, int32_t n_trip, const int32_t *d_ijk,
+                                   double *d_B, int64_t *d_count, double *d_ellbar) {
+    auto eager = [&]() {
+        return estimate_many(ctx, s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar);
+    };
+    if (ctx->profiling || ctx->stream == nullptr) return eager();
+    char key[256];
+    snprintf(key, sizeof key, "%p|%p|%lld|%p|%d|%p|%d|%p|%p|%p|%p", (const void *)&s, (const void *)ctx->stream,
+             (long long)n_vis, (const void *)d_uv, n_real, (const void *)d_vis, n_trip, (const void *)d_ijk,
+             (void *)d_B, (void *)d_count, (void *)d_ellbar);
+    abs_ctx::Graph &g = ctx->graphs[key];
+    if (g.exec) {
+        if (cudaGraphLaunch(g.exec, ctx->stream) == cudaSuccess) return ABS_OK;
+        cudaGetLastError();
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        g.failed = true;
+        return eager();
+    }
+    if (g.failed || g.seen++ == 0) return eager();
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        g.failed = true;
+        return eager();
+    }
+    const abs_status st = eager();
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    if (st != ABS_OK || ce != cudaSuccess || !graph ||
+        cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+        // nothing captured ran: run it eagerly (and never capture this key again)
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        g.exec = nullptr;
+        g.failed = true;
+        ctx->last_error.clear();
+        return eager();
+    }
+    cudaGraphDestroy(graph);
+    if (cudaGraphLaunch(g.exec, ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+        g.failed = true;
+        return eager();
+    }
+    return ABS_OK;
+}
+
 static abs_status estimate_args(abs_ctx *ctx, const Setup &s, int64_t n_vis, const void *uv,
                                 int32_t n_real, const void *vis, int32_t n_trip, const int32_t *&ijk) {
     if (n_vis < 0 || n_vis > 0x7fffffffLL) return fail(ctx, ABS_ERR_INVALID_ARG, "n_vis must be in [0, 2^31)");
@@ -616,7 +676,7 @@ abs_status abs_estimate_many(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis,
     const Setup *s = get_setup(ctx, cfg, st);
     if (!s) return st;
     ABS_CHECK(estimate_args(ctx, *s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk));
-    return estimate_many(ctx, *s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar);
+    return estimate_graphed(ctx, *s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar);
 }
 
 abs_status abs_estimate(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis, const float *d_uv,
@@ -654,7 +714,7 @@ abs_status abs_estimate_host(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis,
         cudaMemcpyAsync(d_vis, h_vis, visb, cudaMemcpyHostToDevice, ctx->stream);
     }
     ABS_CHECK(check_launch(ctx, "host to device copies"));
-    ABS_CHECK(estimate_many(ctx, *s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar));
+    ABS_CHECK(estimate_graphed(ctx, *s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar));
     if (h_B && n_trip > 0)
         cudaMemcpyAsync(h_B, d_B, sizeof(double) * (size_t)n_trip * n_real, cudaMemcpyDeviceToHost, ctx->stream);
     if (h_count && n_trip > 0)

@@ -262,6 +262,54 @@ def test_estimate_end_to_end(ctx, cfg_id):
     assert np.allclose(E.cpu().numpy(), est.ellbar, rtol=1e-12, equal_nan=True)
 
 
+def test_estimate_graph_replay():
+    """abs_estimate on a non-default stream: the first call with a set of
+    arguments runs eagerly, the second is captured as a CUDA graph and the
+    rest replay it; replays read the buffers' current contents, and a
+    workspace that has to grow (a larger workload) drops the graphs."""
+    absbuild.build()
+    st = torch.cuda.Stream(dev())
+    c = absmod.Context(0, st)
+    try:
+        wl = synth.workload(0)
+        cfg = absmod.Config.from_workload(wl)
+        i0, i1 = synth.make_inputs(0, 0), synth.make_inputs(0, 3)
+        ijk = absmod.abs_triplets(cfg)
+        nt = len(ijk)
+        with torch.cuda.stream(st):
+            uv = to_dev(i0.uv)
+            vis = torch.empty((len(i0.uv), 2), dtype=torch.float32, device=dev())
+            v0, v1 = to_dev(synth.vis_as_float2(i0.vis)), to_dev(synth.vis_as_float2(i1.vis))
+            B = torch.empty(nt, dtype=torch.float64, device=dev())
+            T = torch.empty(nt, dtype=torch.int64, device=dev())
+            E = torch.empty(cfg.n_bins, dtype=torch.float64, device=dev())
+            out = []
+            for src in (v0, v1, v0, v1, v0):
+                vis.copy_(src)
+                c.abs_estimate(cfg, uv, vis, nt, None, B, T, E)
+                out.append(B.clone())
+            # a larger problem regrows workspaces (graphs dropped), then back again
+            big = inputs(1)
+            cfg1 = absmod.Config.from_workload(big.wl)
+            absmod.estimate(cfg1, to_dev(big.uv), to_dev(synth.vis_as_float2(big.vis)), c)
+            vis.copy_(v1)
+            for _ in range(3):
+                c.abs_estimate(cfg, uv, vis, nt, None, B, T, E)
+            out.append(B.clone())
+        c.sync()
+        r = [o.cpu().numpy() for o in out]
+        e0 = oracle_run(("est0r0",), wl.n_grid, wl.du, wl.ell_edges, i0.uv, i0.vis)
+        e1 = oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, i1.uv, i1.vis)
+        for got, est in zip(r, (e0, e1, e0, e1, e0, e1)):
+            ok = ~np.isnan(est.B)
+            big_ = ok & (np.abs(est.B) >= 1e-3 * np.nanmax(np.abs(est.B)))
+            rel = np.abs(got[big_] - est.B[big_]) / np.abs(est.B[big_])
+            assert rel.max() <= SUM_TOL, f"B relative error {rel.max():.3e}"
+        assert np.array_equal(T.cpu().numpy(), e1.T)
+    finally:
+        c.close()
+
+
 def test_estimate_many_and_host(ctx):
     wl = synth.workload(0)
     cfg = absmod.Config.from_workload(wl)
