@@ -212,44 +212,22 @@ __global__ void k_ring_cells(CountGeom G, const int64_t *__restrict__ q, const u
     if (lane == 0) rowlen[e] = (double)sh + (double)sl;
 }
 
-// One warp per (family, ring): full counts (twice the upper half plane) and
-// the mean l of the filled cells (the upper half plane has the same mean;
-// fixed-order sums over the rows).
-__global__ void k_ring_finish(CountGeom G, float du, const int32_t *__restrict__ cnt_up,
-                              const double *__restrict__ rowlen, int32_t *__restrict__ counts,
-                              double *__restrict__ ellbar) {
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (w >= NFAM * G.nb) return;
-    const int fam = w / G.nb, m = w - fam * G.nb;
-    const int rows = G.R + 1;
-    const int32_t c = cnt_up[fam * G.nb + m];
-    double len = 0.0;
-    if (fam == FAM_F)
-        for (int y = lane; y < rows; y += 32) len += rowlen[(int64_t)m * rows + y];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(FULL, len, o);
-    if (lane == 0) {
-        counts[fam * G.nb + m] = 2 * c;
-        if (fam == FAM_F && ellbar)
-            ellbar[m] = c > 0 ? 2.0 * 3.14159265358979323846 * (double)du * len / (double)c : nan("");
-    }
-}
-
 // One block: choose the route (direct or holes) from the pair counts it would
 // visit, and write the work items of every job it needs: one per (pair a <= b,
 // chunk of the larger set, chunk of the smaller set).  Items of jobs that look
 // up the filled map go to list 0, the annulus map to list 1.
 // item = (a, b, outer start, inner start | job << 27 | outer-is-x << 31)
-__global__ void __launch_bounds__(1024) k_count_items(int nb, const int32_t *__restrict__ counts, int chunk,
-                                                      int need_full, int4 *__restrict__ items0,
-                                                      int4 *__restrict__ items1, int cap,
-                                                      int *__restrict__ ctl, int32_t *__restrict__ err) {
+__device__ void count_items_block(int nb, const int32_t *__restrict__ counts, int chunk, int need_full,
+                                  int4 *__restrict__ items0, int4 *__restrict__ items1, int cap,
+                                  int *__restrict__ ctl, int32_t *__restrict__ err) {
     __shared__ unsigned long long wdir_s, wexc_s;
     __shared__ int use_holes_s;
     __shared__ int wsum[32];
     __shared__ int carry_s[2];
     const int npair = nb * (nb + 1) / 2;
-    const int32_t *cF = counts, *cH = counts + nb, *cA = counts + 2 * nb;
+    __shared__ int32_t cs[3 * ABS_MAX_BINS];   // the counts, written by other blocks: read once via L2
+    for (int i = threadIdx.x; i < 3 * nb; i += blockDim.x) cs[i] = __ldcg(counts + i);
+    const int32_t *cF = cs, *cH = cs + nb, *cA = cs + 2 * nb;
     if (threadIdx.x == 0) {
         wdir_s = 0;
         wexc_s = 0;
@@ -294,7 +272,7 @@ __global__ void __launch_bounds__(1024) k_count_items(int nb, const int32_t *__r
     for (int jj = 0; jj < nj; ++jj) {
         const int job = jobs[jj];
         const int lst = job_map_a(job) ? 1 : 0;
-        const int32_t *cx = counts + job_x(job) * nb, *cy = counts + job_y(job) * nb;
+        const int32_t *cx = cs + job_x(job) * nb, *cy = cs + job_y(job) * nb;
         for (int p0 = 0; p0 < npair; p0 += blockDim.x) {
             const int pr = p0 + threadIdx.x;
             int a = 0, b = 0, n_ic = 1, nchunks = 0;
@@ -358,6 +336,68 @@ __global__ void __launch_bounds__(1024) k_count_items(int nb, const int32_t *__r
     }
 }
 
+// One warp per (family, ring): full counts (twice the upper half plane) and
+// the mean l of the filled cells (the upper half plane has the same mean;
+// fixed-order sums over the rows).  With items0 given, every block also
+// clears a slice of the pair-count tables, and the last block to finish
+// (ticket) chooses the route and writes the work items (count_items_block).
+struct ItemArgs {
+    int chunk, need_full, cap;
+    int4 *items0, *items1;
+    int *ctl;
+    int32_t *err;
+    unsigned *ticket;
+    unsigned long long *tabs;   // [4][nb^3], cleared
+    unsigned long long *full;   // [nb^3], cleared when need_full
+};
+
+__global__ void k_ring_finish(CountGeom G, float du, const int32_t *__restrict__ cnt_up,
+                              const double *__restrict__ rowlen, int32_t *__restrict__ counts,
+                              double *__restrict__ ellbar, ItemArgs ia) {
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (ia.items0) {
+        const int64_t tw = (int64_t)G.nb * G.nb * G.nb;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 4 * tw;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            ia.tabs[i] = 0ull;
+            if (ia.need_full && i < tw) ia.full[i] = 0ull;
+        }
+    }
+    if (w < NFAM * G.nb) {
+        const int fam = w / G.nb, m = w - fam * G.nb;
+        const int rows = G.R + 1;
+        const int32_t c = cnt_up[fam * G.nb + m];
+        double len = 0.0;
+        if (fam == FAM_F)
+            for (int y = lane; y < rows; y += 32) len += rowlen[(int64_t)m * rows + y];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) len += __shfl_xor_sync(FULL, len, o);
+        if (lane == 0) {
+            counts[fam * G.nb + m] = 2 * c;
+            if (fam == FAM_F && ellbar)
+                ellbar[m] = c > 0 ? 2.0 * 3.14159265358979323846 * (double)du * len / (double)c : nan("");
+        }
+    }
+    if (!ia.items0) return;
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ia.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    count_items_block(G.nb, counts, ia.chunk, ia.need_full, ia.items0, ia.items1, ia.cap, ia.ctl, ia.err);
+    if (threadIdx.x == 0) *ia.ticket = 0u;
+}
+
+struct GatherArgs {   // T_ijk for the listed triplets, by the last CTA to finish (T == nullptr: none)
+    int32_t n_trip;
+    const int32_t *ijk;
+    const int *ctl;
+    int64_t *T;
+    unsigned *ticket;
+};
+
 template <bool MAP_IN_SMEM>
 __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__restrict__ items,
                                                     const int *__restrict__ n_items,
@@ -367,7 +407,7 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
                                                     unsigned long long *__restrict__ t1,
                                                     unsigned long long *__restrict__ t2,
                                                     unsigned long long *__restrict__ t3,
-                                                    unsigned long long *__restrict__ t4) {
+                                                    unsigned long long *__restrict__ t4, GatherArgs ga) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int nwarps = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -377,8 +417,7 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
     uint8_t *map_s = (uint8_t *)(stage + INNER);
     const uint8_t *map = MAP_IN_SMEM ? map_s : map_g;
     const int ni = *n_items;
-    if (ni == 0) return;
-    if (MAP_IN_SMEM) {
+    if (MAP_IN_SMEM && ni > 0) {
         const int64_t mb = G.base + 1;
         const int64_t nv = mb / 16;
         for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) ((uint4 *)map_s)[i] = ((const uint4 *)map_g)[i];
@@ -388,7 +427,7 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
     __syncthreads();
     uint32_t *myhist = hist + (size_t)warp * hs * 32 + lane;
     __shared__ int it_s;
-    for (;;) {
+    for (; ni > 0;) {
         if (threadIdx.x == 0) it_s = atomicAdd(next_item, 1);   // dynamic: items differ in size
         __syncthreads();
         const int it = it_s;
@@ -472,28 +511,32 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
         for (int k = threadIdx.x; k < nwarps * hs * 32; k += blockDim.x) hist[k] = 0u;
         __syncthreads();
     }
-}
-
-// T_ijk for every listed triplet from the tables of the route taken.
-__global__ void k_count_gather(int nb, int32_t n_trip, const int32_t *__restrict__ ijk,
-                               const int *__restrict__ ctl, const unsigned long long *__restrict__ td,
-                               const unsigned long long *__restrict__ tA, const unsigned long long *__restrict__ e1,
-                               const unsigned long long *__restrict__ e2, const unsigned long long *__restrict__ e3,
-                               int64_t *__restrict__ T) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_trip) return;
-    const int i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
-    if (i < 0 || j < i || k < j || k >= nb) {
-        T[t] = 0;
-        return;
+    if (!ga.T) return;
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ga.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int nb = G.nb;
+    const bool holes = __ldcg(ga.ctl + 4) != 0;
+    for (int t = threadIdx.x; t < ga.n_trip; t += blockDim.x) {
+        const int i = ga.ijk[3 * t], j = ga.ijk[3 * t + 1], k = ga.ijk[3 * t + 2];
+        if (i < 0 || j < i || k < j || k >= nb) {
+            ga.T[t] = 0;
+            continue;
+        }
+        const size_t ijkx = ((size_t)i * nb + j) * nb + k;
+        if (holes) {
+            const size_t ikj = ((size_t)i * nb + k) * nb + j;
+            ga.T[t] = 2 * ((int64_t)__ldcg(t4 + ijkx) - (int64_t)__ldcg(t1 + ijkx) - (int64_t)__ldcg(t2 + ijkx) -
+                           (int64_t)__ldcg(t3 + ikj));
+        } else {
+            ga.T[t] = 2 * (int64_t)__ldcg(t0 + ijkx);
+        }
     }
-    const size_t ijkx = ((size_t)i * nb + j) * nb + k;
-    if (ctl[4]) {
-        const size_t ikj = ((size_t)i * nb + k) * nb + j;
-        T[t] = 2 * ((int64_t)tA[ijkx] - (int64_t)e1[ijkx] - (int64_t)e2[ijkx] - (int64_t)e3[ikj]);
-    } else {
-        T[t] = 2 * (int64_t)td[ijkx];
-    }
+    if (threadIdx.x == 0) *ga.ticket = 0u;
 }
 
 CountGeom cgeom(const Setup &s) {
@@ -515,7 +558,7 @@ struct RingBufs {
 };
 
 abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, RingBufs &rb,
-                       double *d_ellbar) {
+                       double *d_ellbar, const ItemArgs *ia) {
     const CountGeom G = cgeom(s);
     const int64_t U = std::max<int64_t>(s.up_off.back(), 1);   // upper-half lattice cells, all rings
     const int64_t nrow = (int64_t)s.nb * (s.R + 1);
@@ -535,28 +578,33 @@ abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, Ring
     cudaMemsetAsync(maps, 0, (size_t)2 * mb + sizeof(int32_t) * NFAM * s.nb, st);
     k_ring_cells<<<(int)cdiv(nrow * 32, 256), 256, 0, st>>>(G, s.d_q, d_mask, rb.ring_off, cnt_up, rb.lists,
                                                             rb.mapF, rb.mapA, rowlen);
-    k_ring_finish<<<(int)cdiv((int64_t)NFAM * s.nb * 32, 256), 256, 0, st>>>(G, s.du, cnt_up, rowlen, rb.counts,
-                                                                           d_ellbar);
+    ItemArgs none{};
+    int blocks = (int)cdiv((int64_t)NFAM * s.nb * 32, 256);
+    if (ia) {   // enough blocks to clear the pair-count tables quickly
+        const int64_t tw = (int64_t)s.nb * s.nb * s.nb;
+        blocks = (int)std::max<int64_t>(blocks, std::min<int64_t>(cdiv(4 * tw, 256 * 8), ctx->sm_count));
+    }
+    k_ring_finish<<<blocks, 256, 0, st>>>(G, s.du, cnt_up, rowlen, rb.counts, d_ellbar, ia ? *ia : none);
     return check_launch(ctx, "ring lists");
 }
 
 template <bool SMEM>
 void launch_pairs(abs_ctx *ctx, const CountGeom &G, int blocks, int threads, size_t smem, const int4 *items,
                   const int *n_items, int *next, const Fams &fam, const uint8_t *map,
-                  unsigned long long *const *tab) {
+                  unsigned long long *const *tab, const GatherArgs &ga) {
     cudaFuncSetAttribute(k_count_pairs<SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_count_pairs<SMEM><<<blocks, threads, smem, ctx->stream>>>(G, items, n_items, next, fam, map, tab[0], tab[1],
-                                                               tab[2], tab[3], tab[4]);
+                                                               tab[2], tab[3], tab[4], ga);
 }
 
 }  // namespace
 
 abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, int32_t n_trip,
                          const int32_t *d_ijk, int64_t *d_count, double *d_ellbar) {
-    RingBufs rb;
-    abs_status st = ring_tables(ctx, s, d_mask, rb, d_ellbar);
-    if (st != ABS_OK) return st;
-    if (n_trip == 0 || !d_count) return ABS_OK;
+    if (n_trip == 0 || !d_count) {
+        RingBufs rb;
+        return ring_tables(ctx, s, d_mask, rb, d_ellbar, nullptr);
+    }
     const CountGeom G = cgeom(s);
     const int hs = s.nb + 1;
     const int64_t map_bytes = cdiv(G.base + 1, 16) * 16;
@@ -577,6 +625,7 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     int4 *items0 = (int4 *)workspace(ctx, "count.items0", sizeof(int4) * cap);
     int4 *items1 = (int4 *)workspace(ctx, "count.items1", sizeof(int4) * cap);
     int *ctl = (int *)workspace(ctx, "count.ctl", sizeof(int) * 8);
+    unsigned *tickets = (unsigned *)workspace_zeroed(ctx, "count.tickets", 2 * sizeof(unsigned));
     const size_t tb = sizeof(unsigned long long) * (size_t)s.nb * s.nb * s.nb;
     unsigned long long *tabs = (unsigned long long *)workspace(ctx, "count.tables", 4 * tb);
     // full-annulus counts: a property of the ring geometry, kept per configuration
@@ -587,42 +636,37 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
             ms.d_full_counts = nullptr;
         }
     }
-    if (!items0 || !items1 || !ctl || !tabs || !ms.d_full_counts) return fail(ctx, ABS_ERR_OOM, "count workspace");
+    if (!items0 || !items1 || !ctl || !tickets || !tabs || !ms.d_full_counts)
+        return fail(ctx, ABS_ERR_OOM, "count workspace");
     const int need_full = ms.full_counts_ready ? 0 : 1;
     unsigned long long *tab[NJOB] = {tabs, tabs + tb / 8, tabs + 2 * (tb / 8), tabs + 3 * (tb / 8), ms.d_full_counts};
-    cudaStream_t stm = ctx->stream;
-    {
-        StageTimer timer(ctx, "count_items");
-        cudaMemsetAsync(tabs, 0, 4 * tb, stm);
-        if (need_full) cudaMemsetAsync(ms.d_full_counts, 0, tb, stm);
-        k_count_items<<<1, 1024, 0, stm>>>(s.nb, rb.counts, chunk, need_full, items0, items1, cap, ctl,
-                                           ctx->d_err);
-    }
+    // ring tables; their last block also clears the tables and writes the work items
+    RingBufs rb;
+    const ItemArgs ia{chunk, need_full, cap, items0, items1, ctl, ctx->d_err, tickets, tabs, ms.d_full_counts};
+    abs_status st = ring_tables(ctx, s, d_mask, rb, d_ellbar, &ia);
+    if (st != ABS_OK) return st;
     Fams fam{rb.lists, rb.ring_off, rb.counts};
     {
+        // pairs against each byte map; the last CTA of the second launch gathers T
         StageTimer timer(ctx, "count_pairs");
         const int blocks = ctx->sm_count * per_sm;
+        const GatherArgs g0{0, nullptr, nullptr, nullptr, nullptr};
+        const GatherArgs g1{n_trip, d_ijk, ctl, d_count, tickets + 1};
         if (map_smem) {
-            launch_pairs<true>(ctx, G, blocks, threads, smem, items0, ctl + 0, ctl + 2, fam, rb.mapF, tab);
-            launch_pairs<true>(ctx, G, blocks, threads, smem, items1, ctl + 1, ctl + 3, fam, rb.mapA, tab);
+            launch_pairs<true>(ctx, G, blocks, threads, smem, items0, ctl + 0, ctl + 2, fam, rb.mapF, tab, g0);
+            launch_pairs<true>(ctx, G, blocks, threads, smem, items1, ctl + 1, ctl + 3, fam, rb.mapA, tab, g1);
         } else {
-            launch_pairs<false>(ctx, G, blocks, threads, smem, items0, ctl + 0, ctl + 2, fam, rb.mapF, tab);
-            launch_pairs<false>(ctx, G, blocks, threads, smem, items1, ctl + 1, ctl + 3, fam, rb.mapA, tab);
+            launch_pairs<false>(ctx, G, blocks, threads, smem, items0, ctl + 0, ctl + 2, fam, rb.mapF, tab, g0);
+            launch_pairs<false>(ctx, G, blocks, threads, smem, items1, ctl + 1, ctl + 3, fam, rb.mapA, tab, g1);
         }
     }
     ms.full_counts_ready = true;
-    {
-        StageTimer t2(ctx, "count_gather");
-        k_count_gather<<<(int)cdiv(n_trip, 256), 256, 0, stm>>>(s.nb, n_trip, d_ijk, ctl, tab[JOB_DIRECT],
-                                                                tab[JOB_FULL], tab[JOB_E1], tab[JOB_E2],
-                                                                tab[JOB_E3], d_count);
-    }
     return check_launch(ctx, "counts");
 }
 
 abs_status launch_ellbar(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, double *d_ellbar) {
     RingBufs rb;
-    return ring_tables(ctx, s, d_mask, rb, d_ellbar);
+    return ring_tables(ctx, s, d_mask, rb, d_ellbar, nullptr);
 }
 
 }  // namespace absk
