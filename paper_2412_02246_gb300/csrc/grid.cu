@@ -361,8 +361,8 @@ __global__ void k_scan_add(uint32_t *__restrict__ out, int64_t len,
 // cell.  A warp takes a task; lane (dy, q) owns the footprint cells
 // (2q, dy) and (2q+1, dy) of the (2r+1)^2 around the run's cell and sums
 // w = wx wy, w Re V, w Im V over the run with packed FP32x2 arithmetic
-// (plain blocks of GFOLD folded into Kahan sums, input order), then adds its
-// cells to the FP64 grid.  No shared accumulators: runs never wait on one
+// (plain blocks of GFOLD, as two interleaved chains, folded into Kahan sums;
+// a fixed order), then adds its cells to the FP64 grid.  No shared accumulators: runs never wait on one
 // another, whether the tile is dense (long runs) or sparse.
 //
 // Staged record of a visibility (RS floats): wx[0..7] (zero beyond 2r),
@@ -397,6 +397,19 @@ __device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 x) {
     const float2 t = __fadd2_rn(s, y);
     c = __ffma2_rn(y, m1, __ffma2_rn(s, m1, t));             // (t - s) - y
     s = t;
+}
+
+// One staged visibility (record at offset o) into this lane's two footprint
+// cells: w = (wx[2q], wx[2q+1]) * wy[dy], re += w Re V, im += w Im V, sum w.
+__device__ __forceinline__ void grid_acc(const float *lw, const float *lwy, const float *lv, int o, float2 &re,
+                                         float2 &im, float2 &ws) {
+    const float2 wxp = *(const float2 *)(lw + o);
+    const float2 wyy = *(const float2 *)(lwy + o);
+    const float4 vv = *(const float4 *)(lv + o);
+    const float2 w = __fmul2_rn(wxp, wyy);
+    re = __ffma2_rn(w, make_float2(vv.x, vv.y), re);
+    im = __ffma2_rn(w, make_float2(vv.z, vv.w), im);
+    ws = __fadd2_rn(w, ws);
 }
 
 // Inputs of one unit as thread (warp, lane) sees them: items t = 64 warp +
@@ -574,18 +587,22 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
                 const int2 T = task[tk];
                 const float2 z = make_float2(0.f, 0.f);
                 float2 sre = z, cre = z, sim = z, cim = z, sw = z, cw = z;
+                const float *lw = st + q2, *lwy = st + R_WY + 2 * dy, *lv = st + R_V;
                 for (int j0 = T.x; j0 < T.y; j0 += GFOLD) {   // plain blocks of GFOLD, folded into Kahan sums
-                    const int je = min(j0 + GFOLD, T.y);
                     float2 bre = z, bim = z, bw = z;
-                    for (int j = j0; j < je; ++j) {
-                        const float *rec = st + j * RS;
-                        const float2 wxp = *(const float2 *)(rec + q2);
-                        const float2 wyy = *(const float2 *)(rec + R_WY + 2 * dy);
-                        const float4 vv = *(const float4 *)(rec + R_V);
-                        const float2 w = __fmul2_rn(wxp, wyy);
-                        bre = __ffma2_rn(w, make_float2(vv.x, vv.y), bre);
-                        bim = __ffma2_rn(w, make_float2(vv.z, vv.w), bim);
-                        bw = __fadd2_rn(w, bw);
+                    if (j0 + GFOLD <= T.y) {
+                        // a full block: unrolled, two independent chains (even, odd visibilities)
+                        float2 bre1 = z, bim1 = z, bw1 = z;
+#pragma unroll
+                        for (int u = 0; u < GFOLD; u += 2) {
+                            grid_acc(lw, lwy, lv, (j0 + u) * RS, bre, bim, bw);
+                            grid_acc(lw, lwy, lv, (j0 + u + 1) * RS, bre1, bim1, bw1);
+                        }
+                        bre = __fadd2_rn(bre, bre1);
+                        bim = __fadd2_rn(bim, bim1);
+                        bw = __fadd2_rn(bw, bw1);
+                    } else {
+                        for (int j = j0; j < T.y; ++j) grid_acc(lw, lwy, lv, j * RS, bre, bim, bw);
                     }
                     kahan_add2(sre, cre, bre);
                     kahan_add2(sim, cim, bim);
