@@ -76,6 +76,10 @@ struct abs_ctx {
     std::map<std::string, std::pair<double, int64_t>> stage_totals;
     int device = 0;
     cudaStream_t stream = nullptr;
+    // a second stream for the exact counts, which abs_estimate runs beside the
+    // transforms and triple sums (fork and join by events; both join a graph capture)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int sm_count = 0;
     std::string last_error;
     int32_t *d_err = nullptr;  // latched device error word: 0 ok, else a code below
@@ -131,9 +135,11 @@ abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc
 void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc);
 // With d_count and d_B also given, B = S / (A T) is written as well (fused
 // into the final reduction on the FP32 path).
+// wait_before_b, if given, is waited for (on ctx->stream) before B is formed.
 abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_fields,
                               int32_t n_trip, const int32_t *d_ijk, double *d_sum,
-                              const int64_t *d_count = nullptr, double *d_B = nullptr);
+                              const int64_t *d_count = nullptr, double *d_B = nullptr,
+                              cudaEvent_t wait_before_b = nullptr);
 // Split-BF16 tcgen05 form of the same sums (precision == ABS_SPLIT_BF16).
 abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
                             int32_t n_trip, const int32_t *d_ijk, double *d_sum);

@@ -412,7 +412,10 @@ abs_status abs_create(abs_ctx **out, int32_t device, void *cuda_stream) {
     ctx->stream = (cudaStream_t)cuda_stream;
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (cudaMalloc(&ctx->d_err, sizeof(int32_t)) != cudaSuccess ||
-        cudaMemset(ctx->d_err, 0, sizeof(int32_t)) != cudaSuccess) {
+        cudaMemset(ctx->d_err, 0, sizeof(int32_t)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         return ABS_ERR_OOM;
@@ -430,6 +433,12 @@ abs_status abs_destroy(abs_ctx *ctx) {
         for (auto &kv : ctx->ws) cudaFree(kv.second.p);
         for (auto &kv : ctx->setups) free_setup(*kv.second);
         cudaFree(ctx->d_err);
+        if (ctx->side) {
+            cudaStreamSynchronize(ctx->side);
+            cudaStreamDestroy(ctx->side);
+        }
+        if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+        if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
         for (auto &p : ctx->pending) {
             cudaEventDestroy(p.a);
             cudaEventDestroy(p.b);
@@ -588,15 +597,36 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
         // the transform reads the FP64 accumulators; the mask is needed once
         ABS_CHECK(launch_grid_accumulate(ctx, s, n_vis, d_vis + (size_t)r * 2 * n_vis, nullptr, nullptr,
                                          r == 0 ? mask : nullptr));
+        cudaEvent_t join = nullptr;
         if (r == 0) {
-            // the filled mask depends on the baselines only: counts and mean l once
-            ABS_CHECK(launch_counts(ctx, s, mask, n_trip, d_ijk, count, d_ellbar));
+            // the filled mask depends on the baselines only: counts and mean l once,
+            // on the side stream beside the transforms (not while profiling stages)
+            if (!ctx->profiling && ctx->side) {
+                cudaEventRecord(ctx->ev_fork, ctx->stream);
+                cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+                cudaStream_t main = ctx->stream;
+                ctx->stream = ctx->side;
+                const abs_status st = launch_counts(ctx, s, mask, n_trip, d_ijk, count, d_ellbar);
+                cudaEventRecord(ctx->ev_join, ctx->side);
+                ctx->stream = main;
+                join = ctx->ev_join;
+                if (st != ABS_OK) {
+                    cudaStreamWaitEvent(ctx->stream, join, 0);
+                    return st;
+                }
+            } else {
+                ABS_CHECK(launch_counts(ctx, s, mask, n_trip, d_ijk, count, d_ellbar));
+            }
         }
         double *acc;
         grid_acc_buffers(ctx, s, &acc);
-        ABS_CHECK(launch_filter_fft_acc(ctx, s, acc, fields));
+        const abs_status sf = launch_filter_fft_acc(ctx, s, acc, fields);
+        if (sf != ABS_OK) {
+            if (join) cudaStreamWaitEvent(ctx->stream, join, 0);
+            return sf;
+        }
         ABS_CHECK(launch_triple_sums(ctx, s, fields, n_trip, d_ijk, sum, count,
-                                     d_B ? d_B + (size_t)r * n_trip : nullptr));
+                                     d_B ? d_B + (size_t)r * n_trip : nullptr, join));
     }
     return ABS_OK;
 }

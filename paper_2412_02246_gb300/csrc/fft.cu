@@ -172,32 +172,56 @@ __device__ float4 *fft_lines(float4 *a, float4 *b, int lines, const FftPlan &P,
     return a;
 }
 
-__device__ __forceinline__ float4 cdf_from_double(double re, double im) {   // (re.hi, im.hi, re.lo, im.lo)
-    const float rh = (float)re, ih = (float)im;
-    return make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
+// Double-float a / b (hi, lo pairs, b > 0): q1 = a_hi / b_hi, the exact
+// remainder a - q1 b by TwoProduct, one correction q2 = r / b_hi, renormalised.
+// Relative error about 2^-44, in FP32 arithmetic only.
+__device__ __forceinline__ void df_div(float a_hi, float a_lo, float b_hi, float b_lo, float &q_hi, float &q_lo) {
+    const float q1 = __fdiv_rn(a_hi, b_hi);
+    const float p_hi = __fmul_rn(q1, b_hi);
+    const float p_lo = fmaf(q1, b_hi, -p_hi);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(__fsub_rn(a_hi, p_hi), p_lo), __fmul_rn(q1, b_lo)), a_lo);
+    const float q2 = __fdiv_rn(r, b_hi);
+    q_hi = __fadd_rn(q1, q2);
+    q_lo = __fsub_rn(q2, __fsub_rn(q_hi, q1));
 }
 
-// Gridded data as the transform reads it: the weighted mean on a filled cell.
+// A double as a double-float pair (two roundings to FP32).
+__device__ __forceinline__ void df_of(double v, float &hi, float &lo) {
+    hi = __double2float_rn(v);
+    lo = __double2float_rn(v - (double)hi);
+}
+
+// Gridded data as the transform reads it: the weighted mean X on a filled
+// cell, as a packed double-float complex (re.hi, im.hi, re.lo, im.lo).
 struct GridF32 {   // abs_grid outputs (FP32)
     const float2 *grid;
     const float *wsum;
     const uint8_t *mask;
-    __device__ bool value(int64_t cell, int64_t mcell, double &re, double &im) const {
+    __device__ bool value(int64_t cell, int64_t mcell, float4 &x) const {
         if (!mask[cell]) return false;
         const float2 g = grid[cell];
-        const double w = (double)wsum[cell];
-        re = (double)g.x / w;
-        im = (double)g.y / w;
+        const float w = wsum[cell];
+        float rh, rl, ih, il;
+        df_div(g.x, 0.f, w, 0.f, rh, rl);
+        df_div(g.y, 0.f, w, 0.f, ih, il);
+        x = make_float4(rh, ih, rl, il);
         return true;
     }
 };
 struct GridF64 {   // FP64 accumulators before the mirror (inside abs_estimate)
     const double *re, *im, *w;
-    __device__ bool value(int64_t cell, int64_t mcell, double &vr, double &vi) const {
+    __device__ bool value(int64_t cell, int64_t mcell, float4 &x) const {
+        // the mirrored sums in FP64, then the division in double-float (GB300's
+        // FP64 pipe is narrow; the sums need FP64, the quotient does not)
         const double ww = w[cell] + w[mcell];   // > 0 exactly on filled cells
         if (!(ww > 0.0)) return false;
-        vr = (re[cell] + re[mcell]) / ww;
-        vi = (im[cell] - im[mcell]) / ww;
+        float wh, wl, ah, al, bh, bl, rh, rl, ih, il;
+        df_of(ww, wh, wl);
+        df_of(re[cell] + re[mcell], ah, al);
+        df_of(im[cell] - im[mcell], bh, bl);
+        df_div(ah, al, wh, wl, rh, rl);
+        df_div(bh, bl, wh, wl, ih, il);
+        x = make_float4(rh, ih, rl, il);
         return true;
     }
 };
@@ -229,10 +253,10 @@ __global__ void __launch_bounds__(256) k_fft_rows(RingGeom G, FftPlan P, int RB,
         if (!in_a && !in_b) continue;
         const int64_t cell = (int64_t)(y < 0 ? y + G.n : y) * G.n + (x < 0 ? x + G.n : x);
         const int64_t mcell = (int64_t)(y > 0 ? G.n - y : -y) * G.n + (x > 0 ? G.n - x : -x);
-        double vr, vi;
-        if (!src.value(cell, mcell, vr, vi)) continue;
-        // Z = X_a + i X_b
-        l0[(size_t)r * G.N + (x < 0 ? x + G.N : x)] = in_a ? cdf_from_double(vr, vi) : cdf_from_double(-vi, vr);
+        float4 v;
+        if (!src.value(cell, mcell, v)) continue;
+        // Z = X_a + i X_b (i (re + i im) = -im + i re)
+        l0[(size_t)r * G.N + (x < 0 ? x + G.N : x)] = in_a ? v : make_float4(-v.y, v.x, -v.w, v.z);
     }
     float4 *res = fft_lines(l0, l1, RB, P, tw);
     for (int e = threadIdx.x; e < RB * G.N; e += blockDim.x) {

@@ -208,10 +208,15 @@ abs_status launch_check_triplets(abs_ctx *ctx, const Setup &s, int32_t n_trip, c
 }
 
 abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_fields, int32_t n_trip,
-                              const int32_t *d_ijk, double *d_sum, const int64_t *d_count, double *d_B) {
-    if (n_trip == 0) return ABS_OK;
+                              const int32_t *d_ijk, double *d_sum, const int64_t *d_count, double *d_B,
+                              cudaEvent_t wait_before_b) {
+    if (n_trip == 0) {
+        if (wait_before_b) cudaStreamWaitEvent(ctx->stream, wait_before_b, 0);
+        return ABS_OK;
+    }
     if (s.precision == ABS_SPLIT_BF16) {
         const abs_status st = launch_triple_tc(ctx, s, d_fields, n_trip, d_ijk, d_sum);
+        if (wait_before_b) cudaStreamWaitEvent(ctx->stream, wait_before_b, 0);
         if (st != ABS_OK || !d_B) return st;
         return launch_normalise(ctx, s, n_trip, d_sum, d_count, d_B);
     }
@@ -227,6 +232,7 @@ abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_field
         k_triple_fp32<<<dim3((unsigned)nsplit, tp.tgroups), tp.threads, tp.smem, ctx->stream>>>(tp.G, d_fields,
                                                                                              d_ijk, partial);
     }
+    if (wait_before_b) cudaStreamWaitEvent(ctx->stream, wait_before_b, 0);
     StageTimer timer(ctx, "triple_reduce");
     k_triple_reduce<<<(int)cdiv(n_trip, 8), 256, 0, ctx->stream>>>(
         n_trip, (int)nsplit, 1.0 / ((double)s.N * (double)s.N), partial, d_sum, d_count, s.norm_A,
