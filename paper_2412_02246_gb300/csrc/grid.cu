@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(KT) k_plan_keys(GridGeom G, int64_t n_vis, con
         const unsigned peers = __match_any_sync(FULL, key);
         if (on && lane == __ffs(peers) - 1) {
             const uint32_t c = (uint32_t)__popc(peers);
-            if (key != key_none) atomicAdd(&tile_hist[key], c);
+            if (tile_hist && key != key_none) atomicAdd(&tile_hist[key], c);
             atomicAdd(&h[key & dmask], c);
         }
     }
@@ -269,13 +269,21 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
 }
 
 // Cut every tile's run of sorted visibilities into units of <= UMAX (one
-// block of 1024 threads; tile totals in hist).
-__device__ void cut_units(const uint32_t *__restrict__ hist, int ntiles, int4 *__restrict__ units,
+// block).  Tile totals come from hist, or, when hist is null (a one-pass sort
+// whose digit is the tile), from the scanned digit histogram itself: tile t
+// starts at the exclusive prefix of entry t * nchunks (out + bsum).
+__device__ void cut_units(const uint32_t *__restrict__ hist, const uint32_t *__restrict__ out,
+                          const uint32_t *__restrict__ bsum, int nchunks, int ntiles, int4 *__restrict__ units,
                           int *__restrict__ n_units, int cap, uint32_t *__restrict__ n_valid_out, uint32_t *sh) {
+    auto tile_start = [&](int t) {
+        const int64_t e = (int64_t)t * nchunks;
+        return __ldcg(out + e) + __ldcg(bsum + e / 4096);
+    };
     uint32_t carry = 0, base = 0;
     for (int b = 0; b < ntiles; b += blockDim.x) {
         const int t = b + threadIdx.x;
-        const uint32_t c = t < ntiles ? __ldcg(hist + t) : 0u;
+        uint32_t c = 0u;
+        if (t < ntiles) c = hist ? __ldcg(hist + t) : tile_start(t + 1) - tile_start(t);
         uint32_t ctot;
         const uint32_t start = base + block_exclusive_scan(c, sh, ctot);   // tile offset in sorted order
         const uint32_t nu = (c + UMAX - 1) / UMAX;
@@ -300,8 +308,9 @@ __device__ void cut_units(const uint32_t *__restrict__ hist, int ntiles, int4 *_
 // Exclusive scan of len values, 4096 per 1024-thread block: every block scans
 // its part into out and writes its total; the last block to finish (ticket)
 // scans the totals in place into block offsets (so element e's exclusive
-// prefix is out[e] + bsum[e / 4096]), optionally cuts the gridding units from
-// the tile totals, and re-arms the ticket.
+// prefix is out[e] + bsum[e / 4096]), optionally cuts the gridding units (from
+// tile_hist, or with tile_hist null from this scan of a tile-digit histogram
+// with ntiles + 1 bins), and re-arms the ticket.
 __global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ in, int64_t len,
                                                uint32_t *__restrict__ out, uint32_t *__restrict__ bsum,
                                                unsigned *__restrict__ ticket,
@@ -342,7 +351,8 @@ __global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ in, 
         if (i < gridDim.x) bsum[i] = carry + p;
         carry += t;
     }
-    if (tile_hist) cut_units(tile_hist, ntiles, units, n_units, cap, n_valid_out, sh);
+    if (units) cut_units(tile_hist, out, bsum, ntiles ? (int)(len / (ntiles + 1)) : 0, ntiles, units, n_units, cap,
+                         n_valid_out, sh);
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
@@ -735,9 +745,12 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
     if (!bsum || !ticket) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
     cudaStream_t st = ctx->stream;
     StageTimer timer(ctx, "grid_plan");
-    cudaMemsetAsync(b.tile_hist, 0, sizeof(uint32_t) * b.ntiles, st);
+    // one pass: the tile totals are read off the scanned histogram; two: counted by atomics
+    uint32_t *tile_hist = passes == 1 ? nullptr : b.tile_hist;
+    if (tile_hist) cudaMemsetAsync(tile_hist, 0, sizeof(uint32_t) * b.ntiles, st);
     if (n_vis == 0) {
         // no visibilities: no units
+        cudaMemsetAsync(b.tile_hist, 0, sizeof(uint32_t) * b.ntiles, st);
         k_scan<<<1, 1024, 0, st>>>(b.rhist, 0, b.roffs, bsum, ticket, b.tile_hist, b.ntiles, b.units, b.n_units,
                                    b.units_cap, b.n_valid);
         return check_launch(ctx, "grid plan");
@@ -745,7 +758,7 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
     const size_t ssmem0 = (size_t)nbins0 * (4 + 2 * ST_W), ssmem = (size_t)(1 << dw) * (4 + 2 * ST_W);
     cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)std::max(ssmem0, ssmem));
-    k_plan_keys<<<b.nchunks, KT, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, b.tile_hist, key_none, nbins0,
+    k_plan_keys<<<b.nchunks, KT, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, tile_hist, key_none, nbins0,
                                           passes == 1 ? 0xffffffffu : (uint32_t)((1 << dw) - 1), b.nchunks,
                                           b.rhist);
     // stable sort of (tile, index): keys -> (k2, v2) -> (s_idx, s_uv); the first
@@ -757,9 +770,10 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
         const uint32_t dmask = passes == 1 ? 0xffffffffu : (uint32_t)((1 << dw) - 1);
         if (ps > 0) k_radix_hist<<<b.nchunks, 256, 0, st>>>(ki, n_vis, dw * ps, dw, b.nchunks, b.rhist);
         const int64_t len = (int64_t)nbins * b.nchunks;
-        k_scan<<<(int)cdiv(len, 4096), 1024, 0, st>>>(b.rhist, len, b.roffs, bsum, ticket,
-                                                      ps == 0 ? b.tile_hist : nullptr, b.ntiles, b.units,
-                                                      b.n_units, b.units_cap, b.n_valid);
+        // the units are cut by the first scan (one pass) or the last (two passes)
+        const bool cut = passes == 1 || last;
+        k_scan<<<(int)cdiv(len, 4096), 1024, 0, st>>>(b.rhist, len, b.roffs, bsum, ticket, tile_hist, b.ntiles,
+                                                      cut ? b.units : nullptr, b.n_units, b.units_cap, b.n_valid);
         k_radix_scatter<<<b.nchunks, ST_W * 32, ps == 0 ? ssmem0 : ssmem, st>>>(
             ki, vi, n_vis, dw * ps, nbins, dmask, b.nchunks, b.roffs, bsum, last ? nullptr : b.k2,
             last ? b.s_idx : b.v2, (const float2 *)d_uv, last ? b.s_uv : nullptr);
