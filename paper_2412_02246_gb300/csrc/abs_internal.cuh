@@ -119,9 +119,10 @@ const Setup *get_setup(abs_ctx *ctx, const abs_config *cfg, abs_status &st);
 // per-realisation accumulation that reuses it.
 abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv);
 // With d_grid == d_wsum == nullptr only the FP64 accumulators (and, if d_mask,
-// the filled mask) are produced.
+// the filled mask) are produced.  acc_zeroed: the caller has already cleared
+// the accumulators (grid_acc_buffers) on this stream's timeline.
 abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_vis,
-                                  float *d_grid, float *d_wsum, uint8_t *d_mask);
+                                  float *d_grid, float *d_wsum, uint8_t *d_mask, bool acc_zeroed = false);
 abs_status launch_filter_fft(abs_ctx *ctx, const Setup &s, const float *d_grid,
                              const float *d_wsum, const uint8_t *d_mask, float *d_fields);
 // The same transform fed directly from the FP64 gridding accumulators (mirror
@@ -143,10 +144,13 @@ abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_field
 // Split-BF16 tcgen05 form of the same sums (precision == ABS_SPLIT_BF16).
 abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
                             int32_t n_trip, const int32_t *d_ijk, double *d_sum);
-// Ring tables (cell lists, byte map) from d_mask, then exact counts (d_count may be
-// NULL) and, if d_ellbar is not NULL, the mean l of every ring.
+// Ring tables (cell lists, byte map) from d_mask, or, with d_accw given, from
+// the FP64 weight sums before the mirror (a cell is filled when it or its
+// mirror has a nonzero sum), then exact counts (d_count may be NULL) and, if
+// d_ellbar is not NULL, the mean l of every ring.
 abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, int32_t n_trip,
-                         const int32_t *d_ijk, int64_t *d_count, double *d_ellbar);
+                         const int32_t *d_ijk, int64_t *d_count, double *d_ellbar,
+                         const double *d_accw = nullptr);
 // Exclusive scan of len uint32 values on the context's stream (2 kernels);
 // bsum holds cdiv(len, 4096) + 1 entries.  False if its counter cannot be allocated.
 bool scan_u32(abs_ctx *ctx, const uint32_t *in, int64_t len, uint32_t *out, uint32_t *bsum);

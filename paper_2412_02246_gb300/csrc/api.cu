@@ -585,18 +585,31 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
                                 const int32_t *d_ijk, double *d_B, int64_t *d_count, double *d_ellbar) {
     const int64_t cells = (int64_t)s.n * s.n;
     const int64_t P = (int64_t)s.N * s.N;
-    uint8_t *mask = (uint8_t *)workspace(ctx, "est.mask", cells);
     float *fields = (float *)workspace(ctx, "est.fields", sizeof(float) * (size_t)s.nb * P);
     double *sum = (double *)workspace(ctx, "est.sum", sizeof(double) * std::max(n_trip, 1));
     int64_t *count = d_count ? d_count : (int64_t *)workspace(ctx, "est.count", sizeof(int64_t) * std::max(n_trip, 1));
-    if (!mask || !fields || !sum || !count) return fail(ctx, ABS_ERR_OOM, "estimate workspace");
+    if (!fields || !sum || !count) return fail(ctx, ABS_ERR_OOM, "estimate workspace");
     // the canonical list (d_ijk == NULL at the ABI) was built and checked with the setup
     if (d_ijk != s.d_ijk) ABS_CHECK(launch_check_triplets(ctx, s, n_trip, d_ijk));
-    ABS_CHECK(launch_grid_plan(ctx, s, n_vis, d_uv));
+    // the first realisation's accumulators are cleared on the side stream while
+    // the plan runs (not while profiling stages)
+    double *acc0 = nullptr;
+    grid_acc_buffers(ctx, s, &acc0);
+    if (!acc0) return fail(ctx, ABS_ERR_OOM, "grid accumulation workspace");
+    const bool pre_zero = !ctx->profiling && ctx->side;
+    if (pre_zero) {
+        cudaEventRecord(ctx->ev_fork, ctx->stream);
+        cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+        cudaMemsetAsync(acc0, 0, sizeof(double) * 3 * (size_t)cells, ctx->side);
+        cudaEventRecord(ctx->ev_join, ctx->side);
+    }
+    const abs_status sp = launch_grid_plan(ctx, s, n_vis, d_uv);
+    if (pre_zero) cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
+    if (sp != ABS_OK) return sp;
     for (int32_t r = 0; r < n_real; ++r) {
-        // the transform reads the FP64 accumulators; the mask is needed once
-        ABS_CHECK(launch_grid_accumulate(ctx, s, n_vis, d_vis + (size_t)r * 2 * n_vis, nullptr, nullptr,
-                                         r == 0 ? mask : nullptr));
+        // the transform and the counts read the FP64 accumulators directly
+        ABS_CHECK(launch_grid_accumulate(ctx, s, n_vis, d_vis + (size_t)r * 2 * n_vis, nullptr, nullptr, nullptr,
+                                         r == 0 && pre_zero));
         cudaEvent_t join = nullptr;
         if (r == 0) {
             // the filled mask depends on the baselines only: counts and mean l once,
@@ -606,7 +619,8 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
                 cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
                 cudaStream_t main = ctx->stream;
                 ctx->stream = ctx->side;
-                const abs_status st = launch_counts(ctx, s, mask, n_trip, d_ijk, count, d_ellbar);
+                const abs_status st = launch_counts(ctx, s, nullptr, n_trip, d_ijk, count, d_ellbar,
+                                                    acc0 + 2 * cells);
                 cudaEventRecord(ctx->ev_join, ctx->side);
                 ctx->stream = main;
                 join = ctx->ev_join;
@@ -615,7 +629,7 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
                     return st;
                 }
             } else {
-                ABS_CHECK(launch_counts(ctx, s, mask, n_trip, d_ijk, count, d_ellbar));
+                ABS_CHECK(launch_counts(ctx, s, nullptr, n_trip, d_ijk, count, d_ellbar, acc0 + 2 * cells));
             }
         }
         double *acc;

@@ -154,6 +154,7 @@ __device__ __forceinline__ void df_add(float &sh, float &sl, float h, float l) {
 // it).  Also writes the byte maps of F and A (at lin > 0) and the row's sum of
 // |g| over filled cells in double-float.
 __global__ void k_ring_cells(CountGeom G, const int64_t *__restrict__ q, const uint8_t *__restrict__ mask,
+                             const unsigned long long *__restrict__ accw,
                              const int64_t *__restrict__ ring_off, int32_t *__restrict__ cnt_up,
                              short2 *__restrict__ lists, uint8_t *__restrict__ mapF, uint8_t *__restrict__ mapA,
                              double *__restrict__ rowlen) {
@@ -177,7 +178,12 @@ __global__ void k_ring_cells(CountGeom G, const int64_t *__restrict__ q, const u
             x = span_x(sp, t);
             in = y > 0 || x > 0;
         }
-        const bool on = in && mask[cell_index(G.n, x, y)] != 0;
+        // filled: the mask, or (accw given) a nonzero weight sum at g or -g
+        bool on = false;
+        if (in) {
+            if (accw) on = accw[cell_index(G.n, x, y)] != 0ull || accw[cell_index(G.n, -x, -y)] != 0ull;
+            else on = mask[cell_index(G.n, x, y)] != 0;
+        }
         const unsigned bf = __ballot_sync(FULL, on), bh = __ballot_sync(FULL, in && !on);
         const unsigned ba = __ballot_sync(FULL, in);
         int pf = 0, ph = 0, pa = 0;
@@ -557,7 +563,7 @@ struct RingBufs {
     uint8_t *mapF, *mapA;
 };
 
-abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, RingBufs &rb,
+abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, const double *d_accw, RingBufs &rb,
                        double *d_ellbar, const ItemArgs *ia) {
     const CountGeom G = cgeom(s);
     const int64_t U = std::max<int64_t>(s.up_off.back(), 1);   // upper-half lattice cells, all rings
@@ -576,7 +582,8 @@ abs_status ring_tables(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, Ring
     StageTimer timer(ctx, "ring_lists");
     cudaStream_t st = ctx->stream;
     cudaMemsetAsync(maps, 0, (size_t)2 * mb + sizeof(int32_t) * NFAM * s.nb, st);
-    k_ring_cells<<<(int)cdiv(nrow * 32, 256), 256, 0, st>>>(G, s.d_q, d_mask, rb.ring_off, cnt_up, rb.lists,
+    k_ring_cells<<<(int)cdiv(nrow * 32, 256), 256, 0, st>>>(G, s.d_q, d_mask, (const unsigned long long *)d_accw,
+                                                            rb.ring_off, cnt_up, rb.lists,
                                                             rb.mapF, rb.mapA, rowlen);
     ItemArgs none{};
     int blocks = (int)cdiv((int64_t)NFAM * s.nb * 32, 256);
@@ -600,10 +607,10 @@ void launch_pairs(abs_ctx *ctx, const CountGeom &G, int blocks, int threads, siz
 }  // namespace
 
 abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, int32_t n_trip,
-                         const int32_t *d_ijk, int64_t *d_count, double *d_ellbar) {
+                         const int32_t *d_ijk, int64_t *d_count, double *d_ellbar, const double *d_accw) {
     if (n_trip == 0 || !d_count) {
         RingBufs rb;
-        return ring_tables(ctx, s, d_mask, rb, d_ellbar, nullptr);
+        return ring_tables(ctx, s, d_mask, d_accw, rb, d_ellbar, nullptr);
     }
     const CountGeom G = cgeom(s);
     const int hs = s.nb + 1;
@@ -643,7 +650,7 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     // ring tables; their last block also clears the tables and writes the work items
     RingBufs rb;
     const ItemArgs ia{chunk, need_full, cap, items0, items1, ctl, ctx->d_err, tickets, tabs, ms.d_full_counts};
-    abs_status st = ring_tables(ctx, s, d_mask, rb, d_ellbar, &ia);
+    abs_status st = ring_tables(ctx, s, d_mask, d_accw, rb, d_ellbar, &ia);
     if (st != ABS_OK) return st;
     Fams fam{rb.lists, rb.ring_off, rb.counts};
     {
@@ -666,7 +673,7 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
 
 abs_status launch_ellbar(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, double *d_ellbar) {
     RingBufs rb;
-    return ring_tables(ctx, s, d_mask, rb, d_ellbar, nullptr);
+    return ring_tables(ctx, s, d_mask, nullptr, rb, d_ellbar, nullptr);
 }
 
 }  // namespace absk

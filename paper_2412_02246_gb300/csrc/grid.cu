@@ -380,8 +380,8 @@ __global__ void k_scan_add(uint32_t *__restrict__ out, int64_t len,
 constexpr int GT = 256;          // threads per gridding CTA (8 warps x UMAX/8 items)
 constexpr int RS = 28;           // floats per staged record
 constexpr int R_WY = 8, R_V = 24;
-constexpr int GFOLD = 8;
-constexpr int CHUNK = 64;        // visibilities per task at most
+constexpr int GFOLD = 16;
+constexpr int CHUNK = 128;       // visibilities per task at most
 constexpr int MAXTASK = UMAX / CHUNK + 256;   // sum over cells of ceil(run / CHUNK)
 static_assert(UMAX == 8 * 64, "the in-unit sort gives each of 8 warps two rounds of 32 items");
 constexpr size_t GRID_SMEM = UMAX * sizeof(float) * RS + sizeof(int2) * MAXTASK + sizeof(uint16_t) * 8 * 256 +
@@ -789,7 +789,7 @@ void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc) {
 }
 
 abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_vis,
-                                  float *d_grid, float *d_wsum, uint8_t *d_mask) {
+                                  float *d_grid, float *d_wsum, uint8_t *d_mask, bool acc_zeroed) {
     const GridGeom G = geom(s);
     PlanBufs b;
     if (!plan_bufs(ctx, G, n_vis, b)) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
@@ -797,7 +797,7 @@ abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, c
     double *acc = (double *)workspace(ctx, "grid.acc", sizeof(double) * 3 * cells);
     if (!acc) return fail(ctx, ABS_ERR_OOM, "grid accumulation workspace");
     cudaStream_t st = ctx->stream;
-    {
+    if (!acc_zeroed) {
         StageTimer timer(ctx, "grid_zero");
         cudaMemsetAsync(acc, 0, sizeof(double) * 3 * cells, st);
     }

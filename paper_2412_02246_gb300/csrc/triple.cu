@@ -113,7 +113,7 @@ __global__ void k_triple_fp32(TripleGeom G, const float *__restrict__ fields, co
     }
 }
 
-// Launch shape of k_triple_fp32: pixel splits (about two CTAs per SM, or
+// Launch shape of k_triple_fp32: pixel splits (about one CTA per SM, or
 // fewer when max_split caps them) x triplet groups of up to 4096 (one warp per
 // 32 triplets, at most 1024 threads, walked in at most four rounds), and the
 // staged chunk.
@@ -135,7 +135,7 @@ bool triple_plan(int nb, int N, int n_trip, int sms, int64_t max_split, const fl
     tp.threads = 32 * warps;
     G.rounds = (int)std::min<int64_t>(4, cdiv(ngroups, warps));
     tp.tgroups = (int)cdiv(n_trip, (int64_t)G.rounds * tp.threads);
-    int64_t target = std::max<int64_t>(1, std::min<int64_t>(cdiv(2 * (int64_t)sms, tp.tgroups), max_split));
+    int64_t target = std::max<int64_t>(1, std::min<int64_t>(cdiv((int64_t)sms, tp.tgroups), max_split));
     int64_t per = cdiv(cdiv(G.P, target), 4) * 4;
     const int64_t pc_max = std::max<int64_t>(4, ((96 * 1024) / (4 * (int64_t)nb) - 4) / 4 * 4);
     G.PC = (int)std::min<int64_t>(per, pc_max);
