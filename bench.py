@@ -160,6 +160,19 @@ def dist_setup():
     return world, rank, local
 
 
+def whole_job_rate(total_ms, steps, world, dev):
+    """Whole-job estimates/s over all ranks: every rank ran `steps` independent
+    replicas in `total_ms`; the job takes as long as its slowest rank (MAX over
+    ranks), and the units are those of all ranks.  Returns (rate, max_ms)."""
+    import torch
+    t_max = float(total_ms)
+    if world > 1:
+        t = torch.tensor([t_max], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    return world * steps / (t_max * 1e-3), t_max
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -334,12 +347,7 @@ def run_ours(args):
     prof = ctx.profile_read()
     ctx.profile(False)
     ctx.sync()
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps / (t_max * 1e-3)
+    value, t_max = whole_job_rate(total_ms, args.steps, world, dev)
 
     # batched form: realisations sharing baselines (plan and counts once per batch)
     R = args.batch
