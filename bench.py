@@ -55,7 +55,7 @@ KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "grid_mask":
 def plan_kernels(n_grid, radius):
     tiles = -(-(n_grid - 1 + 2 * radius) // 16)
     passes = -(-int(tiles * tiles).bit_length() // 11)
-    return 3 * passes
+    return 3 * passes + (1 if passes == 1 else 0)   # + the unit cutter beside the one-pass scatter
 
 
 def load_peaks():

@@ -305,6 +305,16 @@ __device__ void cut_units(const uint32_t *__restrict__ hist, const uint32_t *__r
     }
 }
 
+// One block: the gridding units of a one-pass sort, cut from its scanned tile
+// histogram (run on the side stream beside the scatter).
+__global__ void __launch_bounds__(1024) k_units_scan(const uint32_t *__restrict__ out,
+                                                     const uint32_t *__restrict__ bsum, int nchunks, int ntiles,
+                                                     int4 *__restrict__ units, int *__restrict__ n_units, int cap,
+                                                     uint32_t *__restrict__ n_valid_out) {
+    __shared__ uint32_t sh[32];
+    cut_units(nullptr, out, bsum, nchunks, ntiles, units, n_units, cap, n_valid_out, sh);
+}
+
 // Exclusive scan of len values, 4096 per 1024-thread block: every block scans
 // its part into out and writes its total; the last block to finish (ticket)
 // scans the totals in place into block offsets (so element e's exclusive
@@ -761,8 +771,11 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
     k_plan_keys<<<b.nchunks, KT, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, tile_hist, key_none, nbins0,
                                           passes == 1 ? 0xffffffffu : (uint32_t)((1 << dw) - 1), b.nchunks,
                                           b.rhist);
-    // stable sort of (tile, index): keys -> (k2, v2) -> (s_idx, s_uv); the first
-    // scan also cuts the units from the tile totals
+    // stable sort of (tile, index): keys -> (k2, v2) -> (s_idx, s_uv).  Units:
+    // one pass, cut from the scanned histogram by one block on the side stream
+    // while the scatter runs (by the scan's last block while profiling); two
+    // passes, from the tile totals by the last scan's last block
+    const bool fork = passes == 1 && !ctx->profiling && ctx->side;
     const uint32_t *ki = b.keys, *vi = nullptr;
     for (int ps = 0; ps < passes; ++ps) {
         const bool last = ps == passes - 1;
@@ -770,16 +783,23 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
         const uint32_t dmask = passes == 1 ? 0xffffffffu : (uint32_t)((1 << dw) - 1);
         if (ps > 0) k_radix_hist<<<b.nchunks, 256, 0, st>>>(ki, n_vis, dw * ps, dw, b.nchunks, b.rhist);
         const int64_t len = (int64_t)nbins * b.nchunks;
-        // the units are cut by the first scan (one pass) or the last (two passes)
-        const bool cut = passes == 1 || last;
+        const bool cut = !fork && (passes == 1 || last);
         k_scan<<<(int)cdiv(len, 4096), 1024, 0, st>>>(b.rhist, len, b.roffs, bsum, ticket, tile_hist, b.ntiles,
                                                       cut ? b.units : nullptr, b.n_units, b.units_cap, b.n_valid);
+        if (fork) {
+            cudaEventRecord(ctx->ev_fork2, st);
+            cudaStreamWaitEvent(ctx->side, ctx->ev_fork2, 0);
+            k_units_scan<<<1, 1024, 0, ctx->side>>>(b.roffs, bsum, b.nchunks, b.ntiles, b.units, b.n_units,
+                                                    b.units_cap, b.n_valid);
+            cudaEventRecord(ctx->ev_join2, ctx->side);
+        }
         k_radix_scatter<<<b.nchunks, ST_W * 32, ps == 0 ? ssmem0 : ssmem, st>>>(
             ki, vi, n_vis, dw * ps, nbins, dmask, b.nchunks, b.roffs, bsum, last ? nullptr : b.k2,
             last ? b.s_idx : b.v2, (const float2 *)d_uv, last ? b.s_uv : nullptr);
         ki = b.k2;
         vi = b.v2;
     }
+    if (fork) cudaStreamWaitEvent(st, ctx->ev_join2, 0);
     return check_launch(ctx, "grid plan");
 }
 
