@@ -167,6 +167,33 @@ abs_status abs_estimate_many(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis,
                              int32_t n_trip, const int32_t *d_ijk, double *d_B,
                              int64_t *d_count, double *d_ellbar);
 
+/* One independent estimate of a batch (abs_estimate_batched): its own
+ * configuration, which may differ in grid size, rings and triplets from the
+ * other items', and its own device buffers, with the meaning they have in
+ * abs_estimate.  cfg and its ell_edges are read during the call only. */
+typedef struct abs_item {
+    const abs_config *cfg;
+    int64_t n_vis;
+    const float *d_uv;        /* [n_vis][2] float32 */
+    const float *d_vis;       /* [n_vis][2] float32 */
+    int32_t n_trip;
+    const int32_t *d_ijk;     /* [n_trip][3], NULL = the canonical list */
+    double *d_B;              /* [n_trip] or NULL */
+    int64_t *d_count;         /* [n_trip] or NULL */
+    double *d_ellbar;         /* [n_bins] or NULL */
+} abs_item;
+
+/* Many independent estimates of uneven size in one call, in item order on
+ * the context's stream: the batching form of the ensemble of Sec. 3 (many
+ * realisations or channels with their own baselines, grids and rings).
+ * Every item is validated before any work is queued (ABS_ERR_INVALID_ARG
+ * names nothing queued).  On a non-default stream the whole batch is
+ * captured as one CUDA graph on its second call with the same items (same
+ * configurations and buffer addresses) and replayed from then on; the
+ * buffers' contents may change between calls.  Workspaces are shared by the
+ * items, sized for the largest. */
+abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *items);
+
 /* abs_estimate_many from HOST memory: copies h_uv, h_vis to the device,
  * runs, copies h_B, h_count, h_ellbar back, and waits for completion.
  * h_ijk NULL = canonical list.  Pinned host buffers make the copies

@@ -8,7 +8,7 @@ every call raises.
 
 Names follow the C ABI: ``abs_grid``, ``abs_filter_fft``, ``abs_triple``,
 ``abs_normalise``, ``abs_estimate``, ``abs_estimate_many``,
-``abs_estimate_host``, plus the host helpers ``abs_ring_q``,
+``abs_estimate_batched``, ``abs_estimate_host``, plus the host helpers ``abs_ring_q``,
 ``abs_fft_size``, ``abs_triplets``.
 """
 from __future__ import annotations
@@ -47,6 +47,12 @@ class abs_config(ctypes.Structure):
                 ("n_fft", ctypes.c_int32), ("precision", ctypes.c_int32), ("norm_A", ctypes.c_double)]
 
 
+class abs_item(ctypes.Structure):
+    _fields_ = [("cfg", ctypes.POINTER(abs_config)), ("n_vis", ctypes.c_int64), ("d_uv", ctypes.c_void_p),
+                ("d_vis", ctypes.c_void_p), ("n_trip", ctypes.c_int32), ("d_ijk", ctypes.c_void_p),
+                ("d_B", ctypes.c_void_p), ("d_count", ctypes.c_void_p), ("d_ellbar", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -76,6 +82,7 @@ def load(path: str | None = None):
         "abs_estimate": ([P, C, i64, P, P, i32, P, P, P, P], ctypes.c_int),
         "abs_estimate_many": ([P, C, i64, P, i32, P, i32, P, P, P, P], ctypes.c_int),
         "abs_estimate_host": ([P, C, i64, P, i32, P, i32, P, P, P, P], ctypes.c_int),
+        "abs_estimate_batched": ([P, i32, P], ctypes.c_int),
         "abs_triple_sums_static": ([C, P, i32, P, P, P], ctypes.c_int),
         "abs_profile": ([P, i32], ctypes.c_int),
         "abs_profile_read": ([P, i32, P, P], ctypes.c_int),
@@ -232,6 +239,20 @@ class Context:
         _check(load().abs_estimate_many(self.h, cfg.ref(), uv.shape[0], _ptr(uv), n_real, _ptr(vis), int(n_trip),
                                         _ptr(ijk), _ptr(B), _ptr(counts), _ptr(ellbar)), self.h,
                "abs_estimate_many")
+
+    def abs_estimate_batched(self, items):
+        """items: sequence of (cfg, uv, vis, n_trip, ijk, B, counts, ellbar), torch CUDA tensors or None,
+        one independent estimate each (configurations may differ)."""
+        arr = (abs_item * max(len(items), 1))()
+        for a, (cfg, uv, vis, n_trip, ijk, B, counts, ellbar) in zip(arr, items):
+            a.cfg = ctypes.pointer(cfg._c)
+            a.n_vis = uv.shape[0]
+            a.d_uv, a.d_vis = uv.data_ptr(), vis.data_ptr()
+            a.n_trip = int(n_trip)
+            a.d_ijk, a.d_B, a.d_count, a.d_ellbar = [None if t is None else t.data_ptr()
+                                                     for t in (ijk, B, counts, ellbar)]
+        _check(load().abs_estimate_batched(self.h, len(items), ctypes.cast(arr, ctypes.c_void_p)), self.h,
+               "abs_estimate_batched")
 
     def abs_estimate_host(self, cfg: Config, uv: np.ndarray, vis: np.ndarray, n_trip: int, ijk=None,
                           B=None, counts=None, ellbar=None):

@@ -651,46 +651,47 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
 
 // estimate_many through the context's graph cache (see abs_ctx::graphs).  Not
 // used while the stage profiler runs or on the legacy default stream.
-static abs_status estimate_graphed(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv,
-                                   int32_t n_real, const float *d_vis, int32_t n_trip, const int32_t *d_ijk,
-                                   double *d_B, int64_t *d_count, double *d_ellbar) {
-    auto eager = [&]() {
-        return estimate_many(ctx, s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar);
-    };
+// Runs `eager` through the context's graph cache (see abs_ctx::graphs) under
+// `key`: eagerly the first time, captured and launched the second, replayed
+// after that.  Not used while the stage profiler runs or on the legacy
+// default stream.  The cache entry is looked up again after every eager run,
+// since a workspace regrowth inside it drops the whole cache.
+extern "C++" {
+template <class F>
+static abs_status graphed(abs_ctx *ctx, const std::string &key, const F &eager) {
     if (ctx->profiling || ctx->stream == nullptr) return eager();
-    char key[256];
-    snprintf(key, sizeof key, "%p|%p|%lld|%p|%d|%p|%d|%p|%p|%p|%p", (const void *)&s, (const void *)ctx->stream,
-             (long long)n_vis, (const void *)d_uv, n_real, (const void *)d_vis, n_trip, (const void *)d_ijk,
-             (void *)d_B, (void *)d_count, (void *)d_ellbar);
-    abs_ctx::Graph &g = ctx->graphs[key];
-    if (g.exec) {
-        if (cudaGraphLaunch(g.exec, ctx->stream) == cudaSuccess) return ABS_OK;
-        cudaGetLastError();
-        cudaGraphExecDestroy(g.exec);
-        g.exec = nullptr;
-        g.failed = true;
-        return eager();
+    {
+        abs_ctx::Graph &g = ctx->graphs[key];
+        if (g.exec) {
+            if (cudaGraphLaunch(g.exec, ctx->stream) == cudaSuccess) return ABS_OK;
+            cudaGetLastError();
+            cudaGraphExecDestroy(g.exec);
+            g.exec = nullptr;
+            g.failed = true;
+            return eager();
+        }
+        if (g.failed || g.seen++ == 0) return eager();
     }
-    if (g.failed || g.seen++ == 0) return eager();
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
-        g.failed = true;
+        ctx->graphs[key].failed = true;
         return eager();
     }
     const abs_status st = eager();
     const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
-    if (st != ABS_OK || ce != cudaSuccess || !graph ||
-        cudaGraphInstantiate(&g.exec, graph, 0) != cudaSuccess) {
+    cudaGraphExec_t exec = nullptr;
+    if (st != ABS_OK || ce != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
         // nothing captured ran: run it eagerly (and never capture this key again)
         cudaGetLastError();
         if (graph) cudaGraphDestroy(graph);
-        g.exec = nullptr;
-        g.failed = true;
+        ctx->graphs[key].failed = true;
         ctx->last_error.clear();
         return eager();
     }
     cudaGraphDestroy(graph);
+    abs_ctx::Graph &g = ctx->graphs[key];
+    g.exec = exec;
     if (cudaGraphLaunch(g.exec, ctx->stream) != cudaSuccess) {
         cudaGetLastError();
         cudaGraphExecDestroy(g.exec);
@@ -699,6 +700,19 @@ static abs_status estimate_graphed(abs_ctx *ctx, const Setup &s, int64_t n_vis, 
         return eager();
     }
     return ABS_OK;
+}
+}  // extern "C++"
+
+static abs_status estimate_graphed(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv,
+                                   int32_t n_real, const float *d_vis, int32_t n_trip, const int32_t *d_ijk,
+                                   double *d_B, int64_t *d_count, double *d_ellbar) {
+    char key[256];
+    snprintf(key, sizeof key, "%p|%p|%lld|%p|%d|%p|%d|%p|%p|%p|%p", (const void *)&s, (const void *)ctx->stream,
+             (long long)n_vis, (const void *)d_uv, n_real, (const void *)d_vis, n_trip, (const void *)d_ijk,
+             (void *)d_B, (void *)d_count, (void *)d_ellbar);
+    return graphed(ctx, key, [&]() {
+        return estimate_many(ctx, s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar);
+    });
 }
 
 static abs_status estimate_args(abs_ctx *ctx, const Setup &s, int64_t n_vis, const void *uv,
@@ -731,6 +745,41 @@ abs_status abs_estimate(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis, cons
                         const float *d_vis, int32_t n_trip, const int32_t *d_ijk, double *d_B,
                         int64_t *d_count, double *d_ellbar) {
     return abs_estimate_many(ctx, cfg, n_vis, d_uv, 1, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar);
+}
+
+abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *items) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    if (n_items < 0 || (n_items > 0 && !items)) return fail(ctx, ABS_ERR_INVALID_ARG, "n_items < 0 or items NULL");
+    DeviceGuard g(ctx->device);
+    // validate every item and resolve its setup and triplet list before queuing anything
+    std::vector<const Setup *> setups(n_items);
+    std::vector<const int32_t *> ijks(n_items);
+    std::string key = "batch";
+    for (int32_t i = 0; i < n_items; ++i) {
+        abs_status st;
+        const abs_item &it = items[i];
+        setups[i] = get_setup(ctx, it.cfg, st);
+        if (!setups[i]) return fail(ctx, st, "item " + std::to_string(i) + ": " + ctx->last_error);
+        ijks[i] = it.d_ijk;
+        if (estimate_args(ctx, *setups[i], it.n_vis, it.d_uv, 1, it.d_vis, it.n_trip, ijks[i]) != ABS_OK)
+            return fail(ctx, ABS_ERR_INVALID_ARG, "item " + std::to_string(i) + ": " + ctx->last_error);
+        char k[256];
+        snprintf(k, sizeof k, "|%p|%lld|%p|%p|%d|%p|%p|%p|%p", (const void *)setups[i], (long long)it.n_vis,
+                 (const void *)it.d_uv, (const void *)it.d_vis, it.n_trip, (const void *)ijks[i], (void *)it.d_B,
+                 (void *)it.d_count, (void *)it.d_ellbar);
+        key += k;
+    }
+    char ks[32];
+    snprintf(ks, sizeof ks, "|%p", (const void *)ctx->stream);
+    key += ks;
+    return graphed(ctx, key, [&]() {
+        for (int32_t i = 0; i < n_items; ++i) {
+            const abs_item &it = items[i];
+            ABS_CHECK(estimate_many(ctx, *setups[i], it.n_vis, it.d_uv, 1, it.d_vis, it.n_trip, ijks[i], it.d_B,
+                                    it.d_count, it.d_ellbar));
+        }
+        return ABS_OK;
+    });
 }
 
 abs_status abs_estimate_host(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis, const float *h_uv,

@@ -340,6 +340,86 @@ def test_estimate_many_and_host(ctx):
     assert np.allclose(hE, E.cpu().numpy(), rtol=0, equal_nan=True)
 
 
+@pytest.mark.gpu
+def test_estimate_batched_uneven():
+    """abs_estimate_batched over items of different grid sizes, ring counts
+    and precisions equals abs_estimate item by item, on the eager call, the
+    captured one and replays (which read the buffers' current contents); the
+    small item is also checked against the oracle."""
+    absbuild.build()
+    st = torch.cuda.Stream(dev())
+    c = absmod.Context(0, st)
+    try:
+        rng = np.random.default_rng(11)
+        wls = [synth.workload(0)]
+        for i in range(3):
+            wls.append(synth.batch_item(rng, i))
+        wls[1] = synth.Workload(**{**wls[1].__dict__, "precision": "fp32"})
+        n_vis = [None, 30000, 50000, 20000]
+        items, alt, cfgs = [], [], []
+        with torch.cuda.stream(st):
+            for k, (wl, nv) in enumerate(zip(wls, n_vis)):
+                i0 = synth.make_inputs(0 if k == 0 else 3, 0, wl=wl, n_vis=nv)
+                i1 = synth.make_inputs(0 if k == 0 else 3, 2, wl=wl, n_vis=nv)
+                cfg = absmod.Config.from_workload(i0.wl)
+                nt = len(absmod.abs_triplets(cfg))
+                v0, v1 = to_dev(synth.vis_as_float2(i0.vis)), to_dev(synth.vis_as_float2(i1.vis))
+                vis = v0.clone()
+                outs = (torch.empty(nt, dtype=torch.float64, device=dev()),
+                        torch.empty(nt, dtype=torch.int64, device=dev()),
+                        torch.empty(cfg.n_bins, dtype=torch.float64, device=dev()))
+                cfgs.append(cfg)
+                items.append((cfg, to_dev(i0.uv), vis, nt, None) + outs)
+                alt.append((v0, v1, i0, i1))
+
+            def per_item():
+                res = []
+                for cfg, uv, vis, nt, _, *_o in items:
+                    B = torch.empty(nt, dtype=torch.float64, device=dev())
+                    T = torch.empty(nt, dtype=torch.int64, device=dev())
+                    E = torch.empty(cfg.n_bins, dtype=torch.float64, device=dev())
+                    c.abs_estimate(cfg, uv, vis, nt, None, B, T, E)
+                    res.append((B, T, E))
+                return res
+
+            calls = []
+            for which in (0, 0, 1, 0):          # eager, capture, replay on changed inputs, replay
+                for it, a in zip(items, alt):
+                    it[2].copy_(a[0] if which == 0 else a[1])
+                for it in items:
+                    for o in it[5:]:
+                        o.fill_(-1)
+                c.abs_estimate_batched(items)
+                got = [tuple(o.clone() for o in it[5:]) for it in items]
+                calls.append((got, per_item()))
+        c.sync()
+        for got, ref in calls:
+            for (gB, gT, gE), (rB, rT, rE) in zip(got, ref):
+                gB, rB = gB.cpu().numpy(), rB.cpu().numpy()
+                assert np.array_equal(gT.cpu().numpy(), rT.cpu().numpy())
+                assert np.allclose(gE.cpu().numpy(), rE.cpu().numpy(), rtol=1e-12, atol=0, equal_nan=True)
+                assert np.array_equal(np.isnan(gB), np.isnan(rB))
+                ok = ~np.isnan(rB)
+                assert np.allclose(gB[ok], rB[ok], rtol=1e-9, atol=1e-12 * np.abs(rB[ok]).max())
+        # the small item against the oracle (first and third call: realisations 0 and 2)
+        wl = wls[0]
+        for call, inp in ((calls[0], alt[0][2]), (calls[2], alt[0][3])):
+            est = oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+            B = call[0][0][0].cpu().numpy()
+            assert np.array_equal(call[0][0][1].cpu().numpy(), est.T)
+            ok = ~np.isnan(est.B)
+            big = ok & (np.abs(est.B) >= 1e-3 * np.nanmax(np.abs(est.B)))
+            assert (np.abs(B[big] - est.B[big]) / np.abs(est.B[big])).max() <= SUM_TOL
+        # an invalid item anywhere is reported before any work is queued
+        bad = list(items)
+        bad[2] = (cfgs[2], items[2][1], items[2][2], items[2][3] + 1, None) + tuple(items[2][5:])
+        with pytest.raises(absmod.AbsError):
+            c.abs_estimate_batched(bad)
+        c.abs_estimate_batched([])
+    finally:
+        c.close()
+
+
 def test_counts_deterministic(ctx):
     inp = inputs(1)
     wl = inp.wl
