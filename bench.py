@@ -209,6 +209,26 @@ def workload_config(wl):
             "parallelism": "replicas"}
 
 
+def uneven_batch(n_items, dev):
+    """The first n_items of the seeded 256-item uneven batch, resident on the device."""
+    import torch
+
+    import paper_2412_02246_gb300 as absmod
+    from paper_2412_02246_gb300 import synth
+    rng = np.random.default_rng(2412)
+    items = []
+    for i in range(n_items):
+        inp = synth.make_inputs(3, i, wl=synth.batch_item(rng, i))
+        cfg = absmod.Config.from_workload(inp.wl)
+        nt = len(absmod.abs_triplets(cfg))
+        items.append((cfg, torch.from_numpy(inp.uv).to(dev),
+                      torch.from_numpy(synth.vis_as_float2(inp.vis)).to(dev), nt, None,
+                      torch.empty(nt, dtype=torch.float64, device=dev),
+                      torch.empty(nt, dtype=torch.int64, device=dev),
+                      torch.empty(cfg.n_bins, dtype=torch.float64, device=dev)))
+    return {"items": items}
+
+
 def roofline_for(stage, avg_ms, geo, peaks):
     """Algorithmic work of one launch of `stage` over its average duration.
 
@@ -366,6 +386,20 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     batched = R * reps / (e0.elapsed_time(e1) * 1e-3)
 
+    # uneven batch: independent items of different grid sizes, rings and precisions in one call
+    bi = uneven_batch(args.batch_items, dev)
+    for _ in range(2):                     # eager (setups, workspaces), then graph capture
+        ctx.abs_estimate_batched(bi["items"])
+    ctx.sync()
+    reps_u = max(1, args.steps // 10)
+    e0.record(stream)
+    for _ in range(reps_u):
+        ctx.abs_estimate_batched(bi["items"])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    uneven = len(bi["items"]) * reps_u / (e0.elapsed_time(e1) * 1e-3)
+    del bi
+
     # end to end through the host-buffer entry point (pinned buffers, copies inside)
     huv = torch.from_numpy(inp.uv).pin_memory()
     hvis = torch.from_numpy(synth.vis_as_float2(inp.vis)).pin_memory()
@@ -454,6 +488,11 @@ def run_ours(args):
         "batched": {"value": batched, "unit": UNIT, "realisations_per_call": R,
                     "note": "abs_estimate_many: realisations sharing one baseline set (plan, counts "
                             "and ring tables once per call)"},
+        "batched_uneven": {"value": uneven, "unit": UNIT, "items_per_call": args.batch_items,
+                           "note": "abs_estimate_batched: independent items, grid {256,512,1024}^2, "
+                                   "1e5-1e6 visibilities, 16-48 log l bins, split-BF16 triplets, one CUDA "
+                                   "graph per call; seeded item shapes, the first items_per_call of the "
+                                   "256-item batch"},
         "split_bf16": {"value": args.steps / (tc_ms * 1e-3), "unit": UNIT,
                        "triple_tc_us": round(tc_avg, 2),
                        "triple_tc_tflops_executed": tri_tc["achieved"],
@@ -478,6 +517,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--batch-items", type=int, default=64)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     args = ap.parse_args()
     if args.impl == "reference":
