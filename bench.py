@@ -43,9 +43,9 @@ UNIT = "estimates/s"
 
 # kernels launched per stage-timer entry (the profiler brackets stages); the
 # gridding plan runs the key kernel and, per radix pass of up to 11-bit digits
-# of the uv tile id, a fused scan and a scatter (plus a histogram kernel on
-# passes after the first); the ring lists run cells and finish; the pair
-# counts run once per byte map (filled, annulus)
+# of the (uv tile, cell) key, a scan and a scatter (which counts the next
+# pass's histogram); the ring lists run cells and finish; the pair counts run
+# once per byte map (filled, annulus)
 KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "grid_mask": 1, "ring_lists": 2,
                      "count_items": 1, "count_pairs": 2, "count_gather": 1, "ellbar": 2,
                      "fft_rows": 1, "fft_cols": 1, "triple_fp32": 1, "triple_reduce": 1,
@@ -54,8 +54,8 @@ KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "grid_mask":
 
 def plan_kernels(n_grid, radius):
     tiles = -(-(n_grid - 1 + 2 * radius) // 16)
-    passes = -(-int(tiles * tiles).bit_length() // 11)
-    return 3 * passes + (1 if passes == 1 else 0)   # + the unit cutter beside the one-pass scatter
+    passes = -(-int(tiles * tiles * 256).bit_length() // 11)   # keys: (tile, cell in the tile)
+    return 1 + 2 * passes
 
 
 def load_peaks():

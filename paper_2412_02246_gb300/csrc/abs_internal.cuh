@@ -80,7 +80,6 @@ struct abs_ctx {
     // transforms and triple sums (fork and join by events; both join a graph capture)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;   // the gridding plan's own fork
     int sm_count = 0;
     std::string last_error;
     int32_t *d_err = nullptr;  // latched device error word: 0 ok, else a code below

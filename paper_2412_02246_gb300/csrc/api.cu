@@ -415,9 +415,7 @@ abs_status abs_create(abs_ctx **out, int32_t device, void *cuda_stream) {
         cudaMemset(ctx->d_err, 0, sizeof(int32_t)) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_fork2, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
         return ABS_ERR_OOM;
@@ -441,8 +439,6 @@ abs_status abs_destroy(abs_ctx *ctx) {
         }
         if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
         if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
-        if (ctx->ev_fork2) cudaEventDestroy(ctx->ev_fork2);
-        if (ctx->ev_join2) cudaEventDestroy(ctx->ev_join2);
         for (auto &p : ctx->pending) {
             cudaEventDestroy(p.a);
             cudaEventDestroy(p.b);

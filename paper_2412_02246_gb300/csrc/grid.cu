@@ -74,15 +74,19 @@ __device__ __forceinline__ float wexp(float d, float f_hi, float f_lo, float s_h
 }
 
 // ------------------------------------------------------------------ plan kernels
-// The plan is a stable counting sort of the visibilities by uv tile: LSD radix
-// with digits of up to DMAX bits (one pass while the tile count fits 2^DMAX,
-// two for the largest grids), so every tile's visibilities keep their input
-// order and the gridded sums are reproducible run to run.  A pass is per-chunk
-// digit histograms (digit-major) -> exclusive scan -> order-preserving scatter.
+// The plan is a stable counting sort of the visibilities by (uv tile, cell in
+// the tile): LSD radix with digits of up to DMAX bits (two passes up to about
+// 2040^2 cells, three beyond), so a tile's visibilities are grouped by cell
+// whatever the input order (baseline-major tracks or time-major snapshots)
+// and keep their input order inside a cell: the gridded sums are reproducible
+// run to run.  A pass is per-chunk digit histograms (digit-major) -> exclusive
+// scan -> order-preserving scatter.
 constexpr int RT = 4096;               // visibilities per sort chunk (256 threads x 16)
 constexpr int DMAX = 11;               // widest digit: 2048 bins
+constexpr int CB = 8;                  // key bits of the cell inside its tile (TS x TS = 2^CB)
+static_assert(TS * TS == 1 << CB, "tile cells must fill CB bits");
 
-__device__ __forceinline__ uint32_t tile_key(const GridGeom &G, float2 p, uint32_t key_none) {
+__device__ __forceinline__ uint32_t cell_key(const GridGeom &G, float2 p, uint32_t key_none) {
     if (!(isfinite(p.x) && isfinite(p.y))) return key_none;
     const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
     if (!(fabsf(qx) < 1.0e7f && fabsf(qy) < 1.0e7f)) return key_none;
@@ -90,18 +94,17 @@ __device__ __forceinline__ uint32_t tile_key(const GridGeom &G, float2 p, uint32
     const int cy = (int)floorf(__fadd_rn(qy, 0.5f));
     const int kx = cx + G.off, ky = cy + G.off;
     if (kx < 0 || kx >= G.ks || ky < 0 || ky >= G.ks) return key_none;
-    return (uint32_t)((ky / TS) * G.tt + kx / TS);
+    const uint32_t tile = (uint32_t)((ky / TS) * G.tt + kx / TS);
+    return tile << CB | (uint32_t)((ky % TS) * TS + kx % TS);
 }
 
-// One CTA per chunk: the tile key of every visibility (key_none for non-finite
-// or off-grid positions), per-tile totals and the chunk's histogram of the
-// first digit (nbins bins; digit = key & dmask).  Counts are added once per
-// distinct key in a warp (consecutive visibilities of a baseline usually share
-// a tile).  1024 threads, RT / 1024 visibilities each, all loads in flight.
+// One CTA per chunk: the (tile, cell) key of every visibility (key_none for
+// non-finite or off-grid positions) and the chunk's histogram of the first
+// digit (nbins bins; digit = key & dmask), added once per distinct digit in a
+// warp.  1024 threads, RT / 1024 visibilities each, all loads in flight.
 constexpr int KT = 1024;
 __global__ void __launch_bounds__(KT) k_plan_keys(GridGeom G, int64_t n_vis, const float2 *__restrict__ uv,
-                                                  uint32_t *__restrict__ keys,
-                                                  uint32_t *__restrict__ tile_hist, uint32_t key_none,
+                                                  uint32_t *__restrict__ keys, uint32_t key_none,
                                                   int nbins, uint32_t dmask, int nchunks,
                                                   uint32_t *__restrict__ rhist) {
     __shared__ uint32_t h[1 << DMAX];
@@ -121,127 +124,18 @@ __global__ void __launch_bounds__(KT) k_plan_keys(GridGeom G, int64_t n_vis, con
         const bool on = i < n_vis;
         uint32_t key = 0xffffffffu;
         if (on) {
-            key = tile_key(G, pv[k], key_none);
+            key = cell_key(G, pv[k], key_none);
             keys[i] = key;
         }
-        const unsigned peers = __match_any_sync(FULL, key);
-        if (on && lane == __ffs(peers) - 1) {
-            const uint32_t c = (uint32_t)__popc(peers);
-            if (tile_hist && key != key_none) atomicAdd(&tile_hist[key], c);
-            atomicAdd(&h[key & dmask], c);
-        }
+        const uint32_t dig = on ? key & dmask : 0x10000000u + lane;
+        const unsigned peers = __match_any_sync(FULL, dig);
+        if (on && lane == __ffs(peers) - 1) atomicAdd(&h[dig], (uint32_t)__popc(peers));
     }
     __syncthreads();
     for (int d = threadIdx.x; d < nbins; d += KT) rhist[(int64_t)d * nchunks + blockIdx.x] = h[d];
 }
 
-// Digit histogram of one chunk for the passes after the first.
-__global__ void __launch_bounds__(256) k_radix_hist(const uint32_t *__restrict__ keys, int64_t n, int shift,
-                                                    int dw, int nchunks, uint32_t *__restrict__ rhist) {
-    __shared__ uint32_t h[1 << DMAX];
-    const int nb = 1 << dw, lane = threadIdx.x & 31;   // passes after the first use full dw-bit digits
-    for (int d = threadIdx.x; d < nb; d += 256) h[d] = 0;
-    __syncthreads();
-    const int64_t c0 = (int64_t)blockIdx.x * RT;
-    for (int k = 0; k < RT / 256; ++k) {
-        const int64_t i = c0 + k * 256 + threadIdx.x;
-        const bool on = i < n;
-        const uint32_t d = on ? (keys[i] >> shift) & (uint32_t)(nb - 1) : 0x10000u + lane;
-        const unsigned peers = __match_any_sync(FULL, d);
-        if (on && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < nb; d += 256) rhist[(int64_t)d * nchunks + blockIdx.x] = h[d];
-}
-
-// Order-preserving scatter of one chunk.  Warp w owns the contiguous
-// [w RT/ST_W, (w+1) RT/ST_W) of the chunk: a first sweep counts its digits, a
-// prefix over warps gives every warp its place inside the chunk's run of each
-// digit, and a second sweep places the items (rank among equal digits from
-// __match_any_sync, lower lanes first).  The chunk's start of each digit is
-// the scanned histogram (local scan + its block's offset).  vin == nullptr
-// means the identity (first pass); on the last pass (uv_out != nullptr) the
-// sorted original indices and positions are written instead of keys.
-constexpr int ST_W = 16;                 // warps per scatter CTA
-constexpr int ST_R = RT / ST_W / 32;     // rounds per warp
-__global__ void __launch_bounds__(ST_W * 32) k_radix_scatter(const uint32_t *__restrict__ kin,
-                                                             const uint32_t *__restrict__ vin, int64_t n,
-                                                             int shift, int nbins, uint32_t dmask, int nchunks,
-                                                             const uint32_t *__restrict__ offs,
-                                                             const uint32_t *__restrict__ bsum,
-                                                             uint32_t *__restrict__ kout,
-                                                             uint32_t *__restrict__ vout,
-                                                             const float2 *__restrict__ uv,
-                                                             float2 *__restrict__ uv_out) {
-    extern __shared__ __align__(16) uint8_t ssm[];
-    uint32_t *base = (uint32_t *)ssm;                    // [nbins]
-    uint16_t *wloc = (uint16_t *)(base + nbins);         // [ST_W][nbins]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int d = threadIdx.x; d < nbins; d += blockDim.x) {
-        const int64_t e = (int64_t)d * nchunks + blockIdx.x;
-        base[d] = offs[e] + bsum[e / 4096];
-#pragma unroll
-        for (int w = 0; w < ST_W; ++w) wloc[w * nbins + d] = 0;
-    }
-    __syncthreads();
-    const int64_t w0 = (int64_t)blockIdx.x * RT + warp * (RT / ST_W);
-    uint32_t kv[ST_R];                // the warp's keys, loaded once with all loads in flight
-#pragma unroll
-    for (int k = 0; k < ST_R; ++k) {
-        const int64_t e = w0 + k * 32 + lane;
-        kv[k] = e < n ? kin[e] : 0u;
-    }
-#pragma unroll
-    for (int k = 0; k < ST_R; ++k) {
-        const int64_t e = w0 + k * 32 + lane;
-        const bool on = e < n;
-        const uint32_t d = on ? (kv[k] >> shift) & dmask : 0x10000u + lane;
-        const unsigned peers = __match_any_sync(FULL, d);
-        if (on && lane == __ffs(peers) - 1) wloc[warp * nbins + d] += (uint16_t)__popc(peers);
-        __syncwarp();
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < nbins; d += blockDim.x) {
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < ST_W; ++w) {
-            const uint32_t c = wloc[w * nbins + d];
-            wloc[w * nbins + d] = (uint16_t)run;
-            run += c;
-        }
-    }
-    __syncthreads();
-    uint32_t vv[ST_R];
-#pragma unroll
-    for (int k = 0; k < ST_R; ++k) {
-        const int64_t e = w0 + k * 32 + lane;
-        vv[k] = vin ? (e < n ? vin[e] : 0u) : (uint32_t)e;
-    }
-    float2 pv[ST_R];
-    if (uv_out) {
-#pragma unroll
-        for (int k = 0; k < ST_R; ++k) pv[k] = w0 + k * 32 + lane < n ? uv[vv[k]] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int k = 0; k < ST_R; ++k) {
-        const int64_t e = w0 + k * 32 + lane;
-        const bool on = e < n;
-        const uint32_t key = kv[k];
-        const uint32_t d = on ? (key >> shift) & dmask : 0x10000u + lane;
-        const unsigned peers = __match_any_sync(FULL, d);
-        if (on) {
-            const uint32_t pos = base[d] + wloc[warp * nbins + d] + (uint32_t)__popc(peers & ((1u << lane) - 1u));
-            vout[pos] = vv[k];
-            if (uv_out) uv_out[pos] = pv[k];
-            else kout[pos] = key;
-        }
-        __syncwarp();
-        if (on && lane == __ffs(peers) - 1) wloc[warp * nbins + d] += (uint16_t)__popc(peers);
-        __syncwarp();
-    }
-}
-
-// Block-wide exclusive scan of one value per thread (blockDim.x == 1024).
+// Block-wide exclusive scan of one value per thread (blockDim.x a multiple of 32, at most 1024).
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *sh, uint32_t &total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
@@ -268,65 +162,175 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     return warp_base + x - v;
 }
 
-// Cut every tile's run of sorted visibilities into units of <= UMAX (one
-// block).  Tile totals come from hist, or, when hist is null (a one-pass sort
-// whose digit is the tile), from the scanned digit histogram itself: tile t
-// starts at the exclusive prefix of entry t * nchunks (out + bsum).
-__device__ void cut_units(const uint32_t *__restrict__ hist, const uint32_t *__restrict__ out,
-                          const uint32_t *__restrict__ bsum, int nchunks, int ntiles, int4 *__restrict__ units,
-                          int *__restrict__ n_units, int cap, uint32_t *__restrict__ n_valid_out, uint32_t *sh) {
-    auto tile_start = [&](int t) {
-        const int64_t e = (int64_t)t * nchunks;
-        return __ldcg(out + e) + __ldcg(bsum + e / 4096);
-    };
-    uint32_t carry = 0, base = 0;
-    for (int b = 0; b < ntiles; b += blockDim.x) {
-        const int t = b + threadIdx.x;
-        uint32_t c = 0u;
-        if (t < ntiles) c = hist ? __ldcg(hist + t) : tile_start(t + 1) - tile_start(t);
-        uint32_t ctot;
-        const uint32_t start = base + block_exclusive_scan(c, sh, ctot);   // tile offset in sorted order
-        const uint32_t nu = (c + UMAX - 1) / UMAX;
-        uint32_t total;
-        const uint32_t pre = block_exclusive_scan(nu, sh, total);
-        for (uint32_t k = 0; k < nu; ++k) {
-            const uint32_t u = carry + pre + k;
-            if ((int)u < cap) {
-                const uint32_t s0 = start + k * UMAX;
-                units[u] = make_int4(t, (int)s0, (int)min(start + c, s0 + UMAX), 0);
+// Order-preserving scatter of one chunk (RT items, ST_W warps; warp w owns
+// the contiguous [w RT/ST_W, (w+1) RT/ST_W) of the chunk).  One sweep ranks
+// every item among the warp's earlier items of its digit (__match_any_sync,
+// lower lanes first) and counts the warp's digits; a prefix over (digit,
+// warp) then gives every item its place in the chunk ordered by digit, where
+// it is staged in shared memory, and the staged chunk is written out in that
+// order: each digit's run goes to consecutive addresses, starting where the
+// scanned histogram puts this chunk's part of the digit (local scan + its
+// block's offset).  vin == nullptr means the identity (first pass); on the
+// last pass (uv_out != nullptr) the sorted original indices and positions
+// are written instead of keys.  Before the last pass, the next pass's
+// per-chunk digit histogram (digit at shift + dw of every placed key, chunk
+// = position / RT) is counted into nhist, which must hold zeros: one global
+// add per distinct (digit, chunk) in a warp.
+constexpr int ST_W = 16;                 // warps per scatter CTA
+constexpr int ST_T = ST_W * 32;
+constexpr int ST_R = RT / ST_T;          // items per thread
+constexpr int ST_D = (1 << DMAX) / ST_T; // digits per thread at most
+__host__ __device__ constexpr int scatter_row(int nbins) { return (nbins + 7) & ~7; }
+__host__ __device__ constexpr size_t scatter_smem(int nbins) {
+    return sizeof(uint32_t) * (2 * RT + 2 * (size_t)scatter_row(nbins)) +
+           sizeof(uint16_t) * ST_W * (size_t)scatter_row(nbins);
+}
+__global__ void __launch_bounds__(ST_T) k_radix_scatter(const uint32_t *__restrict__ kin,
+                                                        const uint32_t *__restrict__ vin, int64_t n,
+                                                        int shift, int nbins, uint32_t dmask, int nchunks,
+                                                        const uint32_t *__restrict__ offs,
+                                                        const uint32_t *__restrict__ bsum,
+                                                        uint32_t *__restrict__ kout,
+                                                        uint32_t *__restrict__ vout,
+                                                        const float2 *__restrict__ uv,
+                                                        float2 *__restrict__ uv_out, int dw,
+                                                        uint32_t *__restrict__ nhist) {
+    extern __shared__ __align__(16) uint8_t ssm[];
+    const int row = scatter_row(nbins);                  // nbins rounded up to 8 (16-byte rows)
+    uint32_t *skey = (uint32_t *)ssm;                    // [RT] the chunk ordered by digit
+    uint32_t *sval = skey + RT;                          // [RT]
+    uint32_t *gbase = sval + RT;                         // [row] global position of local 0 for the digit
+    uint32_t *lstart = gbase + row;                      // [row] the digit's first local position
+    uint16_t *wcnt = (uint16_t *)(lstart + row);         // [ST_W][row] per-warp counts, then offsets
+    __shared__ uint32_t sh[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t c0 = (int64_t)blockIdx.x * RT;
+    const int64_t w0 = c0 + warp * (RT / ST_W);
+    const int nloc = (int)min((int64_t)RT, n - c0);
+    // every load in flight at once: keys, values, this thread's digit offsets
+    uint32_t kv[ST_R], vv[ST_R], go[ST_D];
+#pragma unroll
+    for (int k = 0; k < ST_R; ++k) {
+        const int64_t e = w0 + k * 32 + lane;
+        kv[k] = e < n ? kin[e] : 0u;
+        vv[k] = vin ? (e < n ? vin[e] : 0u) : (uint32_t)e;
+    }
+    const int d0 = threadIdx.x * ST_D;   // this thread's digits [d0, d0 + ST_D)
+#pragma unroll
+    for (int j = 0; j < ST_D; ++j) {
+        const int64_t e = (int64_t)(d0 + j) * nchunks + blockIdx.x;
+        go[j] = d0 + j < nbins ? offs[e] + bsum[e / 4096] : 0u;
+    }
+    for (int i = threadIdx.x; i < ST_W * row / 8; i += ST_T) ((uint4 *)wcnt)[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    // rank of every item among its warp's earlier items of the same digit
+    uint32_t rk[ST_R];
+#pragma unroll
+    for (int k = 0; k < ST_R; ++k) {
+        const bool on = w0 + k * 32 + lane < n;
+        const uint32_t d = on ? (kv[k] >> shift) & dmask : 0x10000u + lane;
+        const unsigned peers = __match_any_sync(FULL, d);
+        uint32_t before = 0;
+        if (on) before = wcnt[warp * row + d];
+        rk[k] = before + (uint32_t)__popc(peers & lt);
+        __syncwarp();
+        if (on && lane == __ffs(peers) - 1) wcnt[warp * row + d] = (uint16_t)(before + __popc(peers));
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: offsets of the warps inside its run; the runs' local starts
+    uint32_t cnt[ST_D], mine = 0;
+#pragma unroll
+    for (int j = 0; j < ST_D; ++j) {
+        const int d = d0 + j;
+        uint32_t run = 0;
+        if (d < nbins) {
+#pragma unroll
+            for (int w = 0; w < ST_W; ++w) {
+                const uint32_t c = wcnt[w * row + d];
+                wcnt[w * row + d] = (uint16_t)run;
+                run += c;
             }
         }
-        carry += total;
-        base += ctot;
+        cnt[j] = run;
+        mine += run;
     }
-    if (threadIdx.x == 0) {
-        *n_units = min((int)carry, cap);
-        *n_valid_out = base;
+    uint32_t total;
+    uint32_t ls = block_exclusive_scan(mine, sh, total);
+#pragma unroll
+    for (int j = 0; j < ST_D; ++j) {
+        const int d = d0 + j;
+        if (d < nbins) {
+            lstart[d] = ls;
+            gbase[d] = go[j] - ls;   // global position = gbase[d] + local position
+        }
+        ls += cnt[j];
     }
-}
-
-// One block: the gridding units of a one-pass sort, cut from its scanned tile
-// histogram (run on the side stream beside the scatter).
-__global__ void __launch_bounds__(1024) k_units_scan(const uint32_t *__restrict__ out,
-                                                     const uint32_t *__restrict__ bsum, int nchunks, int ntiles,
-                                                     int4 *__restrict__ units, int *__restrict__ n_units, int cap,
-                                                     uint32_t *__restrict__ n_valid_out) {
-    __shared__ uint32_t sh[32];
-    cut_units(nullptr, out, bsum, nchunks, ntiles, units, n_units, cap, n_valid_out, sh);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ST_R; ++k) {
+        if (w0 + k * 32 + lane < n) {
+            const uint32_t d = (kv[k] >> shift) & dmask;
+            const uint32_t L = lstart[d] + wcnt[warp * row + d] + rk[k];
+            skey[L] = kv[k];
+            sval[L] = vv[k];
+        }
+    }
+    __syncthreads();
+    // write-out in digit order: consecutive threads, consecutive addresses within a run
+    if (uv_out) {
+        float2 pv[ST_R];
+        uint32_t gp[ST_R], vl[ST_R];
+#pragma unroll
+        for (int k = 0; k < ST_R; ++k) {
+            const int L = k * ST_T + threadIdx.x;
+            if (L < nloc) {
+                const uint32_t key = skey[L];
+                vl[k] = sval[L];
+                gp[k] = gbase[(key >> shift) & dmask] + (uint32_t)L;
+                pv[k] = uv[vl[k]];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < ST_R; ++k) {
+            if (k * ST_T + (int)threadIdx.x < nloc) {
+                vout[gp[k]] = vl[k];
+                uv_out[gp[k]] = pv[k];
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < ST_R; ++k) {
+        const int L = k * ST_T + threadIdx.x;
+        const bool on = L < nloc;
+        uint32_t key = 0, pos = 0;
+        if (on) {
+            key = skey[L];
+            pos = gbase[(key >> shift) & dmask] + (uint32_t)L;
+            kout[pos] = key;
+            vout[pos] = sval[L];
+        }
+        if (nhist) {   // (next digit, destination chunk): below 2^11 x 2^20 for valid lanes
+            const uint32_t d2 = (key >> (shift + dw)) & (uint32_t)((1 << dw) - 1);
+            const uint32_t h2 = on ? d2 << 20 | pos / RT : 0x80000000u + lane;
+            const unsigned p2 = __match_any_sync(FULL, h2);
+            if (on && lane == __ffs(p2) - 1)
+                atomicAdd(&nhist[(int64_t)d2 * nchunks + pos / RT], (uint32_t)__popc(p2));
+        }
+    }
 }
 
 // Exclusive scan of len values, 4096 per 1024-thread block: every block scans
 // its part into out and writes its total; the last block to finish (ticket)
 // scans the totals in place into block offsets (so element e's exclusive
-// prefix is out[e] + bsum[e / 4096]), optionally cuts the gridding units (from
-// tile_hist, or with tile_hist null from this scan of a tile-digit histogram
-// with ntiles + 1 bins), and re-arms the ticket.
-__global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ in, int64_t len,
+// prefix is out[e] + bsum[e / 4096]) and re-arms the ticket.  zero_in, when
+// given, is the input array itself, cleared once read (the next radix pass
+// counts into it).
+__global__ void __launch_bounds__(1024) k_scan(const uint32_t *in, int64_t len,
                                                uint32_t *__restrict__ out, uint32_t *__restrict__ bsum,
-                                               unsigned *__restrict__ ticket,
-                                               const uint32_t *__restrict__ tile_hist, int ntiles,
-                                               int4 *__restrict__ units, int *__restrict__ n_units, int cap,
-                                               uint32_t *__restrict__ n_valid_out) {
+                                               unsigned *__restrict__ ticket, uint32_t *zero_in) {
     __shared__ uint32_t sh[32];
     __shared__ bool last;
     const int64_t base = (int64_t)blockIdx.x * 4096 + threadIdx.x * 4;
@@ -336,6 +340,11 @@ __global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ in, 
     for (int k = 0; k < 4; ++k) {
         v[k] = base + k < len ? in[base + k] : 0u;
         s += v[k];
+    }
+    if (zero_in) {   // the same array as in
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (base + k < len) zero_in[base + k] = 0u;
     }
     uint32_t total;
     uint32_t pre = block_exclusive_scan(s, sh, total);
@@ -361,8 +370,6 @@ __global__ void __launch_bounds__(1024) k_scan(const uint32_t *__restrict__ in, 
         if (i < gridDim.x) bsum[i] = carry + p;
         carry += t;
     }
-    if (units) cut_units(tile_hist, out, bsum, ntiles ? (int)(len / (ntiles + 1)) : 0, ntiles, units, n_units, cap,
-                         n_valid_out, sh);
     if (threadIdx.x == 0) *ticket = 0u;
 }
 
@@ -373,17 +380,18 @@ __global__ void k_scan_add(uint32_t *__restrict__ out, int64_t len,
 }
 
 // ------------------------------------------------------------------ accumulation
-// One CTA per work unit (<= UMAX visibilities of one 16x16-cell tile, in input
-// order).  The unit is staged in shared memory and stably sorted by cell
-// (per-warp counts, prefix over (cell, warp), ranked placement), each
-// visibility's 2 (2r+1) one-dimensional weights are formed once, and the
-// unit is cut into tasks: runs of at most CHUNK visibilities that share a
-// cell.  A warp takes a task; lane (dy, q) owns the footprint cells
-// (2q, dy) and (2q+1, dy) of the (2r+1)^2 around the run's cell and sums
-// w = wx wy, w Re V, w Im V over the run with packed FP32x2 arithmetic
-// (plain blocks of GFOLD, as two interleaved chains, folded into Kahan sums;
-// a fixed order), then adds its cells to the FP64 grid.  No shared accumulators: runs never wait on one
-// another, whether the tile is dense (long runs) or sparse.
+// One CTA per work unit: UMAX consecutive visibilities of the sorted order,
+// so a unit's visibilities come grouped by cell (any number of cells and
+// tiles).  Each visibility's 2 (2r+1) one-dimensional weights are formed
+// once and staged in shared memory, and the unit is cut into tasks: runs of
+// one cell, also cut at every CHUNK-th item of the unit, so a task holds at
+// most CHUNK visibilities.  A warp takes a task; lane (dy, q) owns the
+// footprint cells (2q, dy) and (2q+1, dy) of the (2r+1)^2 around the run's
+// cell and sums w = wx wy, w Re V, w Im V over the run with packed FP32x2
+// arithmetic (plain blocks of GFOLD, as two interleaved chains, folded into
+// Kahan sums; a fixed order), then adds its cells to the FP64 grid.  No
+// shared accumulators: runs never wait on one another, whether the cell is
+// dense (long runs) or sparse.
 //
 // Staged record of a visibility (RS floats): wx[0..7] (zero beyond 2r),
 // (wy[d], wy[d]) for d = 0..6, two pad floats, (Re V, Re V, Im V, Im V).
@@ -392,10 +400,9 @@ constexpr int RS = 28;           // floats per staged record
 constexpr int R_WY = 8, R_V = 24;
 constexpr int GFOLD = 16;
 constexpr int CHUNK = 128;       // visibilities per task at most
-constexpr int MAXTASK = UMAX / CHUNK + 256;   // sum over cells of ceil(run / CHUNK)
-static_assert(UMAX == 8 * 64, "the in-unit sort gives each of 8 warps two rounds of 32 items");
-constexpr size_t GRID_SMEM = UMAX * sizeof(float) * RS + sizeof(int2) * MAXTASK + sizeof(uint16_t) * 8 * 256 +
-                             sizeof(uint32_t) * 260 + 2 * UMAX;
+static_assert(UMAX == 8 * 64, "each of 8 warps holds two rounds of 32 items of a unit");
+static_assert(UMAX % CHUNK == 0 && UMAX <= 65535, "task starts are 16-bit unit offsets");
+constexpr size_t GRID_SMEM = UMAX * sizeof(float) * RS + sizeof(uint32_t) * UMAX + sizeof(uint16_t) * (UMAX + 8);
 
 // The double with the value of x, built with integer operations only (GB300's
 // FP64 pipe is narrow: one hardware conversion per flushed value is what kept
@@ -433,30 +440,30 @@ __device__ __forceinline__ void grid_acc(const float *lw, const float *lwy, cons
 }
 
 // Inputs of one unit as thread (warp, lane) sees them: items t = 64 warp +
-// 32 h + lane, h = 0, 1, in input order.
+// 32 h + lane, h = 0, 1, in sorted order.
 struct UnitIn {
-    int4 U;
+    int cnt;
     float2 p[2];
     uint32_t idx[2];
 };
 
-__device__ __forceinline__ void load_unit(UnitIn &in, int u, int nu, const int4 *__restrict__ units,
+__device__ __forceinline__ void load_unit(UnitIn &in, int64_t u, int64_t nu, int64_t n_vis,
                                           const float2 *__restrict__ s_uv, const uint32_t *__restrict__ s_idx,
                                           int warp, int lane) {
     if (u >= nu) return;
-    in.U = units[u];
+    const int64_t b = u * UMAX;
+    in.cnt = n_vis - b < UMAX ? (int)(n_vis - b) : UMAX;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int t = warp * 64 + h * 32 + lane;
-        if (t < in.U.z - in.U.y) {
-            in.p[h] = s_uv[in.U.y + t];
-            in.idx[h] = s_idx[in.U.y + t];
+        if (t < in.cnt) {
+            in.p[h] = s_uv[b + t];
+            in.idx[h] = s_idx[b + t];
         }
     }
 }
 
-__global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict__ units,
-                                             const int *__restrict__ n_units,
+__global__ void __launch_bounds__(GT, 3) k_grid(GridGeom G, int64_t n_vis, uint32_t key_none,
                                              const float2 *__restrict__ s_uv,
                                              const uint32_t *__restrict__ s_idx,
                                              const float2 *__restrict__ vis,
@@ -465,81 +472,72 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
                                              double *__restrict__ acc_w) {
     extern __shared__ __align__(16) uint8_t dsm[];
     float *st = (float *)dsm;                                          // [UMAX][RS] staged records
-    int2 *task = (int2 *)(st + UMAX * RS);                             // [MAXTASK] (first, end)
-    uint16_t *wloc = (uint16_t *)(task + MAXTASK);                     // [8][256] per-warp cell counts
-    uint32_t *cstart = (uint32_t *)(wloc + 8 * 256);                   // [257] first item of each cell
-    uint8_t *in_c = (uint8_t *)(cstart + 260);                         // [UMAX] cell, input order
-    uint8_t *st_c = in_c + UMAX;                                       // [UMAX] cell, sorted order
-    __shared__ uint32_t sh_scan[32];
-    __shared__ int ntask_s;
+    uint32_t *skey = (uint32_t *)(st + UMAX * RS);                     // [UMAX] key of every item
+    uint16_t *tstart = (uint16_t *)(skey + UMAX);                      // [UMAX + 1] first item of each task
+    __shared__ uint32_t wsum_s[8], wvalid_s[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = GT / 32;
     const int r = G.r, fw = 2 * r + 1;
     const bool gauss = G.kernel == ABS_KERNEL_GAUSS;
     // this lane's footprint cells: (2q, dy) and (2q + 1, dy)
     const int dy = lane >> 2, q2 = 2 * (lane & 3);
     const bool on_a = lane < 28 && dy < fw && q2 < fw, on_b = on_a && q2 + 1 < fw;
-    const int nu = *n_units;
+    const int64_t nu = cdiv(n_vis, UMAX);
     UnitIn nxt;
-    load_unit(nxt, blockIdx.x, nu, units, s_uv, s_idx, warp, lane);
-    for (int u = blockIdx.x; u < nu; u += gridDim.x) {
+    load_unit(nxt, blockIdx.x, nu, n_vis, s_uv, s_idx, warp, lane);
+    for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) {
         const UnitIn cur = nxt;
-        const int4 U = cur.U;
-        const int total = U.z - U.y;
-        const int tile = U.x, tx = tile % G.tt, ty = tile / G.tt;
-        float2 v[2];   // this unit's visibilities: gathered now, used at placement
+        const int total = cur.cnt;
+        float2 v[2];   // this unit's visibilities: gathered now, used at staging
 #pragma unroll
         for (int h = 0; h < 2; ++h)
             if (warp * 64 + h * 32 + lane < total) v[h] = vis[cur.idx[h]];
-        load_unit(nxt, u + gridDim.x, nu, units, s_uv, s_idx, warp, lane);   // in flight during this unit
+        load_unit(nxt, u + gridDim.x, nu, n_vis, s_uv, s_idx, warp, lane);   // in flight during this unit
         __syncthreads();   // previous unit done with the staging buffers
-        // cells, and per-warp counts over the warp's 64 items (input order)
-        for (int k = lane; k < 256; k += 32) wloc[warp * 256 + k] = 0;
-        __syncwarp();
+        // keys (the plan's, recomputed from the same positions); invalid items sort last
         float2 q[2];   // u/dU, v/dU of this thread's items
+        bool valid[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int t = warp * 64 + h * 32 + lane;
-            const bool on = t < total;
-            uint32_t c = 0x10000u + lane;
-            if (on) {
+            valid[h] = false;
+            if (t < total) {
+                const uint32_t key = cell_key(G, cur.p[h], key_none);
+                skey[t] = key;
+                valid[h] = key != key_none;
                 q[h] = make_float2(__fdiv_rn(cur.p[h].x, G.du), __fdiv_rn(cur.p[h].y, G.du));
-                const int kx = (int)floorf(__fadd_rn(q[h].x, 0.5f)) + G.off;
-                const int ky = (int)floorf(__fadd_rn(q[h].y, 0.5f)) + G.off;
-                c = (uint32_t)((ky - ty * TS) * TS + (kx - tx * TS));
-                in_c[t] = (uint8_t)c;
-            }
-            const unsigned peers = __match_any_sync(FULL, c);
-            if (on && lane == __ffs(peers) - 1) wloc[warp * 256 + c] += (uint16_t)__popc(peers);
-            __syncwarp();
-        }
-        __syncthreads();
-        {   // cell threadIdx.x: its start, and each warp's place inside its run
-            const int c = threadIdx.x;
-            uint32_t cnt = 0;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) cnt += wloc[w * 256 + c];
-            uint32_t tot;
-            const uint32_t start = block_exclusive_scan(cnt, sh_scan, tot);
-            cstart[c] = start;
-            if (c == 255) cstart[256] = start + cnt;
-            uint32_t run = start;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) {
-                const uint32_t x = wloc[w * 256 + c];
-                wloc[w * 256 + c] = (uint16_t)run;
-                run += x;
             }
         }
         __syncthreads();
-        // placement in cell order: weights, visibility and cell of every item
+        // task starts: a valid item that begins a cell run or sits at a multiple of CHUNK
+        bool ts[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int t = warp * 64 + h * 32 + lane;
-            const bool on = t < total;
-            const uint32_t c = on ? (uint32_t)in_c[t] : 0x10000u + lane;
-            const unsigned peers = __match_any_sync(FULL, c);
-            if (on) {
-                const int pos = (int)wloc[warp * 256 + c] + __popc(peers & ((1u << lane) - 1u));
+            ts[h] = valid[h] && (t % CHUNK == 0 || skey[t] != skey[t - 1]);
+        }
+        const unsigned b0 = __ballot_sync(FULL, ts[0]), b1 = __ballot_sync(FULL, ts[1]);
+        const unsigned nv0 = __ballot_sync(FULL, valid[0]), nv1 = __ballot_sync(FULL, valid[1]);
+        if (lane == 0) {
+            wsum_s[warp] = (uint32_t)(__popc(b0) + __popc(b1));
+            wvalid_s[warp] = (uint32_t)(__popc(nv0) + __popc(nv1));
+        }
+        __syncthreads();
+        uint32_t wbase = 0, ntask = 0, nvalid = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            wbase += w < warp ? wsum_s[w] : 0u;
+            ntask += wsum_s[w];
+            nvalid += wvalid_s[w];
+        }
+        const unsigned lt = (1u << lane) - 1u;
+        if (ts[0]) tstart[wbase + __popc(b0 & lt)] = (uint16_t)(warp * 64 + lane);
+        if (ts[1]) tstart[wbase + __popc(b0) + __popc(b1 & lt)] = (uint16_t)(warp * 64 + 32 + lane);
+        if (threadIdx.x == 0) tstart[ntask] = (uint16_t)nvalid;
+        // staging: weights and visibility of every valid item, in place
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = warp * 64 + h * 32 + lane;
+            if (valid[h]) {
                 const float2 p = cur.p[h], qq = q[h];
                 const float cxf = floorf(__fadd_rn(qq.x, 0.5f)), cyf = floorf(__fadd_rn(qq.y, 0.5f));
                 const float fxh = __fsub_rn(qq.x, cxf), fyh = __fsub_rn(qq.y, cyf);
@@ -547,7 +545,7 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
                 // relative size 2^-24, so one rounding of its own does not matter
                 const float fxl = __fmul_rn(fmaf(-qq.x, G.du, p.x), G.inv_du);
                 const float fyl = __fmul_rn(fmaf(-qq.y, G.du, p.y), G.inv_du);
-                float *rec = st + pos * RS;
+                float *rec = st + t * RS;
                 float wx[8], wy[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
@@ -565,72 +563,41 @@ __global__ void __launch_bounds__(GT) k_grid(GridGeom G, const int4 *__restrict_
                     ((float4 *)(rec + R_WY))[k] = make_float4(wy[2 * k], wy[2 * k], wy[2 * k + 1], wy[2 * k + 1]);
                 ((float2 *)(rec + R_WY))[6] = make_float2(wy[6], wy[6]);
                 ((float4 *)(rec + R_V))[0] = make_float4(v[h].x, v[h].x, v[h].y, v[h].y);
-                st_c[pos] = (uint8_t)c;
             }
-            __syncwarp();
-            if (on && lane == __ffs(peers) - 1) wloc[warp * 256 + c] += (uint16_t)__popc(peers);
-            __syncwarp();
         }
         __syncthreads();
-        if (warp == 0) {   // tasks: every cell's run cut into chunks of <= CHUNK
-            uint32_t nt[8], run = 0;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int c = lane * 8 + k;
-                const uint32_t n = cstart[c + 1] - cstart[c];
-                nt[k] = (n + CHUNK - 1) / CHUNK;
-                run += nt[k];
-            }
-            uint32_t incl = run;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += y;
-            }
-            uint32_t pos = incl - run;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int c = lane * 8 + k;
-                const int j0 = (int)cstart[c], j1 = (int)cstart[c + 1];
-                for (uint32_t qn = 0; qn < nt[k]; ++qn, ++pos) {
-                    const int a = j0 + (int)qn * CHUNK;
-                    task[pos] = make_int2(a, min(j1, a + CHUNK));
-                }
-            }
-            if (lane == 31) ntask_s = (int)incl;
-        }
-        __syncthreads();
-        const int ntask = ntask_s;
-        const int gx0 = tx * TS - G.off, gy0 = ty * TS - G.off;
         if (on_a) {   // lanes without a footprint cell take no part in the sums
-            for (int tk = warp; tk < ntask; tk += nwarps) {
-                const int2 T = task[tk];
+            for (int tk = warp; tk < (int)ntask; tk += nwarps) {
+                const int j_begin = tstart[tk], j_end = tstart[tk + 1];
                 const float2 z = make_float2(0.f, 0.f);
                 float2 sre = z, cre = z, sim = z, cim = z, sw = z, cw = z;
                 const float *lw = st + q2, *lwy = st + R_WY + 2 * dy, *lv = st + R_V;
-                for (int j0 = T.x; j0 < T.y; j0 += GFOLD) {   // plain blocks of GFOLD, folded into Kahan sums
+                for (int j0 = j_begin; j0 < j_end; j0 += GFOLD) {   // plain blocks of GFOLD, folded into Kahan sums
                     float2 bre = z, bim = z, bw = z;
-                    if (j0 + GFOLD <= T.y) {
+                    if (j0 + GFOLD <= j_end) {
                         // a full block: unrolled, two independent chains (even, odd visibilities)
                         float2 bre1 = z, bim1 = z, bw1 = z;
 #pragma unroll
-                        for (int u = 0; u < GFOLD; u += 2) {
-                            grid_acc(lw, lwy, lv, (j0 + u) * RS, bre, bim, bw);
-                            grid_acc(lw, lwy, lv, (j0 + u + 1) * RS, bre1, bim1, bw1);
+                        for (int k = 0; k < GFOLD; k += 2) {
+                            grid_acc(lw, lwy, lv, (j0 + k) * RS, bre, bim, bw);
+                            grid_acc(lw, lwy, lv, (j0 + k + 1) * RS, bre1, bim1, bw1);
                         }
                         bre = __fadd2_rn(bre, bre1);
                         bim = __fadd2_rn(bim, bim1);
                         bw = __fadd2_rn(bw, bw1);
                     } else {
-                        for (int j = j0; j < T.y; ++j) grid_acc(lw, lwy, lv, j * RS, bre, bim, bw);
+                        for (int j = j0; j < j_end; ++j) grid_acc(lw, lwy, lv, j * RS, bre, bim, bw);
                     }
                     kahan_add2(sre, cre, bre);
                     kahan_add2(sim, cim, bim);
                     kahan_add2(sw, cw, bw);
                 }
-                const int cell = st_c[T.x];
-                const int gy = gy0 + (cell >> 4) + dy - r;
-                const int gxa = gx0 + (cell & (TS - 1)) + q2 - r;
+                // the run's cell from its key: tile (kx / TS, ky / TS), cell in the tile
+                const uint32_t key = skey[j_begin];
+                const int tile = (int)(key >> CB), loc = (int)(key & (uint32_t)(TS * TS - 1));
+                const int kx = (tile % G.tt) * TS + (loc & (TS - 1)), ky = (tile / G.tt) * TS + (loc >> 4);
+                const int gy = ky - G.off + dy - r;
+                const int gxa = kx - G.off + q2 - r;
                 if (gy < -G.half || gy > G.half) continue;
                 // the run's sums s - c, rounded once to FP32 (relative 2^-24 of the run)
                 const float2 m1 = make_float2(-1.f, -1.f);
@@ -694,34 +661,27 @@ __global__ void k_grid_mask(int n, const double *__restrict__ acc_w, uint8_t *__
 }
 
 struct PlanBufs {
-    uint32_t *keys, *tile_hist, *k2, *v2, *rhist, *roffs, *n_valid;
+    uint32_t *keys, *k2, *v2, *k3, *v3, *rhist, *roffs;
     uint32_t *s_idx;      // sorted original indices
     float2 *s_uv;         // sorted positions
-    int4 *units;
-    int *n_units;
     int64_t n_vis;
-    int ntiles, units_cap, nchunks;
+    int ntiles, nchunks;
 };
 
 bool plan_bufs(abs_ctx *ctx, const GridGeom &G, int64_t n_vis, PlanBufs &b) {
     b.ntiles = G.tt * G.tt;
     b.n_vis = n_vis;
-    b.units_cap = (int)(b.ntiles + cdiv(n_vis, UMAX) + 1);
     const int64_t nv = n_vis > 0 ? n_vis : 1;
     b.nchunks = (int)cdiv(nv, RT);
     b.keys = (uint32_t *)workspace(ctx, "plan.keys", sizeof(uint32_t) * nv);
-    b.tile_hist = (uint32_t *)workspace(ctx, "plan.tile_hist", sizeof(uint32_t) * b.ntiles);
     b.k2 = (uint32_t *)workspace(ctx, "plan.k2", sizeof(uint32_t) * nv);
     b.v2 = (uint32_t *)workspace(ctx, "plan.v2", sizeof(uint32_t) * nv);
+    b.k3 = b.v3 = nullptr;   // the middle pass of a three-pass sort only
     b.rhist = (uint32_t *)workspace(ctx, "plan.rhist", sizeof(uint32_t) * ((size_t)1 << DMAX) * b.nchunks);
     b.roffs = (uint32_t *)workspace(ctx, "plan.roffs", sizeof(uint32_t) * ((size_t)1 << DMAX) * b.nchunks);
-    b.n_valid = (uint32_t *)workspace(ctx, "plan.n_valid", sizeof(uint32_t));
     b.s_idx = (uint32_t *)workspace(ctx, "plan.s_idx", sizeof(uint32_t) * nv);
     b.s_uv = (float2 *)workspace(ctx, "plan.s_uv", sizeof(float2) * nv);
-    b.units = (int4 *)workspace(ctx, "plan.units", sizeof(int4) * b.units_cap);
-    b.n_units = (int *)workspace(ctx, "plan.n_units", sizeof(int));
-    return b.keys && b.tile_hist && b.k2 && b.v2 && b.rhist && b.roffs && b.n_valid && b.s_idx &&
-           b.s_uv && b.units && b.n_units;
+    return b.keys && b.k2 && b.v2 && b.rhist && b.roffs && b.s_idx && b.s_uv;
 }
 
 }  // namespace
@@ -732,74 +692,61 @@ bool scan_u32(abs_ctx *ctx, const uint32_t *in, int64_t len, uint32_t *out, uint
     if (!ticket) return false;
     const int nblk = (int)cdiv(len, 4096);
     if (nblk == 0) return true;
-    k_scan<<<nblk, 1024, 0, ctx->stream>>>(in, len, out, bsum, ticket, nullptr, 0, nullptr, nullptr, 0, nullptr);
+    k_scan<<<nblk, 1024, 0, ctx->stream>>>(in, len, out, bsum, ticket, nullptr);
     k_scan_add<<<(int)cdiv(len, 256), 256, 0, ctx->stream>>>(out, len, bsum);
     return true;
 }
+
+// The key of an invalid visibility: above every (tile, cell) key.
+static uint32_t plan_key_none(const PlanBufs &b) { return (uint32_t)b.ntiles << CB; }
 
 abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv) {
     const GridGeom G = geom(s);
     PlanBufs b;
     if (!plan_bufs(ctx, G, n_vis, b)) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
-    const uint32_t key_none = (uint32_t)b.ntiles;     // invalid visibilities sort last
+    if ((uint64_t)b.ntiles << CB >= 0x7fffffffull) return fail(ctx, ABS_ERR_UNSUPPORTED, "uv grid too large");
+    if (n_vis == 0) return ABS_OK;   // no visibilities: no units
+    const uint32_t key_none = plan_key_none(b);     // invalid visibilities sort last
     int bits = 1;
     while (((uint64_t)1 << bits) <= (uint64_t)key_none) ++bits;
     const int passes = (bits + DMAX - 1) / DMAX;
-    if (passes > 2) return fail(ctx, ABS_ERR_UNSUPPORTED, "uv tile count beyond two radix passes");
     const int dw = (bits + passes - 1) / passes;
-    // one pass: the digit is the key itself, so exactly ntiles + 1 bins
-    const int nbins0 = passes == 1 ? b.ntiles + 1 : 1 << dw;
-    const int64_t rlen = (int64_t)(1 << dw) * b.nchunks;
+    if (passes == 3) {
+        b.k3 = (uint32_t *)workspace(ctx, "plan.k3", sizeof(uint32_t) * n_vis);
+        b.v3 = (uint32_t *)workspace(ctx, "plan.v3", sizeof(uint32_t) * n_vis);
+        if (!b.k3 || !b.v3) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
+    }
+    // one pass: the digit is the key itself, so exactly key_none + 1 bins
+    const int nbins0 = passes == 1 ? (int)key_none + 1 : 1 << dw;
+    const int64_t rlen = (int64_t)std::max(nbins0, 1 << dw) * b.nchunks;
     uint32_t *bsum = (uint32_t *)workspace(ctx, "plan.bsum", sizeof(uint32_t) * (cdiv(rlen, 4096) + 1));
     unsigned *ticket = (unsigned *)workspace_zeroed(ctx, "scan.ticket", sizeof(unsigned));
     if (!bsum || !ticket) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
     cudaStream_t st = ctx->stream;
     StageTimer timer(ctx, "grid_plan");
-    // one pass: the tile totals are read off the scanned histogram; two: counted by atomics
-    uint32_t *tile_hist = passes == 1 ? nullptr : b.tile_hist;
-    if (tile_hist) cudaMemsetAsync(tile_hist, 0, sizeof(uint32_t) * b.ntiles, st);
-    if (n_vis == 0) {
-        // no visibilities: no units
-        cudaMemsetAsync(b.tile_hist, 0, sizeof(uint32_t) * b.ntiles, st);
-        k_scan<<<1, 1024, 0, st>>>(b.rhist, 0, b.roffs, bsum, ticket, b.tile_hist, b.ntiles, b.units, b.n_units,
-                                   b.units_cap, b.n_valid);
-        return check_launch(ctx, "grid plan");
-    }
-    const size_t ssmem0 = (size_t)nbins0 * (4 + 2 * ST_W), ssmem = (size_t)(1 << dw) * (4 + 2 * ST_W);
+    const size_t ssmem0 = scatter_smem(nbins0), ssmem = scatter_smem(1 << dw);
     cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)std::max(ssmem0, ssmem));
-    k_plan_keys<<<b.nchunks, KT, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, tile_hist, key_none, nbins0,
-                                          passes == 1 ? 0xffffffffu : (uint32_t)((1 << dw) - 1), b.nchunks,
-                                          b.rhist);
-    // stable sort of (tile, index): keys -> (k2, v2) -> (s_idx, s_uv).  Units:
-    // one pass, cut from the scanned histogram by one block on the side stream
-    // while the scatter runs (by the scan's last block while profiling); two
-    // passes, from the tile totals by the last scan's last block
-    const bool fork = passes == 1 && !ctx->profiling && ctx->side;
+    const uint32_t dmask = passes == 1 ? 0xffffffffu : (uint32_t)((1 << dw) - 1);
+    k_plan_keys<<<b.nchunks, KT, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, key_none, nbins0, dmask,
+                                          b.nchunks, b.rhist);
+    // stable sort of (key, index): keys -> (k2, v2) [-> (k3, v3)] -> (s_idx, s_uv).
+    // Every scan clears the histogram it read, and every scatter but the last
+    // counts the next pass's histogram into it.
     const uint32_t *ki = b.keys, *vi = nullptr;
     for (int ps = 0; ps < passes; ++ps) {
         const bool last = ps == passes - 1;
         const int nbins = ps == 0 ? nbins0 : 1 << dw;
-        const uint32_t dmask = passes == 1 ? 0xffffffffu : (uint32_t)((1 << dw) - 1);
-        if (ps > 0) k_radix_hist<<<b.nchunks, 256, 0, st>>>(ki, n_vis, dw * ps, dw, b.nchunks, b.rhist);
         const int64_t len = (int64_t)nbins * b.nchunks;
-        const bool cut = !fork && (passes == 1 || last);
-        k_scan<<<(int)cdiv(len, 4096), 1024, 0, st>>>(b.rhist, len, b.roffs, bsum, ticket, tile_hist, b.ntiles,
-                                                      cut ? b.units : nullptr, b.n_units, b.units_cap, b.n_valid);
-        if (fork) {
-            cudaEventRecord(ctx->ev_fork2, st);
-            cudaStreamWaitEvent(ctx->side, ctx->ev_fork2, 0);
-            k_units_scan<<<1, 1024, 0, ctx->side>>>(b.roffs, bsum, b.nchunks, b.ntiles, b.units, b.n_units,
-                                                    b.units_cap, b.n_valid);
-            cudaEventRecord(ctx->ev_join2, ctx->side);
-        }
-        k_radix_scatter<<<b.nchunks, ST_W * 32, ps == 0 ? ssmem0 : ssmem, st>>>(
-            ki, vi, n_vis, dw * ps, nbins, dmask, b.nchunks, b.roffs, bsum, last ? nullptr : b.k2,
-            last ? b.s_idx : b.v2, (const float2 *)d_uv, last ? b.s_uv : nullptr);
-        ki = b.k2;
-        vi = b.v2;
+        k_scan<<<(int)cdiv(len, 4096), 1024, 0, st>>>(b.rhist, len, b.roffs, bsum, ticket,
+                                                      last ? nullptr : b.rhist);
+        uint32_t *ko = ps % 2 == 0 ? b.k2 : b.k3, *vo = ps % 2 == 0 ? b.v2 : b.v3;
+        k_radix_scatter<<<b.nchunks, ST_T, ps == 0 ? ssmem0 : ssmem, st>>>(
+            ki, vi, n_vis, dw * ps, nbins, dmask, b.nchunks, b.roffs, bsum, last ? nullptr : ko,
+            last ? b.s_idx : vo, (const float2 *)d_uv, last ? b.s_uv : nullptr, dw, last ? nullptr : b.rhist);
+        ki = ko;
+        vi = vo;
     }
-    if (fork) cudaStreamWaitEvent(st, ctx->ev_join2, 0);
     return check_launch(ctx, "grid plan");
 }
 
@@ -823,10 +770,10 @@ abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, c
     }
     if (n_vis > 0) {
         StageTimer timer(ctx, "grid");
-        const int blocks = std::min(b.units_cap, ctx->sm_count * 3);
+        const int blocks = (int)std::min<int64_t>(cdiv(n_vis, UMAX), ctx->sm_count * 3);
         cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRID_SMEM);
-        k_grid<<<blocks, GT, GRID_SMEM, st>>>(G, b.units, b.n_units, b.s_uv, b.s_idx, (const float2 *)d_vis, acc,
-                                           acc + cells, acc + 2 * cells);
+        k_grid<<<blocks, GT, GRID_SMEM, st>>>(G, n_vis, plan_key_none(b), b.s_uv, b.s_idx, (const float2 *)d_vis,
+                                           acc, acc + cells, acc + 2 * cells);
     }
     if (!d_grid && !d_wsum) {   // estimate path: the mask alone, if asked for
         if (d_mask) {
