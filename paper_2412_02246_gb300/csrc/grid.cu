@@ -185,7 +185,7 @@ __host__ __device__ constexpr size_t scatter_smem(int nbins) {
     return sizeof(uint32_t) * (2 * RT + 2 * (size_t)scatter_row(nbins)) +
            sizeof(uint16_t) * ST_W * (size_t)scatter_row(nbins);
 }
-__global__ void __launch_bounds__(ST_T) k_radix_scatter(const uint32_t *__restrict__ kin,
+__global__ void __launch_bounds__(ST_T, 2) k_radix_scatter(const uint32_t *__restrict__ kin,
                                                         const uint32_t *__restrict__ vin, int64_t n,
                                                         int shift, int nbins, uint32_t dmask, int nchunks,
                                                         const uint32_t *__restrict__ offs,
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(ST_T) k_radix_scatter(const uint32_t *__restri
     const int64_t w0 = c0 + warp * (RT / ST_W);
     const int nloc = (int)min((int64_t)RT, n - c0);
     // every load in flight at once: keys, values, this thread's digit offsets
-    uint32_t kv[ST_R], vv[ST_R], go[ST_D];
+    uint32_t kv[ST_R], vv[ST_R];
 #pragma unroll
     for (int k = 0; k < ST_R; ++k) {
         const int64_t e = w0 + k * 32 + lane;
@@ -220,12 +220,13 @@ __global__ void __launch_bounds__(ST_T) k_radix_scatter(const uint32_t *__restri
 #pragma unroll
     for (int j = 0; j < ST_D; ++j) {
         const int64_t e = (int64_t)(d0 + j) * nchunks + blockIdx.x;
-        go[j] = d0 + j < nbins ? offs[e] + bsum[e / 4096] : 0u;
+        if (d0 + j < nbins) gbase[d0 + j] = offs[e] + bsum[e / 4096];
     }
     for (int i = threadIdx.x; i < ST_W * row / 8; i += ST_T) ((uint4 *)wcnt)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     // rank of every item among its warp's earlier items of the same digit
-    uint32_t rk[ST_R];
+    // (below 256: two 16-bit ranks to a register)
+    uint32_t rk[ST_R / 2];
 #pragma unroll
     for (int k = 0; k < ST_R; ++k) {
         const bool on = w0 + k * 32 + lane < n;
@@ -233,7 +234,9 @@ __global__ void __launch_bounds__(ST_T) k_radix_scatter(const uint32_t *__restri
         const unsigned peers = __match_any_sync(FULL, d);
         uint32_t before = 0;
         if (on) before = wcnt[warp * row + d];
-        rk[k] = before + (uint32_t)__popc(peers & lt);
+        const uint32_t rank = before + (uint32_t)__popc(peers & lt);
+        if (k % 2 == 0) rk[k / 2] = rank;
+        else rk[k / 2] |= rank << 16;
         __syncwarp();
         if (on && lane == __ffs(peers) - 1) wcnt[warp * row + d] = (uint16_t)(before + __popc(peers));
         __syncwarp();
@@ -263,7 +266,7 @@ __global__ void __launch_bounds__(ST_T) k_radix_scatter(const uint32_t *__restri
         const int d = d0 + j;
         if (d < nbins) {
             lstart[d] = ls;
-            gbase[d] = go[j] - ls;   // global position = gbase[d] + local position
+            gbase[d] -= ls;   // global position = gbase[d] + local position
         }
         ls += cnt[j];
     }
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(ST_T) k_radix_scatter(const uint32_t *__restri
     for (int k = 0; k < ST_R; ++k) {
         if (w0 + k * 32 + lane < n) {
             const uint32_t d = (kv[k] >> shift) & dmask;
-            const uint32_t L = lstart[d] + wcnt[warp * row + d] + rk[k];
+            const uint32_t L = lstart[d] + wcnt[warp * row + d] + ((rk[k / 2] >> (16 * (k % 2))) & 0xffffu);
             skey[L] = kv[k];
             sval[L] = vv[k];
         }

@@ -9,19 +9,38 @@
 // in FP32 in tensor memory: C = Ah Bh^T + Ah Bl^T + Al Bh^T (the Al Bl^T term
 // is below FP32 resolution of the result).
 //
-// One CTA owns a tile of 128 rows and a range of pixels; per chunk of 64
-// pixels the 8 warps stage the fields in shared memory, form the four BF16
-// operand tiles in the canonical K-major no-swizzle layout (8-row x 16-byte
-// core matrices; K-adjacent core matrices 128 B apart, 8-row groups 256 B
-// apart, one 16-column K slab after the other), and one thread issues the 12
-// MMAs (4 K-steps x 3 products, M = 128, N = rings rounded up to 16, K = 16)
-// and commits them to the chunk buffer's mbarrier.  Two buffers alternate, so
-// forming chunk c+1 overlaps the MMAs of chunk c.  At the end the accumulator
-// is read back with tcgen05.ld and each row writes the partial sums of its
-// triplets; a second kernel adds the pixel ranges in FP64 in a fixed order.
+// Rows are ordered by j (then i) and cut into tiles of 128.  A row (i, j)
+// only meets the rings k in [j, k_max(i, j)] (the triangle condition), so a
+// tile of neighbouring j meets a narrow band of rings: the tile's MMA N is
+// that band rounded up to 16, not every ring.
+//
+// One CTA owns a row tile and a range of pixels, streamed in chunks of 64
+// pixels by three roles through two rings of shared-memory stages, one of
+// field chunks (deep, so loads run well ahead) and one of operand tiles:
+//   loader warp    copies the chunk's fields, all rings x 68 pixels (the
+//                  padded row keeps the producers' reads off one bank), with
+//                  one 2-D TMA tensor copy (zero fill past the last pixel)
+//                  into a field stage, completion counted on f_full,
+//   producer warps form the four BF16 operand tiles (A = D_i D_j and the
+//                  band of B = D_k, hi and lo) in the canonical K-major
+//                  no-swizzle layout (8-row x 16-byte core matrices, K-adjacent
+//                  ones 128 B apart, 8-row groups 256 B apart, one 16-column K
+//                  slab after the other) in an operand stage, arrive on
+//                  ab_full and release the field stage (f_empty),
+//   MMA warp       issues the 12 MMAs of the chunk (4 K-steps x 3 products,
+//                  M = 128, N = band, K = 16) and commits them to ab_empty,
+//                  which frees the operand stage.
+// At the end the accumulator is read back with tcgen05.ld and each row writes
+// the partial sums of its triplets; a second kernel adds the pixel ranges in
+// FP64 in a fixed order.
 //
 // Every mbarrier wait is bounded; on timeout the kernel latches an error,
-// waits (bounded) for its own MMAs, frees its tensor memory and returns.
+// every role leaves its loop, the CTA waits (bounded) for its own copies and
+// MMAs in flight, frees its tensor memory and returns.  Where the fields
+// cannot be described as a TMA tensor (rows not 16-byte aligned), the loader
+// warp copies them with plain loads.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include "abs_internal.cuh"
@@ -31,18 +50,27 @@ namespace {
 
 constexpr int TM = 128;          // rows per tile (MMA M)
 constexpr int KC = 64;           // pixels per chunk (4 MMA K-steps)
-constexpr int NT = 256;          // threads per CTA
-constexpr int FPAD = 4;          // field row padding (floats)
+constexpr int NPW = 16;          // producer warps
+constexpr int KA = TM * (KC / 8) / (NPW * 32);          // A units (row, 8 pixels) per producer thread
+constexpr int KB = 256 * (KC / 8) / (NPW * 32);         // B units per producer thread at most (band <= 256)
+static_assert(KA * NPW * 32 == TM * (KC / 8), "A units split evenly over the producers");
+constexpr int LOADER = NPW, ISSUER = NPW + 1;   // the two control warps
+constexpr int NT = (NPW + 2) * 32;
+constexpr int FS = KC + 4;       // field row in a stage (floats; 272 B, a multiple of 16): the TMA box width
+constexpr int MAX_AB = 3, MAX_F = 8;   // operand and field stages
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
 struct TcGeom {
-    int nb, NP;                  // rings, MMA N (rings rounded up to 16)
+    int nb, NP;                  // rings, largest MMA N (rings rounded up to 16)
     int tmem_cols;               // power of two >= max(32, NP)
     int64_t P;                   // pixels
     int64_t per_split;           // pixels per CTA (multiple of KC)
     int n_trip;
-    int a_bytes, b_bytes;        // one operand tile (hi or lo) in bytes
+    int sf, sa;                  // field and operand stages
+    int f_bytes, ab_bytes;       // one field stage [nb][FS] floats; one operand stage [Ah][Al][Bh][Bl]
+    int a_bytes, b_bytes;        // one operand tile (hi or lo)
+    int tma;                     // fields by TMA tensor copy (else plain loads by the loader warp)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -79,6 +107,19 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  ::"r"(mbar) : "memory");
 }
 
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;\n"
+                 ::"r"(mbar), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -89,21 +130,45 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// Bounded wait for the phase of the given parity; false on timeout, or once
+// another role has given up (abort set).
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const volatile int *abort_flag) {
+    for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+        if (mbar_try(mbar, parity)) return true;
+        if ((it & 255u) == 255u && *abort_flag) return false;
+    }
+    return false;
+}
+
+// Bounded wait for work already in flight (copies, MMAs), whatever the abort flag says.
+__device__ __forceinline__ bool mbar_drain(uint32_t mbar, uint32_t parity) {
     for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
         if (mbar_try(mbar, parity)) return true;
     return false;
 }
 
-__device__ __forceinline__ void store_split8(uint8_t *hi_tile, uint8_t *lo_tile, int off, const float *v) {
-    __align__(16) __nv_bfloat16 h[8], l[8];
+// 2-D tensor copy of the box at (x, y) into shared memory, counted on mbar.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar) : "memory");
+}
+
+// Eight FP32 values (four pairs) as their BF16 hi parts and BF16 residuals,
+// stored as one 16-byte core-matrix row each.
+__device__ __forceinline__ void store_split8(uint8_t *hi_tile, uint8_t *lo_tile, int off, const float2 *v) {
+    uint32_t h[4], l[4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-        h[e] = __float2bfloat16_rn(v[e]);
-        l[e] = __float2bfloat16_rn(v[e] - __bfloat162float(h[e]));
+    for (int e = 0; e < 4; ++e) {
+        const __nv_bfloat162 hb = __float22bfloat162_rn(v[e]);
+        const float2 hf = __bfloat1622float2(hb);
+        const float2 r = __ffma2_rn(hf, make_float2(-1.f, -1.f), v[e]);   // v - hi, exact in FP32
+        const __nv_bfloat162 lb = __float22bfloat162_rn(r);
+        h[e] = *(const uint32_t *)&hb;
+        l[e] = *(const uint32_t *)&lb;
     }
-    *(uint4 *)(hi_tile + off) = *(const uint4 *)h;
-    *(uint4 *)(lo_tile + off) = *(const uint4 *)l;
+    *(uint4 *)(hi_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *(uint4 *)(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
 // Byte offset of (row r, 8-column group g) of a K-major tile with rows8 8-row groups.
@@ -112,25 +177,47 @@ __device__ __forceinline__ int core_off(int r, int g, int rows8) {
     return slab * rows8 * 256 + (r >> 3) * 256 + cb * 128 + (r & 7) * 16;
 }
 
-__global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const float *__restrict__ fields,
+// Eight consecutive field values at f (16-byte aligned), as four pairs.
+__device__ __forceinline__ void ld8(const float *f, float2 *v) {
+    const float4 a = *(const float4 *)f;
+    const float4 b = *(const float4 *)(f + 4);
+    v[0] = make_float2(a.x, a.y);
+    v[1] = make_float2(a.z, a.w);
+    v[2] = make_float2(b.x, b.y);
+    v[3] = make_float2(b.z, b.w);
+}
+
+// Zero the pixels of group g at or past `valid` (the end of the pixel range).
+__device__ __forceinline__ void mask_tail(float2 *v, int g, int valid) {
+    if (g * 8 + 8 <= valid) return;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (g * 8 + 2 * e >= valid) v[e].x = 0.f;
+        if (g * 8 + 2 * e + 1 >= valid) v[e].y = 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_constant__ CUtensorMap fmap,
+                                                     const float *__restrict__ fields,
                                                      const int4 *__restrict__ rows,
+                                                     const int2 *__restrict__ tiles,
                                                      const int *__restrict__ n_rows_p,
                                                      const int32_t *__restrict__ ijk,
                                                      double *__restrict__ partial,
                                                      int32_t *__restrict__ err) {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t f_full[MAX_F], f_empty[MAX_F], ab_full[MAX_AB], ab_empty[MAX_AB];
+    // stages on a 1024-byte boundary (TMA destinations want 128; the launch adds 1 KB of slack)
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ uint32_t tmem_holder;
     __shared__ int rowi[TM], rowj[TM];
-    __shared__ int abort_s;
+    __shared__ volatile int abort_s;
     const int n_rows = *n_rows_p;
     const int r0 = blockIdx.x * TM;
     if (r0 >= n_rows) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // layout: [buf 0: Ah Al Bh Bl][buf 1: Ah Al Bh Bl][fields nb x (KC + FPAD)]
-    const int buf_bytes = 2 * G.a_bytes + 2 * G.b_bytes;
-    float *F = (float *)(smem + 2 * buf_bytes);
-    const int fstride = KC + FPAD;
+    const int2 band = tiles[blockIdx.x];            // (first ring of the band, band width)
+    const int klo = band.x, NB = band.y;
     if (threadIdx.x < TM) {
         const int r = r0 + threadIdx.x;
         int i = -1, j = -1;
@@ -144,11 +231,17 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const float *__re
     }
     if (threadIdx.x == 0) {
         abort_s = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
+        for (int s = 0; s < G.sf; ++s) {
+            mbar_init(smem_u32(&f_full[s]), 1);
+            mbar_init(smem_u32(&f_empty[s]), NPW);
+        }
+        for (int s = 0; s < G.sa; ++s) {
+            mbar_init(smem_u32(&ab_full[s]), NPW);
+            mbar_init(smem_u32(&ab_empty[s]), 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == ISSUER) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
                      ::"r"(smem_u32(&tmem_holder)), "r"(G.tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
@@ -157,161 +250,293 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const float *__re
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_holder;
-    const uint32_t idesc = make_idesc(TM, G.NP);
     const int64_t p_begin = (int64_t)blockIdx.y * G.per_split;
     const int64_t p_end = min(G.P, p_begin + G.per_split);
     const int nchunks = (int)cdiv(p_end - p_begin, KC);
     const int rows8_a = TM / 8, rows8_b = G.NP / 8;
-    uint32_t phase[2] = {0u, 0u};
-    bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
-        const int bsel = c & 1;
-        uint8_t *Ah = smem + bsel * buf_bytes, *Al = Ah + G.a_bytes;
-        uint8_t *Bh = Al + G.a_bytes, *Bl = Bh + G.b_bytes;
-        if (c >= 2) {   // MMAs that read this buffer two chunks ago must be done
-            if (threadIdx.x == 0 && !mbar_wait(smem_u32(&mbar[bsel]), phase[bsel] ^ 1u)) abort_s = 1;
+    uint8_t *fbase = smem, *abase = smem + (size_t)G.sf * G.f_bytes;
+
+    if (warp == LOADER) {
+        // ---------------- loader: a field chunk (every ring) per field stage
+        int issued = 0;
+        for (int c = 0; c < nchunks; ++c) {
+            const int s = c % G.sf, use = c / G.sf;
+            bool ok = true;
+            if (use > 0) {   // the producers are done with chunk c - sf
+                if (lane == 0) ok = mbar_wait(smem_u32(&f_empty[s]), (uint32_t)((use - 1) & 1), &abort_s);
+                ok = __shfl_sync(FULL, ok, 0);
+            }
+            if (!ok) {
+                abort_s = 1;
+                break;
+            }
+            float *F = (float *)(fbase + (size_t)s * G.f_bytes);
+            const int64_t pc = p_begin + (int64_t)c * KC;
+            if (G.tma) {
+                if (lane == 0) {
+                    mbar_arrive_tx(smem_u32(&f_full[s]), (uint32_t)(G.nb * FS * 4));
+                    tma_load_2d(smem_u32(F), &fmap, (int)pc, 0, smem_u32(&f_full[s]));
+                }
+            } else {
+                for (int e = lane; e < G.nb * FS; e += 32) {
+                    const int m = e / FS, px = e - m * FS;
+                    F[e] = pc + px < G.P ? __ldg(&fields[(size_t)m * G.P + pc + px]) : 0.f;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&f_full[s]));
+            }
+            ++issued;
         }
-        __syncthreads();
-        if (abort_s) {
-            ok = false;
-            break;
+        // copies still in flight land before the CTA moves on
+        if (lane == 0 && G.tma)
+            for (int s = 0; s < G.sf && s < issued; ++s) {
+                const int uses = (issued - s + G.sf - 1) / G.sf;
+                if (!mbar_drain(smem_u32(&f_full[s]), (uint32_t)((uses - 1) & 1))) abort_s = 1;
+            }
+    } else if (warp == ISSUER) {
+        // ---------------- MMA issue: one thread
+        if (lane == 0) {
+            const uint32_t idesc = make_idesc(TM, NB);
+            int committed = 0;
+            for (int c = 0; c < nchunks; ++c) {
+                const int s = c % G.sa, use = c / G.sa;
+                if (!mbar_wait(smem_u32(&ab_full[s]), (uint32_t)(use & 1), &abort_s)) {
+                    abort_s = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                uint8_t *Ah = abase + (size_t)s * G.ab_bytes, *Al = Ah + G.a_bytes;
+                uint8_t *Bh = Al + G.a_bytes, *Bl = Bh + G.b_bytes;
+#pragma unroll
+                for (int ks = 0; ks < KC / 16; ++ks) {
+                    const uint64_t ah = make_desc(smem_u32(Ah + ks * rows8_a * 256), 128, 256);
+                    const uint64_t al = make_desc(smem_u32(Al + ks * rows8_a * 256), 128, 256);
+                    const uint64_t bh = make_desc(smem_u32(Bh + ks * rows8_b * 256), 128, 256);
+                    const uint64_t bl = make_desc(smem_u32(Bl + ks * rows8_b * 256), 128, 256);
+                    mma_bf16(tmem, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+                    mma_bf16(tmem, ah, bl, idesc, 1u);
+                    mma_bf16(tmem, al, bh, idesc, 1u);
+                }
+                mma_commit(smem_u32(&ab_empty[s]));
+                ++committed;
+            }
+            // every MMA issued is done before tensor memory is read or freed
+            if (committed > 0) {
+                const int c = committed - 1, s = c % G.sa, use = c / G.sa;
+                if (!mbar_drain(smem_u32(&ab_empty[s]), (uint32_t)(use & 1))) abort_s = 1;
+            }
+            if (committed < nchunks) abort_s = 1;
         }
-        // stage fields of this chunk (zero beyond the last pixel)
-        const int64_t pc = p_begin + (int64_t)c * KC;
-        for (int e = threadIdx.x; e < G.nb * KC; e += NT) {
-            const int m = e / KC, px = e - m * KC;
-            F[m * fstride + px] = pc + px < p_end ? __ldg(&fields[(size_t)m * G.P + pc + px]) : 0.f;
-        }
-        __syncthreads();
-        // A: 128 rows x 64 pixels as 128 x 8 groups of 8; lane -> (row within 8, group)
-        for (int u = threadIdx.x; u < TM * (KC / 8); u += NT) {
-            const int rg = u >> 6, rem = u & 63;        // 8-row group, (group, row) inside
+    } else {
+        // ---------------- producers: the operand tiles of a chunk.  A thread's
+        // units are the same in every chunk: field offsets and tile offsets
+        // are worked out once.  A: unit u = (8-row group, 8 rows x 8 groups);
+        // a warp's 32 units are 8 rows x 4 groups (conflict-free 16-byte stores)
+        const int p = threadIdx.x;
+        int a_fi[KA], a_fj[KA], a_so[KA], a_g[KA];
+#pragma unroll
+        for (int k = 0; k < KA; ++k) {
+            const int u = p + k * NPW * 32;
+            const int rg = u >> 6, rem = u & 63;
             const int g = rem >> 3, r = rg * 8 + (rem & 7);
             const int i = rowi[r], j = rowj[r];
-            float v[8];
-            if (i >= 0) {
-                const float *fi = F + i * fstride + g * 8, *fj = F + j * fstride + g * 8;
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = fi[e] * fj[e];
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = 0.f;
-            }
-            store_split8(Ah, Al, core_off(r, g, rows8_a), v);
+            a_fi[k] = i >= 0 ? i * FS + g * 8 : -1;
+            a_fj[k] = i >= 0 ? j * FS + g * 8 : -1;
+            a_so[k] = core_off(r, g, rows8_a);
+            a_g[k] = g;
         }
-        // B: NP rings x 64 pixels
-        for (int u = threadIdx.x; u < G.NP * (KC / 8); u += NT) {
+        int b_fk[KB], b_so[KB], b_g[KB];
+#pragma unroll
+        for (int k = 0; k < KB; ++k) {
+            const int u = p + k * NPW * 32;
             const int rg = u >> 6, rem = u & 63;
-            const int g = rem >> 3, k = rg * 8 + (rem & 7);
-            float v[8];
-            if (k < G.nb) {
-                const float *fk = F + k * fstride + g * 8;
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = fk[e];
-            } else {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) v[e] = 0.f;
-            }
-            store_split8(Bh, Bl, core_off(k, g, rows8_b), v);
+            const int g = rem >> 3, kk = rg * 8 + (rem & 7);
+            b_fk[k] = u < NB * (KC / 8) ? (klo + kk < G.nb ? (klo + kk) * FS + g * 8 : -1) : -2;
+            b_so[k] = core_off(kk, g, rows8_b);
+            b_g[k] = g;
         }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-#pragma unroll
-            for (int ks = 0; ks < KC / 16; ++ks) {
-                const uint64_t ah = make_desc(smem_u32(Ah + ks * rows8_a * 256), 128, 256);
-                const uint64_t al = make_desc(smem_u32(Al + ks * rows8_a * 256), 128, 256);
-                const uint64_t bh = make_desc(smem_u32(Bh + ks * rows8_b * 256), 128, 256);
-                const uint64_t bl = make_desc(smem_u32(Bl + ks * rows8_b * 256), 128, 256);
-                mma_bf16(tmem, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-                mma_bf16(tmem, ah, bl, idesc, 1u);
-                mma_bf16(tmem, al, bh, idesc, 1u);
-            }
-            mma_commit(smem_u32(&mbar[bsel]));
-        }
-        phase[bsel] ^= 1u;
-    }
-    // wait for the last commit of each used buffer
-    if (threadIdx.x == 0) {
-        for (int b = 0; b < 2; ++b) {
-            const int uses = nchunks > b ? (nchunks - b + 1) / 2 : 0;
-            if (uses > 0 && !mbar_wait(smem_u32(&mbar[b]), (uint32_t)((uses - 1) & 1))) {
+        for (int c = 0; c < nchunks; ++c) {
+            const int sf = c % G.sf, uf = c / G.sf;
+            const int sa = c % G.sa, ua = c / G.sa;
+            bool ok = mbar_wait(smem_u32(&f_full[sf]), (uint32_t)(uf & 1), &abort_s);
+            if (ok && ua > 0) ok = mbar_wait(smem_u32(&ab_empty[sa]), (uint32_t)((ua - 1) & 1), &abort_s);
+            if (!ok) {
                 abort_s = 1;
+                break;
+            }
+            const float *F = (const float *)(fbase + (size_t)sf * G.f_bytes);
+            uint8_t *Ah = abase + (size_t)sa * G.ab_bytes, *Al = Ah + G.a_bytes;
+            uint8_t *Bh = Al + G.a_bytes, *Bl = Bh + G.b_bytes;
+            const int64_t pc = p_begin + (int64_t)c * KC;
+            const int valid = (int)min((int64_t)KC, p_end - pc);
+#pragma unroll
+            for (int k = 0; k < KA; ++k) {
+                float2 v[4];
+                if (a_fi[k] >= 0) {
+                    float2 x[4], y[4];
+                    ld8(F + a_fi[k], x);
+                    ld8(F + a_fj[k], y);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v[e] = __fmul2_rn(x[e], y[e]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
+                }
+                if (valid < KC) mask_tail(v, a_g[k], valid);
+                store_split8(Ah, Al, a_so[k], v);
+            }
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                if (b_fk[k] == -2) continue;   // past the band
+                float2 v[4];
+                if (b_fk[k] >= 0) {
+                    ld8(F + b_fk[k], v);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
+                }
+                if (valid < KC) mask_tail(v, b_g[k], valid);
+                store_split8(Bh, Bl, b_so[k], v);
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(smem_u32(&ab_full[sa]));
+                mbar_arrive(smem_u32(&f_empty[sf]));
             }
         }
     }
+    // every role is done: MMAs and copies have landed (or the CTA gave up)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (!ok || abort_s) {
+    if (abort_s) {
         if (threadIdx.x == 0) atomicCAS(err, 0, DERR_TIMEOUT);
     } else {
-        // epilogue: TMEM -> shared [128][NP] (reuse buffer 0) -> per-triplet partials
+        // epilogue: TMEM -> shared [128][NB + 1] (over the stages) -> per-triplet partials
         float *D = (float *)smem;
-        const int lane_base = (warp & 3) * 32;
-        const int r = lane_base + lane;
-        for (int col = (warp >> 2) * 16; col < G.NP; col += 32) {
-            uint32_t v[16];
-            const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)col;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-                "%11, %12, %13, %14, %15}, [%16];\n"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                  "=r"(v[14]), "=r"(v[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        if (warp < 4) {   // warp w reads tensor-memory lanes 32 w .. 32 w + 31
+            const int lane_base = warp * 32;
+            const int r = lane_base + lane;
+            for (int col = 0; col < NB; col += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)col;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+                    "%11, %12, %13, %14, %15}, [%16];\n"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-            for (int e = 0; e < 16; ++e) D[r * (G.NP + 1) + col + e] = __uint_as_float(v[e]);
+                for (int e = 0; e < 16; ++e) D[r * (NB + 1) + col + e] = __uint_as_float(v[e]);
+            }
         }
         __syncthreads();
         if (threadIdx.x < TM && r0 + (int)threadIdx.x < n_rows) {
             const int4 R = rows[r0 + threadIdx.x];
             for (int t = R.z; t < R.w; ++t) {
-                const int k = ijk[3 * t + 2];
-                if (k >= 0 && k < G.nb)
-                    partial[(size_t)blockIdx.y * G.n_trip + t] = (double)D[threadIdx.x * (G.NP + 1) + k];
+                const int kk = ijk[3 * t + 2] - klo;
+                if (kk >= 0 && kk < NB)
+                    partial[(size_t)blockIdx.y * G.n_trip + t] = (double)D[threadIdx.x * (NB + 1) + kk];
             }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    if (warp == 0)
+    if (warp == ISSUER)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(G.tmem_cols));
 }
 
-// Row table: one entry (i, j, first triplet, end) per run of equal (i, j).
-__global__ void __launch_bounds__(1024) k_rows(int n_trip, const int32_t *__restrict__ ijk,
-                                               int4 *__restrict__ rows, int *__restrict__ n_rows) {
+// Row table of a (canonical, sorted) triplet list: one entry (i, j, first
+// triplet, end) per run of equal (i, j), ordered by (j, i); then per tile of
+// TM rows its band of rings (first k, width rounded up to 16, at most np).
+// One block of 1024 threads; dynamic shared memory: nb x ceil(nb / 32) words
+// of presence bits, (j, i) of every row.
+__global__ void __launch_bounds__(1024) k_rows(int n_trip, int nb, int np, const int32_t *__restrict__ ijk,
+                                               int4 *__restrict__ rows, int *__restrict__ n_rows,
+                                               int2 *__restrict__ tiles) {
+    extern __shared__ uint32_t presence[];
+    __shared__ int jstart[ABS_MAX_BINS + 1];
     __shared__ int wsum[32];
-    __shared__ int carry_s;
-    if (threadIdx.x == 0) carry_s = 0;
-    __syncthreads();
+    __shared__ int nr_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int b = 0; b < n_trip; b += blockDim.x) {
-        const int t = b + threadIdx.x;
-        bool start = false;
-        if (t < n_trip)
-            start = t == 0 || ijk[3 * t] != ijk[3 * t - 3] || ijk[3 * t + 1] != ijk[3 * t - 2];
-        const unsigned bal = __ballot_sync(FULL, start);
-        if (lane == 0) wsum[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, tot = 0;
-        for (int w = 0; w < 32; ++w) {
-            if (w < warp) before += wsum[w];
-            tot += wsum[w];
-        }
-        if (start) {
-            const int pos = carry_s + before + __popc(bal & ((1u << lane) - 1u));
-            int e = t + 1;
-            while (e < n_trip && ijk[3 * e] == ijk[3 * t] && ijk[3 * e + 1] == ijk[3 * t + 1]) ++e;
-            rows[pos] = make_int4(ijk[3 * t], ijk[3 * t + 1], t, e);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) carry_s += tot;
-        __syncthreads();
+    const int words = (nb + 31) / 32;
+    auto row_start = [&](int t, int &i, int &j) {
+        i = ijk[3 * t];
+        j = ijk[3 * t + 1];
+        const bool start = t == 0 || i != ijk[3 * t - 3] || j != ijk[3 * t - 2];
+        return start && i >= 0 && i <= j && j < nb;   // a checked list has nothing else
+    };
+    for (int e = threadIdx.x; e < nb * words; e += blockDim.x) presence[e] = 0u;
+    for (int e = threadIdx.x; e <= nb; e += blockDim.x) jstart[e] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_trip; t += blockDim.x) {
+        int i, j;
+        if (row_start(t, i, j)) atomicOr(&presence[j * words + (i >> 5)], 1u << (i & 31));
     }
-    if (threadIdx.x == 0) *n_rows = carry_s;
+    __syncthreads();
+    // rows per j (distinct (i, j) pairs), exclusive prefix over j (nb <= 1024: one pass)
+    int cnt = 0;
+    if (threadIdx.x < nb)
+        for (int w = 0; w < words; ++w) cnt += __popc(presence[threadIdx.x * words + w]);
+    int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < 32; ++w) {
+        if (w < warp) before += wsum[w];
+        total += wsum[w];
+    }
+    if (threadIdx.x < nb) jstart[threadIdx.x] = before + x - cnt;
+    if (threadIdx.x == 0) {
+        nr_s = total;
+        *n_rows = total;
+    }
+    __syncthreads();
+    // every row at (rows of smaller j) + (rows of its j with smaller i)
+    for (int t = threadIdx.x; t < n_trip; t += blockDim.x) {
+        int i, j;
+        if (row_start(t, i, j)) {
+            int below = 0;
+            for (int w = 0; w < (i >> 5); ++w) below += __popc(presence[j * words + w]);
+            below += __popc(presence[j * words + (i >> 5)] & ((1u << (i & 31)) - 1u));
+            int e = t + 1;
+            while (e < n_trip && ijk[3 * e] == i && ijk[3 * e + 1] == j) ++e;
+            rows[jstart[j] + below] = make_int4(i, j, t, e);
+        }
+    }
+    __syncthreads();
+    // bands: one warp per tile
+    const int nr = nr_s;
+    const int ntiles = (nr + TM - 1) / TM;
+    for (int tl = warp; tl < ntiles; tl += blockDim.x / 32) {
+        int lo = 1 << 30, hi = -1;
+        for (int r = tl * TM + lane; r < min(nr, tl * TM + TM); r += 32) {
+            const int4 R = rows[r];
+            lo = min(lo, ijk[3 * R.z + 2]);
+            hi = max(hi, ijk[3 * (R.w - 1) + 2]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(FULL, lo, o));
+            hi = max(hi, __shfl_xor_sync(FULL, hi, o));
+        }
+        if (lane == 0) {
+            lo = max(0, min(lo, nb - 1));
+            int w = ((max(hi - lo + 1, 1) + 15) / 16) * 16;
+            if (w > np) {   // only for a list that fails its check; stay inside the operand tile
+                w = np;
+                lo = 0;
+            }
+            tiles[tl] = make_int2(lo, w);
+        }
+    }
 }
 
 // S[t] = inv_p * sum over splits of partial[split][t]: 32 triplets per block,
@@ -336,6 +561,23 @@ __global__ void __launch_bounds__(256) k_tc_reduce(int n_trip, int nsplit, doubl
 
 }  // namespace
 
+// cuTensorMapEncodeTiled from the driver, looked up once (no link against libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
 abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields, int32_t n_trip,
                             const int32_t *d_ijk, double *d_sum) {
     if (n_trip == 0) return ABS_OK;
@@ -349,7 +591,32 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
     G.n_trip = n_trip;
     G.a_bytes = TM * KC * 2;
     G.b_bytes = G.NP * KC * 2;
-    const int max_rows = std::min<int64_t>(n_trip, (int64_t)s.nb * (s.nb + 1) / 2);
+    G.f_bytes = (int)(cdiv((int64_t)s.nb * FS * 4, 1024) * 1024);
+    G.ab_bytes = (int)(cdiv(2 * G.a_bytes + 2 * G.b_bytes, 1024) * 1024);
+    // stages: three operand stages if the field ring still gets two, then as many field stages as fit
+    const int64_t budget = 215 * 1024;   // dynamic shared memory, below the 227 KB per CTA with the static part
+    G.sa = MAX_AB;
+    while (G.sa > 2 && budget - (int64_t)G.sa * G.ab_bytes < 2 * (int64_t)G.f_bytes) --G.sa;
+    G.sf = (int)std::min<int64_t>(MAX_F, (budget - (int64_t)G.sa * G.ab_bytes) / G.f_bytes);
+    if (G.sf < 2) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 stages do not fit shared memory");
+    const size_t smem =
+        1024 + std::max((size_t)G.sf * G.f_bytes + (size_t)G.sa * G.ab_bytes, (size_t)TM * (G.NP + 1) * 4);
+    // the field chunk as one TMA box (FS pixels x every ring) of the [nb][P] FP32 array; the
+    // row pitch P x 4 bytes and the array must be 16-byte aligned, else the loader warp copies
+    CUtensorMap fmap;
+    memset(&fmap, 0, sizeof fmap);
+    G.tma = 0;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (encode && G.P % 4 == 0 && ((uintptr_t)d_fields & 15) == 0) {
+        const cuuint64_t dims[2] = {(cuuint64_t)G.P, (cuuint64_t)s.nb};
+        const cuuint64_t strides[1] = {(cuuint64_t)G.P * 4};
+        const cuuint32_t box[2] = {(cuuint32_t)FS, (cuuint32_t)s.nb};
+        const cuuint32_t estr[2] = {1, 1};
+        G.tma = encode(&fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)d_fields, dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    const int max_rows = (int)std::min<int64_t>(n_trip, (int64_t)s.nb * (s.nb + 1) / 2);
     const int tiles = (int)cdiv(max_rows, TM);
     // pixel ranges: enough CTAs for about one wave, at most 4096 pixels each
     // (bounds the FP32 accumulation length inside the tensor core)
@@ -358,23 +625,21 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
     G.per_split = per;
     const int64_t nsplit = cdiv(G.P, per);
     int4 *rows = (int4 *)workspace(ctx, "tc.rows", sizeof(int4) * std::max(max_rows, 1));
+    int2 *tl = (int2 *)workspace(ctx, "tc.tiles", sizeof(int2) * std::max(tiles, 1));
     int *n_rows = (int *)workspace(ctx, "tc.n_rows", sizeof(int));
     double *partial = (double *)workspace(ctx, "tc.partial", sizeof(double) * nsplit * n_trip);
-    if (!rows || !n_rows || !partial) return fail(ctx, ABS_ERR_OOM, "split-BF16 workspace");
+    if (!rows || !tl || !n_rows || !partial) return fail(ctx, ABS_ERR_OOM, "split-BF16 workspace");
     cudaStream_t st = ctx->stream;
-    const size_t buf = 2 * (size_t)G.a_bytes + 2 * (size_t)G.b_bytes;
-    const size_t smem = std::max(2 * buf + (size_t)G.nb * (KC + FPAD) * 4, (size_t)TM * (G.NP + 1) * 4);
-    if (smem > 220 * 1024) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 tile does not fit shared memory");
     cudaFuncSetAttribute(k_triple_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     {
         StageTimer timer(ctx, "tc_rows");
-        cudaMemsetAsync(partial, 0, sizeof(double) * nsplit * n_trip, st);
-        k_rows<<<1, 1024, 0, st>>>(n_trip, d_ijk, rows, n_rows);
+        const size_t psmem = sizeof(uint32_t) * (size_t)s.nb * ((s.nb + 31) / 32);
+        k_rows<<<1, 1024, psmem, st>>>(n_trip, s.nb, G.NP, d_ijk, rows, n_rows, tl);
     }
     {
         StageTimer timer(ctx, "triple_tc");
-        k_triple_tc<<<dim3(tiles, (unsigned)nsplit), NT, smem, st>>>(G, d_fields, rows, n_rows, d_ijk, partial,
-                                                                    ctx->d_err);
+        k_triple_tc<<<dim3(tiles, (unsigned)nsplit), NT, smem, st>>>(G, fmap, d_fields, rows, tl, n_rows, d_ijk,
+                                                                    partial, ctx->d_err);
     }
     {
         StageTimer timer(ctx, "triple_reduce");
