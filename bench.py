@@ -72,8 +72,8 @@ def load_peaks():
 # source file the kernel was built from when it was captured.  A kernel whose
 # source has changed since then reports null.
 MEASURED_TRAFFIC = {
-    "grid": {"bytes": 20375296, "source": "paper_2412_02246_gb300/csrc/grid.cu",
-              "sha256": "ea627f46557ef2c4876acaa256914dd6e05f4faaa58b13af19352d5aece76b7f",
+    "grid": {"bytes": 20331008, "source": "paper_2412_02246_gb300/csrc/grid.cu",
+              "sha256": "2c7ea0823a5637a181d2492bdb68744b705870c3bf80379f0aed717d9bafbe48",
               "profile": "profiles/k_grid_mwa975k.md"},
     "fft_rows": {"bytes": 726528, "source": "paper_2412_02246_gb300/csrc/fft.cu",
                   "sha256": "758edcce293b2d61271b37c5017ca5b6b45c22eb36d1378556ef5c9108a66ef8",
@@ -84,6 +84,9 @@ MEASURED_TRAFFIC = {
     "triple_fp32": {"bytes": 6663680, "source": "paper_2412_02246_gb300/csrc/triple.cu",
                      "sha256": "c6b500d5208e4ecb0e37a44871930b539e7b037c5de0dcc9ff5505ce53cf4bbd",
                      "profile": "profiles/k_triple_fp32_mwa975k.md"},
+    "triple_tc": {"bytes": 6689536, "source": "paper_2412_02246_gb300/csrc/triple_tc.cu",
+                   "sha256": "7d57d71e183ee0da44813b238b3a13fa857abb334a26179ee136e96a5e32a12a",
+                   "profile": "profiles/k_triple_tc_mwa975k.md"},
 }
 
 
@@ -235,7 +238,8 @@ def roofline_for(stage, avg_ms, geo, peaks):
     grid:        FP32 lane-ops, 4 per (visibility, footprint cell): w = wx wy, two FMAs, one add
     count_pairs: integer pair visits x 2 lane-ops (index add, ring compare)
     triple_fp32: 2 flops per (triplet, pixel)
-    triple_tc:   executed BF16 tensor flops, 2 M N K x 3 products (M, N padded tiles)
+    triple_tc:   executed BF16 tensor flops: per 128-row tile 2 M N K with M = 128, N = 3 x its ring
+                 band (the stacked [Bh; Bl] MMA and the Al Bh MMA), K = pixels
     fft_rows/cols, others: algorithmic bytes (reads + writes of the data the kernel must move)
     """
     s = avg_ms * 1e-3
@@ -251,7 +255,7 @@ def roofline_for(stage, avg_ms, geo, peaks):
         fl = 2.0 * geo["n_trip"] * geo["P"]
         out = {"bound": "alu", "achieved": fl / s / 1e12, "peak": 2 * lane_ops / 1e12, "unit": "TFLOP/s"}
     elif stage == "triple_tc":
-        fl = 2.0 * geo["tc_rows"] * geo["tc_np"] * geo["P"] * 3
+        fl = 2.0 * 128 * 3 * geo["tc_band_sum"] * geo["P"]
         out = {"bound": "tensor", "achieved": fl / s / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s"}
     else:
         byts = geo["bytes"].get(stage)
@@ -281,6 +285,18 @@ def workload_geometry(m, cfg, ctx, uv, vis, ijk, N, wl, dev, torch):
     c = np.array([int(((mask > 0) & (r2 >= q[b]) & (r2 < q[b + 1])).sum()) for b in range(cfg.n_bins)])
     rows = sorted({(int(i), int(j)) for i, j, _ in ijk})
     visits = sum((c[i] // 2) * c[j] for i, j in rows)
+    # the split-BF16 kernel's row tiles: rows by (j, i), 128 a tile, each with its band of k rounded to 16
+    kr = {}
+    for i, j, kk in ijk:
+        lo, hi = kr.get((int(i), int(j)), (1 << 30, -1))
+        kr[(int(i), int(j))] = (min(lo, int(kk)), max(hi, int(kk)))
+    by_j = sorted(kr, key=lambda ij: (ij[1], ij[0]))
+    band_sum = 0
+    for t in range(0, len(by_j), 128):
+        tile = by_j[t:t + 128]
+        lo = min(kr[r][0] for r in tile)
+        hi = max(kr[r][1] for r in tile)
+        band_sum += -(-(hi - lo + 1) // 16) * 16
     nb = cfg.n_bins
     npairs = (nb + 1) // 2
     R = int(np.floor(np.sqrt(float(q[-1] - 1))))
@@ -289,7 +305,7 @@ def workload_geometry(m, cfg, ctx, uv, vis, ijk, N, wl, dev, torch):
     fft_cols_bytes = npairs * (2 * R + 1) * N * 16 + nb * P * 4
     return {"pair_visits": int(visits), "n_trip": len(ijk), "P": P, "n_vis": len(uv),
             "footprint": (2 * cfg.radius_cells + 1) ** 2,
-            "tc_rows": -(-len(rows) // 128) * 128, "tc_np": -(-max(nb, 16) // 16) * 16,
+            "tc_band_sum": band_sum,
             "bytes": {"fft_rows": fft_rows_bytes, "fft_cols": fft_cols_bytes,
                       "ring_lists": n * n * 2}}
 
@@ -387,18 +403,20 @@ def run_ours(args):
     batched = R * reps / (e0.elapsed_time(e1) * 1e-3)
 
     # uneven batch: independent items of different grid sizes, rings and precisions in one call
-    bi = uneven_batch(args.batch_items, dev)
-    for _ in range(2):                     # eager (setups, workspaces), then graph capture
-        ctx.abs_estimate_batched(bi["items"])
-    ctx.sync()
-    reps_u = max(1, args.steps // 10)
-    e0.record(stream)
-    for _ in range(reps_u):
-        ctx.abs_estimate_batched(bi["items"])
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    uneven = len(bi["items"]) * reps_u / (e0.elapsed_time(e1) * 1e-3)
-    del bi
+    uneven = None
+    if args.batch_items > 0:
+        bi = uneven_batch(args.batch_items, dev)
+        for _ in range(2):                     # eager (setups, workspaces), then graph capture
+            ctx.abs_estimate_batched(bi["items"])
+        ctx.sync()
+        reps_u = max(1, args.steps // 10)
+        e0.record(stream)
+        for _ in range(reps_u):
+            ctx.abs_estimate_batched(bi["items"])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        uneven = len(bi["items"]) * reps_u / (e0.elapsed_time(e1) * 1e-3)
+        del bi
 
     # end to end through the host-buffer entry point (pinned buffers, copies inside)
     huv = torch.from_numpy(inp.uv).pin_memory()
@@ -497,6 +515,7 @@ def run_ours(args):
                        "triple_tc_us": round(tc_avg, 2),
                        "triple_tc_tflops_executed": tri_tc["achieved"],
                        "triple_tc_frac_bf16_peak": tri_tc["frac"],
+                       "triple_tc_traffic": tri_tc["traffic"],
                        "triple_useful_tflops": useful / (tc_avg * 1e-6) / 1e12},
         "fp32": {"triple_fp32_us": round(stages["triple_fp32"]["avg_us"], 2),
                  "triple_useful_tflops": useful / (stages["triple_fp32"]["avg_us"] * 1e-6) / 1e12,
@@ -517,7 +536,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--batch", type=int, default=16)
-    ap.add_argument("--batch-items", type=int, default=64)
+    ap.add_argument("--batch-items", type=int, default=64, help="items of the uneven batch (0: skip it)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     args = ap.parse_args()
     if args.impl == "reference":

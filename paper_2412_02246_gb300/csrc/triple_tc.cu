@@ -7,7 +7,10 @@
 // x_hi = bf16(x) and x_lo = bf16(x - x_hi) (x - x_hi is exact in FP32, so the
 // pair carries 16 significant bits), and three BF16 products are accumulated
 // in FP32 in tensor memory: C = Ah Bh^T + Ah Bl^T + Al Bh^T (the Al Bl^T term
-// is below FP32 resolution of the result).
+// is below FP32 resolution of the result).  Bh and Bl are stacked into one
+// operand [Bh; Bl], so one MMA gives Ah Bh^T and Ah Bl^T side by side and Ah
+// is read from shared memory once per K-step; the three FP32 accumulators
+// are added in the epilogue.
 //
 // Rows are ordered by j (then i) and cut into tiles of 128.  A row (i, j)
 // only meets the rings k in [j, k_max(i, j)] (the triangle condition), so a
@@ -27,9 +30,9 @@
 //                  ones 128 B apart, 8-row groups 256 B apart, one 16-column K
 //                  slab after the other) in an operand stage, arrive on
 //                  ab_full and release the field stage (f_empty),
-//   MMA warp       issues the 12 MMAs of the chunk (4 K-steps x 3 products,
-//                  M = 128, N = band, K = 16) and commits them to ab_empty,
-//                  which frees the operand stage.
+//   MMA warp       issues the 8 MMAs of the chunk (4 K-steps x {Ah [Bh; Bl],
+//                  Al Bh}, M = 128, N = 2 band and band, K = 16) and commits
+//                  them to ab_empty, which frees the operand stage.
 // At the end the accumulator is read back with tcgen05.ld and each row writes
 // the partial sums of its triplets; a second kernel adds the pixel ranges in
 // FP64 in a fixed order.
@@ -51,7 +54,8 @@ namespace {
 constexpr int TM = 128;          // rows per tile (MMA M)
 constexpr int KC = 64;           // pixels per chunk (4 MMA K-steps)
 constexpr int NPW = 16;          // producer warps
-constexpr int KA = TM * (KC / 8) / (NPW * 32);          // A units (row, 8 pixels) per producer thread
+constexpr int GPR = KC / 8;                             // 8-pixel groups per row of a chunk
+constexpr int KA = TM * GPR / (NPW * 32);               // A units (row, 8 pixels) per producer thread
 constexpr int KB = 256 * (KC / 8) / (NPW * 32);         // B units per producer thread at most (band <= 256)
 static_assert(KA * NPW * 32 == TM * (KC / 8), "A units split evenly over the producers");
 constexpr int LOADER = NPW, ISSUER = NPW + 1;   // the two control warps
@@ -63,13 +67,13 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
 struct TcGeom {
     int nb, NP;                  // rings, largest MMA N (rings rounded up to 16)
-    int tmem_cols;               // power of two >= max(32, NP)
+    int tmem_cols;               // power of two >= max(32, 3 NP): three accumulators of a band
     int64_t P;                   // pixels
     int64_t per_split;           // pixels per CTA (multiple of KC)
     int n_trip;
     int sf, sa;                  // field and operand stages
-    int f_bytes, ab_bytes;       // one field stage [nb][FS] floats; one operand stage [Ah][Al][Bh][Bl]
-    int a_bytes, b_bytes;        // one operand tile (hi or lo)
+    int f_bytes, ab_bytes;       // one field stage [nb][FS] floats; one operand stage [Ah][Al][Bh; Bl]
+    int a_bytes, b_bytes;        // one A tile (hi or lo); the stacked B tile (2 NP rows)
     int tma;                     // fields by TMA tensor copy (else plain loads by the loader warp)
 };
 
@@ -253,7 +257,7 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
     const int64_t p_begin = (int64_t)blockIdx.y * G.per_split;
     const int64_t p_end = min(G.P, p_begin + G.per_split);
     const int nchunks = (int)cdiv(p_end - p_begin, KC);
-    const int rows8_a = TM / 8, rows8_b = G.NP / 8;
+    const int rows8_a = TM / 8, rows8_b = 2 * NB / 8;   // B: [Bh; Bl], 2 NB rows
     uint8_t *fbase = smem, *abase = smem + (size_t)G.sf * G.f_bytes;
 
     if (warp == LOADER) {
@@ -296,7 +300,8 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
     } else if (warp == ISSUER) {
         // ---------------- MMA issue: one thread
         if (lane == 0) {
-            const uint32_t idesc = make_idesc(TM, NB);
+            const bool stacked = 2 * NB <= 256;   // one MMA for Ah [Bh; Bl] (N <= 256)
+            const uint32_t id2 = make_idesc(TM, 2 * NB), id1 = make_idesc(TM, NB);
             int committed = 0;
             for (int c = 0; c < nchunks; ++c) {
                 const int s = c % G.sa, use = c / G.sa;
@@ -306,16 +311,22 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 uint8_t *Ah = abase + (size_t)s * G.ab_bytes, *Al = Ah + G.a_bytes;
-                uint8_t *Bh = Al + G.a_bytes, *Bl = Bh + G.b_bytes;
+                uint8_t *Bs = Al + G.a_bytes;
 #pragma unroll
                 for (int ks = 0; ks < KC / 16; ++ks) {
+                    const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
                     const uint64_t ah = make_desc(smem_u32(Ah + ks * rows8_a * 256), 128, 256);
                     const uint64_t al = make_desc(smem_u32(Al + ks * rows8_a * 256), 128, 256);
-                    const uint64_t bh = make_desc(smem_u32(Bh + ks * rows8_b * 256), 128, 256);
-                    const uint64_t bl = make_desc(smem_u32(Bl + ks * rows8_b * 256), 128, 256);
-                    mma_bf16(tmem, ah, bh, idesc, (c > 0 || ks > 0) ? 1u : 0u);
-                    mma_bf16(tmem, ah, bl, idesc, 1u);
-                    mma_bf16(tmem, al, bh, idesc, 1u);
+                    const uint32_t bslab = smem_u32(Bs + ks * rows8_b * 256);
+                    const uint64_t bh = make_desc(bslab, 128, 256);                // rows [0, NB): Bh
+                    if (stacked) {
+                        mma_bf16(tmem, ah, bh, id2, acc);                            // cols [0, 2 NB)
+                    } else {
+                        const uint64_t bl = make_desc(bslab + (NB / 8) * 256, 128, 256);   // rows [NB, 2 NB): Bl
+                        mma_bf16(tmem, ah, bh, id1, acc);
+                        mma_bf16(tmem + (uint32_t)NB, ah, bl, id1, acc);
+                    }
+                    mma_bf16(tmem + (uint32_t)(2 * NB), al, bh, id1, acc);      // cols [2 NB, 3 NB)
                 }
                 mma_commit(smem_u32(&ab_empty[s]));
                 ++committed;
@@ -330,14 +341,14 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
     } else {
         // ---------------- producers: the operand tiles of a chunk.  A thread's
         // units are the same in every chunk: field offsets and tile offsets
-        // are worked out once.  A: unit u = (8-row group, 8 rows x 8 groups);
-        // a warp's 32 units are 8 rows x 4 groups (conflict-free 16-byte stores)
+        // are worked out once.  Unit u = (8-row group, 8 rows x GPR groups); a
+        // warp's 32 units are 8 rows x 4 groups (conflict-free 16-byte stores)
         const int p = threadIdx.x;
         int a_fi[KA], a_fj[KA], a_so[KA], a_g[KA];
 #pragma unroll
         for (int k = 0; k < KA; ++k) {
             const int u = p + k * NPW * 32;
-            const int rg = u >> 6, rem = u & 63;
+            const int rg = u / (8 * GPR), rem = u % (8 * GPR);
             const int g = rem >> 3, r = rg * 8 + (rem & 7);
             const int i = rowi[r], j = rowj[r];
             a_fi[k] = i >= 0 ? i * FS + g * 8 : -1;
@@ -349,10 +360,10 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
             const int u = p + k * NPW * 32;
-            const int rg = u >> 6, rem = u & 63;
+            const int rg = u / (8 * GPR), rem = u % (8 * GPR);
             const int g = rem >> 3, kk = rg * 8 + (rem & 7);
-            b_fk[k] = u < NB * (KC / 8) ? (klo + kk < G.nb ? (klo + kk) * FS + g * 8 : -1) : -2;
-            b_so[k] = core_off(kk, g, rows8_b);
+            b_fk[k] = u < NB * GPR ? (klo + kk < G.nb ? (klo + kk) * FS + g * 8 : -1) : -2;
+            b_so[k] = core_off(kk, g, rows8_b);   // Bh row kk; Bl row NB + kk
             b_g[k] = g;
         }
         for (int c = 0; c < nchunks; ++c) {
@@ -366,7 +377,8 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
             }
             const float *F = (const float *)(fbase + (size_t)sf * G.f_bytes);
             uint8_t *Ah = abase + (size_t)sa * G.ab_bytes, *Al = Ah + G.a_bytes;
-            uint8_t *Bh = Al + G.a_bytes, *Bl = Bh + G.b_bytes;
+            uint8_t *Bs = Al + G.a_bytes;
+            const int bl_off = (NB / 8) * 256;   // row NB of the stacked tile
             const int64_t pc = p_begin + (int64_t)c * KC;
             const int valid = (int)min((int64_t)KC, p_end - pc);
 #pragma unroll
@@ -396,7 +408,7 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
                     for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
                 }
                 if (valid < KC) mask_tail(v, b_g[k], valid);
-                store_split8(Bh, Bl, b_so[k], v);
+                store_split8(Bs, Bs + bl_off, b_so[k], v);
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncwarp();
@@ -412,12 +424,14 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
     if (abort_s) {
         if (threadIdx.x == 0) atomicCAS(err, 0, DERR_TIMEOUT);
     } else {
-        // epilogue: TMEM -> shared [128][NB + 1] (over the stages) -> per-triplet partials
+        // epilogue: TMEM -> shared [128][3 NB + 1] (over the stages) -> per-triplet
+        // partials, (Ah Bh + Ah Bl) + Al Bh
         float *D = (float *)smem;
+        const int dw = 3 * NB + 1;
         if (warp < 4) {   // warp w reads tensor-memory lanes 32 w .. 32 w + 31
             const int lane_base = warp * 32;
             const int r = lane_base + lane;
-            for (int col = 0; col < NB; col += 16) {
+            for (int col = 0; col < 3 * NB; col += 16) {
                 uint32_t v[16];
                 const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)col;
                 asm volatile(
@@ -429,7 +443,7 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-                for (int e = 0; e < 16; ++e) D[r * (NB + 1) + col + e] = __uint_as_float(v[e]);
+                for (int e = 0; e < 16; ++e) D[r * dw + col + e] = __uint_as_float(v[e]);
             }
         }
         __syncthreads();
@@ -437,8 +451,10 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
             const int4 R = rows[r0 + threadIdx.x];
             for (int t = R.z; t < R.w; ++t) {
                 const int kk = ijk[3 * t + 2] - klo;
-                if (kk >= 0 && kk < NB)
-                    partial[(size_t)blockIdx.y * G.n_trip + t] = (double)D[threadIdx.x * (NB + 1) + kk];
+                if (kk >= 0 && kk < NB) {
+                    const float *d = D + threadIdx.x * dw + kk;
+                    partial[(size_t)blockIdx.y * G.n_trip + t] = (double)(d[0] + d[NB]) + (double)d[2 * NB];
+                }
             }
         }
     }
@@ -586,13 +602,14 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
     G.NP = (int)cdiv(std::max(s.nb, 16), 16) * 16;
     if (G.NP > 256) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 path supports at most 256 rings");
     G.tmem_cols = 32;
-    while (G.tmem_cols < G.NP) G.tmem_cols <<= 1;
+    while (G.tmem_cols < 3 * G.NP) G.tmem_cols <<= 1;
+    if (G.tmem_cols > 512) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 accumulators exceed tensor memory");
     G.P = (int64_t)s.N * s.N;
     G.n_trip = n_trip;
     G.a_bytes = TM * KC * 2;
-    G.b_bytes = G.NP * KC * 2;
+    G.b_bytes = 2 * G.NP * KC * 2;
     G.f_bytes = (int)(cdiv((int64_t)s.nb * FS * 4, 1024) * 1024);
-    G.ab_bytes = (int)(cdiv(2 * G.a_bytes + 2 * G.b_bytes, 1024) * 1024);
+    G.ab_bytes = (int)(cdiv(2 * G.a_bytes + G.b_bytes, 1024) * 1024);
     // stages: three operand stages if the field ring still gets two, then as many field stages as fit
     const int64_t budget = 215 * 1024;   // dynamic shared memory, below the 227 KB per CTA with the static part
     G.sa = MAX_AB;
@@ -600,7 +617,7 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
     G.sf = (int)std::min<int64_t>(MAX_F, (budget - (int64_t)G.sa * G.ab_bytes) / G.f_bytes);
     if (G.sf < 2) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 stages do not fit shared memory");
     const size_t smem =
-        1024 + std::max((size_t)G.sf * G.f_bytes + (size_t)G.sa * G.ab_bytes, (size_t)TM * (G.NP + 1) * 4);
+        1024 + std::max((size_t)G.sf * G.f_bytes + (size_t)G.sa * G.ab_bytes, (size_t)TM * (3 * G.NP + 1) * 4);
     // the field chunk as one TMA box (FS pixels x every ring) of the [nb][P] FP32 array; the
     // row pitch P x 4 bytes and the array must be 16-byte aligned, else the loader warp copies
     CUtensorMap fmap;
