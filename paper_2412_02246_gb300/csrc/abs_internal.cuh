@@ -47,6 +47,7 @@ struct Setup {
     // a property of the ring geometry, computed on first use
     unsigned long long *d_full_counts = nullptr;
     bool full_counts_ready = false;
+    int tc_groups = -1;           // split-BF16 tile groups of the canonical list (-1: not worked out)
 };
 
 // Host-side validation + derivation.  Returns ABS_OK or an error with text in err.

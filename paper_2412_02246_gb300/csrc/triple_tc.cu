@@ -17,9 +17,13 @@
 // tile of neighbouring j meets a narrow band of rings: the tile's MMA N is
 // that band rounded up to 16, not every ring.
 //
-// One CTA owns a row tile and a range of pixels, streamed in chunks of 64
-// pixels by three roles through two rings of shared-memory stages, one of
-// field chunks (deep, so loads run well ahead) and one of operand tiles:
+// Tiles are grouped so that a group's accumulators (3 x band columns per
+// tile) fit the 512 columns of tensor memory.  One CTA owns a group of row
+// tiles and a range of pixels, so each field chunk is brought in once for
+// every tile of the group.  The range is streamed in chunks of 64 pixels by
+// three roles through two rings of shared-memory stages, one of field chunks
+// (deep, so loads run well ahead) and one of operand tiles (one step per
+// chunk and tile):
 //   loader warp    copies the chunk's fields, all rings x 68 pixels (the
 //                  padded row keeps the producers' reads off one bank), with
 //                  one 2-D TMA tensor copy (zero fill past the last pixel)
@@ -30,9 +34,10 @@
 //                  ones 128 B apart, 8-row groups 256 B apart, one 16-column K
 //                  slab after the other) in an operand stage, arrive on
 //                  ab_full and release the field stage (f_empty),
-//   MMA warp       issues the 8 MMAs of the chunk (4 K-steps x {Ah [Bh; Bl],
-//                  Al Bh}, M = 128, N = 2 band and band, K = 16) and commits
-//                  them to ab_empty, which frees the operand stage.
+//   MMA warp       issues the 8 MMAs of a step (4 K-steps x {Ah [Bh; Bl],
+//                  Al Bh}, M = 128, N = 2 band and band, K = 16) into the
+//                  tile's accumulator columns and commits them to ab_empty,
+//                  which frees the operand stage.
 // At the end the accumulator is read back with tcgen05.ld and each row writes
 // the partial sums of its triplets; a second kernel adds the pixel ranges in
 // FP64 in a fixed order.
@@ -45,6 +50,8 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+
+#include <map>
 
 #include "abs_internal.cuh"
 
@@ -62,12 +69,14 @@ constexpr int LOADER = NPW, ISSUER = NPW + 1;   // the two control warps
 constexpr int NT = (NPW + 2) * 32;
 constexpr int FS = KC + 4;       // field row in a stage (floats; 272 B, a multiple of 16): the TMA box width
 constexpr int MAX_AB = 3, MAX_F = 8;   // operand and field stages
+constexpr int GMAX = 10;         // row tiles per group (3 x 16 accumulator columns each at least)
+constexpr int TMEM_COLS = 512;
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 
 struct TcGeom {
     int nb, NP;                  // rings, largest MMA N (rings rounded up to 16)
-    int tmem_cols;               // power of two >= max(32, 3 NP): three accumulators of a band
+    int tmem_cols;               // columns allocated (the group's accumulators fit them)
     int64_t P;                   // pixels
     int64_t per_split;           // pixels per CTA (multiple of KC)
     int n_trip;
@@ -205,7 +214,8 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
                                                      const float *__restrict__ fields,
                                                      const int4 *__restrict__ rows,
                                                      const int2 *__restrict__ tiles,
-                                                     const int *__restrict__ n_rows_p,
+                                                     const int2 *__restrict__ groups,
+                                                     const int *__restrict__ ctl,
                                                      const int32_t *__restrict__ ijk,
                                                      double *__restrict__ partial,
                                                      int32_t *__restrict__ err) {
@@ -214,27 +224,45 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
     // stages on a 1024-byte boundary (TMA destinations want 128; the launch adds 1 KB of slack)
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     __shared__ uint32_t tmem_holder;
-    __shared__ int rowi[TM], rowj[TM];
+    __shared__ int16_t rowi[GMAX][TM], rowj[GMAX][TM];
+    __shared__ int t_klo[GMAX], t_nb[GMAX], t_col[GMAX];
     __shared__ volatile int abort_s;
-    const int n_rows = *n_rows_p;
-    const int r0 = blockIdx.x * TM;
-    if (r0 >= n_rows) return;
+    const int n_rows = ctl[0], n_groups = ctl[1];
+    if ((int)blockIdx.x >= n_groups) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int2 band = tiles[blockIdx.x];            // (first ring of the band, band width)
-    const int klo = band.x, NB = band.y;
-    if (threadIdx.x < TM) {
-        const int r = r0 + threadIdx.x;
+    const int2 grp = groups[blockIdx.x];            // (first tile, tiles)
+    const int t0 = grp.x, NG = grp.y;
+    if (threadIdx.x < GMAX) {
+        const int t = threadIdx.x;
+        int lo = 0, w = 16;
+        if (t < NG) {
+            const int2 band = tiles[t0 + t];        // (first ring of the band, band width)
+            lo = band.x;
+            w = band.y;
+        }
+        t_klo[t] = lo;
+        t_nb[t] = w;
+    }
+    for (int e = threadIdx.x; e < GMAX * TM; e += blockDim.x) {
+        const int t = e / TM, rr = e - t * TM;
+        const int r = (t0 + t) * TM + rr;
         int i = -1, j = -1;
-        if (r < n_rows) {
+        if (t < NG && r < n_rows) {
             const int4 R = rows[r];
             i = R.x;
             j = R.y;
         }
-        rowi[threadIdx.x] = i;
-        rowj[threadIdx.x] = j;
+        rowi[t][rr] = (int16_t)i;
+        rowj[t][rr] = (int16_t)j;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         abort_s = 0;
+        int col = 0;
+        for (int t = 0; t < GMAX; ++t) {   // accumulator columns of each tile: [Ah Bh | Ah Bl | Al Bh]
+            t_col[t] = col;
+            if (t < NG) col += 3 * t_nb[t];
+        }
         for (int s = 0; s < G.sf; ++s) {
             mbar_init(smem_u32(&f_full[s]), 1);
             mbar_init(smem_u32(&f_empty[s]), NPW);
@@ -257,7 +285,8 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
     const int64_t p_begin = (int64_t)blockIdx.y * G.per_split;
     const int64_t p_end = min(G.P, p_begin + G.per_split);
     const int nchunks = (int)cdiv(p_end - p_begin, KC);
-    const int rows8_a = TM / 8, rows8_b = 2 * NB / 8;   // B: [Bh; Bl], 2 NB rows
+    const int nsteps = nchunks * NG;                // step = chunk x tile
+    const int rows8_a = TM / 8;
     uint8_t *fbase = smem, *abase = smem + (size_t)G.sf * G.f_bytes;
 
     if (warp == LOADER) {
@@ -298,18 +327,20 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
                 if (!mbar_drain(smem_u32(&f_full[s]), (uint32_t)((uses - 1) & 1))) abort_s = 1;
             }
     } else if (warp == ISSUER) {
-        // ---------------- MMA issue: one thread
+        // ---------------- MMA issue: one thread, one step (chunk, tile) per operand stage
         if (lane == 0) {
-            const bool stacked = 2 * NB <= 256;   // one MMA for Ah [Bh; Bl] (N <= 256)
-            const uint32_t id2 = make_idesc(TM, 2 * NB), id1 = make_idesc(TM, NB);
-            int committed = 0;
-            for (int c = 0; c < nchunks; ++c) {
-                const int s = c % G.sa, use = c / G.sa;
+            int committed = 0, c = 0, t = 0, s = 0, use = 0;   // step = (chunk c, tile t), stage s, its use
+            int NB = t_nb[0];
+            uint32_t acc_t = tmem + (uint32_t)t_col[0];
+            for (int st = 0; st < nsteps; ++st) {
                 if (!mbar_wait(smem_u32(&ab_full[s]), (uint32_t)(use & 1), &abort_s)) {
                     abort_s = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const int rows8_b = 2 * NB / 8;                 // B: [Bh; Bl], 2 NB rows
+                const bool stacked = 2 * NB <= 256;             // one MMA for Ah [Bh; Bl] (N <= 256)
+                const uint32_t id2 = make_idesc(TM, 2 * NB), id1 = make_idesc(TM, NB);
                 uint8_t *Ah = abase + (size_t)s * G.ab_bytes, *Al = Ah + G.a_bytes;
                 uint8_t *Bs = Al + G.a_bytes;
 #pragma unroll
@@ -320,101 +351,156 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
                     const uint32_t bslab = smem_u32(Bs + ks * rows8_b * 256);
                     const uint64_t bh = make_desc(bslab, 128, 256);                // rows [0, NB): Bh
                     if (stacked) {
-                        mma_bf16(tmem, ah, bh, id2, acc);                            // cols [0, 2 NB)
+                        mma_bf16(acc_t, ah, bh, id2, acc);                           // cols [0, 2 NB)
                     } else {
                         const uint64_t bl = make_desc(bslab + (NB / 8) * 256, 128, 256);   // rows [NB, 2 NB): Bl
-                        mma_bf16(tmem, ah, bh, id1, acc);
-                        mma_bf16(tmem + (uint32_t)NB, ah, bl, id1, acc);
+                        mma_bf16(acc_t, ah, bh, id1, acc);
+                        mma_bf16(acc_t + (uint32_t)NB, ah, bl, id1, acc);
                     }
-                    mma_bf16(tmem + (uint32_t)(2 * NB), al, bh, id1, acc);      // cols [2 NB, 3 NB)
+                    mma_bf16(acc_t + (uint32_t)(2 * NB), al, bh, id1, acc);     // cols [2 NB, 3 NB)
                 }
                 mma_commit(smem_u32(&ab_empty[s]));
                 ++committed;
+                if (++s == G.sa) {
+                    s = 0;
+                    ++use;
+                }
+                if (++t == NG) {
+                    t = 0;
+                    ++c;
+                }
+                if (NG > 1) {
+                    NB = t_nb[t];
+                    acc_t = tmem + (uint32_t)t_col[t];
+                }
             }
             // every MMA issued is done before tensor memory is read or freed
             if (committed > 0) {
-                const int c = committed - 1, s = c % G.sa, use = c / G.sa;
-                if (!mbar_drain(smem_u32(&ab_empty[s]), (uint32_t)(use & 1))) abort_s = 1;
+                const int st = committed - 1, s2 = st % G.sa, u2 = st / G.sa;
+                if (!mbar_drain(smem_u32(&ab_empty[s2]), (uint32_t)(u2 & 1))) abort_s = 1;
             }
-            if (committed < nchunks) abort_s = 1;
+            if (committed < nsteps) abort_s = 1;
         }
     } else {
-        // ---------------- producers: the operand tiles of a chunk.  A thread's
-        // units are the same in every chunk: field offsets and tile offsets
-        // are worked out once.  Unit u = (8-row group, 8 rows x GPR groups); a
-        // warp's 32 units are 8 rows x 4 groups (conflict-free 16-byte stores)
+        // ---------------- producers: the operand tiles of a step.  A thread's
+        // (row, 8-pixel group) units and band units are the same for every
+        // chunk and tile: their tile offsets are worked out once.  Unit u =
+        // (8-row group, 8 rows x GPR groups); a warp's 32 units are 8 rows x 4
+        // groups (conflict-free 16-byte stores)
         const int p = threadIdx.x;
-        int a_fi[KA], a_fj[KA], a_so[KA], a_g[KA];
+        int a_r[KA], a_g[KA], a_so[KA];
 #pragma unroll
         for (int k = 0; k < KA; ++k) {
             const int u = p + k * NPW * 32;
             const int rg = u / (8 * GPR), rem = u % (8 * GPR);
-            const int g = rem >> 3, r = rg * 8 + (rem & 7);
-            const int i = rowi[r], j = rowj[r];
-            a_fi[k] = i >= 0 ? i * FS + g * 8 : -1;
-            a_fj[k] = i >= 0 ? j * FS + g * 8 : -1;
-            a_so[k] = core_off(r, g, rows8_a);
-            a_g[k] = g;
+            a_g[k] = rem >> 3;
+            a_r[k] = rg * 8 + (rem & 7);
+            a_so[k] = core_off(a_r[k], a_g[k], rows8_a);
         }
-        int b_fk[KB], b_so[KB], b_g[KB];
+        int b_kk[KB], b_g[KB];
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
             const int u = p + k * NPW * 32;
             const int rg = u / (8 * GPR), rem = u % (8 * GPR);
-            const int g = rem >> 3, kk = rg * 8 + (rem & 7);
-            b_fk[k] = u < NB * GPR ? (klo + kk < G.nb ? (klo + kk) * FS + g * 8 : -1) : -2;
-            b_so[k] = core_off(kk, g, rows8_b);   // Bh row kk; Bl row NB + kk
-            b_g[k] = g;
+            b_g[k] = rem >> 3;
+            b_kk[k] = rg * 8 + (rem & 7);
         }
+        // a step's field offsets (ring x FS + group x 8) and band, loaded one step ahead
+        // so that no field load waits on a shared-memory lookup
+        int fi[KA], fj[KA], nfi[KA], nfj[KA];
+        auto row_offsets = [&](int t, int *oi, int *oj) {
+#pragma unroll
+            for (int k = 0; k < KA; ++k) {
+                const int i = rowi[t][a_r[k]], j = rowj[t][a_r[k]];
+                oi[k] = i >= 0 ? i * FS + a_g[k] * 8 : -1;
+                oj[k] = j * FS + a_g[k] * 8;
+            }
+        };
+        row_offsets(0, fi, fj);
+        int nb_cur = t_nb[0], klo_cur = t_klo[0];
+        int sa = 0, ua = 0, sf = 0, uf = 0;   // operand stage and its use; field stage and its use
         for (int c = 0; c < nchunks; ++c) {
-            const int sf = c % G.sf, uf = c / G.sf;
-            const int sa = c % G.sa, ua = c / G.sa;
-            bool ok = mbar_wait(smem_u32(&f_full[sf]), (uint32_t)(uf & 1), &abort_s);
-            if (ok && ua > 0) ok = mbar_wait(smem_u32(&ab_empty[sa]), (uint32_t)((ua - 1) & 1), &abort_s);
-            if (!ok) {
+            if (!mbar_wait(smem_u32(&f_full[sf]), (uint32_t)(uf & 1), &abort_s)) {
                 abort_s = 1;
                 break;
             }
             const float *F = (const float *)(fbase + (size_t)sf * G.f_bytes);
-            uint8_t *Ah = abase + (size_t)sa * G.ab_bytes, *Al = Ah + G.a_bytes;
-            uint8_t *Bs = Al + G.a_bytes;
-            const int bl_off = (NB / 8) * 256;   // row NB of the stacked tile
             const int64_t pc = p_begin + (int64_t)c * KC;
             const int valid = (int)min((int64_t)KC, p_end - pc);
-#pragma unroll
-            for (int k = 0; k < KA; ++k) {
-                float2 v[4];
-                if (a_fi[k] >= 0) {
-                    float2 x[4], y[4];
-                    ld8(F + a_fi[k], x);
-                    ld8(F + a_fj[k], y);
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) v[e] = __fmul2_rn(x[e], y[e]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
+            bool ok = true;
+            for (int t = 0; t < NG; ++t) {
+                if (ua > 0 && !mbar_wait(smem_u32(&ab_empty[sa]), (uint32_t)((ua - 1) & 1), &abort_s)) {
+                    ok = false;
+                    break;
                 }
-                if (valid < KC) mask_tail(v, a_g[k], valid);
-                store_split8(Ah, Al, a_so[k], v);
-            }
-#pragma unroll
-            for (int k = 0; k < KB; ++k) {
-                if (b_fk[k] == -2) continue;   // past the band
-                float2 v[4];
-                if (b_fk[k] >= 0) {
-                    ld8(F + b_fk[k], v);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
+                uint8_t *Ah = abase + (size_t)sa * G.ab_bytes, *Al = Ah + G.a_bytes;
+                uint8_t *Bs = Al + G.a_bytes;
+                const int NB = nb_cur, klo = klo_cur, rows8_b = 2 * NB / 8;
+                const int bl_off = (NB / 8) * 256;   // row NB of the stacked tile
+                const int tn = t + 1 < NG ? t + 1 : 0;   // the next step's tile
+                int nb_next = nb_cur, klo_next = klo_cur;
+                if (NG > 1) {
+                    row_offsets(tn, nfi, nfj);
+                    nb_next = t_nb[tn];
+                    klo_next = t_klo[tn];
                 }
-                if (valid < KC) mask_tail(v, b_g[k], valid);
-                store_split8(Bs, Bs + bl_off, b_so[k], v);
+#pragma unroll
+                for (int k = 0; k < KA; ++k) {
+                    float2 v[4];
+                    if (fi[k] >= 0) {
+                        float2 x[4], y[4];
+                        ld8(F + fi[k], x);
+                        ld8(F + fj[k], y);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) v[e] = __fmul2_rn(x[e], y[e]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
+                    }
+                    if (valid < KC) mask_tail(v, a_g[k], valid);
+                    store_split8(Ah, Al, a_so[k], v);
+                }
+#pragma unroll
+                for (int k = 0; k < KB; ++k) {
+                    if (p + k * NPW * 32 >= NB * GPR) break;   // past the band
+                    const int ring = klo + b_kk[k];
+                    float2 v[4];
+                    if (ring < G.nb) {
+                        ld8(F + ring * FS + b_g[k] * 8, v);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
+                    }
+                    if (valid < KC) mask_tail(v, b_g[k], valid);
+                    const int so = core_off(b_kk[k], b_g[k], rows8_b);   // Bh row kk; Bl row NB + kk
+                    store_split8(Bs, Bs + bl_off, so, v);
+                }
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&ab_full[sa]));
+                if (++sa == G.sa) {
+                    sa = 0;
+                    ++ua;
+                }
+                if (NG > 1) {
+#pragma unroll
+                    for (int k = 0; k < KA; ++k) {
+                        fi[k] = nfi[k];
+                        fj[k] = nfj[k];
+                    }
+                    nb_cur = nb_next;
+                    klo_cur = klo_next;
+                }
             }
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            if (!ok) {
+                abort_s = 1;
+                break;
+            }
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(smem_u32(&ab_full[sa]));
-                mbar_arrive(smem_u32(&f_empty[sf]));
+            if (lane == 0) mbar_arrive(smem_u32(&f_empty[sf]));   // every tile of the chunk is formed
+            if (++sf == G.sf) {
+                sf = 0;
+                ++uf;
             }
         }
     }
@@ -424,38 +510,42 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
     if (abort_s) {
         if (threadIdx.x == 0) atomicCAS(err, 0, DERR_TIMEOUT);
     } else {
-        // epilogue: TMEM -> shared [128][3 NB + 1] (over the stages) -> per-triplet
-        // partials, (Ah Bh + Ah Bl) + Al Bh
+        // epilogue, tile by tile: TMEM -> shared [128][3 NB + 1] (over the stages) ->
+        // per-triplet partials, (Ah Bh + Ah Bl) + Al Bh
         float *D = (float *)smem;
-        const int dw = 3 * NB + 1;
-        if (warp < 4) {   // warp w reads tensor-memory lanes 32 w .. 32 w + 31
-            const int lane_base = warp * 32;
-            const int r = lane_base + lane;
-            for (int col = 0; col < 3 * NB; col += 16) {
-                uint32_t v[16];
-                const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)col;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-                    "%11, %12, %13, %14, %15}, [%16];\n"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+        for (int t = 0; t < NG; ++t) {
+            const int NB = t_nb[t], klo = t_klo[t], dw = 3 * NB + 1;
+            if (warp < 4) {   // warp w reads tensor-memory lanes 32 w .. 32 w + 31
+                const int lane_base = warp * 32;
+                const int r = lane_base + lane;
+                for (int col = 0; col < 3 * NB; col += 16) {
+                    uint32_t v[16];
+                    const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(t_col[t] + col);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+                        "%11, %12, %13, %14, %15}, [%16];\n"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-                for (int e = 0; e < 16; ++e) D[r * dw + col + e] = __uint_as_float(v[e]);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x < TM && r0 + (int)threadIdx.x < n_rows) {
-            const int4 R = rows[r0 + threadIdx.x];
-            for (int t = R.z; t < R.w; ++t) {
-                const int kk = ijk[3 * t + 2] - klo;
-                if (kk >= 0 && kk < NB) {
-                    const float *d = D + threadIdx.x * dw + kk;
-                    partial[(size_t)blockIdx.y * G.n_trip + t] = (double)(d[0] + d[NB]) + (double)d[2 * NB];
+                    for (int e = 0; e < 16; ++e) D[r * dw + col + e] = __uint_as_float(v[e]);
                 }
             }
+            __syncthreads();
+            const int r = (t0 + t) * TM + (int)threadIdx.x;
+            if (threadIdx.x < TM && r < n_rows) {
+                const int4 R = rows[r];
+                for (int q = R.z; q < R.w; ++q) {
+                    const int kk = ijk[3 * q + 2] - klo;
+                    if (kk >= 0 && kk < NB) {
+                        const float *d = D + threadIdx.x * dw + kk;
+                        partial[(size_t)blockIdx.y * G.n_trip + q] = (double)(d[0] + d[NB]) + (double)d[2 * NB];
+                    }
+                }
+            }
+            __syncthreads();
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -466,12 +556,17 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
 
 // Row table of a (canonical, sorted) triplet list: one entry (i, j, first
 // triplet, end) per run of equal (i, j), ordered by (j, i); then per tile of
-// TM rows its band of rings (first k, width rounded up to 16, at most np).
+// TM rows its band of rings (first k, width rounded up to 16, at most np);
+// then groups of consecutive tiles whose accumulators (3 x band columns
+// each) fit TMEM_COLS, at most gmax tiles and about as many tiles in each
+// (gmax = 1: a group per tile).  ctl[0] = rows, ctl[1] = groups.
 // One block of 1024 threads; dynamic shared memory: nb x ceil(nb / 32) words
 // of presence bits, (j, i) of every row.
-__global__ void __launch_bounds__(1024) k_rows(int n_trip, int nb, int np, const int32_t *__restrict__ ijk,
-                                               int4 *__restrict__ rows, int *__restrict__ n_rows,
-                                               int2 *__restrict__ tiles) {
+__global__ void __launch_bounds__(1024) k_rows(int n_trip, int nb, int np, int gmax,
+                                               const int32_t *__restrict__ ijk, int4 *__restrict__ rows,
+                                               int *__restrict__ ctl, int2 *__restrict__ tiles,
+                                               int2 *__restrict__ groups) {
+    int *n_rows = ctl;
     extern __shared__ uint32_t presence[];
     __shared__ int jstart[ABS_MAX_BINS + 1];
     __shared__ int wsum[32];
@@ -553,6 +648,25 @@ __global__ void __launch_bounds__(1024) k_rows(int n_trip, int nb, int np, const
             tiles[tl] = make_int2(lo, w);
         }
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        // greedy groups of consecutive tiles; then again with at most ceil(tiles / groups)
+        // tiles a group, so that the groups carry about the same work
+        int cap = gmax, ng = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            ng = 0;
+            for (int t = 0; t < ntiles;) {
+                const int first = t;
+                int cols = 0;
+                while (t < ntiles && t - first < cap && cols + 3 * tiles[t].y <= TMEM_COLS) cols += 3 * tiles[t++].y;
+                if (t == first) ++t;   // cannot happen: a band is at most np <= TMEM_COLS / 3
+                if (pass == 1) groups[ng] = make_int2(first, t - first);
+                ++ng;
+            }
+            cap = min(gmax, (ntiles + ng - 1) / max(ng, 1));
+        }
+        ctl[1] = ng;
+    }
 }
 
 // S[t] = inv_p * sum over splits of partial[split][t]: 32 triplets per block,
@@ -594,16 +708,52 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
+// Tile groups of the canonical triplet list, worked out on the host the way
+// k_rows does on the device (rows by (j, i), 128 a tile, bands rounded to 16,
+// greedy groups): sizes the grid.  Lists given by the caller use the tile count.
+static int canonical_groups(const Setup &s, int np, int gmax) {
+    std::map<std::pair<int, int>, std::pair<int, int>> kr;   // (j, i) -> (first k, last k)
+    for (size_t t = 0; t + 2 < s.ijk.size(); t += 3) {
+        const auto key = std::make_pair(s.ijk[t + 1], s.ijk[t]);
+        auto it = kr.find(key);
+        if (it == kr.end()) kr[key] = {s.ijk[t + 2], s.ijk[t + 2]};
+        else it->second.second = s.ijk[t + 2];
+    }
+    std::vector<int> w;
+    int n = 0, lo = 1 << 30, hi = -1;
+    for (const auto &e : kr) {
+        lo = std::min(lo, e.second.first);
+        hi = std::max(hi, e.second.second);
+        if (++n == TM) {
+            w.push_back(std::min(np, ((hi - lo + 1 + 15) / 16) * 16));
+            n = 0, lo = 1 << 30, hi = -1;
+        }
+    }
+    if (n > 0) w.push_back(std::min(np, ((hi - lo + 1 + 15) / 16) * 16));
+    const int ntiles = (int)w.size();
+    int cap = gmax, ng = 0;
+    for (int pass = 0; pass < 2; ++pass) {   // as k_rows: greedy, then balanced
+        ng = 0;
+        for (int t = 0; t < ntiles;) {
+            const int first = t;
+            int cols = 0;
+            while (t < ntiles && t - first < cap && cols + 3 * w[t] <= TMEM_COLS) cols += 3 * w[t++];
+            if (t == first) ++t;
+            ++ng;
+        }
+        cap = std::min(gmax, (ntiles + ng - 1) / std::max(ng, 1));
+    }
+    return std::max(ng, 1);
+}
+
 abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields, int32_t n_trip,
                             const int32_t *d_ijk, double *d_sum) {
     if (n_trip == 0) return ABS_OK;
     TcGeom G;
     G.nb = s.nb;
     G.NP = (int)cdiv(std::max(s.nb, 16), 16) * 16;
-    if (G.NP > 256) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 path supports at most 256 rings");
-    G.tmem_cols = 32;
-    while (G.tmem_cols < 3 * G.NP) G.tmem_cols <<= 1;
-    if (G.tmem_cols > 512) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 accumulators exceed tensor memory");
+    if (3 * G.NP > TMEM_COLS) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 accumulators exceed tensor memory");
+    G.tmem_cols = TMEM_COLS;
     G.P = (int64_t)s.N * s.N;
     G.n_trip = n_trip;
     G.a_bytes = TM * KC * 2;
@@ -615,9 +765,10 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
     G.sa = MAX_AB;
     while (G.sa > 2 && budget - (int64_t)G.sa * G.ab_bytes < 2 * (int64_t)G.f_bytes) --G.sa;
     G.sf = (int)std::min<int64_t>(MAX_F, (budget - (int64_t)G.sa * G.ab_bytes) / G.f_bytes);
-    if (G.sf < 2) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 stages do not fit shared memory");
-    const size_t smem =
-        1024 + std::max((size_t)G.sf * G.f_bytes + (size_t)G.sa * G.ab_bytes, (size_t)TM * (3 * G.NP + 1) * 4);
+    const size_t epi = (size_t)TM * (3 * G.NP + 1) * 4;
+    if (G.sf < 2 || (int64_t)epi > budget)
+        return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 stages do not fit shared memory");
+    const size_t smem = 1024 + std::max((size_t)G.sf * G.f_bytes + (size_t)G.sa * G.ab_bytes, epi);
     // the field chunk as one TMA box (FS pixels x every ring) of the [nb][P] FP32 array; the
     // row pitch P x 4 bytes and the array must be 16-byte aligned, else the loader warp copies
     CUtensorMap fmap;
@@ -635,28 +786,55 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
     }
     const int max_rows = (int)std::min<int64_t>(n_trip, (int64_t)s.nb * (s.nb + 1) / 2);
     const int tiles = (int)cdiv(max_rows, TM);
-    // pixel ranges: enough CTAs for about one wave, at most 4096 pixels each
-    // (bounds the FP32 accumulation length inside the tensor core)
-    int64_t per = cdiv(cdiv(G.P, std::max<int64_t>(1, cdiv(ctx->sm_count, tiles))), KC) * KC;
-    per = std::min<int64_t>(per, 4096);
+    // Grouped (several tiles share each field chunk) or a group per tile: whichever
+    // finishes first by a simple count of CTA waves x work per CTA, in tenths of a
+    // tile's 64-pixel step: per chunk 10 per tile plus 3 for bringing the chunk in,
+    // and 80 per tile for its epilogue (fitted to same-GPU timings of both forms on
+    // grids of 144^2 to 576^2 pixels).  Lists given by the caller are not grouped.
+    Setup &ms = const_cast<Setup &>(s);
+    if (d_ijk == s.d_ijk && ms.tc_groups < 0) ms.tc_groups = canonical_groups(s, G.NP, GMAX);
+    auto ranges_for = [&](int groups) {   // pixel range per CTA: whole waves, at most 4096 pixels
+        int64_t per = 0;                   // (bounds the FP32 accumulation length in the tensor core)
+        for (int waves = 1;; ++waves) {
+            const int64_t ranges = std::max<int64_t>(1, (int64_t)ctx->sm_count * waves / groups);
+            per = cdiv(cdiv(G.P, ranges), KC) * KC;
+            if (per <= 4096) return per;
+        }
+    };
+    auto makespan = [&](int groups, int per_group, int64_t per) {
+        const int64_t ctas = groups * cdiv(G.P, per);
+        return cdiv(ctas, ctx->sm_count) * (cdiv(per, KC) * (10 * per_group + 3) + 80 * per_group);
+    };
+    int groups = tiles, gmax = 1;
+    int64_t per = ranges_for(tiles);
+    if (d_ijk == s.d_ijk && ms.tc_groups < tiles) {
+        const int gg = ms.tc_groups;
+        const int64_t pg = ranges_for(gg);
+        if (makespan(gg, (int)cdiv(tiles, gg), pg) < makespan(tiles, 1, per)) {
+            groups = gg;
+            gmax = GMAX;
+            per = pg;
+        }
+    }
     G.per_split = per;
     const int64_t nsplit = cdiv(G.P, per);
     int4 *rows = (int4 *)workspace(ctx, "tc.rows", sizeof(int4) * std::max(max_rows, 1));
     int2 *tl = (int2 *)workspace(ctx, "tc.tiles", sizeof(int2) * std::max(tiles, 1));
-    int *n_rows = (int *)workspace(ctx, "tc.n_rows", sizeof(int));
+    int2 *gr = (int2 *)workspace(ctx, "tc.groups", sizeof(int2) * std::max(tiles, 1));
+    int *ctl = (int *)workspace(ctx, "tc.ctl", sizeof(int) * 2);
     double *partial = (double *)workspace(ctx, "tc.partial", sizeof(double) * nsplit * n_trip);
-    if (!rows || !tl || !n_rows || !partial) return fail(ctx, ABS_ERR_OOM, "split-BF16 workspace");
+    if (!rows || !tl || !gr || !ctl || !partial) return fail(ctx, ABS_ERR_OOM, "split-BF16 workspace");
     cudaStream_t st = ctx->stream;
     cudaFuncSetAttribute(k_triple_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     {
         StageTimer timer(ctx, "tc_rows");
         const size_t psmem = sizeof(uint32_t) * (size_t)s.nb * ((s.nb + 31) / 32);
-        k_rows<<<1, 1024, psmem, st>>>(n_trip, s.nb, G.NP, d_ijk, rows, n_rows, tl);
+        k_rows<<<1, 1024, psmem, st>>>(n_trip, s.nb, G.NP, gmax, d_ijk, rows, ctl, tl, gr);
     }
     {
         StageTimer timer(ctx, "triple_tc");
-        k_triple_tc<<<dim3(tiles, (unsigned)nsplit), NT, smem, st>>>(G, fmap, d_fields, rows, tl, n_rows, d_ijk,
-                                                                    partial, ctx->d_err);
+        k_triple_tc<<<dim3(groups, (unsigned)nsplit), NT, smem, st>>>(G, fmap, d_fields, rows, tl, gr, ctl, d_ijk,
+                                                                     partial, ctx->d_err);
     }
     {
         StageTimer timer(ctx, "triple_reduce");
