@@ -20,7 +20,7 @@
 // Tiles are grouped so that a group's accumulators (3 x band columns per
 // tile) fit the 512 columns of tensor memory.  One CTA owns a group of row
 // tiles and a range of pixels, so each field chunk is brought in once for
-// every tile of the group.  The range is streamed in chunks of 64 pixels by
+// every tile of the group.  The range is streamed in chunks of 64-128 pixels by
 // three roles through two rings of shared-memory stages, one of field chunks
 // (deep, so loads run well ahead) and one of operand tiles (one step per
 // chunk and tile):
@@ -34,8 +34,8 @@
 //                  ones 128 B apart, 8-row groups 256 B apart, one 16-column K
 //                  slab after the other) in an operand stage, arrive on
 //                  ab_full and release the field stage (f_empty),
-//   MMA warp       issues the 8 MMAs of a step (4 K-steps x {Ah [Bh; Bl],
-//                  Al Bh}, M = 128, N = 2 band and band, K = 16) into the
+//   MMA warp       issues the MMAs of a step (per 16-pixel K-step Ah [Bh; Bl]
+//                  and Al Bh, M = 128, N = 2 band and band, K = 16) into the
 //                  tile's accumulator columns and commits them to ab_empty,
 //                  which frees the operand stage.
 // At the end the accumulator is read back with tcgen05.ld and each row writes
@@ -59,15 +59,22 @@ namespace absk {
 namespace {
 
 constexpr int TM = 128;          // rows per tile (MMA M)
-constexpr int KC = 64;           // pixels per chunk (4 MMA K-steps)
 constexpr int NPW = 16;          // producer warps
-constexpr int GPR = KC / 8;                             // 8-pixel groups per row of a chunk
-constexpr int KA = TM * GPR / (NPW * 32);               // A units (row, 8 pixels) per producer thread
-constexpr int KB = 256 * (KC / 8) / (NPW * 32);         // B units per producer thread at most (band <= 256)
-static_assert(KA * NPW * 32 == TM * (KC / 8), "A units split evenly over the producers");
 constexpr int LOADER = NPW, ISSUER = NPW + 1;   // the two control warps
 constexpr int NT = (NPW + 2) * 32;
-constexpr int FS = KC + 4;       // field row in a stage (floats; 272 B, a multiple of 16): the TMA box width
+
+// The chunk: KC pixels (KC / 16 MMA K-steps), the widest of 128, 96, 64 whose
+// stages fit shared memory (wider chunks spread the per-step costs, barrier
+// round trips and the MMA commit, over more work).
+template <int KC>
+struct Chunk {
+    static_assert(KC % 32 == 0 && KC <= 128, "whole 16-pixel K-steps; 8-pixel groups; TMA box <= 256");
+    static constexpr int GPR = KC / 8;                       // 8-pixel groups per row of a chunk
+    static constexpr int KA = TM * GPR / (NPW * 32);         // A units (row, 8 pixels) per producer thread
+    static constexpr int KB = 256 * GPR / (NPW * 32);        // B units per producer thread at most (band <= 256)
+    static constexpr int FS = KC + 4;   // field row in a stage (floats, a multiple of 4): the TMA box width
+    static_assert(KA * NPW * 32 == TM * GPR, "A units split evenly over the producers");
+};
 constexpr int MAX_AB = 3, MAX_F = 8;   // operand and field stages
 constexpr int GMAX = 10;         // row tiles per group (3 x 16 accumulator columns each at least)
 constexpr int TMEM_COLS = 512;
@@ -78,10 +85,10 @@ struct TcGeom {
     int nb, NP;                  // rings, largest MMA N (rings rounded up to 16)
     int tmem_cols;               // columns allocated (the group's accumulators fit them)
     int64_t P;                   // pixels
-    int64_t per_split;           // pixels per CTA (multiple of KC)
+    int64_t per_split;           // pixels per CTA (multiple of the chunk)
     int n_trip;
     int sf, sa;                  // field and operand stages
-    int f_bytes, ab_bytes;       // one field stage [nb][FS] floats; one operand stage [Ah][Al][Bh; Bl]
+    int f_bytes, ab_bytes;       // one field stage [nb][KC + 4] floats; one operand stage [Ah][Al][Bh; Bl]
     int a_bytes, b_bytes;        // one A tile (hi or lo); the stacked B tile (2 NP rows)
     int tma;                     // fields by TMA tensor copy (else plain loads by the loader warp)
 };
@@ -210,6 +217,7 @@ __device__ __forceinline__ void mask_tail(float2 *v, int g, int valid) {
     }
 }
 
+template <int KC>
 __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_constant__ CUtensorMap fmap,
                                                      const float *__restrict__ fields,
                                                      const int4 *__restrict__ rows,
@@ -219,6 +227,7 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
                                                      const int32_t *__restrict__ ijk,
                                                      double *__restrict__ partial,
                                                      int32_t *__restrict__ err) {
+    constexpr int GPR = Chunk<KC>::GPR, KA = Chunk<KC>::KA, KB = Chunk<KC>::KB, FS = Chunk<KC>::FS;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t f_full[MAX_F], f_empty[MAX_F], ab_full[MAX_AB], ab_empty[MAX_AB];
     // stages on a 1024-byte boundary (TMA destinations want 128; the launch adds 1 KB of slack)
@@ -756,20 +765,30 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
     G.tmem_cols = TMEM_COLS;
     G.P = (int64_t)s.N * s.N;
     G.n_trip = n_trip;
-    G.a_bytes = TM * KC * 2;
-    G.b_bytes = 2 * G.NP * KC * 2;
-    G.f_bytes = (int)(cdiv((int64_t)s.nb * FS * 4, 1024) * 1024);
-    G.ab_bytes = (int)(cdiv(2 * G.a_bytes + G.b_bytes, 1024) * 1024);
-    // stages: three operand stages if the field ring still gets two, then as many field stages as fit
+    // the chunk: the widest KC whose stages fit, at least two of each ring (three field stages
+    // for the wider chunks); then three operand stages if the field ring keeps its stages,
+    // then as many field stages as fit
     const int64_t budget = 215 * 1024;   // dynamic shared memory, below the 227 KB per CTA with the static part
-    G.sa = MAX_AB;
-    while (G.sa > 2 && budget - (int64_t)G.sa * G.ab_bytes < 2 * (int64_t)G.f_bytes) --G.sa;
-    G.sf = (int)std::min<int64_t>(MAX_F, (budget - (int64_t)G.sa * G.ab_bytes) / G.f_bytes);
     const size_t epi = (size_t)TM * (3 * G.NP + 1) * 4;
-    if (G.sf < 2 || (int64_t)epi > budget)
+    int KC = 0;
+    for (int kc : {128, 96, 64}) {
+        const int min_f = kc > 64 ? 3 : 2;
+        G.a_bytes = TM * kc * 2;
+        G.b_bytes = 2 * G.NP * kc * 2;
+        G.f_bytes = (int)(cdiv((int64_t)s.nb * (kc + 4) * 4, 1024) * 1024);
+        G.ab_bytes = (int)(cdiv(2 * G.a_bytes + G.b_bytes, 1024) * 1024);
+        G.sa = MAX_AB;
+        while (G.sa > 2 && budget - (int64_t)G.sa * G.ab_bytes < min_f * (int64_t)G.f_bytes) --G.sa;
+        G.sf = (int)std::min<int64_t>(MAX_F, (budget - (int64_t)G.sa * G.ab_bytes) / G.f_bytes);
+        if (G.sf >= min_f) {
+            KC = kc;
+            break;
+        }
+    }
+    if (KC == 0 || (int64_t)epi > budget)
         return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 stages do not fit shared memory");
     const size_t smem = 1024 + std::max((size_t)G.sf * G.f_bytes + (size_t)G.sa * G.ab_bytes, epi);
-    // the field chunk as one TMA box (FS pixels x every ring) of the [nb][P] FP32 array; the
+    // the field chunk as one TMA box (KC + 4 pixels x every ring) of the [nb][P] FP32 array; the
     // row pitch P x 4 bytes and the array must be 16-byte aligned, else the loader warp copies
     CUtensorMap fmap;
     memset(&fmap, 0, sizeof fmap);
@@ -778,7 +797,7 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
     if (encode && G.P % 4 == 0 && ((uintptr_t)d_fields & 15) == 0) {
         const cuuint64_t dims[2] = {(cuuint64_t)G.P, (cuuint64_t)s.nb};
         const cuuint64_t strides[1] = {(cuuint64_t)G.P * 4};
-        const cuuint32_t box[2] = {(cuuint32_t)FS, (cuuint32_t)s.nb};
+        const cuuint32_t box[2] = {(cuuint32_t)(KC + 4), (cuuint32_t)s.nb};
         const cuuint32_t estr[2] = {1, 1};
         G.tma = encode(&fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)d_fields, dims, strides, box, estr,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -788,7 +807,7 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
     const int tiles = (int)cdiv(max_rows, TM);
     // Grouped (several tiles share each field chunk) or a group per tile: whichever
     // finishes first by a simple count of CTA waves x work per CTA, in tenths of a
-    // tile's 64-pixel step: per chunk 10 per tile plus 3 for bringing the chunk in,
+    // tile's chunk step: per chunk 10 per tile plus 3 for bringing the chunk in,
     // and 80 per tile for its epilogue (fitted to same-GPU timings of both forms on
     // grids of 144^2 to 576^2 pixels).  Lists given by the caller are not grouped.
     Setup &ms = const_cast<Setup &>(s);
@@ -825,7 +844,8 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
     double *partial = (double *)workspace(ctx, "tc.partial", sizeof(double) * nsplit * n_trip);
     if (!rows || !tl || !gr || !ctl || !partial) return fail(ctx, ABS_ERR_OOM, "split-BF16 workspace");
     cudaStream_t st = ctx->stream;
-    cudaFuncSetAttribute(k_triple_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = KC == 128 ? k_triple_tc<128> : KC == 96 ? k_triple_tc<96> : k_triple_tc<64>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     {
         StageTimer timer(ctx, "tc_rows");
         const size_t psmem = sizeof(uint32_t) * (size_t)s.nb * ((s.nb + 31) / 32);
@@ -833,8 +853,8 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
     }
     {
         StageTimer timer(ctx, "triple_tc");
-        k_triple_tc<<<dim3(groups, (unsigned)nsplit), NT, smem, st>>>(G, fmap, d_fields, rows, tl, gr, ctl, d_ijk,
-                                                                     partial, ctx->d_err);
+        kern<<<dim3(groups, (unsigned)nsplit), NT, smem, st>>>(G, fmap, d_fields, rows, tl, gr, ctl, d_ijk, partial,
+                                                              ctx->d_err);
     }
     {
         StageTimer timer(ctx, "triple_reduce");
