@@ -183,15 +183,18 @@ typedef struct abs_item {
     double *d_ellbar;         /* [n_bins] or NULL */
 } abs_item;
 
-/* Many independent estimates of uneven size in one call, in item order on
- * the context's stream: the batching form of the ensemble of Sec. 3 (many
- * realisations or channels with their own baselines, grids and rings).
- * Every item is validated before any work is queued (ABS_ERR_INVALID_ARG
- * names nothing queued).  On a non-default stream the whole batch is
- * captured as one CUDA graph on its second call with the same items (same
+/* Many independent estimates of uneven size in one call: the batching form
+ * of the ensemble of Sec. 3 (many realisations or channels with their own
+ * baselines, grids and rings).  Every item is validated before any work is
+ * queued (ABS_ERR_INVALID_ARG names nothing queued).  On a non-default
+ * stream the items run concurrently, round-robin over four internal lanes
+ * (streams of the context with workspaces of their own, forked from and
+ * joined back to the context's stream), and the whole batch is captured as
+ * one CUDA graph on its second call with the same items (same
  * configurations and buffer addresses) and replayed from then on; the
- * buffers' contents may change between calls.  Workspaces are shared by the
- * items, sized for the largest. */
+ * buffers' contents may change between calls.  A lane's workspaces are sized
+ * for the largest item it has run.  Output buffers of different items must
+ * not overlap. */
 abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *items);
 
 /* abs_estimate_many from HOST memory: copies h_uv, h_vis to the device,

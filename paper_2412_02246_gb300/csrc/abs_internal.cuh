@@ -92,9 +92,20 @@ struct abs_ctx {
     // whenever a workspace is reallocated (the graphs hold its old address).
     struct Graph { cudaGraphExec_t exec = nullptr; int seen = 0; bool failed = false; };
     std::map<std::string, Graph> graphs;
+    // lanes: child contexts, each with its own streams and workspaces (sharing
+    // this context's device error word), over which abs_estimate_batched runs
+    // its items concurrently; created on first use.  A lane's parent is the
+    // context whose graphs may hold the lane's buffers.
+    abs_ctx *parent = nullptr;
+    std::vector<abs_ctx *> lanes;
+    bool owns_stream = false;
+    cudaEvent_t ev_lane = nullptr;   // a lane's end, joined by the parent
 };
 
 namespace absk {
+
+// Concurrent lanes of abs_estimate_batched (items round-robin over them).
+constexpr int ABS_BATCH_LANES = 4;
 
 // Device error codes latched into ctx->d_err (first one wins).
 enum : int32_t {

@@ -204,6 +204,7 @@ void drop_graphs(abs_ctx *ctx) {
     for (auto &kv : ctx->graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     ctx->graphs.clear();
+    if (ctx->parent) drop_graphs(ctx->parent);   // the parent's graphs hold this lane's buffers
 }
 
 void *workspace(abs_ctx *ctx, const char *name, size_t bytes) {
@@ -424,28 +425,33 @@ abs_status abs_create(abs_ctx **out, int32_t device, void *cuda_stream) {
     return ABS_OK;
 }
 
-abs_status abs_destroy(abs_ctx *ctx) {
-    if (!ctx) return ABS_ERR_INVALID_ARG;
-    {
-        DeviceGuard g(ctx->device);
-        cudaStreamSynchronize(ctx->stream);
-        drop_graphs(ctx);
-        for (auto &kv : ctx->ws) cudaFree(kv.second.p);
-        for (auto &kv : ctx->setups) free_setup(*kv.second);
-        cudaFree(ctx->d_err);
-        if (ctx->side) {
-            cudaStreamSynchronize(ctx->side);
-            cudaStreamDestroy(ctx->side);
-        }
-        if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
-        if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
-        for (auto &p : ctx->pending) {
-            cudaEventDestroy(p.a);
-            cudaEventDestroy(p.b);
-        }
-        for (auto e : ctx->event_pool) cudaEventDestroy(e);
+// Everything a context (or a lane) owns; the device error word only when it is not a lane.
+static void release_ctx(abs_ctx *ctx) {
+    for (abs_ctx *l : ctx->lanes) release_ctx(l);
+    ctx->lanes.clear();
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->side) cudaStreamSynchronize(ctx->side);
+    drop_graphs(ctx);
+    for (auto &kv : ctx->ws) cudaFree(kv.second.p);
+    for (auto &kv : ctx->setups) free_setup(*kv.second);
+    if (!ctx->parent) cudaFree(ctx->d_err);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
+    if (ctx->owns_stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ev_lane) cudaEventDestroy(ctx->ev_lane);
+    for (auto &p : ctx->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
     }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
     delete ctx;
+}
+
+abs_status abs_destroy(abs_ctx *ctx) {
+    if (!ctx || ctx->parent) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    release_ctx(ctx);
     return ABS_OK;
 }
 
@@ -743,10 +749,39 @@ abs_status abs_estimate(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis, cons
     return abs_estimate_many(ctx, cfg, n_vis, d_uv, 1, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar);
 }
 
+// A lane of ctx: its own non-blocking streams and events, the parent's device error word.
+static abs_ctx *make_lane(abs_ctx *ctx) {
+    abs_ctx *l = new abs_ctx;
+    l->device = ctx->device;
+    l->sm_count = ctx->sm_count;
+    l->parent = ctx;
+    l->d_err = ctx->d_err;
+    l->owns_stream = true;
+    if (cudaStreamCreateWithFlags(&l->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&l->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&l->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&l->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&l->ev_lane, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        release_ctx(l);
+        return nullptr;
+    }
+    return l;
+}
+
 abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *items) {
     if (!ctx) return ABS_ERR_INVALID_ARG;
     if (n_items < 0 || (n_items > 0 && !items)) return fail(ctx, ABS_ERR_INVALID_ARG, "n_items < 0 or items NULL");
     DeviceGuard g(ctx->device);
+    // items run round-robin over lanes (concurrent streams with their own workspaces),
+    // except while the stage profiler runs, on the legacy default stream or for one item
+    const int K = (ctx->profiling || !ctx->stream || n_items < 2) ? 1 : std::min<int>(ABS_BATCH_LANES, n_items);
+    while ((int)ctx->lanes.size() < K && K > 1) {
+        abs_ctx *l = make_lane(ctx);
+        if (!l) return fail(ctx, ABS_ERR_OOM, "batch lanes");
+        ctx->lanes.push_back(l);
+    }
+    auto where = [&](int32_t i) { return K > 1 ? ctx->lanes[i % K] : ctx; };
     // validate every item and resolve its setup and triplet list before queuing anything
     std::vector<const Setup *> setups(n_items);
     std::vector<const int32_t *> ijks(n_items);
@@ -754,27 +789,41 @@ abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *i
     for (int32_t i = 0; i < n_items; ++i) {
         abs_status st;
         const abs_item &it = items[i];
-        setups[i] = get_setup(ctx, it.cfg, st);
-        if (!setups[i]) return fail(ctx, st, "item " + std::to_string(i) + ": " + ctx->last_error);
+        abs_ctx *c = where(i);
+        setups[i] = get_setup(c, it.cfg, st);
+        if (!setups[i]) return fail(ctx, st, "item " + std::to_string(i) + ": " + c->last_error);
         ijks[i] = it.d_ijk;
-        if (estimate_args(ctx, *setups[i], it.n_vis, it.d_uv, 1, it.d_vis, it.n_trip, ijks[i]) != ABS_OK)
-            return fail(ctx, ABS_ERR_INVALID_ARG, "item " + std::to_string(i) + ": " + ctx->last_error);
+        if (estimate_args(c, *setups[i], it.n_vis, it.d_uv, 1, it.d_vis, it.n_trip, ijks[i]) != ABS_OK)
+            return fail(ctx, ABS_ERR_INVALID_ARG, "item " + std::to_string(i) + ": " + c->last_error);
         char k[256];
         snprintf(k, sizeof k, "|%p|%lld|%p|%p|%d|%p|%p|%p|%p", (const void *)setups[i], (long long)it.n_vis,
                  (const void *)it.d_uv, (const void *)it.d_vis, it.n_trip, (const void *)ijks[i], (void *)it.d_B,
                  (void *)it.d_count, (void *)it.d_ellbar);
         key += k;
     }
-    char ks[32];
-    snprintf(ks, sizeof ks, "|%p", (const void *)ctx->stream);
+    char ks[48];
+    snprintf(ks, sizeof ks, "|%p|%d", (const void *)ctx->stream, K);
     key += ks;
     return graphed(ctx, key, [&]() {
-        for (int32_t i = 0; i < n_items; ++i) {
-            const abs_item &it = items[i];
-            ABS_CHECK(estimate_many(ctx, *setups[i], it.n_vis, it.d_uv, 1, it.d_vis, it.n_trip, ijks[i], it.d_B,
-                                    it.d_count, it.d_ellbar));
+        if (K > 1) {   // fork: every lane starts after the work queued so far on ctx->stream
+            cudaEventRecord(ctx->ev_fork, ctx->stream);
+            for (int l = 0; l < K; ++l) cudaStreamWaitEvent(ctx->lanes[l]->stream, ctx->ev_fork, 0);
         }
-        return ABS_OK;
+        abs_status st = ABS_OK;
+        for (int32_t i = 0; i < n_items && st == ABS_OK; ++i) {
+            const abs_item &it = items[i];
+            abs_ctx *c = where(i);
+            st = estimate_many(c, *setups[i], it.n_vis, it.d_uv, 1, it.d_vis, it.n_trip, ijks[i], it.d_B,
+                               it.d_count, it.d_ellbar);
+            if (st != ABS_OK && c != ctx) ctx->last_error = "item " + std::to_string(i) + ": " + c->last_error;
+        }
+        if (K > 1) {   // join: ctx->stream waits for every lane
+            for (int l = 0; l < K; ++l) {
+                cudaEventRecord(ctx->lanes[l]->ev_lane, ctx->lanes[l]->stream);
+                cudaStreamWaitEvent(ctx->stream, ctx->lanes[l]->ev_lane, 0);
+            }
+        }
+        return st;
     });
 }
 

@@ -86,16 +86,24 @@ constexpr int DMAX = 11;               // widest digit: 2048 bins
 constexpr int CB = 8;                  // key bits of the cell inside its tile (TS x TS = 2^CB)
 static_assert(TS * TS == 1 << CB, "tile cells must fill CB bits");
 
-__device__ __forceinline__ uint32_t cell_key(const GridGeom &G, float2 p, uint32_t key_none) {
+// Key of position p given its quotients q = (u / dU, v / dU) in binary32, round to nearest.
+__device__ __forceinline__ uint32_t key_from_q(const GridGeom &G, float2 p, float2 q, uint32_t key_none) {
     if (!(isfinite(p.x) && isfinite(p.y))) return key_none;
-    const float qx = __fdiv_rn(p.x, G.du), qy = __fdiv_rn(p.y, G.du);
-    if (!(fabsf(qx) < 1.0e7f && fabsf(qy) < 1.0e7f)) return key_none;
-    const int cx = (int)floorf(__fadd_rn(qx, 0.5f));
-    const int cy = (int)floorf(__fadd_rn(qy, 0.5f));
+    if (!(fabsf(q.x) < 1.0e7f && fabsf(q.y) < 1.0e7f)) return key_none;
+    const int cx = (int)floorf(__fadd_rn(q.x, 0.5f));
+    const int cy = (int)floorf(__fadd_rn(q.y, 0.5f));
     const int kx = cx + G.off, ky = cy + G.off;
     if (kx < 0 || kx >= G.ks || ky < 0 || ky >= G.ks) return key_none;
     const uint32_t tile = (uint32_t)((ky / TS) * G.tt + kx / TS);
     return tile << CB | (uint32_t)((ky % TS) * TS + kx % TS);
+}
+
+__device__ __forceinline__ float2 quotients(const GridGeom &G, float2 p) {
+    return make_float2(__fdiv_rn(p.x, G.du), __fdiv_rn(p.y, G.du));
+}
+
+__device__ __forceinline__ uint32_t cell_key(const GridGeom &G, float2 p, uint32_t key_none) {
+    return key_from_q(G, p, quotients(G, p), key_none);
 }
 
 // One CTA per chunk: the (tile, cell) key of every visibility (key_none for
@@ -487,13 +495,14 @@ __global__ void __launch_bounds__(GT, 3) k_grid(GridGeom G, int64_t n_vis, uint3
     const int64_t nu = cdiv(n_vis, UMAX);
     UnitIn nxt;
     load_unit(nxt, blockIdx.x, nu, n_vis, s_uv, s_idx, warp, lane);
+    float2 vn[2];   // the next unit's visibilities, gathered one unit ahead
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        if (blockIdx.x < nu && warp * 64 + h * 32 + lane < nxt.cnt) vn[h] = vis[nxt.idx[h]];
     for (int64_t u = blockIdx.x; u < nu; u += gridDim.x) {
         const UnitIn cur = nxt;
         const int total = cur.cnt;
-        float2 v[2];   // this unit's visibilities: gathered now, used at staging
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-            if (warp * 64 + h * 32 + lane < total) v[h] = vis[cur.idx[h]];
+        const float2 v[2] = {vn[0], vn[1]};   // this unit's visibilities
         load_unit(nxt, u + gridDim.x, nu, n_vis, s_uv, s_idx, warp, lane);   // in flight during this unit
         __syncthreads();   // previous unit done with the staging buffers
         // keys (the plan's, recomputed from the same positions); invalid items sort last
@@ -504,10 +513,10 @@ __global__ void __launch_bounds__(GT, 3) k_grid(GridGeom G, int64_t n_vis, uint3
             const int t = warp * 64 + h * 32 + lane;
             valid[h] = false;
             if (t < total) {
-                const uint32_t key = cell_key(G, cur.p[h], key_none);
+                q[h] = quotients(G, cur.p[h]);
+                const uint32_t key = key_from_q(G, cur.p[h], q[h], key_none);
                 skey[t] = key;
                 valid[h] = key != key_none;
-                q[h] = make_float2(__fdiv_rn(cur.p[h].x, G.du), __fdiv_rn(cur.p[h].y, G.du));
             }
         }
         __syncthreads();
@@ -568,6 +577,10 @@ __global__ void __launch_bounds__(GT, 3) k_grid(GridGeom G, int64_t n_vis, uint3
                 ((float4 *)(rec + R_V))[0] = make_float4(v[h].x, v[h].x, v[h].y, v[h].y);
             }
         }
+        // the next unit's visibilities: its indices have arrived by now
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (u + gridDim.x < nu && warp * 64 + h * 32 + lane < nxt.cnt) vn[h] = vis[nxt.idx[h]];
         __syncthreads();
         if (on_a) {   // lanes without a footprint cell take no part in the sums
             for (int tk = warp; tk < (int)ntask; tk += nwarps) {
