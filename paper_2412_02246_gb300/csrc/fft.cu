@@ -335,15 +335,36 @@ struct FftLaunch {
     size_t row_smem, col_smem;
 };
 
-FftLaunch fft_launch(const Setup &s) {
+// Lines per CTA for a pass over `lines` lines of each of `npairs` ring pairs:
+// the count that minimises (CTA waves) x (lines per CTA + 2, the fixed cost of
+// a CTA: its twiddles and barriers), a CTA holding two line buffers and the
+// packed twiddles (2N float4) in shared memory and at most four CTAs sharing
+// an SM (registers); both passes are latency-bound at moderate N, so a last,
+// part-filled wave costs a whole one.
+static int lines_per_cta(size_t line, int lines, int npairs, int sm_count) {
+    int best = 1;
+    int64_t best_cost = INT64_MAX;
+    for (int w = 1; w <= 16; ++w) {
+        const size_t smem = line * (2 * w + 2);
+        if (smem > 200 * 1024) break;
+        const int per_sm = (int)std::min<size_t>(4, (228 * 1024) / (smem + 1024));
+        if (per_sm < 1) break;
+        const int64_t ctas = cdiv(lines, w) * (int64_t)npairs;
+        const int64_t cost = cdiv(ctas, (int64_t)sm_count * per_sm) * (w + 2);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = w;
+        }
+    }
+    return best;
+}
+
+FftLaunch fft_launch(const Setup &s, int sm_count) {
     FftLaunch L;
     const size_t line = sizeof(float4) * (size_t)s.N;
-    // lines per CTA: as many as keep the CTA within 48 KB of shared memory, so
-    // that four CTAs share an SM (both passes are latency-bound at moderate N)
-    L.RB = 8;
-    while (L.RB > 1 && line * (2 * L.RB + 2) > 48 * 1024) L.RB >>= 1;
-    L.CW = 16;
-    while (L.CW > 1 && line * (2 * L.CW + 2) > 48 * 1024) L.CW >>= 1;
+    const int npairs = (s.nb + 1) / 2;
+    L.RB = lines_per_cta(line, 2 * s.R + 1, npairs, sm_count);
+    L.CW = lines_per_cta(line, s.N, npairs, sm_count);
     L.row_smem = line * (2 * L.RB + 2);   // two line buffers + the packed twiddles (2N float4)
     L.col_smem = line * (2 * L.CW + 2);
     return L;
@@ -354,7 +375,7 @@ abs_status run_fft(abs_ctx *ctx, const Setup &s, const Src &src, float *d_fields
     if ((int)s.radices.size() > MAXRAD) return fail(ctx, ABS_ERR_UNSUPPORTED, "FFT radix plan too long");
     RingGeom G{s.n, s.half, s.nb, s.N, s.R};
     const FftPlan P = make_plan(s);
-    const FftLaunch L = fft_launch(s);
+    const FftLaunch L = fft_launch(s, ctx->sm_count);
     const int npairs = (s.nb + 1) / 2;
     const size_t wbytes = sizeof(float4) * (size_t)npairs * (2 * s.R + 1) * s.N;
     float4 *W = (float4 *)workspace(ctx, "fft.rows", wbytes);
