@@ -1,9 +1,6 @@
 // Stage 3 (FP32 form) and stage 5: sky-plane triple sums, Eq. estimator_t.
 //
-// S_ijk = N^-2 sum_p D_i(p) D_j(p) D_k(p) for every listed triplet.  Triplets
-// sharing (i, j) form a row; the product D_i D_j is formed once per pixel and
-// row and multiplied into each D_k of the row (the contraction
-// C[(i,j), k] = sum_p (D_i D_j)(p) D_k(p)).
+// S_ijk = N^-2 sum_p D_i(p) D_j(p) D_k(p) for every listed triplet.
 //
 // A CTA owns a contiguous range of pixels, staged in shared memory for all
 // rings (coalesced loads, rows padded so that lanes on different rings read
