@@ -72,21 +72,21 @@ def load_peaks():
 # source file the kernel was built from when it was captured.  A kernel whose
 # source has changed since then reports null.
 MEASURED_TRAFFIC = {
-    "grid": {"bytes": 20331008, "source": "paper_2412_02246_gb300/csrc/grid.cu",
-              "sha256": "2c7ea0823a5637a181d2492bdb68744b705870c3bf80379f0aed717d9bafbe48",
-              "profile": "profiles/k_grid_mwa975k.md"},
-    "fft_rows": {"bytes": 726528, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-                  "sha256": "758edcce293b2d61271b37c5017ca5b6b45c22eb36d1378556ef5c9108a66ef8",
-                  "profile": "profiles/k_fft_rows_mwa975k.md"},
-    "fft_cols": {"bytes": 2884608, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-                  "sha256": "758edcce293b2d61271b37c5017ca5b6b45c22eb36d1378556ef5c9108a66ef8",
-                  "profile": "profiles/k_fft_cols_mwa975k.md"},
-    "triple_fp32": {"bytes": 6663680, "source": "paper_2412_02246_gb300/csrc/triple.cu",
-                     "sha256": "c6b500d5208e4ecb0e37a44871930b539e7b037c5de0dcc9ff5505ce53cf4bbd",
-                     "profile": "profiles/k_triple_fp32_mwa975k.md"},
-    "triple_tc": {"bytes": 6689536, "source": "paper_2412_02246_gb300/csrc/triple_tc.cu",
-                   "sha256": "7d57d71e183ee0da44813b238b3a13fa857abb334a26179ee136e96a5e32a12a",
-                   "profile": "profiles/k_triple_tc_mwa975k.md"},
+    "grid": {"bytes": 20339968, "source": "paper_2412_02246_gb300/csrc/grid.cu",
+           "sha256": "539943939760fab02949cc5c5ee66ecabbae23e6e1a9d1dfd0412cdfe602a6bd",
+           "profile": "profiles/k_grid_mwa975k.md"},
+    "fft_rows": {"bytes": 727040, "source": "paper_2412_02246_gb300/csrc/fft.cu",
+               "sha256": "4018531ce8b946e2673b39353c8b120c9820be9f2875c29d6571a514563597d2",
+               "profile": "profiles/k_fft_rows_mwa975k.md"},
+    "fft_cols": {"bytes": 2884352, "source": "paper_2412_02246_gb300/csrc/fft.cu",
+               "sha256": "4018531ce8b946e2673b39353c8b120c9820be9f2875c29d6571a514563597d2",
+               "profile": "profiles/k_fft_cols_mwa975k.md"},
+    "triple_fp32": {"bytes": 6663424, "source": "paper_2412_02246_gb300/csrc/triple.cu",
+                  "sha256": "e5ba1ce493a091745b046bb163d765859e4711307b0360ff49ab517b9a4e7f62",
+                  "profile": "profiles/k_triple_fp32_mwa975k.md"},
+    "triple_tc": {"bytes": 6707456, "source": "paper_2412_02246_gb300/csrc/triple_tc.cu",
+                "sha256": "49b35175521025485f6aae81e582375d06b827ff22b14b37bff46d5bf574b1af",
+                "profile": "profiles/k_triple_tc_mwa975k.md"},
 }
 
 
