@@ -123,6 +123,50 @@ def test_grid_parity_two_radix_passes(ctx):
     assert_grid_parity(G, W, M, _E, grid_abs_bound(wl.n_grid, wl.du, inp.uv, inp.vis))
 
 
+@pytest.mark.gpu
+def test_precision_config_sampled(ctx):
+    """The full-size precision workload (2048^2 grid, 4M visibilities, 64 rings,
+    ~15k triplets), run as abs_estimate runs it, FP32 and split-BF16, checked
+    on sampled triplets the oracle sums one by one (brute force over the
+    rings' cells: the ten with the fewest cell pairs, ten more spread over
+    the list), and on the mean l of every ring."""
+    inp = inputs(2)
+    wl = inp.wl
+    uv, vis = to_dev(inp.uv), to_dev(synth.vis_as_float2(inp.vis))
+    res = {}
+    for prec in (absmod.ABS_FP32, absmod.ABS_SPLIT_BF16):
+        cfg = absmod.Config.from_workload(wl, precision=prec)
+        B, T, E, ijk = absmod.estimate(cfg, uv, vis, ctx)
+        ctx.sync()
+        res[prec] = (B.cpu().numpy(), T.cpu().numpy(), E.cpu().numpy(), ijk)
+    gr = oracle.grid(wl.n_grid, wl.du, inp.uv, inp.vis)
+    X, f = oracle.mean_grid(gr)
+    q = oracle.ring_q(wl.ell_edges, wl.du)
+    assert np.allclose(res[absmod.ABS_FP32][2], oracle.ellbar(f, q, wl.du), rtol=1e-12, equal_nan=True)
+    ijk = res[absmod.ABS_FP32][3]
+    r2 = (lambda k: np.where(k > wl.n_grid // 2, k - wl.n_grid, k))(np.arange(wl.n_grid))
+    rr = r2[None, :].astype(np.int64) ** 2 + r2[:, None].astype(np.int64) ** 2
+    cells = np.array([((f > 0) & (rr >= q[m]) & (rr < q[m + 1])).sum() for m in range(len(q) - 1)])
+    cost = cells[ijk[:, 0]].astype(np.int64) * cells[ijk[:, 1]]
+    order = np.argsort(cost, kind="stable")
+    sel = [int(t) for t in order[:10]]
+    for p in np.linspace(10, len(order) - 1, 16).astype(int):
+        if cost[order[p]] < 5e6:
+            sel.append(int(order[p]))
+    Bmax = np.nanmax(np.abs(res[absmod.ABS_FP32][0]))
+    for t in sel:
+        i, j, k = (int(x) for x in ijk[t])
+        S, _, Tt = oracle.triple_one(X, f, q, i, j, k)
+        Bref = oracle.normalise(np.array([S]), np.array([Tt]))[0]
+        for prec, tol in ((absmod.ABS_FP32, SUM_TOL), (absmod.ABS_SPLIT_BF16, 3e-4)):
+            Bg, Tg = res[prec][0][t], res[prec][1][t]
+            assert Tg == Tt, (i, j, k, Tg, Tt)
+            if Tt == 0:
+                assert np.isnan(Bg)
+            else:
+                assert abs(Bg - Bref) <= tol * max(abs(Bref), 1e-3 * Bmax), (prec, i, j, k, Bg, Bref)
+
+
 def test_grid_dense_cells(ctx):
     """Thousands of visibilities inside one cell and one tile (runs longer
     than a task, tiles longer than a work unit), next to sparse ones."""
