@@ -270,16 +270,41 @@ class Estimate:
     grid: Grid
 
 
+def literal_weights(gr: Grid, filled: np.ndarray) -> np.ndarray:
+    """W_g = 1 / N_g on filled cells, 0 elsewhere: the I-field weights of Eq. iFT_I as
+    printed, with N_g read as the cell's weight sum (the divisor of X, Sec. 2)."""
+    W = np.zeros(gr.wsum.shape)
+    W[filled > 0] = 1.0 / gr.wsum[filled > 0]
+    return W
+
+
+def normalise_literal(S: np.ndarray, SW: np.ndarray, norm_A: float = 1.0) -> np.ndarray:
+    """B = Re S / (A S_W), NaN where S_W = 0 (Eq. estimator_t with the I fields of Eq. iFT_I)."""
+    S, SW = np.asarray(S), np.asarray(SW, np.float64)
+    B = np.full(len(S), np.nan)
+    ok = SW != 0
+    B[ok] = np.real(S[ok]) / (norm_A * SW[ok])
+    return B
+
+
 def estimate(n, du, ell_edges, uv, vis, kernel="gauss", sigma_cells=1.0, radius_cells=3,
-             norm_A=1.0, ijk=None) -> Estimate:
-    """V -> B for one realisation: Eq. vg, ring membership, closed-triangle sums, Eq. estimator_t."""
+             norm_A=1.0, ijk=None, weight_mode="unitmask") -> Estimate:
+    """V -> B for one realisation: Eq. vg, ring membership, closed-triangle sums, Eq. estimator_t.
+
+    weight_mode "unitmask": the denominator is A T, T the count of closed triangles
+    (unit-mask I fields); "literal": A S_W, S_W the sum of W1 W2 W3 over the closed
+    triangles with W_g = 1 / N_g (Eq. iFT_I as printed)."""
     q = ring_q(ell_edges, du)
     if ijk is None:
         ijk = triplets(q)
     gr = grid(n, du, uv, vis, kernel, sigma_cells, radius_cells)
     X, f = mean_grid(gr)
     S, A, T = triple_bruteforce(X, f, q, ijk)
-    B = normalise(S, T, norm_A)
+    if weight_mode == "literal":
+        SW, _, _ = triple_bruteforce(literal_weights(gr, f), f, q, ijk)
+        B = normalise_literal(S, SW.real, norm_A)
+    else:
+        B = normalise(S, T, norm_A)
     return Estimate(B, S, A, T, ellbar(f, q, du), np.asarray(ijk, np.int32), q, X, f, gr)
 
 

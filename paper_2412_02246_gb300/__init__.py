@@ -26,6 +26,7 @@ ABS_OK, ABS_ERR_INVALID_ARG, ABS_ERR_CUDA, ABS_ERR_OOM, ABS_ERR_TIMEOUT, ABS_ERR
     ABS_ERR_DEVICE = range(7)
 ABS_KERNEL_NGP, ABS_KERNEL_GAUSS = 0, 1
 ABS_FP32, ABS_SPLIT_BF16 = 0, 1
+ABS_W_MEAN_UNITMASK, ABS_W_PAPER_LITERAL = 0, 1
 _STATUS = {0: "ABS_OK", 1: "ABS_ERR_INVALID_ARG", 2: "ABS_ERR_CUDA", 3: "ABS_ERR_OOM",
            4: "ABS_ERR_TIMEOUT", 5: "ABS_ERR_UNSUPPORTED", 6: "ABS_ERR_DEVICE"}
 
@@ -44,7 +45,8 @@ class abs_config(ctypes.Structure):
     _fields_ = [("n_grid", ctypes.c_int32), ("du", ctypes.c_double), ("kernel", ctypes.c_int32),
                 ("sigma_cells", ctypes.c_double), ("radius_cells", ctypes.c_int32),
                 ("n_bins", ctypes.c_int32), ("ell_edges", ctypes.POINTER(ctypes.c_double)),
-                ("n_fft", ctypes.c_int32), ("precision", ctypes.c_int32), ("norm_A", ctypes.c_double)]
+                ("n_fft", ctypes.c_int32), ("precision", ctypes.c_int32), ("norm_A", ctypes.c_double),
+                ("weight_mode", ctypes.c_int32)]
 
 
 class abs_item(ctypes.Structure):
@@ -109,13 +111,15 @@ class Config:
     n_fft: int = 0
     precision: int = ABS_FP32
     norm_A: float = 1.0
+    weight_mode: int = ABS_W_MEAN_UNITMASK
 
     def __post_init__(self):
         self.ell_edges = np.ascontiguousarray(self.ell_edges, np.float64)
         self._c = abs_config(int(self.n_grid), float(self.du), int(self.kernel), float(self.sigma_cells),
                              int(self.radius_cells), len(self.ell_edges) - 1,
                              self.ell_edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                             int(self.n_fft), int(self.precision), float(self.norm_A))
+                             int(self.n_fft), int(self.precision), float(self.norm_A),
+                             int(self.weight_mode))
 
     @property
     def n_bins(self) -> int:

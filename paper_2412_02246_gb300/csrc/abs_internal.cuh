@@ -35,6 +35,7 @@ struct Setup {
     std::vector<int32_t> ijk;     // canonical closing triplets [t][3]
     int precision = ABS_FP32;
     double norm_A = 1.0;
+    int weight_mode = ABS_W_MEAN_UNITMASK;
     // device copies (owned by the context)
     int64_t *d_q = nullptr;
     int64_t *d_lat_off = nullptr;
@@ -141,6 +142,9 @@ abs_status launch_filter_fft(abs_ctx *ctx, const Setup &s, const float *d_grid,
 // applied on the fly), as abs_estimate uses it.
 abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc,
                                  float *d_fields);
+// The I fields of Eq. iFT_I as printed (ABS_W_PAPER_LITERAL): W_g = 1 / (the
+// cell's mirrored weight sum) on filled cells, from the FP64 accumulators.
+abs_status launch_filter_fft_w(abs_ctx *ctx, const Setup &s, const double *acc, float *d_fields);
 // FP64 accumulators [3][n*n] (re, im, w before the mirror) of the last
 // launch_grid_accumulate on this context.  A cell received a contribution
 // exactly when its weight sum is > 0 (every footprint weight is a normal,
@@ -168,6 +172,9 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
 bool scan_u32(abs_ctx *ctx, const uint32_t *in, int64_t len, uint32_t *out, uint32_t *bsum);
 abs_status launch_normalise(abs_ctx *ctx, const Setup &s, int32_t n_trip, const double *d_sum,
                             const int64_t *d_count, double *d_B);
+// B = Re S / (A S_W) (NaN where S_W = 0), the literal denominator of Eq. estimator_t.
+abs_status launch_normalise_w(abs_ctx *ctx, const Setup &s, int32_t n_trip, const double *d_sum,
+                              const double *d_sumw, double *d_B);
 abs_status launch_ellbar(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, double *d_ellbar);
 abs_status launch_check_triplets(abs_ctx *ctx, const Setup &s, int32_t n_trip,
                                  const int32_t *d_ijk);

@@ -111,6 +111,10 @@ abs_status derive_grid(const abs_config *cfg, int64_t *q, int *Rm, int *R_out, i
         return ABS_ERR_INVALID_ARG;
     }
     if (!(cfg->norm_A > 0.0) || !std::isfinite(cfg->norm_A)) { *err = "norm_A must be finite and > 0"; return ABS_ERR_INVALID_ARG; }
+    if (cfg->weight_mode != ABS_W_MEAN_UNITMASK && cfg->weight_mode != ABS_W_PAPER_LITERAL) {
+        *err = "weight_mode must be ABS_W_MEAN_UNITMASK or ABS_W_PAPER_LITERAL";
+        return ABS_ERR_INVALID_ARG;
+    }
     const int nb = cfg->n_bins, half = cfg->n_grid / 2 - 1;
     for (int m = 0; m <= nb; ++m) q[m] = ring_threshold(cfg->ell_edges[m], du);
     if (q[nb] > (int64_t)1 << 40) { *err = "l range too large for the uv grid spacing"; return ABS_ERR_INVALID_ARG; }
@@ -184,6 +188,7 @@ abs_status make_setup(const abs_config *cfg, Setup &s, std::string &err) {
     closing_triplets(s.q, s.ijk);
     s.precision = cfg->precision;
     s.norm_A = cfg->norm_A;
+    s.weight_mode = cfg->weight_mode;
     return ABS_OK;
 }
 
@@ -249,6 +254,7 @@ static std::string setup_key(const abs_config *c) {
     put(&c->n_fft, sizeof c->n_fft);
     put(&c->precision, sizeof c->precision);
     put(&c->norm_A, sizeof c->norm_A);
+    put(&c->weight_mode, sizeof c->weight_mode);
     return k;
 }
 
@@ -593,6 +599,10 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
     const int64_t P = (int64_t)s.N * s.N;
     float *fields = (float *)workspace(ctx, "est.fields", sizeof(float) * (size_t)s.nb * P);
     double *sum = (double *)workspace(ctx, "est.sum", sizeof(double) * std::max(n_trip, 1));
+    const bool literal = s.weight_mode == ABS_W_PAPER_LITERAL;
+    float *ifields = literal ? (float *)workspace(ctx, "est.ifields", sizeof(float) * (size_t)s.nb * P) : nullptr;
+    double *sumw = literal ? (double *)workspace(ctx, "est.sumw", sizeof(double) * std::max(n_trip, 1)) : nullptr;
+    if (literal && (!ifields || !sumw)) return fail(ctx, ABS_ERR_OOM, "estimate workspace");
     int64_t *count = d_count ? d_count : (int64_t *)workspace(ctx, "est.count", sizeof(int64_t) * std::max(n_trip, 1));
     if (!fields || !sum || !count) return fail(ctx, ABS_ERR_OOM, "estimate workspace");
     // the canonical list (d_ijk == NULL at the ABI) was built and checked with the setup
@@ -645,8 +655,19 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
             if (join) cudaStreamWaitEvent(ctx->stream, join, 0);
             return sf;
         }
-        ABS_CHECK(launch_triple_sums(ctx, s, fields, n_trip, d_ijk, sum, count,
-                                     d_B ? d_B + (size_t)r * n_trip : nullptr, join));
+        if (!literal) {
+            ABS_CHECK(launch_triple_sums(ctx, s, fields, n_trip, d_ijk, sum, count,
+                                         d_B ? d_B + (size_t)r * n_trip : nullptr, join));
+            continue;
+        }
+        // Eq. iFT_I as printed: S, then (once: the weights are the baselines') the sums
+        // S_W of the I fields with W_g = 1 / N_g, then B = Re S / (A S_W)
+        abs_status sl = launch_triple_sums(ctx, s, fields, n_trip, d_ijk, sum);
+        if (sl == ABS_OK && r == 0) sl = launch_filter_fft_w(ctx, s, acc, ifields);
+        if (sl == ABS_OK && r == 0) sl = launch_triple_sums(ctx, s, ifields, n_trip, d_ijk, sumw);
+        if (join) cudaStreamWaitEvent(ctx->stream, join, 0);   // the counts are done before the call ends
+        if (sl != ABS_OK) return sl;
+        ABS_CHECK(launch_normalise_w(ctx, s, n_trip, sum, sumw, d_B ? d_B + (size_t)r * n_trip : nullptr));
     }
     return ABS_OK;
 }

@@ -226,6 +226,22 @@ struct GridF64 {   // FP64 accumulators before the mirror (inside abs_estimate)
     }
 };
 
+// Weights of the I fields of Eq. iFT_I as printed: W_g = 1 / N_g on a filled
+// cell, N_g its mirrored weight sum in FP64 (real: N_g = N_-g), the quotient
+// in double-float.
+struct GridW64 {
+    const double *w;
+    __device__ bool value(int64_t cell, int64_t mcell, float4 &x) const {
+        const double ww = w[cell] + w[mcell];
+        if (!(ww > 0.0)) return false;
+        float wh, wl, rh, rl;
+        df_of(ww, wh, wl);
+        df_div(1.f, 0.f, wh, wl, rh, rl);
+        x = make_float4(rh, 0.f, rl, 0.f);
+        return true;
+    }
+};
+
 // Row pass: one CTA per (block of RB rows, ring pair).  W[pair][y + Rmax][N].
 template <class Src>
 __global__ void __launch_bounds__(256) k_fft_rows(RingGeom G, FftPlan P, int RB, const int64_t *__restrict__ q,
@@ -407,6 +423,12 @@ abs_status launch_filter_fft(abs_ctx *ctx, const Setup &s, const float *d_grid, 
 abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc, float *d_fields) {
     const int64_t cells = (int64_t)s.n * s.n;
     GridF64 src{acc, acc + cells, acc + 2 * cells};
+    return run_fft(ctx, s, src, d_fields);
+}
+
+abs_status launch_filter_fft_w(abs_ctx *ctx, const Setup &s, const double *acc, float *d_fields) {
+    const int64_t cells = (int64_t)s.n * s.n;
+    GridW64 src{acc + 2 * cells};
     return run_fft(ctx, s, src, d_fields);
 }
 

@@ -182,6 +182,14 @@ __global__ void k_normalise(int n_trip, double norm_A, const double *__restrict_
     B[t] = c > 0 ? S[t] / (norm_A * (double)c) : nan("");
 }
 
+__global__ void k_normalise_w(int n_trip, double norm_A, const double *__restrict__ S,
+                              const double *__restrict__ SW, double *__restrict__ B) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_trip) return;
+    const double w = SW[t];
+    B[t] = w != 0.0 ? S[t] / (norm_A * w) : nan("");
+}
+
 __global__ void k_check_triplets(int nb, int n_trip, const int32_t *__restrict__ ijk,
                                  int32_t *__restrict__ err) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -257,6 +265,14 @@ static abs_status static_scratch(int dev, double **out) {
     }
     *out = g_static_ptr[dev];
     return ABS_OK;
+}
+
+abs_status launch_normalise_w(abs_ctx *ctx, const Setup &s, int32_t n_trip, const double *d_sum,
+                              const double *d_sumw, double *d_B) {
+    if (n_trip == 0 || !d_B) return ABS_OK;
+    StageTimer timer(ctx, "normalise");
+    k_normalise_w<<<(int)cdiv(n_trip, 256), 256, 0, ctx->stream>>>(n_trip, s.norm_A, d_sum, d_sumw, d_B);
+    return check_launch(ctx, "normalise");
 }
 
 abs_status launch_normalise(abs_ctx *ctx, const Setup &s, int32_t n_trip, const double *d_sum,

@@ -464,6 +464,37 @@ def test_estimate_batched_uneven():
         c.close()
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [(0, SUM_TOL), (1, 3e-4)])
+def test_literal_weight_mode(ctx, prec, tol):
+    """ABS_W_PAPER_LITERAL (Eq. iFT_I as printed): B = Re S / (A S_W) against the
+    oracle, counts still exact, through abs_estimate and abs_estimate_many."""
+    wl = synth.workload(0)
+    cfg = absmod.Config.from_workload(wl, precision=prec, weight_mode=absmod.ABS_W_PAPER_LITERAL)
+    ins = [inputs(0, r) for r in range(2)]
+    uv = ins[0].uv
+    ests = [oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, uv, i.vis, weight_mode="literal") for i in ins]
+    base = oracle_run(("est0r", 0), wl.n_grid, wl.du, wl.ell_edges, uv, ins[0].vis)
+    B, T, E, ijk = absmod.estimate(cfg, to_dev(uv), to_dev(synth.vis_as_float2(ins[0].vis)), ctx)
+    ctx.sync()
+    nt = len(ijk)
+    Bm = torch.empty((2, nt), dtype=torch.float64, device=dev())
+    Tm = torch.empty(nt, dtype=torch.int64, device=dev())
+    Em = torch.empty(cfg.n_bins, dtype=torch.float64, device=dev())
+    vis2 = np.stack([synth.vis_as_float2(i.vis) for i in ins])
+    ctx.abs_estimate_many(cfg, to_dev(uv), to_dev(vis2), nt, None, Bm, Tm, Em)
+    ctx.sync()
+    for Bg, est in ((B.cpu().numpy(), ests[0]), (Bm[0].cpu().numpy(), ests[0]), (Bm[1].cpu().numpy(), ests[1])):
+        assert np.array_equal(np.isnan(Bg), np.isnan(est.B))
+        ok = ~np.isnan(est.B)
+        big = ok & (np.abs(est.B) >= 1e-3 * np.nanmax(np.abs(est.B)))
+        assert (np.abs(Bg[big] - est.B[big]) / np.abs(est.B[big])).max() <= tol
+    assert np.array_equal(T.cpu().numpy(), base.T) and np.array_equal(Tm.cpu().numpy(), base.T)
+    # the literal denominator differs from the unit-mask one on this workload
+    ok = ~np.isnan(base.B)
+    assert not np.allclose(ests[0].B[ok], base.B[ok], rtol=1e-3)
+
+
 def test_counts_deterministic(ctx):
     inp = inputs(1)
     wl = inp.wl

@@ -267,6 +267,62 @@ def test_bruteforce_matches_python_enumeration_tiny():
         assert t1 == T[t] and s1 == pytest.approx(S[t], rel=1e-12, abs=1e-12)
 
 
+def test_literal_weights_reduce_to_counts_and_scale():
+    """Eq. iFT_I as printed: with NGP and every filled cell holding one visibility
+    (N_g = 1), W = 1 and S_W is the integer count T, so the literal B equals the
+    unit-mask B; doubling every visibility's weight (each position entered twice)
+    halves W, so S_W = T / 8 and the literal B is 8 times the unit-mask B (X, the
+    weighted mean, does not change)."""
+    rng = np.random.default_rng(3)
+    n, du = 32, 1.0
+    cells = set()
+    uv = []
+    while len(uv) < 60:   # distinct cells, none the mirror of another
+        c = tuple(int(x) for x in rng.integers(-12, 13, 2))
+        if c == (0, 0) or c in cells or (-c[0], -c[1]) in cells:
+            continue
+        cells.add(c)
+        uv.append(c)
+    uv = np.array(uv, np.float32) + rng.uniform(-0.3, 0.3, (60, 2)).astype(np.float32)
+    vis = (rng.standard_normal(60) + 1j * rng.standard_normal(60)).astype(np.complex64)
+    edges = 2 * np.pi * np.array([2.0, 5.0, 8.0, 11.0, 14.0])
+    e0 = oracle.estimate(n, du, edges, uv, vis, kernel="ngp")
+    e1 = oracle.estimate(n, du, edges, uv, vis, kernel="ngp", weight_mode="literal")
+    gr = oracle.grid(n, du, uv, vis, kernel="ngp")
+    X, f = oracle.mean_grid(gr)
+    W = oracle.literal_weights(gr, f)
+    assert np.all(W[f > 0] == 1.0) and np.all(W[f == 0] == 0.0)
+    ok = e0.T > 0
+    assert ok.sum() > 5
+    assert np.allclose(e1.B[ok], e0.B[ok], rtol=1e-12) and np.all(np.isnan(e1.B[~ok]))
+    uv2, vis2 = np.concatenate([uv, uv]), np.concatenate([vis, vis])
+    e2 = oracle.estimate(n, du, edges, uv2, vis2, kernel="ngp", weight_mode="literal")
+    assert np.allclose(e2.B[ok], 8 * e0.B[ok], rtol=1e-12)
+
+
+def test_literal_sums_match_python_enumeration_tiny():
+    """S_W by brute force equals the pure-Python enumeration of W1 W2 W3 over
+    closed triangles on a tiny grid with uneven weights."""
+    rng = np.random.default_rng(11)
+    n = 14
+    filled = full_mask(n)
+    gx, gy = coords(n)
+    drop = rng.random((n, n)) < 0.2
+    filled[drop] = 0
+    filled[(-gy[drop]) % n, (-gx[drop]) % n] = 0
+    w = rng.uniform(0.5, 3.0, (n, n))
+    w = 0.5 * (w + w[(-gy) % n, (-gx) % n])            # N_g = N_-g, as the mirror makes it
+    W = np.where(filled > 0, 1.0 / w, 0.0)
+    edges = 2 * np.pi * np.array([1.2, 2.6, 4.0, 5.7])
+    q = oracle.ring_q(edges, 1.0)
+    allc = np.array(list(itertools.product(range(3), repeat=3)), np.int32)
+    SW, _, T = oracle.triple_bruteforce(W.astype(np.complex128), filled, q, allc)
+    Sp, Tp = python_enumeration(W.astype(np.complex128), filled, q)
+    for t, (i, j, k) in enumerate(allc):
+        assert SW[t] == pytest.approx(Sp.get((i, j, k), 0), rel=1e-12, abs=1e-12)
+        assert abs(SW[t].imag) == 0.0
+
+
 def test_fft_identity_and_aliasing():
     # Sec. 2: sum_theta D_i D_j D_k (Eq. iFT) equals N^2 times the sum over closed
     # grid triangles when the sky grid is large enough (N >= 3R+1) to exclude
