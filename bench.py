@@ -76,13 +76,13 @@ MEASURED_TRAFFIC = {
            "sha256": "539943939760fab02949cc5c5ee66ecabbae23e6e1a9d1dfd0412cdfe602a6bd",
            "profile": "profiles/k_grid_mwa975k.md"},
     "fft_rows": {"bytes": 727040, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-               "sha256": "4018531ce8b946e2673b39353c8b120c9820be9f2875c29d6571a514563597d2",
+               "sha256": "53962c14d4a81a6b77a25e6f3491cd430ac01bd45befdb1bcb73fec3c25e3b02",
                "profile": "profiles/k_fft_rows_mwa975k.md"},
     "fft_cols": {"bytes": 2884352, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-               "sha256": "4018531ce8b946e2673b39353c8b120c9820be9f2875c29d6571a514563597d2",
+               "sha256": "53962c14d4a81a6b77a25e6f3491cd430ac01bd45befdb1bcb73fec3c25e3b02",
                "profile": "profiles/k_fft_cols_mwa975k.md"},
     "triple_fp32": {"bytes": 6663424, "source": "paper_2412_02246_gb300/csrc/triple.cu",
-                  "sha256": "e5ba1ce493a091745b046bb163d765859e4711307b0360ff49ab517b9a4e7f62",
+                  "sha256": "9d2104ec79e0019fa0c5dd2937d8d28d0fd2758fd8ab1aaeabc0e456d091bd3b",
                   "profile": "profiles/k_triple_fp32_mwa975k.md"},
     "triple_tc": {"bytes": 6707456, "source": "paper_2412_02246_gb300/csrc/triple_tc.cu",
                 "sha256": "49b35175521025485f6aae81e582375d06b827ff22b14b37bff46d5bf574b1af",
