@@ -298,16 +298,39 @@ def workload_geometry(m, cfg, ctx, uv, vis, ijk, N, wl, dev, torch):
         hi = max(kr[r][1] for r in tile)
         band_sum += -(-(hi - lo + 1) // 16) * 16
     nb = cfg.n_bins
-    npairs = (nb + 1) // 2
-    R = int(np.floor(np.sqrt(float(q[-1] - 1))))
     P = N * N
-    fft_rows_bytes = npairs * (2 * R + 1) * N * 16 + int((mask > 0).sum()) * 24
-    fft_cols_bytes = npairs * (2 * R + 1) * N * 16 + nb * P * 4
+    # transforms: the column pass reads the ring cells' FP64 sums (re, im, w) and writes
+    # 2 R_pair + 1 transformed columns of N points per ring pair; the row pass reads them
+    # back and writes every field.  Points are double-float complex (16 B) on the FP32
+    # path, FP32 complex (8 B) on the split-BF16 path.
+    rm = ring_rmax(q, n // 2 - 1)
+    lines = sum(2 * max(rm[a], rm[a + 1] if a + 1 < nb else -1) + 1 for a in range(0, nb, 2)
+                if max(rm[a], rm[a + 1] if a + 1 < nb else -1) >= 0)
+    pt = 8 if cfg.precision == m.ABS_SPLIT_BF16 else 16
+    fft_cols_bytes = int(c.sum()) * 24 + lines * N * pt
+    fft_rows_bytes = lines * N * pt + nb * P * 4
     return {"pair_visits": int(visits), "n_trip": len(ijk), "P": P, "n_vis": len(uv),
             "footprint": (2 * cfg.radius_cells + 1) ** 2,
             "tc_band_sum": band_sum,
             "bytes": {"fft_rows": fft_rows_bytes, "fft_cols": fft_cols_bytes,
                       "ring_lists": n * n * 2}}
+
+
+def ring_rmax(q, half):
+    """Per ring, the largest |g_x| of a lattice cell on the grid (-1: no cell), as the library derives it."""
+    import math
+    out = []
+    for a in range(len(q) - 1):
+        lo, hi, r = int(q[a]), int(q[a + 1]) - 1, -1
+        if hi >= lo:
+            for x in range(min(half, math.isqrt(hi)), -1, -1):
+                ylo = math.isqrt(lo - x * x - 1) + 1 if lo - x * x > 0 else 0
+                yhi = min(half, math.isqrt(hi - x * x))
+                if ylo <= yhi:
+                    r = x
+                    break
+        out.append(r)
+    return out
 
 
 def run_ours(args):

@@ -5,11 +5,12 @@
 // Because X_m is Hermitian, D_m is real, so two rings a, b are transformed at
 // once as Z = X_a + i X_b, giving D_a = Re FFT(Z) and D_b = Im FFT(Z).
 //
-// The 2D transform is a row pass then a column pass.  Only the rows
-// |g_y| <= R_b of a ring pair are nonzero, so the row pass transforms just
-// those rows into a compact intermediate [2R+1][N]; the column pass reads CW
-// adjacent columns of it, expands each to length N with the zero rows, and
-// writes CW columns of both fields.
+// The 2D transform is a column pass then a row pass.  Only the columns
+// |g_x| <= R_b of a ring pair are nonzero, so the column pass transforms
+// just those columns (along y) into a compact intermediate [2R+1][N]; the
+// row pass reads RB adjacent sky rows of it, expands each to length N with
+// the zero columns, transforms along x and writes RB whole rows of both
+// fields, so the dominant write (the fields) is contiguous.
 //
 // Arithmetic.  Rounding inside an FP32 FFT leaves an error of order
 // eps log N ||X|| on every output, independent of the output's size, and
@@ -17,7 +18,11 @@
 // field to FP32 once costs far less.  The butterflies therefore run in
 // double-float: every real is an unevaluated sum hi + lo of two FP32 values
 // (Dekker/Knuth two-sum and FMA two-product), twiddles and radix constants
-// carry their own low parts, and only the output is rounded to FP32.
+// carry their own low parts, and only the output is rounded to FP32.  That
+// is the FP32 path.  The split-BF16 path rounds its triplet operands to
+// about 2^-17 relative anyway, far above the plain FP32 transform's error,
+// so its butterflies run in plain packed FP32 (float2 complex values, half
+// the intermediate's bytes) with each cell's value rounded once on entry.
 //
 // Both passes are radix-2/3/4/5 Stockham transforms in shared memory (pass
 // with span p and radix R reads x[i + q N/R], applies the twiddle
@@ -101,10 +106,73 @@ __device__ __forceinline__ pdf pconst(double v) {
     return {f2(h, h), f2(l, l)};
 }
 
+// The two arithmetics of the butterflies.  DF: double-float complex values
+// stored as float4, twiddles as two float4 per index (the packed layout of
+// Setup::d_tw).  F32: plain FP32 complex values stored as float2 (re, im),
+// twiddles as one float4 (c, c, -s, s) per index, staged from the high parts.
+struct ArithDF {
+    using E = float4;
+    using C = pdf;
+    static constexpr int TW = 2;   // float4 twiddle entries per index
+    __device__ static C ld(E v) { return ::absk::ld(v); }
+    __device__ static E st(C a) { return ::absk::st(a); }
+    __device__ static C add(C a, C b) { return p_add(a, b); }
+    __device__ static C sub(C a, C b) { return p_sub(a, b); }
+    __device__ static C mi(C a) { return c_mi(a); }
+    __device__ static C half(C a) { return p_half(a); }
+    __device__ static C cst(double v) { return pconst(v); }
+    __device__ static C mul(C a, C c) { return p_mul(a, c); }
+    __device__ static C twiddle(C v, const float4 *tw, int t) {
+        return c_mul_tw(v, ::absk::ld(tw[2 * t]), ::absk::ld(tw[2 * t + 1]));
+    }
+    __device__ static void stage_tw(float4 *tw, const float4 *__restrict__ tw_g, int N) {
+        for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) tw[i] = tw_g[i];
+    }
+    // a cell value (re.hi, im.hi, re.lo, im.lo) as stored, and i times it
+    __device__ static E from_cell(float4 v) { return v; }
+    __device__ static E times_i(float4 v) { return make_float4(-v.y, v.x, -v.w, v.z); }
+    __device__ static E zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+    __device__ static float re(E v) { return __fadd_rn(v.x, v.z); }
+    __device__ static float im(E v) { return __fadd_rn(v.y, v.w); }
+};
+
+struct ArithF32 {
+    using E = float2;
+    using C = float2;
+    static constexpr int TW = 1;
+    __device__ static C ld(E v) { return v; }
+    __device__ static E st(C a) { return a; }
+    __device__ static C add(C a, C b) { return __fadd2_rn(a, b); }
+    __device__ static C sub(C a, C b) { return f2sub(a, b); }
+    __device__ static C mi(C a) { return f2(a.y, -a.x); }
+    __device__ static C half(C a) { return __fmul2_rn(a, f2(0.5f, 0.5f)); }
+    __device__ static C cst(double v) { return f2((float)v, (float)v); }
+    __device__ static C mul(C a, C c) { return __fmul2_rn(a, c); }
+    // v w = v (c, c) + (v.im, v.re) (-s, s)
+    __device__ static C twiddle(C v, const float4 *tw, int t) {
+        const float4 w = tw[t];
+        return __ffma2_rn(f2(v.y, v.x), f2(w.z, w.w), __fmul2_rn(v, f2(w.x, w.y)));
+    }
+    __device__ static void stage_tw(float4 *tw, const float4 *__restrict__ tw_g, int N) {
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const float4 c = tw_g[2 * i], sn = tw_g[2 * i + 1];
+            tw[i] = make_float4(c.x, c.y, sn.x, sn.y);
+        }
+    }
+    // the cell value rounded once to FP32
+    __device__ static E from_cell(float4 v) { return f2(__fadd_rn(v.x, v.z), __fadd_rn(v.y, v.w)); }
+    __device__ static E times_i(float4 v) { return f2(-__fadd_rn(v.y, v.w), __fadd_rn(v.x, v.z)); }
+    __device__ static E zero() { return f2(0.f, 0.f); }
+    __device__ static float re(E v) { return v.x; }
+    __device__ static float im(E v) { return v.y; }
+};
+
 // One Stockham pass over `lines` transforms of length N stored line-major.
-__device__ __forceinline__ void stockham_pass(const float4 *__restrict__ in, float4 *__restrict__ out,
+template <class A>
+__device__ __forceinline__ void stockham_pass(const typename A::E *__restrict__ in, typename A::E *__restrict__ out,
                                               int N, const FftPass &P, int lines,
                                               const float4 *__restrict__ tw) {
+    using C = typename A::C;
     const int R = P.R, p = P.p, T = P.T;
     const int nbf = lines * T;
     for (int b = threadIdx.x; b < nbf; b += blockDim.x) {
@@ -112,59 +180,59 @@ __device__ __forceinline__ void stockham_pass(const float4 *__restrict__ in, flo
         const int i = b - l * T;
         const int ip = p == 1 ? i : (int)__umulhi((uint32_t)i, P.mag_p);
         const int k = i - ip * p;
-        const float4 *src = in + (size_t)l * N + i;
-        float4 *dst = out + (size_t)l * N + ip * p * R + k;
-        pdf x[5];
-        x[0] = ld(src[0]);
+        const typename A::E *src = in + (size_t)l * N + i;
+        typename A::E *dst = out + (size_t)l * N + ip * p * R + k;
+        C x[5];
+        x[0] = A::ld(src[0]);
 #pragma unroll
         for (int q = 1; q < 5; ++q) {
             if (q < R) {
-                const pdf v = ld(src[q * T]);
-                const int ti = 2 * q * k * P.tstep;
-                x[q] = k ? c_mul_tw(v, ld(tw[ti]), ld(tw[ti + 1])) : v;
+                const C v = A::ld(src[q * T]);
+                x[q] = k ? A::twiddle(v, tw, q * k * P.tstep) : v;
             }
         }
         if (R == 4) {
-            const pdf a0 = p_add(x[0], x[2]), a1 = p_sub(x[0], x[2]);
-            const pdf b0 = p_add(x[1], x[3]), b1 = c_mi(p_sub(x[1], x[3]));
-            dst[0] = st(p_add(a0, b0));
-            dst[p] = st(p_add(a1, b1));
-            dst[2 * p] = st(p_sub(a0, b0));
-            dst[3 * p] = st(p_sub(a1, b1));
+            const C a0 = A::add(x[0], x[2]), a1 = A::sub(x[0], x[2]);
+            const C b0 = A::add(x[1], x[3]), b1 = A::mi(A::sub(x[1], x[3]));
+            dst[0] = A::st(A::add(a0, b0));
+            dst[p] = A::st(A::add(a1, b1));
+            dst[2 * p] = A::st(A::sub(a0, b0));
+            dst[3 * p] = A::st(A::sub(a1, b1));
         } else if (R == 2) {
-            dst[0] = st(p_add(x[0], x[1]));
-            dst[p] = st(p_sub(x[0], x[1]));
+            dst[0] = A::st(A::add(x[0], x[1]));
+            dst[p] = A::st(A::sub(x[0], x[1]));
         } else if (R == 3) {
-            const pdf t = p_add(x[1], x[2]);
-            const pdf m = p_sub(x[0], p_half(t));
-            const pdf d = p_mul(c_mi(p_sub(x[1], x[2])), pconst(kS3));
-            dst[0] = st(p_add(x[0], t));
-            dst[p] = st(p_add(m, d));
-            dst[2 * p] = st(p_sub(m, d));
+            const C t = A::add(x[1], x[2]);
+            const C m = A::sub(x[0], A::half(t));
+            const C d = A::mul(A::mi(A::sub(x[1], x[2])), A::cst(kS3));
+            dst[0] = A::st(A::add(x[0], t));
+            dst[p] = A::st(A::add(m, d));
+            dst[2 * p] = A::st(A::sub(m, d));
         } else {  // R == 5
-            const pdf c1 = pconst(kC1), c2 = pconst(kC2), s1 = pconst(kS1), s2 = pconst(kS2);
-            const pdf t1 = p_add(x[1], x[4]), t2 = p_add(x[2], x[3]);
-            const pdf t3 = p_sub(x[1], x[4]), t4 = p_sub(x[2], x[3]);
-            const pdf a1 = p_add(x[0], p_add(p_mul(t1, c1), p_mul(t2, c2)));
-            const pdf a2 = p_add(x[0], p_add(p_mul(t1, c2), p_mul(t2, c1)));
-            const pdf b1 = c_mi(p_add(p_mul(t3, s1), p_mul(t4, s2)));
-            const pdf b2 = c_mi(p_sub(p_mul(t3, s2), p_mul(t4, s1)));
-            dst[0] = st(p_add(x[0], p_add(t1, t2)));
-            dst[p] = st(p_add(a1, b1));
-            dst[4 * p] = st(p_sub(a1, b1));
-            dst[2 * p] = st(p_add(a2, b2));
-            dst[3 * p] = st(p_sub(a2, b2));
+            const C c1 = A::cst(kC1), c2 = A::cst(kC2), s1 = A::cst(kS1), s2 = A::cst(kS2);
+            const C t1 = A::add(x[1], x[4]), t2 = A::add(x[2], x[3]);
+            const C t3 = A::sub(x[1], x[4]), t4 = A::sub(x[2], x[3]);
+            const C a1 = A::add(x[0], A::add(A::mul(t1, c1), A::mul(t2, c2)));
+            const C a2 = A::add(x[0], A::add(A::mul(t1, c2), A::mul(t2, c1)));
+            const C b1 = A::mi(A::add(A::mul(t3, s1), A::mul(t4, s2)));
+            const C b2 = A::mi(A::sub(A::mul(t3, s2), A::mul(t4, s1)));
+            dst[0] = A::st(A::add(x[0], A::add(t1, t2)));
+            dst[p] = A::st(A::add(a1, b1));
+            dst[4 * p] = A::st(A::sub(a1, b1));
+            dst[2 * p] = A::st(A::add(a2, b2));
+            dst[3 * p] = A::st(A::sub(a2, b2));
         }
     }
 }
 
 // Transforms `lines` lines in buffer a (scratch b); returns the buffer holding the result.
-__device__ float4 *fft_lines(float4 *a, float4 *b, int lines, const FftPlan &P,
-                             const float4 *__restrict__ tw) {
+template <class A>
+__device__ typename A::E *fft_lines(typename A::E *a, typename A::E *b, int lines, const FftPlan &P,
+                                    const float4 *__restrict__ tw) {
     for (int s = 0; s < P.nrad; ++s) {
         __syncthreads();
-        stockham_pass(a, b, P.N, P.pass[s], lines, tw);
-        float4 *t = a;
+        stockham_pass<A>(a, b, P.N, P.pass[s], lines, tw);
+        typename A::E *t = a;
         a = b;
         b = t;
     }
@@ -242,28 +310,31 @@ struct GridW64 {
     }
 };
 
-// Row pass: one CTA per (block of RB rows, ring pair).  W[pair][y + Rmax][N].
-template <class Src>
-__global__ void __launch_bounds__(256) k_fft_rows(RingGeom G, FftPlan P, int RB, const int64_t *__restrict__ q,
+// Column pass: one CTA per (block of CB columns x, ring pair), transforming
+// along y the 2R+1 columns |x| <= R that hold ring cells.  W[pair][x + Rmax][N].
+template <class Src, class A>
+__global__ void __launch_bounds__(256) k_fft_cols(RingGeom G, FftPlan P, int CB, const int64_t *__restrict__ q,
                                                   const int32_t *__restrict__ Rm, Src src,
                                                   const float4 *__restrict__ tw_g,
-                                                  float4 *__restrict__ W) {
+                                                  typename A::E *__restrict__ W) {
+    using E = typename A::E;
     extern __shared__ float4 sbuf[];
     const int pair = blockIdx.y;
     const int a = 2 * pair, b = a + 1 < G.nb ? a + 1 : -1;
     const int Rp = max(Rm[a], b >= 0 ? Rm[b] : -1);
-    const int y0 = (int)blockIdx.x * RB - G.Rmax;
-    if (Rp < 0 || y0 > Rp || y0 + RB - 1 < -Rp) return;
+    const int x0 = (int)blockIdx.x * CB - G.Rmax;
+    if (Rp < 0 || x0 > Rp || x0 + CB - 1 < -Rp) return;
     float4 *tw = sbuf;
-    float4 *l0 = sbuf + 2 * G.N, *l1 = l0 + (size_t)RB * G.N;
-    for (int i = threadIdx.x; i < 2 * G.N; i += blockDim.x) tw[i] = tw_g[i];
-    for (int i = threadIdx.x; i < RB * G.N; i += blockDim.x) l0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    E *l0 = (E *)(sbuf + A::TW * G.N), *l1 = l0 + (size_t)CB * G.N;
+    A::stage_tw(tw, tw_g, G.N);
+    for (int i = threadIdx.x; i < CB * G.N; i += blockDim.x) l0[i] = A::zero();
     __syncthreads();
     const int span = 2 * Rp + 1;
     const int64_t qa0 = q[a], qa1 = q[a + 1], qb0 = b >= 0 ? q[b] : 0, qb1 = b >= 0 ? q[b + 1] : 0;
-    for (int e = threadIdx.x; e < RB * span; e += blockDim.x) {
-        const int r = e / span, x = e - r * span - Rp, y = y0 + r;
-        if (y < -Rp || y > Rp || y < -G.half || y > G.half || x < -G.half || x > G.half) continue;
+    // consecutive threads take consecutive x of one row (adjacent cells)
+    for (int e = threadIdx.x; e < CB * span; e += blockDim.x) {
+        const int yy = e / CB, c = e - yy * CB, x = x0 + c, y = yy - Rp;
+        if (x < -Rp || x > Rp || y < -G.half || y > G.half || x < -G.half || x > G.half) continue;
         const int64_t r2 = (int64_t)x * x + (int64_t)y * y;
         const bool in_a = r2 >= qa0 && r2 < qa1, in_b = b >= 0 && r2 >= qb0 && r2 < qb1;
         if (!in_a && !in_b) continue;
@@ -271,56 +342,59 @@ __global__ void __launch_bounds__(256) k_fft_rows(RingGeom G, FftPlan P, int RB,
         const int64_t mcell = (int64_t)(y > 0 ? G.n - y : -y) * G.n + (x > 0 ? G.n - x : -x);
         float4 v;
         if (!src.value(cell, mcell, v)) continue;
-        // Z = X_a + i X_b (i (re + i im) = -im + i re)
-        l0[(size_t)r * G.N + (x < 0 ? x + G.N : x)] = in_a ? v : make_float4(-v.y, v.x, -v.w, v.z);
+        // Z = X_a + i X_b
+        l0[(size_t)c * G.N + (y < 0 ? y + G.N : y)] = in_a ? A::from_cell(v) : A::times_i(v);
     }
-    float4 *res = fft_lines(l0, l1, RB, P, tw);
-    for (int e = threadIdx.x; e < RB * G.N; e += blockDim.x) {
-        const int r = e / G.N, y = y0 + r;
-        if (y < -Rp || y > Rp) continue;
-        W[((size_t)pair * (2 * G.Rmax + 1) + (y + G.Rmax)) * G.N + (e - r * G.N)] = res[e];
+    E *res = fft_lines<A>(l0, l1, CB, P, tw);
+    for (int e = threadIdx.x; e < CB * G.N; e += blockDim.x) {
+        const int c = e / G.N, x = x0 + c;
+        if (x < -Rp || x > Rp) continue;
+        W[((size_t)pair * (2 * G.Rmax + 1) + (x + G.Rmax)) * G.N + (e - c * G.N)] = res[e];
     }
 }
 
-// Column pass: one CTA per (CW-column tile, ring pair).
-__global__ void __launch_bounds__(256) k_fft_cols(RingGeom G, FftPlan P, int CW,
+// Row pass: one CTA per (block of RB sky rows py, ring pair), transforming
+// along x; each output row of both fields is written whole (contiguous).
+template <class A>
+__global__ void __launch_bounds__(256) k_fft_rows(RingGeom G, FftPlan P, int RB,
                                                   const int32_t *__restrict__ Rm,
-                                                  const float4 *__restrict__ W,
+                                                  const typename A::E *__restrict__ W,
                                                   const float4 *__restrict__ tw_g,
                                                   float *__restrict__ fields) {
+    using E = typename A::E;
     extern __shared__ float4 sbuf[];
     const int pair = blockIdx.y;
     const int a = 2 * pair, b = a + 1 < G.nb ? a + 1 : -1;
     const int Rp = max(Rm[a], b >= 0 ? Rm[b] : -1);
-    const int x0 = blockIdx.x * CW;
-    const int cw = min(CW, G.N - x0);
+    const int py0 = blockIdx.x * RB;
+    const int rb = min(RB, G.N - py0);
     const size_t P2 = (size_t)G.N * G.N;
+    float *fa = fields + (size_t)a * P2 + (size_t)py0 * G.N;
+    float *fb = b >= 0 ? fields + (size_t)b * P2 + (size_t)py0 * G.N : nullptr;
     if (Rp < 0) {  // both rings empty: zero fields
-        for (int i = threadIdx.x; i < G.N * cw; i += blockDim.x) {
-            const int py = i / cw, c = i - py * cw;
-            fields[(size_t)a * P2 + (size_t)py * G.N + x0 + c] = 0.f;
-            if (b >= 0) fields[(size_t)b * P2 + (size_t)py * G.N + x0 + c] = 0.f;
+        for (int i = threadIdx.x; i < rb * G.N; i += blockDim.x) {
+            fa[i] = 0.f;
+            if (fb) fb[i] = 0.f;
         }
         return;
     }
     float4 *tw = sbuf;
-    float4 *l0 = sbuf + 2 * G.N, *l1 = l0 + (size_t)CW * G.N;
-    for (int i = threadIdx.x; i < 2 * G.N; i += blockDim.x) tw[i] = tw_g[i];
-    for (int i = threadIdx.x; i < CW * G.N; i += blockDim.x) l0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    E *l0 = (E *)(sbuf + A::TW * G.N), *l1 = l0 + (size_t)RB * G.N;
+    A::stage_tw(tw, tw_g, G.N);
+    for (int i = threadIdx.x; i < RB * G.N; i += blockDim.x) l0[i] = A::zero();
     __syncthreads();
-    const int rows = 2 * Rp + 1;
-    const float4 *src = W + (size_t)pair * (2 * G.Rmax + 1) * G.N;
-    for (int i = threadIdx.x; i < rows * cw; i += blockDim.x) {
-        const int row = i / cw, c = i - row * cw;
-        const int y = row - Rp;
-        l0[(size_t)c * G.N + (y < 0 ? y + G.N : y)] = src[(size_t)(y + G.Rmax) * G.N + x0 + c];
+    const int cols = 2 * Rp + 1;
+    const E *src = W + (size_t)pair * (2 * G.Rmax + 1) * G.N;
+    for (int i = threadIdx.x; i < cols * rb; i += blockDim.x) {
+        const int col = i / rb, r = i - col * rb;
+        const int x = col - Rp;
+        l0[(size_t)r * G.N + (x < 0 ? x + G.N : x)] = src[(size_t)(x + G.Rmax) * G.N + py0 + r];
     }
-    float4 *res = fft_lines(l0, l1, CW, P, tw);
-    for (int i = threadIdx.x; i < G.N * cw; i += blockDim.x) {
-        const int py = i / cw, c = i - py * cw;
-        const float4 v = res[(size_t)c * G.N + py];
-        fields[(size_t)a * P2 + (size_t)py * G.N + x0 + c] = __fadd_rn(v.x, v.z);
-        if (b >= 0) fields[(size_t)b * P2 + (size_t)py * G.N + x0 + c] = __fadd_rn(v.y, v.w);
+    E *res = fft_lines<A>(l0, l1, RB, P, tw);
+    for (int i = threadIdx.x; i < rb * G.N; i += blockDim.x) {
+        const E v = res[i];
+        fa[i] = A::re(v);
+        if (fb) fb[i] = A::im(v);
     }
 }
 
@@ -347,23 +421,23 @@ FftPlan make_plan(const Setup &s) {
 }
 
 struct FftLaunch {
-    int RB, CW;
-    size_t row_smem, col_smem;
+    int CB, RB;   // columns per CTA of the column pass, rows per CTA of the row pass
+    size_t col_smem, row_smem;
 };
 
 // Lines per CTA for a pass over `lines` lines of each of `npairs` ring pairs:
 // the count that minimises (CTA waves) x (lines per CTA + 2, the fixed cost of
 // a CTA: its twiddles and barriers), a CTA holding two line buffers and the
-// packed twiddles (2N float4) in shared memory and at most four CTAs sharing
-// an SM (registers); both passes are latency-bound at moderate N, so a last,
-// part-filled wave costs a whole one.
-static int lines_per_cta(size_t line, int lines, int npairs, int sm_count) {
+// twiddles (two lines' worth) in shared memory and at most max_per_sm CTAs
+// sharing an SM (registers); both passes are latency-bound at moderate N, so
+// a last, part-filled wave costs a whole one.
+static int lines_per_cta(size_t line, int lines, int npairs, int sm_count, int max_per_sm) {
     int best = 1;
     int64_t best_cost = INT64_MAX;
     for (int w = 1; w <= 16; ++w) {
         const size_t smem = line * (2 * w + 2);
         if (smem > 200 * 1024) break;
-        const int per_sm = (int)std::min<size_t>(4, (228 * 1024) / (smem + 1024));
+        const int per_sm = (int)std::min<size_t>(max_per_sm, (228 * 1024) / (smem + 1024));
         if (per_sm < 1) break;
         const int64_t ctas = cdiv(lines, w) * (int64_t)npairs;
         const int64_t cost = cdiv(ctas, (int64_t)sm_count * per_sm) * (w + 2);
@@ -375,41 +449,56 @@ static int lines_per_cta(size_t line, int lines, int npairs, int sm_count) {
     return best;
 }
 
+// The transforms run in double-float on the FP32 path and in plain FP32 on the
+// split-BF16 path, whose triplet products carry a larger error of their own.
+static bool plain_fp32(const Setup &s) { return s.precision == ABS_SPLIT_BF16; }
+
 FftLaunch fft_launch(const Setup &s, int sm_count) {
     FftLaunch L;
-    const size_t line = sizeof(float4) * (size_t)s.N;
+    const bool f32 = plain_fp32(s);
+    const size_t line = (f32 ? sizeof(float2) : sizeof(float4)) * (size_t)s.N;
     const int npairs = (s.nb + 1) / 2;
-    L.RB = lines_per_cta(line, 2 * s.R + 1, npairs, sm_count);
-    L.CW = lines_per_cta(line, s.N, npairs, sm_count);
-    L.row_smem = line * (2 * L.RB + 2);   // two line buffers + the packed twiddles (2N float4)
-    L.col_smem = line * (2 * L.CW + 2);
+    const int per_sm = f32 ? 8 : 4;   // 256 threads at 32 / 60 registers
+    L.CB = lines_per_cta(line, 2 * s.R + 1, npairs, sm_count, per_sm);
+    L.RB = lines_per_cta(line, s.N, npairs, sm_count, per_sm);
+    L.col_smem = line * (2 * L.CB + 2);   // two line buffers + the twiddles
+    L.row_smem = line * (2 * L.RB + 2);
     return L;
+}
+
+template <class Src, class A>
+abs_status run_fft_as(abs_ctx *ctx, const Setup &s, const Src &src, float *d_fields) {
+    using E = typename A::E;
+    RingGeom G{s.n, s.half, s.nb, s.N, s.R};
+    const FftPlan P = make_plan(s);
+    const FftLaunch L = fft_launch(s, ctx->sm_count);
+    const int npairs = (s.nb + 1) / 2;
+    const size_t wbytes = sizeof(E) * (size_t)npairs * (2 * s.R + 1) * s.N;
+    E *W = (E *)workspace(ctx, "fft.rows", wbytes);
+    if (!W) return fail(ctx, ABS_ERR_OOM, "FFT row workspace");
+    if (L.row_smem > 227 * 1024 || L.col_smem > 227 * 1024)
+        return fail(ctx, ABS_ERR_UNSUPPORTED, "FFT lines do not fit shared memory");
+    cudaStream_t st = ctx->stream;
+    cudaFuncSetAttribute(k_fft_cols<Src, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.col_smem);
+    cudaFuncSetAttribute(k_fft_rows<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.row_smem);
+    {
+        StageTimer timer(ctx, "fft_cols");
+        k_fft_cols<Src, A><<<dim3((unsigned)cdiv(2 * s.R + 1, L.CB), npairs), 256, L.col_smem, st>>>(
+            G, P, L.CB, s.d_q, s.d_Rm, src, (const float4 *)s.d_tw, W);
+    }
+    {
+        StageTimer timer(ctx, "fft_rows");
+        k_fft_rows<A><<<dim3((unsigned)cdiv(s.N, L.RB), npairs), 256, L.row_smem, st>>>(
+            G, P, L.RB, s.d_Rm, W, (const float4 *)s.d_tw, d_fields);
+    }
+    return check_launch(ctx, "filter+FFT");
 }
 
 template <class Src>
 abs_status run_fft(abs_ctx *ctx, const Setup &s, const Src &src, float *d_fields) {
     if ((int)s.radices.size() > MAXRAD) return fail(ctx, ABS_ERR_UNSUPPORTED, "FFT radix plan too long");
-    RingGeom G{s.n, s.half, s.nb, s.N, s.R};
-    const FftPlan P = make_plan(s);
-    const FftLaunch L = fft_launch(s, ctx->sm_count);
-    const int npairs = (s.nb + 1) / 2;
-    const size_t wbytes = sizeof(float4) * (size_t)npairs * (2 * s.R + 1) * s.N;
-    float4 *W = (float4 *)workspace(ctx, "fft.rows", wbytes);
-    if (!W) return fail(ctx, ABS_ERR_OOM, "FFT row workspace");
-    cudaStream_t st = ctx->stream;
-    cudaFuncSetAttribute(k_fft_rows<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.row_smem);
-    cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.col_smem);
-    {
-        StageTimer timer(ctx, "fft_rows");
-        k_fft_rows<Src><<<dim3((unsigned)cdiv(2 * s.R + 1, L.RB), npairs), 256, L.row_smem, st>>>(
-            G, P, L.RB, s.d_q, s.d_Rm, src, (const float4 *)s.d_tw, W);
-    }
-    {
-        StageTimer timer(ctx, "fft_cols");
-        k_fft_cols<<<dim3((unsigned)cdiv(s.N, L.CW), npairs), 256, L.col_smem, st>>>(
-            G, P, L.CW, s.d_Rm, W, (const float4 *)s.d_tw, d_fields);
-    }
-    return check_launch(ctx, "filter+FFT");
+    return plain_fp32(s) ? run_fft_as<Src, ArithF32>(ctx, s, src, d_fields)
+                         : run_fft_as<Src, ArithDF>(ctx, s, src, d_fields);
 }
 
 }  // namespace

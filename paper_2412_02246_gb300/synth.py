@@ -24,6 +24,11 @@ not available):
   samples of a rotation of `track_deg` degrees in the uv plane (a flat
   stand-in for Earth-rotation synthesis).
 
+* multi-channel workload: 32 channels evenly over 139-169 MHz share one
+  sky (the quadratic diffuse field plus 2,000 point sources on map pixels
+  with dN/dS ~ S^-1.6 over S in [1, 1000]) and one baseline set drawn at
+  154.25 MHz, scaled by nu / 154.25 MHz per channel; noise per channel.
+
 All randomness is drawn from numpy's PCG64 seeded per workload and
 realisation.
 """
@@ -80,7 +85,11 @@ def _log_edges(lo, hi, n):
 
 
 def workload(cfg_id: int) -> Workload:
-    """The five workload shapes (tiny, MWA-shaped, precision, batch item, channel)."""
+    """The workload shapes: tiny (0), MWA-shaped (1), precision (2), multi-channel (4).
+
+    The uneven batch items (3) come from `batch_item`; the channels of the
+    multi-channel workload from `channel_inputs`.
+    """
     if cfg_id == 0:
         return Workload("tiny-64sq-5k-8lin", 64, 2.0, _lin_edges(25.0, 375.0, 8),
                         map_side=64, layout="annulus", n_vis=5000, u_min=4.0, u_max=60.0)
@@ -92,6 +101,13 @@ def workload(cfg_id: int) -> Workload:
         return Workload("precision-2048sq-4M-64log", 2048, 1.15, _log_edges(46.0, 1320.0, 64),
                         map_side=2048, layout="array", n_ant=128, n_time=0, n_vis=4_000_000,
                         u_min=7.0, u_max=220.0, precision="split_bf16")
+    if cfg_id == 4:
+        return Workload("channels-4096sq-10M-128log", 4096, 0.6, _log_edges(46.0, 1320.0, 128),
+                        map_side=4096, layout="array", n_ant=128, n_time=0, n_vis=10_000_000,
+                        u_min=7.0, u_max=220.0, precision="split_bf16",
+                        extra={"n_chan": 32, "nu_lo_mhz": 139.0, "nu_hi_mhz": 169.0,
+                               "nu_ref_mhz": 154.25, "n_src": 2000, "src_slope": 1.6,
+                               "s_min": 1.0, "s_max": 1000.0})
     raise ValueError(f"unknown workload id {cfg_id}")
 
 
@@ -237,6 +253,65 @@ def make_inputs(cfg_id: int, realisation: int = 0, wl: Workload | None = None,
     rs = np.random.Generator(np.random.PCG64(seed_for(cfg_id, 1 + realisation)))
     vis = make_visibilities(wl, uv, rs)
     return Inputs(uv=uv, vis=vis, ell_edges=np.asarray(wl.ell_edges, np.float64), wl=wl)
+
+
+# ------------------------------------------------------------------ channels
+
+
+def channel_freqs_mhz(wl: Workload) -> np.ndarray:
+    """Channel centre frequencies, evenly spaced over [nu_lo, nu_hi] (end points included)."""
+    e = wl.extra
+    return np.linspace(e["nu_lo_mhz"], e["nu_hi_mhz"], e["n_chan"])
+
+
+def point_sources(m: int, rng: np.random.Generator, n_src: int, slope: float, s_min: float,
+                  s_max: float) -> np.ndarray:
+    """n_src sources on uniformly drawn pixels of an m x m map, fluxes drawn from
+    dN/dS ~ S^-slope on [s_min, s_max] by inverting the cumulative count."""
+    a = 1.0 - slope
+    u = rng.uniform(0.0, 1.0, n_src)
+    flux = (s_min ** a + u * (s_max ** a - s_min ** a)) ** (1.0 / a)
+    img = np.zeros((m, m))
+    np.add.at(img, (rng.integers(0, m, n_src), rng.integers(0, m, n_src)), flux)
+    return img
+
+
+_channel_sky: dict = {}
+
+
+def channel_sky_modes(wl: Workload, realisation: int = 0) -> np.ndarray:
+    """Fourier modes of the multi-channel sky: the quadratic diffuse field of the
+    other workloads plus point sources (one flat-spectrum sky for every channel).
+    The last one made is kept, since every channel reads it."""
+    key = (wl.name, realisation)
+    if key not in _channel_sky:
+        _channel_sky.clear()
+        e = wl.extra
+        rng = np.random.Generator(np.random.PCG64(seed_for(4, 1 + realisation)))
+        delta = quadratic_sky(gaussian_field(wl.map_side, rng, wl.alpha), wl.f_ng)
+        delta += point_sources(wl.map_side, rng, e["n_src"], e["src_slope"], e["s_min"], e["s_max"])
+        _channel_sky[key] = sky_modes(delta)
+    return _channel_sky[key]
+
+
+def channel_inputs(channel: int, realisation: int = 0, wl: Workload | None = None) -> Inputs:
+    """Seeded (U, V) of one channel of the multi-channel workload.
+
+    One set of baselines is drawn at the reference frequency and scaled by
+    nu / nu_ref in every channel (a baseline's length in wavelengths grows
+    with frequency); the sky is shared, the noise is drawn per channel.
+    """
+    wl = workload(4) if wl is None else wl
+    nu = channel_freqs_mhz(wl)[channel]
+    rb = np.random.Generator(np.random.PCG64(seed_for(4, 0)))
+    uv = make_baselines(wl, rb).astype(np.float64) * (nu / wl.extra["nu_ref_mhz"])
+    uv = uv.astype(np.float32)
+    v = bilinear(channel_sky_modes(wl, realisation), uv.astype(np.float64) / np.float64(wl.du))
+    rn = np.random.Generator(np.random.PCG64(seed_for(4, 500 + channel + 100 * realisation)))
+    rms = np.sqrt(np.mean(np.abs(v) ** 2))
+    s = wl.noise_frac * rms / np.sqrt(2.0)
+    v = v + s * (rn.standard_normal(v.shape) + 1j * rn.standard_normal(v.shape))
+    return Inputs(uv=uv, vis=v.astype(np.complex64), ell_edges=np.asarray(wl.ell_edges, np.float64), wl=wl)
 
 
 def vis_as_float2(vis: np.ndarray) -> np.ndarray:

@@ -167,6 +167,94 @@ def test_precision_config_sampled(ctx):
                 assert abs(Bg - Bref) <= tol * max(abs(Bref), 1e-3 * Bmax), (prec, i, j, k, Bg, Bref)
 
 
+def _sampled_triplets(wl, f, q, ijk, n_cheap=10, n_spread=16, n_empty=2, max_pairs=5e6):
+    """Triplets the oracle can sum one by one: those with the fewest filled
+    cell pairs (a few empty ones first), and some spread over the list."""
+    n = wl.n_grid
+    r2 = np.where(np.arange(n) > n // 2, np.arange(n) - n, np.arange(n)).astype(np.int64)
+    rr = r2[None, :] ** 2 + r2[:, None] ** 2
+    cells = np.array([((f > 0) & (rr >= q[m]) & (rr < q[m + 1])).sum() for m in range(len(q) - 1)])
+    cost = cells[ijk[:, 0]].astype(np.int64) * cells[ijk[:, 1]] * (cells[ijk[:, 2]] > 0)
+    order = np.argsort(cost, kind="stable")
+    empty = [int(t) for t in order[:n_empty] if cost[t] == 0]
+    live = order[cost[order] > 0]
+    sel = empty + [int(t) for t in live[:n_cheap]]
+    for p in np.linspace(n_cheap, len(live) - 1, n_spread).astype(int):
+        if cost[live[p]] < max_pairs:
+            sel.append(int(live[p]))
+    return sel
+
+
+@pytest.mark.gpu
+def test_channels_config_sampled(ctx):
+    """The multi-channel workload at full size (4096^2 grid, 1e7 visibilities
+    per channel, 128 rings, ~109k triplets, N = 1080, split-BF16): four
+    channels in one abs_estimate_batched call equal abs_estimate channel by
+    channel; the first and last channel against the oracle on sampled
+    triplets (brute force per triplet; counts exact) and on the mean l of
+    every ring, the first channel also through the FP32 path."""
+    wl = synth.workload(4)
+    cfg = absmod.Config.from_workload(wl)
+    assert cfg.precision == absmod.ABS_SPLIT_BF16
+    ijk = absmod.abs_triplets(cfg)
+    nt = len(ijk)
+    chans = (0, 11, 20, 31)
+    items, host = [], {}
+    for ch in chans:
+        inp = synth.channel_inputs(ch, wl=wl)
+        if ch in (0, 31):
+            host[ch] = inp
+        outs = (torch.full((nt,), -1.0, dtype=torch.float64, device=dev()),
+                torch.full((nt,), -1, dtype=torch.int64, device=dev()),
+                torch.full((cfg.n_bins,), -1.0, dtype=torch.float64, device=dev()))
+        items.append((cfg, to_dev(inp.uv), to_dev(synth.vis_as_float2(inp.vis)), nt, None) + outs)
+    ctx.abs_estimate_batched(items)
+    single = []
+    for it in items:
+        B = torch.empty(nt, dtype=torch.float64, device=dev())
+        T = torch.empty(nt, dtype=torch.int64, device=dev())
+        E = torch.empty(cfg.n_bins, dtype=torch.float64, device=dev())
+        ctx.abs_estimate(cfg, it[1], it[2], nt, None, B, T, E)
+        single.append((B, T, E))
+    cfg32 = absmod.Config.from_workload(wl, precision=absmod.ABS_FP32)
+    B32, T32, E32, _ = absmod.estimate(cfg32, items[0][1], items[0][2], ctx)
+    ctx.sync()
+    res = {}
+    for ch, it, (rB, rT, rE) in zip(chans, items, single):
+        gB, gT, gE = (o.cpu().numpy() for o in it[5:])
+        rB, rT, rE = rB.cpu().numpy(), rT.cpu().numpy(), rE.cpu().numpy()
+        assert np.array_equal(gT, rT)
+        assert np.allclose(gE, rE, rtol=1e-12, atol=0, equal_nan=True)
+        assert np.array_equal(np.isnan(gB), np.isnan(rB))
+        ok = ~np.isnan(rB)
+        assert ok.sum() > nt // 2
+        assert np.allclose(gB[ok], rB[ok], rtol=1e-9, atol=1e-12 * np.abs(rB[ok]).max())
+        res[ch] = {absmod.ABS_SPLIT_BF16: (gB, gT, gE)}
+    res[0][absmod.ABS_FP32] = (B32.cpu().numpy(), T32.cpu().numpy(), E32.cpu().numpy())
+    q = oracle.ring_q(wl.ell_edges, wl.du)
+    for ch, inp in host.items():
+        gr = oracle.grid(wl.n_grid, wl.du, inp.uv, inp.vis)
+        X, f = oracle.mean_grid(gr)
+        del gr
+        el = oracle.ellbar(f, q, wl.du)
+        sel = _sampled_triplets(wl, f, q, ijk)
+        assert len(sel) >= 20
+        Bmax = np.nanmax(np.abs(res[ch][absmod.ABS_SPLIT_BF16][0]))
+        for t in sel:
+            i, j, k = (int(x) for x in ijk[t])
+            S, _, Tt = oracle.triple_one(X, f, q, i, j, k)
+            Bref = oracle.normalise(np.array([S]), np.array([Tt]))[0]
+            for prec, (gB, gT, gE) in res[ch].items():
+                tol = SUM_TOL if prec == absmod.ABS_FP32 else 3e-4
+                assert np.allclose(gE, el, rtol=1e-12, equal_nan=True)
+                assert gT[t] == Tt, (ch, prec, i, j, k, gT[t], Tt)
+                if Tt == 0:
+                    assert np.isnan(gB[t])
+                else:
+                    assert abs(gB[t] - Bref) <= tol * max(abs(Bref), 1e-3 * Bmax), (ch, prec, i, j, k,
+                                                                                      gB[t], Bref)
+
+
 def test_grid_dense_cells(ctx):
     """Thousands of visibilities inside one cell and one tile (runs longer
     than a task, tiles longer than a work unit), next to sparse ones."""
@@ -221,11 +309,16 @@ def gpu_fields(ctx, cfg, gwm):
     return f
 
 
-@pytest.mark.parametrize("cfg_id,n_fft", [(0, 0), (0, 96), (0, 135), (1, 0)])
-def test_fields_parity(ctx, cfg_id, n_fft):
+@pytest.mark.parametrize("cfg_id,n_fft,prec", [(0, 0, 0), (0, 96, 0), (0, 135, 0), (1, 0, 0),
+                                               (0, 0, 1), (0, 135, 1), (1, 0, 1)])
+def test_fields_parity(ctx, cfg_id, n_fft, prec):
+    """Ring fields of abs_filter_fft: double-float butterflies on the FP32 path
+    (prec 0), plain FP32 ones on the split-BF16 path (prec 1), both within
+    1e-5 of the DFT bound sum |X|."""
     inp = inputs(cfg_id)
     wl = inp.wl
-    cfg = absmod.Config.from_workload(wl, n_fft=n_fft)
+    cfg = absmod.Config.from_workload(wl, n_fft=n_fft,
+                                      precision=absmod.ABS_SPLIT_BF16 if prec else absmod.ABS_FP32)
     est = oracle_run(("est", cfg_id), wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
     _, _, _, gwm = gpu_grid(ctx, cfg, inp.uv, inp.vis)
     f = gpu_fields(ctx, cfg, gwm).cpu().numpy().astype(np.float64)
