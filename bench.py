@@ -232,11 +232,105 @@ def uneven_batch(n_items, dev):
     return {"items": items}
 
 
+def multichannel(args, m, synth, torch, dev, stream, peaks_sm):
+    """The multi-channel workload: args.channels channels spread over 139-169 MHz (4096^2 grid,
+    1e7 visibilities, 128 log rings, split-BF16), one abs_estimate_batched call over all of them,
+    timed as channels/s; then each channel once more through abs_estimate with the stage profiler
+    for the large-size rooflines (transforms, split-BF16 triplets, exact counts)."""
+    if args.channels <= 0:
+        return None
+    wl = synth.workload(4)
+    cfg = m.Config.from_workload(wl)
+    ijk = m.abs_triplets(cfg)
+    nt, N = len(ijk), m.abs_fft_size(cfg)
+    nch = wl.extra["n_chan"]
+    chans = sorted({int(round(x)) for x in np.linspace(0, nch - 1, args.channels)})
+    ctx = m.Context(dev.index or 0, stream)
+    items = []
+    for ch in chans:
+        inp = synth.channel_inputs(ch, wl=wl)
+        items.append((cfg, torch.from_numpy(inp.uv).to(dev), torch.from_numpy(synth.vis_as_float2(inp.vis)).to(dev),
+                      nt, None, torch.empty(nt, dtype=torch.float64, device=dev),
+                      torch.empty(nt, dtype=torch.int64, device=dev),
+                      torch.empty(cfg.n_bins, dtype=torch.float64, device=dev)))
+    for _ in range(2):                         # eager (setups, workspaces), then graph capture
+        ctx.abs_estimate_batched(items)
+    ctx.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.abs_estimate_batched(items)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    # per-channel stage times (eager, one channel at a time) and the work each stage did
+    ctx.profile(True)
+    visits = 0
+    for it in items:
+        ctx.abs_estimate(cfg, it[1], it[2], nt, None, *it[5:])
+    torch.cuda.synchronize(dev)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    n = cfg.n_grid
+    q = m.abs_ring_q(cfg)
+    mk = torch.empty((n, n), dtype=torch.uint8, device=dev)
+    g = torch.empty((n, n, 2), dtype=torch.float32, device=dev)
+    w = torch.empty((n, n), dtype=torch.float32, device=dev)
+    fills = 0
+    for it in items:
+        ctx.abs_grid(cfg, it[1], it[2], g, w, mk)
+        ctx.sync()
+        A, F = ring_census(mk.cpu().numpy(), q, n)
+        visits += count_route_visits(A, F)
+        fills += int(F.sum())
+    ctx.close()
+    per = {k: 1e3 * v[0] / len(items) for k, v in prof.items()}   # us per channel
+    rm = ring_rmax(q, n // 2 - 1)
+    nb = cfg.n_bins
+    lines = sum(2 * r + 1 for r in (max(rm[a], rm[a + 1] if a + 1 < nb else -1) for a in range(0, nb, 2)) if r >= 0)
+    P = N * N
+    hbm = load_peaks()
+    kr = {}
+    for i, j, k in ijk.tolist():
+        lo, hi = kr.get((i, j), (1 << 30, -1))
+        kr[(i, j)] = (min(lo, k), max(hi, k))
+    by_j = sorted(kr, key=lambda ij: (ij[1], ij[0]))
+    band = 0
+    for t in range(0, len(by_j), 128):
+        tile = by_j[t:t + 128]
+        band += -(-(max(kr[r][1] for r in tile) - min(kr[r][0] for r in tile) + 1) // 16) * 16
+    out = {"value": len(items) * 1e3 / ms, "unit": "channels/s", "channels": chans,
+           "ms_per_call": ms, "n_trip": nt, "n_fft": N,
+           "stages_us_per_channel": {k: round(v, 1) for k, v in sorted(per.items())}}
+
+    def frac(ach, peak):
+        return {"achieved": ach, "peak": peak, "frac": ach / peak}
+    if "fft_rows" in per:
+        out["fft_rows"] = dict(frac((lines * N * 8 + nb * P * 4) / (per["fft_rows"] * 1e-6) / 1e9,
+                                    hbm["hbm_gbs"]), bound="hbm", unit="GB/s")
+    if "fft_cols" in per:
+        out["fft_cols"] = dict(frac((fills * 24 / len(items) + lines * N * 8) / (per["fft_cols"] * 1e-6) / 1e9,
+                                    hbm["hbm_gbs"]), bound="hbm", unit="GB/s")
+    if "triple_tc" in per:
+        out["triple_tc"] = dict(frac(2.0 * 128 * 3 * band * P / (per["triple_tc"] * 1e-6) / 1e12,
+                                     hbm["bf16_tflops"]), bound="tensor", unit="TFLOP/s",
+                                useful_tflops=2.0 * nt * P / (per["triple_tc"] * 1e-6) / 1e12)
+    if "count_pairs" in per:
+        out["count_pairs"] = {"pair_visits_per_channel": visits // len(items),
+                              "gvisits_per_s": visits / len(items) / (per["count_pairs"] * 1e-6) / 1e9}
+    out["note"] = ("4096^2 grid, 1e7 visibilities, 128 log rings over l 46-1320, split-BF16, one baseline set "
+                   "scaled by frequency; value = channels / device time of one abs_estimate_batched call "
+                   "(inputs resident); stage times from one eager abs_estimate per channel")
+    return out
+
+
 def roofline_for(stage, avg_ms, geo, peaks):
     """Algorithmic work of one launch of `stage` over its average duration.
 
     grid:        FP32 lane-ops, 4 per (visibility, footprint cell): w = wx wy, two FMAs, one add
-    count_pairs: integer pair visits x 2 lane-ops (index add, ring compare)
+    count_pairs: integer pair visits (of the route the kernel takes) x 2 lane-ops (index add, ring
+                 compare); a grid with no holes takes the holes route with no visits at all
     triple_fp32: 2 flops per (triplet, pixel)
     triple_tc:   executed BF16 tensor flops: per 128-row tile 2 M N K with M = 128, N = 3 x its ring
                  band (the stacked [Bh; Bl] MMA and the Al Bh MMA), K = pixels
@@ -250,7 +344,8 @@ def roofline_for(stage, avg_ms, geo, peaks):
         out = {"bound": "alu", "achieved": ops / s / 1e12, "peak": lane_ops / 1e12, "unit": "Tlane-op/s"}
     elif stage == "count_pairs":
         ops = 2.0 * geo["pair_visits"]
-        out = {"bound": "alu", "achieved": ops / s / 1e12, "peak": lane_ops / 1e12, "unit": "Tlane-op/s"}
+        out = {"bound": "alu", "achieved": ops / s / 1e12, "peak": lane_ops / 1e12, "unit": "Tlane-op/s",
+               "pair_visits": geo["pair_visits"]}
     elif stage == "triple_fp32":
         fl = 2.0 * geo["n_trip"] * geo["P"]
         out = {"bound": "alu", "achieved": fl / s / 1e12, "peak": 2 * lane_ops / 1e12, "unit": "TFLOP/s"}
@@ -278,13 +373,8 @@ def workload_geometry(m, cfg, ctx, uv, vis, ijk, N, wl, dev, torch):
     ctx.sync()
     mask = mk.cpu().numpy()
     q = m.abs_ring_q(cfg)
-    k = np.arange(n)
-    k = np.where(k > n // 2, k - n, k)
-    gy, gx = np.meshgrid(k, k, indexing="ij")
-    r2 = gx.astype(np.int64) ** 2 + gy.astype(np.int64) ** 2
-    c = np.array([int(((mask > 0) & (r2 >= q[b]) & (r2 < q[b + 1])).sum()) for b in range(cfg.n_bins)])
-    rows = sorted({(int(i), int(j)) for i, j, _ in ijk})
-    visits = sum((c[i] // 2) * c[j] for i, j in rows)
+    A, c = ring_census(mask, q, n)
+    visits = count_route_visits(A, c)
     # the split-BF16 kernel's row tiles: rows by (j, i), 128 a tile, each with its band of k rounded to 16
     kr = {}
     for i, j, kk in ijk:
@@ -314,6 +404,32 @@ def workload_geometry(m, cfg, ctx, uv, vis, ijk, N, wl, dev, torch):
             "tc_band_sum": band_sum,
             "bytes": {"fft_rows": fft_rows_bytes, "fft_cols": fft_cols_bytes,
                       "ring_lists": n * n * 2}}
+
+
+def ring_census(mask, q, n):
+    """Lattice cells (A) and filled cells (F) of every ring on an n x n FFT-ordered grid."""
+    k = np.arange(n, dtype=np.int64)
+    k = np.where(k > n // 2, k - n, k)
+    on = np.abs(k) <= n // 2 - 1
+    r2 = k[None, :] ** 2 + k[:, None] ** 2
+    inr = (r2 >= q[0]) & (r2 < q[-1]) & on[None, :] & on[:, None]
+    ring = np.searchsorted(np.asarray(q), r2[inr], side="right") - 1
+    nb = len(q) - 1
+    A = np.bincount(ring, minlength=nb)
+    F = np.bincount(ring[mask[inr] > 0], minlength=nb)
+    return A.astype(np.int64), F.astype(np.int64)
+
+
+def count_route_visits(A, F):
+    """Pair visits of the exact count kernel, which takes the cheaper of its two routes: the
+    direct enumeration of the filled cells, sum over a <= b of floor(F_a / 2) F_b, or the
+    holes route (H = A - F), sum over a <= b of floor(H_a / 2) A_b + 2 floor(F_a / 2) H_b
+    (the full-annulus table it subtracts from is computed once per configuration)."""
+    H = A - F
+    tail = lambda v: np.cumsum(v[::-1])[::-1]          # sum over b >= a
+    direct = int(np.sum((F // 2) * tail(F)))
+    holes = int(np.sum((H // 2) * tail(A) + 2 * (F // 2) * tail(H)))
+    return holes if holes < direct else direct
 
 
 def ring_rmax(q, half):
@@ -441,6 +557,9 @@ def run_ours(args):
         uneven = len(bi["items"]) * reps_u / (e0.elapsed_time(e1) * 1e-3)
         del bi
 
+    chan = multichannel(args, m, synth, torch, dev, stream, peaks_sm=(torch.cuda.get_device_properties(dev)
+                                                                      .multi_processor_count))
+
     # end to end through the host-buffer entry point (pinned buffers, copies inside)
     huv = torch.from_numpy(inp.uv).pin_memory()
     hvis = torch.from_numpy(synth.vis_as_float2(inp.vis)).pin_memory()
@@ -509,7 +628,8 @@ def run_ours(args):
     for k in ("grid", "fft_rows", "fft_cols", "count_pairs", "triple_fp32"):
         if k in stages and k != dom:
             rr = roofline_for(k, stages[k]["avg_us"] * 1e-3, geo, peaks)
-            other_roofs[k] = {kk: rr[kk] for kk in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+            other_roofs[k] = {kk: rr[kk] for kk in ("bound", "achieved", "peak", "unit", "frac", "traffic",
+                                                    "pair_visits") if kk in rr}
     tri_fp32 = roofline_for("triple_fp32", stages["triple_fp32"]["avg_us"] * 1e-3, geo, peaks)
     tc_avg = 1e3 * prof_tc["triple_tc"][0] / max(prof_tc["triple_tc"][1], 1)
     tri_tc = roofline_for("triple_tc", tc_avg * 1e-3, geo, peaks)
@@ -540,6 +660,7 @@ def run_ours(args):
                        "triple_tc_frac_bf16_peak": tri_tc["frac"],
                        "triple_tc_traffic": tri_tc["traffic"],
                        "triple_useful_tflops": useful / (tc_avg * 1e-6) / 1e12},
+        "multichannel": chan,
         "fp32": {"triple_fp32_us": round(stages["triple_fp32"]["avg_us"], 2),
                  "triple_useful_tflops": useful / (stages["triple_fp32"]["avg_us"] * 1e-6) / 1e12,
                  "frac_fp32_simt_peak": tri_fp32["frac"]},
@@ -560,6 +681,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--batch-items", type=int, default=64, help="items of the uneven batch (0: skip it)")
+    ap.add_argument("--channels", type=int, default=8,
+                    help="channels of the multi-channel workload, spread over the band (0: skip it)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -42,7 +42,8 @@ struct Setup {
     int64_t *d_ring_off = nullptr;  // [3][nb+1] family f, ring m: f * up_off[nb] + up_off[m]
     int32_t *d_ijk = nullptr;
     float4 *d_tw = nullptr;       // exp(-2 pi i t / N) = c + i s, t < N, as packed double-float pairs:
-                                  // [2t] = (c.hi, c.hi, c.lo, c.lo), [2t+1] = (-s.hi, s.hi, -s.lo, s.lo)
+                                  // [2t] = (c.hi, c.hi, c.lo, c.lo), [2t+1] = (-s.hi, s.hi, -s.lo, s.lo),
+                                  // then in FP32: [2N + t] = (c, c, -s, s)
     int32_t *d_Rm = nullptr;
     // ordered closed-triangle counts of the full annuli [nb][nb][nb] (halved),
     // a property of the ring geometry, computed on first use

@@ -307,8 +307,9 @@ const Setup *get_setup(abs_ctx *ctx, const abs_config *cfg, abs_status &st) {
         fail(ctx, st, err);
         return nullptr;
     }
-    // twiddles laid out for the packed (re, im) complex multiply of the transforms
-    std::vector<float4> tw(2 * (size_t)s->N);
+    // twiddles laid out for the packed (re, im) complex multiply of the transforms:
+    // double-float pairs [2t], [2t + 1], then the FP32 ones [2N + t]
+    std::vector<float4> tw(3 * (size_t)s->N);
     for (int t = 0; t < s->N; ++t) {
         const double a = 2.0 * M_PI * (double)t / (double)s->N;
         const double c = std::cos(a), sn = -std::sin(a);
@@ -316,6 +317,7 @@ const Setup *get_setup(abs_ctx *ctx, const abs_config *cfg, abs_status &st) {
         const float cl = (float)(c - (double)ch), sl = (float)(sn - (double)sh);
         tw[2 * t] = make_float4(ch, ch, cl, cl);
         tw[2 * t + 1] = make_float4(-sh, sh, -sl, sl);
+        tw[2 * (size_t)s->N + t] = make_float4(ch, ch, -sh, sh);
     }
     s->d_q = upload(s->q);
     s->d_lat_off = upload(s->lat_off);

@@ -36,6 +36,7 @@
 // the smaller set streamed through shared memory); each thread keeps
 // run-length state (consecutive cells in row order usually land in the same
 // ring) and adds finished runs into a lane-private shared-memory histogram
+// of 16-bit counters (an item adds at most INNER x G1 to one counter)
 // over the third ring, reduced into an int64 table at the end.
 #include "abs_internal.cuh"
 
@@ -43,6 +44,7 @@ namespace absk {
 namespace {
 
 constexpr int G1 = 4;            // g1 cells per thread
+constexpr int KU = 4;            // inner cells whose map loads are issued together
 constexpr int CT = 256;          // threads per counting CTA (max)
 constexpr int INNER = 512;       // inner cells per work item (bounds the work of one item)
 constexpr unsigned FULL = 0xffffffffu;
@@ -418,7 +420,9 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
     const int nwarps = blockDim.x >> 5;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int hs = G.nb + 1;                       // histogram slots (0 = none)
-    uint32_t *hist = (uint32_t *)smem;             // [nwarps][hs][32]
+    uint16_t *hist = (uint16_t *)smem;             // [nwarps][hs][32]
+    uint32_t *hist32 = (uint32_t *)smem;           // the same, as pairs of counters (clearing)
+    const int hwords = nwarps * hs * 16;
     int32_t *stage = (int32_t *)(hist + (size_t)nwarps * hs * 32);   // [INNER]
     uint8_t *map_s = (uint8_t *)(stage + INNER);
     const uint8_t *map = MAP_IN_SMEM ? map_s : map_g;
@@ -429,9 +433,9 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
         for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) ((uint4 *)map_s)[i] = ((const uint4 *)map_g)[i];
         for (int64_t i = nv * 16 + threadIdx.x; i < mb; i += blockDim.x) map_s[i] = map_g[i];
     }
-    for (int i = threadIdx.x; i < nwarps * hs * 32; i += blockDim.x) hist[i] = 0u;
+    for (int i = threadIdx.x; i < hwords; i += blockDim.x) hist32[i] = 0u;
     __syncthreads();
-    uint32_t *myhist = hist + (size_t)warp * hs * 32 + lane;
+    uint16_t *myhist = hist + (size_t)warp * hs * 32 + lane;
     __shared__ int it_s;
     for (; ni > 0;) {
         if (threadIdx.x == 0) it_s = atomicAdd(next_item, 1);   // dynamic: items differ in size
@@ -487,13 +491,37 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
             stage[k] = l;
         }
         __syncthreads();
-        for (int k = 0; k < nin; ++k) {
+        // the map loads of KU inner cells are issued before their run-length updates,
+        // which never feed a load: KU x G1 lookups in flight per thread
+        int k = 0;
+        for (; k + KU <= nin; k += KU) {
+            int rr[KU][G1];
+#pragma unroll
+            for (int u = 0; u < KU; ++u) {
+                const int l2 = stage[k + u];
+#pragma unroll
+                for (int q = 0; q < G1; ++q) rr[u][q] = v1[q] ? (int)map[abs(lin1[q] + l2)] : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < KU; ++u) {
+#pragma unroll
+                for (int q = 0; q < G1; ++q) {
+                    if (rr[u][q] != cur[q]) {
+                        myhist[(size_t)cur[q] * 32] += (uint16_t)cnt[q];
+                        cur[q] = rr[u][q];
+                        cnt[q] = 0;
+                    }
+                    ++cnt[q];
+                }
+            }
+        }
+        for (; k < nin; ++k) {
             const int l2 = stage[k];
 #pragma unroll
             for (int q = 0; q < G1; ++q) {
                 const int r = v1[q] ? (int)map[abs(lin1[q] + l2)] : 0;
                 if (r != cur[q]) {
-                    myhist[(size_t)cur[q] * 32] += cnt[q];
+                    myhist[(size_t)cur[q] * 32] += (uint16_t)cnt[q];
                     cur[q] = r;
                     cnt[q] = 0;
                 }
@@ -501,7 +529,7 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
             }
         }
 #pragma unroll
-        for (int q = 0; q < G1; ++q) myhist[(size_t)cur[q] * 32] += cnt[q];
+        for (int q = 0; q < G1; ++q) myhist[(size_t)cur[q] * 32] += (uint16_t)cnt[q];
         __syncthreads();
         unsigned long long *T = job == JOB_DIRECT ? t0 : job == JOB_E1 ? t1 : job == JOB_E2 ? t2
                                 : job == JOB_E3 ? t3 : t4;
@@ -514,7 +542,7 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
                 atomicAdd(&T[((size_t)a * G.nb + b) * G.nb + (k - 1)], (unsigned long long)sacc);
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < nwarps * hs * 32; k += blockDim.x) hist[k] = 0u;
+        for (int k = threadIdx.x; k < hwords; k += blockDim.x) hist32[k] = 0u;
         __syncthreads();
     }
     if (!ga.T) return;
@@ -616,14 +644,23 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     const int hs = s.nb + 1;
     const int64_t map_bytes = cdiv(G.base + 1, 16) * 16;
     const size_t hist_budget = 96 * 1024;
-    int nwarps = (int)std::min<size_t>(CT / 32, hist_budget / ((size_t)hs * 32 * 4));
+    int nwarps = (int)std::min<size_t>(CT / 32, hist_budget / ((size_t)hs * 32 * 2));
     if (nwarps < 1) return fail(ctx, ABS_ERR_UNSUPPORTED, "too many rings for the count kernel");
     const int threads = nwarps * 32;
     const int chunk = threads * G1;
-    const int64_t cta_bytes = map_bytes + (int64_t)nwarps * hs * 32 * 4 + INNER * 4;
-    const bool map_smem = cta_bytes <= 220 * 1024;
-    const int per_sm = map_smem ? std::max<int>(1, (int)std::min<int64_t>(4, (226 * 1024) / (cta_bytes + 1024))) : 2;
-    const size_t smem = (size_t)nwarps * hs * 32 * 4 + INNER * 4 + (map_smem ? map_bytes : 0);
+    const int64_t hist_bytes = (int64_t)nwarps * hs * 32 * 2;
+    const bool map_smem = map_bytes + hist_bytes + INNER * 4 <= 220 * 1024;
+    const size_t smem = (size_t)hist_bytes + INNER * 4 + (map_smem ? map_bytes : 0);
+    // resident CTAs an SM (shared memory, threads and registers), for the persistent grid
+    int per_sm = 1;
+    if (map_smem) {
+        cudaFuncSetAttribute(k_count_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_pairs<true>, threads, smem);
+    } else {
+        cudaFuncSetAttribute(k_count_pairs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_pairs<false>, threads, smem);
+    }
+    per_sm = std::max(per_sm, 1);
     int64_t max_ring = 0;
     for (int m = 0; m < s.nb; ++m) max_ring = std::max<int64_t>(max_ring, s.lat[m]);
     const int64_t npair = (int64_t)s.nb * (s.nb + 1) / 2;

@@ -35,6 +35,8 @@ namespace absk {
 namespace {
 
 constexpr int MAXRAD = 16;
+constexpr int FFT_NT = 128;     // threads per transform CTA
+constexpr int FFT_FIXED = 2;    // a CTA's fixed cost (barriers, first loads) in lines of work
 
 struct FftPass {
     int R, p, T, tstep;
@@ -109,11 +111,12 @@ __device__ __forceinline__ pdf pconst(double v) {
 // The two arithmetics of the butterflies.  DF: double-float complex values
 // stored as float4, twiddles as two float4 per index (the packed layout of
 // Setup::d_tw).  F32: plain FP32 complex values stored as float2 (re, im),
-// twiddles as one float4 (c, c, -s, s) per index, staged from the high parts.
+// twiddles as one float4 (c, c, -s, s) per index (the table after it).  The
+// twiddles are read through the L1 cache, shared by every CTA on the SM.
 struct ArithDF {
     using E = float4;
     using C = pdf;
-    static constexpr int TW = 2;   // float4 twiddle entries per index
+    __host__ __device__ static const float4 *table(const float4 *tw, int N) { return tw; }
     __device__ static C ld(E v) { return ::absk::ld(v); }
     __device__ static E st(C a) { return ::absk::st(a); }
     __device__ static C add(C a, C b) { return p_add(a, b); }
@@ -122,11 +125,8 @@ struct ArithDF {
     __device__ static C half(C a) { return p_half(a); }
     __device__ static C cst(double v) { return pconst(v); }
     __device__ static C mul(C a, C c) { return p_mul(a, c); }
-    __device__ static C twiddle(C v, const float4 *tw, int t) {
-        return c_mul_tw(v, ::absk::ld(tw[2 * t]), ::absk::ld(tw[2 * t + 1]));
-    }
-    __device__ static void stage_tw(float4 *tw, const float4 *__restrict__ tw_g, int N) {
-        for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) tw[i] = tw_g[i];
+    __device__ static C twiddle(C v, const float4 *__restrict__ tw, int t) {
+        return c_mul_tw(v, ::absk::ld(__ldg(tw + 2 * t)), ::absk::ld(__ldg(tw + 2 * t + 1)));
     }
     // a cell value (re.hi, im.hi, re.lo, im.lo) as stored, and i times it
     __device__ static E from_cell(float4 v) { return v; }
@@ -139,7 +139,7 @@ struct ArithDF {
 struct ArithF32 {
     using E = float2;
     using C = float2;
-    static constexpr int TW = 1;
+    __host__ __device__ static const float4 *table(const float4 *tw, int N) { return tw + 2 * (size_t)N; }
     __device__ static C ld(E v) { return v; }
     __device__ static E st(C a) { return a; }
     __device__ static C add(C a, C b) { return __fadd2_rn(a, b); }
@@ -149,15 +149,9 @@ struct ArithF32 {
     __device__ static C cst(double v) { return f2((float)v, (float)v); }
     __device__ static C mul(C a, C c) { return __fmul2_rn(a, c); }
     // v w = v (c, c) + (v.im, v.re) (-s, s)
-    __device__ static C twiddle(C v, const float4 *tw, int t) {
-        const float4 w = tw[t];
+    __device__ static C twiddle(C v, const float4 *__restrict__ tw, int t) {
+        const float4 w = __ldg(tw + t);
         return __ffma2_rn(f2(v.y, v.x), f2(w.z, w.w), __fmul2_rn(v, f2(w.x, w.y)));
-    }
-    __device__ static void stage_tw(float4 *tw, const float4 *__restrict__ tw_g, int N) {
-        for (int i = threadIdx.x; i < N; i += blockDim.x) {
-            const float4 c = tw_g[2 * i], sn = tw_g[2 * i + 1];
-            tw[i] = make_float4(c.x, c.y, sn.x, sn.y);
-        }
     }
     // the cell value rounded once to FP32
     __device__ static E from_cell(float4 v) { return f2(__fadd_rn(v.x, v.z), __fadd_rn(v.y, v.w)); }
@@ -313,9 +307,9 @@ struct GridW64 {
 // Column pass: one CTA per (block of CB columns x, ring pair), transforming
 // along y the 2R+1 columns |x| <= R that hold ring cells.  W[pair][x + Rmax][N].
 template <class Src, class A>
-__global__ void __launch_bounds__(256) k_fft_cols(RingGeom G, FftPlan P, int CB, const int64_t *__restrict__ q,
+__global__ void __launch_bounds__(FFT_NT) k_fft_cols(RingGeom G, FftPlan P, int CB, const int64_t *__restrict__ q,
                                                   const int32_t *__restrict__ Rm, Src src,
-                                                  const float4 *__restrict__ tw_g,
+                                                  const float4 *__restrict__ tw,
                                                   typename A::E *__restrict__ W) {
     using E = typename A::E;
     extern __shared__ float4 sbuf[];
@@ -324,9 +318,7 @@ __global__ void __launch_bounds__(256) k_fft_cols(RingGeom G, FftPlan P, int CB,
     const int Rp = max(Rm[a], b >= 0 ? Rm[b] : -1);
     const int x0 = (int)blockIdx.x * CB - G.Rmax;
     if (Rp < 0 || x0 > Rp || x0 + CB - 1 < -Rp) return;
-    float4 *tw = sbuf;
-    E *l0 = (E *)(sbuf + A::TW * G.N), *l1 = l0 + (size_t)CB * G.N;
-    A::stage_tw(tw, tw_g, G.N);
+    E *l0 = (E *)sbuf, *l1 = l0 + (size_t)CB * G.N;
     for (int i = threadIdx.x; i < CB * G.N; i += blockDim.x) l0[i] = A::zero();
     __syncthreads();
     const int span = 2 * Rp + 1;
@@ -356,10 +348,10 @@ __global__ void __launch_bounds__(256) k_fft_cols(RingGeom G, FftPlan P, int CB,
 // Row pass: one CTA per (block of RB sky rows py, ring pair), transforming
 // along x; each output row of both fields is written whole (contiguous).
 template <class A>
-__global__ void __launch_bounds__(256) k_fft_rows(RingGeom G, FftPlan P, int RB,
+__global__ void __launch_bounds__(FFT_NT) k_fft_rows(RingGeom G, FftPlan P, int RB,
                                                   const int32_t *__restrict__ Rm,
                                                   const typename A::E *__restrict__ W,
-                                                  const float4 *__restrict__ tw_g,
+                                                  const float4 *__restrict__ tw,
                                                   float *__restrict__ fields) {
     using E = typename A::E;
     extern __shared__ float4 sbuf[];
@@ -378,9 +370,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(RingGeom G, FftPlan P, int RB,
         }
         return;
     }
-    float4 *tw = sbuf;
-    E *l0 = (E *)(sbuf + A::TW * G.N), *l1 = l0 + (size_t)RB * G.N;
-    A::stage_tw(tw, tw_g, G.N);
+    E *l0 = (E *)sbuf, *l1 = l0 + (size_t)RB * G.N;
     for (int i = threadIdx.x; i < RB * G.N; i += blockDim.x) l0[i] = A::zero();
     __syncthreads();
     const int cols = 2 * Rp + 1;
@@ -426,21 +416,20 @@ struct FftLaunch {
 };
 
 // Lines per CTA for a pass over `lines` lines of each of `npairs` ring pairs:
-// the count that minimises (CTA waves) x (lines per CTA + 2, the fixed cost of
-// a CTA: its twiddles and barriers), a CTA holding two line buffers and the
-// twiddles (two lines' worth) in shared memory and at most max_per_sm CTAs
-// sharing an SM (registers); both passes are latency-bound at moderate N, so
-// a last, part-filled wave costs a whole one.
+// the count that minimises (CTA waves) x (lines per CTA + FFT_FIXED), a CTA
+// holding two line buffers in shared memory and at most max_per_sm CTAs
+// sharing an SM (threads and registers); both passes are latency-bound at
+// moderate N, so a last, part-filled wave costs a whole one.
 static int lines_per_cta(size_t line, int lines, int npairs, int sm_count, int max_per_sm) {
     int best = 1;
     int64_t best_cost = INT64_MAX;
     for (int w = 1; w <= 16; ++w) {
-        const size_t smem = line * (2 * w + 2);
+        const size_t smem = line * 2 * w;
         if (smem > 200 * 1024) break;
         const int per_sm = (int)std::min<size_t>(max_per_sm, (228 * 1024) / (smem + 1024));
         if (per_sm < 1) break;
         const int64_t ctas = cdiv(lines, w) * (int64_t)npairs;
-        const int64_t cost = cdiv(ctas, (int64_t)sm_count * per_sm) * (w + 2);
+        const int64_t cost = cdiv(ctas, (int64_t)sm_count * per_sm) * (w + FFT_FIXED);
         if (cost < best_cost) {
             best_cost = cost;
             best = w;
@@ -458,11 +447,13 @@ FftLaunch fft_launch(const Setup &s, int sm_count) {
     const bool f32 = plain_fp32(s);
     const size_t line = (f32 ? sizeof(float2) : sizeof(float4)) * (size_t)s.N;
     const int npairs = (s.nb + 1) / 2;
-    const int per_sm = f32 ? 8 : 4;   // 256 threads at 32 / 60 registers
+    // resident CTAs per SM: 2048 threads, and 65,536 registers at about 32 (FP32) or 64
+    // (double-float) a thread
+    const int per_sm = std::min(2048 / FFT_NT, 65536 / (FFT_NT * (f32 ? 32 : 64)));
     L.CB = lines_per_cta(line, 2 * s.R + 1, npairs, sm_count, per_sm);
     L.RB = lines_per_cta(line, s.N, npairs, sm_count, per_sm);
-    L.col_smem = line * (2 * L.CB + 2);   // two line buffers + the twiddles
-    L.row_smem = line * (2 * L.RB + 2);
+    L.col_smem = line * 2 * L.CB;   // two line buffers
+    L.row_smem = line * 2 * L.RB;
     return L;
 }
 
@@ -483,13 +474,13 @@ abs_status run_fft_as(abs_ctx *ctx, const Setup &s, const Src &src, float *d_fie
     cudaFuncSetAttribute(k_fft_rows<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.row_smem);
     {
         StageTimer timer(ctx, "fft_cols");
-        k_fft_cols<Src, A><<<dim3((unsigned)cdiv(2 * s.R + 1, L.CB), npairs), 256, L.col_smem, st>>>(
-            G, P, L.CB, s.d_q, s.d_Rm, src, (const float4 *)s.d_tw, W);
+        k_fft_cols<Src, A><<<dim3((unsigned)cdiv(2 * s.R + 1, L.CB), npairs), FFT_NT, L.col_smem, st>>>(
+            G, P, L.CB, s.d_q, s.d_Rm, src, A::table(s.d_tw, s.N), W);
     }
     {
         StageTimer timer(ctx, "fft_rows");
-        k_fft_rows<A><<<dim3((unsigned)cdiv(s.N, L.RB), npairs), 256, L.row_smem, st>>>(
-            G, P, L.RB, s.d_Rm, W, (const float4 *)s.d_tw, d_fields);
+        k_fft_rows<A><<<dim3((unsigned)cdiv(s.N, L.RB), npairs), FFT_NT, L.row_smem, st>>>(
+            G, P, L.RB, s.d_Rm, W, A::table(s.d_tw, s.N), d_fields);
     }
     return check_launch(ctx, "filter+FFT");
 }
