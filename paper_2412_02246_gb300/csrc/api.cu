@@ -594,9 +594,15 @@ abs_status abs_normalise(abs_ctx *ctx, const abs_config *cfg, int32_t n_trip, co
     return ABS_OK;
 }
 
+// With h_uv / h_vis (page-locked host buffers) the inputs are first copied into
+// d_uv / d_vis: the positions on the main stream ahead of the gridding plan, the
+// visibilities on the side stream beside it (the plan needs only the positions).
+// (The plan's first kernel reading the positions from the host buffer through
+// its device-mapped address was slower than the copy engine.)
 static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv,
                                 int32_t n_real, const float *d_vis, int32_t n_trip,
-                                const int32_t *d_ijk, double *d_B, int64_t *d_count, double *d_ellbar) {
+                                const int32_t *d_ijk, double *d_B, int64_t *d_count, double *d_ellbar,
+                                const float *h_uv = nullptr, const float *h_vis = nullptr) {
     const int64_t cells = (int64_t)s.n * s.n;
     const int64_t P = (int64_t)s.N * s.N;
     float *fields = (float *)workspace(ctx, "est.fields", sizeof(float) * (size_t)s.nb * P);
@@ -615,12 +621,19 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
     grid_acc_buffers(ctx, s, &acc0);
     if (!acc0) return fail(ctx, ABS_ERR_OOM, "grid accumulation workspace");
     const bool pre_zero = !ctx->profiling && ctx->side;
+    const size_t uvb = sizeof(float) * 2 * (size_t)n_vis;
+    const bool copy_in = h_uv && h_vis && n_vis > 0;
     if (pre_zero) {
         cudaEventRecord(ctx->ev_fork, ctx->stream);
         cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
         cudaMemsetAsync(acc0, 0, sizeof(double) * 3 * (size_t)cells, ctx->side);
+        if (copy_in)
+            cudaMemcpyAsync((void *)d_vis, h_vis, uvb * (size_t)n_real, cudaMemcpyHostToDevice, ctx->side);
         cudaEventRecord(ctx->ev_join, ctx->side);
+    } else if (copy_in) {
+        cudaMemcpyAsync((void *)d_vis, h_vis, uvb * (size_t)n_real, cudaMemcpyHostToDevice, ctx->stream);
     }
+    if (copy_in) cudaMemcpyAsync((void *)d_uv, h_uv, uvb, cudaMemcpyHostToDevice, ctx->stream);
     const abs_status sp = launch_grid_plan(ctx, s, n_vis, d_uv);
     if (pre_zero) cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
     if (sp != ABS_OK) return sp;
@@ -730,14 +743,27 @@ static abs_status graphed(abs_ctx *ctx, const std::string &key, const F &eager) 
 
 static abs_status estimate_graphed(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv,
                                    int32_t n_real, const float *d_vis, int32_t n_trip, const int32_t *d_ijk,
-                                   double *d_B, int64_t *d_count, double *d_ellbar) {
-    char key[256];
-    snprintf(key, sizeof key, "%p|%p|%lld|%p|%d|%p|%d|%p|%p|%p|%p", (const void *)&s, (const void *)ctx->stream,
-             (long long)n_vis, (const void *)d_uv, n_real, (const void *)d_vis, n_trip, (const void *)d_ijk,
-             (void *)d_B, (void *)d_count, (void *)d_ellbar);
+                                   double *d_B, int64_t *d_count, double *d_ellbar,
+                                   const float *h_uv = nullptr, const float *h_vis = nullptr) {
+    char key[320];
+    snprintf(key, sizeof key, "%p|%p|%lld|%p|%d|%p|%d|%p|%p|%p|%p|%p|%p", (const void *)&s,
+             (const void *)ctx->stream, (long long)n_vis, (const void *)d_uv, n_real, (const void *)d_vis, n_trip,
+             (const void *)d_ijk, (void *)d_B, (void *)d_count, (void *)d_ellbar, (const void *)h_uv,
+             (const void *)h_vis);
     return graphed(ctx, key, [&]() {
-        return estimate_many(ctx, s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar);
+        return estimate_many(ctx, s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar, h_uv,
+                             h_vis);
     });
+}
+
+// Page-locked (pinned or registered) host memory: its copies can be captured into a graph.
+static bool page_locked(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
 }
 
 static abs_status estimate_args(abs_ctx *ctx, const Setup &s, int64_t n_vis, const void *uv,
@@ -874,12 +900,19 @@ abs_status abs_estimate_host(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis,
         d_ijk = p;
     }
     if (!d_uv || !d_vis || !d_B || !d_count || !d_ellbar) return fail(ctx, ABS_ERR_OOM, "host staging");
-    if (n_vis > 0) {
-        cudaMemcpyAsync(d_uv, h_uv, uvb, cudaMemcpyHostToDevice, ctx->stream);
-        cudaMemcpyAsync(d_vis, h_vis, visb, cudaMemcpyHostToDevice, ctx->stream);
+    if (n_vis > 0 && page_locked(h_uv) && page_locked(h_vis)) {
+        // the copies go inside the estimate (and its graph): the visibilities' copy runs
+        // beside the gridding plan
+        ABS_CHECK(estimate_graphed(ctx, *s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar,
+                                   h_uv, h_vis));
+    } else {
+        if (n_vis > 0) {
+            cudaMemcpyAsync(d_uv, h_uv, uvb, cudaMemcpyHostToDevice, ctx->stream);
+            cudaMemcpyAsync(d_vis, h_vis, visb, cudaMemcpyHostToDevice, ctx->stream);
+        }
+        ABS_CHECK(check_launch(ctx, "host to device copies"));
+        ABS_CHECK(estimate_graphed(ctx, *s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar));
     }
-    ABS_CHECK(check_launch(ctx, "host to device copies"));
-    ABS_CHECK(estimate_graphed(ctx, *s, n_vis, d_uv, n_real, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar));
     if (h_B && n_trip > 0)
         cudaMemcpyAsync(h_B, d_B, sizeof(double) * (size_t)n_trip * n_real, cudaMemcpyDeviceToHost, ctx->stream);
     if (h_count && n_trip > 0)

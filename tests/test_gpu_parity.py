@@ -478,6 +478,31 @@ def test_estimate_many_and_host(ctx):
 
 
 @pytest.mark.gpu
+def test_estimate_host_pinned_replays(ctx):
+    """abs_estimate_host with page-locked buffers copies inside the estimate
+    (and its graph): the eager call, the capture and replays on changed host
+    contents equal abs_estimate on device copies of the same inputs."""
+    ins = [inputs(0, r) for r in range(2)]
+    wl = ins[0].wl
+    cfg = absmod.Config.from_workload(wl)
+    nt = len(absmod.abs_triplets(cfg))
+    huv = torch.from_numpy(np.ascontiguousarray(ins[0].uv)).pin_memory()
+    hvis = torch.empty((wl.n_vis, 2), dtype=torch.float32).pin_memory()
+    hB = torch.empty(nt, dtype=torch.float64).pin_memory()
+    hT = torch.empty(nt, dtype=torch.int64).pin_memory()
+    hE = torch.empty(cfg.n_bins, dtype=torch.float64).pin_memory()
+    for call, r in enumerate((0, 0, 1, 0, 1)):      # eager, capture, then replays
+        hvis.copy_(torch.from_numpy(synth.vis_as_float2(ins[r].vis)))
+        hB.fill_(-1.0)
+        ctx.abs_estimate_host(cfg, huv, hvis, nt, None, hB, hT, hE)
+        B, T, E, _ = absmod.estimate(cfg, to_dev(ins[r].uv), to_dev(synth.vis_as_float2(ins[r].vis)), ctx)
+        ctx.sync()
+        assert np.array_equal(hT.numpy(), T.cpu().numpy()), call
+        assert np.allclose(hB.numpy(), B.cpu().numpy(), rtol=1e-12, equal_nan=True), call
+        assert np.allclose(hE.numpy(), E.cpu().numpy(), rtol=0, equal_nan=True), call
+
+
+@pytest.mark.gpu
 def test_estimate_batched_uneven():
     """abs_estimate_batched over items of different grid sizes, ring counts
     and precisions equals abs_estimate item by item, on the eager call, the
