@@ -291,6 +291,7 @@ def multichannel(args, m, synth, torch, dev, stream, peaks_sm):
         A, F = ring_census(mk.cpu().numpy(), q, n)
         visits += count_route_visits(A, F)
         fills += int(F.sum())
+    shape = ctx.tuned_shape(cfg)
     ctx.close()
     per = {k: 1e3 * v[0] / len(items) for k, v in prof.items()}   # us per channel
     rm = ring_rmax(q, n // 2 - 1)
@@ -308,7 +309,7 @@ def multichannel(args, m, synth, torch, dev, stream, peaks_sm):
         tile = by_j[t:t + 128]
         band += -(-(max(kr[r][1] for r in tile) - min(kr[r][0] for r in tile) + 1) // 16) * 16
     out = {"value": len(items) * 1e3 / ms, "unit": "channels/s", "channels": chans,
-           "ms_per_call": ms, "n_trip": nt, "n_fft": N,
+           "ms_per_call": ms, "n_trip": nt, "n_fft": N, "tc_shape": shape,
            "stages_us_per_channel": {k: round(v, 1) for k, v in sorted(per.items())}}
 
     def frac(ach, peak):
@@ -644,6 +645,7 @@ def run_ours(args):
                                                     "pair_visits") if kk in rr}
     tri_fp32 = roofline_for("triple_fp32", stages["triple_fp32"]["avg_us"] * 1e-3, geo, peaks)
     tc_avg = 1e3 * prof_tc["triple_tc"][0] / max(prof_tc["triple_tc"][1], 1)
+    tc_shape = ctx.tuned_shape(cfg_tc)      # the autotuner's pick (chunk width, grouped tiles)
     tri_tc = roofline_for("triple_tc", tc_avg * 1e-3, geo, peaks)
     useful = 2.0 * nt * N * N
 
@@ -668,6 +670,7 @@ def run_ours(args):
                                    "256-item batch"},
         "split_bf16": {"value": args.steps / (tc_ms * 1e-3), "unit": UNIT,
                        "triple_tc_us": round(tc_avg, 2),
+                       "tc_shape": tc_shape,
                        "triple_tc_tflops_executed": tri_tc["achieved"],
                        "triple_tc_frac_bf16_peak": tri_tc["frac"],
                        "triple_tc_traffic": tri_tc["traffic"],

@@ -260,6 +260,22 @@ typedef struct abs_stage_time {
 abs_status abs_profile(abs_ctx *ctx, int32_t on);
 abs_status abs_profile_read(abs_ctx *ctx, int32_t cap, int32_t *n, abs_stage_time *out);
 
+/* Autotuner of the split-BF16 triple-sum kernel (Sec. 2, Eq. estimator_t on
+ * tensor cores).  On the first call of a configuration that runs eagerly (not
+ * under stream capture, not while the stage profiler runs) with the canonical
+ * triplet list, every feasible launch shape (pixel chunk of 128, 96 or 64
+ * pixels; one row tile per CTA or groups of row tiles sharing each field
+ * chunk) is timed twice on the call's own fields and the fastest is kept, by
+ * configuration, for the context and its batch lanes (an abs_estimate_batched
+ * call with an untuned split-BF16 item runs its items one after another for
+ * that call).  With the autotuner off the shape comes from a cost model.
+ * abs_autotune(ctx, 0 | 1) turns it off / on (on by default); shapes already
+ * chosen are kept.  abs_tuned_shape writes the shape chosen for cfg: *kc the
+ * chunk width (0: none yet), *grouped 1 for grouped row tiles, *measured 1 if
+ * the autotuner timed it (0: the cost model).  Any output pointer may be NULL. */
+abs_status abs_autotune(abs_ctx *ctx, int32_t enable);
+abs_status abs_tuned_shape(abs_ctx *ctx, const abs_config *cfg, int32_t *kc, int32_t *grouped, int32_t *measured);
+
 #ifdef __cplusplus
 }
 #endif

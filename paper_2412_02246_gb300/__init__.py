@@ -88,6 +88,8 @@ def load(path: str | None = None):
         "abs_triple_sums_static": ([C, P, i32, P, P, P], ctypes.c_int),
         "abs_profile": ([P, i32], ctypes.c_int),
         "abs_profile_read": ([P, i32, P, P], ctypes.c_int),
+        "abs_autotune": ([P, i32], ctypes.c_int),
+        "abs_tuned_shape": ([P, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -208,6 +210,17 @@ class Context:
     def profile(self, on: bool = True):
         """Turn the per-kernel CUDA-event profiler on (clearing totals) or off."""
         _check(load().abs_profile(self.h, 1 if on else 0), self.h, "abs_profile")
+
+    def autotune(self, on: bool = True):
+        """Turn the split-BF16 launch-shape autotuner on (default) or off (cost model)."""
+        _check(load().abs_autotune(self.h, 1 if on else 0), self.h, "abs_autotune")
+
+    def tuned_shape(self, cfg: "Config") -> dict:
+        """The split-BF16 launch shape chosen for cfg: chunk width (0: none yet), grouped, measured."""
+        kc, gr, me = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().abs_tuned_shape(self.h, cfg.ref(), ctypes.byref(kc), ctypes.byref(gr), ctypes.byref(me)),
+               self.h, "abs_tuned_shape")
+        return {"kc": kc.value, "grouped": bool(gr.value), "measured": bool(me.value)}
 
     def profile_read(self) -> dict:
         """{stage: (total ms, launches)} accumulated since profile(True); waits for the stream."""

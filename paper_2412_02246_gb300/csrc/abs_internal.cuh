@@ -50,6 +50,7 @@ struct Setup {
     unsigned long long *d_full_counts = nullptr;
     bool full_counts_ready = false;
     int tc_groups = -1;           // split-BF16 tile groups of the canonical list (-1: not worked out)
+    std::string key;              // the configuration's key (setups, tuned shapes)
 };
 
 // Host-side validation + derivation.  Returns ABS_OK or an error with text in err.
@@ -99,6 +100,11 @@ struct abs_ctx {
     // its items concurrently; created on first use.  A lane's parent is the
     // context whose graphs may hold the lane's buffers.
     abs_ctx *parent = nullptr;
+    // autotuner: launch shapes of the split-BF16 kernel measured on a configuration's
+    // first eager call, by configuration key; kept by the root context (lanes share it)
+    bool autotune = true;
+    struct TcShape { int kc = 0; bool grouped = false; bool measured = false; };
+    std::map<std::string, TcShape> tc_shapes;
     std::vector<abs_ctx *> lanes;
     bool owns_stream = false;
     cudaEvent_t ev_lane = nullptr;   // a lane's end, joined by the parent

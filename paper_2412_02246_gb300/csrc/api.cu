@@ -303,6 +303,7 @@ const Setup *get_setup(abs_ctx *ctx, const abs_config *cfg, abs_status &st) {
     }
     std::unique_ptr<Setup> s(new Setup);
     st = make_setup(cfg, *s, err);
+    s->key = key;
     if (st != ABS_OK) {
         fail(ctx, st, err);
         return nullptr;
@@ -356,7 +357,7 @@ static cudaEvent_t pool_get(abs_ctx *ctx) {
 }
 
 StageTimer::StageTimer(abs_ctx *c, const char *n) : ctx(c), name(n) {
-    if (!ctx->profiling) return;
+    if (!ctx->profiling || !n) return;
     a = pool_get(ctx);
     b = pool_get(ctx);
     if (a) cudaEventRecord(a, ctx->stream);
@@ -487,6 +488,23 @@ abs_status abs_profile(abs_ctx *ctx, int32_t on) {
     profile_drain(ctx);
     ctx->stage_totals.clear();
     ctx->profiling = on != 0;
+    return ABS_OK;
+}
+
+abs_status abs_autotune(abs_ctx *ctx, int32_t enable) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    ctx->autotune = enable != 0;
+    return ABS_OK;
+}
+
+abs_status abs_tuned_shape(abs_ctx *ctx, const abs_config *cfg, int32_t *kc, int32_t *grouped, int32_t *measured) {
+    if (!ctx || !cfg || !cfg->ell_edges || cfg->n_bins < 1 || cfg->n_bins > ABS_MAX_BINS)
+        return ABS_ERR_INVALID_ARG;
+    auto it = ctx->tc_shapes.find(setup_key(cfg));
+    const bool have = it != ctx->tc_shapes.end();
+    if (kc) *kc = have ? it->second.kc : 0;
+    if (grouped) *grouped = have && it->second.grouped ? 1 : 0;
+    if (measured) *measured = have && it->second.measured ? 1 : 0;
     return ABS_OK;
 }
 
@@ -823,8 +841,19 @@ abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *i
     if (n_items < 0 || (n_items > 0 && !items)) return fail(ctx, ABS_ERR_INVALID_ARG, "n_items < 0 or items NULL");
     DeviceGuard g(ctx->device);
     // items run round-robin over lanes (concurrent streams with their own workspaces),
-    // except while the stage profiler runs, on the legacy default stream or for one item
-    const int K = (ctx->profiling || !ctx->stream || n_items < 2) ? 1 : std::min<int>(ABS_BATCH_LANES, n_items);
+    // except while the stage profiler runs, on the legacy default stream, for one item,
+    // or while a split-BF16 configuration still waits for its launch shape to be
+    // measured (the autotuner times candidates on an otherwise idle device, once)
+    bool untuned = false;
+    if (ctx->autotune)
+        for (int32_t i = 0; i < n_items && !untuned; ++i) {
+            const abs_config *c = items[i].cfg;
+            if (c && c->ell_edges && c->n_bins >= 1 && c->n_bins <= ABS_MAX_BINS && c->precision == ABS_SPLIT_BF16 &&
+                !items[i].d_ijk && items[i].n_trip > 0 && !ctx->tc_shapes.count(setup_key(c)))
+                untuned = true;
+        }
+    const int K = (ctx->profiling || !ctx->stream || n_items < 2 || untuned)
+                      ? 1 : std::min<int>(ABS_BATCH_LANES, n_items);
     while ((int)ctx->lanes.size() < K && K > 1) {
         abs_ctx *l = make_lane(ctx);
         if (!l) return fail(ctx, ABS_ERR_OOM, "batch lanes");

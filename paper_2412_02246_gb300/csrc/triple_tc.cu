@@ -755,39 +755,64 @@ static int canonical_groups(const Setup &s, int np, int gmax) {
     return std::max(ng, 1);
 }
 
-abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields, int32_t n_trip,
-                            const int32_t *d_ijk, double *d_sum) {
-    if (n_trip == 0) return ABS_OK;
+// One launch shape of the kernel: the chunk width and whether a CTA owns a
+// group of row tiles (the field chunks brought in once for all of them) or a
+// single tile; everything else follows from these and the problem.
+struct TcLaunch {
     TcGeom G;
-    G.nb = s.nb;
-    G.NP = (int)cdiv(std::max(s.nb, 16), 16) * 16;
-    if (3 * G.NP > TMEM_COLS) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 accumulators exceed tensor memory");
-    G.tmem_cols = TMEM_COLS;
-    G.P = (int64_t)s.N * s.N;
-    G.n_trip = n_trip;
-    // the chunk: the widest KC whose stages fit, at least two of each ring (three field stages
-    // for the wider chunks); then three operand stages if the field ring keeps its stages,
-    // then as many field stages as fit
+    int KC = 0;
+    bool grouped = false;
+    int groups = 0, gmax = 1;
+    size_t smem = 0;
+};
+
+// Shared-memory stages for chunk width kc: at least two of each ring (three
+// field stages for the wider chunks), three operand stages if the field ring
+// keeps its stages, then as many field stages as fit.  False if they do not fit.
+static bool tc_stages(TcGeom &G, int kc, int nb, size_t &smem) {
     const int64_t budget = 215 * 1024;   // dynamic shared memory, below the 227 KB per CTA with the static part
     const size_t epi = (size_t)TM * (3 * G.NP + 1) * 4;
-    int KC = 0;
-    for (int kc : {128, 96, 64}) {
-        const int min_f = kc > 64 ? 3 : 2;
-        G.a_bytes = TM * kc * 2;
-        G.b_bytes = 2 * G.NP * kc * 2;
-        G.f_bytes = (int)(cdiv((int64_t)s.nb * (kc + 4) * 4, 1024) * 1024);
-        G.ab_bytes = (int)(cdiv(2 * G.a_bytes + G.b_bytes, 1024) * 1024);
-        G.sa = MAX_AB;
-        while (G.sa > 2 && budget - (int64_t)G.sa * G.ab_bytes < min_f * (int64_t)G.f_bytes) --G.sa;
-        G.sf = (int)std::min<int64_t>(MAX_F, (budget - (int64_t)G.sa * G.ab_bytes) / G.f_bytes);
-        if (G.sf >= min_f) {
-            KC = kc;
-            break;
-        }
+    const int min_f = kc > 64 ? 3 : 2;
+    G.a_bytes = TM * kc * 2;
+    G.b_bytes = 2 * G.NP * kc * 2;
+    G.f_bytes = (int)(cdiv((int64_t)nb * (kc + 4) * 4, 1024) * 1024);
+    G.ab_bytes = (int)(cdiv(2 * G.a_bytes + G.b_bytes, 1024) * 1024);
+    G.sa = MAX_AB;
+    while (G.sa > 2 && budget - (int64_t)G.sa * G.ab_bytes < min_f * (int64_t)G.f_bytes) --G.sa;
+    G.sf = (int)std::min<int64_t>(MAX_F, (budget - (int64_t)G.sa * G.ab_bytes) / G.f_bytes);
+    if (G.sf < min_f || (int64_t)epi > budget) return false;
+    smem = 1024 + std::max((size_t)G.sf * G.f_bytes + (size_t)G.sa * G.ab_bytes, epi);
+    return true;
+}
+
+// The pixel range of a CTA: whole waves of CTAs, at most 4096 pixels (which
+// bounds the FP32 accumulation length in the tensor core), a multiple of kc.
+static int64_t tc_range(int64_t P, int kc, int groups, int sm_count) {
+    for (int waves = 1;; ++waves) {
+        const int64_t ranges = std::max<int64_t>(1, (int64_t)sm_count * waves / groups);
+        const int64_t per = cdiv(cdiv(P, ranges), kc) * kc;
+        if (per <= 4096) return per;
     }
-    if (KC == 0 || (int64_t)epi > budget)
-        return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 stages do not fit shared memory");
-    const size_t smem = 1024 + std::max((size_t)G.sf * G.f_bytes + (size_t)G.sa * G.ab_bytes, epi);
+}
+
+static bool tc_shape(const TcGeom &base, int kc, bool grouped, int tiles, int tc_groups, int nb, int sm_count,
+                     TcLaunch &L) {
+    L.G = base;
+    L.KC = kc;
+    if (!tc_stages(L.G, kc, nb, L.smem)) return false;
+    L.grouped = grouped && tc_groups < tiles;
+    L.groups = L.grouped ? tc_groups : tiles;
+    L.gmax = L.grouped ? GMAX : 1;
+    L.G.per_split = tc_range(base.P, kc, L.groups, sm_count);
+    return true;
+}
+
+// k_rows and the kernel for one shape, with events around the kernel when given.
+static abs_status tc_run(abs_ctx *ctx, const Setup &s, const TcLaunch &L, const float *d_fields, int32_t n_trip,
+                         const int32_t *d_ijk, int max_rows, int tiles, double *partial, cudaEvent_t e0,
+                         cudaEvent_t e1) {
+    TcGeom G = L.G;
+    const int KC = L.KC;
     // the field chunk as one TMA box (KC + 4 pixels x every ring) of the [nb][P] FP32 array; the
     // row pitch P x 4 bytes and the array must be 16-byte aligned, else the loader warp copies
     CUtensorMap fmap;
@@ -803,63 +828,138 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     }
-    const int max_rows = (int)std::min<int64_t>(n_trip, (int64_t)s.nb * (s.nb + 1) / 2);
-    const int tiles = (int)cdiv(max_rows, TM);
-    // Grouped (several tiles share each field chunk) or a group per tile: whichever
-    // finishes first by a simple count of CTA waves x work per CTA, in tenths of a
-    // tile's chunk step: per chunk 10 per tile plus 3 for bringing the chunk in,
-    // and 80 per tile for its epilogue (fitted to same-GPU timings of both forms on
-    // grids of 144^2 to 576^2 pixels).  Lists given by the caller are not grouped.
-    Setup &ms = const_cast<Setup &>(s);
-    if (d_ijk == s.d_ijk && ms.tc_groups < 0) ms.tc_groups = canonical_groups(s, G.NP, GMAX);
-    auto ranges_for = [&](int groups) {   // pixel range per CTA: whole waves, at most 4096 pixels
-        int64_t per = 0;                   // (bounds the FP32 accumulation length in the tensor core)
-        for (int waves = 1;; ++waves) {
-            const int64_t ranges = std::max<int64_t>(1, (int64_t)ctx->sm_count * waves / groups);
-            per = cdiv(cdiv(G.P, ranges), KC) * KC;
-            if (per <= 4096) return per;
-        }
-    };
-    auto makespan = [&](int groups, int per_group, int64_t per) {
-        const int64_t ctas = groups * cdiv(G.P, per);
-        return cdiv(ctas, ctx->sm_count) * (cdiv(per, KC) * (10 * per_group + 3) + 80 * per_group);
-    };
-    int groups = tiles, gmax = 1;
-    int64_t per = ranges_for(tiles);
-    if (d_ijk == s.d_ijk && ms.tc_groups < tiles) {
-        const int gg = ms.tc_groups;
-        const int64_t pg = ranges_for(gg);
-        if (makespan(gg, (int)cdiv(tiles, gg), pg) < makespan(tiles, 1, per)) {
-            groups = gg;
-            gmax = GMAX;
-            per = pg;
-        }
-    }
-    G.per_split = per;
-    const int64_t nsplit = cdiv(G.P, per);
+    const int64_t nsplit = cdiv(G.P, G.per_split);
     int4 *rows = (int4 *)workspace(ctx, "tc.rows", sizeof(int4) * std::max(max_rows, 1));
     int2 *tl = (int2 *)workspace(ctx, "tc.tiles", sizeof(int2) * std::max(tiles, 1));
     int2 *gr = (int2 *)workspace(ctx, "tc.groups", sizeof(int2) * std::max(tiles, 1));
     int *ctl = (int *)workspace(ctx, "tc.ctl", sizeof(int) * 2);
-    double *partial = (double *)workspace(ctx, "tc.partial", sizeof(double) * nsplit * n_trip);
-    if (!rows || !tl || !gr || !ctl || !partial) return fail(ctx, ABS_ERR_OOM, "split-BF16 workspace");
+    if (!rows || !tl || !gr || !ctl) return fail(ctx, ABS_ERR_OOM, "split-BF16 workspace");
     cudaStream_t st = ctx->stream;
     auto kern = KC == 128 ? k_triple_tc<128> : KC == 96 ? k_triple_tc<96> : k_triple_tc<64>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     {
-        StageTimer timer(ctx, "tc_rows");
+        StageTimer timer(ctx, e0 ? nullptr : "tc_rows");
         const size_t psmem = sizeof(uint32_t) * (size_t)s.nb * ((s.nb + 31) / 32);
-        k_rows<<<1, 1024, psmem, st>>>(n_trip, s.nb, G.NP, gmax, d_ijk, rows, ctl, tl, gr);
+        k_rows<<<1, 1024, psmem, st>>>(n_trip, s.nb, G.NP, L.gmax, d_ijk, rows, ctl, tl, gr);
     }
-    {
-        StageTimer timer(ctx, "triple_tc");
-        kern<<<dim3(groups, (unsigned)nsplit), NT, smem, st>>>(G, fmap, d_fields, rows, tl, gr, ctl, d_ijk, partial,
-                                                              ctx->d_err);
+    StageTimer timer(ctx, e0 ? nullptr : "triple_tc");
+    if (e0) cudaEventRecord(e0, st);
+    kern<<<dim3(L.groups, (unsigned)nsplit), NT, L.smem, st>>>(G, fmap, d_fields, rows, tl, gr, ctl, d_ijk, partial,
+                                                               ctx->d_err);
+    if (e1) cudaEventRecord(e1, st);
+    return check_launch(ctx, "split-BF16 triple sums");
+}
+
+abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields, int32_t n_trip,
+                            const int32_t *d_ijk, double *d_sum) {
+    if (n_trip == 0) return ABS_OK;
+    TcGeom G;
+    G.nb = s.nb;
+    G.NP = (int)cdiv(std::max(s.nb, 16), 16) * 16;
+    if (3 * G.NP > TMEM_COLS) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 accumulators exceed tensor memory");
+    G.tmem_cols = TMEM_COLS;
+    G.P = (int64_t)s.N * s.N;
+    G.n_trip = n_trip;
+    const int max_rows = (int)std::min<int64_t>(n_trip, (int64_t)s.nb * (s.nb + 1) / 2);
+    const int tiles = (int)cdiv(max_rows, TM);
+    Setup &ms = const_cast<Setup &>(s);
+    const bool canonical = d_ijk == s.d_ijk;
+    if (canonical && ms.tc_groups < 0) ms.tc_groups = canonical_groups(s, G.NP, GMAX);
+    const int tc_groups = canonical ? ms.tc_groups : tiles;   // lists given by the caller are not grouped
+    // the candidate shapes: every chunk width that fits, each with a tile per CTA and grouped
+    std::vector<TcLaunch> cand;
+    for (int kc : {128, 96, 64})
+        for (bool grp : {false, true}) {
+            TcLaunch L;
+            if ((!grp || tc_groups < tiles) && tc_shape(G, kc, grp, tiles, tc_groups, s.nb, ctx->sm_count, L))
+                cand.push_back(L);
+        }
+    if (cand.empty()) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 stages do not fit shared memory");
+    int64_t max_split = 1;
+    for (const TcLaunch &L : cand) max_split = std::max<int64_t>(max_split, cdiv(G.P, L.G.per_split));
+    double *partial = (double *)workspace(ctx, "tc.partial", sizeof(double) * max_split * n_trip);
+    if (!partial) return fail(ctx, ABS_ERR_OOM, "split-BF16 workspace");
+    // The shape: measured on this configuration's first eager call (autotuner), else
+    // the model: the widest chunk, grouped or one tile a CTA by a count of CTA waves x
+    // work per CTA in tenths of a tile's chunk step (per chunk 10 per tile plus 3 for
+    // bringing the chunk in, 80 per tile for its epilogue; fitted to same-GPU timings).
+    auto model = [&]() {
+        const TcLaunch *one = nullptr, *grp = nullptr;
+        for (const TcLaunch &L : cand) {
+            if (L.KC != cand[0].KC) continue;
+            (L.grouped ? grp : one) = &L;
+        }
+        auto makespan = [&](const TcLaunch &L) {
+            const int per_group = (int)cdiv(tiles, L.groups);
+            const int64_t ctas = L.groups * cdiv(G.P, L.G.per_split);
+            return cdiv(ctas, ctx->sm_count) * (cdiv(L.G.per_split, L.KC) * (10 * per_group + 3) + 80 * per_group);
+        };
+        if (grp && (!one || makespan(*grp) < makespan(*one))) return *grp;
+        return *one;
+    };
+    abs_ctx *root = ctx->parent ? ctx->parent : ctx;
+    const TcLaunch *pick = nullptr;
+    if (canonical) {
+        auto it = root->tc_shapes.find(s.key);
+        if (it != root->tc_shapes.end())
+            for (const TcLaunch &L : cand)
+                if (L.KC == it->second.kc && L.grouped == it->second.grouped) pick = &L;
     }
+    TcLaunch chosen;
+    if (pick) {
+        chosen = *pick;
+    } else {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(ctx->stream, &cs);
+        const bool tune = canonical && root->autotune && !ctx->profiling && cs == cudaStreamCaptureStatusNone &&
+                          ctx->stream != nullptr && cand.size() > 1;
+        chosen = model();
+        if (tune) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            float best = 1e30f;
+            if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+                for (const TcLaunch &L : cand) {
+                    float ms_min = 1e30f;
+                    for (int rep = 0; rep < 2; ++rep) {   // the first run warms caches and the code
+                        const abs_status rs = tc_run(ctx, s, L, d_fields, n_trip, d_ijk, max_rows, tiles, partial,
+                                                     e0, e1);
+                        if (rs != ABS_OK) {
+                            cudaEventDestroy(e0);
+                            cudaEventDestroy(e1);
+                            return rs;
+                        }
+                        float t = 0.f;
+                        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+                            cudaGetLastError();
+                            t = 1e30f;
+                        }
+                        ms_min = std::min(ms_min, t);
+                    }
+                    if (ms_min < best) {
+                        best = ms_min;
+                        chosen = L;
+                    }
+                }
+            }
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            cudaGetLastError();
+        }
+        if (canonical && (tune || !root->autotune || cand.size() == 1)) {
+            abs_ctx::TcShape &c = root->tc_shapes[s.key];
+            c.kc = chosen.KC;
+            c.grouped = chosen.grouped;
+            c.measured = tune;
+        }
+    }
+    const abs_status rs = tc_run(ctx, s, chosen, d_fields, n_trip, d_ijk, max_rows, tiles, partial, nullptr, nullptr);
+    if (rs != ABS_OK) return rs;
+    const int64_t nsplit = cdiv(G.P, chosen.G.per_split);
     {
         StageTimer timer(ctx, "triple_reduce");
-        k_tc_reduce<<<(int)cdiv(n_trip, 32), 256, 0, st>>>(n_trip, (int)nsplit,
-                                                             1.0 / ((double)s.N * (double)s.N), partial, d_sum);
+        k_tc_reduce<<<(int)cdiv(n_trip, 32), 256, 0, ctx->stream>>>(n_trip, (int)nsplit,
+                                                                   1.0 / ((double)s.N * (double)s.N), partial,
+                                                                   d_sum);
     }
     return check_launch(ctx, "split-BF16 triple sums");
 }

@@ -503,6 +503,71 @@ def test_estimate_host_pinned_replays(ctx):
 
 
 @pytest.mark.gpu
+def test_autotuner_split_bf16():
+    """The split-BF16 launch shape: measured on a configuration's first eager
+    call (autotuner on, the default) or from the cost model (off); either way
+    the estimate matches the oracle.  A batched call with untuned items tunes
+    them, and its lanes then reuse the shapes."""
+    absbuild.build()
+    inp = inputs(1)
+    wl = inp.wl
+    cfg = absmod.Config.from_workload(wl, precision=absmod.ABS_SPLIT_BF16)
+    est = oracle_run(("est", 1), wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+    uv, vis = to_dev(inp.uv), to_dev(synth.vis_as_float2(inp.vis))
+    ok = ~np.isnan(est.B)
+    big = ok & (np.abs(est.B) >= 1e-3 * np.nanmax(np.abs(est.B)))
+    for tune in (True, False):
+        st = torch.cuda.Stream(dev())
+        c = absmod.Context(0, st)
+        try:
+            c.autotune(tune)
+            assert c.tuned_shape(cfg)["kc"] == 0
+            with torch.cuda.stream(st):
+                for _ in range(3):      # eager (tunes), capture, replay
+                    B, T, E, _ = absmod.estimate(cfg, uv, vis, c)
+            c.sync()
+            shape = c.tuned_shape(cfg)
+            assert shape["kc"] in (64, 96, 128) and shape["measured"] == tune, shape
+            assert np.array_equal(T.cpu().numpy(), est.T)
+            Bg = B.cpu().numpy()
+            assert (np.abs(Bg[big] - est.B[big]) / np.abs(est.B[big])).max() <= BF16_TOL
+        finally:
+            c.close()
+    # batched: three split-BF16 configurations, tuned by the first call
+    st = torch.cuda.Stream(dev())
+    c = absmod.Context(0, st)
+    try:
+        rng = np.random.default_rng(5)
+        items, cfgs = [], []
+        with torch.cuda.stream(st):
+            for i in range(3):
+                w = synth.batch_item(rng, i)
+                bi = synth.make_inputs(3, 0, wl=w, n_vis=40000)
+                cf = absmod.Config.from_workload(bi.wl)
+                nt = len(absmod.abs_triplets(cf))
+                items.append((cf, to_dev(bi.uv), to_dev(synth.vis_as_float2(bi.vis)), nt, None,
+                              torch.empty(nt, dtype=torch.float64, device=dev()),
+                              torch.empty(nt, dtype=torch.int64, device=dev()),
+                              torch.empty(cf.n_bins, dtype=torch.float64, device=dev())))
+                cfgs.append(cf)
+            for _ in range(4):
+                c.abs_estimate_batched(items)
+            got = [tuple(o.clone() for o in it[5:]) for it in items]
+            for cf, it, (gB, gT, gE) in zip(cfgs, items, got):
+                assert c.tuned_shape(cf)["measured"]
+                B = torch.empty_like(gB); T = torch.empty_like(gT); E = torch.empty_like(gE)
+                c.abs_estimate(cf, it[1], it[2], it[3], None, B, T, E)
+                c.sync()
+                assert np.array_equal(gT.cpu().numpy(), T.cpu().numpy())
+                rB, gBn = B.cpu().numpy(), gB.cpu().numpy()
+                assert np.array_equal(np.isnan(rB), np.isnan(gBn))
+                m = ~np.isnan(rB)
+                assert np.allclose(gBn[m], rB[m], rtol=1e-9, atol=1e-12 * np.abs(rB[m]).max())
+    finally:
+        c.close()
+
+
+@pytest.mark.gpu
 def test_estimate_batched_uneven():
     """abs_estimate_batched over items of different grid sizes, ring counts
     and precisions equals abs_estimate item by item, on the eager call, the
