@@ -21,6 +21,9 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   (discrete Eq. bsana)
 * ellbar: direct closed form on a hand-built mask
 * normalise: closed forms above
+* shape_params / rebin (results layer): hand-worked triangle shapes
+  (equilateral, squeezed, folded), the bin edges, count-weighted means of a
+  constant and of a linear B, and the ensemble mean / spread of +-B
 """
 from __future__ import annotations
 
@@ -320,3 +323,69 @@ def beam_constants(theta_f_deg: float = 24.68):
     decor = np.exp(-np.pi ** 2 * th0 ** 2 * (dug ** 2 / 2.0) / 3.0)
     A = np.pi * th0 ** 2 / 3.0
     return {"theta0": th0, "du_g": dug, "decorrelation": decor, "A": A}
+
+
+# ------------------------------------------------------------------ results layer
+
+
+def shape_params(ellbar: np.ndarray, ijk: np.ndarray):
+    """The triangle shape of every ring triplet in the (l1, mu, t) form of Sec. 1.
+
+    The paper orders l1 >= l2 >= l3, which for a canonical triplet (i <= j <= k,
+    rings ascending in l) is (k, j, i); each side is its ring's mean l.  With
+    l1 + l2 + l3 = 0 as vectors, mu = -l1.l2 / (l1 l2) = (l1^2 + l2^2 - l3^2) /
+    (2 l1 l2) and t = l2 / l1, both evaluated left to right in FP64 without
+    fused operations (the kernel takes the same decisions from the same values).
+    """
+    ijk = np.asarray(ijk).reshape(-1, 3)
+    l3, l2, l1 = (np.asarray(ellbar, np.float64)[ijk[:, c]] for c in range(3))
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mu = ((l1 * l1 + l2 * l2) - l3 * l3) / ((2.0 * l1) * l2)
+        t = l2 / l1
+    return l1, mu, t
+
+
+def shape_cell(ijk: np.ndarray, mu: np.ndarray, t: np.ndarray, n_mu: int, n_t: int):
+    """Cell (ring of l1, mu bin, t bin) of every triplet: n_mu x n_t equal bins over
+    [0.5, 1] (the range of closed triangles with l1 >= l2 >= l3, Sec. 4); ring means
+    can put a shape just outside it, which is clamped into the edge bins."""
+    ijk = np.asarray(ijk).reshape(-1, 3)
+    def b(x, n):
+        v = np.floor((x - 0.5) * (2.0 * n))
+        v = np.where(np.isfinite(v), v, 0)
+        return np.clip(v, 0, n - 1).astype(np.int64)
+    return (ijk[:, 2] * n_mu + b(mu, n_mu)) * n_t + b(t, n_t)
+
+
+def rebin(B: np.ndarray, T: np.ndarray, ellbar: np.ndarray, ijk: np.ndarray, n_bins: int,
+          n_mu: int = 5, n_t: int = 5):
+    """Count-weighted (l1, mu, t) averages of B and their ensemble statistics (Sec. 4).
+
+    Per realisation r, cell c: B_r(c) = sum T B_r / sum T over the cell's triplets
+    with T > 0 and finite B (the triangle count is the weight, Sec. 4); then over
+    the R realisations the mean and the spread sigma^2 = <B_r(c)^2> - <B_r(c)>^2.
+    Returns (mean, sigma, weight = sum T) as [n_bins][n_mu][n_t]; cells without
+    triangles are NaN (weight 0).
+    """
+    B = np.atleast_2d(np.asarray(B, np.float64))
+    T = np.asarray(T, np.int64)
+    _, mu, t = shape_params(ellbar, ijk)
+    cell = shape_cell(ijk, mu, t, n_mu, n_t)
+    nc = n_bins * n_mu * n_t
+    den = np.zeros(nc)
+    num = np.zeros((B.shape[0], nc))
+    for r in range(B.shape[0]):
+        for q in range(len(T)):
+            if T[q] > 0 and np.isfinite(B[r, q]):
+                num[r, cell[q]] += float(T[q]) * B[r, q]
+                if r == 0:
+                    den[cell[q]] += float(T[q])
+    with np.errstate(invalid="ignore", divide="ignore"):
+        v = num / den
+        mean = v.mean(axis=0)
+        var = (v * v).mean(axis=0) - mean * mean
+    sigma = np.sqrt(np.maximum(var, 0.0))
+    sigma[den == 0] = np.nan
+    shape = (n_bins, n_mu, n_t)
+    return mean.reshape(shape), sigma.reshape(shape), den.reshape(shape)
+

@@ -537,3 +537,72 @@ def test_paper_constants():
     assert round(c["du_g"], 0) == vals["du_g_approx"]
     assert round(c["decorrelation"], 2) == vals["decorrelation"]
     assert c["A"] == pytest.approx(np.pi * (0.6 * np.deg2rad(vals["theta_F_deg"])) ** 2 / 3)
+
+
+# ----------------------------------------------------------------- results layer: (l1, mu, t) rebinning
+
+
+def test_shape_params_match_vector_triangles():
+    """mu and t against triangles built as 2-D vectors l1 + l2 + l3 = 0: mu is
+    -l1.l2 / (|l1||l2|) taken from the vectors' dot product, t = |l2| / |l1|;
+    equilateral (0.5, 1), folded (1, 0.5) and a 3-4-5 triangle (0.8, 0.8)."""
+    rng = np.random.default_rng(3)
+    cases = []
+    for _ in range(20):
+        a = rng.uniform(0.2, 3.0, 2)
+        b = rng.uniform(0.2, 3.0, 2)
+        v = [a, b, -(a + b)]
+        lens = np.array([np.hypot(*x) for x in v])
+        o = np.argsort(-lens)                       # l1 >= l2 >= l3
+        l1v, l2v = v[o[0]], v[o[1]]
+        mu_ref = -np.dot(l1v, l2v) / (lens[o[0]] * lens[o[1]])
+        cases.append((lens[o[2]], lens[o[1]], lens[o[0]], mu_ref, lens[o[1]] / lens[o[0]]))
+    cases += [(1.0, 1.0, 1.0, 0.5, 1.0), (1.0, 1.0, 2.0, 1.0, 0.5), (3.0, 4.0, 5.0, 0.8, 0.8)]
+    ell = np.array([x for c in cases for x in c[:3]])
+    ijk = np.arange(len(ell)).reshape(-1, 3)
+    l1, mu, t = oracle.shape_params(ell, ijk)
+    for q, c in enumerate(cases):
+        assert l1[q] == c[2]
+        assert abs(mu[q] - c[3]) < 1e-12 and abs(t[q] - c[4]) < 1e-12
+
+
+def test_shape_cell_edges_and_clamping():
+    ijk = np.array([[0, 0, 2]] * 7)
+    # bins of width 0.1 from 0.5; values away from the edges except the exact ones 0.5 and 1
+    mu = np.array([0.5, 0.5999999, 0.625, 0.95, 1.0, 0.49, 1.02])
+    t = np.array([1.0, 0.5, 0.55, 0.75, 0.9999, 0.3, np.nan])
+    c = oracle.shape_cell(ijk, mu, t, 5, 5)
+    want = [(0, 4), (0, 0), (1, 0), (4, 2), (4, 4), (0, 0), (4, 0)]
+    assert [tuple(divmod(int(x) - 2 * 25, 5)) for x in c] == want
+
+
+def _rebin_case(seed=4, nb=6, R=3):
+    rng = np.random.default_rng(seed)
+    ell = np.sort(rng.uniform(50.0, 400.0, nb))
+    ijk = np.array([(i, j, k) for i in range(nb) for j in range(i, nb) for k in range(j, nb)
+                    if ell[k] < ell[i] + ell[j]])
+    T = rng.integers(0, 50, len(ijk))
+    T[::5] = 0
+    B = rng.normal(size=(R, len(ijk)))
+    B[:, T == 0] = np.nan
+    return ell, ijk, T, B, nb
+
+
+def test_rebin_constant_and_weights():
+    ell, ijk, T, B, nb = _rebin_case()
+    mean, sig, w = oracle.rebin(np.full_like(B, 2.5), T, ell, ijk, nb)
+    live = w > 0
+    assert np.allclose(mean[live], 2.5, rtol=0, atol=1e-14) and np.all(sig[live] < 1e-7)
+    assert np.all(np.isnan(mean[~live])) and w.sum() == T.sum()
+
+
+def test_rebin_is_linear_and_symmetric_ensembles_spread():
+    ell, ijk, T, B, nb = _rebin_case(R=1)
+    m1, _, w = oracle.rebin(B, T, ell, ijk, nb)
+    m2, _, _ = oracle.rebin(3.0 * B - 1.0, T, ell, ijk, nb)
+    live = w > 0
+    assert np.allclose(m2[live], 3.0 * m1[live] - 1.0, rtol=1e-12, atol=1e-12)
+    # two realisations +B and -B: mean 0, spread |count-weighted mean of B|
+    mean, sig, _ = oracle.rebin(np.vstack([B, -B]), T, ell, ijk, nb)
+    assert np.allclose(mean[live], 0.0, atol=1e-14)
+    assert np.allclose(sig[live], np.abs(m1[live]), rtol=1e-9, atol=1e-14)
