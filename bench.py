@@ -550,6 +550,15 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     batched = R * reps / (e0.elapsed_time(e1) * 1e-3)
+    # results layer over the batch: (l1, mu, t) cells (5 x 5 shape bins) and ensemble mean / spread
+    cells = [torch.empty((cfg.n_bins, 5, 5), dtype=torch.float64, device=dev) for _ in range(3)]
+    ctx.abs_rebin(cfg, BR, T, E, None, 5, 5, *cells)
+    e0.record(stream)
+    for _ in range(reps):
+        ctx.abs_rebin(cfg, BR, T, E, None, 5, 5, *cells)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    rebin_us = 1e3 * e0.elapsed_time(e1) / reps
 
     # uneven batch: independent items of different grid sizes, rings and precisions in one call
     uneven = None
@@ -661,6 +670,7 @@ def run_ours(args):
                          "sample": "one full realisation of the workload (plain C FP64, brute-force "
                                    "closed-triangle sums)"},
         "batched": {"value": batched, "unit": UNIT, "realisations_per_call": R,
+                    "rebin_us": round(rebin_us, 2),
                     "note": "abs_estimate_many: realisations sharing one baseline set (plan, counts "
                             "and ring tables once per call)"},
         "batched_uneven": {"value": uneven, "unit": UNIT, "items_per_call": args.batch_items,

@@ -260,6 +260,28 @@ typedef struct abs_stage_time {
 abs_status abs_profile(abs_ctx *ctx, int32_t on);
 abs_status abs_profile_read(abs_ctx *ctx, int32_t cap, int32_t *n, abs_stage_time *out);
 
+/* Results layer (Sec. 4): B in the (l1, mu, t) shape form, count-weighted, and
+ * its ensemble statistics over realisations.  A canonical triplet (i, j, k) is
+ * the paper's l1 >= l2 >= l3 as (k, j, i), each side its ring's mean l
+ * (d_ellbar, as abs_estimate writes it); mu = (l1^2 + l2^2 - l3^2) / (2 l1 l2),
+ * t = l2 / l1, in n_mu x n_t equal bins over [0.5, 1] (values just outside,
+ * from ring means, go to the edge bins).  Per realisation r and cell c:
+ * B_r(c) = sum T B_r / sum T over the cell's triplets with T > 0 and finite B;
+ * then d_mean[c] = <B_r(c)>, d_sigma[c]^2 = <B_r(c)^2> - <B_r(c)>^2 over the
+ * n_real realisations, d_weight[c] = sum T.  Cells without triangles: NaN
+ * (weight 0).
+ *   d_B       [n_real][n_trip] FP64 (abs_estimate_many's output)
+ *   d_count   [n_trip] int64 triangle counts
+ *   d_ellbar  [n_bins] FP64 mean l per ring
+ *   d_ijk     [n_trip][3] canonical triplets, or NULL for cfg's own list
+ *   n_mu, n_t bins in mu and t, each in [1, 64]
+ *   d_mean, d_sigma, d_weight  [n_bins][n_mu][n_t] FP64 outputs (any may be NULL)
+ * Asynchronous on the context's stream; the FP64 sums are atomic, so their
+ * last bits may vary from run to run. */
+abs_status abs_rebin(abs_ctx *ctx, const abs_config *cfg, int32_t n_real, int32_t n_trip, const double *d_B,
+                     const int64_t *d_count, const double *d_ellbar, const int32_t *d_ijk, int32_t n_mu,
+                     int32_t n_t, double *d_mean, double *d_sigma, double *d_weight);
+
 /* Autotuner of the split-BF16 triple-sum kernel (Sec. 2, Eq. estimator_t on
  * tensor cores).  On the first call of a configuration that runs eagerly (not
  * under stream capture, not while the stage profiler runs) with the canonical

@@ -89,6 +89,7 @@ def load(path: str | None = None):
         "abs_profile": ([P, i32], ctypes.c_int),
         "abs_profile_read": ([P, i32, P, P], ctypes.c_int),
         "abs_autotune": ([P, i32], ctypes.c_int),
+        "abs_rebin": ([P, P, i32, i32, P, P, P, P, i32, i32, P, P, P], ctypes.c_int),
         "abs_tuned_shape": ([P, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -210,6 +211,17 @@ class Context:
     def profile(self, on: bool = True):
         """Turn the per-kernel CUDA-event profiler on (clearing totals) or off."""
         _check(load().abs_profile(self.h, 1 if on else 0), self.h, "abs_profile")
+
+    def abs_rebin(self, cfg: "Config", B, counts, ellbar, ijk=None, n_mu: int = 5, n_t: int = 5,
+                  mean=None, sigma=None, weight=None):
+        """(l1, mu, t) cells of B ([R][n_trip] or [n_trip] CUDA FP64): count-weighted means per
+        realisation, then their ensemble mean and spread; outputs [n_bins][n_mu][n_t] FP64."""
+        n_real = B.shape[0] if B.dim() == 2 else 1
+        n_trip = B.shape[-1]
+        _check(load().abs_rebin(self.h, cfg.ref(), int(n_real), int(n_trip), _ptr(B), _ptr(counts), _ptr(ellbar),
+                                None if ijk is None else _ptr(ijk), int(n_mu), int(n_t),
+                                None if mean is None else _ptr(mean), None if sigma is None else _ptr(sigma),
+                                None if weight is None else _ptr(weight)), self.h, "abs_rebin")
 
     def autotune(self, on: bool = True):
         """Turn the split-BF16 launch-shape autotuner on (default) or off (cost model)."""

@@ -183,6 +183,10 @@ abs_status launch_normalise(abs_ctx *ctx, const Setup &s, int32_t n_trip, const 
 abs_status launch_normalise_w(abs_ctx *ctx, const Setup &s, int32_t n_trip, const double *d_sum,
                               const double *d_sumw, double *d_B);
 abs_status launch_ellbar(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, double *d_ellbar);
+// Count-weighted (l1, mu, t) cells of B and their ensemble mean and spread (results layer).
+abs_status launch_rebin(abs_ctx *ctx, const Setup &s, int32_t n_real, int32_t n_trip, const double *d_B,
+                        const int64_t *d_count, const double *d_ellbar, const int32_t *d_ijk, int32_t n_mu,
+                        int32_t n_t, double *d_mean, double *d_sigma, double *d_weight);
 abs_status launch_check_triplets(abs_ctx *ctx, const Setup &s, int32_t n_trip,
                                  const int32_t *d_ijk);
 

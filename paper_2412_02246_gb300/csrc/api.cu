@@ -491,6 +491,27 @@ abs_status abs_profile(abs_ctx *ctx, int32_t on) {
     return ABS_OK;
 }
 
+abs_status abs_rebin(abs_ctx *ctx, const abs_config *cfg, int32_t n_real, int32_t n_trip, const double *d_B,
+                     const int64_t *d_count, const double *d_ellbar, const int32_t *d_ijk, int32_t n_mu,
+                     int32_t n_t, double *d_mean, double *d_sigma, double *d_weight) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    abs_status st;
+    const Setup *s = get_setup(ctx, cfg, st);
+    if (!s) return st;
+    if (n_real < 1 || n_trip < 0) return fail(ctx, ABS_ERR_INVALID_ARG, "n_real must be >= 1 and n_trip >= 0");
+    if (n_mu < 1 || n_mu > 64 || n_t < 1 || n_t > 64) return fail(ctx, ABS_ERR_INVALID_ARG, "n_mu, n_t must be in [1, 64]");
+    if (n_trip > 0 && (!d_B || !d_count || !d_ellbar))
+        return fail(ctx, ABS_ERR_INVALID_ARG, "d_B, d_count and d_ellbar are required");
+    if (!d_ijk) {
+        if (n_trip != (int32_t)(s->ijk.size() / 3))
+            return fail(ctx, ABS_ERR_INVALID_ARG, "n_trip must equal the canonical triplet count when d_ijk is NULL");
+        d_ijk = s->d_ijk;
+    }
+    return launch_rebin(ctx, *s, n_real, n_trip, d_B, d_count, d_ellbar, d_ijk, n_mu, n_t, d_mean, d_sigma,
+                        d_weight);
+}
+
 abs_status abs_autotune(abs_ctx *ctx, int32_t enable) {
     if (!ctx) return ABS_ERR_INVALID_ARG;
     ctx->autotune = enable != 0;

@@ -503,6 +503,42 @@ def test_estimate_host_pinned_replays(ctx):
 
 
 @pytest.mark.gpu
+def test_rebin_shapes_and_ensemble(ctx):
+    """abs_rebin over four realisations of the tiny workload (abs_estimate_many):
+    the (l1, mu, t) cells equal the oracle's rebinning of the same B, counts and
+    ring means (weights exact, values to rounding), and, end to end, the
+    oracle's rebinning of its own estimates within the FP32 tolerance."""
+    R = 4
+    ins = [inputs(0, r) for r in range(R)]
+    wl = ins[0].wl
+    cfg = absmod.Config.from_workload(wl)
+    ijk = absmod.abs_triplets(cfg)
+    nt, nb = len(ijk), cfg.n_bins
+    vis = np.stack([synth.vis_as_float2(i.vis) for i in ins])
+    B = torch.empty((R, nt), dtype=torch.float64, device=dev())
+    T = torch.empty(nt, dtype=torch.int64, device=dev())
+    E = torch.empty(nb, dtype=torch.float64, device=dev())
+    ctx.abs_estimate_many(cfg, to_dev(ins[0].uv), to_dev(vis), nt, None, B, T, E)
+    outs = [torch.full((nb, 5, 5), -7.0, dtype=torch.float64, device=dev()) for _ in range(3)]
+    ctx.abs_rebin(cfg, B, T, E, None, 5, 5, *outs)
+    ctx.sync()
+    gm, gs, gw = (o.cpu().numpy() for o in outs)
+    Bh, Th, Eh = B.cpu().numpy(), T.cpu().numpy(), E.cpu().numpy()
+    om, osg, ow = oracle.rebin(Bh, Th, Eh, ijk, nb)
+    assert np.array_equal(gw, ow) and ow.sum() == Th.sum() and (ow > 0).sum() >= 10
+    live = ow > 0
+    assert np.array_equal(np.isnan(gm), ~live) and np.array_equal(np.isnan(gs), ~live)
+    scale = np.abs(om[live]).max()
+    assert np.allclose(gm[live], om[live], rtol=1e-12, atol=1e-13 * scale)
+    assert np.allclose(gs[live] ** 2, osg[live] ** 2, rtol=1e-9, atol=1e-12 * scale ** 2)
+    # end to end against the oracle's own estimates
+    est = [oracle_run(("rebin", r), wl.n_grid, wl.du, wl.ell_edges, ins[0].uv, ins[r].vis) for r in range(R)]
+    em, _, ew = oracle.rebin(np.stack([e.B for e in est]), est[0].T, est[0].ellbar, ijk, nb)
+    assert np.array_equal(ew, gw)
+    assert np.allclose(gm[live], em[live], rtol=0, atol=SUM_TOL * scale)
+
+
+@pytest.mark.gpu
 def test_autotuner_split_bf16():
     """The split-BF16 launch shape: measured on a configuration's first eager
     call (autotuner on, the default) or from the cost model (off); either way
