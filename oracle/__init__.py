@@ -21,6 +21,8 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   (discrete Eq. bsana)
 * ellbar: direct closed form on a hand-built mask
 * normalise: closed forms above
+* bana_d (discretely sampled prediction): constant C, a pure-Python
+  enumeration on a tiny grid, symmetry in the three rings
 * shape_params / rebin (results layer): hand-worked triangle shapes
   (equilateral, squeezed, folded), the bin edges, count-weighted means of a
   constant and of a linear B, and the ensemble mean / spread of +-B
@@ -70,6 +72,8 @@ def _load():
     lib.orc_mean_grid.restype = None
     lib.orc_triple_bruteforce.argtypes = [i32, P, P, i32, P, i32, P, P, P, P]
     lib.orc_triple_bruteforce.restype = ctypes.c_int
+    lib.orc_bana_bruteforce.argtypes = [i32, P, P, i32, P, i32, P, P, P]
+    lib.orc_bana_bruteforce.restype = ctypes.c_int
     lib.orc_triple_one.argtypes = [i32, P, P, i32, P, i32, i32, i32, P, P, P]
     lib.orc_triple_one.restype = ctypes.c_int
     lib.orc_ellbar.argtypes = [i32, f32, P, i32, P, P]
@@ -388,4 +392,25 @@ def rebin(B: np.ndarray, T: np.ndarray, ellbar: np.ndarray, ijk: np.ndarray, n_b
     sigma[den == 0] = np.nan
     shape = (n_bins, n_mu, n_t)
     return mean.reshape(shape), sigma.reshape(shape), den.reshape(shape)
+
+
+def bana_d(C: np.ndarray, filled: np.ndarray, q: np.ndarray, ijk: np.ndarray, f_over_sigma: float):
+    """[B_Ana]_d of Sec. 4 (Fig. 2): Eq. bsana's 2 (f_NG / sigma_T) (C1 C2 + C2 C3 + C3 C1)
+    averaged over the closed triangles of filled cells in each ring triplet, with C the
+    angular power spectrum at each cell's l (real [n][n], FFT order).  NaN where T = 0.
+    Returns (bana_d, T)."""
+    n = filled.shape[0]
+    ijk = np.ascontiguousarray(np.asarray(ijk, np.int32).reshape(-1, 3))
+    nt = len(ijk)
+    S = np.zeros(max(nt, 1))
+    T = np.zeros(max(nt, 1), np.int64)
+    rc = _load().orc_bana_bruteforce(n, _p(np.ascontiguousarray(C, np.float64)),
+                                     _p(np.ascontiguousarray(filled, np.uint8)), len(q) - 1,
+                                     _p(np.ascontiguousarray(q, np.int64)), nt, _p(ijk), _p(S), _p(T))
+    if rc != 0:
+        raise MemoryError("oracle bana_d")
+    S, T = S[:nt], T[:nt]
+    with np.errstate(invalid="ignore", divide="ignore"):
+        out = np.where(T > 0, 2.0 * f_over_sigma * S / T, np.nan)
+    return out, T
 

@@ -244,6 +244,41 @@ int orc_triple_bruteforce(int32_t n, const double *X, const uint8_t *filled, int
     return 0;
 }
 
+/* The discretely sampled analytic bispectrum of the quadratic sky (Sec. 4,
+ * Fig. 2): for every ordered closed triangle (g1 in a_i, g2 in a_j, g3 in a_k,
+ * all filled) the sum of C(g1) C(g2) + C(g2) C(g3) + C(g3) C(g1), with C a
+ * real value per cell ([n][n], FFT order), and the triangle count. */
+int orc_bana_bruteforce(int32_t n, const double *C, const uint8_t *filled, int32_t n_bins,
+                        const int64_t *q, int32_t n_trip, const int32_t *ijk, double *S, int64_t *T)
+{
+    ring_cell *c = NULL;
+    const int32_t nc = collect_ring_cells(n, filled, n_bins, q, &c);
+    const int64_t nb = n_bins, nb3 = nb * nb * nb;
+    double *sd = (double *)calloc((size_t)nb3, sizeof(double));
+    int64_t *td = (int64_t *)calloc((size_t)nb3, sizeof(int64_t));
+    if (!sd || !td) { free(c); free(sd); free(td); return 2; }
+    for (int32_t a = 0; a < nc; ++a) {
+        const double c1 = C[c[a].p];
+        for (int32_t b = 0; b < nc; ++b) {
+            int64_t p3 = 0;
+            const int32_t k = bin_of_cell(n, filled, n_bins, q, -(c[a].gx + c[b].gx),
+                                          -(c[a].gy + c[b].gy), &p3);
+            if (k < 0) continue;
+            const double c2 = C[c[b].p], c3 = C[p3];
+            const int64_t idx = ((int64_t)c[a].m * nb + c[b].m) * nb + k;
+            sd[idx] += c1 * c2 + c2 * c3 + c3 * c1;
+            td[idx] += 1;
+        }
+    }
+    for (int32_t t = 0; t < n_trip; ++t) {
+        const int64_t idx = ((int64_t)ijk[3 * t] * nb + ijk[3 * t + 1]) * nb + ijk[3 * t + 2];
+        S[t] = sd[idx];
+        T[t] = td[idx];
+    }
+    free(c); free(sd); free(td);
+    return 0;
+}
+
 /* The same sums for one triplet only (cost |a_i| |a_j|): used to check
  * sampled outputs of full-size runs. */
 int orc_triple_one(int32_t n, const double *X, const uint8_t *filled, int32_t n_bins,

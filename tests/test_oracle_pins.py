@@ -606,3 +606,64 @@ def test_rebin_is_linear_and_symmetric_ensembles_spread():
     mean, sig, _ = oracle.rebin(np.vstack([B, -B]), T, ell, ijk, nb)
     assert np.allclose(mean[live], 0.0, atol=1e-14)
     assert np.allclose(sig[live], np.abs(m1[live]), rtol=1e-9, atol=1e-14)
+
+
+# ----------------------------------------------------------------- discretely sampled prediction [B_Ana]_d
+
+
+def _bana_case(seed=12, n=14):
+    rng = np.random.default_rng(seed)
+    filled = full_mask(n)
+    gx, gy = coords(n)
+    drop = rng.random((n, n)) < 0.2
+    filled[drop] = 0
+    filled[(-gy[drop]) % n, (-gx[drop]) % n] = 0
+    ell = 2 * np.pi * np.hypot(gx, gy)
+    with np.errstate(divide="ignore"):
+        C = np.where(ell > 0, ell ** -2.5, 0.0) * 1e4
+    edges = 2 * np.pi * np.array([1.2, 2.6, 4.0, 5.7])
+    return C, filled, oracle.ring_q(edges, 1.0)
+
+
+def test_bana_d_matches_python_enumeration_tiny():
+    """Sum of C1 C2 + C2 C3 + C3 C1 over every ordered closed triangle of filled
+    ring cells, enumerated in pure Python, on a tiny grid with holes; all 27
+    ring orders (the sum is symmetric in them, so the permuted triplets agree)."""
+    C, filled, q = _bana_case()
+    n = C.shape[0]
+    half = n // 2 - 1
+    cells = []
+    for gy in range(-half, half + 1):
+        for gx in range(-half, half + 1):
+            r2 = gx * gx + gy * gy
+            m = [b for b in range(len(q) - 1) if q[b] <= r2 < q[b + 1]]
+            if filled[gy % n, gx % n] and m:
+                cells.append((gx, gy, m[0], C[gy % n, gx % n]))
+    S, T = {}, {}
+    for a in cells:
+        for b in cells:
+            for c in cells:
+                if a[0] + b[0] + c[0] == 0 and a[1] + b[1] + c[1] == 0:
+                    key = (a[2], b[2], c[2])
+                    S[key] = S.get(key, 0.0) + a[3] * b[3] + b[3] * c[3] + c[3] * a[3]
+                    T[key] = T.get(key, 0) + 1
+    allc = np.array(list(itertools.product(range(3), repeat=3)), np.int32)
+    out, Tb = oracle.bana_d(C, filled, q, allc, 0.05)
+    for t, (i, j, k) in enumerate(allc):
+        assert Tb[t] == T.get((i, j, k), 0)
+        if Tb[t]:
+            assert out[t] == pytest.approx(2 * 0.05 * S[(i, j, k)] / T[(i, j, k)], rel=1e-12)
+            assert out[t] == pytest.approx(out[list(map(tuple, allc)).index((k, i, j))], rel=1e-12)
+        else:
+            assert np.isnan(out[t])
+
+
+def test_bana_d_constant_spectrum():
+    """C = c on every cell: each triangle contributes 3 c^2, so [B_Ana]_d = 6 (f/sigma) c^2
+    (the equilateral form of Eq. bsana) on every triplet with triangles."""
+    _, filled, q = _bana_case()
+    C = np.full(filled.shape, 0.7)
+    ijk = oracle.triplets(q)
+    out, T = oracle.bana_d(C, filled, q, ijk, 0.2)
+    assert np.all(T[T > 0] > 0) and (T > 0).sum() >= 3
+    assert np.allclose(out[T > 0], 6 * 0.2 * 0.49, rtol=1e-14)
