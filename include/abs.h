@@ -282,6 +282,25 @@ abs_status abs_rebin(abs_ctx *ctx, const abs_config *cfg, int32_t n_real, int32_
                      const int64_t *d_count, const double *d_ellbar, const int32_t *d_ijk, int32_t n_mu,
                      int32_t n_t, double *d_mean, double *d_sigma, double *d_weight);
 
+/* Discretely sampled analytic prediction [B_Ana]_d (Sec. 4, Fig. 2): Eq. bsana,
+ * B_Ana = 2 (f_NG / sigma_T) (C1 C2 + C2 C3 + C3 C1), averaged over the same
+ * closed triangles of filled cells that the estimate averages over:
+ *   d_out[t] = 2 f_over_sigma sum (C(g1) C(g2) + C(g2) C(g3) + C(g3) C(g1)) / T_t
+ * over ordered closed triangles (g1, g2, g3) in the triplet's rings, NaN where
+ * T_t = 0.  It runs through the same transforms as the estimate: fields of C
+ * on the filled ring cells and of the unit mask, and a mixed triple sum.
+ *   d_C      [n_grid][n_grid] FP64, C(l_g) per uv cell in FFT order; C(l_-g)
+ *            must equal C(l_g) (a function of |g|, as an angular power spectrum is)
+ *   d_mask   [n_grid][n_grid] uint8 filled mask (abs_grid's)
+ *   d_count  [n_trip] int64 triangle counts T of the same mask (abs_triple's or
+ *            abs_estimate's)
+ *   d_ijk    [n_trip][3] canonical triplets or NULL for cfg's list
+ *   d_out    [n_trip] FP64
+ * Asynchronous on the context's stream. */
+abs_status abs_bana_d(abs_ctx *ctx, const abs_config *cfg, const double *d_C, const uint8_t *d_mask,
+                      int32_t n_trip, const int32_t *d_ijk, const int64_t *d_count, double f_over_sigma,
+                      double *d_out);
+
 /* Autotuner of the split-BF16 triple-sum kernel (Sec. 2, Eq. estimator_t on
  * tensor cores).  On the first call of a configuration that runs eagerly (not
  * under stream capture, not while the stage profiler runs) with the canonical

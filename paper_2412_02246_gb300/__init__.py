@@ -90,6 +90,7 @@ def load(path: str | None = None):
         "abs_profile_read": ([P, i32, P, P], ctypes.c_int),
         "abs_autotune": ([P, i32], ctypes.c_int),
         "abs_rebin": ([P, P, i32, i32, P, P, P, P, i32, i32, P, P, P], ctypes.c_int),
+        "abs_bana_d": ([P, P, P, P, i32, P, P, ctypes.c_double, P], ctypes.c_int),
         "abs_tuned_shape": ([P, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -222,6 +223,12 @@ class Context:
                                 None if ijk is None else _ptr(ijk), int(n_mu), int(n_t),
                                 None if mean is None else _ptr(mean), None if sigma is None else _ptr(sigma),
                                 None if weight is None else _ptr(weight)), self.h, "abs_rebin")
+
+    def abs_bana_d(self, cfg: "Config", C, mask, counts, out, ijk=None, f_over_sigma: float = 0.3):
+        """[B_Ana]_d per triplet (CUDA FP64 out) from C(l_g) per uv cell (CUDA FP64 [n][n]),
+        the filled mask (CUDA uint8 [n][n]) and the triangle counts of that mask."""
+        _check(load().abs_bana_d(self.h, cfg.ref(), _ptr(C), _ptr(mask), int(out.shape[0]), _ptr(ijk),
+                                 _ptr(counts), float(f_over_sigma), _ptr(out)), self.h, "abs_bana_d")
 
     def autotune(self, on: bool = True):
         """Turn the split-BF16 launch-shape autotuner on (default) or off (cost model)."""

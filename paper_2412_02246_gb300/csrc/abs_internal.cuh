@@ -183,6 +183,13 @@ abs_status launch_normalise(abs_ctx *ctx, const Setup &s, int32_t n_trip, const 
 abs_status launch_normalise_w(abs_ctx *ctx, const Setup &s, int32_t n_trip, const double *d_sum,
                               const double *d_sumw, double *d_B);
 abs_status launch_ellbar(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, double *d_ellbar);
+// Fields of a real value per filled cell (d_c [n][n], C(l_g) = C(l_-g); nullptr: the unit mask).
+abs_status launch_filter_fft_real(abs_ctx *ctx, const Setup &s, const double *d_c, const uint8_t *d_mask,
+                                  float *d_fields);
+// out[t] = 2 fs sum_p (P_i P_j I_k + P_j P_k I_i + P_k P_i I_j) / (N^2 T_t): the discretely
+// sampled prediction from C fields P and unit-mask fields I (NaN where T = 0).
+abs_status launch_bana_sums(abs_ctx *ctx, const Setup &s, const float *d_P, const float *d_I, int32_t n_trip,
+                            const int32_t *d_ijk, const int64_t *d_count, double fs, double *d_out);
 // Count-weighted (l1, mu, t) cells of B and their ensemble mean and spread (results layer).
 abs_status launch_rebin(abs_ctx *ctx, const Setup &s, int32_t n_real, int32_t n_trip, const double *d_B,
                         const int64_t *d_count, const double *d_ellbar, const int32_t *d_ijk, int32_t n_mu,

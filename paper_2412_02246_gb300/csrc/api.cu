@@ -512,6 +512,34 @@ abs_status abs_rebin(abs_ctx *ctx, const abs_config *cfg, int32_t n_real, int32_
                         d_weight);
 }
 
+abs_status abs_bana_d(abs_ctx *ctx, const abs_config *cfg, const double *d_C, const uint8_t *d_mask,
+                      int32_t n_trip, const int32_t *d_ijk, const int64_t *d_count, double f_over_sigma,
+                      double *d_out) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    abs_status st;
+    const Setup *s = get_setup(ctx, cfg, st);
+    if (!s) return st;
+    if (n_trip < 0) return fail(ctx, ABS_ERR_INVALID_ARG, "n_trip < 0");
+    if (!d_C || !d_mask || (n_trip > 0 && (!d_count || !d_out)))
+        return fail(ctx, ABS_ERR_INVALID_ARG, "d_C, d_mask, d_count and d_out are required");
+    if (!std::isfinite(f_over_sigma)) return fail(ctx, ABS_ERR_INVALID_ARG, "f_over_sigma must be finite");
+    if (!d_ijk) {
+        if (n_trip != (int32_t)(s->ijk.size() / 3))
+            return fail(ctx, ABS_ERR_INVALID_ARG, "n_trip must equal the canonical triplet count when d_ijk is NULL");
+        d_ijk = s->d_ijk;
+    } else {
+        ABS_CHECK(launch_check_triplets(ctx, *s, n_trip, d_ijk));
+    }
+    const size_t fb = sizeof(float) * (size_t)s->nb * s->N * s->N;
+    float *P = (float *)workspace(ctx, "bana.P", fb);
+    float *I = (float *)workspace(ctx, "bana.I", fb);
+    if (!P || !I) return fail(ctx, ABS_ERR_OOM, "prediction fields");
+    ABS_CHECK(launch_filter_fft_real(ctx, *s, d_C, d_mask, P));
+    ABS_CHECK(launch_filter_fft_real(ctx, *s, nullptr, d_mask, I));
+    return launch_bana_sums(ctx, *s, P, I, n_trip, d_ijk, d_count, f_over_sigma, d_out);
+}
+
 abs_status abs_autotune(abs_ctx *ctx, int32_t enable) {
     if (!ctx) return ABS_ERR_INVALID_ARG;
     ctx->autotune = enable != 0;

@@ -304,6 +304,21 @@ struct GridW64 {
     }
 };
 
+// A real value per cell on the filled cells (the caller's C(l_g), which must
+// equal C(l_-g); with C == nullptr the unit mask): the fields of the
+// discretely sampled prediction.
+struct GridReal {
+    const double *c;
+    const uint8_t *mask;
+    __device__ bool value(int64_t cell, int64_t mcell, float4 &x) const {
+        if (!mask[cell]) return false;
+        float h = 1.f, l = 0.f;
+        if (c) df_of(c[cell], h, l);
+        x = make_float4(h, 0.f, l, 0.f);
+        return true;
+    }
+};
+
 // Column pass: one CTA per (block of CB columns x, ring pair), transforming
 // along y the 2R+1 columns |x| <= R that hold ring cells.  W[pair][x + Rmax][N].
 template <class Src, class A>
@@ -509,6 +524,12 @@ abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc
 abs_status launch_filter_fft_w(abs_ctx *ctx, const Setup &s, const double *acc, float *d_fields) {
     const int64_t cells = (int64_t)s.n * s.n;
     GridW64 src{acc + 2 * cells};
+    return run_fft(ctx, s, src, d_fields);
+}
+
+abs_status launch_filter_fft_real(abs_ctx *ctx, const Setup &s, const double *d_c, const uint8_t *d_mask,
+                                  float *d_fields) {
+    GridReal src{d_c, d_mask};
     return run_fft(ctx, s, src, d_fields);
 }
 

@@ -190,6 +190,71 @@ __global__ void k_normalise_w(int n_trip, double norm_A, const double *__restric
     B[t] = w != 0.0 ? S[t] / (norm_A * w) : nan("");
 }
 
+// The sums of the discretely sampled prediction (Sec. 4): per triplet, over the
+// pixels, P_i P_j I_k + P_j P_k I_i + P_k P_i I_j from fields P (of C(l_g)) and I
+// (of the unit mask): the ordered closed triangles' C1 C2 + C2 C3 + C3 C1, times
+// N^2.  Layout and accumulation as k_triple_fp32, with the P rows and then the
+// I rows staged (G.nb rings each).
+__global__ void k_triple_bana(TripleGeom G, const float *__restrict__ Pf, const float *__restrict__ If,
+                              const int32_t *__restrict__ ijk, double *__restrict__ partial) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    float *F = (float *)smem;                                    // [2 nb][stride]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t p_begin = (int64_t)blockIdx.x * G.per_split;
+    const int64_t p_end = min(G.P, p_begin + G.per_split);
+    const int t_base = blockIdx.y * G.rounds * blockDim.x;
+    const int rounds = G.rounds;
+    float Sh[4] = {0.f, 0.f, 0.f, 0.f}, Sl[4] = {0.f, 0.f, 0.f, 0.f};
+    const int rows = 2 * G.nb;
+    for (int64_t pc = p_begin; pc < p_end; pc += G.PC) {
+        const int np = (int)min((int64_t)G.PC, p_end - pc);
+        const int np4 = (np + 3) >> 2;
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * np4 * 4; e += blockDim.x) {
+            const int m = e / (np4 * 4), v = e - m * (np4 * 4);
+            const float *src = m < G.nb ? Pf + (size_t)m * G.P : If + (size_t)(m - G.nb) * G.P;
+            F[(size_t)m * G.stride + v] = v < np ? src[pc + v] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rd = 0; rd < 4; ++rd) {
+            if (rd >= rounds) break;
+            const int t = t_base + ((rd * nwarps + warp) << 5) + lane;
+            if (t >= G.n_trip) continue;
+            const int i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
+            if (i < 0 || i >= G.nb || j < 0 || j >= G.nb || k < 0 || k >= G.nb) continue;
+            const float4 *Pi = (const float4 *)(F + (size_t)i * G.stride);
+            const float4 *Pj = (const float4 *)(F + (size_t)j * G.stride);
+            const float4 *Pk = (const float4 *)(F + (size_t)k * G.stride);
+            const float4 *Ii = (const float4 *)(F + (size_t)(G.nb + i) * G.stride);
+            const float4 *Ij = (const float4 *)(F + (size_t)(G.nb + j) * G.stride);
+            const float4 *Ik = (const float4 *)(F + (size_t)(G.nb + k) * G.stride);
+            float sh = Sh[rd], sl = Sl[rd];
+            for (int q0 = 0; q0 < np4; q0 += FOLD) {
+                float2 a = make_float2(0.f, 0.f);
+                const int qe = min(np4, q0 + FOLD);
+                for (int q = q0; q < qe; ++q) {
+                    step4(Pi[q], Pj[q], Ik[q], a);
+                    step4(Pj[q], Pk[q], Ii[q], a);
+                    step4(Pk[q], Pi[q], Ij[q], a);
+                }
+                const float v = __fadd_rn(a.x, a.y);
+                const float tt = __fadd_rn(sh, v);             // TwoSum(sh, v)
+                const float bp = __fsub_rn(tt, sh);
+                sl = __fadd_rn(sl, __fadd_rn(__fsub_rn(sh, __fsub_rn(tt, bp)), __fsub_rn(v, bp)));
+                sh = tt;
+            }
+            Sh[rd] = sh;
+            Sl[rd] = sl;
+        }
+    }
+#pragma unroll
+    for (int rd = 0; rd < 4; ++rd) {
+        const int t = t_base + ((rd * nwarps + warp) << 5) + lane;
+        if (rd < rounds && t < G.n_trip) partial[(size_t)blockIdx.x * G.n_trip + t] = (double)Sh[rd] + (double)Sl[rd];
+    }
+}
+
 __global__ void k_check_triplets(int nb, int n_trip, const int32_t *__restrict__ ijk,
                                  int32_t *__restrict__ err) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -243,6 +308,27 @@ abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_field
         n_trip, (int)nsplit, 1.0 / ((double)s.N * (double)s.N), partial, d_sum, d_count, s.norm_A,
         d_B && d_count ? d_B : nullptr);
     return check_launch(ctx, "triple sums");
+}
+
+abs_status launch_bana_sums(abs_ctx *ctx, const Setup &s, const float *d_P, const float *d_I, int32_t n_trip,
+                            const int32_t *d_ijk, const int64_t *d_count, double fs, double *d_out) {
+    if (n_trip == 0) return ABS_OK;
+    TriplePlan tp;   // sized for both field sets in shared memory
+    if (!triple_plan(2 * s.nb, s.N, n_trip, ctx->sm_count, INT64_MAX, d_P, tp))
+        return fail(ctx, ABS_ERR_UNSUPPORTED, "prediction triple-sum tiling");
+    tp.G.nb = s.nb;
+    const int64_t nsplit = tp.nsplit;
+    double *partial = (double *)workspace(ctx, "bana.partial", sizeof(double) * nsplit * n_trip);
+    double *sum = (double *)workspace(ctx, "bana.sum", sizeof(double) * n_trip);
+    if (!partial || !sum) return fail(ctx, ABS_ERR_OOM, "prediction workspace");
+    cudaFuncSetAttribute(k_triple_bana, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem);
+    StageTimer timer(ctx, "bana_sums");
+    k_triple_bana<<<dim3((unsigned)nsplit, tp.tgroups), tp.threads, tp.smem, ctx->stream>>>(tp.G, d_P, d_I, d_ijk,
+                                                                                         partial);
+    // out = sum / (N^2 A T) with A = 1 / (2 fs)
+    k_triple_reduce<<<(int)cdiv(n_trip, 8), 256, 0, ctx->stream>>>(
+        n_trip, (int)nsplit, 1.0 / ((double)s.N * (double)s.N), partial, sum, d_count, 1.0 / (2.0 * fs), d_out);
+    return check_launch(ctx, "prediction sums");
 }
 
 // ------------------------------------------------------------------ allocation-free variant

@@ -539,6 +539,33 @@ def test_rebin_shapes_and_ensemble(ctx):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("cfg_id,prec,tol", [(0, 0, SUM_TOL), (0, 1, 1e-4), (1, 0, SUM_TOL)])
+def test_bana_d_prediction(ctx, cfg_id, prec, tol):
+    """[B_Ana]_d through abs_bana_d (the estimate's transforms on C(l_g) and on the
+    unit mask, a mixed triple sum) against the oracle's brute-force average over
+    the same closed filled triangles, with the generator's C_l on the map modes."""
+    inp = inputs(cfg_id)
+    wl = inp.wl
+    cfg = absmod.Config.from_workload(wl, precision=absmod.ABS_SPLIT_BF16 if prec else absmod.ABS_FP32)
+    est = oracle_run(("est", cfg_id), wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+    _, _, M, gwm = gpu_grid(ctx, cfg, inp.uv, inp.vis)
+    C = synth.power_spectrum_model(wl.n_grid) * 1e3
+    nt = len(est.ijk)
+    T = to_dev(est.T)
+    out = torch.full((nt,), -1.0, dtype=torch.float64, device=dev())
+    ctx.abs_bana_d(cfg, to_dev(C), gwm[2], T, out, None, 0.3)
+    ctx.sync()
+    ref, Tr = oracle.bana_d(C, est.filled, est.q, est.ijk, 0.3)
+    assert np.array_equal(Tr, est.T)
+    g = out.cpu().numpy()
+    ok = Tr > 0
+    assert np.array_equal(np.isnan(g), ~ok)
+    big = ok & (np.abs(ref) >= 1e-3 * np.nanmax(np.abs(ref)))
+    rel = np.abs(g[big] - ref[big]) / np.abs(ref[big])
+    assert rel.max() <= tol, rel.max()
+
+
+@pytest.mark.gpu
 def test_autotuner_split_bf16():
     """The split-BF16 launch shape: measured on a configuration's first eager
     call (autotuner on, the default) or from the cost model (off); either way
