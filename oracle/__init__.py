@@ -23,6 +23,8 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
 * normalise: closed forms above
 * bana_d (discretely sampled prediction): constant C, a pure-Python
   enumeration on a tiny grid, symmetry in the three rings
+* sky_weights / simulate_vis (visibility simulator): single-pixel closed
+  forms, Hermitian symmetry of a real sky, the MWA tile beam's printed FWHM
 * shape_params / rebin (results layer): hand-worked triangle shapes
   (equilateral, squeezed, folded), the bin edges, count-weighted means of a
   constant and of a linear B, and the ensemble mean / spread of +-B
@@ -413,4 +415,41 @@ def bana_d(C: np.ndarray, filled: np.ndarray, q: np.ndarray, ijk: np.ndarray, f_
     with np.errstate(invalid="ignore", divide="ignore"):
         out = np.where(T > 0, 2.0 * f_over_sigma * S / T, np.nan)
     return out, T
+
+
+# ------------------------------------------------------------------ visibility simulator
+
+
+def sky_weights(sky: np.ndarray, dtheta: float, beam: str = "none", beam_param: float = 0.0) -> np.ndarray:
+    """dtheta^2 A(theta) T(theta) on an m x m flat-sky grid (Sec. 3): pixel (row b, column a)
+    at theta = ((a - m/2) dtheta, (b - m/2) dtheta).  beam "mwa": Eq. beam, sinc^2(pi (d/lambda)
+    theta_x) sinc^2(pi (d/lambda) theta_y) with beam_param = d / lambda; "gauss": Eq. A_G,
+    exp(-theta^2 / theta_0^2) with beam_param = theta_0 (radians); "none": A = 1."""
+    m = sky.shape[0]
+    th = (np.arange(m) - m // 2) * float(dtheta)
+    tx, ty = th[None, :], th[:, None]
+    if beam == "mwa":
+        A = np.sinc(beam_param * tx) ** 2 * np.sinc(beam_param * ty) ** 2   # np.sinc(x) = sin(pi x)/(pi x)
+    elif beam == "gauss":
+        A = np.exp(-(tx * tx + ty * ty) / (beam_param * beam_param))
+    else:
+        A = np.ones((m, m))
+    return float(dtheta) ** 2 * A * np.asarray(sky, np.float64)
+
+
+def simulate_vis(sky: np.ndarray, dtheta: float, uv: np.ndarray, beam: str = "none",
+                 beam_param: float = 0.0) -> np.ndarray:
+    """Eq. vis with Q = 1 (map units): V(U) = sum over pixels of dtheta^2 A T exp(+i 2 pi U.theta),
+    the direct DFT of Sec. 3, in FP64.  Returns complex128 [n_vis]."""
+    W = sky_weights(sky, dtheta, beam, beam_param)
+    m = W.shape[0]
+    th = (np.arange(m) - m // 2) * float(dtheta)
+    uv = np.asarray(uv, np.float64)
+    out = np.zeros(len(uv), np.complex128)
+    for s0 in range(0, len(uv), 256):
+        u = uv[s0:s0 + 256, 0][:, None, None]
+        v = uv[s0:s0 + 256, 1][:, None, None]
+        ph = np.exp(2j * np.pi * (u * th[None, None, :] + v * th[None, :, None]))
+        out[s0:s0 + 256] = (ph * W[None]).sum(axis=(1, 2))
+    return out
 

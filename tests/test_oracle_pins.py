@@ -667,3 +667,47 @@ def test_bana_d_constant_spectrum():
     out, T = oracle.bana_d(C, filled, q, ijk, 0.2)
     assert np.all(T[T > 0] > 0) and (T > 0).sum() >= 3
     assert np.allclose(out[T > 0], 6 * 0.2 * 0.49, rtol=1e-14)
+
+
+# ----------------------------------------------------------------- visibility simulator (Eqs. vis, beam)
+
+
+def test_simulator_single_pixel_closed_forms():
+    """One bright pixel: at the phase centre V(U) = dtheta^2 A(0) T for every U; at
+    theta_0 V(U) = dtheta^2 A(theta_0) T exp(+i 2 pi U.theta_0) (the sign of Eq. vis)."""
+    m, dth = 32, 0.01
+    rng = np.random.default_rng(2)
+    uv = rng.uniform(-60, 60, (50, 2))
+    sky = np.zeros((m, m))
+    sky[m // 2, m // 2] = 3.0
+    V = oracle.simulate_vis(sky, dth, uv, "gauss", 0.2)
+    assert np.allclose(V, 3.0 * dth ** 2, rtol=1e-13, atol=0)
+    sky[:] = 0
+    a0, b0 = m // 2 + 5, m // 2 - 3
+    sky[b0, a0] = 2.0
+    th0 = np.array([5 * dth, -3 * dth])
+    A0 = np.sinc(1.7 * th0[0]) ** 2 * np.sinc(1.7 * th0[1]) ** 2
+    V = oracle.simulate_vis(sky, dth, uv, "mwa", 1.7)
+    want = 2.0 * dth ** 2 * A0 * np.exp(2j * np.pi * (uv @ th0))
+    assert np.allclose(V, want, rtol=1e-12, atol=1e-18)
+
+
+def test_simulator_real_sky_is_hermitian():
+    rng = np.random.default_rng(8)
+    sky = rng.normal(size=(24, 24))
+    uv = rng.uniform(-40, 40, (30, 2))
+    V = oracle.simulate_vis(sky, 0.02, uv, "mwa", 2.0)
+    Vm = oracle.simulate_vis(sky, 0.02, -uv, "mwa", 2.0)
+    assert np.allclose(Vm, np.conj(V), rtol=1e-12, atol=1e-15)
+
+
+def test_mwa_tile_beam_fwhm_is_the_printed_one():
+    """Eq. beam for a d = 4 m tile at 154.25 MHz has the FWHM quoted beside it (24.68 deg)."""
+    lam = 299792458.0 / 154.25e6
+    d_over_lam = 4.0 / lam
+    m, dth = 1501, np.deg2rad(0.02)                  # a 30 deg wide grid
+    A = oracle.sky_weights(np.ones((m, m)), dth, "mwa", d_over_lam)[m // 2] / dth ** 2
+    th = (np.arange(m) - m // 2) * dth
+    i = np.nonzero(A >= 0.5)[0].max()                # last sample above half power, then interpolate
+    x_half = th[i] + (A[i] - 0.5) / (A[i] - A[i + 1]) * (th[i + 1] - th[i])
+    assert abs(np.rad2deg(2 * x_half) - 24.68) < 0.05
