@@ -576,6 +576,24 @@ def run_ours(args):
         uneven = len(bi["items"]) * reps_u / (e0.elapsed_time(e1) * 1e-3)
         del bi
 
+    # visibility simulator (Eqs. beam, vis): 10^5 of the workload's baselines, a 256^2 map of the
+    # paper's 0.029 deg pixels times the MWA tile beam, direct DFT
+    msim, nsim = 256, 100_000
+    sky = torch.from_numpy(synth.quadratic_sky(synth.gaussian_field(msim, np.random.default_rng(5)), 0.3)
+                           .astype(np.float32)).to(dev)
+    vsim = torch.empty((nsim, 2), dtype=torch.float32, device=dev)
+    dth = float(np.deg2rad(0.029))
+    ctx.abs_simulate_vis(sky, dth, uv[:nsim], vsim, m.ABS_BEAM_MWA_TILE, 4.0 / (299792458.0 / 154.25e6))
+    e0.record(stream)
+    ctx.abs_simulate_vis(sky, dth, uv[:nsim], vsim, m.ABS_BEAM_MWA_TILE, 4.0 / (299792458.0 / 154.25e6))
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    sim_s = e0.elapsed_time(e1) * 1e-3
+    simulator = {"vis_per_s": nsim / sim_s, "phase_terms_per_s": nsim * msim * msim / sim_s, "ms": sim_s * 1e3,
+                 "n_vis": nsim, "map": msim, "note": "abs_simulate_vis: MWA tile beam, 0.029 deg pixels, "
+                 "direct DFT (one FP64 phase and one FP32 sincos per term)"}
+    del sky, vsim
+
     # (an NVTX range, so that a profiler can select this section's launches)
     torch.cuda.nvtx.range_push("multichannel")
     chan = multichannel(args, m, synth, torch, dev, stream, peaks_sm=(torch.cuda.get_device_properties(dev)
@@ -686,6 +704,7 @@ def run_ours(args):
                        "triple_tc_traffic": tri_tc["traffic"],
                        "triple_useful_tflops": useful / (tc_avg * 1e-6) / 1e12},
         "multichannel": chan,
+        "simulator": simulator,
         "fp32": {"triple_fp32_us": round(stages["triple_fp32"]["avg_us"], 2),
                  "triple_useful_tflops": useful / (stages["triple_fp32"]["avg_us"] * 1e-6) / 1e12,
                  "frac_fp32_simt_peak": tri_fp32["frac"]},

@@ -301,6 +301,20 @@ abs_status abs_bana_d(abs_ctx *ctx, const abs_config *cfg, const double *d_C, co
                       int32_t n_trip, const int32_t *d_ijk, const int64_t *d_count, double f_over_sigma,
                       double *d_out);
 
+/* Visibility simulator (Sec. 3): the sky on an m x m flat grid (pixel (row b,
+ * column a) at theta = ((a - m/2) dtheta, (b - m/2) dtheta), radians) times
+ * the primary beam, then Eq. vis by direct DFT with Q = 1 (map units):
+ *   d_vis[i] = sum over pixels dtheta^2 A(theta) T(theta) exp(+i 2 pi U_i.theta)
+ * beam ABS_BEAM_NONE: A = 1; ABS_BEAM_MWA_TILE: Eq. beam, sinc^2(pi (d/lambda)
+ * theta_x) sinc^2(pi (d/lambda) theta_y) with beam_param = d / lambda (4 m at
+ * 154.25 MHz: 2.058); ABS_BEAM_GAUSS: Eq. A_G, exp(-theta^2 / theta_0^2) with
+ * beam_param = theta_0 in radians.
+ *   d_sky [m][m] FP32, d_uv [n_vis][2] FP32 wavelengths, d_vis [n_vis][2] FP32 out
+ * m in [1, 8192].  Cost: n_vis x m^2 phase terms.  Asynchronous. */
+enum { ABS_BEAM_NONE = 0, ABS_BEAM_MWA_TILE = 1, ABS_BEAM_GAUSS = 2 };
+abs_status abs_simulate_vis(abs_ctx *ctx, int32_t m, double dtheta, const float *d_sky, int32_t beam,
+                            double beam_param, int64_t n_vis, const float *d_uv, float *d_vis);
+
 /* Autotuner of the split-BF16 triple-sum kernel (Sec. 2, Eq. estimator_t on
  * tensor cores).  On the first call of a configuration that runs eagerly (not
  * under stream capture, not while the stage profiler runs) with the canonical

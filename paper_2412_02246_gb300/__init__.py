@@ -27,6 +27,7 @@ ABS_OK, ABS_ERR_INVALID_ARG, ABS_ERR_CUDA, ABS_ERR_OOM, ABS_ERR_TIMEOUT, ABS_ERR
 ABS_KERNEL_NGP, ABS_KERNEL_GAUSS = 0, 1
 ABS_FP32, ABS_SPLIT_BF16 = 0, 1
 ABS_W_MEAN_UNITMASK, ABS_W_PAPER_LITERAL = 0, 1
+ABS_BEAM_NONE, ABS_BEAM_MWA_TILE, ABS_BEAM_GAUSS = 0, 1, 2
 _STATUS = {0: "ABS_OK", 1: "ABS_ERR_INVALID_ARG", 2: "ABS_ERR_CUDA", 3: "ABS_ERR_OOM",
            4: "ABS_ERR_TIMEOUT", 5: "ABS_ERR_UNSUPPORTED", 6: "ABS_ERR_DEVICE"}
 
@@ -91,6 +92,7 @@ def load(path: str | None = None):
         "abs_autotune": ([P, i32], ctypes.c_int),
         "abs_rebin": ([P, P, i32, i32, P, P, P, P, i32, i32, P, P, P], ctypes.c_int),
         "abs_bana_d": ([P, P, P, P, i32, P, P, ctypes.c_double, P], ctypes.c_int),
+        "abs_simulate_vis": ([P, i32, ctypes.c_double, P, i32, ctypes.c_double, i64, P, P], ctypes.c_int),
         "abs_tuned_shape": ([P, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -229,6 +231,13 @@ class Context:
         the filled mask (CUDA uint8 [n][n]) and the triangle counts of that mask."""
         _check(load().abs_bana_d(self.h, cfg.ref(), _ptr(C), _ptr(mask), int(out.shape[0]), _ptr(ijk),
                                  _ptr(counts), float(f_over_sigma), _ptr(out)), self.h, "abs_bana_d")
+
+    def abs_simulate_vis(self, sky, dtheta: float, uv, vis, beam: int = 0, beam_param: float = 0.0):
+        """Eq. vis by direct DFT of the beam-weighted map (CUDA FP32 [m][m]) at the baselines uv
+        (CUDA FP32 [n][2]) into vis (CUDA FP32 [n][2]); beam ABS_BEAM_NONE / MWA_TILE / GAUSS."""
+        _check(load().abs_simulate_vis(self.h, int(sky.shape[0]), float(dtheta), _ptr(sky), int(beam),
+                                       float(beam_param), int(uv.shape[0]), _ptr(uv), _ptr(vis)),
+               self.h, "abs_simulate_vis")
 
     def autotune(self, on: bool = True):
         """Turn the split-BF16 launch-shape autotuner on (default) or off (cost model)."""

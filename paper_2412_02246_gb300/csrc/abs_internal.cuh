@@ -190,6 +190,9 @@ abs_status launch_filter_fft_real(abs_ctx *ctx, const Setup &s, const double *d_
 // sampled prediction from C fields P and unit-mask fields I (NaN where T = 0).
 abs_status launch_bana_sums(abs_ctx *ctx, const Setup &s, const float *d_P, const float *d_I, int32_t n_trip,
                             const int32_t *d_ijk, const int64_t *d_count, double fs, double *d_out);
+// Beam-weighted flat sky and its direct DFT at every baseline (visibility simulator).
+abs_status launch_simulate_vis(abs_ctx *ctx, int32_t m, double dtheta, const float *d_sky, int32_t beam,
+                               double beam_param, int64_t n_vis, const float *d_uv, float *d_vis);
 // Count-weighted (l1, mu, t) cells of B and their ensemble mean and spread (results layer).
 abs_status launch_rebin(abs_ctx *ctx, const Setup &s, int32_t n_real, int32_t n_trip, const double *d_B,
                         const int64_t *d_count, const double *d_ellbar, const int32_t *d_ijk, int32_t n_mu,

@@ -540,6 +540,21 @@ abs_status abs_bana_d(abs_ctx *ctx, const abs_config *cfg, const double *d_C, co
     return launch_bana_sums(ctx, *s, P, I, n_trip, d_ijk, d_count, f_over_sigma, d_out);
 }
 
+abs_status abs_simulate_vis(abs_ctx *ctx, int32_t m, double dtheta, const float *d_sky, int32_t beam,
+                            double beam_param, int64_t n_vis, const float *d_uv, float *d_vis) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (m < 1 || m > 8192) return fail(ctx, ABS_ERR_INVALID_ARG, "m must be in [1, 8192]");
+    if (!(dtheta > 0.0) || !std::isfinite(dtheta)) return fail(ctx, ABS_ERR_INVALID_ARG, "dtheta must be finite and > 0");
+    if (beam != ABS_BEAM_NONE && beam != ABS_BEAM_MWA_TILE && beam != ABS_BEAM_GAUSS)
+        return fail(ctx, ABS_ERR_INVALID_ARG, "unknown beam");
+    if (beam != ABS_BEAM_NONE && (!(beam_param > 0.0) || !std::isfinite(beam_param)))
+        return fail(ctx, ABS_ERR_INVALID_ARG, "beam_param must be finite and > 0");
+    if (n_vis < 0) return fail(ctx, ABS_ERR_INVALID_ARG, "n_vis < 0");
+    if (!d_sky || (n_vis > 0 && (!d_uv || !d_vis))) return fail(ctx, ABS_ERR_INVALID_ARG, "NULL buffer");
+    return launch_simulate_vis(ctx, m, dtheta, d_sky, beam, beam_param, n_vis, d_uv, d_vis);
+}
+
 abs_status abs_autotune(abs_ctx *ctx, int32_t enable) {
     if (!ctx) return ABS_ERR_INVALID_ARG;
     ctx->autotune = enable != 0;
