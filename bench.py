@@ -591,7 +591,7 @@ def run_ours(args):
     sim_s = e0.elapsed_time(e1) * 1e-3
     simulator = {"vis_per_s": nsim / sim_s, "phase_terms_per_s": nsim * msim * msim / sim_s, "ms": sim_s * 1e3,
                  "n_vis": nsim, "map": msim, "note": "abs_simulate_vis: MWA tile beam, 0.029 deg pixels, "
-                 "direct DFT (one FP64 phase and one FP32 sincos per term)"}
+                 "direct DFT (double-float phase and SFU sincos every 16 pixels, complex rotation between)"}
     del sky, vsim
 
     # (an NVTX range, so that a profiler can select this section's launches)
