@@ -76,23 +76,23 @@ MEASURED_TRAFFIC = {
            "sha256": "539943939760fab02949cc5c5ee66ecabbae23e6e1a9d1dfd0412cdfe602a6bd",
            "profile": "profiles/k_grid_mwa975k.md"},
     "fft_rows": {"bytes": 2880000, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-               "sha256": "cc3fbf6bcf0a678a177264e40093b43ce3e181a376e68f303cdbb387e23d4b99",
+               "sha256": "1984ade213fcfb20e731a44d3d468b56a35a27e7ce649bf884a7b84438f65268",
                "profile": "profiles/k_fft_rows_mwa975k.md"},
     "fft_cols": {"bytes": 722688, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-               "sha256": "cc3fbf6bcf0a678a177264e40093b43ce3e181a376e68f303cdbb387e23d4b99",
+               "sha256": "1984ade213fcfb20e731a44d3d468b56a35a27e7ce649bf884a7b84438f65268",
                "profile": "profiles/k_fft_cols_mwa975k.md"},
     "triple_fp32": {"bytes": 6663424, "source": "paper_2412_02246_gb300/csrc/triple.cu",
-                  "sha256": "9d2104ec79e0019fa0c5dd2937d8d28d0fd2758fd8ab1aaeabc0e456d091bd3b",
+                  "sha256": "8262a89b40cb36126d6ab915a19627160a3de8e026406e5bf76d26fd642ff862",
                   "profile": "profiles/k_triple_fp32_mwa975k.md"},
-    "triple_tc": {"bytes": 6707456, "source": "paper_2412_02246_gb300/csrc/triple_tc.cu",
-                "sha256": "49b35175521025485f6aae81e582375d06b827ff22b14b37bff46d5bf574b1af",
+    "triple_tc": {"bytes": 6703872, "source": "paper_2412_02246_gb300/csrc/triple_tc.cu",
+                "sha256": "2366406142f503e351c2cf81f0169e8a6f3923eb458df2fbe972621d9f20abd3",
                 "profile": "profiles/k_triple_tc_mwa975k.md"},
     # one channel of the multi-channel workload (channel 0)
     "channel_fft_rows": {"bytes": 660686848, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-                         "sha256": "cc3fbf6bcf0a678a177264e40093b43ce3e181a376e68f303cdbb387e23d4b99",
+                         "sha256": "1984ade213fcfb20e731a44d3d468b56a35a27e7ce649bf884a7b84438f65268",
                          "profile": "profiles/k_fft_rows_channels4096.md"},
     "channel_triple_tc": {"bytes": 828804096, "source": "paper_2412_02246_gb300/csrc/triple_tc.cu",
-                          "sha256": "49b35175521025485f6aae81e582375d06b827ff22b14b37bff46d5bf574b1af",
+                          "sha256": "2366406142f503e351c2cf81f0169e8a6f3923eb458df2fbe972621d9f20abd3",
                           "profile": "profiles/k_triple_tc_channels4096.md"},
 }
 
