@@ -105,6 +105,7 @@ struct abs_ctx {
     bool autotune = true;
     struct TcShape { int kc = 0; bool grouped = false; bool measured = false; };
     std::map<std::string, TcShape> tc_shapes;
+    std::map<std::string, std::pair<int, int>> fft_shapes;   // lines per CTA: column pass, row pass
     std::vector<abs_ctx *> lanes;
     bool owns_stream = false;
     cudaEvent_t ev_lane = nullptr;   // a lane's end, joined by the parent

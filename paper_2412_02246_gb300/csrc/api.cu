@@ -912,8 +912,10 @@ abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *i
     if (ctx->autotune)
         for (int32_t i = 0; i < n_items && !untuned; ++i) {
             const abs_config *c = items[i].cfg;
-            if (c && c->ell_edges && c->n_bins >= 1 && c->n_bins <= ABS_MAX_BINS && c->precision == ABS_SPLIT_BF16 &&
-                !items[i].d_ijk && items[i].n_trip > 0 && !ctx->tc_shapes.count(setup_key(c)))
+            if (!c || !c->ell_edges || c->n_bins < 1 || c->n_bins > ABS_MAX_BINS) continue;
+            const std::string k = setup_key(c);
+            if (!ctx->fft_shapes.count(k + "|fft|f64") ||
+                (c->precision == ABS_SPLIT_BF16 && !items[i].d_ijk && items[i].n_trip > 0 && !ctx->tc_shapes.count(k)))
                 untuned = true;
         }
     const int K = (ctx->profiling || !ctx->stream || n_items < 2 || untuned)

@@ -256,6 +256,7 @@ __device__ __forceinline__ void df_of(double v, float &hi, float &lo) {
 // Gridded data as the transform reads it: the weighted mean X on a filled
 // cell, as a packed double-float complex (re.hi, im.hi, re.lo, im.lo).
 struct GridF32 {   // abs_grid outputs (FP32)
+    static constexpr const char *tag = "f32";
     const float2 *grid;
     const float *wsum;
     const uint8_t *mask;
@@ -271,6 +272,7 @@ struct GridF32 {   // abs_grid outputs (FP32)
     }
 };
 struct GridF64 {   // FP64 accumulators before the mirror (inside abs_estimate)
+    static constexpr const char *tag = "f64";
     const double *re, *im, *w;
     __device__ bool value(int64_t cell, int64_t mcell, float4 &x) const {
         // the mirrored sums in FP64, then the division in double-float (GB300's
@@ -292,6 +294,7 @@ struct GridF64 {   // FP64 accumulators before the mirror (inside abs_estimate)
 // cell, N_g its mirrored weight sum in FP64 (real: N_g = N_-g), the quotient
 // in double-float.
 struct GridW64 {
+    static constexpr const char *tag = "w64";
     const double *w;
     __device__ bool value(int64_t cell, int64_t mcell, float4 &x) const {
         const double ww = w[cell] + w[mcell];
@@ -308,6 +311,7 @@ struct GridW64 {
 // equal C(l_-g); with C == nullptr the unit mask): the fields of the
 // discretely sampled prediction.
 struct GridReal {
+    static constexpr const char *tag = "real";
     const double *c;
     const uint8_t *mask;
     __device__ bool value(int64_t cell, int64_t mcell, float4 &x) const {
@@ -477,25 +481,82 @@ abs_status run_fft_as(abs_ctx *ctx, const Setup &s, const Src &src, float *d_fie
     using E = typename A::E;
     RingGeom G{s.n, s.half, s.nb, s.N, s.R};
     const FftPlan P = make_plan(s);
-    const FftLaunch L = fft_launch(s, ctx->sm_count);
+    FftLaunch L = fft_launch(s, ctx->sm_count);
     const int npairs = (s.nb + 1) / 2;
     const size_t wbytes = sizeof(E) * (size_t)npairs * (2 * s.R + 1) * s.N;
     E *W = (E *)workspace(ctx, "fft.rows", wbytes);
     if (!W) return fail(ctx, ABS_ERR_OOM, "FFT row workspace");
-    if (L.row_smem > 227 * 1024 || L.col_smem > 227 * 1024)
-        return fail(ctx, ABS_ERR_UNSUPPORTED, "FFT lines do not fit shared memory");
+    const size_t line = sizeof(E) * (size_t)s.N;
     cudaStream_t st = ctx->stream;
-    cudaFuncSetAttribute(k_fft_cols<Src, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.col_smem);
-    cudaFuncSetAttribute(k_fft_rows<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.row_smem);
+    const float4 *tw = A::table(s.d_tw, s.N);
+    auto cols = [&](int cb) {
+        const size_t sm = line * 2 * cb;
+        cudaFuncSetAttribute(k_fft_cols<Src, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_fft_cols<Src, A><<<dim3((unsigned)cdiv(2 * s.R + 1, cb), npairs), FFT_NT, sm, st>>>(G, P, cb, s.d_q,
+                                                                                             s.d_Rm, src, tw, W);
+    };
+    auto rows = [&](int rb) {
+        const size_t sm = line * 2 * rb;
+        cudaFuncSetAttribute(k_fft_rows<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_fft_rows<A><<<dim3((unsigned)cdiv(s.N, rb), npairs), FFT_NT, sm, st>>>(G, P, rb, s.d_Rm, W, tw, d_fields);
+    };
+    // Autotuner: lines per CTA of each pass, measured on the configuration's first eager
+    // call (the model's count and 1, 2, 4, 8 lines, each timed twice) and kept by the
+    // root context per configuration and source; else the model above.
+    abs_ctx *root = ctx->parent ? ctx->parent : ctx;
+    const std::string key = s.key + "|fft|" + Src::tag;
+    auto hit = root->fft_shapes.find(key);
+    if (hit != root->fft_shapes.end()) {
+        L.CB = hit->second.first;
+        L.RB = hit->second.second;
+    } else {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (st) cudaStreamIsCapturing(st, &cs);
+        if (root->autotune && !ctx->profiling && st && cs == cudaStreamCaptureStatusNone && !s.key.empty()) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
+                auto best_of = [&](int model, const auto &run) {
+                    int best = model;
+                    float tbest = 1e30f;
+                    for (int w : {model, 1, 2, 4, 8}) {
+                        if (line * 2 * w > 200 * 1024 || (w != model && w == best && tbest < 1e30f)) continue;
+                        float tmin = 1e30f;
+                        for (int rep = 0; rep < 2; ++rep) {
+                            cudaEventRecord(e0, st);
+                            run(w);
+                            cudaEventRecord(e1, st);
+                            float t = 1e30f;
+                            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+                                cudaGetLastError();
+                                t = 1e30f;
+                            }
+                            tmin = std::min(tmin, t);
+                        }
+                        if (tmin < tbest) {
+                            tbest = tmin;
+                            best = w;
+                        }
+                    }
+                    return best;
+                };
+                L.CB = best_of(L.CB, cols);     // leaves W transformed (any count gives the same W)
+                L.RB = best_of(L.RB, rows);
+                root->fft_shapes[key] = {L.CB, L.RB};
+            }
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            cudaGetLastError();
+        }
+    }
+    if (line * 2 * L.RB > 227 * 1024 || line * 2 * L.CB > 227 * 1024)
+        return fail(ctx, ABS_ERR_UNSUPPORTED, "FFT lines do not fit shared memory");
     {
         StageTimer timer(ctx, "fft_cols");
-        k_fft_cols<Src, A><<<dim3((unsigned)cdiv(2 * s.R + 1, L.CB), npairs), FFT_NT, L.col_smem, st>>>(
-            G, P, L.CB, s.d_q, s.d_Rm, src, A::table(s.d_tw, s.N), W);
+        cols(L.CB);
     }
     {
         StageTimer timer(ctx, "fft_rows");
-        k_fft_rows<A><<<dim3((unsigned)cdiv(s.N, L.RB), npairs), FFT_NT, L.row_smem, st>>>(
-            G, P, L.RB, s.d_Rm, W, A::table(s.d_tw, s.N), d_fields);
+        rows(L.RB);
     }
     return check_launch(ctx, "filter+FFT");
 }
