@@ -76,10 +76,10 @@ MEASURED_TRAFFIC = {
            "sha256": "539943939760fab02949cc5c5ee66ecabbae23e6e1a9d1dfd0412cdfe602a6bd",
            "profile": "profiles/k_grid_mwa975k.md"},
     "fft_rows": {"bytes": 2880000, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-               "sha256": "1984ade213fcfb20e731a44d3d468b56a35a27e7ce649bf884a7b84438f65268",
+               "sha256": "eb38a2816f985ec629765661f3343c9580143cf0c7c03b76c4de5f6d4d3858b1",
                "profile": "profiles/k_fft_rows_mwa975k.md"},
     "fft_cols": {"bytes": 722688, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-               "sha256": "1984ade213fcfb20e731a44d3d468b56a35a27e7ce649bf884a7b84438f65268",
+               "sha256": "eb38a2816f985ec629765661f3343c9580143cf0c7c03b76c4de5f6d4d3858b1",
                "profile": "profiles/k_fft_cols_mwa975k.md"},
     "triple_fp32": {"bytes": 6663424, "source": "paper_2412_02246_gb300/csrc/triple.cu",
                   "sha256": "8262a89b40cb36126d6ab915a19627160a3de8e026406e5bf76d26fd642ff862",
@@ -89,7 +89,7 @@ MEASURED_TRAFFIC = {
                 "profile": "profiles/k_triple_tc_mwa975k.md"},
     # one channel of the multi-channel workload (channel 0)
     "channel_fft_rows": {"bytes": 660686848, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-                         "sha256": "1984ade213fcfb20e731a44d3d468b56a35a27e7ce649bf884a7b84438f65268",
+                         "sha256": "eb38a2816f985ec629765661f3343c9580143cf0c7c03b76c4de5f6d4d3858b1",
                          "profile": "profiles/k_fft_rows_channels4096.md"},
     "channel_triple_tc": {"bytes": 828804096, "source": "paper_2412_02246_gb300/csrc/triple_tc.cu",
                           "sha256": "2366406142f503e351c2cf81f0169e8a6f3923eb458df2fbe972621d9f20abd3",
