@@ -28,10 +28,12 @@
 // Ring lists are built row-major, so the upper half plane of each ring is
 // the second half of its list.  A byte map holds 1 + ring id of every cell of
 // a family (0 elsewhere), indexed by |lin(h)| with lin(g) = g_y W + g_x,
-// W = 4R + 1: lin is linear and odd, so lin(g1 + g2) = lin(g1) + lin(g2) and
+// W = 2R + 1: lin is linear and odd, so lin(g1 + g2) = lin(g1) + lin(g2) and
 // |lin(h)| = lin(+-h) picks the upper-half-plane representative of h, whose
-// ring and membership are those of h.  A pair is then classified by one add,
-// one abs and one byte load, with no bounds test.  One CTA per work item
+// ring and membership are those of h.  A pair sum with |h_x| > R is in no ring;
+// for |h_x| <= R and |h_y| <= 2R, lin is one-to-one, so a pair is classified
+// by one add and compare on x, one add, one abs and one byte load (a map of
+// about 4R^2 bytes, in shared memory up to R of about 230).  One CTA per work item
 // (pair of rings, chunk of the larger set spread over the threads, chunk of
 // the smaller set streamed through shared memory); each thread keeps
 // run-length state (consecutive cells in row order usually land in the same
@@ -50,8 +52,8 @@ constexpr int INNER = 512;       // inner cells per work item (bounds the work o
 constexpr unsigned FULL = 0xffffffffu;
 
 struct CountGeom {
-    int n, half, nb, R, W;       // W = 4R + 1
-    int64_t base;                // 2R W + 2R
+    int n, half, nb, R, W;       // W = 2R + 1
+    int64_t base;                // 2R W + R: the largest |lin| of a pair sum with |h_x| <= R
 };
 
 __device__ __forceinline__ int64_t cell_index(int n, int gx, int gy) {
@@ -423,8 +425,9 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
     uint16_t *hist = (uint16_t *)smem;             // [nwarps][hs][32]
     uint32_t *hist32 = (uint32_t *)smem;           // the same, as pairs of counters (clearing)
     const int hwords = nwarps * hs * 16;
-    int32_t *stage = (int32_t *)(hist + (size_t)nwarps * hs * 32);   // [INNER]
-    uint8_t *map_s = (uint8_t *)(stage + INNER);
+    int32_t *stage = (int32_t *)(hist + (size_t)nwarps * hs * 32);   // [INNER] lin of the inner cells
+    int32_t *stage_x = stage + INNER;                                 // [INNER] their x
+    uint8_t *map_s = (uint8_t *)(stage_x + INNER);
     const uint8_t *map = MAP_IN_SMEM ? map_s : map_g;
     const int ni = *n_items;
     if (MAP_IN_SMEM && ni > 0) {
@@ -433,8 +436,10 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
         for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) ((uint4 *)map_s)[i] = ((const uint4 *)map_g)[i];
         for (int64_t i = nv * 16 + threadIdx.x; i < mb; i += blockDim.x) map_s[i] = map_g[i];
     }
-    for (int i = threadIdx.x; i < hwords; i += blockDim.x) hist32[i] = 0u;
-    __syncthreads();
+    if (ni > 0) {   // nothing to clear when there are no items (a grid without holes)
+        for (int i = threadIdx.x; i < hwords; i += blockDim.x) hist32[i] = 0u;
+        __syncthreads();
+    }
     uint16_t *myhist = hist + (size_t)warp * hs * 32 + lane;
     __shared__ int it_s;
     for (; ni > 0;) {
@@ -455,20 +460,26 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
         const int nx = cxa / 2, hy = cyb / 2;
         const int no = outer_x ? nx : cyb;
         const int nin = min(INNER, (outer_x ? cyb : nx) - in0);
-        int lin1[G1];
+        int lin1[G1], xr1[G1];   // lin and x + R of this thread's outer cells
         bool v1[G1];
 #pragma unroll
         for (int q = 0; q < G1; ++q) {
             const int k = I.z + q * blockDim.x + threadIdx.x;
             v1[q] = k < no;
-            int l = 0;
+            int l = 0, x = 0;
             if (v1[q]) {
                 const short2 g = outer_x ? X[k] : Yu[k < hy ? k : k - hy];
                 l = g.y * G.W + g.x;
-                if (!outer_x && k >= hy) l = -l;
+                x = g.x;
+                if (!outer_x && k >= hy) {
+                    l = -l;
+                    x = -x;
+                }
             }
             lin1[q] = l;
+            xr1[q] = x + G.R;
         }
+        const uint32_t span = 2u * (uint32_t)G.R;   // |x1 + x2| <= R  <=>  x1 + R + x2 in [0, 2R]
         int cur[G1];
         uint32_t cnt[G1];
 #pragma unroll
@@ -479,16 +490,22 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
         __syncthreads();
         for (int k = threadIdx.x; k < nin; k += blockDim.x) {
             const int kk = in0 + k;
-            int l;
+            int l, x;
             if (outer_x) {
                 const short2 g = Yu[kk < hy ? kk : kk - hy];
                 l = g.y * G.W + g.x;
-                if (kk >= hy) l = -l;
+                x = g.x;
+                if (kk >= hy) {
+                    l = -l;
+                    x = -x;
+                }
             } else {
                 const short2 g = X[kk];
                 l = g.y * G.W + g.x;
+                x = g.x;
             }
             stage[k] = l;
+            stage_x[k] = x;
         }
         __syncthreads();
         // the map loads of KU inner cells are issued before their run-length updates,
@@ -498,9 +515,10 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
             int rr[KU][G1];
 #pragma unroll
             for (int u = 0; u < KU; ++u) {
-                const int l2 = stage[k + u];
+                const int l2 = stage[k + u], x2 = stage_x[k + u];
 #pragma unroll
-                for (int q = 0; q < G1; ++q) rr[u][q] = v1[q] ? (int)map[abs(lin1[q] + l2)] : 0;
+                for (int q = 0; q < G1; ++q)
+                    rr[u][q] = (v1[q] && (uint32_t)(xr1[q] + x2) <= span) ? (int)map[abs(lin1[q] + l2)] : 0;
             }
 #pragma unroll
             for (int u = 0; u < KU; ++u) {
@@ -516,10 +534,10 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
             }
         }
         for (; k < nin; ++k) {
-            const int l2 = stage[k];
+            const int l2 = stage[k], x2 = stage_x[k];
 #pragma unroll
             for (int q = 0; q < G1; ++q) {
-                const int r = v1[q] ? (int)map[abs(lin1[q] + l2)] : 0;
+                const int r = (v1[q] && (uint32_t)(xr1[q] + x2) <= span) ? (int)map[abs(lin1[q] + l2)] : 0;
                 if (r != cur[q]) {
                     myhist[(size_t)cur[q] * 32] += (uint16_t)cnt[q];
                     cur[q] = r;
@@ -579,8 +597,8 @@ CountGeom cgeom(const Setup &s) {
     G.half = s.half;
     G.nb = s.nb;
     G.R = s.R;
-    G.W = 4 * s.R + 1;
-    G.base = (int64_t)2 * s.R * G.W + 2 * s.R;   // largest |lin| of a pair sum
+    G.W = 2 * s.R + 1;
+    G.base = (int64_t)2 * s.R * G.W + s.R;   // largest |lin| of a pair sum with |h_x| <= R
     return G;
 }
 
@@ -649,8 +667,8 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     const int threads = nwarps * 32;
     const int chunk = threads * G1;
     const int64_t hist_bytes = (int64_t)nwarps * hs * 32 * 2;
-    const bool map_smem = map_bytes + hist_bytes + INNER * 4 <= 220 * 1024;
-    const size_t smem = (size_t)hist_bytes + INNER * 4 + (map_smem ? map_bytes : 0);
+    const bool map_smem = map_bytes + hist_bytes + INNER * 8 <= 220 * 1024;
+    const size_t smem = (size_t)hist_bytes + INNER * 8 + (map_smem ? map_bytes : 0);
     // resident CTAs an SM (shared memory, threads and registers), for the persistent grid
     int per_sm = 1;
     if (map_smem) {
