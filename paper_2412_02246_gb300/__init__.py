@@ -8,7 +8,11 @@ every call raises.
 
 Names follow the C ABI: ``abs_grid``, ``abs_filter_fft``, ``abs_triple``,
 ``abs_normalise``, ``abs_estimate``, ``abs_estimate_many``,
-``abs_estimate_batched``, ``abs_estimate_host``, plus the host helpers ``abs_ring_q``,
+``abs_estimate_batched``, ``abs_estimate_host``; around the path ``abs_rebin``
+((l1, mu, t) cells and ensemble statistics), ``abs_bana_d`` (the discretely
+sampled prediction), ``abs_simulate_vis`` (the visibility simulator),
+``autotune`` / ``tuned_shape`` (launch-shape autotuner) and ``profile`` /
+``profile_read`` (stage tracing); plus the host helpers ``abs_ring_q``,
 ``abs_fft_size``, ``abs_triplets``.
 """
 from __future__ import annotations
