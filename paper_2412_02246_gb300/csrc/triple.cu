@@ -10,8 +10,9 @@
 // float2 partial sum, folded every FOLD steps into a double-float (FP32
 // pair, TwoSum) accumulator.  No
 // cross-lane reduction is needed.  Per-CTA partial sums go to
-// [split][triplet] and a second kernel adds the splits in a fixed order (so
-// the result does not depend on scheduling) and applies N^-2 in FP64.
+// [split][triplet] as double-float pairs and a second kernel adds the splits
+// in double-float in a fixed order (so the result does not depend on
+// scheduling), then applies N^-2 in FP64.
 //
 // B_ijk = S_ijk / (A T_ijk) is then formed in FP64 (NaN for T = 0).
 #include <mutex>
@@ -106,7 +107,8 @@ __global__ void k_triple_fp32(TripleGeom G, const float *__restrict__ fields, co
 #pragma unroll
     for (int rd = 0; rd < 4; ++rd) {
         const int t = t_base + ((rd * nwarps + warp) << 5) + lane;
-        if (rd < rounds && t < G.n_trip) partial[(size_t)blockIdx.x * G.n_trip + t] = (double)Sh[rd] + (double)Sl[rd];
+        if (rd < rounds && t < G.n_trip)
+            ((float2 *)partial)[(size_t)blockIdx.x * G.n_trip + t] = make_float2(Sh[rd], Sl[rd]);
     }
 }
 
@@ -149,10 +151,22 @@ bool triple_plan(int nb, int N, int n_trip, int sms, int64_t max_split, const fl
     return true;
 }
 
-// S[t] = inv_p * sum over splits of partial[split][t]: one warp per triplet,
-// lane l adds splits l, l + 32, ... and a fixed butterfly combines the lanes
-// (the order never depends on scheduling, so results are reproducible).
-// With B != nullptr also B[t] = S[t] / (A T[t]) (NaN for T = 0).
+// x + y for double-float pairs (TwoSum of the high parts, low parts added).
+__device__ __forceinline__ float2 df2_add(float2 x, float2 y) {
+    const float s = __fadd_rn(x.x, y.x);
+    const float bp = __fsub_rn(s, x.x);
+    const float e = __fadd_rn(__fsub_rn(x.x, __fsub_rn(s, bp)), __fsub_rn(y.x, bp));
+    const float t = __fadd_rn(e, __fadd_rn(x.y, y.y));
+    const float h = __fadd_rn(s, t);
+    return make_float2(h, __fsub_rn(t, __fsub_rn(h, s)));
+}
+
+// S[t] = inv_p * sum over splits of partial[split][t] (double-float pairs, stored
+// as float2 in the 8 bytes of each entry): one warp per triplet, lane l adds
+// splits l, l + 32, ... in double-float (GB300's FP64 pipe is narrow) and a
+// fixed butterfly combines the lanes (the order never depends on scheduling, so
+// results are reproducible); the total is widened to FP64 once.  With B != nullptr
+// also B[t] = S[t] / (A T[t]) (NaN for T = 0).
 __global__ void __launch_bounds__(256) k_triple_reduce(int n_trip, int nsplit, double inv_p,
                                                        const double *__restrict__ partial,
                                                        double *__restrict__ S, const int64_t *__restrict__ T,
@@ -160,12 +174,14 @@ __global__ void __launch_bounds__(256) k_triple_reduce(int n_trip, int nsplit, d
     const int lane = threadIdx.x & 31;
     const int t = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (t >= n_trip) return;
-    double s = 0.0;
-    for (int k = lane; k < nsplit; k += 32) s += partial[(size_t)k * n_trip + t];
+    const float2 *pf = (const float2 *)partial;
+    float2 s = make_float2(0.f, 0.f);
+    for (int k = lane; k < nsplit; k += 32) s = df2_add(s, pf[(size_t)k * n_trip + t]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    for (int o = 16; o > 0; o >>= 1)
+        s = df2_add(s, make_float2(__shfl_xor_sync(FULL, s.x, o), __shfl_xor_sync(FULL, s.y, o)));
     if (lane == 0) {
-        const double v = s * inv_p;
+        const double v = ((double)s.x + (double)s.y) * inv_p;
         S[t] = v;
         if (B) {
             const int64_t c = T[t];
@@ -251,7 +267,8 @@ __global__ void k_triple_bana(TripleGeom G, const float *__restrict__ Pf, const 
 #pragma unroll
     for (int rd = 0; rd < 4; ++rd) {
         const int t = t_base + ((rd * nwarps + warp) << 5) + lane;
-        if (rd < rounds && t < G.n_trip) partial[(size_t)blockIdx.x * G.n_trip + t] = (double)Sh[rd] + (double)Sl[rd];
+        if (rd < rounds && t < G.n_trip)
+            ((float2 *)partial)[(size_t)blockIdx.x * G.n_trip + t] = make_float2(Sh[rd], Sl[rd]);
     }
 }
 
