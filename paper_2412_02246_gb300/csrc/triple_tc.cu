@@ -550,7 +550,11 @@ __global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_cons
                     const int kk = ijk[3 * q + 2] - klo;
                     if (kk >= 0 && kk < NB) {
                         const float *d = D + threadIdx.x * dw + kk;
-                        partial[(size_t)blockIdx.y * G.n_trip + q] = (double)(d[0] + d[NB]) + (double)d[2 * NB];
+                        // (hh + hl) + lh as an exact double-float pair (TwoSum), stored in the entry's 8 bytes
+                        const float x = d[0] + d[NB], y = d[2 * NB];
+                        const float sm = __fadd_rn(x, y), bp = __fsub_rn(sm, x);
+                        const float er = __fadd_rn(__fsub_rn(x, __fsub_rn(sm, bp)), __fsub_rn(y, bp));
+                        ((float2 *)partial)[(size_t)blockIdx.y * G.n_trip + q] = make_float2(sm, er);
                     }
                 }
             }
@@ -678,23 +682,36 @@ __global__ void __launch_bounds__(1024) k_rows(int n_trip, int nb, int np, int g
     }
 }
 
-// S[t] = inv_p * sum over splits of partial[split][t]: 32 triplets per block,
-// 8 lanes of splits per triplet, summed in a fixed order (deterministic).
+// x + y for double-float pairs (TwoSum of the high parts, low parts added).
+__device__ __forceinline__ float2 df2_add(float2 x, float2 y) {
+    const float s = __fadd_rn(x.x, y.x);
+    const float bp = __fsub_rn(s, x.x);
+    const float e = __fadd_rn(__fsub_rn(x.x, __fsub_rn(s, bp)), __fsub_rn(y.x, bp));
+    const float t = __fadd_rn(e, __fadd_rn(x.y, y.y));
+    const float h = __fadd_rn(s, t);
+    return make_float2(h, __fsub_rn(t, __fsub_rn(h, s)));
+}
+
+// S[t] = inv_p * sum over splits of partial[split][t] (double-float pairs stored as
+// float2): 32 triplets per block, 8 lanes of splits per triplet, summed in
+// double-float in a fixed order (deterministic; GB300's FP64 pipe is narrow), the
+// total widened to FP64 once.
 __global__ void __launch_bounds__(256) k_tc_reduce(int n_trip, int nsplit, double inv_p,
                                                        const double *__restrict__ partial,
                                                        double *__restrict__ S) {
-    __shared__ double sh[8][33];
+    __shared__ float2 sh[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int t = blockIdx.x * 32 + tx;
-    double s = 0.0;
+    const float2 *pf = (const float2 *)partial;
+    float2 s = make_float2(0.f, 0.f);
     if (t < n_trip)
-        for (int k = ty; k < nsplit; k += 8) s += partial[(size_t)k * n_trip + t];
+        for (int k = ty; k < nsplit; k += 8) s = df2_add(s, pf[(size_t)k * n_trip + t]);
     sh[ty][tx] = s;
     __syncthreads();
     if (ty == 0 && t < n_trip) {
-        double a = 0.0;
-        for (int k = 0; k < 8; ++k) a += sh[k][tx];
-        S[t] = a * inv_p;
+        float2 a = make_float2(0.f, 0.f);
+        for (int k = 0; k < 8; ++k) a = df2_add(a, sh[k][tx]);
+        S[t] = ((double)a.x + (double)a.y) * inv_p;
     }
 }
 
