@@ -73,7 +73,7 @@ def load_peaks():
 # source has changed since then reports null.
 MEASURED_TRAFFIC = {
     "grid": {"bytes": 20339968, "source": "paper_2412_02246_gb300/csrc/grid.cu",
-           "sha256": "539943939760fab02949cc5c5ee66ecabbae23e6e1a9d1dfd0412cdfe602a6bd",
+           "sha256": "70be2b06c383f602aaf00e7804b1cc35bdaa232fc73ae16926d4d3499348f46e",
            "profile": "profiles/k_grid_mwa975k.md"},
     "fft_rows": {"bytes": 2880000, "source": "paper_2412_02246_gb300/csrc/fft.cu",
                "sha256": "eb38a2816f985ec629765661f3343c9580143cf0c7c03b76c4de5f6d4d3858b1",

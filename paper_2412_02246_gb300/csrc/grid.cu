@@ -5,18 +5,17 @@
 // V*.  The mirror is applied after accumulation (G(g) + conj G(-g)), which is
 // the same sum.
 //
-// Plan (per baseline set): key every visibility by its 16x16-cell uv tile,
-// stable-sort by tile (one radix pass while there are fewer than 2048 tiles,
-// about 700 cells a side; two beyond), write the sorted positions and original
-// indices, and cut every tile's run into work units of at most UMAX
-// visibilities.
+// Plan (per baseline set): key every visibility by its 16x16-cell uv tile and
+// its cell in the tile, stable-sort by that key (LSD radix, two passes up to
+// about 2040^2 cells, three beyond), and write the sorted positions and
+// original indices; the sorted order is cut into work units of UMAX records.
 //
 // Accumulation (per realisation): one CTA per unit stages the unit in shared
-// memory, sorts it by cell (stable), forms the 1-D Gaussian weights and cuts
-// it into runs of visibilities that share a cell; a warp sums the (2r+1)^2
-// footprint cells of a run (lane per footprint cell, compensated FP32, input
-// order) and adds them to an FP64 grid.  A final pass applies the Hermitian
-// mirror and writes the FP32 outputs.
+// memory, forms the 1-D Gaussian weights and cuts it into runs of
+// visibilities that share a cell (and at every CHUNK-th record); a warp sums
+// the (2r+1)^2 footprint cells of a run (lane per pair of footprint cells,
+// compensated FP32, input order) and adds them to an FP64 grid.  A final pass
+// applies the Hermitian mirror and writes the FP32 outputs.
 //
 // Weights: w = exp(-(dx - fx)^2 s) exp(-(dy - fy)^2 s), s = 1/(2 sigma^2),
 // with the fractional offset f = u/dU - c carried as a float pair (the exact
