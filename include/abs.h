@@ -323,7 +323,10 @@ abs_status abs_simulate_vis(abs_ctx *ctx, int32_t m, double dtheta, const float 
  * chunk) is timed twice on the call's own fields and the fastest is kept, by
  * configuration, for the context and its batch lanes (an abs_estimate_batched
  * call with an untuned split-BF16 item runs its items one after another for
- * that call).  With the autotuner off the shape comes from a cost model.
+ * that call).  The ring transforms' pass split (lines per CTA of the column
+ * and the row pass) is tuned the same way, per configuration and input form.
+ * Tuning synchronises the stream on that first call.  With the autotuner off
+ * the shapes come from cost models.
  * abs_autotune(ctx, 0 | 1) turns it off / on (on by default); shapes already
  * chosen are kept.  abs_tuned_shape writes the shape chosen for cfg: *kc the
  * chunk width (0: none yet), *grouped 1 for grouped row tiles, *measured 1 if
