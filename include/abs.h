@@ -332,6 +332,14 @@ abs_status abs_simulate_vis(abs_ctx *ctx, int32_t m, double dtheta, const float 
  * chunk width (0: none yet), *grouped 1 for grouped row tiles, *measured 1 if
  * the autotuner timed it (0: the cost model).  Any output pointer may be NULL. */
 abs_status abs_autotune(abs_ctx *ctx, int32_t enable);
+
+/* Failure detection check: one kernel waits on a device flag of the context
+ * that nothing sets, polling at most max_polls times (about 1 us apart), then
+ * latches ABS_ERR_TIMEOUT into the context's error word, as every bounded
+ * device-side wait of the library does when it gives up.  The next abs_sync
+ * returns ABS_ERR_TIMEOUT and clears it; the context stays usable.
+ * max_polls in [1, 2^20]. */
+abs_status abs_probe_timeout(abs_ctx *ctx, int32_t max_polls);
 abs_status abs_tuned_shape(abs_ctx *ctx, const abs_config *cfg, int32_t *kc, int32_t *grouped, int32_t *measured);
 
 #ifdef __cplusplus

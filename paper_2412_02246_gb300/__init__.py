@@ -94,6 +94,7 @@ def load(path: str | None = None):
         "abs_profile": ([P, i32], ctypes.c_int),
         "abs_profile_read": ([P, i32, P, P], ctypes.c_int),
         "abs_autotune": ([P, i32], ctypes.c_int),
+        "abs_probe_timeout": ([P, i32], ctypes.c_int),
         "abs_rebin": ([P, P, i32, i32, P, P, P, P, i32, i32, P, P, P], ctypes.c_int),
         "abs_bana_d": ([P, P, P, P, i32, P, P, ctypes.c_double, P], ctypes.c_int),
         "abs_simulate_vis": ([P, i32, ctypes.c_double, P, i32, ctypes.c_double, i64, P, P], ctypes.c_int),
@@ -242,6 +243,11 @@ class Context:
         _check(load().abs_simulate_vis(self.h, int(sky.shape[0]), float(dtheta), _ptr(sky), int(beam),
                                        float(beam_param), int(uv.shape[0]), _ptr(uv), _ptr(vis)),
                self.h, "abs_simulate_vis")
+
+    def probe_timeout(self, max_polls: int = 1000):
+        """Queue a bounded device-side wait that runs out (see include/abs.h); the next sync raises
+        ABS_ERR_TIMEOUT."""
+        _check(load().abs_probe_timeout(self.h, int(max_polls)), self.h, "abs_probe_timeout")
 
     def autotune(self, on: bool = True):
         """Turn the split-BF16 launch-shape autotuner on (default) or off (cost model)."""

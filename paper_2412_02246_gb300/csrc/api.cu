@@ -555,6 +555,28 @@ abs_status abs_simulate_vis(abs_ctx *ctx, int32_t m, double dtheta, const float 
     return launch_simulate_vis(ctx, m, dtheta, d_sky, beam, beam_param, n_vis, d_uv, d_vis);
 }
 
+namespace absk {
+// A bounded wait on a flag nothing sets: gives up after max_polls and latches a timeout.
+__global__ void k_wait_probe(const volatile int *flag, int max_polls, int32_t *err) {
+    if (threadIdx.x != 0) return;
+    for (int i = 0; i < max_polls; ++i) {
+        if (*flag) return;
+        __nanosleep(1000);
+    }
+    atomicCAS(err, 0, DERR_TIMEOUT);
+}
+}  // namespace absk
+
+abs_status abs_probe_timeout(abs_ctx *ctx, int32_t max_polls) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    if (max_polls < 1 || max_polls > (1 << 20)) return fail(ctx, ABS_ERR_INVALID_ARG, "max_polls must be in [1, 2^20]");
+    int *flag = (int *)workspace_zeroed(ctx, "probe.flag", sizeof(int));
+    if (!flag) return fail(ctx, ABS_ERR_OOM, "probe flag");
+    k_wait_probe<<<1, 32, 0, ctx->stream>>>(flag, max_polls, ctx->d_err);
+    return check_launch(ctx, "timeout probe");
+}
+
 abs_status abs_autotune(abs_ctx *ctx, int32_t enable) {
     if (!ctx) return ABS_ERR_INVALID_ARG;
     ctx->autotune = enable != 0;

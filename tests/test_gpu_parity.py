@@ -588,6 +588,30 @@ def test_simulate_vis(ctx, beam, param):
 
 
 @pytest.mark.gpu
+def test_bounded_wait_timeout_is_reported_and_context_survives():
+    """A device-side wait that runs out (a flag nothing sets, 2,000 polls) latches
+    ABS_ERR_TIMEOUT, which the next sync reports; the same context then estimates
+    the tiny workload correctly."""
+    absbuild.build()
+    c = absmod.Context(0)
+    try:
+        c.probe_timeout(2000)
+        with pytest.raises(absmod.AbsError) as ei:
+            c.sync()
+        assert ei.value.status == absmod.ABS_ERR_TIMEOUT
+        c.sync()                                   # cleared
+        inp = inputs(0)
+        wl = inp.wl
+        cfg = absmod.Config.from_workload(wl)
+        est = oracle_run(("est", 0), wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+        B, T, E, _ = absmod.estimate(cfg, to_dev(inp.uv), to_dev(synth.vis_as_float2(inp.vis)), c)
+        c.sync()
+        assert np.array_equal(T.cpu().numpy(), est.T)
+    finally:
+        c.close()
+
+
+@pytest.mark.gpu
 def test_autotuner_split_bf16():
     """The split-BF16 launch shape: measured on a configuration's first eager
     call (autotuner on, the default) or from the cost model (off); either way
