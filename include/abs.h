@@ -340,6 +340,12 @@ abs_status abs_autotune(abs_ctx *ctx, int32_t enable);
  * returns ABS_ERR_TIMEOUT and clears it; the context stays usable.
  * max_polls in [1, 2^20]. */
 abs_status abs_probe_timeout(abs_ctx *ctx, int32_t max_polls);
+
+/* Failure injection on the host: the next `count` workspace allocations of the
+ * context fail as if the device were out of memory (no device call is made
+ * for them), so the calls that need them return ABS_ERR_OOM; later calls
+ * allocate normally.  count >= 0 (0 turns it off). */
+abs_status abs_inject_alloc_failures(abs_ctx *ctx, int32_t count);
 abs_status abs_tuned_shape(abs_ctx *ctx, const abs_config *cfg, int32_t *kc, int32_t *grouped, int32_t *measured);
 
 #ifdef __cplusplus

@@ -95,6 +95,7 @@ def load(path: str | None = None):
         "abs_profile_read": ([P, i32, P, P], ctypes.c_int),
         "abs_autotune": ([P, i32], ctypes.c_int),
         "abs_probe_timeout": ([P, i32], ctypes.c_int),
+        "abs_inject_alloc_failures": ([P, i32], ctypes.c_int),
         "abs_rebin": ([P, P, i32, i32, P, P, P, P, i32, i32, P, P, P], ctypes.c_int),
         "abs_bana_d": ([P, P, P, P, i32, P, P, ctypes.c_double, P], ctypes.c_int),
         "abs_simulate_vis": ([P, i32, ctypes.c_double, P, i32, ctypes.c_double, i64, P, P], ctypes.c_int),
@@ -248,6 +249,10 @@ class Context:
         """Queue a bounded device-side wait that runs out (see include/abs.h); the next sync raises
         ABS_ERR_TIMEOUT."""
         _check(load().abs_probe_timeout(self.h, int(max_polls)), self.h, "abs_probe_timeout")
+
+    def inject_alloc_failures(self, count: int):
+        """Make the next `count` workspace allocations fail (host-side failure injection)."""
+        _check(load().abs_inject_alloc_failures(self.h, int(count)), self.h, "abs_inject_alloc_failures")
 
     def autotune(self, on: bool = True):
         """Turn the split-BF16 launch-shape autotuner on (default) or off (cost model)."""

@@ -103,6 +103,7 @@ struct abs_ctx {
     // autotuner: launch shapes of the split-BF16 kernel measured on a configuration's
     // first eager call, by configuration key; kept by the root context (lanes share it)
     bool autotune = true;
+    int32_t fail_allocs = 0;         // test hook: this many workspace allocations fail next
     struct TcShape { int kc = 0; bool grouped = false; bool measured = false; };
     std::map<std::string, TcShape> tc_shapes;
     std::map<std::string, std::pair<int, int>> fft_shapes;   // lines per CTA: column pass, row pass

@@ -224,6 +224,10 @@ void *workspace(abs_ctx *ctx, const char *name, size_t bytes) {
         w.bytes = 0;
     }
     const size_t want = bytes + bytes / 8;   // some headroom against regrowth
+    if (ctx->fail_allocs > 0) {              // injected failure (abs_inject_alloc_failures)
+        --ctx->fail_allocs;
+        return nullptr;
+    }
     if (cudaMalloc(&w.p, want) != cudaSuccess) {
         cudaGetLastError();
         w.p = nullptr;
@@ -566,6 +570,12 @@ __global__ void k_wait_probe(const volatile int *flag, int max_polls, int32_t *e
     atomicCAS(err, 0, DERR_TIMEOUT);
 }
 }  // namespace absk
+
+abs_status abs_inject_alloc_failures(abs_ctx *ctx, int32_t count) {
+    if (!ctx || count < 0) return ABS_ERR_INVALID_ARG;
+    ctx->fail_allocs = count;
+    return ABS_OK;
+}
 
 abs_status abs_probe_timeout(abs_ctx *ctx, int32_t max_polls) {
     if (!ctx) return ABS_ERR_INVALID_ARG;

@@ -612,6 +612,30 @@ def test_bounded_wait_timeout_is_reported_and_context_survives():
 
 
 @pytest.mark.gpu
+def test_injected_allocation_failure_reports_oom_and_recovers():
+    """Host-side failure injection: the first workspace allocation of a fresh
+    context fails, abs_estimate returns ABS_ERR_OOM, and the next call on the
+    same context allocates and estimates correctly."""
+    absbuild.build()
+    c = absmod.Context(0)
+    try:
+        inp = inputs(0)
+        wl = inp.wl
+        cfg = absmod.Config.from_workload(wl)
+        uv, vis = to_dev(inp.uv), to_dev(synth.vis_as_float2(inp.vis))
+        c.inject_alloc_failures(1)
+        with pytest.raises(absmod.AbsError) as ei:
+            absmod.estimate(cfg, uv, vis, c)
+        assert ei.value.status == absmod.ABS_ERR_OOM
+        B, T, E, _ = absmod.estimate(cfg, uv, vis, c)
+        c.sync()
+        est = oracle_run(("est", 0), wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+        assert np.array_equal(T.cpu().numpy(), est.T)
+    finally:
+        c.close()
+
+
+@pytest.mark.gpu
 def test_autotuner_split_bf16():
     """The split-BF16 launch shape: measured on a configuration's first eager
     call (autotuner on, the default) or from the cost model (off); either way
