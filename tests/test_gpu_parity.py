@@ -636,6 +636,35 @@ def test_injected_allocation_failure_reports_oom_and_recovers():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("prec", [0, 1])
+def test_run_to_run_determinism(ctx, prec):
+    """The same estimate three times (eager, captured, replayed): counts bit-exact and
+    mean l identical; B equal to rounding (the gridding's FP64 atomics may add in a
+    different order)."""
+    inp = inputs(1)
+    wl = inp.wl
+    cfg = absmod.Config.from_workload(wl, precision=absmod.ABS_SPLIT_BF16 if prec else absmod.ABS_FP32)
+    uv, vis = to_dev(inp.uv), to_dev(synth.vis_as_float2(inp.vis))
+    nt = len(absmod.abs_triplets(cfg))
+    B = torch.empty(nt, dtype=torch.float64, device=dev())
+    T = torch.empty(nt, dtype=torch.int64, device=dev())
+    E = torch.empty(cfg.n_bins, dtype=torch.float64, device=dev())
+    runs = []
+    for _ in range(3):
+        B.fill_(-1.0)
+        T.fill_(-1)
+        ctx.abs_estimate(cfg, uv, vis, nt, None, B, T, E)
+        ctx.sync()
+        runs.append((B.cpu().numpy().copy(), T.cpu().numpy().copy(), E.cpu().numpy().copy()))
+    for Bk, Tk, Ek in runs[1:]:
+        assert np.array_equal(Tk, runs[0][1])
+        assert np.array_equal(Ek, runs[0][2], equal_nan=True)
+        ok = ~np.isnan(runs[0][0])
+        assert np.array_equal(np.isnan(Bk), ~ok)
+        assert np.allclose(Bk[ok], runs[0][0][ok], rtol=1e-9, atol=1e-12 * np.abs(runs[0][0][ok]).max())
+
+
+@pytest.mark.gpu
 def test_autotuner_split_bf16():
     """The split-BF16 launch shape: measured on a configuration's first eager
     call (autotuner on, the default) or from the cost model (off); either way
