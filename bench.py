@@ -73,27 +73,20 @@ def load_peaks():
 # source has changed since then reports null.
 MEASURED_TRAFFIC = {
     "grid": {"bytes": 20339968, "source": "paper_2412_02246_gb300/csrc/grid.cu",
-           "sha256": "70be2b06c383f602aaf00e7804b1cc35bdaa232fc73ae16926d4d3499348f46e",
-           "profile": "profiles/k_grid_mwa975k.md"},
+           "sha256": "70be2b06c383f602aaf00e7804b1cc35bdaa232fc73ae16926d4d3499348f46e"},
     "fft_rows": {"bytes": 2880000, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-               "sha256": "eb38a2816f985ec629765661f3343c9580143cf0c7c03b76c4de5f6d4d3858b1",
-               "profile": "profiles/k_fft_rows_mwa975k.md"},
+               "sha256": "eb38a2816f985ec629765661f3343c9580143cf0c7c03b76c4de5f6d4d3858b1"},
     "fft_cols": {"bytes": 722688, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-               "sha256": "eb38a2816f985ec629765661f3343c9580143cf0c7c03b76c4de5f6d4d3858b1",
-               "profile": "profiles/k_fft_cols_mwa975k.md"},
+               "sha256": "eb38a2816f985ec629765661f3343c9580143cf0c7c03b76c4de5f6d4d3858b1"},
     "triple_fp32": {"bytes": 6663168, "source": "paper_2412_02246_gb300/csrc/triple.cu",
-                  "sha256": "9a60a87aacafce2b1892ae57df49c65a93128134aa022893817ffe6aa540d175",
-                  "profile": "profiles/k_triple_fp32_mwa975k.md"},
+                  "sha256": "9a60a87aacafce2b1892ae57df49c65a93128134aa022893817ffe6aa540d175"},
     "triple_tc": {"bytes": 6703872, "source": "paper_2412_02246_gb300/csrc/triple_tc.cu",
-                "sha256": "2366406142f503e351c2cf81f0169e8a6f3923eb458df2fbe972621d9f20abd3",
-                "profile": "profiles/k_triple_tc_mwa975k.md"},
+                "sha256": "2366406142f503e351c2cf81f0169e8a6f3923eb458df2fbe972621d9f20abd3"},
     # one channel of the multi-channel workload (channel 0)
     "channel_fft_rows": {"bytes": 660686848, "source": "paper_2412_02246_gb300/csrc/fft.cu",
-                         "sha256": "eb38a2816f985ec629765661f3343c9580143cf0c7c03b76c4de5f6d4d3858b1",
-                         "profile": "profiles/k_fft_rows_channels4096.md"},
+                         "sha256": "eb38a2816f985ec629765661f3343c9580143cf0c7c03b76c4de5f6d4d3858b1"},
     "channel_triple_tc": {"bytes": 829349120, "source": "paper_2412_02246_gb300/csrc/triple_tc.cu",
-                          "sha256": "df4ad8e191f63240b08a8b4097b641d8d02e4da3c61b2ae31542aad2c465f3a9",
-                          "profile": "profiles/k_triple_tc_channels4096.md"},
+                          "sha256": "df4ad8e191f63240b08a8b4097b641d8d02e4da3c61b2ae31542aad2c465f3a9"},
 }
 
 

@@ -237,7 +237,12 @@ abs_status abs_estimate_host(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis,
  * scratch holds at least one partial per triplet; larger problems use fewer
  * pixel splits).  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the one array and it keeps
+ * call before any stream capture.  The address is kept for the life of the
+ * process, so resetting a device (cudaDeviceReset) after its first call is
+ * not supported: the kept address would no longer be the array's.  A launch
+ * failure of this call's own kernels returns ABS_ERR_CUDA; errors left over
+ * from earlier work of the caller are neither reported nor cleared.  All
+ * calls share the one array and it keeps
  * the last call's contents: calls whose work overlaps on the GPU (different
  * streams, or host threads) race on it and give wrong sums, so serialise them.
  * The paper has no counterpart to this entry point; it is a deployment aid. */

@@ -137,6 +137,13 @@ class Config:
     def n_bins(self) -> int:
         return len(self.ell_edges) - 1
 
+    @property
+    def N(self) -> int:
+        """The sky-grid side the library uses for this configuration (abs_fft_size)."""
+        if not hasattr(self, "_N"):
+            self._N = abs_fft_size(self)
+        return self._N
+
     def ref(self):
         return ctypes.byref(self._c)
 
@@ -160,6 +167,41 @@ def _ptr(t):
     if t is None:
         return None
     return ctypes.c_void_p(t.data_ptr())
+
+
+_DT = {"f32": "float32", "f64": "float64", "i32": "int32", "i64": "int64", "u8": "uint8"}
+
+
+def _dev(t, dt: str, numel: int, name: str, device: int | None = None, optional: bool = False):
+    """Pointer of a device-buffer argument, after checking what the C ABI cannot:
+    a contiguous CUDA tensor of the documented element type, on the expected
+    device, holding at least `numel` elements.  A wrong buffer would otherwise
+    be read or written out of bounds by the kernels.  Raises ValueError."""
+    import torch
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{name}: a CUDA tensor is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor, got {type(t).__name__}"
+                         + ("" if not isinstance(t, torch.Tensor) else f" on {t.device}"))
+    if t.dtype != getattr(torch, _DT[dt]):
+        raise ValueError(f"{name}: dtype {t.dtype}, expected torch.{_DT[dt]}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: tensor must be contiguous")
+    want = torch.cuda.current_device() if device is None else device
+    if t.device.index != want:
+        raise ValueError(f"{name}: on cuda:{t.device.index}, expected cuda:{want}")
+    if t.numel() < numel:
+        raise ValueError(f"{name}: {t.numel()} elements, at least {numel} required")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ijk_rows(ijk, name="ijk", device=None):
+    """(pointer, rows) of a triplet list: int32 [n][3] on the device."""
+    if ijk.dim() != 2 or ijk.shape[1] != 3:
+        raise ValueError(f"{name}: shape {tuple(ijk.shape)}, expected (n, 3)")
+    return _dev(ijk, "i32", ijk.numel(), name, device), int(ijk.shape[0])
 
 
 # ------------------------------------------------------------------ host helpers
@@ -226,23 +268,40 @@ class Context:
         """(l1, mu, t) cells of B ([R][n_trip] or [n_trip] CUDA FP64): count-weighted means per
         realisation, then their ensemble mean and spread; outputs [n_bins][n_mu][n_t] FP64."""
         n_real = B.shape[0] if B.dim() == 2 else 1
-        n_trip = B.shape[-1]
-        _check(load().abs_rebin(self.h, cfg.ref(), int(n_real), int(n_trip), _ptr(B), _ptr(counts), _ptr(ellbar),
-                                None if ijk is None else _ptr(ijk), int(n_mu), int(n_t),
-                                None if mean is None else _ptr(mean), None if sigma is None else _ptr(sigma),
-                                None if weight is None else _ptr(weight)), self.h, "abs_rebin")
+        n_trip = int(B.shape[-1])
+        d, nc = self.device, cfg.n_bins * int(n_mu) * int(n_t)
+        pijk = None
+        if ijk is not None:
+            pijk, rows = _ijk_rows(ijk, device=d)
+            if rows < n_trip:
+                raise ValueError(f"ijk: {rows} triplets, B has {n_trip}")
+        _check(load().abs_rebin(self.h, cfg.ref(), int(n_real), n_trip, _dev(B, "f64", n_real * n_trip, "B", d),
+                                _dev(counts, "i64", n_trip, "counts", d),
+                                _dev(ellbar, "f64", cfg.n_bins, "ellbar", d), pijk, int(n_mu), int(n_t),
+                                _dev(mean, "f64", nc, "mean", d, optional=True),
+                                _dev(sigma, "f64", nc, "sigma", d, optional=True),
+                                _dev(weight, "f64", nc, "weight", d, optional=True)), self.h, "abs_rebin")
 
     def abs_bana_d(self, cfg: "Config", C, mask, counts, out, ijk=None, f_over_sigma: float = 0.3):
         """[B_Ana]_d per triplet (CUDA FP64 out) from C(l_g) per uv cell (CUDA FP64 [n][n]),
         the filled mask (CUDA uint8 [n][n]) and the triangle counts of that mask."""
-        _check(load().abs_bana_d(self.h, cfg.ref(), _ptr(C), _ptr(mask), int(out.shape[0]), _ptr(ijk),
-                                 _ptr(counts), float(f_over_sigma), _ptr(out)), self.h, "abs_bana_d")
+        d, c, nt = self.device, cfg.n_grid * cfg.n_grid, int(out.shape[0])
+        pijk = None
+        if ijk is not None:
+            pijk, rows = _ijk_rows(ijk, device=d)
+            if rows < nt:
+                raise ValueError(f"ijk: {rows} triplets, out has {nt}")
+        _check(load().abs_bana_d(self.h, cfg.ref(), _dev(C, "f64", c, "C", d), _dev(mask, "u8", c, "mask", d), nt,
+                                 pijk, _dev(counts, "i64", nt, "counts", d), float(f_over_sigma),
+                                 _dev(out, "f64", nt, "out", d)), self.h, "abs_bana_d")
 
     def abs_simulate_vis(self, sky, dtheta: float, uv, vis, beam: int = 0, beam_param: float = 0.0):
         """Eq. vis by direct DFT of the beam-weighted map (CUDA FP32 [m][m]) at the baselines uv
         (CUDA FP32 [n][2]) into vis (CUDA FP32 [n][2]); beam ABS_BEAM_NONE / MWA_TILE / GAUSS."""
-        _check(load().abs_simulate_vis(self.h, int(sky.shape[0]), float(dtheta), _ptr(sky), int(beam),
-                                       float(beam_param), int(uv.shape[0]), _ptr(uv), _ptr(vis)),
+        m, nv, d = int(sky.shape[0]), int(uv.shape[0]), self.device
+        _check(load().abs_simulate_vis(self.h, m, float(dtheta), _dev(sky, "f32", m * m, "sky", d), int(beam),
+                                       float(beam_param), nv, _dev(uv, "f32", 2 * nv, "uv", d),
+                                       _dev(vis, "f32", 2 * nv, "vis", d)),
                self.h, "abs_simulate_vis")
 
     def probe_timeout(self, max_polls: int = 1000):
@@ -275,42 +334,72 @@ class Context:
 
     # ------------- stages (torch CUDA tensors in, torch CUDA tensors out)
     def abs_grid(self, cfg: Config, uv, vis, grid, wsum, mask):
-        _check(load().abs_grid(self.h, cfg.ref(), uv.shape[0], _ptr(uv), _ptr(vis), _ptr(grid), _ptr(wsum),
-                               _ptr(mask)), self.h, "abs_grid")
+        nv, c = int(uv.shape[0]), cfg.n_grid * cfg.n_grid
+        d = self.device
+        _check(load().abs_grid(self.h, cfg.ref(), nv, _dev(uv, "f32", 2 * nv, "uv", d),
+                               _dev(vis, "f32", 2 * nv, "vis", d), _dev(grid, "f32", 2 * c, "grid", d),
+                               _dev(wsum, "f32", c, "wsum", d), _dev(mask, "u8", c, "mask", d)),
+               self.h, "abs_grid")
 
     def abs_filter_fft(self, cfg: Config, grid, wsum, mask, fields):
-        _check(load().abs_filter_fft(self.h, cfg.ref(), _ptr(grid), _ptr(wsum), _ptr(mask), _ptr(fields)),
+        c, d = cfg.n_grid * cfg.n_grid, self.device
+        _check(load().abs_filter_fft(self.h, cfg.ref(), _dev(grid, "f32", 2 * c, "grid", d),
+                                     _dev(wsum, "f32", c, "wsum", d), _dev(mask, "u8", c, "mask", d),
+                                     _dev(fields, "f32", cfg.n_bins * cfg.N * cfg.N, "fields", d)),
                self.h, "abs_filter_fft")
 
     def abs_triple(self, cfg: Config, fields, mask, ijk, sums=None, counts=None):
-        _check(load().abs_triple(self.h, cfg.ref(), _ptr(fields), _ptr(mask), ijk.shape[0], _ptr(ijk),
-                                 _ptr(sums), _ptr(counts)), self.h, "abs_triple")
+        d = self.device
+        pijk, nt = _ijk_rows(ijk, device=d)
+        _check(load().abs_triple(self.h, cfg.ref(), _dev(fields, "f32", cfg.n_bins * cfg.N * cfg.N, "fields", d,
+                                                                 optional=sums is None),
+                                 _dev(mask, "u8", cfg.n_grid * cfg.n_grid, "mask", d, optional=counts is None),
+                                 nt, pijk, _dev(sums, "f64", nt, "sums", d, optional=True),
+                                 _dev(counts, "i64", nt, "counts", d, optional=True)), self.h, "abs_triple")
 
     def abs_normalise(self, cfg: Config, sums, counts, B, mask=None, ellbar=None):
-        _check(load().abs_normalise(self.h, cfg.ref(), sums.shape[0], _ptr(sums), _ptr(counts), _ptr(B),
-                                    _ptr(mask), _ptr(ellbar)), self.h, "abs_normalise")
+        nt, d = int(sums.shape[0]), self.device
+        _check(load().abs_normalise(self.h, cfg.ref(), nt, _dev(sums, "f64", nt, "sums", d),
+                                    _dev(counts, "i64", nt, "counts", d), _dev(B, "f64", nt, "B", d),
+                                    _dev(mask, "u8", cfg.n_grid * cfg.n_grid, "mask", d, optional=True),
+                                    _dev(ellbar, "f64", cfg.n_bins, "ellbar", d, optional=True)),
+               self.h, "abs_normalise")
+
+    def _est_ptrs(self, cfg, uv, vis, n_real, n_trip, ijk, B, counts, ellbar):
+        nv, d, nt = int(uv.shape[0]), self.device, int(n_trip)
+        if ijk is not None:
+            pijk, rows = _ijk_rows(ijk, device=d)
+            if rows < nt:
+                raise ValueError(f"ijk: {rows} triplets, n_trip = {nt}")
+        else:
+            pijk = None
+        return (nv, _dev(uv, "f32", 2 * nv, "uv", d), _dev(vis, "f32", 2 * nv * n_real, "vis", d), pijk,
+                _dev(B, "f64", nt * n_real, "B", d, optional=True),
+                _dev(counts, "i64", nt, "counts", d, optional=True),
+                _dev(ellbar, "f64", cfg.n_bins, "ellbar", d, optional=True))
 
     def abs_estimate(self, cfg: Config, uv, vis, n_trip, ijk=None, B=None, counts=None, ellbar=None):
-        _check(load().abs_estimate(self.h, cfg.ref(), uv.shape[0], _ptr(uv), _ptr(vis), int(n_trip), _ptr(ijk),
-                                   _ptr(B), _ptr(counts), _ptr(ellbar)), self.h, "abs_estimate")
+        nv, puv, pvis, pijk, pB, pT, pE = self._est_ptrs(cfg, uv, vis, 1, n_trip, ijk, B, counts, ellbar)
+        _check(load().abs_estimate(self.h, cfg.ref(), nv, puv, pvis, int(n_trip), pijk, pB, pT, pE),
+               self.h, "abs_estimate")
 
     def abs_estimate_many(self, cfg: Config, uv, vis, n_trip, ijk=None, B=None, counts=None, ellbar=None):
-        n_real = vis.shape[0]
-        _check(load().abs_estimate_many(self.h, cfg.ref(), uv.shape[0], _ptr(uv), n_real, _ptr(vis), int(n_trip),
-                                        _ptr(ijk), _ptr(B), _ptr(counts), _ptr(ellbar)), self.h,
-               "abs_estimate_many")
+        n_real = int(vis.shape[0])
+        nv, puv, pvis, pijk, pB, pT, pE = self._est_ptrs(cfg, uv, vis, n_real, n_trip, ijk, B, counts, ellbar)
+        _check(load().abs_estimate_many(self.h, cfg.ref(), nv, puv, n_real, pvis, int(n_trip), pijk, pB, pT, pE),
+               self.h, "abs_estimate_many")
 
     def abs_estimate_batched(self, items):
         """items: sequence of (cfg, uv, vis, n_trip, ijk, B, counts, ellbar), torch CUDA tensors or None,
         one independent estimate each (configurations may differ)."""
         arr = (abs_item * max(len(items), 1))()
         for a, (cfg, uv, vis, n_trip, ijk, B, counts, ellbar) in zip(arr, items):
+            nv, puv, pvis, pijk, pB, pT, pE = self._est_ptrs(cfg, uv, vis, 1, n_trip, ijk, B, counts, ellbar)
             a.cfg = ctypes.pointer(cfg._c)
-            a.n_vis = uv.shape[0]
-            a.d_uv, a.d_vis = uv.data_ptr(), vis.data_ptr()
+            a.n_vis = nv
+            a.d_uv, a.d_vis = puv.value, pvis.value
             a.n_trip = int(n_trip)
-            a.d_ijk, a.d_B, a.d_count, a.d_ellbar = [None if t is None else t.data_ptr()
-                                                     for t in (ijk, B, counts, ellbar)]
+            a.d_ijk, a.d_B, a.d_count, a.d_ellbar = [None if p is None else p.value for p in (pijk, pB, pT, pE)]
         _check(load().abs_estimate_batched(self.h, len(items), ctypes.cast(arr, ctypes.c_void_p)), self.h,
                "abs_estimate_batched")
 
@@ -338,8 +427,9 @@ def abs_triple_sums_static(cfg: Config, fields, ijk, sums, stream=None):
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
-    st = load().abs_triple_sums_static(cfg.ref(), _ptr(fields), int(ijk.shape[0]), _ptr(ijk), _ptr(sums),
-                                       ctypes.c_void_p(stream.cuda_stream))
+    pijk, nt = _ijk_rows(ijk)
+    st = load().abs_triple_sums_static(cfg.ref(), _dev(fields, "f32", cfg.n_bins * cfg.N * cfg.N, "fields"), nt,
+                                       pijk, _dev(sums, "f64", nt, "sums"), ctypes.c_void_p(stream.cuda_stream))
     _check(st, None, "abs_triple_sums_static")
 
 

@@ -417,11 +417,29 @@ extern "C" abs_status abs_triple_sums_static(const abs_config *cfg, const float 
     if (!triple_plan(cfg->n_bins, N, n_trip, sms, std::max<int64_t>(1, cap / n_trip), d_fields, tp))
         return ABS_ERR_UNSUPPORTED;
     const int64_t nsplit = tp.nsplit;
-    cudaFuncSetAttribute(k_triple_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem);
-    k_triple_fp32<<<dim3((unsigned)nsplit, tp.tgroups), tp.threads, tp.smem, stream>>>(tp.G, d_fields, d_ijk,
-                                                                                        partial);
-    k_triple_reduce<<<(int)cdiv(n_trip, 8), 256, 0, stream>>>(n_trip, (int)nsplit,
-                                                               1.0 / ((double)N * (double)N), partial, d_sum,
-                                                               nullptr, 1.0, nullptr);
-    return cudaGetLastError() == cudaSuccess ? ABS_OK : ABS_ERR_CUDA;
+    if (cudaFuncSetAttribute(k_triple_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return ABS_ERR_CUDA;
+    }
+    // each launch's own status (an error left over from the caller's earlier work is not ours to report)
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)nsplit, tp.tgroups);
+    lc.blockDim = dim3(tp.threads);
+    lc.dynamicSmemBytes = tp.smem;
+    lc.stream = stream;
+    if (cudaLaunchKernelEx(&lc, k_triple_fp32, tp.G, d_fields, d_ijk, partial) != cudaSuccess) {
+        cudaGetLastError();
+        return ABS_ERR_CUDA;
+    }
+    lc.gridDim = dim3((unsigned)cdiv(n_trip, 8));
+    lc.blockDim = dim3(256);
+    lc.dynamicSmemBytes = 0;
+    const double *cpartial = partial;
+    if (cudaLaunchKernelEx(&lc, k_triple_reduce, (int)n_trip, (int)nsplit, 1.0 / ((double)N * (double)N), cpartial,
+                           d_sum, (const int64_t *)nullptr, 1.0, (double *)nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        return ABS_ERR_CUDA;
+    }
+    return ABS_OK;
 }

@@ -95,3 +95,21 @@ def test_product_path_has_no_cpu_fallback(monkeypatch, tmp_path):
     monkeypatch.setattr(absmod, "_lib", None)
     with pytest.raises(RuntimeError):
         absmod.load(str(tmp_path / "missing.so"))
+
+
+def test_binding_rejects_wrong_buffers_before_the_call():
+    """The binding checks device-buffer arguments (CUDA, dtype, contiguity, size)
+    before any pointer crosses the ABI; CPU tensors and misshapen triplet lists
+    are refused on the host."""
+    import torch
+    import paper_2412_02246_gb300 as m
+    cfg = m.Config(n_grid=64, du=2.0, ell_edges=np.linspace(25.0, 375.0, 9))
+    f = torch.zeros((8, cfg.N, cfg.N), dtype=torch.float32)
+    with pytest.raises(ValueError, match="CUDA"):
+        m.abs_triple_sums_static(cfg, f, torch.zeros((3, 3), dtype=torch.int32), torch.zeros(3, dtype=torch.float64),
+                                 stream=type("S", (), {"cuda_stream": 0})())
+    with pytest.raises(ValueError, match=r"\(n, 3\)"):
+        m._ijk_rows(torch.zeros((3, 2), dtype=torch.int32))
+    with pytest.raises(ValueError, match="required"):
+        m._dev(None, "f32", 1, "x")
+    assert m._dev(None, "f32", 1, "x", optional=True) is None

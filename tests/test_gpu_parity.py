@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances (stated by the method's accuracy requirements):
+Tolerances (the method's accuracy requirements):
   * masks and triangle counts: bit-exact;
   * gridded sums: |dV_g| <= 1e-6 sum_i w |V_i| per cell (normwise: the
     componentwise error of a sum that cancels is unbounded), weights 1e-6;

@@ -52,3 +52,17 @@ def test_interrupted_run_resumes_where_it_stopped(tmp_path):
 def test_names_must_be_unique(tmp_path):
     with pytest.raises(ValueError):
         resume.run_resumable(FakeCtx(), _items(2), ["a", "a"], str(tmp_path))
+
+
+def test_stale_results_of_another_setup_are_rerun(tmp_path):
+    """A result on disk from a different setup (here another triplet count, then
+    another caller tag) does not count as done."""
+    names = [f"item{k}" for k in range(3)]
+    resume.run_resumable(FakeCtx(), _items(3), names, str(tmp_path), tags=["s0", "s1", "s2"])
+    ctx = FakeCtx()
+    changed = _items(3)
+    changed[1] = changed[1][:3] + (5,) + changed[1][4:]
+    assert resume.run_resumable(ctx, changed, names, str(tmp_path), tags=["s0", "s1", "s2"]) == ["item1"]
+    ctx = FakeCtx()
+    assert resume.run_resumable(ctx, changed, names, str(tmp_path), tags=["s0", "s1", "x"]) == ["item2"]
+    assert resume.run_resumable(FakeCtx(), changed, names, str(tmp_path), tags=["s0", "s1", "x"]) == []
