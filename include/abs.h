@@ -208,6 +208,19 @@ typedef struct abs_item {
  * not overlap. */
 abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *items);
 
+/* abs_estimate_batched from HOST memory: every item's d_uv and d_vis are host
+ * inputs and its d_B, d_count and d_ellbar host outputs (each may be NULL), with
+ * the layouts of abs_item; d_ijk, if given, is a device list.  Each item's
+ * inputs are copied to device buffers of the lane it runs on, its estimate
+ * runs there and its outputs are copied back, all on that lane's streams, so
+ * one item's copies overlap the other lanes' work.  With page-locked host
+ * buffers the copies are part of the batch's CUDA graph (captured on the
+ * second call with the same items, as for abs_estimate_batched); pageable
+ * buffers work too, without the graph.  Validation as abs_estimate_batched;
+ * the call waits until every output is in host memory and reports latched
+ * device errors as abs_sync does. */
+abs_status abs_estimate_batched_host(abs_ctx *ctx, int32_t n_items, const abs_item *items);
+
 /* abs_estimate_many from HOST memory: copies h_uv, h_vis to the device,
  * runs, copies h_B, h_count, h_ellbar back, and waits for completion.
  * h_ijk NULL = canonical list.  Pinned host buffers make the copies

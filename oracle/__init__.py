@@ -14,6 +14,8 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
 
 * cell / ring thresholds / triplets: explicit worked cases, integer brute force
 * grid: single-visibility closed forms, Hermitian mirror, NGP exact sums
+* fft_form / fft_form_all: against brute force on tiny grids (sums to rounding,
+  counts exact), at two admissible sky-grid sizes, aliasing below 3R+1
 * triple_bruteforce / triple_one: pure-Python enumeration on tiny grids,
   FFT identity, constant-sky B = s^3, point-source phase closure,
   ring-constant product, rotation/reflection invariance, permutation
@@ -207,27 +209,42 @@ def normalise(S: np.ndarray, T: np.ndarray, norm_A: float = 1.0) -> np.ndarray:
 # ------------------------------------------------------------------ FFT form
 
 
+def _fft2(Z):
+    """Unnormalised forward 2-D DFT (numpy's convention), on every host core when scipy is there."""
+    try:
+        import scipy.fft
+        return scipy.fft.fft2(Z, workers=os.cpu_count() or 1)
+    except ImportError:
+        return np.fft.fft2(Z)
+
+
 def ring_fields(X: np.ndarray, filled: np.ndarray, q: np.ndarray, N: int, unit: bool = False):
     """Real fields D_m(p) = sum_{g in a_m} X_g exp(-2 pi i g.p / N) (Eq. iFT) on an N x N
     sky grid, via numpy's FFT; with unit=True the unit-mask fields (X = 1 on filled
     ring cells).  Returns float64 [n_bins, N, N] (imaginary parts dropped) and the
     largest |imaginary part| seen."""
-    n = X.shape[0]
+    n = filled.shape[0]
     half = n // 2 - 1
     gy, gx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     gy = np.where(gy > n // 2, gy - n, gy)
     gx = np.where(gx > n // 2, gx - n, gx)
     r2 = gx.astype(np.int64) ** 2 + gy.astype(np.int64) ** 2
-    inside = (np.abs(gx) <= half) & (np.abs(gy) <= half) & (filled > 0)
+    inside = (np.abs(gx) <= half) & (np.abs(gy) <= half) & (filled > 0) & (r2 >= q[0]) & (r2 < q[-1])
+    # the filled cells of every ring, ring by ring (ring m: Q_m <= |g|^2 < Q_{m+1})
+    cells = np.nonzero(inside.ravel())[0]
+    ring = np.searchsorted(np.asarray(q), r2.ravel()[cells], side="right") - 1
+    order = np.argsort(ring, kind="stable")
+    cells, ring = cells[order], ring[order]
     nb = len(q) - 1
+    start = np.searchsorted(ring, np.arange(nb + 1))
     D = np.zeros((nb, N, N))
     im = 0.0
     for m in range(nb):
-        sel = inside & (r2 >= q[m]) & (r2 < q[m + 1])
+        c = cells[start[m]:start[m + 1]]
         Z = np.zeros((N, N), np.complex128)
-        vals = np.ones(sel.sum()) if unit else X[sel]
-        np.add.at(Z, (gy[sel] % N, gx[sel] % N), vals)
-        F = np.fft.fft2(Z)
+        vals = np.ones(len(c)) if unit else X.ravel()[c]
+        np.add.at(Z, (gy.ravel()[c] % N, gx.ravel()[c] % N), vals)
+        F = _fft2(Z)
         im = max(im, float(np.abs(F.imag).max()) if F.size else 0.0)
         D[m] = F.real
     return D, im
@@ -240,6 +257,50 @@ def fft_form(X, filled, q, ijk, N: int):
     S = np.array([np.sum(D[i] * D[j] * D[k]) for i, j, k in ijk]) / (N * N)
     T = np.array([np.sum(I[i] * I[j] * I[k]) for i, j, k in ijk]) / (N * N)
     return S, np.rint(T).astype(np.int64), T
+
+
+def fft_form_all(X, filled, q, ijk, N: int, fields=None, block: int = 65536):
+    """fft_form for a whole triplet list at large sizes (Eq. estimator_t).
+
+    The same sums, S_ijk = N^-2 sum_p D_i D_j D_k and T_ijk = N^-2 sum_p I_i I_j I_k,
+    with the sum over pixels taken by matrix products: for every middle ring j, the
+    fields D_i(p) of the rings i that pair with j, one row per i, times the products
+    (D_j D_k)(p) of its rings k, one column per k; entry (i, k) is the sum for (i, j, k).
+    The pixels are taken `block` at a time (the products for every block added up),
+    which only bounds the memory.  fields: optional (D, I) from ring_fields, to reuse.
+    Returns (S, T rounded, T before rounding, D, I)."""
+    ijk = np.asarray(ijk, np.int64).reshape(-1, 3)
+    if fields is None:
+        D, _ = ring_fields(X, filled, q, N)
+        I, _ = ring_fields(X, filled, q, N, unit=True)
+    else:
+        D, I = fields
+    nb = D.shape[0]
+    Df, If = D.reshape(nb, -1), I.reshape(nb, -1)
+    P = Df.shape[1]
+    js = np.unique(ijk[:, 1])
+    span = {}
+    for j in js:
+        sel = np.nonzero(ijk[:, 1] == j)[0]
+        span[j] = (sel, int(ijk[sel, 0].min()), int(ijk[sel, 0].max()) + 1, int(ijk[sel, 2].min()),
+                   int(ijk[sel, 2].max()) + 1)
+    MS = {j: np.zeros((span[j][2] - span[j][1], span[j][4] - span[j][3])) for j in js}
+    MT = {j: np.zeros_like(MS[j]) for j in js}
+    for p0 in range(0, P, block):
+        Db, Ib = Df[:, p0:p0 + block], If[:, p0:p0 + block]
+        for j in js:
+            _, i0, i1, k0, k1 = span[j]
+            MS[j] += Db[i0:i1] @ (Db[k0:k1] * Db[j]).T
+            MT[j] += Ib[i0:i1] @ (Ib[k0:k1] * Ib[j]).T
+    S = np.zeros(len(ijk))
+    T = np.zeros(len(ijk))
+    for j in js:
+        sel, i0, _, k0, _ = span[j]
+        S[sel] = MS[j][ijk[sel, 0] - i0, ijk[sel, 2] - k0]
+        T[sel] = MT[j][ijk[sel, 0] - i0, ijk[sel, 2] - k0]
+    S /= N * N
+    T /= N * N
+    return S, np.rint(T).astype(np.int64), T, D, I
 
 
 def min_fft_size(q: np.ndarray, n: int | None = None) -> int:

@@ -90,6 +90,7 @@ def load(path: str | None = None):
         "abs_estimate_many": ([P, C, i64, P, i32, P, i32, P, P, P, P], ctypes.c_int),
         "abs_estimate_host": ([P, C, i64, P, i32, P, i32, P, P, P, P], ctypes.c_int),
         "abs_estimate_batched": ([P, i32, P], ctypes.c_int),
+        "abs_estimate_batched_host": ([P, i32, P], ctypes.c_int),
         "abs_triple_sums_static": ([C, P, i32, P, P, P], ctypes.c_int),
         "abs_profile": ([P, i32], ctypes.c_int),
         "abs_profile_read": ([P, i32, P, P], ctypes.c_int),
@@ -195,6 +196,25 @@ def _dev(t, dt: str, numel: int, name: str, device: int | None = None, optional:
     if t.numel() < numel:
         raise ValueError(f"{name}: {t.numel()} elements, at least {numel} required")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a, dt: str, numel: int, name: str, optional: bool = False):
+    """Address (int) of a host-buffer argument: a C-contiguous numpy array or CPU torch tensor of
+    the documented element type with at least `numel` elements.  Raises ValueError."""
+    if a is None:
+        if optional:
+            return None
+        raise ValueError(f"{name}: a host array is required")
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda:
+            raise ValueError(f"{name}: expected host memory, got a CUDA tensor")
+        if str(a.dtype) != "torch." + _DT[dt] or not a.is_contiguous() or a.numel() < numel:
+            raise ValueError(f"{name}: need a contiguous {_DT[dt]} tensor of >= {numel} elements")
+        return a.data_ptr()
+    a = np.asarray(a)
+    if a.dtype != np.dtype(_DT[dt]) or not a.flags["C_CONTIGUOUS"] or a.size < numel:
+        raise ValueError(f"{name}: need a C-contiguous {_DT[dt]} array of >= {numel} elements")
+    return a.ctypes.data
 
 
 def _ijk_rows(ijk, name="ijk", device=None):
@@ -402,6 +422,29 @@ class Context:
             a.d_ijk, a.d_B, a.d_count, a.d_ellbar = [None if p is None else p.value for p in (pijk, pB, pT, pE)]
         _check(load().abs_estimate_batched(self.h, len(items), ctypes.cast(arr, ctypes.c_void_p)), self.h,
                "abs_estimate_batched")
+
+    def abs_estimate_batched_host(self, items):
+        """items: sequence of (cfg, uv, vis, n_trip, ijk, B, counts, ellbar) with uv / vis host inputs
+        and B / counts / ellbar host outputs (numpy arrays or CPU torch tensors, pinned ones let the
+        copies run inside the batch's graph; float32 [n_vis, 2], float64 [n_trip], int64 [n_trip],
+        float64 [n_bins]) and ijk None or a device triplet list; blocks until the outputs are written."""
+        arr = (abs_item * max(len(items), 1))()
+        keep = []
+        for a, (cfg, uv, vis, n_trip, ijk, B, counts, ellbar) in zip(arr, items):
+            nv, nt = int(uv.shape[0]), int(n_trip)
+            ptrs = []
+            for name, t, dt, n in (("uv", uv, "f32", 2 * nv), ("vis", vis, "f32", 2 * nv), ("B", B, "f64", nt),
+                                   ("counts", counts, "i64", nt), ("ellbar", ellbar, "f64", cfg.n_bins)):
+                ptrs.append(_host(t, dt, n, name, optional=name not in ("uv", "vis")))
+                keep.append(t)
+            a.cfg = ctypes.pointer(cfg._c)
+            a.n_vis = nv
+            a.d_uv, a.d_vis = ptrs[0], ptrs[1]
+            a.n_trip = nt
+            a.d_ijk = None if ijk is None else _ijk_rows(ijk, device=self.device)[0].value
+            a.d_B, a.d_count, a.d_ellbar = ptrs[2], ptrs[3], ptrs[4]
+        _check(load().abs_estimate_batched_host(self.h, len(items), ctypes.cast(arr, ctypes.c_void_p)), self.h,
+               "abs_estimate_batched_host")
 
     def abs_estimate_host(self, cfg: Config, uv: np.ndarray, vis: np.ndarray, n_trip: int, ijk=None,
                           B=None, counts=None, ellbar=None):

@@ -932,7 +932,12 @@ static abs_ctx *make_lane(abs_ctx *ctx) {
     return l;
 }
 
-abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *items) {
+// The batch driver of abs_estimate_batched and abs_estimate_batched_host.  With
+// host = true the items' uv / vis are host inputs and B / count / ellbar host
+// outputs: each item is staged through its lane's own device buffers (copies in,
+// estimate, copies out, all on the lane's streams, so one item's copies overlap the
+// other lanes' work), and the call waits for the batch.
+static abs_status batched(abs_ctx *ctx, int32_t n_items, const abs_item *items, bool host) {
     if (!ctx) return ABS_ERR_INVALID_ARG;
     if (n_items < 0 || (n_items > 0 && !items)) return fail(ctx, ABS_ERR_INVALID_ARG, "n_items < 0 or items NULL");
     DeviceGuard g(ctx->device);
@@ -961,7 +966,8 @@ abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *i
     // validate every item and resolve its setup and triplet list before queuing anything
     std::vector<const Setup *> setups(n_items);
     std::vector<const int32_t *> ijks(n_items);
-    std::string key = "batch";
+    std::string key = host ? "batch-host" : "batch";
+    bool locked = true;
     for (int32_t i = 0; i < n_items; ++i) {
         abs_status st;
         const abs_item &it = items[i];
@@ -971,6 +977,11 @@ abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *i
         ijks[i] = it.d_ijk;
         if (estimate_args(c, *setups[i], it.n_vis, it.d_uv, 1, it.d_vis, it.n_trip, ijks[i]) != ABS_OK)
             return fail(ctx, ABS_ERR_INVALID_ARG, "item " + std::to_string(i) + ": " + c->last_error);
+        if (host) {
+            for (const void *p : {(const void *)it.d_uv, (const void *)it.d_vis, (const void *)it.d_B,
+                                  (const void *)it.d_count, (const void *)it.d_ellbar})
+                if (p && !page_locked(p)) locked = false;
+        }
         char k[256];
         snprintf(k, sizeof k, "|%p|%lld|%p|%p|%d|%p|%p|%p|%p", (const void *)setups[i], (long long)it.n_vis,
                  (const void *)it.d_uv, (const void *)it.d_vis, it.n_trip, (const void *)ijks[i], (void *)it.d_B,
@@ -980,17 +991,49 @@ abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *i
     char ks[48];
     snprintf(ks, sizeof ks, "|%p|%d", (const void *)ctx->stream, K);
     key += ks;
-    return graphed(ctx, key, [&]() {
+    // one item on context c: its estimate, staged through c's buffers for host items
+    auto run_item = [&](int32_t i) -> abs_status {
+        const abs_item &it = items[i];
+        abs_ctx *c = where(i);
+        const Setup &s = *setups[i];
+        if (!host)
+            return estimate_many(c, s, it.n_vis, it.d_uv, 1, it.d_vis, it.n_trip, ijks[i], it.d_B, it.d_count,
+                                 it.d_ellbar);
+        const size_t uvb = sizeof(float) * 2 * (size_t)it.n_vis;
+        float *d_uv = (float *)workspace(c, "host.uv", uvb);
+        float *d_vis = (float *)workspace(c, "host.vis", uvb);
+        double *d_B = (double *)workspace(c, "host.B", sizeof(double) * (size_t)std::max(it.n_trip, 1));
+        int64_t *d_count = (int64_t *)workspace(c, "host.count", sizeof(int64_t) * std::max(it.n_trip, 1));
+        double *d_ellbar = (double *)workspace(c, "host.ellbar", sizeof(double) * s.nb);
+        if (!d_uv || !d_vis || !d_B || !d_count || !d_ellbar) return fail(c, ABS_ERR_OOM, "host staging");
+        abs_status st;
+        if (locked) {   // the copies in go inside the estimate (the visibilities beside the plan)
+            st = estimate_many(c, s, it.n_vis, d_uv, 1, d_vis, it.n_trip, ijks[i], d_B, d_count, d_ellbar, it.d_uv,
+                               it.d_vis);
+        } else {
+            if (it.n_vis > 0) {
+                cudaMemcpyAsync(d_uv, it.d_uv, uvb, cudaMemcpyHostToDevice, c->stream);
+                cudaMemcpyAsync(d_vis, it.d_vis, uvb, cudaMemcpyHostToDevice, c->stream);
+            }
+            st = estimate_many(c, s, it.n_vis, d_uv, 1, d_vis, it.n_trip, ijks[i], d_B, d_count, d_ellbar);
+        }
+        if (st != ABS_OK) return st;
+        if (it.d_B && it.n_trip > 0)
+            cudaMemcpyAsync(it.d_B, d_B, sizeof(double) * it.n_trip, cudaMemcpyDeviceToHost, c->stream);
+        if (it.d_count && it.n_trip > 0)
+            cudaMemcpyAsync(it.d_count, d_count, sizeof(int64_t) * it.n_trip, cudaMemcpyDeviceToHost, c->stream);
+        if (it.d_ellbar) cudaMemcpyAsync(it.d_ellbar, d_ellbar, sizeof(double) * s.nb, cudaMemcpyDeviceToHost, c->stream);
+        return check_launch(c, "device to host copies");
+    };
+    auto eager = [&]() {
         if (K > 1) {   // fork: every lane starts after the work queued so far on ctx->stream
             cudaEventRecord(ctx->ev_fork, ctx->stream);
             for (int l = 0; l < K; ++l) cudaStreamWaitEvent(ctx->lanes[l]->stream, ctx->ev_fork, 0);
         }
         abs_status st = ABS_OK;
         for (int32_t i = 0; i < n_items && st == ABS_OK; ++i) {
-            const abs_item &it = items[i];
             abs_ctx *c = where(i);
-            st = estimate_many(c, *setups[i], it.n_vis, it.d_uv, 1, it.d_vis, it.n_trip, ijks[i], it.d_B,
-                               it.d_count, it.d_ellbar);
+            st = run_item(i);
             if (st != ABS_OK && c != ctx) ctx->last_error = "item " + std::to_string(i) + ": " + c->last_error;
         }
         if (K > 1) {   // join: ctx->stream waits for every lane
@@ -1000,7 +1043,19 @@ abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *i
             }
         }
         return st;
-    });
+    };
+    if (!host) return graphed(ctx, key, eager);
+    // pageable host buffers cannot be copied inside a captured graph
+    ABS_CHECK(locked ? graphed(ctx, key, eager) : eager());
+    return abs_sync(ctx);
+}
+
+abs_status abs_estimate_batched(abs_ctx *ctx, int32_t n_items, const abs_item *items) {
+    return batched(ctx, n_items, items, false);
+}
+
+abs_status abs_estimate_batched_host(abs_ctx *ctx, int32_t n_items, const abs_item *items) {
+    return batched(ctx, n_items, items, true);
 }
 
 abs_status abs_estimate_host(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis, const float *h_uv,

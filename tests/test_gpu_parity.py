@@ -123,87 +123,96 @@ def test_grid_parity_two_radix_passes(ctx):
     assert_grid_parity(G, W, M, _E, grid_abs_bound(wl.n_grid, wl.du, inp.uv, inp.vis))
 
 
+REPORT = {}
+
+
+def _report(key, **kw):
+    """Per-configuration parity figures (max relative error, the worst triplet and
+    its condition number); written to the JSON file named by ABS_PARITY_REPORT."""
+    import json
+    import os
+    REPORT[key] = kw
+    path = os.environ.get("ABS_PARITY_REPORT")
+    if path:
+        with open(path, "w") as fh:
+            json.dump(REPORT, fh, indent=1, default=float)
+    print(f"PARITY {key}: " + ", ".join(f"{k}={v}" for k, v in kw.items()))
+
+
+def full_oracle(wl, uv, vis):
+    """The oracle's sums and counts for every canonical triplet (FFT form in FP64,
+    pinned against brute force), its B and the fields for condition numbers."""
+    gr = oracle.grid(wl.n_grid, wl.du, uv, vis)
+    X, f = oracle.mean_grid(gr)
+    del gr
+    q = oracle.ring_q(wl.ell_edges, wl.du)
+    ijk = oracle.triplets(q)
+    N = oracle.min_fft_size(q, wl.n_grid)
+    S, T, T_raw, D, _ = oracle.fft_form_all(X, f, q, ijk, N)
+    assert np.max(np.abs(T_raw - T)) < 0.01, "oracle counts not integral"
+    B = oracle.normalise(S.astype(np.complex128), T)
+    return {"ijk": ijk, "S": S, "T": T, "B": B, "D": D, "N": N, "ellbar": oracle.ellbar(f, q, wl.du)}
+
+
+def assert_all_triplets(key, ref, gB, gT, gE, tol):
+    """Every triplet: counts bit-exact; B within tol relative where |B| >= 1e-3 max|B|,
+    within tol * 1e-3 max|B| elsewhere; NaN exactly where T = 0; mean l to 1e-12."""
+    assert np.array_equal(gT, ref["T"]), f"{key}: counts differ at {np.nonzero(gT != ref['T'])[0][:5]}"
+    assert np.array_equal(np.isnan(gB), ref["T"] == 0)
+    assert np.allclose(gE, ref["ellbar"], rtol=1e-12, equal_nan=True)
+    ok = ref["T"] > 0
+    Bref = ref["B"]
+    bmax = np.max(np.abs(Bref[ok]))
+    big = ok & (np.abs(Bref) >= 1e-3 * bmax)
+    rel = np.abs(gB[big] - Bref[big]) / np.abs(Bref[big])
+    small = ok & ~big
+    absr = np.abs(gB[small] - Bref[small]) / (1e-3 * bmax) if small.any() else np.zeros(1)
+    w = np.nonzero(big)[0][int(np.argmax(rel))]
+    i, j, k = (int(x) for x in ref["ijk"][w])
+    D = ref["D"]
+    t = D[i] * D[j] * D[k]
+    kappa = float(np.sum(np.abs(t)) / abs(np.sum(t)))
+    _report(key, n_trip=int(len(gB)), compared_big=int(big.sum()), max_rel=float(rel.max()),
+            max_small_rel_to_1e3max=float(absr.max()), worst=(i, j, k), kappa_worst=round(kappa, 2),
+            tol=tol)
+    assert rel.max() <= tol, f"{key}: max rel {rel.max():.3e} at {(i, j, k)} (kappa {kappa:.1f})"
+    assert absr.max() <= tol, f"{key}: small-|B| triplets off by {absr.max():.3e} of 1e-3 max|B|"
+
+
 @pytest.mark.gpu
-def test_precision_config_sampled(ctx):
+def test_precision_config_full(ctx):
     """The full-size precision workload (2048^2 grid, 4M visibilities, 64 rings,
-    ~15k triplets), run as abs_estimate runs it, FP32 and split-BF16, checked
-    on sampled triplets the oracle sums one by one (brute force over the
-    rings' cells: the ten with the fewest cell pairs, ten more spread over
-    the list), and on the mean l of every ring."""
+    15,221 triplets, N = 576), run as abs_estimate runs it, FP32 and split-BF16,
+    against the oracle on every triplet."""
     inp = inputs(2)
     wl = inp.wl
     uv, vis = to_dev(inp.uv), to_dev(synth.vis_as_float2(inp.vis))
-    res = {}
-    for prec in (absmod.ABS_FP32, absmod.ABS_SPLIT_BF16):
+    ref = full_oracle(wl, inp.uv, inp.vis)
+    for prec, tol, name in ((absmod.ABS_FP32, SUM_TOL, "fp32"), (absmod.ABS_SPLIT_BF16, 3e-4, "split_bf16")):
         cfg = absmod.Config.from_workload(wl, precision=prec)
         B, T, E, ijk = absmod.estimate(cfg, uv, vis, ctx)
         ctx.sync()
-        res[prec] = (B.cpu().numpy(), T.cpu().numpy(), E.cpu().numpy(), ijk)
-    gr = oracle.grid(wl.n_grid, wl.du, inp.uv, inp.vis)
-    X, f = oracle.mean_grid(gr)
-    q = oracle.ring_q(wl.ell_edges, wl.du)
-    assert np.allclose(res[absmod.ABS_FP32][2], oracle.ellbar(f, q, wl.du), rtol=1e-12, equal_nan=True)
-    ijk = res[absmod.ABS_FP32][3]
-    r2 = (lambda k: np.where(k > wl.n_grid // 2, k - wl.n_grid, k))(np.arange(wl.n_grid))
-    rr = r2[None, :].astype(np.int64) ** 2 + r2[:, None].astype(np.int64) ** 2
-    cells = np.array([((f > 0) & (rr >= q[m]) & (rr < q[m + 1])).sum() for m in range(len(q) - 1)])
-    cost = cells[ijk[:, 0]].astype(np.int64) * cells[ijk[:, 1]]
-    order = np.argsort(cost, kind="stable")
-    sel = [int(t) for t in order[:10]]
-    for p in np.linspace(10, len(order) - 1, 16).astype(int):
-        if cost[order[p]] < 5e6:
-            sel.append(int(order[p]))
-    Bmax = np.nanmax(np.abs(res[absmod.ABS_FP32][0]))
-    for t in sel:
-        i, j, k = (int(x) for x in ijk[t])
-        S, _, Tt = oracle.triple_one(X, f, q, i, j, k)
-        Bref = oracle.normalise(np.array([S]), np.array([Tt]))[0]
-        for prec, tol in ((absmod.ABS_FP32, SUM_TOL), (absmod.ABS_SPLIT_BF16, 3e-4)):
-            Bg, Tg = res[prec][0][t], res[prec][1][t]
-            assert Tg == Tt, (i, j, k, Tg, Tt)
-            if Tt == 0:
-                assert np.isnan(Bg)
-            else:
-                assert abs(Bg - Bref) <= tol * max(abs(Bref), 1e-3 * Bmax), (prec, i, j, k, Bg, Bref)
-
-
-def _sampled_triplets(wl, f, q, ijk, n_cheap=10, n_spread=16, n_empty=2, max_pairs=5e6):
-    """Triplets the oracle can sum one by one: those with the fewest filled
-    cell pairs (a few empty ones first), and some spread over the list."""
-    n = wl.n_grid
-    r2 = np.where(np.arange(n) > n // 2, np.arange(n) - n, np.arange(n)).astype(np.int64)
-    rr = r2[None, :] ** 2 + r2[:, None] ** 2
-    cells = np.array([((f > 0) & (rr >= q[m]) & (rr < q[m + 1])).sum() for m in range(len(q) - 1)])
-    cost = cells[ijk[:, 0]].astype(np.int64) * cells[ijk[:, 1]] * (cells[ijk[:, 2]] > 0)
-    order = np.argsort(cost, kind="stable")
-    empty = [int(t) for t in order[:n_empty] if cost[t] == 0]
-    live = order[cost[order] > 0]
-    sel = empty + [int(t) for t in live[:n_cheap]]
-    for p in np.linspace(n_cheap, len(live) - 1, n_spread).astype(int):
-        if cost[live[p]] < max_pairs:
-            sel.append(int(live[p]))
-    return sel
+        assert np.array_equal(ijk, ref["ijk"])
+        assert_all_triplets(f"precision-2048sq/{name}", ref, B.cpu().numpy(), T.cpu().numpy(), E.cpu().numpy(),
+                            tol)
 
 
 @pytest.mark.gpu
-def test_channels_config_sampled(ctx):
+def test_channels_config_full(ctx):
     """The multi-channel workload at full size (4096^2 grid, 1e7 visibilities
-    per channel, 128 rings, ~109k triplets, N = 1080, split-BF16): four
+    per channel, 128 rings, 109,157 triplets, N = 1080, split-BF16): four
     channels in one abs_estimate_batched call equal abs_estimate channel by
-    channel; the first and last channel against the oracle on sampled
-    triplets (brute force per triplet; counts exact) and on the mean l of
-    every ring, the first channel also through the FP32 path."""
+    channel; the first and last channel against the oracle on every triplet,
+    the first also through the FP32 path."""
     wl = synth.workload(4)
     cfg = absmod.Config.from_workload(wl)
     assert cfg.precision == absmod.ABS_SPLIT_BF16
     ijk = absmod.abs_triplets(cfg)
     nt = len(ijk)
     chans = (0, 11, 20, 31)
-    items, host = [], {}
+    items = []
     for ch in chans:
         inp = synth.channel_inputs(ch, wl=wl)
-        if ch in (0, 31):
-            host[ch] = inp
         outs = (torch.full((nt,), -1.0, dtype=torch.float64, device=dev()),
                 torch.full((nt,), -1, dtype=torch.int64, device=dev()),
                 torch.full((cfg.n_bins,), -1.0, dtype=torch.float64, device=dev()))
@@ -229,30 +238,52 @@ def test_channels_config_sampled(ctx):
         ok = ~np.isnan(rB)
         assert ok.sum() > nt // 2
         assert np.allclose(gB[ok], rB[ok], rtol=1e-9, atol=1e-12 * np.abs(rB[ok]).max())
-        res[ch] = {absmod.ABS_SPLIT_BF16: (gB, gT, gE)}
-    res[0][absmod.ABS_FP32] = (B32.cpu().numpy(), T32.cpu().numpy(), E32.cpu().numpy())
-    q = oracle.ring_q(wl.ell_edges, wl.du)
-    for ch, inp in host.items():
-        gr = oracle.grid(wl.n_grid, wl.du, inp.uv, inp.vis)
-        X, f = oracle.mean_grid(gr)
-        del gr
-        el = oracle.ellbar(f, q, wl.du)
-        sel = _sampled_triplets(wl, f, q, ijk)
-        assert len(sel) >= 20
-        Bmax = np.nanmax(np.abs(res[ch][absmod.ABS_SPLIT_BF16][0]))
-        for t in sel:
-            i, j, k = (int(x) for x in ijk[t])
-            S, _, Tt = oracle.triple_one(X, f, q, i, j, k)
-            Bref = oracle.normalise(np.array([S]), np.array([Tt]))[0]
-            for prec, (gB, gT, gE) in res[ch].items():
-                tol = SUM_TOL if prec == absmod.ABS_FP32 else 3e-4
-                assert np.allclose(gE, el, rtol=1e-12, equal_nan=True)
-                assert gT[t] == Tt, (ch, prec, i, j, k, gT[t], Tt)
-                if Tt == 0:
-                    assert np.isnan(gB[t])
-                else:
-                    assert abs(gB[t] - Bref) <= tol * max(abs(Bref), 1e-3 * Bmax), (ch, prec, i, j, k,
-                                                                                      gB[t], Bref)
+        res[ch] = (gB, gT, gE)
+    del items, single
+    for ch in (0, 31):
+        inp = synth.channel_inputs(ch, wl=wl)
+        ref = full_oracle(wl, inp.uv, inp.vis)
+        assert np.array_equal(ijk, ref["ijk"])
+        assert_all_triplets(f"channels-4096sq/ch{ch}/split_bf16", ref, *res[ch], 3e-4)
+        if ch == 0:
+            assert_all_triplets("channels-4096sq/ch0/fp32", ref, B32.cpu().numpy(), T32.cpu().numpy(),
+                                E32.cpu().numpy(), SUM_TOL)
+        del ref
+
+
+@pytest.mark.gpu
+def test_uneven_batch_largest_items_full(ctx):
+    """The largest items of the seeded uneven batch (1024^2 grids with at least
+    40 rings, N = 576), in one abs_estimate_batched call with smaller items
+    around them, against the oracle on every triplet (split-BF16)."""
+    rng = np.random.default_rng(2412)
+    big, small = [], []
+    for i in range(256):
+        w = synth.batch_item(rng, i)
+        if w.n_grid == 1024 and w.n_bins >= 40 and len(big) < 3:
+            big.append((i, w))
+        elif w.n_grid < 1024 and len(small) < 3:
+            small.append((i, w))
+        if len(big) == 3 and len(small) == 3:
+            break
+    assert len(big) == 3
+    items, host = [], []
+    for i, w in big + small:
+        inp = synth.make_inputs(3, i, wl=w)
+        cfg = absmod.Config.from_workload(inp.wl)
+        nt = len(absmod.abs_triplets(cfg))
+        items.append((cfg, to_dev(inp.uv), to_dev(synth.vis_as_float2(inp.vis)), nt, None,
+                      torch.full((nt,), -1.0, dtype=torch.float64, device=dev()),
+                      torch.full((nt,), -1, dtype=torch.int64, device=dev()),
+                      torch.full((cfg.n_bins,), -1.0, dtype=torch.float64, device=dev())))
+        host.append(inp)
+    ctx.abs_estimate_batched(items)
+    ctx.sync()
+    for (i, w), it, inp in zip(big, items, host):
+        ref = full_oracle(inp.wl, inp.uv, inp.vis)
+        assert ref["N"] == absmod.abs_fft_size(it[0])
+        assert_all_triplets(f"uneven-batch/item{i}-{w.n_grid}sq-{w.n_bins}rings/split_bf16", ref,
+                            *(o.cpu().numpy() for o in it[5:]), 3e-4)
 
 
 def test_grid_dense_cells(ctx):
@@ -727,6 +758,64 @@ def test_autotuner_split_bf16():
                 assert np.allclose(gBn[m], rB[m], rtol=1e-9, atol=1e-12 * np.abs(rB[m]).max())
     finally:
         c.close()
+
+
+@pytest.mark.gpu
+def test_estimate_batched_host_matches_device():
+    """abs_estimate_batched_host (host buffers in and out, staged per lane) gives what
+    abs_estimate_batched gives on device copies of the same inputs: pinned buffers
+    (the graphed path over four lanes: eager, captured, replayed) and pageable ones."""
+    absbuild.build()
+    st = torch.cuda.Stream(dev())
+    ctx = absmod.Context(0, st)
+    try:
+        with torch.cuda.stream(st):
+            _batched_host_case(ctx)
+    finally:
+        ctx.close()
+
+
+def _batched_host_case(ctx):
+    rng = np.random.default_rng(17)
+    wls = [synth.workload(0)] + [synth.batch_item(rng, i) for i in range(3)]
+    host, dev_items = [], []
+    for k, wl in enumerate(wls):
+        inp = synth.make_inputs(0 if k == 0 else 3, k, wl=wl, n_vis=None if k == 0 else 30000)
+        cfg = absmod.Config.from_workload(inp.wl)
+        nt = len(absmod.abs_triplets(cfg))
+        uv, vis = inp.uv, synth.vis_as_float2(inp.vis)
+        dev_items.append((cfg, to_dev(uv), to_dev(vis), nt, None,
+                          torch.empty(nt, dtype=torch.float64, device=dev()),
+                          torch.empty(nt, dtype=torch.int64, device=dev()),
+                          torch.empty(cfg.n_bins, dtype=torch.float64, device=dev())))
+        host.append((cfg, uv, vis, nt))
+    ctx.abs_estimate_batched(dev_items)
+    ctx.sync()
+    want = [tuple(o.cpu().numpy() for o in it[5:]) for it in dev_items]
+    for pinned in (True, False):
+        items = []
+        for cfg, uv, vis, nt in host:
+            if pinned:
+                u, v = torch.from_numpy(uv).pin_memory(), torch.from_numpy(vis).pin_memory()
+                outs = (torch.full((nt,), -1.0, dtype=torch.float64).pin_memory(),
+                        torch.full((nt,), -1, dtype=torch.int64).pin_memory(),
+                        torch.full((cfg.n_bins,), -1.0, dtype=torch.float64).pin_memory())
+            else:
+                u, v = uv.copy(), vis.copy()
+                outs = (np.full(nt, -1.0), np.full(nt, -1, np.int64), np.full(cfg.n_bins, -1.0))
+            items.append((cfg, u, v, nt, None) + outs)
+        for call in range(3 if pinned else 1):
+            for it in items:
+                for o in it[5:]:
+                    o.fill(-7) if isinstance(o, np.ndarray) else o.fill_(-7)
+            ctx.abs_estimate_batched_host(items)
+            for it, (wB, wT, wE) in zip(items, want):
+                gB, gT, gE = (np.asarray(o) if isinstance(o, np.ndarray) else o.numpy() for o in it[5:])
+                assert np.array_equal(gT, wT), (pinned, call)
+                assert np.array_equal(np.isnan(gB), np.isnan(wB))
+                m = ~np.isnan(wB)
+                assert np.allclose(gB[m], wB[m], rtol=1e-9, atol=1e-12 * np.abs(wB[m]).max()), (pinned, call)
+                assert np.allclose(gE, wE, rtol=1e-12, equal_nan=True)
 
 
 @pytest.mark.gpu

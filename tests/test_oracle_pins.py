@@ -340,6 +340,31 @@ def test_fft_identity_and_aliasing():
     assert np.sum(T_al != est.T) > 0
 
 
+def test_fft_form_all_matches_bruteforce():
+    # The matrix-product route of fft_form_all is the same Eq. estimator_t sums:
+    # against the brute-force closed-triangle sums of the tiny workload at the
+    # smallest admissible N and at a larger one (results independent of N once
+    # N >= 3R+1), sums to rounding of sum |X1 X2 X3|, counts exact; and entry
+    # for entry against the per-triplet fft_form.  Triplets are taken in a
+    # shuffled subset too, so that the (j, i, k) bookkeeping cannot hide behind
+    # the canonical order (the matrix shapes change, so the sums agree to
+    # rounding, the counts exactly).
+    inp = synth.make_inputs(0)
+    wl = inp.wl
+    est = oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, inp.uv, inp.vis)
+    for N in (90, 128):
+        S, T, T_raw, D, I = oracle.fft_form_all(est.X, est.filled, est.q, est.ijk, N)
+        assert np.max(np.abs(S - est.S.real) / np.maximum(est.absum, 1e-300)) < 1e-12
+        assert np.array_equal(T, est.T)
+        assert np.max(np.abs(T_raw - est.T)) < 1e-6
+    S1, T1, _ = oracle.fft_form(est.X, est.filled, est.q, est.ijk, 90)
+    S, T, _, D, I = oracle.fft_form_all(est.X, est.filled, est.q, est.ijk, 90)
+    assert np.allclose(S, S1, rtol=1e-12, atol=1e-12 * np.abs(S1).max()) and np.array_equal(T, T1)
+    perm = np.random.default_rng(3).permutation(len(est.ijk))[:40]
+    Sp, Tp, _, _, _ = oracle.fft_form_all(None, None, None, est.ijk[perm], 90, fields=(D, I))
+    assert np.allclose(Sp, S[perm], rtol=1e-12, atol=1e-12 * np.abs(S).max()) and np.array_equal(Tp, T[perm])
+
+
 def test_constant_visibilities_give_s_cubed():
     # V = s (real) everywhere -> every filled X_g = s (the gridded mean of a constant,
     # mirror included) -> B = s^3 on every triplet with T > 0, whatever the gridding
