@@ -53,7 +53,7 @@ UNIT = "estimates/s"
 KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "grid_mask": 1, "ring_lists": 2,
                      "count_items": 1, "count_pairs": 2, "count_gather": 1, "ellbar": 2,
                      "fft_rows": 1, "fft_cols": 1, "triple_fp32": 1, "triple_reduce": 1,
-                     "normalise": 1, "check_triplets": 1, "tc_rows": 1, "triple_tc": 1}
+                     "normalise": 1, "check_triplets": 1, "tc_split": 1, "triple_tc": 1, "tc_reduce": 2}
 
 
 def plan_kernels(n_grid, radius):
@@ -475,10 +475,13 @@ def run_reference(args):
 # ----------------------------------------------------------------------------- our arm
 
 
-def timed_calls(fn, steps, stream, torch, dev):
-    """Device milliseconds of `steps` calls of fn, each bracketed by CUDA events on `stream`."""
+def timed_calls(fn, steps, stream, torch, dev, before=None):
+    """Device milliseconds of `steps` calls of fn, each bracketed by CUDA events on `stream`
+    (before(), if given, runs ahead of each start event: an L2 flush)."""
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for k in range(steps):
+        if before:
+            before()
         ev[k][0].record(stream)
         fn()
         ev[k][1].record(stream)
@@ -516,13 +519,9 @@ def mwa_extras(m, synth, ctx, torch, dev, stream, steps, rank):
             ctx.abs_estimate(cfg, uv, vis, nt, None, B, T, E)
         ctx.sync()
 
-        def one():
-            flush.fill_(1.0)
-            ctx.abs_estimate(cfg, uv, vis, nt, None, B, T, E)
-        # the flush is inside the events; time it alone and take it out
-        tf = timed_calls(lambda: flush.fill_(1.0), steps, stream, torch, dev)
-        t = timed_calls(one, steps, stream, torch, dev)
-        out[name] = {"value": steps / ((sum(t) - sum(tf)) * 1e-3), "unit": UNIT}
+        t = timed_calls(lambda: ctx.abs_estimate(cfg, uv, vis, nt, None, B, T, E), steps, stream, torch, dev,
+                        before=lambda: flush.fill_(1.0))
+        out[name] = {"value": steps / (sum(t) * 1e-3), "unit": UNIT}
         if prec == m.ABS_FP32:
             huv, hvis = torch.from_numpy(inp.uv).pin_memory(), torch.from_numpy(synth.vis_as_float2(inp.vis)).pin_memory()
             hB = torch.empty(nt, dtype=torch.float64).pin_memory()

@@ -49,7 +49,9 @@ struct Setup {
     // a property of the ring geometry, computed on first use
     unsigned long long *d_full_counts = nullptr;
     bool full_counts_ready = false;
-    int tc_groups = -1;           // split-BF16 tile groups of the canonical list (-1: not worked out)
+    // the split-BF16 kernel's tiling of the canonical list, made on first use (type
+    // known to triple_tc.cu; its deleter frees the device copies)
+    std::shared_ptr<void> tc_plan;
     std::string key;              // the configuration's key (setups, tuned shapes)
 };
 
@@ -104,7 +106,8 @@ struct abs_ctx {
     // first eager call, by configuration key; kept by the root context (lanes share it)
     bool autotune = true;
     int32_t fail_allocs = 0;         // test hook: this many workspace allocations fail next
-    struct TcShape { int kc = 0; bool grouped = false; bool measured = false; };
+    // budget: accumulator columns per set; waves: work items per CTA (pixel ranges x sets / SMs)
+    struct TcShape { int kc = 0; bool grouped = false; bool measured = false; int budget = 0; int waves = 0; };
     std::map<std::string, TcShape> tc_shapes;
     std::map<std::string, std::pair<int, int>> fft_shapes;   // lines per CTA: column pass, row pass
     std::vector<abs_ctx *> lanes;

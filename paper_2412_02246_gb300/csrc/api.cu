@@ -285,6 +285,7 @@ static void free_setup(Setup &s) {
     cudaFree(s.d_Rm);
     cudaFree(s.d_full_counts);
     s.d_full_counts = nullptr;
+    s.tc_plan.reset();
     s.full_counts_ready = false;
     s.d_q = nullptr;
     s.d_lat_off = nullptr;

@@ -1,56 +1,58 @@
-// Stage 3, precision form: triple sums as a split-BF16 contraction on the
-// 5th-generation tensor cores (tcgen05), Eq. estimator_t numerator.
+// Stage 3, precision form: the numerator of Eq. estimator_t as a split-BF16
+// contraction on the 5th-generation tensor cores (tcgen05), middle-ring major.
 //
-// C[r, k] = sum_p A[r, p] B[k, p],  r = (i, j) row of the triplet list,
-//   A[r, p] = D_i(p) D_j(p),  B[k, p] = D_k(p),
-// and S_ijk = N^-2 C[(i,j), k].  Each FP32 operand x is split into
-// x_hi = bf16(x) and x_lo = bf16(x - x_hi) (x - x_hi is exact in FP32, so the
-// pair carries 16 significant bits), and three BF16 products are accumulated
-// in FP32 in tensor memory: C = Ah Bh^T + Ah Bl^T + Al Bh^T (the Al Bl^T term
-// is below FP32 resolution of the result).  Bh and Bl are stacked into one
-// operand [Bh; Bl], so one MMA gives Ah Bh^T and Ah Bl^T side by side and Ah
-// is read from shared memory once per K-step; the three FP32 accumulators
-// are added in the epilogue.
+// Rows r = (j, k), a pair of rings j <= k that closes a triangle with some
+// ring i <= j, and columns i:
+//   C[r][i] = sum_p A[r][p] B[i][p],  A[r][p] = D_j(p) D_k(p),  B[i][p] = D_i(p),
+// so that S_ijk = N^-2 C[(j, k)][i].  B is the plain fields, the same for every
+// row, and A the only operand that has to be formed.  Each FP32 operand x is
+// split into x_hi = bf16(x) and x_lo = bf16(x - x_hi) (x - x_hi is exact in
+// FP32, so the pair carries 16 significant bits) and the three products
+// Ah Bh + Ah Bl + Al Bh accumulate into one FP32 accumulator in tensor memory
+// (Al Bl is below the FP32 resolution of the sum).
 //
-// Rows are ordered by j (then i) and cut into tiles of 128.  A row (i, j)
-// only meets the rings k in [j, k_max(i, j)] (the triangle condition), so a
-// tile of neighbouring j meets a narrow band of rings: the tile's MMA N is
-// that band rounded up to 16, not every ring.
+// Layout.  The fields are split once per estimate (k_split_fields) into three
+// planes with a row pitch of P_pad = P rounded up to 64 pixels (zeros past P):
+// BF16 hi, BF16 lo and an FP32 copy.  Rows (j, k) are taken in (j, k) order and
+// cut into tiles of 128; a tile's MMA N covers the rings i of all its rows
+// (from the lowest i rounded down to 8, rounded up to 16 columns); inside a
+// tile the rows are ordered by (k, j), so that a warp's 32 rows read few
+// distinct rings when forming A.  Consecutive tiles form a set whose
+// accumulators fit tensor memory beside two A buffers; a work item is one set
+// over one range of pixels, and the items (sets x pixel ranges) are dealt to
+// a persistent grid of one CTA per SM, ranges outermost, so that the sets that
+// read the same pixels run at about the same time and share them in L2.
 //
-// Tiles are grouped so that a group's accumulators (3 x band columns per
-// tile) fit the 512 columns of tensor memory.  One CTA owns a group of row
-// tiles and a range of pixels, so each field chunk is brought in once for
-// every tile of the group.  The range is streamed in chunks of 64-128 pixels by
-// three roles through two rings of shared-memory stages, one of field chunks
-// (deep, so loads run well ahead) and one of operand tiles (one step per
-// chunk and tile):
-//   loader warp    copies the chunk's fields, all rings x 68 pixels (the
-//                  padded row keeps the producers' reads off one bank), with
-//                  one 2-D TMA tensor copy (zero fill past the last pixel)
-//                  into a field stage, completion counted on f_full,
-//   producer warps form the four BF16 operand tiles (A = D_i D_j and the
-//                  band of B = D_k, hi and lo) in the canonical K-major
-//                  no-swizzle layout (8-row x 16-byte core matrices, K-adjacent
-//                  ones 128 B apart, 8-row groups 256 B apart, one 16-column K
-//                  slab after the other) in an operand stage, arrive on
-//                  ab_full and release the field stage (f_empty),
-//   MMA warp       issues the MMAs of a step (per 16-pixel K-step Ah [Bh; Bl]
-//                  and Al Bh, M = 128, N = 2 band and band, K = 16) into the
-//                  tile's accumulator columns and commits them to ab_empty,
-//                  which frees the operand stage.
-// At the end the accumulator is read back with tcgen05.ld and each row writes
-// the partial sums of its triplets; a second kernel adds the pixel ranges in
-// FP64 in a fixed order.
+// Per 64-pixel chunk, three roles and three kinds of mbarrier:
+//   loader (warp 0)    TMA copies of the chunk into a shared-memory stage: the
+//                      set's window of rings of the hi and lo planes (the MMA
+//                      operand B, 128-byte swizzled K-major: 64 BF16 pixels a
+//                      row) and the window of rings its rows form A from (FP32,
+//                      two 32-pixel boxes, 128-byte swizzled), in 16-row boxes,
+//                      counted on full[s];
+//   formers (warps 2-9) per tile of the set: thread = one row (its tensor-memory
+//                      lane) and 32 of the 64 pixels; A = D_j D_k in FP32, split,
+//                      packed in BF16 pairs and stored to an A buffer in tensor
+//                      memory (tcgen05.st), then a_full[buf];
+//   MMA issuer (warp 1) per tile: 4 K-steps x 3 MMAs (A from tensor memory,
+//                      B from the stage), M = 128, N = the tile's ring columns,
+//                      committed to a_empty[buf] (the A buffer is free again),
+//                      after the chunk's last tile to empty[s] (the stage is free),
+//                      after the item's last chunk to acc_full.
+// The formers then read the accumulators back (tcgen05.ld) and write them,
+// column-major by tile (lanes contiguous), to the item's pixel range of the
+// partial-sum array, and release the accumulators (acc_empty).  A second
+// kernel adds the pixel ranges in FP64 in a fixed order and gathers each
+// triplet's entry.
 //
-// Every mbarrier wait is bounded; on timeout the kernel latches an error,
-// every role leaves its loop, the CTA waits (bounded) for its own copies and
-// MMAs in flight, frees its tensor memory and returns.  Where the fields
-// cannot be described as a TMA tensor (rows not 16-byte aligned), the loader
-// warp copies them with plain loads.
-#include <cuda.h>
-#include <cudaTypedefs.h>
+// Every mbarrier wait is bounded: on timeout the role sets a shared abort flag
+// and leaves; the CTA then waits (bounded) for its copies and MMAs in flight,
+// latches DERR_TIMEOUT, frees its tensor memory and returns.
+
+
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <map>
 
 #include "abs_internal.cuh"
@@ -58,68 +60,112 @@
 namespace absk {
 namespace {
 
-constexpr int TM = 128;          // rows per tile (MMA M)
-constexpr int NPW = 16;          // producer warps
-constexpr int LOADER = NPW, ISSUER = NPW + 1;   // the two control warps
-constexpr int NT = (NPW + 2) * 32;
-
-// The chunk: KC pixels (KC / 16 MMA K-steps), the widest of 128, 96, 64 whose
-// stages fit shared memory (wider chunks spread the per-step costs, barrier
-// round trips and the MMA commit, over more work).
-template <int KC>
-struct Chunk {
-    static_assert(KC % 32 == 0 && KC <= 128, "whole 16-pixel K-steps; 8-pixel groups; TMA box <= 256");
-    static constexpr int GPR = KC / 8;                       // 8-pixel groups per row of a chunk
-    static constexpr int KA = TM * GPR / (NPW * 32);         // A units (row, 8 pixels) per producer thread
-    static constexpr int KB = 256 * GPR / (NPW * 32);        // B units per producer thread at most (band <= 256)
-    static constexpr int FS = KC + 4;   // field row in a stage (floats, a multiple of 4): the TMA box width
-    static_assert(KA * NPW * 32 == TM * GPR, "A units split evenly over the producers");
-};
-constexpr int MAX_AB = 3, MAX_F = 8;   // operand and field stages
-constexpr int GMAX = 10;         // row tiles per group (3 x 16 accumulator columns each at least)
+constexpr int TM = 128;              // rows per tile (MMA M)
+constexpr int KC = 64;               // pixels per chunk (4 MMA K-steps of 16)
+#ifndef ABS_TC_FORMERS
+#define ABS_TC_FORMERS 8
+#endif
+constexpr int NFORM = ABS_TC_FORMERS;   // forming / epilogue warps (8 or 16)
+constexpr int FQ = NFORM / 4;           // forming warps per tensor-memory lane quadrant
+constexpr int FPX = KC / FQ;            // pixels of a chunk per forming thread
+constexpr int NT = (NFORM + 2) * 32; // threads per CTA
+// registers per thread: the register file is split over the SM's four schedulers (16,384
+// each) and warps are dealt to them in turn, so the scheduler with the most warps
+// (3 of 10, or 5 of 18) bounds it, in steps of 8
+#define TC_MAXREG (NFORM == 8 ? 168 : 96)
+constexpr int MAX_TILES = 16;        // tiles per set
+constexpr int MAX_STAGES = 8;
 constexpr int TMEM_COLS = 512;
-constexpr unsigned FULL = 0xffffffffu;
-constexpr uint32_t WAIT_LIMIT = 1u << 22;
+constexpr int A_COLS = 64;           // one A buffer: 32 columns of hi pairs, 32 of lo pairs
+#ifndef ABS_TC_ABUF
+#define ABS_TC_ABUF 4
+#endif
+constexpr int NABUF = ABS_TC_ABUF;   // A buffers: formers run up to NABUF - 1 tiles ahead of the MMAs
+constexpr int BOX_ROWS = 16;         // rows per TMA box (window sizes are multiples of it)
+#ifndef ABS_TC_DRAIN
+#define ABS_TC_DRAIN 8
+#endif
+constexpr int DRAIN = ABS_TC_DRAIN;  // chunks accumulated in tensor memory before the formers drain them
+#ifndef ABS_TC_SET_COLS
+#define ABS_TC_SET_COLS 128
+#endif
+// accumulator columns of a set: two accumulation regions beside the A buffers fit tensor
+// memory up to 192; the forming threads' long accumulators (set columns / (4 FQ) each)
+// bound it by registers
+constexpr int MAX_SET_COLS = ABS_TC_SET_COLS;
+static_assert(NABUF * A_COLS + 2 * MAX_SET_COLS <= TMEM_COLS, "A buffers and two regions fit tensor memory");
+constexpr int MAX_TILE_N = 128;      // MMA N of a tile (wider column ranges are cut into several tiles)
+constexpr int MAXBLK = (MAX_SET_COLS / 8 + FQ - 1) / FQ;     // drain blocks of 8 columns per forming thread
+constexpr int MAXSLOT = 8 * MAXBLK;  // long accumulators per forming thread
+// A wait suspends the warp for up to WAIT_HINT_NS per try (it resumes as soon as the
+// phase completes, so waiting warps take no issue slots), at most WAIT_LIMIT tries.
+constexpr uint32_t WAIT_HINT_NS = 100000;
+constexpr uint32_t WAIT_LIMIT = 1u << 15;
 
-struct TcGeom {
-    int nb, NP;                  // rings, largest MMA N (rings rounded up to 16)
-    int tmem_cols;               // columns allocated (the group's accumulators fit them)
-    int64_t P;                   // pixels
-    int64_t per_split;           // pixels per CTA (multiple of the chunk)
-    int n_trip;
-    int sf, sa;                  // field and operand stages
-    int f_bytes, ab_bytes;       // one field stage [nb][KC + 4] floats; one operand stage [Ah][Al][Bh; Bl]
-    int a_bytes, b_bytes;        // one A tile (hi or lo); the stacked B tile (2 NP rows)
-    int tma;                     // fields by TMA tensor copy (else plain loads by the loader warp)
+struct TcParams {
+    int n_items;                 // sets x pixel ranges
+    int n_sets;
+    int64_t per_item;            // pixels of a range (a multiple of KC)
+    int64_t P_pad;               // pixels per plane row
+    int64_t dense;               // accumulator entries of one range (sum over tiles of 128 x N)
+    int stage_bytes;             // one shared-memory stage (the largest set's)
+    int n_stages;
+};
+
+// The split fields, chunk-blocked: [P_pad / 64][nbp][64] (nbp >= n_bins rings a block, zeros past
+// n_bins and past P).  BF16 rows are 128 bytes in the 128-byte swizzle of the MMA operand (16-byte
+// units XOR-permuted by ring & 7), FP32 rows 256 bytes permuted the same way, so that a set's window
+// of rings of one chunk is one contiguous bulk copy and lands in shared memory ready for use.
+struct TcPlanes {
+    const __nv_bfloat16 *hi, *lo;
+    const float *f32;
+    int nbp;
+};
+
+// Set descriptor: first tile, tiles, B window (first ring, rows), F window (first ring, rows).
+struct TcSet {
+    int tile0, ntiles;
+    int b_lo, b_n;
+    int f_lo, f_n;
+    int pad0, pad1;
+};
+
+// Tile descriptor: first column ring (multiple of 8), MMA N, offset in the dense accumulator.
+struct TcTile {
+    int i_lo, n;
+    int64_t acc_off;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Shared-memory matrix descriptor: start, leading (K) and stride (8-row group)
-// byte offsets, descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t make_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzle:
+// start address, leading byte offset 16 (unused by this layout), 8-row groups
+// 1024 bytes apart, descriptor version 1, layout SWIZZLE_128B.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
-    d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+    d |= (uint64_t)(16 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
     d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
     return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
 __host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t accumulate) {
+// D (tensor memory) += A (tensor memory) x B (shared-memory descriptor)^T.
+__device__ __forceinline__ void mma_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(tmem_d), "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+        ::"r"(tmem_d), "r"(tmem_a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -144,802 +190,776 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+        : "=r"(ok) : "r"(mbar), "r"(parity), "r"(WAIT_HINT_NS) : "memory");
     return ok != 0;
 }
 
-// Bounded wait for the phase of the given parity; false on timeout, or once
+// Bounded wait for the phase of the given parity; false on timeout or once
 // another role has given up (abort set).
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const volatile int *abort_flag) {
     for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
         if (mbar_try(mbar, parity)) return true;
-        if ((it & 255u) == 255u && *abort_flag) return false;
+        if (*abort_flag) return false;
     }
     return false;
 }
 
-// Bounded wait for work already in flight (copies, MMAs), whatever the abort flag says.
+// Bounded wait for work already in flight, whatever the abort flag says.
 __device__ __forceinline__ bool mbar_drain(uint32_t mbar, uint32_t parity) {
     for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
         if (mbar_try(mbar, parity)) return true;
     return false;
 }
 
-// 2-D tensor copy of the box at (x, y) into shared memory, counted on mbar.
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+// Bulk copy of `bytes` contiguous bytes from global into shared memory, counted on mbar.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+
+// Four FP32 values (16-byte unit u of 16) of ring m's 64-pixel row in an F window
+// starting at ring f_lo: rows are 256 bytes, units XOR-permuted by m & 7.
+__device__ __forceinline__ float4 ld_frow(const uint8_t *F, int m, int f_lo, int u) {
+    return *(const float4 *)(F + (m - f_lo) * 256 + ((u ^ (m & 7)) << 4));
+}
+
+// Eight consecutive tensor-memory columns of one lane (completion awaited separately).
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(ta));
+}
+
+// Eight packed BF16 pairs of one lane to consecutive tensor-memory columns.
+__device__ __forceinline__ void tmem_st(uint32_t ta, const uint32_t (&v)[8]) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
-        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(mbar) : "memory");
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n"
+        ::"r"(ta), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+        : "memory");
 }
 
-// Eight FP32 values (four pairs) as their BF16 hi parts and BF16 residuals,
-// stored as one 16-byte core-matrix row each.
-__device__ __forceinline__ void store_split8(uint8_t *hi_tile, uint8_t *lo_tile, int off, const float2 *v) {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const __nv_bfloat162 hb = __float22bfloat162_rn(v[e]);
-        const float2 hf = __bfloat1622float2(hb);
-        const float2 r = __ffma2_rn(hf, make_float2(-1.f, -1.f), v[e]);   // v - hi, exact in FP32
-        const __nv_bfloat162 lb = __float22bfloat162_rn(r);
-        h[e] = *(const uint32_t *)&hb;
-        l[e] = *(const uint32_t *)&lb;
-    }
-    *(uint4 *)(hi_tile + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *(uint4 *)(lo_tile + off) = make_uint4(l[0], l[1], l[2], l[3]);
+// A pair of FP32 values as BF16 hi parts and BF16 residuals, each packed (first value low).
+__device__ __forceinline__ void split2(float2 v, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __float22bfloat162_rn(v);
+    const float2 hf = __bfloat1622float2(h);
+    const float2 r = __ffma2_rn(hf, make_float2(-1.f, -1.f), v);   // v - hi, exact in FP32
+    const __nv_bfloat162 l = __float22bfloat162_rn(r);
+    hi = *(const uint32_t *)&h;
+    lo = *(const uint32_t *)&l;
 }
 
-// Byte offset of (row r, 8-column group g) of a K-major tile with rows8 8-row groups.
-__device__ __forceinline__ int core_off(int r, int g, int rows8) {
-    const int slab = g >> 1, cb = g & 1;
-    return slab * rows8 * 256 + (r >> 3) * 256 + cb * 128 + (r & 7) * 16;
-}
-
-// Eight consecutive field values at f (16-byte aligned), as four pairs.
-__device__ __forceinline__ void ld8(const float *f, float2 *v) {
-    const float4 a = *(const float4 *)f;
-    const float4 b = *(const float4 *)(f + 4);
-    v[0] = make_float2(a.x, a.y);
-    v[1] = make_float2(a.z, a.w);
-    v[2] = make_float2(b.x, b.y);
-    v[3] = make_float2(b.z, b.w);
-}
-
-// Zero the pixels of group g at or past `valid` (the end of the pixel range).
-__device__ __forceinline__ void mask_tail(float2 *v, int g, int valid) {
-    if (g * 8 + 8 <= valid) return;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        if (g * 8 + 2 * e >= valid) v[e].x = 0.f;
-        if (g * 8 + 2 * e + 1 >= valid) v[e].y = 0.f;
-    }
-}
-
-template <int KC>
-__global__ void __launch_bounds__(NT, 1) k_triple_tc(TcGeom G, const __grid_constant__ CUtensorMap fmap,
-                                                     const float *__restrict__ fields,
-                                                     const int4 *__restrict__ rows,
-                                                     const int2 *__restrict__ tiles,
-                                                     const int2 *__restrict__ groups,
-                                                     const int *__restrict__ ctl,
-                                                     const int32_t *__restrict__ ijk,
-                                                     double *__restrict__ partial,
+__global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
+                                                     const TcSet *__restrict__ sets,
+                                                     const TcTile *__restrict__ tiles,
+                                                     const short2 *__restrict__ rowjk,
+                                                     float *__restrict__ partial, int *__restrict__ next_item,
                                                      int32_t *__restrict__ err) {
-    constexpr int GPR = Chunk<KC>::GPR, KA = Chunk<KC>::KA, KB = Chunk<KC>::KB, FS = Chunk<KC>::FS;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t f_full[MAX_F], f_empty[MAX_F], ab_full[MAX_AB], ab_empty[MAX_AB];
-    // stages on a 1024-byte boundary (TMA destinations want 128; the launch adds 1 KB of slack)
-    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES], a_full[NABUF], a_empty[NABUF], d_full[2],
+        d_empty[2], fin;
     __shared__ uint32_t tmem_holder;
-    __shared__ int16_t rowi[GMAX][TM], rowj[GMAX][TM];
-    __shared__ int t_klo[GMAX], t_nb[GMAX], t_col[GMAX];
     __shared__ volatile int abort_s;
-    const int n_rows = ctl[0], n_groups = ctl[1];
-    if ((int)blockIdx.x >= n_groups) return;
+    __shared__ int item_s;
+    __shared__ TcSet set_s;
+    __shared__ int t_ilo[MAX_TILES], t_n[MAX_TILES], t_col[MAX_TILES], sum_n;
+    __shared__ int64_t t_off[MAX_TILES];
+    __shared__ short2 rows_s[MAX_TILES][TM];
+    __shared__ int blk_col[FQ][MAXBLK], n_blk[FQ];   // drain blocks of 8 columns per forming warp of a quadrant
+    __shared__ int64_t blk_out[FQ][MAXBLK];
+    // stages on a 1024-byte boundary (the 128-byte swizzle's atom); the launch adds 1 KB of slack
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int2 grp = groups[blockIdx.x];            // (first tile, tiles)
-    const int t0 = grp.x, NG = grp.y;
-    if (threadIdx.x < GMAX) {
-        const int t = threadIdx.x;
-        int lo = 0, w = 16;
-        if (t < NG) {
-            const int2 band = tiles[t0 + t];        // (first ring of the band, band width)
-            lo = band.x;
-            w = band.y;
-        }
-        t_klo[t] = lo;
-        t_nb[t] = w;
-    }
-    for (int e = threadIdx.x; e < GMAX * TM; e += blockDim.x) {
-        const int t = e / TM, rr = e - t * TM;
-        const int r = (t0 + t) * TM + rr;
-        int i = -1, j = -1;
-        if (t < NG && r < n_rows) {
-            const int4 R = rows[r];
-            i = R.x;
-            j = R.y;
-        }
-        rowi[t][rr] = (int16_t)i;
-        rowj[t][rr] = (int16_t)j;
-    }
-    __syncthreads();
     if (threadIdx.x == 0) {
         abort_s = 0;
-        int col = 0;
-        for (int t = 0; t < GMAX; ++t) {   // accumulator columns of each tile: [Ah Bh | Ah Bl | Al Bh]
-            t_col[t] = col;
-            if (t < NG) col += 3 * t_nb[t];
+        for (int s = 0; s < G.n_stages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
         }
-        for (int s = 0; s < G.sf; ++s) {
-            mbar_init(smem_u32(&f_full[s]), 1);
-            mbar_init(smem_u32(&f_empty[s]), NPW);
+        for (int b = 0; b < NABUF; ++b) {
+            mbar_init(smem_u32(&a_full[b]), NFORM);
+            mbar_init(smem_u32(&a_empty[b]), 1);
         }
-        for (int s = 0; s < G.sa; ++s) {
-            mbar_init(smem_u32(&ab_full[s]), NPW);
-            mbar_init(smem_u32(&ab_empty[s]), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&d_full[b]), 1);
+            mbar_init(smem_u32(&d_empty[b]), NFORM);
         }
+        mbar_init(smem_u32(&fin), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-    if (warp == ISSUER) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
-                     ::"r"(smem_u32(&tmem_holder)), "r"(G.tmem_cols));
+                     ::"r"(smem_u32(&tmem_holder)), "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = tmem_holder;
-    const int64_t p_begin = (int64_t)blockIdx.y * G.per_split;
-    const int64_t p_end = min(G.P, p_begin + G.per_split);
-    const int nchunks = (int)cdiv(p_end - p_begin, KC);
-    const int nsteps = nchunks * NG;                // step = chunk x tile
-    const int rows8_a = TM / 8;
-    uint8_t *fbase = smem, *abase = smem + (size_t)G.sf * G.f_bytes;
 
-    if (warp == LOADER) {
-        // ---------------- loader: a field chunk (every ring) per field stage
-        int issued = 0;
-        for (int c = 0; c < nchunks; ++c) {
-            const int s = c % G.sf, use = c / G.sf;
-            bool ok = true;
-            if (use > 0) {   // the producers are done with chunk c - sf
-                if (lane == 0) ok = mbar_wait(smem_u32(&f_empty[s]), (uint32_t)((use - 1) & 1), &abort_s);
-                ok = __shfl_sync(FULL, ok, 0);
-            }
-            if (!ok) {
-                abort_s = 1;
-                break;
-            }
-            float *F = (float *)(fbase + (size_t)s * G.f_bytes);
-            const int64_t pc = p_begin + (int64_t)c * KC;
-            if (G.tma) {
-                if (lane == 0) {
-                    mbar_arrive_tx(smem_u32(&f_full[s]), (uint32_t)(G.nb * FS * 4));
-                    tma_load_2d(smem_u32(F), &fmap, (int)pc, 0, smem_u32(&f_full[s]));
+    // role state that lives across items
+    int st = 0, su = 0;      // stage and its use (loader, formers and issuer walk the same sequence)
+    int ag = 0;              // A steps so far (buffer ag % NABUF, its use ag / NABUF)
+    int grp = 0;             // accumulation groups so far (region grp & 1, its use grp >> 1)
+    int issued = 0;          // stages the loader filled (for the drain)
+    float accl[MAXSLOT];     // formers: this thread's long accumulators (FP32, rounded to nearest)
+#pragma unroll
+    for (int x = 0; x < MAXSLOT; ++x) accl[x] = 0.f;
+    for (;;) {
+        // every thread is between items here, and no role writes the abort flag; the next
+        // item comes from the launch's work counter (items in pixel-range order, so the
+        // CTAs work on neighbouring ranges at any time and share them in L2)
+        __syncthreads();
+        if (abort_s) break;
+        if (threadIdx.x == 0) item_s = atomicAdd(next_item, 1);
+        __syncthreads();
+        const int e = item_s;
+        if (e >= G.n_items) break;
+        const int set_id = e % G.n_sets;
+        const int64_t p0 = (int64_t)(e / G.n_sets) * G.per_item;
+        const int nchunks = (int)(min(G.per_item, G.P_pad - p0) / KC);
+        // the set's tiles and rows
+        if (threadIdx.x == 0) set_s = sets[set_id];
+        __syncthreads();
+        const TcSet S = set_s;
+        if (threadIdx.x < S.ntiles) {
+            const TcTile T = tiles[S.tile0 + threadIdx.x];
+            t_ilo[threadIdx.x] = T.i_lo;
+            t_n[threadIdx.x] = T.n;
+            t_off[threadIdx.x] = T.acc_off;
+        }
+        for (int x = threadIdx.x; x < S.ntiles * TM; x += NT)
+            rows_s[x / TM][x % TM] = rowjk[(size_t)S.tile0 * TM + x];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // tile columns inside an accumulation region; drain blocks dealt round robin
+            int col = 0, b = 0;
+            for (int h = 0; h < FQ; ++h) n_blk[h] = 0;
+            for (int t = 0; t < S.ntiles; ++t) {
+                t_col[t] = col;
+                for (int c0 = 0; c0 < t_n[t]; c0 += 8, ++b) {
+                    const int h = b % FQ, k = n_blk[h]++;
+                    blk_col[h][k] = col + c0;
+                    blk_out[h][k] = t_off[t] + (int64_t)c0 * TM;
                 }
+                col += t_n[t];
+            }
+            sum_n = col;
+        }
+        __syncthreads();
+        const int b_bytes = S.b_n * 128;              // one plane of the B window
+        const int f_bytes = S.f_n * 256;              // the F window (FP32 rows)
+        const uint32_t tx_bytes = (uint32_t)(2 * b_bytes + f_bytes);
+        const int region_cols = sum_n;
+
+        if (warp == 0) {
+            // ---------------- loader
+            if (lane == 0) {
+                for (int c = 0; c < nchunks; ++c) {
+                    if (su > 0 && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((su - 1) & 1), &abort_s)) {
+                        abort_s = 1;
+                        break;
+                    }
+                    uint8_t *stage = smem + (size_t)st * G.stage_bytes;
+                    const size_t blk = ((size_t)(p0 / KC) + c) * PL.nbp;   // the chunk's block of rings
+                    const uint32_t fb = smem_u32(&full[st]);
+                    mbar_arrive_tx(fb, tx_bytes);
+                    bulk_g2s(smem_u32(stage), PL.hi + (blk + S.b_lo) * KC, (uint32_t)b_bytes, fb);
+                    bulk_g2s(smem_u32(stage + b_bytes), PL.lo + (blk + S.b_lo) * KC, (uint32_t)b_bytes, fb);
+                    bulk_g2s(smem_u32(stage + 2 * b_bytes), PL.f32 + (blk + S.f_lo) * KC, (uint32_t)f_bytes, fb);
+                    ++issued;
+                    if (++st == G.n_stages) {
+                        st = 0;
+                        ++su;
+                    }
+                }
+            }
+        } else if (warp == 1) {
+            // ---------------- MMA issue (one thread): groups of DRAIN chunks into alternating regions
+            if (lane == 0) {
+                for (int c = 0; c < nchunks && !abort_s; ++c) {
+                    const int gc = c % DRAIN;
+                    const uint32_t region = (uint32_t)(NABUF * A_COLS + (grp & 1) * region_cols);
+                    if (gc == 0 && grp >= 2) {   // the group before last in this region has been drained
+                        if (!mbar_wait(smem_u32(&d_empty[grp & 1]), (uint32_t)(((grp >> 1) - 1) & 1), &abort_s)) {
+                            abort_s = 1;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    }
+                    if (!mbar_wait(smem_u32(&full[st]), (uint32_t)(su & 1), &abort_s)) {
+                        abort_s = 1;
+                        break;
+                    }
+                    // the stage's B descriptors (hi, lo); a tile's rows and a K-step move only the
+                    // start-address field (16-byte units: 8 per ring row, 2 per 16 pixels)
+                    const uint32_t bh = smem_u32(smem + (size_t)st * G.stage_bytes);
+                    const uint64_t dh0 = desc_sw128(bh), dl0 = desc_sw128(bh + (uint32_t)b_bytes);
+                    bool step_ok = true;
+                    for (int t = 0; t < S.ntiles; ++t) {
+                        const int buf = ag % NABUF, use = ag / NABUF;
+                        if (!mbar_wait(smem_u32(&a_full[buf]), (uint32_t)(use & 1), &abort_s)) {
+                            step_ok = false;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                        const uint32_t idesc = make_idesc(TM, t_n[t]);
+                        const uint32_t acc = tmem + region + (uint32_t)t_col[t];
+                        const uint32_t a_hi = tmem + (uint32_t)(buf * A_COLS), a_lo = a_hi + 32;
+                        const uint64_t rows = (uint64_t)(t_ilo[t] - S.b_lo) * 8u;
+#pragma unroll
+                        for (int ks = 0; ks < KC / 16; ++ks) {
+                            const uint64_t dh = dh0 + rows + 2u * ks;
+                            const uint64_t dl = dl0 + rows + 2u * ks;
+                            mma_ts(acc, a_hi + 8u * ks, dh, idesc, (gc > 0 || ks > 0) ? 1u : 0u);
+                            mma_ts(acc, a_hi + 8u * ks, dl, idesc, 1u);
+                            mma_ts(acc, a_lo + 8u * ks, dh, idesc, 1u);
+                        }
+                        mma_commit(smem_u32(&a_empty[buf]));
+                        ++ag;
+                    }
+                    if (!step_ok) {
+                        abort_s = 1;
+                        break;
+                    }
+                    mma_commit(smem_u32(&empty[st]));
+                    if (++st == G.n_stages) {
+                        st = 0;
+                        ++su;
+                    }
+                    if (gc == DRAIN - 1 || c == nchunks - 1) {   // the group is complete: the formers drain it
+                        mma_commit(smem_u32(&d_full[grp & 1]));
+                        ++grp;
+                    }
+                }
+            }
+        } else {
+            // ---------------- formers; after the first chunk of each group they drain the group before
+            const int q = warp & 3;                   // tensor-memory lanes 32 q .. 32 q + 31
+            const int h = (warp - 2) >> 2;            // pixel part of the chunk (FPX pixels), drain blocks
+            const int row = 32 * q + lane;
+            const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+            const int nb_h = n_blk[h];
+            int gdrained = grp;                       // this item's first group
+            bool fail_f = false;
+            // chunk c is formed; after the first chunk of a group (and after the last chunk) the group
+            // before is drained: its accumulation region is added into accl and released
+            for (int c = 0; c <= nchunks && !fail_f; ++c) {
+                if (c < nchunks) {
+                    if (!mbar_wait(smem_u32(&full[st]), (uint32_t)(su & 1), &abort_s)) {
+                        fail_f = true;
+                        break;
+                    }
+                    // the F window, and this thread's first 16-byte unit (FPX pixels from h * FPX)
+                    const uint8_t *F = smem + (size_t)st * G.stage_bytes + 2 * b_bytes;
+                    const int cc0 = (h * FPX) / 4;
+                    for (int t = 0; t < S.ntiles; ++t) {
+                        const int buf = ag % NABUF, use = ag / NABUF;
+                        if (use > 0 &&
+                            !mbar_wait(smem_u32(&a_empty[buf]), (uint32_t)((use - 1) & 1), &abort_s)) {
+                            fail_f = true;
+                            break;
+                        }
+                        const short2 jk = rows_s[t][row];
+                        const uint32_t ta = lane_base + (uint32_t)(buf * A_COLS + (FPX / 2) * h);
+                        // 16 pixels at a time: products, hi / lo split, 8 packed pairs of each to tensor memory
+#pragma unroll
+                        for (int part = 0; part < FPX / 16; ++part) {
+                            uint32_t hi[8], lo[8];
+                            if (jk.x >= 0) {
+#pragma unroll
+                                for (int cc = 0; cc < 4; ++cc) {
+                                    const int c16 = cc0 + 4 * part + cc;
+                                    const float4 x = ld_frow(F, jk.x, S.f_lo, c16),
+                                                 y = ld_frow(F, jk.y, S.f_lo, c16);
+                                    split2(__fmul2_rn(make_float2(x.x, x.y), make_float2(y.x, y.y)), hi[2 * cc],
+                                           lo[2 * cc]);
+                                    split2(__fmul2_rn(make_float2(x.z, x.w), make_float2(y.z, y.w)), hi[2 * cc + 1],
+                                           lo[2 * cc + 1]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int cc = 0; cc < 8; ++cc) hi[cc] = lo[cc] = 0u;
+                            }
+                            tmem_st(ta + 8u * part, hi);
+                            tmem_st(ta + 32u + 8u * part, lo);
+                        }
+                        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+                        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&a_full[buf]));
+                        ++ag;
+                    }
+                    if (fail_f) break;
+                    if (++st == G.n_stages) {
+                        st = 0;
+                        ++su;
+                    }
+                }
+                if (c == nchunks || (c % DRAIN == 0 && c > 0)) {
+                    const int g = gdrained;
+                    if (!mbar_wait(smem_u32(&d_full[g & 1]), (uint32_t)((g >> 1) & 1), &abort_s)) {
+                        fail_f = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const uint32_t base = lane_base + (uint32_t)(NABUF * A_COLS + (g & 1) * region_cols);
+#pragma unroll
+                    for (int b0 = 0; b0 < MAXBLK; b0 += 4) {
+                        uint32_t v[4][8];
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            if (b0 + b < MAXBLK && b0 + b < nb_h) tmem_ld8(base + (uint32_t)blk_col[h][b0 + b], v[b]);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+                        for (int b = 0; b < 4; ++b)
+                            if (b0 + b < MAXBLK && b0 + b < nb_h) {
+#pragma unroll
+                                for (int x = 0; x < 8; ++x) accl[8 * (b0 + b) + x] += __uint_as_float(v[b][x]);
+                            }
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&d_empty[g & 1]));
+                    ++gdrained;
+                }
+            }
+            if (fail_f) {
+                abort_s = 1;
             } else {
-                for (int e = lane; e < G.nb * FS; e += 32) {
-                    const int m = e / FS, px = e - m * FS;
-                    F[e] = pc + px < G.P ? __ldg(&fields[(size_t)m * G.P + pc + px]) : 0.f;
-                }
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&f_full[s]));
-            }
-            ++issued;
-        }
-        // copies still in flight land before the CTA moves on
-        if (lane == 0 && G.tma)
-            for (int s = 0; s < G.sf && s < issued; ++s) {
-                const int uses = (issued - s + G.sf - 1) / G.sf;
-                if (!mbar_drain(smem_u32(&f_full[s]), (uint32_t)((uses - 1) & 1))) abort_s = 1;
-            }
-    } else if (warp == ISSUER) {
-        // ---------------- MMA issue: one thread, one step (chunk, tile) per operand stage
-        if (lane == 0) {
-            int committed = 0, c = 0, t = 0, s = 0, use = 0;   // step = (chunk c, tile t), stage s, its use
-            int NB = t_nb[0];
-            uint32_t acc_t = tmem + (uint32_t)t_col[0];
-            for (int st = 0; st < nsteps; ++st) {
-                if (!mbar_wait(smem_u32(&ab_full[s]), (uint32_t)(use & 1), &abort_s)) {
-                    abort_s = 1;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const int rows8_b = 2 * NB / 8;                 // B: [Bh; Bl], 2 NB rows
-                const bool stacked = 2 * NB <= 256;             // one MMA for Ah [Bh; Bl] (N <= 256)
-                const uint32_t id2 = make_idesc(TM, 2 * NB), id1 = make_idesc(TM, NB);
-                uint8_t *Ah = abase + (size_t)s * G.ab_bytes, *Al = Ah + G.a_bytes;
-                uint8_t *Bs = Al + G.a_bytes;
+                // the long accumulators into the item's range of partials
+                float *out = partial + (size_t)(e / G.n_sets) * G.dense + row;
 #pragma unroll
-                for (int ks = 0; ks < KC / 16; ++ks) {
-                    const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
-                    const uint64_t ah = make_desc(smem_u32(Ah + ks * rows8_a * 256), 128, 256);
-                    const uint64_t al = make_desc(smem_u32(Al + ks * rows8_a * 256), 128, 256);
-                    const uint32_t bslab = smem_u32(Bs + ks * rows8_b * 256);
-                    const uint64_t bh = make_desc(bslab, 128, 256);                // rows [0, NB): Bh
-                    if (stacked) {
-                        mma_bf16(acc_t, ah, bh, id2, acc);                           // cols [0, 2 NB)
-                    } else {
-                        const uint64_t bl = make_desc(bslab + (NB / 8) * 256, 128, 256);   // rows [NB, 2 NB): Bl
-                        mma_bf16(acc_t, ah, bh, id1, acc);
-                        mma_bf16(acc_t + (uint32_t)NB, ah, bl, id1, acc);
+                for (int b = 0; b < MAXBLK; ++b)
+                    if (b < nb_h) {
+                        float *o = out + blk_out[h][b];
+#pragma unroll
+                        for (int x = 0; x < 8; ++x) {
+                            o[x * TM] = accl[8 * b + x];
+                            accl[8 * b + x] = 0.f;
+                        }
                     }
-                    mma_bf16(acc_t + (uint32_t)(2 * NB), al, bh, id1, acc);     // cols [2 NB, 3 NB)
-                }
-                mma_commit(smem_u32(&ab_empty[s]));
-                ++committed;
-                if (++s == G.sa) {
-                    s = 0;
-                    ++use;
-                }
-                if (++t == NG) {
-                    t = 0;
-                    ++c;
-                }
-                if (NG > 1) {
-                    NB = t_nb[t];
-                    acc_t = tmem + (uint32_t)t_col[t];
-                }
             }
-            // every MMA issued is done before tensor memory is read or freed
-            if (committed > 0) {
-                const int st = committed - 1, s2 = st % G.sa, u2 = st / G.sa;
-                if (!mbar_drain(smem_u32(&ab_empty[s2]), (uint32_t)(u2 & 1))) abort_s = 1;
-            }
-            if (committed < nsteps) abort_s = 1;
-        }
-    } else {
-        // ---------------- producers: the operand tiles of a step.  A thread's
-        // (row, 8-pixel group) units and band units are the same for every
-        // chunk and tile: their tile offsets are worked out once.  Unit u =
-        // (8-row group, 8 rows x GPR groups); a warp's 32 units are 8 rows x 4
-        // groups (conflict-free 16-byte stores)
-        const int p = threadIdx.x;
-        int a_r[KA], a_g[KA], a_so[KA];
-#pragma unroll
-        for (int k = 0; k < KA; ++k) {
-            const int u = p + k * NPW * 32;
-            const int rg = u / (8 * GPR), rem = u % (8 * GPR);
-            a_g[k] = rem >> 3;
-            a_r[k] = rg * 8 + (rem & 7);
-            a_so[k] = core_off(a_r[k], a_g[k], rows8_a);
-        }
-        int b_kk[KB], b_g[KB];
-#pragma unroll
-        for (int k = 0; k < KB; ++k) {
-            const int u = p + k * NPW * 32;
-            const int rg = u / (8 * GPR), rem = u % (8 * GPR);
-            b_g[k] = rem >> 3;
-            b_kk[k] = rg * 8 + (rem & 7);
-        }
-        // a step's field offsets (ring x FS + group x 8) and band, loaded one step ahead
-        // so that no field load waits on a shared-memory lookup
-        int fi[KA], fj[KA], nfi[KA], nfj[KA];
-        auto row_offsets = [&](int t, int *oi, int *oj) {
-#pragma unroll
-            for (int k = 0; k < KA; ++k) {
-                const int i = rowi[t][a_r[k]], j = rowj[t][a_r[k]];
-                oi[k] = i >= 0 ? i * FS + a_g[k] * 8 : -1;
-                oj[k] = j * FS + a_g[k] * 8;
-            }
-        };
-        row_offsets(0, fi, fj);
-        int nb_cur = t_nb[0], klo_cur = t_klo[0];
-        int sa = 0, ua = 0, sf = 0, uf = 0;   // operand stage and its use; field stage and its use
-        for (int c = 0; c < nchunks; ++c) {
-            if (!mbar_wait(smem_u32(&f_full[sf]), (uint32_t)(uf & 1), &abort_s)) {
-                abort_s = 1;
-                break;
-            }
-            const float *F = (const float *)(fbase + (size_t)sf * G.f_bytes);
-            const int64_t pc = p_begin + (int64_t)c * KC;
-            const int valid = (int)min((int64_t)KC, p_end - pc);
-            bool ok = true;
-            for (int t = 0; t < NG; ++t) {
-                if (ua > 0 && !mbar_wait(smem_u32(&ab_empty[sa]), (uint32_t)((ua - 1) & 1), &abort_s)) {
-                    ok = false;
-                    break;
-                }
-                uint8_t *Ah = abase + (size_t)sa * G.ab_bytes, *Al = Ah + G.a_bytes;
-                uint8_t *Bs = Al + G.a_bytes;
-                const int NB = nb_cur, klo = klo_cur, rows8_b = 2 * NB / 8;
-                const int bl_off = (NB / 8) * 256;   // row NB of the stacked tile
-                const int tn = t + 1 < NG ? t + 1 : 0;   // the next step's tile
-                int nb_next = nb_cur, klo_next = klo_cur;
-                if (NG > 1) {
-                    row_offsets(tn, nfi, nfj);
-                    nb_next = t_nb[tn];
-                    klo_next = t_klo[tn];
-                }
-#pragma unroll
-                for (int k = 0; k < KA; ++k) {
-                    float2 v[4];
-                    if (fi[k] >= 0) {
-                        float2 x[4], y[4];
-                        ld8(F + fi[k], x);
-                        ld8(F + fj[k], y);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) v[e] = __fmul2_rn(x[e], y[e]);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
-                    }
-                    if (valid < KC) mask_tail(v, a_g[k], valid);
-                    store_split8(Ah, Al, a_so[k], v);
-                }
-#pragma unroll
-                for (int k = 0; k < KB; ++k) {
-                    if (p + k * NPW * 32 >= NB * GPR) break;   // past the band
-                    const int ring = klo + b_kk[k];
-                    float2 v[4];
-                    if (ring < G.nb) {
-                        ld8(F + ring * FS + b_g[k] * 8, v);
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) v[e] = make_float2(0.f, 0.f);
-                    }
-                    if (valid < KC) mask_tail(v, b_g[k], valid);
-                    const int so = core_off(b_kk[k], b_g[k], rows8_b);   // Bh row kk; Bl row NB + kk
-                    store_split8(Bs, Bs + bl_off, so, v);
-                }
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&ab_full[sa]));
-                if (++sa == G.sa) {
-                    sa = 0;
-                    ++ua;
-                }
-                if (NG > 1) {
-#pragma unroll
-                    for (int k = 0; k < KA; ++k) {
-                        fi[k] = nfi[k];
-                        fj[k] = nfj[k];
-                    }
-                    nb_cur = nb_next;
-                    klo_cur = klo_next;
-                }
-            }
-            if (!ok) {
-                abort_s = 1;
-                break;
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&f_empty[sf]));   // every tile of the chunk is formed
-            if (++sf == G.sf) {
-                sf = 0;
-                ++uf;
-            }
+            grp = gdrained;                           // formers keep their own count of groups
         }
     }
-    // every role is done: MMAs and copies have landed (or the CTA gave up)
+    // every role is done (or gave up): copies and MMAs in flight land before the memory goes
     __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (abort_s) {
-        if (threadIdx.x == 0) atomicCAS(err, 0, DERR_TIMEOUT);
-    } else {
-        // epilogue, tile by tile: TMEM -> shared [128][3 NB + 1] (over the stages) ->
-        // per-triplet partials, (Ah Bh + Ah Bl) + Al Bh
-        float *D = (float *)smem;
-        for (int t = 0; t < NG; ++t) {
-            const int NB = t_nb[t], klo = t_klo[t], dw = 3 * NB + 1;
-            if (warp < 4) {   // warp w reads tensor-memory lanes 32 w .. 32 w + 31
-                const int lane_base = warp * 32;
-                const int r = lane_base + lane;
-                for (int col = 0; col < 3 * NB; col += 16) {
-                    uint32_t v[16];
-                    const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(t_col[t] + col);
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-                        "%11, %12, %13, %14, %15}, [%16];\n"
-                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                          "=r"(v[14]), "=r"(v[15])
-                        : "r"(taddr));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) D[r * dw + col + e] = __uint_as_float(v[e]);
-                }
+        if (warp == 0 && lane == 0) {
+            // the loader's last fills of each stage
+            for (int s = 0; s < G.n_stages && s < issued; ++s) {
+                const int uses = (issued - s + G.n_stages - 1) / G.n_stages;
+                if (!mbar_drain(smem_u32(&full[s]), (uint32_t)((uses - 1) & 1))) break;
             }
-            __syncthreads();
-            const int r = (t0 + t) * TM + (int)threadIdx.x;
-            if (threadIdx.x < TM && r < n_rows) {
-                const int4 R = rows[r];
-                for (int q = R.z; q < R.w; ++q) {
-                    const int kk = ijk[3 * q + 2] - klo;
-                    if (kk >= 0 && kk < NB) {
-                        const float *d = D + threadIdx.x * dw + kk;
-                        // (hh + hl) + lh as an exact double-float pair (TwoSum), stored in the entry's 8 bytes
-                        const float x = d[0] + d[NB], y = d[2 * NB];
-                        const float sm = __fadd_rn(x, y), bp = __fsub_rn(sm, x);
-                        const float er = __fadd_rn(__fsub_rn(x, __fsub_rn(sm, bp)), __fsub_rn(y, bp));
-                        ((float2 *)partial)[(size_t)blockIdx.y * G.n_trip + q] = make_float2(sm, er);
-                    }
-                }
-            }
-            __syncthreads();
         }
+        if (warp == 1 && lane == 0) {
+            // every MMA this thread issued is done once a fresh commit arrives
+            mma_commit(smem_u32(&fin));
+            mbar_drain(smem_u32(&fin), 0u);
+        }
+        if (threadIdx.x == 0) atomicCAS(err, 0, DERR_TIMEOUT);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    if (warp == ISSUER)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(G.tmem_cols));
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
-// Row table of a (canonical, sorted) triplet list: one entry (i, j, first
-// triplet, end) per run of equal (i, j), ordered by (j, i); then per tile of
-// TM rows its band of rings (first k, width rounded up to 16, at most np);
-// then groups of consecutive tiles whose accumulators (3 x band columns
-// each) fit TMEM_COLS, at most gmax tiles and about as many tiles in each
-// (gmax = 1: a group per tile).  ctl[0] = rows, ctl[1] = groups.
-// One block of 1024 threads; dynamic shared memory: nb x ceil(nb / 32) words
-// of presence bits, (j, i) of every row.
-__global__ void __launch_bounds__(1024) k_rows(int n_trip, int nb, int np, int gmax,
-                                               const int32_t *__restrict__ ijk, int4 *__restrict__ rows,
-                                               int *__restrict__ ctl, int2 *__restrict__ tiles,
-                                               int2 *__restrict__ groups) {
-    int *n_rows = ctl;
-    extern __shared__ uint32_t presence[];
-    __shared__ int jstart[ABS_MAX_BINS + 1];
-    __shared__ int wsum[32];
-    __shared__ int nr_s;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int words = (nb + 31) / 32;
-    auto row_start = [&](int t, int &i, int &j) {
-        i = ijk[3 * t];
-        j = ijk[3 * t + 1];
-        const bool start = t == 0 || i != ijk[3 * t - 3] || j != ijk[3 * t - 2];
-        return start && i >= 0 && i <= j && j < nb;   // a checked list has nothing else
-    };
-    for (int e = threadIdx.x; e < nb * words; e += blockDim.x) presence[e] = 0u;
-    for (int e = threadIdx.x; e <= nb; e += blockDim.x) jstart[e] = 0;
-    __syncthreads();
-    for (int t = threadIdx.x; t < n_trip; t += blockDim.x) {
-        int i, j;
-        if (row_start(t, i, j)) atomicOr(&presence[j * words + (i >> 5)], 1u << (i & 31));
-    }
-    __syncthreads();
-    // rows per j (distinct (i, j) pairs), exclusive prefix over j (nb <= 1024: one pass)
-    int cnt = 0;
-    if (threadIdx.x < nb)
-        for (int w = 0; w < words; ++w) cnt += __popc(presence[threadIdx.x * words + w]);
-    int x = cnt;
+// The fields [nb][P] FP32 as the three chunk-blocked planes of TcPlanes: BF16 hi, BF16 lo
+// and FP32, nbp rings a block (zeros past nb and past P).  One thread per 4 pixels of a ring.
+__global__ void __launch_bounds__(256) k_split_fields(int nb, int nbp, int64_t P, int64_t P_pad,
+                                                      const float *__restrict__ f, __nv_bfloat16 *__restrict__ hi,
+                                                      __nv_bfloat16 *__restrict__ lo, float *__restrict__ f32) {
+    const int64_t per = P_pad / 4;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= per * nbp) return;
+    const int m = (int)(g / per);
+    const int64_t p = (g - (int64_t)m * per) * 4;
+    float v[4];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    int before = 0, total = 0;
-    for (int w = 0; w < 32; ++w) {
-        if (w < warp) before += wsum[w];
-        total += wsum[w];
-    }
-    if (threadIdx.x < nb) jstart[threadIdx.x] = before + x - cnt;
-    if (threadIdx.x == 0) {
-        nr_s = total;
-        *n_rows = total;
-    }
-    __syncthreads();
-    // every row at (rows of smaller j) + (rows of its j with smaller i)
-    for (int t = threadIdx.x; t < n_trip; t += blockDim.x) {
-        int i, j;
-        if (row_start(t, i, j)) {
-            int below = 0;
-            for (int w = 0; w < (i >> 5); ++w) below += __popc(presence[j * words + w]);
-            below += __popc(presence[j * words + (i >> 5)] & ((1u << (i & 31)) - 1u));
-            int e = t + 1;
-            while (e < n_trip && ijk[3 * e] == i && ijk[3 * e + 1] == j) ++e;
-            rows[jstart[j] + below] = make_int4(i, j, t, e);
-        }
-    }
-    __syncthreads();
-    // bands: one warp per tile
-    const int nr = nr_s;
-    const int ntiles = (nr + TM - 1) / TM;
-    for (int tl = warp; tl < ntiles; tl += blockDim.x / 32) {
-        int lo = 1 << 30, hi = -1;
-        for (int r = tl * TM + lane; r < min(nr, tl * TM + TM); r += 32) {
-            const int4 R = rows[r];
-            lo = min(lo, ijk[3 * R.z + 2]);
-            hi = max(hi, ijk[3 * (R.w - 1) + 2]);
-        }
+    for (int e = 0; e < 4; ++e) v[e] = (m < nb && p + e < P) ? f[(size_t)m * P + p + e] : 0.f;
+    uint32_t h[2], l[2];
+    split2(make_float2(v[0], v[1]), h[0], l[0]);
+    split2(make_float2(v[2], v[3]), h[1], l[1]);
+    const int x = (int)(p % KC), key = m & 7;
+    const size_t row = ((size_t)(p / KC) * nbp + m) * KC;
+    const size_t ob = row + (size_t)((((x >> 3) ^ key) << 3) | (x & 7));   // 8 BF16 per 16-byte unit
+    const size_t of = row + (size_t)(((x >> 2) ^ key) << 2);                // 4 FP32 per 16-byte unit
+    *(uint2 *)(hi + ob) = make_uint2(h[0], h[1]);
+    *(uint2 *)(lo + ob) = make_uint2(l[0], l[1]);
+    *(float4 *)(f32 + of) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// dense[x] = sum over pixel ranges of partial[r][x] in FP64 (a fixed order).
+__global__ void __launch_bounds__(256) k_tc_reduce(int64_t dense, int n_ranges, const float *__restrict__ partial,
+                                                   double *__restrict__ out) {
+    const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= dense) return;
+    // eight loads in flight, added in range order
+    double s = 0.0;
+    int r = 0;
+    for (; r + 8 <= n_ranges; r += 8) {
+        float v[8];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            lo = min(lo, __shfl_xor_sync(FULL, lo, o));
-            hi = max(hi, __shfl_xor_sync(FULL, hi, o));
-        }
-        if (lane == 0) {
-            lo = max(0, min(lo, nb - 1));
-            int w = ((max(hi - lo + 1, 1) + 15) / 16) * 16;
-            if (w > np) {   // only for a list that fails its check; stay inside the operand tile
-                w = np;
-                lo = 0;
-            }
-            tiles[tl] = make_int2(lo, w);
-        }
+        for (int u = 0; u < 8; ++u) v[u] = __ldcs(&partial[(size_t)(r + u) * dense + x]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (double)v[u];
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        // greedy groups of consecutive tiles; then again with at most ceil(tiles / groups)
-        // tiles a group, so that the groups carry about the same work
-        int cap = gmax, ng = 0;
-        for (int pass = 0; pass < 2; ++pass) {
-            ng = 0;
-            for (int t = 0; t < ntiles;) {
-                const int first = t;
-                int cols = 0;
-                while (t < ntiles && t - first < cap && cols + 3 * tiles[t].y <= TMEM_COLS) cols += 3 * tiles[t++].y;
-                if (t == first) ++t;   // cannot happen: a band is at most np <= TMEM_COLS / 3
-                if (pass == 1) groups[ng] = make_int2(first, t - first);
-                ++ng;
-            }
-            cap = min(gmax, (ntiles + ng - 1) / max(ng, 1));
-        }
-        ctl[1] = ng;
-    }
+    for (; r < n_ranges; ++r) s += (double)__ldcs(&partial[(size_t)r * dense + x]);
+    out[x] = s;
 }
 
-// x + y for double-float pairs (TwoSum of the high parts, low parts added).
-__device__ __forceinline__ float2 df2_add(float2 x, float2 y) {
-    const float s = __fadd_rn(x.x, y.x);
-    const float bp = __fsub_rn(s, x.x);
-    const float e = __fadd_rn(__fsub_rn(x.x, __fsub_rn(s, bp)), __fsub_rn(y.x, bp));
-    const float t = __fadd_rn(e, __fadd_rn(x.y, y.y));
-    const float h = __fadd_rn(s, t);
-    return make_float2(h, __fsub_rn(t, __fsub_rn(h, s)));
-}
-
-// S[t] = inv_p * sum over splits of partial[split][t] (double-float pairs stored as
-// float2): 32 triplets per block, 8 lanes of splits per triplet, summed in
-// double-float in a fixed order (deterministic; GB300's FP64 pipe is narrow), the
-// total widened to FP64 once.
-__global__ void __launch_bounds__(256) k_tc_reduce(int n_trip, int nsplit, double inv_p,
-                                                       const double *__restrict__ partial,
-                                                       double *__restrict__ S) {
-    __shared__ float2 sh[8][33];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int t = blockIdx.x * 32 + tx;
-    const float2 *pf = (const float2 *)partial;
-    float2 s = make_float2(0.f, 0.f);
-    if (t < n_trip)
-        for (int k = ty; k < nsplit; k += 8) s = df2_add(s, pf[(size_t)k * n_trip + t]);
-    sh[ty][tx] = s;
-    __syncthreads();
-    if (ty == 0 && t < n_trip) {
-        float2 a = make_float2(0.f, 0.f);
-        for (int k = 0; k < 8; ++k) a = df2_add(a, sh[k][tx]);
-        S[t] = ((double)a.x + (double)a.y) * inv_p;
-    }
+// S[t] = inv_p dense[pos[t]].
+__global__ void __launch_bounds__(256) k_tc_gather(int n_trip, double inv_p, const int64_t *__restrict__ pos,
+                                                   const double *__restrict__ dense, double *__restrict__ S) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_trip) S[t] = dense[pos[t]] * inv_p;
 }
 
 }  // namespace
 
-// cuTensorMapEncodeTiled from the driver, looked up once (no link against libcuda).
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool looked = false;
-    if (!looked) {
-        looked = true;
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-        cudaGetLastError();
-    }
-    return fn;
-}
-
-// Tile groups of the canonical triplet list, worked out on the host the way
-// k_rows does on the device (rows by (j, i), 128 a tile, bands rounded to 16,
-// greedy groups): sizes the grid.  Lists given by the caller use the tile count.
-static int canonical_groups(const Setup &s, int np, int gmax) {
-    std::map<std::pair<int, int>, std::pair<int, int>> kr;   // (j, i) -> (first k, last k)
-    for (size_t t = 0; t + 2 < s.ijk.size(); t += 3) {
-        const auto key = std::make_pair(s.ijk[t + 1], s.ijk[t]);
-        auto it = kr.find(key);
-        if (it == kr.end()) kr[key] = {s.ijk[t + 2], s.ijk[t + 2]};
-        else it->second.second = s.ijk[t + 2];
-    }
-    std::vector<int> w;
-    int n = 0, lo = 1 << 30, hi = -1;
-    for (const auto &e : kr) {
-        lo = std::min(lo, e.second.first);
-        hi = std::max(hi, e.second.second);
-        if (++n == TM) {
-            w.push_back(std::min(np, ((hi - lo + 1 + 15) / 16) * 16));
-            n = 0, lo = 1 << 30, hi = -1;
-        }
-    }
-    if (n > 0) w.push_back(std::min(np, ((hi - lo + 1 + 15) / 16) * 16));
-    const int ntiles = (int)w.size();
-    int cap = gmax, ng = 0;
-    for (int pass = 0; pass < 2; ++pass) {   // as k_rows: greedy, then balanced
-        ng = 0;
-        for (int t = 0; t < ntiles;) {
-            const int first = t;
-            int cols = 0;
-            while (t < ntiles && t - first < cap && cols + 3 * w[t] <= TMEM_COLS) cols += 3 * w[t++];
-            if (t == first) ++t;
-            ++ng;
-        }
-        cap = std::min(gmax, (ntiles + ng - 1) / std::max(ng, 1));
-    }
-    return std::max(ng, 1);
-}
-
-// One launch shape of the kernel: the chunk width and whether a CTA owns a
-// group of row tiles (the field chunks brought in once for all of them) or a
-// single tile; everything else follows from these and the problem.
-struct TcLaunch {
-    TcGeom G;
-    int KC = 0;
-    bool grouped = false;
-    int groups = 0, gmax = 1;
-    size_t smem = 0;
+// The tiling of a triplet list (see the file comment): rows (j, k) in (j, k)
+// order, tiles of 128 rows ordered inside by (k, j), sets of consecutive tiles
+// whose accumulator columns fit col_budget, each triplet's place in the dense
+// accumulator.  A block of 128 rows whose rings i span more than MAX_TILE_N
+// columns becomes several tiles with the same rows.  False for a list the
+// kernel cannot take (ring out of range, i > j or j > k).
+struct TcPlanHost {
+    std::vector<TcSet> sets;
+    std::vector<TcTile> tiles;
+    std::vector<short2> rowjk;
+    std::vector<int64_t> pos;
+    int64_t dense = 0;
+    int max_stage = 0;       // bytes of the largest set's stage
+    int plane_rows = 0;      // rings a block of the planes must hold (every set's windows inside it)
+    double work = 0;         // sum over tiles of 128 x N (executed MMA columns x rows per pixel)
 };
 
-// Shared-memory stages for chunk width kc: at least two of each ring (three
-// field stages for the wider chunks), three operand stages if the field ring
-// keeps its stages, then as many field stages as fit.  False if they do not fit.
-static bool tc_stages(TcGeom &G, int kc, int nb, size_t &smem) {
-    const int64_t budget = 215 * 1024;   // dynamic shared memory, below the 227 KB per CTA with the static part
-    const size_t epi = (size_t)TM * (3 * G.NP + 1) * 4;
-    const int min_f = kc > 64 ? 3 : 2;
-    G.a_bytes = TM * kc * 2;
-    G.b_bytes = 2 * G.NP * kc * 2;
-    G.f_bytes = (int)(cdiv((int64_t)nb * (kc + 4) * 4, 1024) * 1024);
-    G.ab_bytes = (int)(cdiv(2 * G.a_bytes + G.b_bytes, 1024) * 1024);
-    G.sa = MAX_AB;
-    while (G.sa > 2 && budget - (int64_t)G.sa * G.ab_bytes < min_f * (int64_t)G.f_bytes) --G.sa;
-    G.sf = (int)std::min<int64_t>(MAX_F, (budget - (int64_t)G.sa * G.ab_bytes) / G.f_bytes);
-    if (G.sf < min_f || (int64_t)epi > budget) return false;
-    smem = 1024 + std::max((size_t)G.sf * G.f_bytes + (size_t)G.sa * G.ab_bytes, epi);
-    return true;
-}
-
-// The pixel range of a CTA: whole waves of CTAs, at most 4096 pixels (which
-// bounds the FP32 accumulation length in the tensor core), a multiple of kc.
-static int64_t tc_range(int64_t P, int kc, int groups, int sm_count) {
-    for (int waves = 1;; ++waves) {
-        const int64_t ranges = std::max<int64_t>(1, (int64_t)sm_count * waves / groups);
-        const int64_t per = cdiv(cdiv(P, ranges), kc) * kc;
-        if (per <= 4096) return per;
+static bool tc_plan(const int32_t *ijk, int n_trip, int nb, int col_budget, int stage_cap, TcPlanHost &pl) {
+    std::map<std::pair<int, int>, std::pair<int, int>> rows;   // (j, k) -> (lowest i, highest i)
+    for (int t = 0; t < n_trip; ++t) {
+        const int i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
+        if (i < 0 || i > j || j > k || k >= nb) return false;
+        auto it = rows.find({j, k});
+        if (it == rows.end()) rows[{j, k}] = {i, i};
+        else {
+            it->second.first = std::min(it->second.first, i);
+            it->second.second = std::max(it->second.second, i);
+        }
     }
-}
-
-static bool tc_shape(const TcGeom &base, int kc, bool grouped, int tiles, int tc_groups, int nb, int sm_count,
-                     TcLaunch &L) {
-    L.G = base;
-    L.KC = kc;
-    if (!tc_stages(L.G, kc, nb, L.smem)) return false;
-    L.grouped = grouped && tc_groups < tiles;
-    L.groups = L.grouped ? tc_groups : tiles;
-    L.gmax = L.grouped ? GMAX : 1;
-    L.G.per_split = tc_range(base.P, kc, L.groups, sm_count);
+    std::vector<std::pair<std::pair<int, int>, std::pair<int, int>>> R(rows.begin(), rows.end());
+    const int nblocks = (int)cdiv((int64_t)R.size(), TM);      // blocks of 128 rows
+    pl.tiles.clear();
+    pl.rowjk.clear();
+    std::vector<int> first_tile(nblocks);
+    std::map<std::pair<int, int>, int> lane_of;   // (j, k) -> row block * TM + lane
+    pl.dense = 0;
+    pl.work = 0;
+    for (int rb = 0; rb < nblocks; ++rb) {
+        const int r0 = rb * TM, r1 = std::min<int>((int)R.size(), r0 + TM);
+        int lo = 1 << 30, hi = -1;
+        std::vector<std::pair<int, int>> kj;
+        for (int r = r0; r < r1; ++r) {
+            lo = std::min(lo, R[r].second.first);
+            hi = std::max(hi, R[r].second.second);
+            kj.push_back({R[r].first.second, R[r].first.first});
+        }
+        std::sort(kj.begin(), kj.end());
+        std::vector<short2> lanes(TM, make_short2(-1, -1));
+        for (int x = 0; x < (int)kj.size(); ++x) {
+            lanes[x] = make_short2((short)kj[x].second, (short)kj[x].first);
+            lane_of[{kj[x].second, kj[x].first}] = rb * TM + x;
+        }
+        // the block's ring columns, cut into tiles of at most MAX_TILE_N (same rows)
+        const int ilo = lo & ~7;
+        const int n_all = (int)cdiv(hi - ilo + 1, 16) * 16;
+        first_tile[rb] = (int)pl.tiles.size();
+        for (int c0 = 0; c0 < n_all; c0 += MAX_TILE_N) {
+            TcTile T;
+            T.i_lo = ilo + c0;
+            T.n = std::min(MAX_TILE_N, n_all - c0);
+            if (T.n > col_budget) return false;
+            T.acc_off = pl.dense;
+            pl.dense += (int64_t)TM * T.n;
+            pl.work += (double)TM * T.n;
+            pl.tiles.push_back(T);
+            pl.rowjk.insert(pl.rowjk.end(), lanes.begin(), lanes.end());
+        }
+    }
+    const int ntiles = (int)pl.tiles.size();
+    // sets: greedy runs of tiles within the column budget, the stage cap and MAX_TILES
+    pl.sets.clear();
+    pl.max_stage = 0;
+    pl.plane_rows = nb;
+    for (int t = 0; t < ntiles;) {
+        TcSet S{};
+        S.tile0 = t;
+        int cols = 0, blo = 1 << 30, bhi = -1, flo = 1 << 30, fhi = -1;
+        while (t < ntiles && S.ntiles < MAX_TILES) {
+            const TcTile &T = pl.tiles[t];
+            int jmin = 1 << 30, kmax = -1;
+            for (int x = 0; x < TM; ++x) {
+                const short2 v = pl.rowjk[(size_t)t * TM + x];
+                if (v.x < 0) continue;
+                jmin = std::min(jmin, (int)v.x);
+                kmax = std::max(kmax, (int)v.y);
+            }
+            const int nblo = std::min(blo, T.i_lo), nbhi = std::max(bhi, T.i_lo + T.n);
+            const int nflo = std::min(flo, jmin), nfhi = std::max(fhi, kmax + 1);
+            const int bn = (int)cdiv(nbhi - nblo, BOX_ROWS) * BOX_ROWS, fn = (int)cdiv(nfhi - nflo, BOX_ROWS) * BOX_ROWS;
+            const int stage = 2 * bn * 128 + 2 * fn * 128;
+            if (S.ntiles > 0 && (cols + T.n > col_budget || stage > stage_cap)) break;
+            cols += T.n;
+            blo = nblo, bhi = nbhi, flo = nflo, fhi = nfhi;
+            S.b_lo = blo, S.b_n = bn, S.f_lo = flo, S.f_n = fn;
+            ++S.ntiles;
+            ++t;
+        }
+        pl.max_stage = std::max(pl.max_stage, 2 * S.b_n * 128 + 2 * S.f_n * 128);
+        pl.plane_rows = std::max(pl.plane_rows, std::max(S.b_lo + S.b_n, S.f_lo + S.f_n));
+        pl.sets.push_back(S);
+    }
+    pl.pos.resize(n_trip);
+    for (int t = 0; t < n_trip; ++t) {
+        const int i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
+        const int l = lane_of[{j, k}];
+        const int tl = first_tile[l / TM] + (i - pl.tiles[first_tile[l / TM]].i_lo) / MAX_TILE_N;
+        const TcTile &T = pl.tiles[tl];
+        pl.pos[t] = T.acc_off + (int64_t)(i - T.i_lo) * TM + (l % TM);
+    }
     return true;
 }
 
-// k_rows and the kernel for one shape, with events around the kernel when given.
-static abs_status tc_run(abs_ctx *ctx, const Setup &s, const TcLaunch &L, const float *d_fields, int32_t n_trip,
-                         const int32_t *d_ijk, int max_rows, int tiles, double *partial, cudaEvent_t e0,
+// A plan on the device: the host plan and device copies of its tables.  The
+// canonical list's plans (one per column budget) are kept in the setup; a
+// caller's list is read back and planned into context workspaces on each call.
+struct TcPlanDev {
+    TcPlanHost h;
+    TcSet *d_sets = nullptr;
+    TcTile *d_tiles = nullptr;
+    short2 *d_rowjk = nullptr;
+    int64_t *d_pos = nullptr;
+    bool owned = false;
+    ~TcPlanDev() {
+        if (owned) {
+            cudaFree(d_sets);
+            cudaFree(d_tiles);
+            cudaFree(d_rowjk);
+            cudaFree(d_pos);
+        }
+    }
+};
+struct TcPlans {
+    std::map<int, std::unique_ptr<TcPlanDev>> by_budget;
+};
+
+template <class T>
+static bool upload_to(T *&dst, const std::vector<T> &v) {
+    if (cudaMalloc((void **)&dst, sizeof(T) * std::max<size_t>(v.size(), 1)) != cudaSuccess) {
+        cudaGetLastError();
+        dst = nullptr;
+        return false;
+    }
+    if (!v.empty() && cudaMemcpy(dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
+// The split-BF16 launch shape: the accumulator-column budget of a set (how many
+// tiles share each chunk) and the work items per CTA (which sets the pixel
+// range of an item, at most MAX_RANGE_PIXELS so that one FP32 tensor-memory
+// accumulation covers a bounded number of terms).
+#ifndef ABS_TC_MAX_RANGE
+#define ABS_TC_MAX_RANGE 16384
+#endif
+constexpr int64_t MAX_RANGE_PIXELS = ABS_TC_MAX_RANGE;
+constexpr int BUDGETS[] = {MAX_SET_COLS, MAX_SET_COLS * 3 / 4 / 16 * 16};
+
+struct TcShapeSel {
+    int budget = MAX_SET_COLS;
+    int waves = 2;
+};
+
+// Pixel range per work item for a plan, SM count and waves: items = sets x ranges
+// close to waves x SMs, each range a multiple of the chunk and at most MAX_RANGE_PIXELS.
+static int64_t tc_range(const TcPlanHost &pl, int64_t P_pad, int sms, int waves) {
+    const int64_t nsets = (int64_t)pl.sets.size();
+    int64_t ranges = std::max<int64_t>(1, cdiv((int64_t)sms * 4 * waves, nsets));
+    int64_t per = cdiv(cdiv(P_pad, ranges), KC) * KC;
+    const int64_t cap = std::min<int64_t>(MAX_RANGE_PIXELS, (int64_t)4096 << (waves - 1));
+    if (per > cap) per = cap;
+    return std::max<int64_t>(per, KC);
+}
+
+}  // namespace absk
+
+namespace absk {
+
+// dynamic shared memory for the stages (with 1 KB of alignment slack and the kernel's
+// 9 KB of static shared memory, below the 227 KB a CTA may have)
+static const int SMEM_BUDGET = 200 * 1024;
+
+// Plan of cfg's canonical list for a column budget (made and uploaded on first use).
+static const TcPlanDev *canonical_plan(const Setup &s, int budget) {
+    Setup &ms = const_cast<Setup &>(s);
+    if (!ms.tc_plan) ms.tc_plan = std::make_shared<TcPlans>();
+    TcPlans &pls = *static_cast<TcPlans *>(ms.tc_plan.get());
+    auto it = pls.by_budget.find(budget);
+    if (it != pls.by_budget.end()) return it->second.get();
+    auto pd = std::make_unique<TcPlanDev>();
+    if (!tc_plan(s.ijk.data(), (int)(s.ijk.size() / 3), s.nb, budget, SMEM_BUDGET / 2, pd->h)) return nullptr;
+    pd->owned = true;
+    if (!upload_to(pd->d_sets, pd->h.sets) || !upload_to(pd->d_tiles, pd->h.tiles) ||
+        !upload_to(pd->d_rowjk, pd->h.rowjk) || !upload_to(pd->d_pos, pd->h.pos))
+        return nullptr;
+    const TcPlanDev *r = pd.get();
+    pls.by_budget[budget] = std::move(pd);
+    return r;
+}
+
+// One launch of the kernel and its reduction for a plan and shape; events around the kernel when given.
+static abs_status tc_run(abs_ctx *ctx, const Setup &s, const TcPlanDev &pd, const TcShapeSel &sh,
+                         const TcPlanes &planes, int64_t P_pad, int32_t n_trip, double *d_sum, cudaEvent_t e0,
                          cudaEvent_t e1) {
-    TcGeom G = L.G;
-    const int KC = L.KC;
-    // the field chunk as one TMA box (KC + 4 pixels x every ring) of the [nb][P] FP32 array; the
-    // row pitch P x 4 bytes and the array must be 16-byte aligned, else the loader warp copies
-    CUtensorMap fmap;
-    memset(&fmap, 0, sizeof fmap);
-    G.tma = 0;
-    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
-    if (encode && G.P % 4 == 0 && ((uintptr_t)d_fields & 15) == 0) {
-        const cuuint64_t dims[2] = {(cuuint64_t)G.P, (cuuint64_t)s.nb};
-        const cuuint64_t strides[1] = {(cuuint64_t)G.P * 4};
-        const cuuint32_t box[2] = {(cuuint32_t)(KC + 4), (cuuint32_t)s.nb};
-        const cuuint32_t estr[2] = {1, 1};
-        G.tma = encode(&fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)d_fields, dims, strides, box, estr,
-                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    const TcPlanHost &pl = pd.h;
+    TcParams G;
+    G.n_sets = (int)pl.sets.size();
+    G.P_pad = P_pad;
+    G.per_item = tc_range(pl, P_pad, ctx->sm_count, sh.waves);
+    const int64_t ranges = cdiv(P_pad, G.per_item);
+    G.n_items = (int)(ranges * G.n_sets);
+    G.dense = pl.dense;
+    G.stage_bytes = pl.max_stage;
+    G.n_stages = std::min(MAX_STAGES, SMEM_BUDGET / std::max(G.stage_bytes, 1));
+    if (G.n_stages < 2) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 stages do not fit shared memory");
+    float *partial = (float *)workspace(ctx, "tc.partial", sizeof(float) * (size_t)(ranges * G.dense));
+    double *dsum = (double *)workspace(ctx, "tc.dense", sizeof(double) * (size_t)G.dense);
+    int *next = (int *)workspace(ctx, "tc.next", sizeof(int));
+    if (!partial || !dsum || !next) return fail(ctx, ABS_ERR_OOM, "split-BF16 workspace");
+    const size_t smem = 1024 + (size_t)G.n_stages * G.stage_bytes;
+    if (cudaFuncSetAttribute(k_triple_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16: shared memory attribute refused");
     }
-    const int64_t nsplit = cdiv(G.P, G.per_split);
-    int4 *rows = (int4 *)workspace(ctx, "tc.rows", sizeof(int4) * std::max(max_rows, 1));
-    int2 *tl = (int2 *)workspace(ctx, "tc.tiles", sizeof(int2) * std::max(tiles, 1));
-    int2 *gr = (int2 *)workspace(ctx, "tc.groups", sizeof(int2) * std::max(tiles, 1));
-    int *ctl = (int *)workspace(ctx, "tc.ctl", sizeof(int) * 2);
-    if (!rows || !tl || !gr || !ctl) return fail(ctx, ABS_ERR_OOM, "split-BF16 workspace");
-    cudaStream_t st = ctx->stream;
-    auto kern = KC == 128 ? k_triple_tc<128> : KC == 96 ? k_triple_tc<96> : k_triple_tc<64>;
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     {
-        StageTimer timer(ctx, e0 ? nullptr : "tc_rows");
-        const size_t psmem = sizeof(uint32_t) * (size_t)s.nb * ((s.nb + 31) / 32);
-        k_rows<<<1, 1024, psmem, st>>>(n_trip, s.nb, G.NP, L.gmax, d_ijk, rows, ctl, tl, gr);
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k_triple_tc) == cudaSuccess && fa.maxThreadsPerBlock < NT)
+            return fail(ctx, ABS_ERR_UNSUPPORTED,
+                        "split-BF16: kernel needs " + std::to_string(fa.numRegs) + " registers a thread, " +
+                            std::to_string(fa.maxThreadsPerBlock) + " threads fit a CTA");
+        cudaGetLastError();
     }
-    StageTimer timer(ctx, e0 ? nullptr : "triple_tc");
-    if (e0) cudaEventRecord(e0, st);
-    kern<<<dim3(L.groups, (unsigned)nsplit), NT, L.smem, st>>>(G, fmap, d_fields, rows, tl, gr, ctl, d_ijk, partial,
-                                                               ctx->d_err);
-    if (e1) cudaEventRecord(e1, st);
+    cudaStream_t st = ctx->stream;
+    const int grid = std::min(G.n_items, ctx->sm_count);
+    {
+        StageTimer timer(ctx, e0 ? nullptr : "triple_tc");
+        if (e0) cudaEventRecord(e0, st);
+        cudaMemsetAsync(next, 0, sizeof(int), st);
+        k_triple_tc<<<grid, NT, smem, st>>>(G, planes, pd.d_sets, pd.d_tiles, pd.d_rowjk, partial, next,
+                                             ctx->d_err);
+    }
+    {
+        StageTimer timer(ctx, e0 ? nullptr : "tc_reduce");
+        k_tc_reduce<<<(int)cdiv(G.dense, 256), 256, 0, st>>>(G.dense, (int)ranges, partial, dsum);
+        k_tc_gather<<<(int)cdiv(n_trip, 256), 256, 0, st>>>(n_trip, 1.0 / ((double)s.N * (double)s.N), pd.d_pos,
+                                                             dsum, d_sum);
+    }
+    if (e1) cudaEventRecord(e1, st);   // the autotuner times the kernel with its reduction
     return check_launch(ctx, "split-BF16 triple sums");
 }
 
 abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields, int32_t n_trip,
                             const int32_t *d_ijk, double *d_sum) {
     if (n_trip == 0) return ABS_OK;
-    TcGeom G;
-    G.nb = s.nb;
-    G.NP = (int)cdiv(std::max(s.nb, 16), 16) * 16;
-    if (3 * G.NP > TMEM_COLS) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 accumulators exceed tensor memory");
-    G.tmem_cols = TMEM_COLS;
-    G.P = (int64_t)s.N * s.N;
-    G.n_trip = n_trip;
-    const int max_rows = (int)std::min<int64_t>(n_trip, (int64_t)s.nb * (s.nb + 1) / 2);
-    const int tiles = (int)cdiv(max_rows, TM);
-    Setup &ms = const_cast<Setup &>(s);
+    const int64_t P = (int64_t)s.N * s.N;
+    const int64_t P_pad = cdiv(P, KC) * KC;
     const bool canonical = d_ijk == s.d_ijk;
-    if (canonical && ms.tc_groups < 0) ms.tc_groups = canonical_groups(s, G.NP, GMAX);
-    const int tc_groups = canonical ? ms.tc_groups : tiles;   // lists given by the caller are not grouped
-    // the candidate shapes: every chunk width that fits, each with a tile per CTA and grouped
-    std::vector<TcLaunch> cand;
-    for (int kc : {128, 96, 64})
-        for (bool grp : {false, true}) {
-            TcLaunch L;
-            if ((!grp || tc_groups < tiles) && tc_shape(G, kc, grp, tiles, tc_groups, s.nb, ctx->sm_count, L))
-                cand.push_back(L);
-        }
-    if (cand.empty()) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 stages do not fit shared memory");
-    int64_t max_split = 1;
-    for (const TcLaunch &L : cand) max_split = std::max<int64_t>(max_split, cdiv(G.P, L.G.per_split));
-    double *partial = (double *)workspace(ctx, "tc.partial", sizeof(double) * max_split * n_trip);
-    if (!partial) return fail(ctx, ABS_ERR_OOM, "split-BF16 workspace");
-    // The shape: measured on this configuration's first eager call (autotuner), else
-    // the model: the widest chunk, grouped or one tile a CTA by a count of CTA waves x
-    // work per CTA in tenths of a tile's chunk step (per chunk 10 per tile plus 3 for
-    // bringing the chunk in, 80 per tile for its epilogue; fitted to same-GPU timings).
-    auto model = [&]() {
-        const TcLaunch *one = nullptr, *grp = nullptr;
-        for (const TcLaunch &L : cand) {
-            if (L.KC != cand[0].KC) continue;
-            (L.grouped ? grp : one) = &L;
-        }
-        auto makespan = [&](const TcLaunch &L) {
-            const int per_group = (int)cdiv(tiles, L.groups);
-            const int64_t ctas = L.groups * cdiv(G.P, L.G.per_split);
-            return cdiv(ctas, ctx->sm_count) * (cdiv(L.G.per_split, L.KC) * (10 * per_group + 3) + 80 * per_group);
-        };
-        if (grp && (!one || makespan(*grp) < makespan(*one))) return *grp;
-        return *one;
-    };
     abs_ctx *root = ctx->parent ? ctx->parent : ctx;
-    const TcLaunch *pick = nullptr;
+    // the plans: the canonical list's, one per column budget (kept by the setup), or the caller's
+    // list read back and planned (one synchronisation)
+    TcPlanDev caller;
+    std::vector<std::pair<int, const TcPlanDev *>> plans;
     if (canonical) {
-        auto it = root->tc_shapes.find(s.key);
-        if (it != root->tc_shapes.end())
-            for (const TcLaunch &L : cand)
-                if (L.KC == it->second.kc && L.grouped == it->second.grouped) pick = &L;
+        for (int b : BUDGETS)
+            if (const TcPlanDev *pd = canonical_plan(s, b)) plans.push_back({b, pd});
+        if (plans.empty()) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16: no tiling fits the tensor memory");
+    } else {
+        std::vector<int32_t> h((size_t)3 * n_trip);
+        if (cudaMemcpyAsync(h.data(), d_ijk, sizeof(int32_t) * h.size(), cudaMemcpyDeviceToHost, ctx->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, ABS_ERR_CUDA, "split-BF16: reading the triplet list back");
+        }
+        if (!tc_plan(h.data(), n_trip, s.nb, BUDGETS[0], SMEM_BUDGET / 2, caller.h))
+            return fail(ctx, ABS_ERR_INVALID_ARG, "split-BF16: triplet list outside i <= j <= k < n_bins");
+        caller.d_sets = (TcSet *)workspace(ctx, "tc.sets", sizeof(TcSet) * caller.h.sets.size());
+        caller.d_tiles = (TcTile *)workspace(ctx, "tc.tiles", sizeof(TcTile) * caller.h.tiles.size());
+        caller.d_rowjk = (short2 *)workspace(ctx, "tc.rowjk", sizeof(short2) * caller.h.rowjk.size());
+        caller.d_pos = (int64_t *)workspace(ctx, "tc.pos", sizeof(int64_t) * caller.h.pos.size());
+        if (!caller.d_sets || !caller.d_tiles || !caller.d_rowjk || !caller.d_pos)
+            return fail(ctx, ABS_ERR_OOM, "split-BF16 plan");
+        cudaMemcpy(caller.d_sets, caller.h.sets.data(), sizeof(TcSet) * caller.h.sets.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(caller.d_tiles, caller.h.tiles.data(), sizeof(TcTile) * caller.h.tiles.size(),
+                   cudaMemcpyHostToDevice);
+        cudaMemcpy(caller.d_rowjk, caller.h.rowjk.data(), sizeof(short2) * caller.h.rowjk.size(),
+                   cudaMemcpyHostToDevice);
+        cudaMemcpy(caller.d_pos, caller.h.pos.data(), sizeof(int64_t) * caller.h.pos.size(), cudaMemcpyHostToDevice);
+        plans.push_back({BUDGETS[0], &caller});
     }
-    TcLaunch chosen;
-    if (pick) {
-        chosen = *pick;
+    // the three planes, with room for every plan's windows
+    int nbp = s.nb;
+    for (const auto &pp : plans) nbp = std::max(nbp, pp.second->h.plane_rows);
+    nbp = (int)cdiv(nbp, 8) * 8;
+    const size_t plane = (size_t)nbp * P_pad;
+    __nv_bfloat16 *hi = (__nv_bfloat16 *)workspace(ctx, "tc.hi", sizeof(__nv_bfloat16) * plane);
+    __nv_bfloat16 *lo = (__nv_bfloat16 *)workspace(ctx, "tc.lo", sizeof(__nv_bfloat16) * plane);
+    float *f32 = (float *)workspace(ctx, "tc.f32", sizeof(float) * plane);
+    if (!hi || !lo || !f32) return fail(ctx, ABS_ERR_OOM, "split-BF16 planes");
+    {
+        StageTimer timer(ctx, "tc_split");
+        k_split_fields<<<(int)cdiv((int64_t)plane / 4, 256), 256, 0, ctx->stream>>>(s.nb, nbp, P, P_pad, d_fields, hi,
+                                                                                     lo, f32);
+    }
+    {
+        const abs_status sl = check_launch(ctx, "split-BF16 planes");
+        if (sl != ABS_OK) return sl;
+    }
+    const TcPlanes planes{hi, lo, f32, nbp};
+    if (!canonical) return tc_run(ctx, s, caller, TcShapeSel{}, planes, P_pad, n_trip, d_sum, nullptr, nullptr);
+    // the canonical list: the shape measured on this configuration's first eager call
+    // (every budget x item length timed twice, kernel and reduction, the faster kept),
+    // else the first budget that plans with the middle item length
+    auto it = root->tc_shapes.find(s.key);
+    TcShapeSel pick;
+    pick.budget = plans[0].first;
+    if (it != root->tc_shapes.end() && it->second.budget > 0) {
+        pick.budget = it->second.budget;
+        pick.waves = it->second.waves;
     } else {
         cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
         cudaStreamIsCapturing(ctx->stream, &cs);
-        const bool tune = canonical && root->autotune && !ctx->profiling && cs == cudaStreamCaptureStatusNone &&
-                          ctx->stream != nullptr && cand.size() > 1;
-        chosen = model();
+        const bool tune = root->autotune && !ctx->profiling && cs == cudaStreamCaptureStatusNone &&
+                          ctx->stream != nullptr;
         if (tune) {
             cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+                cudaGetLastError();
+                if (e0) cudaEventDestroy(e0);
+                return fail(ctx, ABS_ERR_CUDA, "autotuner events");
+            }
             float best = 1e30f;
-            if (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess) {
-                for (const TcLaunch &L : cand) {
+            for (const auto &pp : plans)
+                for (int w = 1; w <= 3; ++w) {
+                    const TcShapeSel c{pp.first, w};
                     float ms_min = 1e30f;
-                    for (int rep = 0; rep < 2; ++rep) {   // the first run warms caches and the code
-                        const abs_status rs = tc_run(ctx, s, L, d_fields, n_trip, d_ijk, max_rows, tiles, partial,
-                                                     e0, e1);
+                    for (int rep = 0; rep < 2; ++rep) {
+                        const abs_status rs = tc_run(ctx, s, *pp.second, c, planes, P_pad, n_trip, d_sum, e0, e1);
                         if (rs != ABS_OK) {
                             cudaEventDestroy(e0);
                             cudaEventDestroy(e1);
@@ -954,31 +974,25 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
                     }
                     if (ms_min < best) {
                         best = ms_min;
-                        chosen = L;
+                        pick = c;
                     }
                 }
-            }
-            if (e0) cudaEventDestroy(e0);
-            if (e1) cudaEventDestroy(e1);
-            cudaGetLastError();
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
         }
-        if (canonical && (tune || !root->autotune || cand.size() == 1)) {
+        if (tune || !root->autotune) {
             abs_ctx::TcShape &c = root->tc_shapes[s.key];
-            c.kc = chosen.KC;
-            c.grouped = chosen.grouped;
+            c.kc = KC;
+            c.budget = pick.budget;
+            c.waves = pick.waves;
             c.measured = tune;
+            const TcPlanDev *pd = canonical_plan(s, pick.budget);
+            c.grouped = pd && pd->h.sets.size() < pd->h.tiles.size();
         }
     }
-    const abs_status rs = tc_run(ctx, s, chosen, d_fields, n_trip, d_ijk, max_rows, tiles, partial, nullptr, nullptr);
-    if (rs != ABS_OK) return rs;
-    const int64_t nsplit = cdiv(G.P, chosen.G.per_split);
-    {
-        StageTimer timer(ctx, "triple_reduce");
-        k_tc_reduce<<<(int)cdiv(n_trip, 32), 256, 0, ctx->stream>>>(n_trip, (int)nsplit,
-                                                                   1.0 / ((double)s.N * (double)s.N), partial,
-                                                                   d_sum);
-    }
-    return check_launch(ctx, "split-BF16 triple sums");
+    const TcPlanDev *pd = canonical_plan(s, pick.budget);
+    if (!pd) return fail(ctx, ABS_ERR_OOM, "split-BF16 plan");
+    return tc_run(ctx, s, *pd, pick, planes, P_pad, n_trip, d_sum, nullptr, nullptr);
 }
 
 }  // namespace absk
