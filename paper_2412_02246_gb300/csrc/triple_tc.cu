@@ -73,14 +73,11 @@ constexpr int NT = (NFORM + 2) * 32; // threads per CTA
 // each) and warps are dealt to them in turn, so the scheduler with the most warps
 // (3 of 10, or 5 of 18) bounds it, in steps of 8
 #define TC_MAXREG (NFORM == 8 ? 168 : 96)
-constexpr int MAX_TILES = 16;        // tiles per set
+constexpr int MAX_TILES = 2;         // tiles per set (their A buffers for two chunks fit tensor memory)
 constexpr int MAX_STAGES = 8;
 constexpr int TMEM_COLS = 512;
 constexpr int A_COLS = 64;           // one A buffer: 32 columns of hi pairs, 32 of lo pairs
-#ifndef ABS_TC_ABUF
-#define ABS_TC_ABUF 4
-#endif
-constexpr int NABUF = ABS_TC_ABUF;   // A buffers: formers run up to NABUF - 1 tiles ahead of the MMAs
+constexpr int NABUF = 2 * MAX_TILES; // A buffers: every tile of two chunks (formers one chunk ahead)
 constexpr int BOX_ROWS = 16;         // rows per TMA box (window sizes are multiples of it)
 #ifndef ABS_TC_DRAIN
 #define ABS_TC_DRAIN 8
@@ -257,8 +254,7 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                                                      float *__restrict__ partial, int *__restrict__ next_item,
                                                      int32_t *__restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full[MAX_STAGES], empty[MAX_STAGES], a_full[NABUF], a_empty[NABUF], d_full[2],
-        d_empty[2], fin;
+    __shared__ __align__(8) uint64_t full[MAX_STAGES], done[MAX_STAGES], a_full[2], d_full[2], d_empty[2], fin;
     __shared__ uint32_t tmem_holder;
     __shared__ volatile int abort_s;
     __shared__ int item_s;
@@ -275,13 +271,10 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
         abort_s = 0;
         for (int s = 0; s < G.n_stages; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
-            mbar_init(smem_u32(&empty[s]), 1);
-        }
-        for (int b = 0; b < NABUF; ++b) {
-            mbar_init(smem_u32(&a_full[b]), NFORM);
-            mbar_init(smem_u32(&a_empty[b]), 1);
+            mbar_init(smem_u32(&done[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&a_full[b]), NFORM);
             mbar_init(smem_u32(&d_full[b]), 1);
             mbar_init(smem_u32(&d_empty[b]), NFORM);
         }
@@ -300,7 +293,8 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
 
     // role state that lives across items
     int st = 0, su = 0;      // stage and its use (loader, formers and issuer walk the same sequence)
-    int ag = 0;              // A steps so far (buffer ag % NABUF, its use ag / NABUF)
+    int cg = 0;              // chunks so far (A buffer pair cg & 1, its use cg >> 1)
+    int st2[2] = {0, 0}, su2[2] = {0, 0};   // formers: stage and use of the chunks cg - 2, cg - 1
     int grp = 0;             // accumulation groups so far (region grp & 1, its use grp >> 1)
     int issued = 0;          // stages the loader filled (for the drain)
     float accl[MAXSLOT];     // formers: this thread's long accumulators (FP32, rounded to nearest)
@@ -357,7 +351,7 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
             // ---------------- loader
             if (lane == 0) {
                 for (int c = 0; c < nchunks; ++c) {
-                    if (su > 0 && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((su - 1) & 1), &abort_s)) {
+                    if (su > 0 && !mbar_wait(smem_u32(&done[st]), (uint32_t)((su - 1) & 1), &abort_s)) {
                         abort_s = 1;
                         break;
                     }
@@ -396,17 +390,16 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                     // start-address field (16-byte units: 8 per ring row, 2 per 16 pixels)
                     const uint32_t bh = smem_u32(smem + (size_t)st * G.stage_bytes);
                     const uint64_t dh0 = desc_sw128(bh), dl0 = desc_sw128(bh + (uint32_t)b_bytes);
-                    bool step_ok = true;
+                    // the chunk's A buffers (every tile of the set), formed one chunk ahead
+                    if (!mbar_wait(smem_u32(&a_full[cg & 1]), (uint32_t)((cg >> 1) & 1), &abort_s)) {
+                        abort_s = 1;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     for (int t = 0; t < S.ntiles; ++t) {
-                        const int buf = ag % NABUF, use = ag / NABUF;
-                        if (!mbar_wait(smem_u32(&a_full[buf]), (uint32_t)(use & 1), &abort_s)) {
-                            step_ok = false;
-                            break;
-                        }
-                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                         const uint32_t idesc = make_idesc(TM, t_n[t]);
                         const uint32_t acc = tmem + region + (uint32_t)t_col[t];
-                        const uint32_t a_hi = tmem + (uint32_t)(buf * A_COLS), a_lo = a_hi + 32;
+                        const uint32_t a_hi = tmem + (uint32_t)(((cg & 1) * MAX_TILES + t) * A_COLS), a_lo = a_hi + 32;
                         const uint64_t rows = (uint64_t)(t_ilo[t] - S.b_lo) * 8u;
 #pragma unroll
                         for (int ks = 0; ks < KC / 16; ++ks) {
@@ -416,14 +409,10 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                             mma_ts(acc, a_hi + 8u * ks, dl, idesc, 1u);
                             mma_ts(acc, a_lo + 8u * ks, dh, idesc, 1u);
                         }
-                        mma_commit(smem_u32(&a_empty[buf]));
-                        ++ag;
                     }
-                    if (!step_ok) {
-                        abort_s = 1;
-                        break;
-                    }
-                    mma_commit(smem_u32(&empty[st]));
+                    // one commit a chunk: its MMAs done frees the stage and the chunk's A buffers
+                    mma_commit(smem_u32(&done[st]));
+                    ++cg;
                     if (++st == G.n_stages) {
                         st = 0;
                         ++su;
@@ -454,15 +443,17 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                     // the F window, and this thread's first 16-byte unit (FPX pixels from h * FPX)
                     const uint8_t *F = smem + (size_t)st * G.stage_bytes + 2 * b_bytes;
                     const int cc0 = (h * FPX) / 4;
+                    // the A buffers of this chunk's pair were read by the MMAs of chunk cg - 2
+                    if (cg >= 2 &&
+                        !mbar_wait(smem_u32(&done[st2[cg & 1]]), (uint32_t)(su2[cg & 1] & 1), &abort_s)) {
+                        fail_f = true;
+                        break;
+                    }
+                    st2[cg & 1] = st;
+                    su2[cg & 1] = su;
                     for (int t = 0; t < S.ntiles; ++t) {
-                        const int buf = ag % NABUF, use = ag / NABUF;
-                        if (use > 0 &&
-                            !mbar_wait(smem_u32(&a_empty[buf]), (uint32_t)((use - 1) & 1), &abort_s)) {
-                            fail_f = true;
-                            break;
-                        }
                         const short2 jk = rows_s[t][row];
-                        const uint32_t ta = lane_base + (uint32_t)(buf * A_COLS + (FPX / 2) * h);
+                        const uint32_t ta = lane_base + (uint32_t)(((cg & 1) * MAX_TILES + t) * A_COLS + (FPX / 2) * h);
                         // 16 pixels at a time: products, hi / lo split, 8 packed pairs of each to tensor memory
 #pragma unroll
                         for (int part = 0; part < FPX / 16; ++part) {
@@ -485,12 +476,12 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                             tmem_st(ta + 8u * part, hi);
                             tmem_st(ta + 32u + 8u * part, lo);
                         }
-                        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-                        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(smem_u32(&a_full[buf]));
-                        ++ag;
                     }
+                    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&a_full[cg & 1]));
+                    ++cg;
                     if (fail_f) break;
                     if (++st == G.n_stages) {
                         st = 0;
