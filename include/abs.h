@@ -336,19 +336,20 @@ abs_status abs_simulate_vis(abs_ctx *ctx, int32_t m, double dtheta, const float 
 /* Autotuner of the split-BF16 triple-sum kernel (Sec. 2, Eq. estimator_t on
  * tensor cores).  On the first call of a configuration that runs eagerly (not
  * under stream capture, not while the stage profiler runs) with the canonical
- * triplet list, every feasible launch shape (pixel chunk of 128, 96 or 64
- * pixels; one row tile per CTA or groups of row tiles sharing each field
- * chunk) is timed twice on the call's own fields and the fastest is kept, by
+ * triplet list, every launch shape (accumulator columns a work item of 128 or
+ * 96, times work items of about 1, 2 or 3 per SM) is timed twice on the
+ * call's own fields, kernel and reduction, and the fastest is kept, by
  * configuration, for the context and its batch lanes (an abs_estimate_batched
  * call with an untuned split-BF16 item runs its items one after another for
  * that call).  The ring transforms' pass split (lines per CTA of the column
  * and the row pass) is tuned the same way, per configuration and input form.
  * Tuning synchronises the stream on that first call.  With the autotuner off
- * the shapes come from cost models.
+ * the shapes come from cost models (128 columns, about 2 items per SM).
  * abs_autotune(ctx, 0 | 1) turns it off / on (on by default); shapes already
- * chosen are kept.  abs_tuned_shape writes the shape chosen for cfg: *kc the
- * chunk width (0: none yet), *grouped 1 for grouped row tiles, *measured 1 if
- * the autotuner timed it (0: the cost model).  Any output pointer may be NULL. */
+ * chosen are kept.  abs_tuned_shape writes the shape chosen for cfg: *set_cols
+ * the accumulator columns of a work item (0: none chosen yet), *waves the work
+ * items per SM, *measured 1 if the autotuner timed it (0: the cost model).  Any
+ * output pointer may be NULL. */
 abs_status abs_autotune(abs_ctx *ctx, int32_t enable);
 
 /* Failure detection check: one kernel waits on a device flag of the context
@@ -364,7 +365,8 @@ abs_status abs_probe_timeout(abs_ctx *ctx, int32_t max_polls);
  * for them), so the calls that need them return ABS_ERR_OOM; later calls
  * allocate normally.  count >= 0 (0 turns it off). */
 abs_status abs_inject_alloc_failures(abs_ctx *ctx, int32_t count);
-abs_status abs_tuned_shape(abs_ctx *ctx, const abs_config *cfg, int32_t *kc, int32_t *grouped, int32_t *measured);
+abs_status abs_tuned_shape(abs_ctx *ctx, const abs_config *cfg, int32_t *set_cols, int32_t *waves,
+                           int32_t *measured);
 
 #ifdef __cplusplus
 }

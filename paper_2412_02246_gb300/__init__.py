@@ -338,11 +338,12 @@ class Context:
         _check(load().abs_autotune(self.h, 1 if on else 0), self.h, "abs_autotune")
 
     def tuned_shape(self, cfg: "Config") -> dict:
-        """The split-BF16 launch shape chosen for cfg: chunk width (0: none yet), grouped, measured."""
-        kc, gr, me = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        _check(load().abs_tuned_shape(self.h, cfg.ref(), ctypes.byref(kc), ctypes.byref(gr), ctypes.byref(me)),
+        """The split-BF16 launch shape chosen for cfg: accumulator columns of a work item
+        (0: none chosen yet), work items per SM, and whether the autotuner timed it."""
+        sc, wv, me = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().abs_tuned_shape(self.h, cfg.ref(), ctypes.byref(sc), ctypes.byref(wv), ctypes.byref(me)),
                self.h, "abs_tuned_shape")
-        return {"kc": kc.value, "grouped": bool(gr.value), "measured": bool(me.value)}
+        return {"set_cols": sc.value, "waves": wv.value, "measured": bool(me.value)}
 
     def profile_read(self) -> dict:
         """{stage: (total ms, launches)} accumulated since profile(True); waits for the stream."""

@@ -106,8 +106,9 @@ struct abs_ctx {
     // first eager call, by configuration key; kept by the root context (lanes share it)
     bool autotune = true;
     int32_t fail_allocs = 0;         // test hook: this many workspace allocations fail next
-    // budget: accumulator columns per set; waves: work items per CTA (pixel ranges x sets / SMs)
-    struct TcShape { int kc = 0; bool grouped = false; bool measured = false; int budget = 0; int waves = 0; };
+    // split-BF16 launch shape. budget: accumulator columns per set; waves: work items
+    // per CTA (pixel ranges x sets / SMs)
+    struct TcShape { bool measured = false; int budget = 0; int waves = 0; };
     std::map<std::string, TcShape> tc_shapes;
     std::map<std::string, std::pair<int, int>> fft_shapes;   // lines per CTA: column pass, row pass
     std::vector<abs_ctx *> lanes;
@@ -216,5 +217,36 @@ struct StageTimer {
 
 // --------------------------------------------------------------------------- helpers
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Lets `kernel` take dynamic shared memory up to the current device's opt-in
+// limit less its static shared memory; false when `bytes` is above that or the
+// attribute is refused.  The
+// attribute belongs to the function, not to a launch: set per call to that
+// call's own size, it would go down again for a later configuration while a
+// graph captured earlier still holds launches of the larger size, and any
+// replay that checks a node against the function (a profiler relaunching the
+// nodes one by one does) would refuse them.  It is therefore only ever raised,
+// to the limit.
+template <class K>
+inline bool allow_smem(K kernel, size_t bytes) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int limit = optin - (int)fa.sharedSizeBytes;
+    if (limit < 0 || bytes > (size_t)limit) return false;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
 
 }  // namespace absk

@@ -594,13 +594,14 @@ abs_status abs_autotune(abs_ctx *ctx, int32_t enable) {
     return ABS_OK;
 }
 
-abs_status abs_tuned_shape(abs_ctx *ctx, const abs_config *cfg, int32_t *kc, int32_t *grouped, int32_t *measured) {
+abs_status abs_tuned_shape(abs_ctx *ctx, const abs_config *cfg, int32_t *set_cols, int32_t *waves,
+                           int32_t *measured) {
     if (!ctx || !cfg || !cfg->ell_edges || cfg->n_bins < 1 || cfg->n_bins > ABS_MAX_BINS)
         return ABS_ERR_INVALID_ARG;
     auto it = ctx->tc_shapes.find(setup_key(cfg));
     const bool have = it != ctx->tc_shapes.end();
-    if (kc) *kc = have ? it->second.kc : 0;
-    if (grouped) *grouped = have && it->second.grouped ? 1 : 0;
+    if (set_cols) *set_cols = have ? it->second.budget : 0;
+    if (waves) *waves = have ? it->second.waves : 0;
     if (measured) *measured = have && it->second.measured ? 1 : 0;
     return ABS_OK;
 }

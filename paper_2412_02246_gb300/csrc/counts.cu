@@ -645,7 +645,7 @@ template <bool SMEM>
 void launch_pairs(abs_ctx *ctx, const CountGeom &G, int blocks, int threads, size_t smem, const int4 *items,
                   const int *n_items, int *next, const Fams &fam, const uint8_t *map,
                   unsigned long long *const *tab, const GatherArgs &ga) {
-    cudaFuncSetAttribute(k_count_pairs<SMEM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_smem(k_count_pairs<SMEM>, smem);
     k_count_pairs<SMEM><<<blocks, threads, smem, ctx->stream>>>(G, items, n_items, next, fam, map, tab[0], tab[1],
                                                                tab[2], tab[3], tab[4], ga);
 }
@@ -672,10 +672,10 @@ abs_status launch_counts(abs_ctx *ctx, const Setup &s, const uint8_t *d_mask, in
     // resident CTAs an SM (shared memory, threads and registers), for the persistent grid
     int per_sm = 1;
     if (map_smem) {
-        cudaFuncSetAttribute(k_count_pairs<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_smem(k_count_pairs<true>, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_pairs<true>, threads, smem);
     } else {
-        cudaFuncSetAttribute(k_count_pairs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_smem(k_count_pairs<false>, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_pairs<false>, threads, smem);
     }
     per_sm = std::max(per_sm, 1);

@@ -491,13 +491,13 @@ abs_status run_fft_as(abs_ctx *ctx, const Setup &s, const Src &src, float *d_fie
     const float4 *tw = A::table(s.d_tw, s.N);
     auto cols = [&](int cb) {
         const size_t sm = line * 2 * cb;
-        cudaFuncSetAttribute(k_fft_cols<Src, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        allow_smem(k_fft_cols<Src, A>, sm);
         k_fft_cols<Src, A><<<dim3((unsigned)cdiv(2 * s.R + 1, cb), npairs), FFT_NT, sm, st>>>(G, P, cb, s.d_q,
                                                                                              s.d_Rm, src, tw, W);
     };
     auto rows = [&](int rb) {
         const size_t sm = line * 2 * rb;
-        cudaFuncSetAttribute(k_fft_rows<A>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        allow_smem(k_fft_rows<A>, sm);
         k_fft_rows<A><<<dim3((unsigned)cdiv(s.N, rb), npairs), FFT_NT, sm, st>>>(G, P, rb, s.d_Rm, W, tw, d_fields);
     };
     // Autotuner: lines per CTA of each pass, measured on the configuration's first eager

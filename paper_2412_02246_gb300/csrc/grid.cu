@@ -740,8 +740,7 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
     cudaStream_t st = ctx->stream;
     StageTimer timer(ctx, "grid_plan");
     const size_t ssmem0 = scatter_smem(nbins0), ssmem = scatter_smem(1 << dw);
-    cudaFuncSetAttribute(k_radix_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)std::max(ssmem0, ssmem));
+    allow_smem(k_radix_scatter, std::max(ssmem0, ssmem));
     const uint32_t dmask = passes == 1 ? 0xffffffffu : (uint32_t)((1 << dw) - 1);
     k_plan_keys<<<b.nchunks, KT, 0, st>>>(G, n_vis, (const float2 *)d_uv, b.keys, key_none, nbins0, dmask,
                                           b.nchunks, b.rhist);
@@ -786,7 +785,7 @@ abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, c
     if (n_vis > 0) {
         StageTimer timer(ctx, "grid");
         const int blocks = (int)std::min<int64_t>(cdiv(n_vis, UMAX), ctx->sm_count * 3);
-        cudaFuncSetAttribute(k_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GRID_SMEM);
+        allow_smem(k_grid, GRID_SMEM);
         k_grid<<<blocks, GT, GRID_SMEM, st>>>(G, n_vis, plan_key_none(b), b.s_uv, b.s_idx, (const float2 *)d_vis,
                                            acc, acc + cells, acc + 2 * cells);
     }

@@ -313,7 +313,7 @@ abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_field
     const int64_t nsplit = tp.nsplit;
     double *partial = (double *)workspace(ctx, "triple.partial", sizeof(double) * nsplit * n_trip);
     if (!partial) return fail(ctx, ABS_ERR_OOM, "triple-sum workspace");
-    cudaFuncSetAttribute(k_triple_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem);
+    allow_smem(k_triple_fp32, tp.smem);
     {
         StageTimer timer(ctx, "triple_fp32");
         k_triple_fp32<<<dim3((unsigned)nsplit, tp.tgroups), tp.threads, tp.smem, ctx->stream>>>(tp.G, d_fields,
@@ -338,7 +338,7 @@ abs_status launch_bana_sums(abs_ctx *ctx, const Setup &s, const float *d_P, cons
     double *partial = (double *)workspace(ctx, "bana.partial", sizeof(double) * nsplit * n_trip);
     double *sum = (double *)workspace(ctx, "bana.sum", sizeof(double) * n_trip);
     if (!partial || !sum) return fail(ctx, ABS_ERR_OOM, "prediction workspace");
-    cudaFuncSetAttribute(k_triple_bana, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem);
+    allow_smem(k_triple_bana, tp.smem);
     StageTimer timer(ctx, "bana_sums");
     k_triple_bana<<<dim3((unsigned)nsplit, tp.tgroups), tp.threads, tp.smem, ctx->stream>>>(tp.G, d_P, d_I, d_ijk,
                                                                                          partial);
@@ -417,11 +417,7 @@ extern "C" abs_status abs_triple_sums_static(const abs_config *cfg, const float 
     if (!triple_plan(cfg->n_bins, N, n_trip, sms, std::max<int64_t>(1, cap / n_trip), d_fields, tp))
         return ABS_ERR_UNSUPPORTED;
     const int64_t nsplit = tp.nsplit;
-    if (cudaFuncSetAttribute(k_triple_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tp.smem) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return ABS_ERR_CUDA;
-    }
+    if (!allow_smem(k_triple_fp32, tp.smem)) return ABS_ERR_CUDA;
     // each launch's own status (an error left over from the caller's earlier work is not ours to report)
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)nsplit, tp.tgroups);

@@ -12,38 +12,58 @@
 // (Al Bl is below the FP32 resolution of the sum).
 //
 // Layout.  The fields are split once per estimate (k_split_fields) into three
-// planes with a row pitch of P_pad = P rounded up to 64 pixels (zeros past P):
-// BF16 hi, BF16 lo and an FP32 copy.  Rows (j, k) are taken in (j, k) order and
-// cut into tiles of 128; a tile's MMA N covers the rings i of all its rows
-// (from the lowest i rounded down to 8, rounded up to 16 columns); inside a
-// tile the rows are ordered by (k, j), so that a warp's 32 rows read few
-// distinct rings when forming A.  Consecutive tiles form a set whose
-// accumulators fit tensor memory beside two A buffers; a work item is one set
-// over one range of pixels, and the items (sets x pixel ranges) are dealt to
-// a persistent grid of one CTA per SM, ranges outermost, so that the sets that
-// read the same pixels run at about the same time and share them in L2.
+// chunk-blocked planes [P_pad / 64][nbp][64] (P_pad = P rounded up to 64
+// pixels, zeros past P and past the last ring): BF16 hi, BF16 lo and an FP32
+// copy, each row already in the 128-byte swizzle the kernel reads it in, so
+// that a window of consecutive rings of one chunk is one contiguous bulk copy
+// (cp.async.bulk) that lands in shared memory ready for use.
 //
-// Per 64-pixel chunk, three roles and three kinds of mbarrier:
-//   loader (warp 0)    TMA copies of the chunk into a shared-memory stage: the
-//                      set's window of rings of the hi and lo planes (the MMA
-//                      operand B, 128-byte swizzled K-major: 64 BF16 pixels a
-//                      row) and the window of rings its rows form A from (FP32,
-//                      two 32-pixel boxes, 128-byte swizzled), in 16-row boxes,
-//                      counted on full[s];
-//   formers (warps 2-9) per tile of the set: thread = one row (its tensor-memory
-//                      lane) and 32 of the 64 pixels; A = D_j D_k in FP32, split,
-//                      packed in BF16 pairs and stored to an A buffer in tensor
-//                      memory (tcgen05.st), then a_full[buf];
-//   MMA issuer (warp 1) per tile: 4 K-steps x 3 MMAs (A from tensor memory,
-//                      B from the stage), M = 128, N = the tile's ring columns,
-//                      committed to a_empty[buf] (the A buffer is free again),
-//                      after the chunk's last tile to empty[s] (the stage is free),
-//                      after the item's last chunk to acc_full.
-// The formers then read the accumulators back (tcgen05.ld) and write them,
-// column-major by tile (lanes contiguous), to the item's pixel range of the
-// partial-sum array, and release the accumulators (acc_empty).  A second
-// kernel adds the pixel ranges in FP64 in a fixed order and gathers each
+// Rows (j, k) are taken in (j, k) order and cut into blocks of 128 rows; inside
+// a block the rows are ordered by (k, j), so that a warp's 32 rows read few
+// distinct rings when forming A.  A block's ring columns i (from its lowest i
+// rounded down to 8, rounded up to 16) are cut into column tiles of at most
+// 128 (the MMA N).  Consecutive tiles form a set of at most two whose
+// accumulator columns stay within a budget (autotuned, at most 128); a work item
+// is one set over one range of pixels, and a persistent grid of one CTA per SM
+// takes items from a queue (one atomic counter), ranges outermost, so that the
+// sets that read the same pixels run at about the same time and share them in L2.
+//
+// Per 64-pixel chunk c of an item, three roles and their mbarriers:
+//   loader (warp 0)    bulk copies of chunk c into stage s = c mod n_stages:
+//                      the set's window of rings of the hi and lo planes (the
+//                      MMA operand B, K-major, 128-byte swizzle) and the window
+//                      of rings its rows form A from (FP32), counted on full[s];
+//                      it reuses stage s once done[s] says chunk c - n_stages has
+//                      finished with it;
+//   formers (warps 2..) thread = one row (its tensor-memory lane) and 64 / FQ
+//                      of the 64 pixels (32 with eight forming warps), for every tile
+//                      of the set: A = D_j D_k in FP32, split, packed in BF16
+//                      pairs and stored to A buffer (c & 1) of the tile in
+//                      tensor memory (tcgen05.st); one arrival on a_full[c & 1]
+//                      a warp per chunk.  Buffer (c & 1) is free again once
+//                      done[] of chunk c - 2 has completed;
+//   MMA issuer (warp 1) per tile, 4 K-steps x 3 MMAs (A from tensor memory, B
+//                      from the stage), M = 128, N = the tile's ring columns,
+//                      into accumulation region (g & 1) of group g = c / DRAIN;
+//                      one tcgen05.commit per chunk to done[s] (the stage and
+//                      the A buffers of chunk c are free), and at the end of
+//                      a group one to d_full[g & 1].
+// Tensor-core accumulation in FP32 over long pixel ranges loses accuracy (the
+// error grows with the number of chunks summed into one accumulator), so every
+// DRAIN chunks the formers read the group's region back (tcgen05.ld) into FP32
+// registers, one long accumulator per (row, column) a thread owns, and release
+// it (d_empty); the issuer meanwhile fills the other region.  After the item's
+// last chunk the formers write the long accumulators, column-major by tile
+// (lanes contiguous), to the item's pixel range of the partial-sum array.  A
+// second kernel adds the pixel ranges in FP64 in a fixed order and gathers each
 // triplet's entry.
+//
+// Rates that shaped this design, measured on GB300 with microbenchmarks: an MMA
+// of M = 128, K = 16 costs max(45.5, N / 2) cycles of the tensor pipe, with A in
+// tensor or shared memory alike; a tcgen05.commit between short MMAs costs about
+// 270 cycles of issue, hence one per chunk for the whole set; tiled TMA loads
+// of 128-byte rows reached about 26 bytes per clock per SM, contiguous bulk
+// copies of the pre-swizzled blocks about 2.5 times that.
 //
 // Every mbarrier wait is bounded: on timeout the role sets a shared abort flag
 // and leaves; the CTA then waits (bounded) for its copies and MMAs in flight,
@@ -78,7 +98,7 @@ constexpr int MAX_STAGES = 8;
 constexpr int TMEM_COLS = 512;
 constexpr int A_COLS = 64;           // one A buffer: 32 columns of hi pairs, 32 of lo pairs
 constexpr int NABUF = 2 * MAX_TILES; // A buffers: every tile of two chunks (formers one chunk ahead)
-constexpr int BOX_ROWS = 16;         // rows per TMA box (window sizes are multiples of it)
+constexpr int BOX_ROWS = 16;         // window sizes (rings a copy) are multiples of it
 #ifndef ABS_TC_DRAIN
 #define ABS_TC_DRAIN 8
 #endif
@@ -833,10 +853,7 @@ static abs_status tc_run(abs_ctx *ctx, const Setup &s, const TcPlanDev &pd, cons
     int *next = (int *)workspace(ctx, "tc.next", sizeof(int));
     if (!partial || !dsum || !next) return fail(ctx, ABS_ERR_OOM, "split-BF16 workspace");
     const size_t smem = 1024 + (size_t)G.n_stages * G.stage_bytes;
-    if (cudaFuncSetAttribute(k_triple_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16: shared memory attribute refused");
-    }
+    if (!allow_smem(k_triple_tc, smem)) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16: shared memory attribute refused");
     {
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, k_triple_tc) == cudaSuccess && fa.maxThreadsPerBlock < NT)
@@ -973,12 +990,9 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
         }
         if (tune || !root->autotune) {
             abs_ctx::TcShape &c = root->tc_shapes[s.key];
-            c.kc = KC;
             c.budget = pick.budget;
             c.waves = pick.waves;
             c.measured = tune;
-            const TcPlanDev *pd = canonical_plan(s, pick.budget);
-            c.grouped = pd && pd->h.sets.size() < pd->h.tiles.size();
         }
     }
     const TcPlanDev *pd = canonical_plan(s, pick.budget);
