@@ -151,10 +151,25 @@ abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, c
                                   float *d_grid, float *d_wsum, uint8_t *d_mask, bool acc_zeroed = false);
 abs_status launch_filter_fft(abs_ctx *ctx, const Setup &s, const float *d_grid,
                              const float *d_wsum, const uint8_t *d_mask, float *d_fields);
+// The split-BF16 kernel's operands: the fields as three chunk-blocked planes
+// [P_pad / 64][nbp][64] (BF16 hi, BF16 lo, FP32), every 64-pixel row of a ring
+// in the 128-byte swizzle of the tensor-core operand (16-byte units XOR-permuted
+// by ring & 7), zeros past the last pixel and the last ring.
+struct SplitOut {
+    void *hi, *lo;   // __nv_bfloat16
+    float *f32;
+    int nbp;
+    int64_t P_pad;
+};
+// The planes of the canonical triplet list's tiling (workspace of ctx), for the
+// transform to write directly; launch_triple_tc with d_fields == NULL then
+// reads them as they are (clearing only the padding).
+abs_status tc_split_target(abs_ctx *ctx, const Setup &s, SplitOut &out);
 // The same transform fed directly from the FP64 gridding accumulators (mirror
-// applied on the fly), as abs_estimate uses it.
+// applied on the fly), as abs_estimate uses it; with split given (split-BF16
+// precision) the fields go straight into those planes instead of d_fields.
 abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc,
-                                 float *d_fields);
+                                 float *d_fields, const SplitOut *split = nullptr);
 // The I fields of Eq. iFT_I as printed (ABS_W_PAPER_LITERAL): W_g = 1 / (the
 // cell's mirrored weight sum) on filled cells, from the FP64 accumulators.
 abs_status launch_filter_fft_w(abs_ctx *ctx, const Setup &s, const double *acc, float *d_fields);
@@ -171,6 +186,8 @@ abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_field
                               const int64_t *d_count = nullptr, double *d_B = nullptr,
                               cudaEvent_t wait_before_b = nullptr);
 // Split-BF16 tcgen05 form of the same sums (precision == ABS_SPLIT_BF16).
+// d_fields == NULL (canonical list only): the planes of tc_split_target hold
+// the fields already.
 abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
                             int32_t n_trip, const int32_t *d_ijk, double *d_sum);
 // Ring tables (cell lists, byte map) from d_mask, or, with d_accw given, from

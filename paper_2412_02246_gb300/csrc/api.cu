@@ -1,6 +1,9 @@
 // C ABI of libabs: context, argument validation, host-side setup, and the
 // orchestration of the stage kernels (grid.cu, fft.cu, counts.cu, triple.cu).
+#include <algorithm>
 #include <cmath>
+#include <functional>
+#include <map>
 #include <cstdio>
 #include <cstring>
 
@@ -55,13 +58,35 @@ static bool smooth235(int v) {
     return v == 1;
 }
 
+// Radices of the transform passes for a 2,3,5-smooth N: the fewest passes with
+// radices from the in-register DFTs (2, 3, 4, 5 and their products up to 16),
+// ties going to the plan whose smallest radix is largest (fewer idle threads
+// in its widest pass).
 static std::vector<int> radix_plan(int N) {
-    std::vector<int> r;
-    while (N % 4 == 0) { r.push_back(4); N /= 4; }
-    while (N % 2 == 0) { r.push_back(2); N /= 2; }
-    while (N % 3 == 0) { r.push_back(3); N /= 3; }
-    while (N % 5 == 0) { r.push_back(5); N /= 5; }
-    return r;
+    static const int menu[] = {16, 15, 12, 10, 9, 8, 6, 5, 4, 3, 2};
+    std::map<int, std::vector<int>> best;   // by remaining length
+    std::function<const std::vector<int> &(int)> plan = [&](int n) -> const std::vector<int> & {
+        auto it = best.find(n);
+        if (it != best.end()) return it->second;
+        std::vector<int> b;
+        if (n > 1) {
+            bool have = false;
+            for (int r : menu) {
+                if (n % r) continue;
+                std::vector<int> c = plan(n / r);
+                if (c.empty() && n / r != 1) continue;
+                c.insert(c.begin(), r);
+                const int cmin = *std::min_element(c.begin(), c.end());
+                const int bmin = have ? *std::min_element(b.begin(), b.end()) : 0;
+                if (!have || c.size() < b.size() || (c.size() == b.size() && cmin > bmin)) {
+                    b = c;
+                    have = true;
+                }
+            }
+        }
+        return best[n] = b;
+    };
+    return plan(N);
 }
 
 // Validates cfg and derives the ring thresholds q[0..nb], the largest |g_x| of
@@ -721,14 +746,19 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
                                 const float *h_uv = nullptr, const float *h_vis = nullptr) {
     const int64_t cells = (int64_t)s.n * s.n;
     const int64_t P = (int64_t)s.N * s.N;
-    float *fields = (float *)workspace(ctx, "est.fields", sizeof(float) * (size_t)s.nb * P);
-    double *sum = (double *)workspace(ctx, "est.sum", sizeof(double) * std::max(n_trip, 1));
     const bool literal = s.weight_mode == ABS_W_PAPER_LITERAL;
+    // split-BF16 sums over the canonical list: the transform writes the kernel's split
+    // planes directly, and no FP32 fields are kept
+    const bool to_planes = s.precision == ABS_SPLIT_BF16 && d_ijk == s.d_ijk && !literal && n_trip > 0;
+    SplitOut planes{};
+    if (to_planes) ABS_CHECK(tc_split_target(ctx, s, planes));
+    float *fields = to_planes ? nullptr : (float *)workspace(ctx, "est.fields", sizeof(float) * (size_t)s.nb * P);
+    double *sum = (double *)workspace(ctx, "est.sum", sizeof(double) * std::max(n_trip, 1));
     float *ifields = literal ? (float *)workspace(ctx, "est.ifields", sizeof(float) * (size_t)s.nb * P) : nullptr;
     double *sumw = literal ? (double *)workspace(ctx, "est.sumw", sizeof(double) * std::max(n_trip, 1)) : nullptr;
     if (literal && (!ifields || !sumw)) return fail(ctx, ABS_ERR_OOM, "estimate workspace");
     int64_t *count = d_count ? d_count : (int64_t *)workspace(ctx, "est.count", sizeof(int64_t) * std::max(n_trip, 1));
-    if (!fields || !sum || !count) return fail(ctx, ABS_ERR_OOM, "estimate workspace");
+    if ((!fields && !to_planes) || !sum || !count) return fail(ctx, ABS_ERR_OOM, "estimate workspace");
     // the canonical list (d_ijk == NULL at the ABI) was built and checked with the setup
     if (d_ijk != s.d_ijk) ABS_CHECK(launch_check_triplets(ctx, s, n_trip, d_ijk));
     // the first realisation's accumulators are cleared on the side stream while
@@ -781,7 +811,7 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
         }
         double *acc;
         grid_acc_buffers(ctx, s, &acc);
-        const abs_status sf = launch_filter_fft_acc(ctx, s, acc, fields);
+        const abs_status sf = launch_filter_fft_acc(ctx, s, acc, fields, to_planes ? &planes : nullptr);
         if (sf != ABS_OK) {
             if (join) cudaStreamWaitEvent(ctx->stream, join, 0);
             return sf;

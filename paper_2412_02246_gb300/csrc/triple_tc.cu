@@ -604,6 +604,32 @@ __global__ void __launch_bounds__(256) k_split_fields(int nb, int nbp, int64_t P
     *(float4 *)(f32 + of) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
+// The padding of planes the transform wrote directly: rings nb .. nbp-1 of every
+// chunk block, and the pixels past P of the last block's rings (zeros).
+__global__ void __launch_bounds__(256) k_split_pad(int nb, int nbp, int64_t P, int64_t P_pad,
+                                                   __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo,
+                                                   float *__restrict__ f32) {
+    const int64_t nblk = P_pad / KC;
+    const int64_t rows_pad = nblk * (nbp - nb) * KC;   // whole padding rings
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < rows_pad) {
+        const int64_t blk = g / ((int64_t)(nbp - nb) * KC), rem = g - blk * (nbp - nb) * KC;
+        const size_t o = (size_t)(blk * nbp + nb) * KC + rem;
+        hi[o] = __float2bfloat16_rn(0.f);
+        lo[o] = __float2bfloat16_rn(0.f);
+        f32[o] = 0.f;
+        return;
+    }
+    const int64_t t = g - rows_pad;
+    if (t >= (int64_t)nb * KC) return;
+    const int m = (int)(t / KC), u = (int)(t - (int64_t)m * KC), key = m & 7;
+    if ((nblk - 1) * KC + u < P) return;
+    const size_t row = ((size_t)(nblk - 1) * nbp + m) * KC;
+    hi[row + ((((u >> 3) ^ key) << 3) | (u & 7))] = __float2bfloat16_rn(0.f);
+    lo[row + ((((u >> 3) ^ key) << 3) | (u & 7))] = __float2bfloat16_rn(0.f);
+    f32[row + ((((u >> 2) ^ key) << 2) | (u & 3))] = 0.f;
+}
+
 // dense[x] = sum over pixel ranges of partial[r][x] in FP64 (a fixed order).
 __global__ void __launch_bounds__(256) k_tc_reduce(int64_t dense, int n_ranges, const float *__restrict__ partial,
                                                    double *__restrict__ out) {
@@ -881,12 +907,44 @@ static abs_status tc_run(abs_ctx *ctx, const Setup &s, const TcPlanDev &pd, cons
     return check_launch(ctx, "split-BF16 triple sums");
 }
 
+// Planes of nbp rings, in the context's workspace.
+struct PlaneBufs {
+    __nv_bfloat16 *hi, *lo;
+    float *f32;
+};
+static bool tc_plane_buffers(abs_ctx *ctx, int nbp, int64_t P_pad, PlaneBufs &pl) {
+    const size_t plane = (size_t)nbp * P_pad;
+    pl.hi = (__nv_bfloat16 *)workspace(ctx, "tc.hi", sizeof(__nv_bfloat16) * plane);
+    pl.lo = (__nv_bfloat16 *)workspace(ctx, "tc.lo", sizeof(__nv_bfloat16) * plane);
+    pl.f32 = (float *)workspace(ctx, "tc.f32", sizeof(float) * plane);
+    return pl.hi && pl.lo && pl.f32;
+}
+
+// Rings a plane block must hold for the canonical plans: every window of every budget's tiling.
+static int canonical_nbp(const Setup &s) {
+    int nbp = 0;
+    for (int b : BUDGETS)
+        if (const TcPlanDev *pd = canonical_plan(s, b)) nbp = std::max({nbp, s.nb, pd->h.plane_rows});
+    return nbp > 0 ? (int)cdiv(nbp, 8) * 8 : 0;
+}
+
+abs_status tc_split_target(abs_ctx *ctx, const Setup &s, SplitOut &out) {
+    const int nbp = canonical_nbp(s);
+    if (nbp == 0) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16: no tiling fits the tensor memory");
+    const int64_t P_pad = cdiv((int64_t)s.N * s.N, KC) * KC;
+    PlaneBufs pl;
+    if (!tc_plane_buffers(ctx, nbp, P_pad, pl)) return fail(ctx, ABS_ERR_OOM, "split-BF16 planes");
+    out = SplitOut{pl.hi, pl.lo, pl.f32, nbp, P_pad};
+    return ABS_OK;
+}
+
 abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields, int32_t n_trip,
                             const int32_t *d_ijk, double *d_sum) {
     if (n_trip == 0) return ABS_OK;
     const int64_t P = (int64_t)s.N * s.N;
     const int64_t P_pad = cdiv(P, KC) * KC;
     const bool canonical = d_ijk == s.d_ijk;
+    if (!d_fields && !canonical) return fail(ctx, ABS_ERR_INVALID_ARG, "split-BF16: planes without fields need the canonical list");
     abs_ctx *root = ctx->parent ? ctx->parent : ctx;
     // the plans: the canonical list's, one per column budget (kept by the setup), or the caller's
     // list read back and planned (one synchronisation)
@@ -920,25 +978,26 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
         cudaMemcpy(caller.d_pos, caller.h.pos.data(), sizeof(int64_t) * caller.h.pos.size(), cudaMemcpyHostToDevice);
         plans.push_back({BUDGETS[0], &caller});
     }
-    // the three planes, with room for every plan's windows
-    int nbp = s.nb;
-    for (const auto &pp : plans) nbp = std::max(nbp, pp.second->h.plane_rows);
-    nbp = (int)cdiv(nbp, 8) * 8;
+    // the three planes, with room for every plan's windows (the canonical ones: as
+    // tc_split_target sized them)
+    int nbp = canonical ? canonical_nbp(s) : (int)cdiv(std::max(s.nb, caller.h.plane_rows), 8) * 8;
+    PlaneBufs pb;
+    if (!tc_plane_buffers(ctx, nbp, P_pad, pb)) return fail(ctx, ABS_ERR_OOM, "split-BF16 planes");
     const size_t plane = (size_t)nbp * P_pad;
-    __nv_bfloat16 *hi = (__nv_bfloat16 *)workspace(ctx, "tc.hi", sizeof(__nv_bfloat16) * plane);
-    __nv_bfloat16 *lo = (__nv_bfloat16 *)workspace(ctx, "tc.lo", sizeof(__nv_bfloat16) * plane);
-    float *f32 = (float *)workspace(ctx, "tc.f32", sizeof(float) * plane);
-    if (!hi || !lo || !f32) return fail(ctx, ABS_ERR_OOM, "split-BF16 planes");
-    {
+    if (d_fields) {
         StageTimer timer(ctx, "tc_split");
-        k_split_fields<<<(int)cdiv((int64_t)plane / 4, 256), 256, 0, ctx->stream>>>(s.nb, nbp, P, P_pad, d_fields, hi,
-                                                                                     lo, f32);
+        k_split_fields<<<(int)cdiv((int64_t)plane / 4, 256), 256, 0, ctx->stream>>>(
+            s.nb, nbp, P, P_pad, d_fields, pb.hi, pb.lo, pb.f32);
+    } else if (nbp > s.nb || P < P_pad) {
+        StageTimer timer(ctx, "tc_pad");
+        const int64_t n = (P_pad / KC) * (nbp - s.nb) * KC + (int64_t)s.nb * KC;
+        k_split_pad<<<(int)cdiv(n, 256), 256, 0, ctx->stream>>>(s.nb, nbp, P, P_pad, pb.hi, pb.lo, pb.f32);
     }
     {
         const abs_status sl = check_launch(ctx, "split-BF16 planes");
         if (sl != ABS_OK) return sl;
     }
-    const TcPlanes planes{hi, lo, f32, nbp};
+    const TcPlanes planes{pb.hi, pb.lo, pb.f32, nbp};
     if (!canonical) return tc_run(ctx, s, caller, TcShapeSel{}, planes, P_pad, n_trip, d_sum, nullptr, nullptr);
     // the canonical list: the shape measured on this configuration's first eager call
     // (every budget x item length timed twice, kernel and reduction, the faster kept),

@@ -343,12 +343,15 @@ def gpu_fields(ctx, cfg, gwm):
     return f
 
 
-@pytest.mark.parametrize("cfg_id,n_fft,prec", [(0, 0, 0), (0, 96, 0), (0, 135, 0), (1, 0, 0),
-                                               (0, 0, 1), (0, 135, 1), (1, 0, 1)])
+@pytest.mark.parametrize("cfg_id,n_fft,prec", [(0, 0, 0), (0, 96, 0), (0, 135, 0), (1, 0, 0), (1, 576, 0),
+                                               (0, 0, 1), (0, 135, 1), (1, 0, 1), (1, 576, 1), (1, 1024, 1)])
 def test_fields_parity(ctx, cfg_id, n_fft, prec):
     """Ring fields of abs_filter_fft: double-float butterflies on the FP32 path
     (prec 0), plain FP32 ones on the split-BF16 path (prec 1), both within
-    1e-5 of the DFT bound sum |X|."""
+    1e-5 of the DFT bound sum |X|.  The sizes cover two- and three-pass plans
+    with the composite radices 6 to 16 in first, middle and last passes
+    (90 = 10 x 9, 96 = 12 x 8, 135 = 15 x 9, 288 = 8 x 6 x 6, 576 = 9 x 8 x 8,
+    1024 = 16 x 8 x 8)."""
     inp = inputs(cfg_id)
     wl = inp.wl
     cfg = absmod.Config.from_workload(wl, n_fft=n_fft,
