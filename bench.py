@@ -53,7 +53,8 @@ UNIT = "estimates/s"
 KERNELS_PER_STAGE = {"grid_zero": 0, "grid": 1, "grid_finalize": 1, "grid_mask": 1, "ring_lists": 2,
                      "count_items": 1, "count_pairs": 2, "count_gather": 1, "ellbar": 2,
                      "fft_rows": 1, "fft_cols": 1, "triple_fp32": 1, "triple_reduce": 1,
-                     "normalise": 1, "check_triplets": 1, "tc_split": 1, "triple_tc": 1, "tc_reduce": 2}
+                     "normalise": 1, "check_triplets": 1, "tc_split": 1, "tc_pad": 1, "triple_tc": 1,
+                     "tc_reduce": 2}
 
 
 def plan_kernels(n_grid, radius):
@@ -357,7 +358,9 @@ def algorithmic_work(stage, geo):
     fft_cols:    HBM bytes, 24 per filled ring cell read (FP64 re, im, weight sums) and 8 per
                  transformed point written ((2 R_p + 1) N points per ring pair, FP32 complex
                  on the split-BF16 path, 16 B double-float on the FP32 path)
-    fft_rows:    HBM bytes, those points read back and 4 per field value written
+    fft_rows:    HBM bytes, those points read back and, per field value, 4 written (FP32
+                 fields) or 8 (the split-BF16 planes the estimate's row pass writes: BF16 hi
+                 and lo, FP32 copy)
     triple_tc:   BF16 tensor flops, 3 products x 2 flops per (closing triplet, pixel)
     triple_fp32: FP32 flops, 2 per (closing triplet, pixel)
     count_pairs: integer lane-ops, 2 per pair visit of the route the kernel takes
@@ -368,7 +371,7 @@ def algorithmic_work(stage, geo):
     if stage == "fft_cols":
         return "hbm", 24.0 * geo["filled"] + pt * geo["lines"] * geo["N"]
     if stage == "fft_rows":
-        return "hbm", pt * geo["lines"] * geo["N"] + 4.0 * geo["nb"] * P
+        return "hbm", pt * geo["lines"] * geo["N"] + geo.get("field_bytes", 4) * geo["nb"] * P
     if stage == "triple_tc":
         return "tensor", 6.0 * nt * P
     if stage == "triple_fp32":
@@ -423,7 +426,8 @@ def channel_geometry(m, cfg, ctx, items, torch, dev):
     k = len(items)
     return {"pair_visits": visits / k, "filled": fills / k, "n_trip": len(m.abs_triplets(cfg)), "P": N * N,
             "N": N, "nb": cfg.n_bins, "n_vis": int(items[0][1].shape[0]), "cells": n * n,
-            "lines": pair_lines(q, n), "point_bytes": 8 if cfg.precision == m.ABS_SPLIT_BF16 else 16}
+            "lines": pair_lines(q, n), "point_bytes": 8 if cfg.precision == m.ABS_SPLIT_BF16 else 16,
+            "field_bytes": 8 if cfg.precision == m.ABS_SPLIT_BF16 else 4}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -569,8 +573,19 @@ def uneven_extras(m, ctx, batch_inputs, torch, dev, stream, steps):
         ctx.abs_estimate_batched(items)
     ctx.sync()
     t = timed_calls(lambda: ctx.abs_estimate_batched(items), max(2, steps // 2), stream, torch, dev)
+
+    # the same items one after another on the context's stream, each replayed from its own graph
+    def serial():
+        for it in items:
+            ctx.abs_estimate(*it)
+    for _ in range(3):
+        serial()
+    ctx.sync()
+    ts = timed_calls(serial, max(2, steps // 2), stream, torch, dev)
     return {"value": len(items) * len(t) / (sum(t) * 1e-3), "unit": UNIT, "items_per_call": len(items),
             "ms_per_call": sum(t) / len(t),
+            "serial": {"value": len(items) * len(ts) / (sum(ts) * 1e-3), "unit": UNIT, "ms": sum(ts) / len(ts),
+                       "note": "the same items through abs_estimate one after another on one stream"},
             "note": "abs_estimate_batched over the seeded uneven batch: grids {256,512,1024}^2, 1e5-1e6 "
                     "visibilities, 16-48 log l bins, split-BF16, one CUDA graph over four lanes"}
 
@@ -728,7 +743,7 @@ def run_ours(args):
     tc_exec = None
     if "triple_tc" in prof:
         tc_exec = ctx.tuned_shape(cfg)
-    geo32 = dict(geo, point_bytes=16)
+    geo32 = dict(geo, point_bytes=16, field_bytes=4)
     fp32_triple = roofline("triple_fp32", avg_ms("triple_fp32", prof32), geo32, peaks, clk.get("sm_mhz"), sms) \
         if "triple_fp32" in prof32 else None
 

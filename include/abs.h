@@ -64,13 +64,21 @@ typedef enum {
 
 enum { ABS_KERNEL_NGP = 0, ABS_KERNEL_GAUSS = 1 };
 enum { ABS_FP32 = 0, ABS_SPLIT_BF16 = 1 };
-/* Denominator of Eq. estimator_t.  ABS_W_MEAN_UNITMASK: unit-mask I fields
- * (X = 1 on filled cells), so that sum_theta I_i I_j I_k = N^2 T with T the
- * integer count of closed grid triangles and B is the mean of X1 X2 X3 over
- * them.  ABS_W_PAPER_LITERAL: Eq. iFT_I as printed, I fields with W_g = 1 / N_g,
- * N_g read as the cell's weight sum (the divisor of X, Sec. 2), so that
- * B = Re S / (A S_W) with S_W the sum of W1 W2 W3 over the closed triangles. */
-enum { ABS_W_MEAN_UNITMASK = 0, ABS_W_PAPER_LITERAL = 1 };
+/* Weights W_g of Eqs. iFT and iFT_I (Sec. 2).
+ * ABS_W_MEAN_UNITMASK: D fields of the weighted mean X_g = V_g / sum w, unit-mask
+ *   I fields (1 on filled cells), so that sum_theta I_i I_j I_k = N^2 T with T the
+ *   integer count of closed grid triangles and B is the mean of X1 X2 X3 over them.
+ * ABS_W_PAPER_LITERAL: as printed, W_g = 1 / N_g with N_g the number of
+ *   visibilities entered at the cell by Eq. vg (each visibility counts once in
+ *   every cell of its footprint, and once more at the mirror): D fields of
+ *   V_g / N_g, I fields of 1 / N_g.
+ * ABS_W_NOISE: noise-optimised weights for equal, uncorrelated visibility noise
+ *   (Sec. 2): W_g = N_eff,g = (sum w)^2 / sum w^2, the inverse noise variance of
+ *   X_g in units of one visibility's; D fields of N_eff X_g, I fields of N_eff.
+ *   With nearest-grid-point gridding N_eff = N_g and D carries the plain sums V_g.
+ * The two weighted forms give B = Re S / (A S_W), S_W the sum of W1 W2 W3 over the
+ * closed triangles (NaN where it is 0). */
+enum { ABS_W_MEAN_UNITMASK = 0, ABS_W_PAPER_LITERAL = 1, ABS_W_NOISE = 2 };
 
 #define ABS_MAX_BINS 254      /* ring ids fit a byte with one code to spare */
 #define ABS_MAX_RADIUS 3      /* largest Gaussian footprint half-width (cells) */
@@ -91,10 +99,10 @@ typedef struct abs_config {
                                  2^a 3^b 5^c value with 3R+1 <= N <= ABS_MAX_FFT */
     int32_t precision;        /* triple sums: ABS_FP32 or ABS_SPLIT_BF16 */
     double norm_A;            /* A of Eq. estimator_t (> 0; 1 leaves B in grid units) */
-    int32_t weight_mode;      /* ABS_W_MEAN_UNITMASK (default, 0) or ABS_W_PAPER_LITERAL; the literal
-                                 form applies to abs_estimate, abs_estimate_many, abs_estimate_batched
-                                 and abs_estimate_host (d_count is the integer count either way); the
-                                 stage calls give the unit-mask pieces */
+    int32_t weight_mode;      /* ABS_W_MEAN_UNITMASK (default, 0), ABS_W_PAPER_LITERAL or ABS_W_NOISE;
+                                 the weighted forms apply to abs_estimate, abs_estimate_many,
+                                 abs_estimate_batched and abs_estimate_host (d_count is the integer
+                                 count either way); the stage calls give the unit-mask pieces */
 } abs_config;
 
 typedef struct abs_ctx abs_ctx;

@@ -70,7 +70,7 @@ def _load():
     lib.orc_ring_q.restype = None
     lib.orc_triplets.argtypes = [i32, P, i32, P]
     lib.orc_triplets.restype = i32
-    lib.orc_grid.argtypes = [i32, f32, i32, f64, i32, i64, P, P, P, P, P]
+    lib.orc_grid.argtypes = [i32, f32, i32, f64, i32, i64, P, P, P, P, P, P]
     lib.orc_grid.restype = ctypes.c_int
     lib.orc_mean_grid.argtypes = [i32, P, P, P, P, P]
     lib.orc_mean_grid.restype = None
@@ -122,8 +122,9 @@ def triplets(q: np.ndarray) -> np.ndarray:
 @dataclass
 class Grid:
     grid: np.ndarray      # complex128 [n, n] (FFT order), Eq. vg sums incl. mirror
-    wsum: np.ndarray      # float64 [n, n]
-    ncontrib: np.ndarray  # int64 [n, n]
+    wsum: np.ndarray      # float64 [n, n]: sum of the weights
+    ncontrib: np.ndarray  # int64 [n, n]: N_g, the visibilities entered at the cell (Eq. vg)
+    wsum2: np.ndarray = None   # float64 [n, n]: sum of the squared weights
 
     @property
     def n(self):
@@ -136,12 +137,13 @@ def grid(n: int, du: float, uv: np.ndarray, vis: np.ndarray, kernel: str = "gaus
     v2 = np.ascontiguousarray(np.asarray(vis, np.complex64)).view(np.float32)
     g = np.zeros((n, n, 2), np.float64)
     w = np.zeros((n, n), np.float64)
+    w2 = np.zeros((n, n), np.float64)
     c = np.zeros((n, n), np.int64)
     rc = _load().orc_grid(n, float(np.float32(du)), 0 if kernel == "ngp" else 1, float(sigma_cells),
-                          int(radius_cells), len(uv), _p(uv), _p(v2), _p(g), _p(w), _p(c))
+                          int(radius_cells), len(uv), _p(uv), _p(v2), _p(g), _p(w), _p(w2), _p(c))
     if rc != 0:
         raise ValueError(f"orc_grid rejected its arguments (code {rc})")
-    return Grid(g[..., 0] + 1j * g[..., 1], w, c)
+    return Grid(g[..., 0] + 1j * g[..., 1], w, c, w2)
 
 
 def mean_grid(gr: Grid):
@@ -341,10 +343,23 @@ class Estimate:
 
 
 def literal_weights(gr: Grid, filled: np.ndarray) -> np.ndarray:
-    """W_g = 1 / N_g on filled cells, 0 elsewhere: the I-field weights of Eq. iFT_I as
-    printed, with N_g read as the cell's weight sum (the divisor of X, Sec. 2)."""
+    """W_g = 1 / N_g on filled cells, 0 elsewhere, with N_g the number of visibilities
+    entered at the cell (Eq. vg; Sec. 2 takes W_g = N_g^-1 on filled cells): the weights
+    of the literal D and I fields (Eqs. iFT, iFT_I)."""
     W = np.zeros(gr.wsum.shape)
-    W[filled > 0] = 1.0 / gr.wsum[filled > 0]
+    W[filled > 0] = 1.0 / gr.ncontrib[filled > 0]
+    return W
+
+
+def noise_weights(gr: Grid, filled: np.ndarray) -> np.ndarray:
+    """N_eff,g = (sum w)^2 / sum w^2 on filled cells, 0 elsewhere: the inverse noise
+    variance of the weighted mean X_g = V_g / sum w when every visibility carries
+    the same uncorrelated noise (Sec. 2), in units of one visibility's inverse
+    variance.  The noise-optimised form weights X_g by it in the D fields and uses
+    it as the I-field weight."""
+    W = np.zeros(gr.wsum.shape)
+    m = filled > 0
+    W[m] = gr.wsum[m] ** 2 / gr.wsum2[m]
     return W
 
 
@@ -361,20 +376,28 @@ def estimate(n, du, ell_edges, uv, vis, kernel="gauss", sigma_cells=1.0, radius_
              norm_A=1.0, ijk=None, weight_mode="unitmask") -> Estimate:
     """V -> B for one realisation: Eq. vg, ring membership, closed-triangle sums, Eq. estimator_t.
 
-    weight_mode "unitmask": the denominator is A T, T the count of closed triangles
-    (unit-mask I fields); "literal": A S_W, S_W the sum of W1 W2 W3 over the closed
-    triangles with W_g = 1 / N_g (Eq. iFT_I as printed)."""
+    weight_mode "unitmask": D fields of the weighted mean X_g, denominator A T with T
+    the count of closed triangles (unit-mask I fields).  "literal": Eqs. iFT and
+    iFT_I as printed with W_g = 1 / N_g, N_g the visibilities entered at the cell:
+    D fields of W_g V_g, denominator A S_W with S_W the sum of W1 W2 W3 over the closed
+    triangles.  "noise": D fields of N_eff X_g, denominator A S_W with W = N_eff
+    (noise_weights).  S is always the numerator sum of the D-field values."""
     q = ring_q(ell_edges, du)
     if ijk is None:
         ijk = triplets(q)
     gr = grid(n, du, uv, vis, kernel, sigma_cells, radius_cells)
     X, f = mean_grid(gr)
-    S, A, T = triple_bruteforce(X, f, q, ijk)
-    if weight_mode == "literal":
-        SW, _, _ = triple_bruteforce(literal_weights(gr, f), f, q, ijk)
+    if weight_mode == "unitmask":
+        S, A, T = triple_bruteforce(X, f, q, ijk)
+        B = normalise(S, T, norm_A)
+    elif weight_mode in ("literal", "noise"):
+        W = literal_weights(gr, f) if weight_mode == "literal" else noise_weights(gr, f)
+        Y = gr.grid * W if weight_mode == "literal" else X * W
+        S, A, T = triple_bruteforce(Y, f, q, ijk)
+        SW, _, _ = triple_bruteforce(W, f, q, ijk)
         B = normalise_literal(S, SW.real, norm_A)
     else:
-        B = normalise(S, T, norm_A)
+        raise ValueError(f"unknown weight_mode {weight_mode!r}")
     return Estimate(B, S, A, T, ellbar(f, q, du), np.asarray(ijk, np.int32), q, X, f, gr)
 
 

@@ -106,15 +106,19 @@ static int64_t cell_at(int32_t n, int32_t gx, int32_t gy)
  * grid point, w = exp(-|U_g - U_i|^2 / (2 sigma^2 dU^2)).  Cells with
  * |gx| or |gy| > n/2 - 1 are dropped (so g and -g are both on the grid).
  * Each visibility is also entered at -U_i with V* and the same weight.
- * Outputs (all n*n, FFT order, zeroed here): grid (re,im), wsum, ncontrib. */
+ * Outputs (all n*n, FFT order, zeroed here): grid (re,im), wsum, the sum of
+ * the squared weights wsum2 (the noise variance of V_g in units of one
+ * visibility's, for equal uncorrelated visibility noise, Sec. 2), and
+ * ncontrib, the number N_g of visibilities entered at the cell (Eq. vg). */
 int orc_grid(int32_t n, float du, int32_t kernel, double sigma, int32_t radius,
              int64_t n_vis, const float *uv, const float *vis,
-             double *grid, double *wsum, int64_t *ncontrib)
+             double *grid, double *wsum, double *wsum2, int64_t *ncontrib)
 {
     if (n < 4 || (n & 1)) return 1;
     const int64_t cells = (int64_t)n * n;
     memset(grid, 0, sizeof(double) * 2 * cells);
     memset(wsum, 0, sizeof(double) * cells);
+    memset(wsum2, 0, sizeof(double) * cells);
     memset(ncontrib, 0, sizeof(int64_t) * cells);
     const int32_t half = n / 2 - 1;
     const double d = (double)du;
@@ -136,10 +140,12 @@ int orc_grid(int32_t n, float du, int32_t kernel, double sigma, int32_t radius,
                 grid[2 * p] += w * vre;
                 grid[2 * p + 1] += w * vim;
                 wsum[p] += w;
+                wsum2[p] += w * w;
                 ncontrib[p] += 1;
                 grid[2 * pm] += w * vre;      /* mirror: V* at -U */
                 grid[2 * pm + 1] -= w * vim;
                 wsum[pm] += w;
+                wsum2[pm] += w * w;
                 ncontrib[pm] += 1;
             }
     }

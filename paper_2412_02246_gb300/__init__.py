@@ -30,7 +30,7 @@ ABS_OK, ABS_ERR_INVALID_ARG, ABS_ERR_CUDA, ABS_ERR_OOM, ABS_ERR_TIMEOUT, ABS_ERR
     ABS_ERR_DEVICE = range(7)
 ABS_KERNEL_NGP, ABS_KERNEL_GAUSS = 0, 1
 ABS_FP32, ABS_SPLIT_BF16 = 0, 1
-ABS_W_MEAN_UNITMASK, ABS_W_PAPER_LITERAL = 0, 1
+ABS_W_MEAN_UNITMASK, ABS_W_PAPER_LITERAL, ABS_W_NOISE = 0, 1, 2
 ABS_BEAM_NONE, ABS_BEAM_MWA_TILE, ABS_BEAM_GAUSS = 0, 1, 2
 _STATUS = {0: "ABS_OK", 1: "ABS_ERR_INVALID_ARG", 2: "ABS_ERR_CUDA", 3: "ABS_ERR_OOM",
            4: "ABS_ERR_TIMEOUT", 5: "ABS_ERR_UNSUPPORTED", 6: "ABS_ERR_DEVICE"}

@@ -173,11 +173,14 @@ abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc
 // The I fields of Eq. iFT_I as printed (ABS_W_PAPER_LITERAL): W_g = 1 / (the
 // cell's mirrored weight sum) on filled cells, from the FP64 accumulators.
 abs_status launch_filter_fft_w(abs_ctx *ctx, const Setup &s, const double *acc, float *d_fields);
-// FP64 accumulators [3][n*n] (re, im, w before the mirror) of the last
+// FP64 accumulators [planes][n*n] (re, im, w before the mirror; see grid_acc_planes) of the last
 // launch_grid_accumulate on this context.  A cell received a contribution
 // exactly when its weight sum is > 0 (every footprint weight is a normal,
 // positive FP32 number, which the sigma_cells bound guarantees).
 void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc);
+// Accumulator planes the estimate path grids into: re, im and the weight sum (the
+// count N_g in the literal form), and the squared-weight sum in the noise form.
+int grid_acc_planes(const Setup &s);
 // With d_count and d_B also given, B = S / (A T) is written as well (fused
 // into the final reduction on the FP32 path).
 // wait_before_b, if given, is waited for (on ctx->stream) before B is formed.

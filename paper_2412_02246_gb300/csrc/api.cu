@@ -136,8 +136,9 @@ abs_status derive_grid(const abs_config *cfg, int64_t *q, int *Rm, int *R_out, i
         return ABS_ERR_INVALID_ARG;
     }
     if (!(cfg->norm_A > 0.0) || !std::isfinite(cfg->norm_A)) { *err = "norm_A must be finite and > 0"; return ABS_ERR_INVALID_ARG; }
-    if (cfg->weight_mode != ABS_W_MEAN_UNITMASK && cfg->weight_mode != ABS_W_PAPER_LITERAL) {
-        *err = "weight_mode must be ABS_W_MEAN_UNITMASK or ABS_W_PAPER_LITERAL";
+    if (cfg->weight_mode != ABS_W_MEAN_UNITMASK && cfg->weight_mode != ABS_W_PAPER_LITERAL &&
+        cfg->weight_mode != ABS_W_NOISE) {
+        *err = "weight_mode must be ABS_W_MEAN_UNITMASK, ABS_W_PAPER_LITERAL or ABS_W_NOISE";
         return ABS_ERR_INVALID_ARG;
     }
     const int nb = cfg->n_bins, half = cfg->n_grid / 2 - 1;
@@ -746,7 +747,8 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
                                 const float *h_uv = nullptr, const float *h_vis = nullptr) {
     const int64_t cells = (int64_t)s.n * s.n;
     const int64_t P = (int64_t)s.N * s.N;
-    const bool literal = s.weight_mode == ABS_W_PAPER_LITERAL;
+    // the weighted forms (literal, noise) divide by the sums S_W of their I fields
+    const bool literal = s.weight_mode != ABS_W_MEAN_UNITMASK;
     // split-BF16 sums over the canonical list: the transform writes the kernel's split
     // planes directly, and no FP32 fields are kept
     const bool to_planes = s.precision == ABS_SPLIT_BF16 && d_ijk == s.d_ijk && !literal && n_trip > 0;
@@ -772,7 +774,7 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
     if (pre_zero) {
         cudaEventRecord(ctx->ev_fork, ctx->stream);
         cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-        cudaMemsetAsync(acc0, 0, sizeof(double) * 3 * (size_t)cells, ctx->side);
+        cudaMemsetAsync(acc0, 0, sizeof(double) * grid_acc_planes(s) * (size_t)cells, ctx->side);
         if (copy_in)
             cudaMemcpyAsync((void *)d_vis, h_vis, uvb * (size_t)n_real, cudaMemcpyHostToDevice, ctx->side);
         cudaEventRecord(ctx->ev_join, ctx->side);
@@ -821,8 +823,8 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
                                          d_B ? d_B + (size_t)r * n_trip : nullptr, join));
             continue;
         }
-        // Eq. iFT_I as printed: S, then (once: the weights are the baselines') the sums
-        // S_W of the I fields with W_g = 1 / N_g, then B = Re S / (A S_W)
+        // the weighted forms: S, then (once: the weights are the baselines') the sums
+        // S_W of the I fields (W_g = 1 / N_g, or N_eff), then B = Re S / (A S_W)
         abs_status sl = launch_triple_sums(ctx, s, fields, n_trip, d_ijk, sum);
         if (sl == ABS_OK && r == 0) sl = launch_filter_fft_w(ctx, s, acc, ifields);
         if (sl == ABS_OK && r == 0) sl = launch_triple_sums(ctx, s, ifields, n_trip, d_ijk, sumw);

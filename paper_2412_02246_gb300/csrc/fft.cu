@@ -444,8 +444,9 @@ struct GridF64 {   // FP64 accumulators before the mirror (inside abs_estimate)
 };
 
 // Weights of the I fields of Eq. iFT_I as printed: W_g = 1 / N_g on a filled
-// cell, N_g its mirrored weight sum in FP64 (real: N_g = N_-g), the quotient
-// in double-float.
+// cell, N_g from the third accumulator plane mirrored in FP64 (real: N_g =
+// N_-g; the estimate's literal form accumulates the count of visibilities
+// there), the quotient in double-float.
 struct GridW64 {
     static constexpr const char *tag = "w64";
     const double *w;
@@ -456,6 +457,36 @@ struct GridW64 {
         df_of(ww, wh, wl);
         df_div(1.f, 0.f, wh, wl, rh, rl);
         x = make_float4(rh, 0.f, rl, 0.f);
+        return true;
+    }
+};
+
+// The noise-optimised weighting: N_eff = (sum w)^2 / sum w^2 from the mirrored
+// FP64 sums (the weight sums w and squared-weight sums w2 before the mirror).
+// D fields: N_eff X_g = V_g (sum w) / (sum w^2); I fields: N_eff.
+struct GridNoise64 {
+    static constexpr const char *tag = "noise";
+    const double *re, *im, *w, *w2;
+    __device__ bool value(int64_t cell, int64_t mcell, float4 &x) const {
+        const double ww = w[cell] + w[mcell];
+        if (!(ww > 0.0)) return false;
+        const double f = ww / (w2[cell] + w2[mcell]);
+        float rh, rl, ih, il;
+        df_of((re[cell] + re[mcell]) * f, rh, rl);
+        df_of((im[cell] - im[mcell]) * f, ih, il);
+        x = make_float4(rh, ih, rl, il);
+        return true;
+    }
+};
+struct GridNeff64 {
+    static constexpr const char *tag = "neff";
+    const double *w, *w2;
+    __device__ bool value(int64_t cell, int64_t mcell, float4 &x) const {
+        const double ww = w[cell] + w[mcell];
+        if (!(ww > 0.0)) return false;
+        float h, l;
+        df_of(ww * ww / (w2[cell] + w2[mcell]), h, l);
+        x = make_float4(h, 0.f, l, 0.f);
         return true;
     }
 };
@@ -953,12 +984,20 @@ abs_status launch_filter_fft(abs_ctx *ctx, const Setup &s, const float *d_grid, 
 abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc, float *d_fields,
                                  const SplitOut *split) {
     const int64_t cells = (int64_t)s.n * s.n;
-    GridF64 src{acc, acc + cells, acc + 2 * cells};
+    if (s.weight_mode == ABS_W_NOISE) {
+        GridNoise64 src{acc, acc + cells, acc + 2 * cells, acc + 3 * cells};
+        return run_fft(ctx, s, src, d_fields, split);
+    }
+    GridF64 src{acc, acc + cells, acc + 2 * cells};   // the literal form holds N_g in plane 2
     return run_fft(ctx, s, src, d_fields, split);
 }
 
 abs_status launch_filter_fft_w(abs_ctx *ctx, const Setup &s, const double *acc, float *d_fields) {
     const int64_t cells = (int64_t)s.n * s.n;
+    if (s.weight_mode == ABS_W_NOISE) {
+        GridNeff64 src{acc + 2 * cells, acc + 3 * cells};
+        return run_fft(ctx, s, src, d_fields);
+    }
     GridW64 src{acc + 2 * cells};
     return run_fft(ctx, s, src, d_fields);
 }

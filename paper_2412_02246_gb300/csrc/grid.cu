@@ -406,6 +406,10 @@ __global__ void k_scan_add(uint32_t *__restrict__ out, int64_t len,
 // Staged record of a visibility (RS floats): wx[0..7] (zero beyond 2r),
 // (wy[d], wy[d]) for d = 0..6, two pad floats, (Re V, Re V, Im V, Im V).
 constexpr int GT = 256;          // threads per gridding CTA (8 warps x UMAX/8 items)
+// What the third (and fourth) accumulator plane of a cell holds: the weight sum
+// (GW_SUM), the number N_g of visibilities entered (GW_COUNT, Eq. vg), or the
+// weight sum and the sum of squared weights (GW_SUM_SQ).
+enum { GW_SUM = 0, GW_COUNT = 1, GW_SUM_SQ = 2 };
 constexpr int RS = 28;           // floats per staged record
 constexpr int R_WY = 8, R_V = 24;
 constexpr int GFOLD = 16;
@@ -438,15 +442,17 @@ __device__ __forceinline__ void kahan_add2(float2 &s, float2 &c, float2 x) {
 
 // One staged visibility (record at offset o) into this lane's two footprint
 // cells: w = (wx[2q], wx[2q+1]) * wy[dy], re += w Re V, im += w Im V, sum w.
+template <int WM>
 __device__ __forceinline__ void grid_acc(const float *lw, const float *lwy, const float *lv, int o, float2 &re,
-                                         float2 &im, float2 &ws) {
+                                         float2 &im, float2 &ws, float2 &ws2) {
     const float2 wxp = *(const float2 *)(lw + o);
     const float2 wyy = *(const float2 *)(lwy + o);
     const float4 vv = *(const float4 *)(lv + o);
     const float2 w = __fmul2_rn(wxp, wyy);
     re = __ffma2_rn(w, make_float2(vv.x, vv.y), re);
     im = __ffma2_rn(w, make_float2(vv.z, vv.w), im);
-    ws = __fadd2_rn(w, ws);
+    if (WM != GW_COUNT) ws = __fadd2_rn(w, ws);
+    if (WM == GW_SUM_SQ) ws2 = __ffma2_rn(w, w, ws2);
 }
 
 // Inputs of one unit as thread (warp, lane) sees them: items t = 64 warp +
@@ -473,13 +479,15 @@ __device__ __forceinline__ void load_unit(UnitIn &in, int64_t u, int64_t nu, int
     }
 }
 
+template <int WM>
 __global__ void __launch_bounds__(GT, 3) k_grid(GridGeom G, int64_t n_vis, uint32_t key_none,
                                              const float2 *__restrict__ s_uv,
                                              const uint32_t *__restrict__ s_idx,
                                              const float2 *__restrict__ vis,
                                              double *__restrict__ acc_re,
                                              double *__restrict__ acc_im,
-                                             double *__restrict__ acc_w) {
+                                             double *__restrict__ acc_w,
+                                             double *__restrict__ acc_w2) {
     extern __shared__ __align__(16) uint8_t dsm[];
     float *st = (float *)dsm;                                          // [UMAX][RS] staged records
     uint32_t *skey = (uint32_t *)(st + UMAX * RS);                     // [UMAX] key of every item
@@ -585,27 +593,29 @@ __global__ void __launch_bounds__(GT, 3) k_grid(GridGeom G, int64_t n_vis, uint3
             for (int tk = warp; tk < (int)ntask; tk += nwarps) {
                 const int j_begin = tstart[tk], j_end = tstart[tk + 1];
                 const float2 z = make_float2(0.f, 0.f);
-                float2 sre = z, cre = z, sim = z, cim = z, sw = z, cw = z;
+                float2 sre = z, cre = z, sim = z, cim = z, sw = z, cw = z, sw2 = z, cw2 = z;
                 const float *lw = st + q2, *lwy = st + R_WY + 2 * dy, *lv = st + R_V;
                 for (int j0 = j_begin; j0 < j_end; j0 += GFOLD) {   // plain blocks of GFOLD, folded into Kahan sums
-                    float2 bre = z, bim = z, bw = z;
+                    float2 bre = z, bim = z, bw = z, bw2 = z;
                     if (j0 + GFOLD <= j_end) {
                         // a full block: unrolled, two independent chains (even, odd visibilities)
-                        float2 bre1 = z, bim1 = z, bw1 = z;
+                        float2 bre1 = z, bim1 = z, bw1 = z, bw21 = z;
 #pragma unroll
                         for (int k = 0; k < GFOLD; k += 2) {
-                            grid_acc(lw, lwy, lv, (j0 + k) * RS, bre, bim, bw);
-                            grid_acc(lw, lwy, lv, (j0 + k + 1) * RS, bre1, bim1, bw1);
+                            grid_acc<WM>(lw, lwy, lv, (j0 + k) * RS, bre, bim, bw, bw2);
+                            grid_acc<WM>(lw, lwy, lv, (j0 + k + 1) * RS, bre1, bim1, bw1, bw21);
                         }
                         bre = __fadd2_rn(bre, bre1);
                         bim = __fadd2_rn(bim, bim1);
-                        bw = __fadd2_rn(bw, bw1);
+                        if (WM != GW_COUNT) bw = __fadd2_rn(bw, bw1);
+                        if (WM == GW_SUM_SQ) bw2 = __fadd2_rn(bw2, bw21);
                     } else {
-                        for (int j = j0; j < j_end; ++j) grid_acc(lw, lwy, lv, j * RS, bre, bim, bw);
+                        for (int j = j0; j < j_end; ++j) grid_acc<WM>(lw, lwy, lv, j * RS, bre, bim, bw, bw2);
                     }
                     kahan_add2(sre, cre, bre);
                     kahan_add2(sim, cim, bim);
-                    kahan_add2(sw, cw, bw);
+                    if (WM != GW_COUNT) kahan_add2(sw, cw, bw);
+                    if (WM == GW_SUM_SQ) kahan_add2(sw2, cw2, bw2);
                 }
                 // the run's cell from its key: tile (kx / TS, ky / TS), cell in the tile
                 const uint32_t key = skey[j_begin];
@@ -617,18 +627,21 @@ __global__ void __launch_bounds__(GT, 3) k_grid(GridGeom G, int64_t n_vis, uint3
                 // the run's sums s - c, rounded once to FP32 (relative 2^-24 of the run)
                 const float2 m1 = make_float2(-1.f, -1.f);
                 const float2 vre = __ffma2_rn(cre, m1, sre), vim = __ffma2_rn(cim, m1, sim);
-                const float2 vw = __ffma2_rn(cw, m1, sw);
+                const float2 vw = __ffma2_rn(cw, m1, sw), vw2 = __ffma2_rn(cw2, m1, sw2);
+                const double run = (double)(j_end - j_begin);   // visibilities the run enters at the cell
                 if (gxa >= -G.half && gxa <= G.half) {
                     const int64_t pidx = cell_index(G.n, gxa, gy);
                     atomicAdd(&acc_re[pidx], widen(vre.x));
                     atomicAdd(&acc_im[pidx], widen(vim.x));
-                    atomicAdd(&acc_w[pidx], widen(vw.x));
+                    atomicAdd(&acc_w[pidx], WM == GW_COUNT ? run : widen(vw.x));
+                    if (WM == GW_SUM_SQ) atomicAdd(&acc_w2[pidx], widen(vw2.x));
                 }
                 if (on_b && gxa + 1 >= -G.half && gxa + 1 <= G.half) {
                     const int64_t pidx = cell_index(G.n, gxa + 1, gy);
                     atomicAdd(&acc_re[pidx], widen(vre.y));
                     atomicAdd(&acc_im[pidx], widen(vim.y));
-                    atomicAdd(&acc_w[pidx], widen(vw.y));
+                    atomicAdd(&acc_w[pidx], WM == GW_COUNT ? run : widen(vw.y));
+                    if (WM == GW_SUM_SQ) atomicAdd(&acc_w2[pidx], widen(vw2.y));
                 }
             }
         }
@@ -764,9 +777,11 @@ abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const f
     return check_launch(ctx, "grid plan");
 }
 
+int grid_acc_planes(const Setup &s) { return s.weight_mode == ABS_W_NOISE ? 4 : 3; }
+
 void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc) {
     const int64_t cells = (int64_t)s.n * s.n;
-    *acc = (double *)workspace(ctx, "grid.acc", sizeof(double) * 3 * cells);
+    *acc = (double *)workspace(ctx, "grid.acc", sizeof(double) * grid_acc_planes(s) * cells);
 }
 
 abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_vis,
@@ -775,19 +790,33 @@ abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, c
     PlanBufs b;
     if (!plan_bufs(ctx, G, n_vis, b)) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
     const int64_t cells = (int64_t)s.n * s.n;
-    double *acc = (double *)workspace(ctx, "grid.acc", sizeof(double) * 3 * cells);
+    // the estimate path (no FP32 outputs) accumulates what its weighting needs
+    const bool estimate = !d_grid && !d_wsum;
+    const int wm = !estimate ? GW_SUM
+                   : s.weight_mode == ABS_W_PAPER_LITERAL ? GW_COUNT
+                   : s.weight_mode == ABS_W_NOISE ? GW_SUM_SQ : GW_SUM;
+    const int planes = wm == GW_SUM_SQ ? 4 : 3;
+    double *acc = (double *)workspace(ctx, "grid.acc", sizeof(double) * planes * cells);
     if (!acc) return fail(ctx, ABS_ERR_OOM, "grid accumulation workspace");
     cudaStream_t st = ctx->stream;
     if (!acc_zeroed) {
         StageTimer timer(ctx, "grid_zero");
-        cudaMemsetAsync(acc, 0, sizeof(double) * 3 * cells, st);
+        cudaMemsetAsync(acc, 0, sizeof(double) * planes * cells, st);
     }
     if (n_vis > 0) {
         StageTimer timer(ctx, "grid");
         const int blocks = (int)std::min<int64_t>(cdiv(n_vis, UMAX), ctx->sm_count * 3);
-        allow_smem(k_grid, GRID_SMEM);
-        k_grid<<<blocks, GT, GRID_SMEM, st>>>(G, n_vis, plan_key_none(b), b.s_uv, b.s_idx, (const float2 *)d_vis,
-                                           acc, acc + cells, acc + 2 * cells);
+        auto run = [&](auto kern) {
+            allow_smem(kern, GRID_SMEM);
+            kern<<<blocks, GT, GRID_SMEM, st>>>(G, n_vis, plan_key_none(b), b.s_uv, b.s_idx, (const float2 *)d_vis,
+                                                acc, acc + cells, acc + 2 * cells, acc + 3 * cells);
+        };
+        if (wm == GW_COUNT)
+            run(k_grid<GW_COUNT>);
+        else if (wm == GW_SUM_SQ)
+            run(k_grid<GW_SUM_SQ>);
+        else
+            run(k_grid<GW_SUM>);
     }
     if (!d_grid && !d_wsum) {   // estimate path: the mask alone, if asked for
         if (d_mask) {

@@ -72,7 +72,7 @@ def test_random_edges_match_oracle(lib):
     dict(du=float("nan")), dict(kernel=5), dict(sigma_cells=0.1), dict(sigma_cells=0.38), dict(radius_cells=4),
     dict(radius_cells=-1), dict(precision=3), dict(norm_A=0.0), dict(n_fft=7), dict(n_fft=80), dict(n_fft=91),
     dict(ell_edges=[10.0, 5.0]), dict(ell_edges=[0.0, 5.0]), dict(ell_edges=[5.0, float("inf")]),
-    dict(weight_mode=2), dict(weight_mode=-1),
+    dict(weight_mode=3), dict(weight_mode=-1),
 ])
 def test_invalid_configs_rejected(lib, bad):
     base = dict(n_grid=64, du=2.0, ell_edges=np.linspace(25, 375, 9))

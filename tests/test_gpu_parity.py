@@ -907,15 +907,19 @@ def test_estimate_batched_uneven():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("mode,name", [(absmod.ABS_W_PAPER_LITERAL, "literal"), (absmod.ABS_W_NOISE, "noise")])
 @pytest.mark.parametrize("prec,tol", [(0, SUM_TOL), (1, 3e-4)])
-def test_literal_weight_mode(ctx, prec, tol):
-    """ABS_W_PAPER_LITERAL (Eq. iFT_I as printed): B = Re S / (A S_W) against the
-    oracle, counts still exact, through abs_estimate and abs_estimate_many."""
+def test_literal_weight_mode(ctx, prec, tol, mode, name):
+    """The weighted forms of Sec. 2 (ABS_W_PAPER_LITERAL: W_g = 1 / N_g with N_g the
+    visibilities entered at the cell; ABS_W_NOISE: W_g = N_eff on the weighted mean):
+    B = Re S / (A S_W) against the oracle on Gaussian-gridded data, where count,
+    weight sum and N_eff differ, counts still exact, through abs_estimate and
+    abs_estimate_many."""
     wl = synth.workload(0)
-    cfg = absmod.Config.from_workload(wl, precision=prec, weight_mode=absmod.ABS_W_PAPER_LITERAL)
+    cfg = absmod.Config.from_workload(wl, precision=prec, weight_mode=mode)
     ins = [inputs(0, r) for r in range(2)]
     uv = ins[0].uv
-    ests = [oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, uv, i.vis, weight_mode="literal") for i in ins]
+    ests = [oracle.estimate(wl.n_grid, wl.du, wl.ell_edges, uv, i.vis, weight_mode=name) for i in ins]
     base = oracle_run(("est0r", 0), wl.n_grid, wl.du, wl.ell_edges, uv, ins[0].vis)
     B, T, E, ijk = absmod.estimate(cfg, to_dev(uv), to_dev(synth.vis_as_float2(ins[0].vis)), ctx)
     ctx.sync()
@@ -930,9 +934,16 @@ def test_literal_weight_mode(ctx, prec, tol):
         assert np.array_equal(np.isnan(Bg), np.isnan(est.B))
         ok = ~np.isnan(est.B)
         big = ok & (np.abs(est.B) >= 1e-3 * np.nanmax(np.abs(est.B)))
-        assert (np.abs(Bg[big] - est.B[big]) / np.abs(est.B[big])).max() <= tol
+        rel = np.abs(Bg[big] - est.B[big]) / np.abs(est.B[big])
+        # split-BF16: every product carries up to about 3 x 2^-17 relative error, so the sum's error
+        # is bounded by 2^-15 of sum |terms|; the weighted D fields spread their terms over a wide
+        # range (kappa = sum |terms| / |S| up to about 250 on this workload), so the bound adds
+        # 3e-5 kappa to the tolerance (the FP32 path keeps the plain 1e-5)
+        kappa = est.absum[big] / np.abs(est.S.real[big])
+        bound = tol + (3e-5 * kappa if prec == 1 else 0.0)
+        assert np.all(rel <= bound), f"{name}: max rel {rel.max():.3e}, worst over bound {(rel / bound).max():.2f}"
     assert np.array_equal(T.cpu().numpy(), base.T) and np.array_equal(Tm.cpu().numpy(), base.T)
-    # the literal denominator differs from the unit-mask one on this workload
+    # the weighted estimate differs from the unit-mask one on this workload
     ok = ~np.isnan(base.B)
     assert not np.allclose(ests[0].B[ok], base.B[ok], rtol=1e-3)
 

@@ -736,3 +736,91 @@ def test_mwa_tile_beam_fwhm_is_the_printed_one():
     i = np.nonzero(A >= 0.5)[0].max()                # last sample above half power, then interpolate
     x_half = th[i] + (A[i] - 0.5) / (A[i] - A[i + 1]) * (th[i + 1] - th[i])
     assert abs(np.rad2deg(2 * x_half) - 24.68) < 0.05
+
+
+def _py_grid(n, du, uv, vis, sigma, r):
+    """Eq. vg written out in Python: every visibility at its nearest grid point's
+    (2r+1)^2 footprint and, conjugated, at the mirror; per cell the weighted sum V_g,
+    the weight sum, the squared-weight sum and the count N_g of entries."""
+    half = n // 2 - 1
+    V = np.zeros((n, n), np.complex128)
+    ws = np.zeros((n, n))
+    w2 = np.zeros((n, n))
+    N = np.zeros((n, n), np.int64)
+    for (u, v), z in zip(uv.astype(np.float64), vis.astype(np.complex128)):
+        cx, cy = int(np.floor(u / du + 0.5)), int(np.floor(v / du + 0.5))
+        for dy in range(-r, r + 1):
+            for dx in range(-r, r + 1):
+                gx, gy = cx + dx, cy + dy
+                if abs(gx) > half or abs(gy) > half:
+                    continue
+                w = np.exp(-((gx * du - u) ** 2 + (gy * du - v) ** 2) / (2 * sigma ** 2 * du ** 2))
+                for sx, sy, val in ((gx, gy, z), (-gx, -gy, np.conj(z))):
+                    V[sy % n, sx % n] += w * val
+                    ws[sy % n, sx % n] += w
+                    w2[sy % n, sx % n] += w * w
+                    N[sy % n, sx % n] += 1
+    return V, ws, w2, N
+
+
+@pytest.mark.parametrize("mode", ["literal", "noise"])
+def test_weighted_estimators_match_python_definition_gaussian(mode):
+    """The weighted estimators against Eqs. vg, iFT, iFT_I and estimator_t written out
+    in Python on a tiny Gaussian-gridded case where cells collect several visibilities,
+    so the count N_g, the weight sum and (sum w)^2 / sum w^2 all differ.  literal: D from
+    V_g / N_g, I from 1 / N_g (Sec. 2's W_g = N_g^-1).  noise: D from the weighted mean
+    times N_eff = (sum w)^2 / sum w^2, I from N_eff."""
+    rng = np.random.default_rng(21)
+    n, du, sigma, r = 16, 1.0, 1.0, 1
+    base = rng.integers(-5, 6, (36, 2)).astype(np.float64)
+    uv = (base + rng.uniform(-0.4, 0.4, base.shape)).astype(np.float32)
+    vis = (rng.standard_normal(36) + 1j * rng.standard_normal(36)).astype(np.complex64)
+    edges = 2 * np.pi * np.array([1.5, 3.0, 4.5, 6.0])
+    est = oracle.estimate(n, du, edges, uv, vis, kernel="gauss", sigma_cells=sigma, radius_cells=r,
+                          weight_mode=mode)
+    V, ws, w2, N = _py_grid(n, du, uv, vis, sigma, r)
+    filled = (N > 0).astype(np.uint8)
+    assert np.any((N > 1) & (np.abs(ws - N) > 0.1))           # count and weight sum differ
+    if mode == "literal":
+        Y = np.where(N > 0, V / np.maximum(N, 1), 0)
+        W = np.where(N > 0, 1.0 / np.maximum(N, 1), 0.0)
+    else:
+        neff = np.where(N > 0, ws ** 2 / np.where(w2 > 0, w2, 1.0), 0.0)
+        Y = np.where(N > 0, V / np.where(ws > 0, ws, 1.0), 0) * neff
+        W = neff
+    q = oracle.ring_q(edges, du)
+    Sp, _ = python_enumeration(Y, filled, q)
+    Wp, _ = python_enumeration(W.astype(np.complex128), filled, q)
+    checked = 0
+    for t, (i, j, k) in enumerate(est.ijk):
+        sw = Wp.get((i, j, k), 0)
+        if sw == 0:
+            assert np.isnan(est.B[t])
+            continue
+        assert est.B[t] == pytest.approx(Sp[(i, j, k)].real / sw.real, rel=1e-10, abs=1e-12)
+        checked += 1
+    assert checked >= 5
+
+
+def test_noise_weights_reduce_to_natural_weighting_ngp():
+    """With nearest-grid-point gridding every weight is 1, so N_eff = N_g and the
+    noise-weighted D fields carry the plain sums V_g (natural weighting): the noise
+    B equals sum V1 V2 V3 / sum N1 N2 N3 over the closed triangles, computed here from
+    the oracle's own grid sums by the brute-force triple sum."""
+    rng = np.random.default_rng(5)
+    n, du = 24, 1.0
+    base = rng.integers(-8, 9, (80, 2)).astype(np.float64)
+    uv = (base + rng.uniform(-0.3, 0.3, base.shape)).astype(np.float32)
+    vis = (rng.standard_normal(80) + 1j * rng.standard_normal(80)).astype(np.complex64)
+    edges = 2 * np.pi * np.array([2.0, 4.5, 7.0, 9.5])
+    est = oracle.estimate(n, du, edges, uv, vis, kernel="ngp", weight_mode="noise")
+    gr = oracle.grid(n, du, uv, vis, kernel="ngp")
+    f = (gr.ncontrib > 0).astype(np.uint8)
+    assert np.array_equal(gr.wsum, gr.ncontrib.astype(np.float64))
+    assert np.array_equal(gr.wsum2, gr.ncontrib.astype(np.float64))
+    assert gr.ncontrib.max() > 1
+    S, _, _ = oracle.triple_bruteforce(gr.grid, f, est.q, est.ijk)
+    SN, _, _ = oracle.triple_bruteforce(gr.ncontrib.astype(np.complex128), f, est.q, est.ijk)
+    ok = SN.real > 0
+    assert ok.sum() >= 5
+    assert np.allclose(est.B[ok], S.real[ok] / SN.real[ok], rtol=1e-12)
