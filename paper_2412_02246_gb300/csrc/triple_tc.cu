@@ -93,11 +93,19 @@ constexpr int NT = (NFORM + 2) * 32; // threads per CTA
 // each) and warps are dealt to them in turn, so the scheduler with the most warps
 // (3 of 10, or 5 of 18) bounds it, in steps of 8
 #define TC_MAXREG (NFORM == 8 ? 168 : 96)
-constexpr int MAX_TILES = 2;         // tiles per set (their A buffers for two chunks fit tensor memory)
+#ifndef ABS_TC_MAX_TILES
+#define ABS_TC_MAX_TILES 2
+#endif
+#ifndef ABS_TC_ASLOTS
+#define ABS_TC_ASLOTS 2
+#endif
+constexpr int MAX_TILES = ABS_TC_MAX_TILES;   // tiles per set
+constexpr int ASLOTS = ABS_TC_ASLOTS;         // chunks whose A buffers are in tensor memory at once (2 or 4)
+static_assert(ASLOTS == 2 || ASLOTS == 4, "A slots: a power of two");
 constexpr int MAX_STAGES = 8;
 constexpr int TMEM_COLS = 512;
 constexpr int A_COLS = 64;           // one A buffer: 32 columns of hi pairs, 32 of lo pairs
-constexpr int NABUF = 2 * MAX_TILES; // A buffers: every tile of two chunks (formers one chunk ahead)
+constexpr int NABUF = ASLOTS * MAX_TILES;   // A buffers: every tile of ASLOTS chunks (formers ahead of the MMAs)
 constexpr int BOX_ROWS = 16;         // window sizes (rings a copy) are multiples of it
 #ifndef ABS_TC_DRAIN
 #define ABS_TC_DRAIN 8
@@ -236,10 +244,21 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
 }
 
-// Four FP32 values (16-byte unit u of 16) of ring m's 64-pixel row in an F window
-// starting at ring f_lo: rows are 256 bytes, units XOR-permuted by m & 7.
-__device__ __forceinline__ float4 ld_frow(const uint8_t *F, int m, int f_lo, int u) {
-    return *(const float4 *)(F + (m - f_lo) * 256 + ((u ^ (m & 7)) << 4));
+// Sixteen bytes of shared memory at a 32-bit shared address.  Volatile, so it stays in program
+// order with the mbarrier waits that make the data visible.
+__device__ __forceinline__ float4 lds128(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
+// Where a forming thread's FP32 values of ring m sit in an F window (rings from f_lo, rows of
+// 256 bytes, 16-byte units XOR-permuted by m & 7): unit u = u0 ^ w of the thread's pixels (u0
+// its first unit, w < 16 / (u0's step)) is at window + (rel ^ (w << 4)), rel = (m - f_lo) 256
+// + ((u0 ^ (m & 7)) << 4), since the window starts on a 256-byte boundary and u0 and w have no
+// bit in common.
+__device__ __forceinline__ uint32_t frow_rel(int m, int f_lo, int u0) {
+    return (uint32_t)((m - f_lo) * 256 + ((u0 ^ (m & 7)) << 4));
 }
 
 // Eight consecutive tensor-memory columns of one lane (completion awaited separately).
@@ -274,7 +293,7 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                                                      float *__restrict__ partial, int *__restrict__ next_item,
                                                      int32_t *__restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full[MAX_STAGES], done[MAX_STAGES], a_full[2], d_full[2], d_empty[2], fin;
+    __shared__ __align__(8) uint64_t full[MAX_STAGES], done[MAX_STAGES], a_full[ASLOTS], d_full[2], d_empty[2], fin;
     __shared__ uint32_t tmem_holder;
     __shared__ volatile int abort_s;
     __shared__ int item_s;
@@ -293,8 +312,8 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&done[s]), 1);
         }
+        for (int b = 0; b < ASLOTS; ++b) mbar_init(smem_u32(&a_full[b]), NFORM);
         for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&a_full[b]), NFORM);
             mbar_init(smem_u32(&d_full[b]), 1);
             mbar_init(smem_u32(&d_empty[b]), NFORM);
         }
@@ -313,8 +332,10 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
 
     // role state that lives across items
     int st = 0, su = 0;      // stage and its use (loader, formers and issuer walk the same sequence)
-    int cg = 0;              // chunks so far (A buffer pair cg & 1, its use cg >> 1)
-    int st2[2] = {0, 0}, su2[2] = {0, 0};   // formers: stage and use of the chunks cg - 2, cg - 1
+    int cg = 0;              // chunks so far (A slot cg % ASLOTS, its use cg / ASLOTS)
+    int hst[ASLOTS], hsu[ASLOTS];   // formers: stage and use of chunks cg - ASLOTS .. cg - 1, oldest first
+#pragma unroll
+    for (int x = 0; x < ASLOTS; ++x) hst[x] = hsu[x] = 0;
     int grp = 0;             // accumulation groups so far (region grp & 1, its use grp >> 1)
     int issued = 0;          // stages the loader filled (for the drain)
     float accl[MAXSLOT];     // formers: this thread's long accumulators (FP32, rounded to nearest)
@@ -390,10 +411,23 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                 }
             }
         } else if (warp == 1) {
-            // ---------------- MMA issue (one thread): groups of DRAIN chunks into alternating regions
+            // ---------------- MMA issue (one thread): groups of DRAIN chunks into alternating regions.
+            // Its per-chunk path is kept short (the tile constants live in registers, the stage's
+            // descriptor advances by addition): the tensor pipe idles while this thread is between
+            // chunks once its short queue has drained.
             if (lane == 0) {
+                uint32_t idesc_t[MAX_TILES], col_t[MAX_TILES], rows_t[MAX_TILES];
+#pragma unroll
+                for (int t = 0; t < MAX_TILES; ++t) {
+                    idesc_t[t] = t < S.ntiles ? make_idesc(TM, t_n[t]) : 0u;
+                    col_t[t] = t < S.ntiles ? (uint32_t)t_col[t] : 0u;
+                    rows_t[t] = t < S.ntiles ? (uint32_t)(t_ilo[t] - S.b_lo) * 8u : 0u;
+                }
+                const uint64_t d_stage = (uint64_t)(G.stage_bytes >> 4), d_lo = (uint64_t)(b_bytes >> 4);
+                const uint64_t d_base = desc_sw128(smem_u32(smem));
+                uint64_t d_cur = d_base + (uint64_t)st * d_stage;   // this chunk's stage, B hi plane
+                int gc = 0;                                          // chunk in the group
                 for (int c = 0; c < nchunks && !abort_s; ++c) {
-                    const int gc = c % DRAIN;
                     const uint32_t region = (uint32_t)(NABUF * A_COLS + (grp & 1) * region_cols);
                     if (gc == 0 && grp >= 2) {   // the group before last in this region has been drained
                         if (!mbar_wait(smem_u32(&d_empty[grp & 1]), (uint32_t)(((grp >> 1) - 1) & 1), &abort_s)) {
@@ -406,28 +440,27 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                         abort_s = 1;
                         break;
                     }
-                    // the stage's B descriptors (hi, lo); a tile's rows and a K-step move only the
-                    // start-address field (16-byte units: 8 per ring row, 2 per 16 pixels)
-                    const uint32_t bh = smem_u32(smem + (size_t)st * G.stage_bytes);
-                    const uint64_t dh0 = desc_sw128(bh), dl0 = desc_sw128(bh + (uint32_t)b_bytes);
-                    // the chunk's A buffers (every tile of the set), formed one chunk ahead
-                    if (!mbar_wait(smem_u32(&a_full[cg & 1]), (uint32_t)((cg >> 1) & 1), &abort_s)) {
+                    // the chunk's A buffers (every tile of the set), formed ahead
+                    if (!mbar_wait(smem_u32(&a_full[cg & (ASLOTS - 1)]), (uint32_t)((cg / ASLOTS) & 1), &abort_s)) {
                         abort_s = 1;
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    for (int t = 0; t < S.ntiles; ++t) {
-                        const uint32_t idesc = make_idesc(TM, t_n[t]);
-                        const uint32_t acc = tmem + region + (uint32_t)t_col[t];
-                        const uint32_t a_hi = tmem + (uint32_t)(((cg & 1) * MAX_TILES + t) * A_COLS), a_lo = a_hi + 32;
-                        const uint64_t rows = (uint64_t)(t_ilo[t] - S.b_lo) * 8u;
+                    const uint32_t a_slot = tmem + (uint32_t)((cg & (ASLOTS - 1)) * MAX_TILES * A_COLS);
+                    const uint32_t first = gc > 0 ? 1u : 0u;
+#pragma unroll
+                    for (int t = 0; t < MAX_TILES; ++t) {
+                        if (t >= S.ntiles) break;
+                        // a tile's rows and a K-step move only the descriptors' start-address field
+                        // (16-byte units: 8 per ring row, 2 per 16 pixels)
+                        const uint32_t acc = tmem + region + col_t[t];
+                        const uint32_t a_hi = a_slot + (uint32_t)(t * A_COLS), a_lo = a_hi + 32;
+                        const uint64_t dh0 = d_cur + rows_t[t], dl0 = dh0 + d_lo;
 #pragma unroll
                         for (int ks = 0; ks < KC / 16; ++ks) {
-                            const uint64_t dh = dh0 + rows + 2u * ks;
-                            const uint64_t dl = dl0 + rows + 2u * ks;
-                            mma_ts(acc, a_hi + 8u * ks, dh, idesc, (gc > 0 || ks > 0) ? 1u : 0u);
-                            mma_ts(acc, a_hi + 8u * ks, dl, idesc, 1u);
-                            mma_ts(acc, a_lo + 8u * ks, dh, idesc, 1u);
+                            mma_ts(acc, a_hi + 8u * ks, dh0 + 2u * ks, idesc_t[t], ks > 0 ? 1u : first);
+                            mma_ts(acc, a_hi + 8u * ks, dl0 + 2u * ks, idesc_t[t], 1u);
+                            mma_ts(acc, a_lo + 8u * ks, dh0 + 2u * ks, idesc_t[t], 1u);
                         }
                     }
                     // one commit a chunk: its MMAs done frees the stage and the chunk's A buffers
@@ -436,11 +469,15 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                     if (++st == G.n_stages) {
                         st = 0;
                         ++su;
+                        d_cur = d_base;
+                    } else {
+                        d_cur += d_stage;
                     }
                     if (gc == DRAIN - 1 || c == nchunks - 1) {   // the group is complete: the formers drain it
                         mma_commit(smem_u32(&d_full[grp & 1]));
                         ++grp;
                     }
+                    if (++gc == DRAIN) gc = 0;
                 }
             }
         } else {
@@ -450,6 +487,16 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
             const int row = 32 * q + lane;
             const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
             const int nb_h = n_blk[h];
+            // this thread's rows of the set's tiles: offsets of D_j and D_k in an F window
+            uint32_t rel_j[MAX_TILES], rel_k[MAX_TILES];
+            bool row_ok[MAX_TILES];
+#pragma unroll
+            for (int t = 0; t < MAX_TILES; ++t) {
+                const short2 jk = t < S.ntiles ? rows_s[t][row] : make_short2(-1, -1);
+                row_ok[t] = jk.x >= 0;
+                rel_j[t] = row_ok[t] ? frow_rel(jk.x, S.f_lo, (h * FPX) / 4) : 0u;
+                rel_k[t] = row_ok[t] ? frow_rel(jk.y, S.f_lo, (h * FPX) / 4) : 0u;
+            }
             int gdrained = grp;                       // this item's first group
             bool fail_f = false;
             // chunk c is formed; after the first chunk of a group (and after the last chunk) the group
@@ -460,30 +507,36 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                         fail_f = true;
                         break;
                     }
-                    // the F window, and this thread's first 16-byte unit (FPX pixels from h * FPX)
+                    // the F window
                     const uint8_t *F = smem + (size_t)st * G.stage_bytes + 2 * b_bytes;
-                    const int cc0 = (h * FPX) / 4;
                     // the A buffers of this chunk's pair were read by the MMAs of chunk cg - 2
-                    if (cg >= 2 &&
-                        !mbar_wait(smem_u32(&done[st2[cg & 1]]), (uint32_t)(su2[cg & 1] & 1), &abort_s)) {
+                    if (cg >= ASLOTS && !mbar_wait(smem_u32(&done[hst[0]]), (uint32_t)(hsu[0] & 1), &abort_s)) {
                         fail_f = true;
                         break;
                     }
-                    st2[cg & 1] = st;
-                    su2[cg & 1] = su;
-                    for (int t = 0; t < S.ntiles; ++t) {
-                        const short2 jk = rows_s[t][row];
-                        const uint32_t ta = lane_base + (uint32_t)(((cg & 1) * MAX_TILES + t) * A_COLS + (FPX / 2) * h);
+#pragma unroll
+                    for (int x = 0; x + 1 < ASLOTS; ++x) {
+                        hst[x] = hst[x + 1];
+                        hsu[x] = hsu[x + 1];
+                    }
+                    hst[ASLOTS - 1] = st;
+                    hsu[ASLOTS - 1] = su;
+                    const uint32_t Fs = smem_u32(F);
+#pragma unroll
+                    for (int t = 0; t < MAX_TILES; ++t) {
+                        if (t >= S.ntiles) break;
+                        const uint32_t ta =
+                            lane_base + (uint32_t)(((cg & (ASLOTS - 1)) * MAX_TILES + t) * A_COLS + (FPX / 2) * h);
+                        const uint32_t pj = Fs + rel_j[t], pk = Fs + rel_k[t];
                         // 16 pixels at a time: products, hi / lo split, 8 packed pairs of each to tensor memory
 #pragma unroll
                         for (int part = 0; part < FPX / 16; ++part) {
                             uint32_t hi[8], lo[8];
-                            if (jk.x >= 0) {
+                            if (row_ok[t]) {
 #pragma unroll
                                 for (int cc = 0; cc < 4; ++cc) {
-                                    const int c16 = cc0 + 4 * part + cc;
-                                    const float4 x = ld_frow(F, jk.x, S.f_lo, c16),
-                                                 y = ld_frow(F, jk.y, S.f_lo, c16);
+                                    const uint32_t w = (uint32_t)(4 * part + cc) << 4;
+                                    const float4 x = lds128(pj ^ w), y = lds128(pk ^ w);
                                     split2(__fmul2_rn(make_float2(x.x, x.y), make_float2(y.x, y.y)), hi[2 * cc],
                                            lo[2 * cc]);
                                     split2(__fmul2_rn(make_float2(x.z, x.w), make_float2(y.z, y.w)), hi[2 * cc + 1],
@@ -500,7 +553,7 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                     asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
                     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&a_full[cg & 1]));
+                    if (lane == 0) mbar_arrive(smem_u32(&a_full[cg & (ASLOTS - 1)]));
                     ++cg;
                     if (fail_f) break;
                     if (++st == G.n_stages) {
@@ -849,7 +902,8 @@ static const TcPlanDev *canonical_plan(const Setup &s, int budget) {
     auto it = pls.by_budget.find(budget);
     if (it != pls.by_budget.end()) return it->second.get();
     auto pd = std::make_unique<TcPlanDev>();
-    if (!tc_plan(s.ijk.data(), (int)(s.ijk.size() / 3), s.nb, budget, SMEM_BUDGET / 2, pd->h)) return nullptr;
+    if (!tc_plan(s.ijk.data(), (int)(s.ijk.size() / 3), s.nb, budget, SMEM_BUDGET / std::max(2, ASLOTS), pd->h))
+        return nullptr;
     pd->owned = true;
     if (!upload_to(pd->d_sets, pd->h.sets) || !upload_to(pd->d_tiles, pd->h.tiles) ||
         !upload_to(pd->d_rowjk, pd->h.rowjk) || !upload_to(pd->d_pos, pd->h.pos))
@@ -873,7 +927,10 @@ static abs_status tc_run(abs_ctx *ctx, const Setup &s, const TcPlanDev &pd, cons
     G.dense = pl.dense;
     G.stage_bytes = pl.max_stage;
     G.n_stages = std::min(MAX_STAGES, SMEM_BUDGET / std::max(G.stage_bytes, 1));
-    if (G.n_stages < 2) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 stages do not fit shared memory");
+    // the formers' wait on the MMAs of chunk c - ASLOTS is unambiguous only while a stage serves
+    // at most one chunk in that span: at least ASLOTS stages
+    if (G.n_stages < std::max(2, ASLOTS))
+        return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16 stages do not fit shared memory");
     float *partial = (float *)workspace(ctx, "tc.partial", sizeof(float) * (size_t)(ranges * G.dense));
     double *dsum = (double *)workspace(ctx, "tc.dense", sizeof(double) * (size_t)G.dense);
     int *next = (int *)workspace(ctx, "tc.next", sizeof(int));
@@ -962,7 +1019,7 @@ abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields,
             cudaGetLastError();
             return fail(ctx, ABS_ERR_CUDA, "split-BF16: reading the triplet list back");
         }
-        if (!tc_plan(h.data(), n_trip, s.nb, BUDGETS[0], SMEM_BUDGET / 2, caller.h))
+        if (!tc_plan(h.data(), n_trip, s.nb, BUDGETS[0], SMEM_BUDGET / std::max(2, ASLOTS), caller.h))
             return fail(ctx, ABS_ERR_INVALID_ARG, "split-BF16: triplet list outside i <= j <= k < n_bins");
         caller.d_sets = (TcSet *)workspace(ctx, "tc.sets", sizeof(TcSet) * caller.h.sets.size());
         caller.d_tiles = (TcTile *)workspace(ctx, "tc.tiles", sizeof(TcTile) * caller.h.tiles.size());
