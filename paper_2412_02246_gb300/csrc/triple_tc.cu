@@ -88,14 +88,21 @@ constexpr int KC = 64;               // pixels per chunk (4 MMA K-steps of 16)
 constexpr int NFORM = ABS_TC_FORMERS;   // forming / epilogue warps (8 or 16)
 constexpr int FQ = NFORM / 4;           // forming warps per tensor-memory lane quadrant
 constexpr int FPX = KC / FQ;            // pixels of a chunk per forming thread
-constexpr int NT = (NFORM + 2) * 32; // threads per CTA
-// registers per thread: the register file is split over the SM's four schedulers (16,384
-// each) and warps are dealt to them in turn, so the scheduler with the most warps
-// (3 of 10, or 5 of 18) bounds it, in steps of 8
-#define TC_MAXREG (NFORM == 8 ? 168 : 96)
 #ifndef ABS_TC_MAX_TILES
 #define ABS_TC_MAX_TILES 2
 #endif
+#ifndef ABS_TC_ISSUERS
+#define ABS_TC_ISSUERS ABS_TC_MAX_TILES
+#endif
+// MMA-issuing warps (one thread each): issuer e takes the tiles t with t % NISS == e.  A single
+// thread issues at most one tcgen05.mma every ~45 cycles, so the tiles of a set issue in parallel.
+constexpr int NISS = ABS_TC_ISSUERS;
+constexpr int FW0 = 1 + NISS;           // first forming warp (warp 0 loads, warps 1 .. NISS issue)
+constexpr int NT = (NFORM + FW0) * 32;  // threads per CTA
+// registers per thread: the register file is split over the SM's four schedulers (16,384
+// each) and warps are dealt to them in turn, so the scheduler with the most warps
+// (3 of 10 or 11, or 5 of 18 or 19) bounds it, in steps of 8
+#define TC_MAXREG (ABS_TC_FORMERS == 8 ? 168 : 96)
 #ifndef ABS_TC_ASLOTS
 #define ABS_TC_ASLOTS 2
 #endif
@@ -310,14 +317,14 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
         abort_s = 0;
         for (int s = 0; s < G.n_stages; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
-            mbar_init(smem_u32(&done[s]), 1);
+            mbar_init(smem_u32(&done[s]), NISS);
         }
         for (int b = 0; b < ASLOTS; ++b) mbar_init(smem_u32(&a_full[b]), NFORM);
         for (int b = 0; b < 2; ++b) {
-            mbar_init(smem_u32(&d_full[b]), 1);
+            mbar_init(smem_u32(&d_full[b]), NISS);
             mbar_init(smem_u32(&d_empty[b]), NFORM);
         }
-        mbar_init(smem_u32(&fin), 1);
+        mbar_init(smem_u32(&fin), NISS);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 1) {
@@ -410,11 +417,13 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                     }
                 }
             }
-        } else if (warp == 1) {
-            // ---------------- MMA issue (one thread): groups of DRAIN chunks into alternating regions.
-            // Its per-chunk path is kept short (the tile constants live in registers, the stage's
-            // descriptor advances by addition): the tensor pipe idles while this thread is between
-            // chunks once its short queue has drained.
+        } else if (warp <= NISS) {
+            // ---------------- MMA issue (one thread a warp): groups of DRAIN chunks into alternating
+            // regions.  Every issuer walks every chunk (waits and commits alike, so that the
+            // barriers count NISS arrivals a phase) and issues the MMAs of its own tiles.  The
+            // per-chunk path is kept short (tile constants in registers, the stage's descriptor
+            // advanced by addition): the tensor pipe idles while an issuer is between chunks.
+            const int iss = warp - 1;
             if (lane == 0) {
                 uint32_t idesc_t[MAX_TILES], col_t[MAX_TILES], rows_t[MAX_TILES];
 #pragma unroll
@@ -451,6 +460,7 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
 #pragma unroll
                     for (int t = 0; t < MAX_TILES; ++t) {
                         if (t >= S.ntiles) break;
+                        if (t % NISS != iss) continue;
                         // a tile's rows and a K-step move only the descriptors' start-address field
                         // (16-byte units: 8 per ring row, 2 per 16 pixels)
                         const uint32_t acc = tmem + region + col_t[t];
@@ -483,7 +493,7 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
         } else {
             // ---------------- formers; after the first chunk of each group they drain the group before
             const int q = warp & 3;                   // tensor-memory lanes 32 q .. 32 q + 31
-            const int h = (warp - 2) >> 2;            // pixel part of the chunk (FPX pixels), drain blocks
+            const int h = (warp - FW0) >> 2;          // pixel part of the chunk (FPX pixels), drain blocks
             const int row = 32 * q + lane;
             const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
             const int nb_h = n_blk[h];
@@ -618,8 +628,8 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                 if (!mbar_drain(smem_u32(&full[s]), (uint32_t)((uses - 1) & 1))) break;
             }
         }
-        if (warp == 1 && lane == 0) {
-            // every MMA this thread issued is done once a fresh commit arrives
+        if (warp >= 1 && warp <= NISS && lane == 0) {
+            // every MMA the issuers issued is done once a fresh commit of each arrives
             mma_commit(smem_u32(&fin));
             mbar_drain(smem_u32(&fin), 0u);
         }
