@@ -228,9 +228,22 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 
+// Non-blocking test of the phase of the given parity.
+__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
 // Bounded wait for the phase of the given parity; false on timeout or once
-// another role has given up (abort set).
+// another role has given up (abort set).  A phase that has already completed
+// is seen by one non-blocking test (cheaper than a suspending try).
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, const volatile int *abort_flag) {
+    if (mbar_test(mbar, parity)) return true;
     for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
         if (mbar_try(mbar, parity)) return true;
         if (*abort_flag) return false;
