@@ -264,12 +264,21 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
 }
 
-// Sixteen bytes of shared memory at a 32-bit shared address.  Volatile, so it stays in program
-// order with the mbarrier waits that make the data visible.
+// Sixteen bytes of shared memory at a 32-bit shared address.  Not volatile, so the compiler may
+// schedule it freely: callers derive the address from after_wait(), which keeps it below the
+// mbarrier wait that makes the data visible.
 __device__ __forceinline__ float4 lds128(uint32_t a) {
     float4 v;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
     return v;
+}
+
+// x, passed through an opaque volatile instruction: values computed from it cannot be moved above
+// the volatile instructions (mbarrier waits) that precede this one.
+__device__ __forceinline__ uint32_t after_wait(uint32_t x) {
+    uint32_t y;
+    asm volatile("mov.b32 %0, %1;\n" : "=r"(y) : "r"(x) : "memory");
+    return y;
 }
 
 // Where a forming thread's FP32 values of ring m sit in an F window (rings from f_lo, rows of
@@ -544,7 +553,7 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                     }
                     hst[ASLOTS - 1] = st;
                     hsu[ASLOTS - 1] = su;
-                    const uint32_t Fs = smem_u32(F);
+                    const uint32_t Fs = after_wait(smem_u32(F));
 #pragma unroll
                     for (int t = 0; t < MAX_TILES; ++t) {
                         if (t >= S.ntiles) break;
