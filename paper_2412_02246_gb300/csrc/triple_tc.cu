@@ -322,7 +322,7 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                                                      float *__restrict__ partial, int *__restrict__ next_item,
                                                      int32_t *__restrict__ err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full[MAX_STAGES], done[MAX_STAGES], a_full[ASLOTS], d_full[2], d_empty[2], fin;
+    __shared__ __align__(8) uint64_t full[MAX_STAGES], done[MAX_STAGES], a_full[ASLOTS * MAX_TILES], d_full[2], d_empty[2], fin;
     __shared__ uint32_t tmem_holder;
     __shared__ volatile int abort_s;
     __shared__ int item_s;
@@ -341,7 +341,7 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&done[s]), NISS);
         }
-        for (int b = 0; b < ASLOTS; ++b) mbar_init(smem_u32(&a_full[b]), NFORM);
+        for (int b = 0; b < ASLOTS * MAX_TILES; ++b) mbar_init(smem_u32(&a_full[b]), NFORM);
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&d_full[b]), NISS);
             mbar_init(smem_u32(&d_empty[b]), NFORM);
@@ -471,18 +471,19 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                         abort_s = 1;
                         break;
                     }
-                    // the chunk's A buffers (every tile of the set), formed ahead
-                    if (!mbar_wait(smem_u32(&a_full[cg & (ASLOTS - 1)]), (uint32_t)((cg / ASLOTS) & 1), &abort_s)) {
-                        abort_s = 1;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const uint32_t a_slot = tmem + (uint32_t)((cg & (ASLOTS - 1)) * MAX_TILES * A_COLS);
                     const uint32_t first = gc > 0 ? 1u : 0u;
 #pragma unroll
                     for (int t = 0; t < MAX_TILES; ++t) {
                         if (t >= S.ntiles) break;
                         if (t % NISS != iss) continue;
+                        // this tile's A buffers, formed ahead
+                        if (!mbar_wait(smem_u32(&a_full[(cg & (ASLOTS - 1)) * MAX_TILES + t]),
+                                       (uint32_t)((cg / ASLOTS) & 1), &abort_s)) {
+                            abort_s = 1;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                         // a tile's rows and a K-step move only the descriptors' start-address field
                         // (16-byte units: 8 per ring row, 2 per 16 pixels)
                         const uint32_t acc = tmem + region + col_t[t];
@@ -581,11 +582,16 @@ __global__ void __maxnreg__(TC_MAXREG) k_triple_tc(TcParams G, TcPlanes PL,
                             tmem_st(ta + 8u * part, hi);
                             tmem_st(ta + 32u + 8u * part, lo);
                         }
+                        // tile t's A buffers are complete: its issuer may start while the next is formed
+                        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+                        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(smem_u32(&a_full[(cg & (ASLOTS - 1)) * MAX_TILES + t]));
                     }
-                    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-                    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(smem_u32(&a_full[cg & (ASLOTS - 1)]));
+                    // tiles the set does not have: their barriers keep step with the chunks
+                    if (lane == 0)
+                        for (int t = S.ntiles; t < MAX_TILES; ++t)
+                            mbar_arrive(smem_u32(&a_full[(cg & (ASLOTS - 1)) * MAX_TILES + t]));
                     ++cg;
                     if (fail_f) break;
                     if (++st == G.n_stages) {
