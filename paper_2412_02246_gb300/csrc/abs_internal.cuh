@@ -143,7 +143,10 @@ const Setup *get_setup(abs_ctx *ctx, const abs_config *cfg, abs_status &st);
 // Each enqueues on ctx->stream and returns ABS_OK / an error status.
 // Gridding is split in a per-baseline-set plan (sort by uv tile and cell) and a
 // per-realisation accumulation that reuses it.
-abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv);
+// rings_only: the estimate's plan, over the visibilities whose footprint can reach a ring
+// cell only (launch_grid_accumulate's estimate form reads it).
+abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv,
+                            bool rings_only = false);
 // With d_grid == d_wsum == nullptr only the FP64 accumulators (and, if d_mask,
 // the filled mask) are produced.  acc_zeroed: the caller has already cleared
 // the accumulators (grid_acc_buffers) on this stream's timeline.

@@ -782,7 +782,7 @@ static abs_status estimate_many(abs_ctx *ctx, const Setup &s, int64_t n_vis, con
         cudaMemcpyAsync((void *)d_vis, h_vis, uvb * (size_t)n_real, cudaMemcpyHostToDevice, ctx->stream);
     }
     if (copy_in) cudaMemcpyAsync((void *)d_uv, h_uv, uvb, cudaMemcpyHostToDevice, ctx->stream);
-    const abs_status sp = launch_grid_plan(ctx, s, n_vis, d_uv);
+    const abs_status sp = launch_grid_plan(ctx, s, n_vis, d_uv, true);
     if (pre_zero) cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
     if (sp != ABS_OK) return sp;
     for (int32_t r = 0; r < n_real; ++r) {

@@ -21,6 +21,8 @@
 // with the fractional offset f = u/dU - c carried as a float pair (the exact
 // division residual) and the exponent argument formed in double-float, so
 // that the only sizeable error is that of expf itself.
+#include <algorithm>
+
 #include "abs_internal.cuh"
 
 namespace absk {
@@ -35,14 +37,20 @@ struct GridGeom {
     float du, inv_du, s_hi, s_lo;
 };
 
-GridGeom geom(const Setup &s) {
+// The key space of the plan: every nearest cell whose footprint can reach the grid
+// (|c| <= half + r), or, with rings_only (the estimate), only those whose footprint can
+// reach a ring cell (|c| <= R + r, R the largest |g_x| of a ring cell): a visibility
+// outside adds to no cell the estimate reads, and the smaller key space sorts in fewer
+// or narrower passes.  Cells keep their place in the full n x n accumulators either way.
+GridGeom geom(const Setup &s, bool rings_only = false) {
     GridGeom g;
     g.n = s.n;
     g.half = s.half;
     g.r = s.kernel == ABS_KERNEL_NGP ? 0 : s.r;
-    g.ks = s.n - 1 + 2 * g.r;
+    const int reach = rings_only ? std::min(s.half, std::max(s.R, 0)) : s.half;
+    g.ks = 2 * (reach + g.r) + 1;
     g.tt = (int)cdiv(g.ks, TS);
-    g.off = s.half + g.r;
+    g.off = reach + g.r;
     g.kernel = s.kernel;
     g.du = s.du;
     g.inv_du = (float)(1.0 / (double)s.du);
@@ -728,8 +736,8 @@ bool scan_u32(abs_ctx *ctx, const uint32_t *in, int64_t len, uint32_t *out, uint
 // The key of an invalid visibility: above every (tile, cell) key.
 static uint32_t plan_key_none(const PlanBufs &b) { return (uint32_t)b.ntiles << CB; }
 
-abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv) {
-    const GridGeom G = geom(s);
+abs_status launch_grid_plan(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_uv, bool rings_only) {
+    const GridGeom G = geom(s, rings_only);
     PlanBufs b;
     if (!plan_bufs(ctx, G, n_vis, b)) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
     if ((uint64_t)b.ntiles << CB >= 0x7fffffffull) return fail(ctx, ABS_ERR_UNSUPPORTED, "uv grid too large");
@@ -786,12 +794,13 @@ void grid_acc_buffers(abs_ctx *ctx, const Setup &s, double **acc) {
 
 abs_status launch_grid_accumulate(abs_ctx *ctx, const Setup &s, int64_t n_vis, const float *d_vis,
                                   float *d_grid, float *d_wsum, uint8_t *d_mask, bool acc_zeroed) {
-    const GridGeom G = geom(s);
+    // the estimate path (no FP32 outputs; its plan was made with rings_only) accumulates what
+    // its weighting needs
+    const bool estimate = !d_grid && !d_wsum;
+    const GridGeom G = geom(s, estimate);
     PlanBufs b;
     if (!plan_bufs(ctx, G, n_vis, b)) return fail(ctx, ABS_ERR_OOM, "grid plan workspace");
     const int64_t cells = (int64_t)s.n * s.n;
-    // the estimate path (no FP32 outputs) accumulates what its weighting needs
-    const bool estimate = !d_grid && !d_wsum;
     const int wm = !estimate ? GW_SUM
                    : s.weight_mode == ABS_W_PAPER_LITERAL ? GW_COUNT
                    : s.weight_mode == ABS_W_NOISE ? GW_SUM_SQ : GW_SUM;
