@@ -55,7 +55,7 @@
 // it (d_empty); the issuer meanwhile fills the other region.  After the item's
 // last chunk the formers write the long accumulators, column-major by tile
 // (lanes contiguous), to the item's pixel range of the partial-sum array.  A
-// second kernel adds the pixel ranges in FP64 in a fixed order and gathers each
+// second kernel adds the pixel ranges in double-float in a fixed order and gathers each
 // triplet's entry.
 //
 // Rates that shaped this design, measured on GB300 with microbenchmarks: an MMA
@@ -721,23 +721,33 @@ __global__ void __launch_bounds__(256) k_split_pad(int nb, int nbp, int64_t P, i
     f32[row + ((((u >> 2) ^ key) << 2) | (u & 3))] = 0.f;
 }
 
-// dense[x] = sum over pixel ranges of partial[r][x] in FP64 (a fixed order).
+// dense[x] = sum over pixel ranges of partial[r][x] (a fixed order).
 __global__ void __launch_bounds__(256) k_tc_reduce(int64_t dense, int n_ranges, const float *__restrict__ partial,
                                                    double *__restrict__ out) {
     const int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= dense) return;
-    // eight loads in flight, added in range order
-    double s = 0.0;
+    // eight loads in flight, added in range order into a double-float sum (TwoSum, then
+    // Fast2Sum; about 2^-44 relative, in FP32 arithmetic: GB300's FP64 pipe, which also
+    // converts, is narrow), widened to FP64 once
+    float sh = 0.f, sl = 0.f;
+    auto add = [&](float v) {
+        const float t = __fadd_rn(sh, v);
+        const float bp = __fsub_rn(t, sh);
+        const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+        const float lo = __fadd_rn(sl, e);
+        sh = __fadd_rn(t, lo);
+        sl = __fsub_rn(lo, __fsub_rn(sh, t));
+    };
     int r = 0;
     for (; r + 8 <= n_ranges; r += 8) {
         float v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) v[u] = __ldcs(&partial[(size_t)(r + u) * dense + x]);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) s += (double)v[u];
+        for (int u = 0; u < 8; ++u) add(v[u]);
     }
-    for (; r < n_ranges; ++r) s += (double)__ldcs(&partial[(size_t)r * dense + x]);
-    out[x] = s;
+    for (; r < n_ranges; ++r) add(__ldcs(&partial[(size_t)r * dense + x]));
+    out[x] = (double)sh + (double)sl;
 }
 
 // S[t] = inv_p dense[pos[t]].
