@@ -225,6 +225,17 @@ __global__ void k_ring_cells(CountGeom G, const int64_t *__restrict__ q, const u
 // One block: choose the route (direct or holes) from the pair counts it would
 // visit, and write the work items of every job it needs: one per (pair a <= b,
 // chunk of the larger set, chunk of the smaller set).  Items of jobs that look
+// Ring pair (a <= b) of pair index pr = a nb - a (a - 1) / 2 + (b - a): a from the
+// quadratic's root in FP32, corrected by whole steps.
+__device__ __forceinline__ void pair_of(int pr, int nb, int &a, int &b) {
+    const float B = 2.f * (float)nb + 1.f;
+    a = (int)((B - sqrtf(fmaxf(B * B - 8.f * (float)pr, 0.f))) * 0.5f);
+    a = max(0, min(a, nb - 1));
+    while (a > 0 && a * nb - a * (a - 1) / 2 > pr) --a;
+    while (a + 1 < nb && (a + 1) * nb - (a + 1) * a / 2 <= pr) ++a;
+    b = a + (pr - (a * nb - a * (a - 1) / 2));
+}
+
 // up the filled map go to list 0, the annulus map to list 1.
 // item = (a, b, outer start, inner start | job << 27 | outer-is-x << 31)
 __device__ void count_items_block(int nb, const int32_t *__restrict__ counts, int chunk, int need_full,
@@ -246,9 +257,8 @@ __device__ void count_items_block(int nb, const int32_t *__restrict__ counts, in
     __syncthreads();
     unsigned long long wd = 0, we = 0;
     for (int pr = threadIdx.x; pr < npair; pr += blockDim.x) {
-        int a = 0, rem = pr;
-        while (rem >= nb - a) { rem -= nb - a; ++a; }
-        const int b = a + rem;
+        int a, b;
+        pair_of(pr, nb, a, b);
         wd += (unsigned long long)(cF[a] / 2) * cF[b];
         we += (unsigned long long)(cH[a] / 2) * cA[b] + 2ull * (cF[a] / 2) * cH[b];
     }
@@ -283,22 +293,31 @@ __device__ void count_items_block(int nb, const int32_t *__restrict__ counts, in
         const int job = jobs[jj];
         const int lst = job_map_a(job) ? 1 : 0;
         const int32_t *cx = cs + job_x(job) * nb, *cy = cs + job_y(job) * nb;
-        for (int p0 = 0; p0 < npair; p0 += blockDim.x) {
-            const int pr = p0 + threadIdx.x;
-            int a = 0, b = 0, n_ic = 1, nchunks = 0;
-            bool outer_x = false;
-            if (pr < npair) {
-                int rem = pr;
-                while (rem >= nb - a) { rem -= nb - a; ++a; }
-                b = a + rem;
-                const int hx = cx[a] / 2, ny = cy[b];
-                outer_x = hx >= ny;
-                const int no = outer_x ? hx : ny, ni = outer_x ? ny : hx;
-                const int n_oc = (no + chunk - 1) / chunk;
-                n_ic = (ni + INNER - 1) / INNER;
-                nchunks = ni > 0 ? n_oc * n_ic : 0;
+        // PPT consecutive pairs a thread, blockDim.x * PPT pairs a batch (b_pos holds 1024 + 1)
+        constexpr int PPT = 4;
+        const int per_batch = (int)blockDim.x * PPT;
+        for (int p0 = 0; p0 < npair; p0 += per_batch) {
+            int nch[PPT], x = 0;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                const int slot = threadIdx.x * PPT + k, pr = p0 + slot;
+                int a = 0, b = 0, n_ic = 1, nchunks = 0;
+                bool outer_x = false;
+                if (pr < npair) {
+                    pair_of(pr, nb, a, b);
+                    const int hx = cx[a] / 2, ny = cy[b];
+                    outer_x = hx >= ny;
+                    const int no = outer_x ? hx : ny, ni = outer_x ? ny : hx;
+                    const int n_oc = (no + chunk - 1) / chunk;
+                    n_ic = (ni + INNER - 1) / INNER;
+                    nchunks = ni > 0 ? n_oc * n_ic : 0;
+                }
+                nch[k] = nchunks;
+                x += nchunks;
+                b_ab[slot] = a | b << 8 | (outer_x ? 1 << 16 : 0);
+                b_nic[slot] = n_ic;
             }
-            int x = nchunks;
+            const int mine = x;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int y = __shfl_up_sync(FULL, x, o);
@@ -311,15 +330,18 @@ __device__ void count_items_block(int nb, const int32_t *__restrict__ counts, in
                 if (w < warp) before += wsum[w];
                 tot += wsum[w];
             }
-            b_pos[threadIdx.x] = before + x - nchunks;
-            if (threadIdx.x == 0) b_pos[blockDim.x] = tot;
-            b_ab[threadIdx.x] = a | b << 8 | (outer_x ? 1 << 16 : 0);
-            b_nic[threadIdx.x] = n_ic;
+            int run = before + x - mine;
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+                b_pos[threadIdx.x * PPT + k] = run;
+                run += nch[k];
+            }
+            if (threadIdx.x == 0) b_pos[per_batch] = tot;
             __syncthreads();
             const int base = carry_s[lst];
             int4 *items = lst ? items1 : items0;
             for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-                int lo = 0, hi = (int)blockDim.x - 1;   // last pair q with b_pos[q] <= t
+                int lo = 0, hi = per_batch - 1;   // last pair q with b_pos[q] <= t
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
                     if (b_pos[mid] <= t) lo = mid;

@@ -113,7 +113,7 @@ constexpr int MAX_STAGES = 8;
 constexpr int TMEM_COLS = 512;
 constexpr int A_COLS = 64;           // one A buffer: 32 columns of hi pairs, 32 of lo pairs
 constexpr int NABUF = ASLOTS * MAX_TILES;   // A buffers: every tile of ASLOTS chunks (formers ahead of the MMAs)
-constexpr int BOX_ROWS = 16;         // window sizes (rings a copy) are multiples of it
+constexpr int B_ROWS = 8;            // B windows start and end on 8-ring boundaries (the swizzle atom)
 #ifndef ABS_TC_DRAIN
 #define ABS_TC_DRAIN 8
 #endif
@@ -811,14 +811,18 @@ static bool tc_plan(const int32_t *ijk, int n_trip, int nb, int col_budget, int 
             lanes[x] = make_short2((short)kj[x].second, (short)kj[x].first);
             lane_of[{kj[x].second, kj[x].first}] = rb * TM + x;
         }
-        // the block's ring columns, cut into tiles of at most MAX_TILE_N (same rows)
+        // the block's ring columns, cut into tiles of at most MAX_TILE_N (same rows); a tile that
+        // would reach past the last ring (rounded up to 8) moves down to end there, so that no
+        // plane needs rings past it (a few columns more at its low end instead)
         const int ilo = lo & ~7;
         const int n_all = (int)cdiv(hi - ilo + 1, 16) * 16;
+        const int ring_cap = (int)cdiv(nb, B_ROWS) * B_ROWS;
         first_tile[rb] = (int)pl.tiles.size();
         for (int c0 = 0; c0 < n_all; c0 += MAX_TILE_N) {
             TcTile T;
             T.i_lo = ilo + c0;
             T.n = std::min(MAX_TILE_N, n_all - c0);
+            if (T.i_lo + T.n > ring_cap) T.i_lo = std::max(0, (ring_cap - T.n) & ~(B_ROWS - 1));
             if (T.n > col_budget) return false;
             T.acc_off = pl.dense;
             pl.dense += (int64_t)TM * T.n;
@@ -847,8 +851,8 @@ static bool tc_plan(const int32_t *ijk, int n_trip, int nb, int col_budget, int 
             }
             const int nblo = std::min(blo, T.i_lo), nbhi = std::max(bhi, T.i_lo + T.n);
             const int nflo = std::min(flo, jmin), nfhi = std::max(fhi, kmax + 1);
-            const int bn = (int)cdiv(nbhi - nblo, BOX_ROWS) * BOX_ROWS, fn = (int)cdiv(nfhi - nflo, BOX_ROWS) * BOX_ROWS;
-            const int stage = 2 * bn * 128 + 2 * fn * 128;
+            const int bn = (int)cdiv(nbhi - nblo, B_ROWS) * B_ROWS, fn = nfhi - nflo;
+            const int stage = (int)cdiv(2 * bn * 128 + fn * 256, 1024) * 1024;   // stages stay 1024-aligned
             if (S.ntiles > 0 && (cols + T.n > col_budget || stage > stage_cap)) break;
             cols += T.n;
             blo = nblo, bhi = nbhi, flo = nflo, fhi = nfhi;
@@ -856,7 +860,7 @@ static bool tc_plan(const int32_t *ijk, int n_trip, int nb, int col_budget, int 
             ++S.ntiles;
             ++t;
         }
-        pl.max_stage = std::max(pl.max_stage, 2 * S.b_n * 128 + 2 * S.f_n * 128);
+        pl.max_stage = std::max(pl.max_stage, (int)cdiv(2 * S.b_n * 128 + S.f_n * 256, 1024) * 1024);
         pl.plane_rows = std::max(pl.plane_rows, std::max(S.b_lo + S.b_n, S.f_lo + S.f_n));
         pl.sets.push_back(S);
     }
