@@ -499,7 +499,9 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
                 }
             }
             lin1[q] = l;
-            xr1[q] = x + G.R;
+            // an empty slot fails the x-range test of every lookup (|x2| <= R), so the lookups
+            // need no separate validity test
+            xr1[q] = v1[q] ? x + G.R : 0x40000000;
         }
         const uint32_t span = 2u * (uint32_t)G.R;   // |x1 + x2| <= R  <=>  x1 + R + x2 in [0, 2R]
         int cur[G1];
@@ -540,7 +542,7 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
                 const int l2 = stage[k + u], x2 = stage_x[k + u];
 #pragma unroll
                 for (int q = 0; q < G1; ++q)
-                    rr[u][q] = (v1[q] && (uint32_t)(xr1[q] + x2) <= span) ? (int)map[abs(lin1[q] + l2)] : 0;
+                    rr[u][q] = ((uint32_t)(xr1[q] + x2) <= span) ? (int)map[abs(lin1[q] + l2)] : 0;
             }
 #pragma unroll
             for (int u = 0; u < KU; ++u) {
@@ -559,7 +561,7 @@ __global__ void __launch_bounds__(CT) k_count_pairs(CountGeom G, const int4 *__r
             const int l2 = stage[k], x2 = stage_x[k];
 #pragma unroll
             for (int q = 0; q < G1; ++q) {
-                const int r = (v1[q] && (uint32_t)(xr1[q] + x2) <= span) ? (int)map[abs(lin1[q] + l2)] : 0;
+                const int r = ((uint32_t)(xr1[q] + x2) <= span) ? (int)map[abs(lin1[q] + l2)] : 0;
                 if (r != cur[q]) {
                     myhist[(size_t)cur[q] * 32] += (uint16_t)cnt[q];
                     cur[q] = r;
