@@ -45,8 +45,14 @@
 namespace absk {
 namespace {
 
-constexpr int G1 = 4;            // g1 cells per thread
-constexpr int KU = 4;            // inner cells whose map loads are issued together
+#ifndef ABS_COUNT_G1
+#define ABS_COUNT_G1 4
+#endif
+#ifndef ABS_COUNT_KU
+#define ABS_COUNT_KU 4
+#endif
+constexpr int G1 = ABS_COUNT_G1;   // g1 cells per thread
+constexpr int KU = ABS_COUNT_KU;   // inner cells whose map loads are issued together
 constexpr int CT = 256;          // threads per counting CTA (max)
 constexpr int INNER = 512;       // inner cells per work item (bounds the work of one item)
 constexpr unsigned FULL = 0xffffffffu;
