@@ -30,6 +30,15 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
 * shape_params / rebin (results layer): hand-worked triangle shapes
   (equilateral, squeezed, folded), the bin edges, count-weighted means of a
   constant and of a linear B, and the ensemble mean / spread of +-B
+* cube_means / delay_modes / triple3d_bruteforce (multi-frequency form):
+  one channel reduces to the 2-D brute force; a separable cube x(g) f(c)
+  factorises into the 2-D sums times the delay sums of numpy's FFT of f;
+  cyclic shifts and reversal of the channel order leave B unchanged;
+  Im S vanishes
+* delay_counts / triplets_3d: closed form of the one-bin delay count,
+  against the brute-force 3-D counts on a fully filled tiny grid
+* fft_form_3d: against the 3-D brute force (sums to rounding), aliasing
+  below N_z = 3 t_max + 1
 """
 from __future__ import annotations
 
@@ -84,6 +93,10 @@ def _load():
     lib.orc_ellbar.restype = None
     lib.orc_normalise.argtypes = [i32, P, P, f64, P]
     lib.orc_normalise.restype = None
+    lib.orc_delay_modes.argtypes = [i32, i32, P, P, i32, P, P]
+    lib.orc_delay_modes.restype = ctypes.c_int
+    lib.orc_triple3d_bruteforce.argtypes = [i32, i32, P, P, i32, P, i32, P, i32, P, P, P, P]
+    lib.orc_triple3d_bruteforce.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -537,3 +550,181 @@ def simulate_vis(sky: np.ndarray, dtheta: float, uv: np.ndarray, beam: str = "no
         out[s0:s0 + 256] = (ph * W[None]).sum(axis=(1, 2))
     return out
 
+
+
+# ------------------------------------------------------------------ multi-frequency (3-D) form
+#
+# A reading of the generalisation that Sec. 1 and Sec. 5 name as future work:
+# the channels are gridded one by one on the same uv grid, the cells filled in
+# every channel are transformed along frequency (delay modes t), and the voxels
+# (g, t) are binned by ring and by |t|; a bin triplet sums over the voxel
+# triangles that close in both g and t.  See abs_oracle.c for the definitions.
+
+
+def cube_means(n: int, du: float, uvs, viss, kernel: str = "gauss", sigma_cells: float = 1.0,
+               radius_cells: int = 3, threads: int | None = None):
+    """Per-channel gridding (Eq. vg) and means: X complex128 [n_chan, n, n], filled uint8.
+    The channels are independent; they are gridded on host threads (the C loops run
+    outside the interpreter lock)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(c):
+        return mean_grid(grid(n, du, uvs[c], viss[c], kernel, sigma_cells, radius_cells))
+
+    with ThreadPoolExecutor(max_workers=threads or os.cpu_count() or 1) as ex:
+        out = list(ex.map(one, range(len(uvs))))
+    return np.stack([o[0] for o in out]), np.stack([o[1] for o in out])
+
+
+def delay_modes(X: np.ndarray, filled: np.ndarray, t_max: int):
+    """Delay modes Xt[t + t_max] = sum_c X_c exp(-2 pi i c t / n_chan) on the cells filled in
+    every channel (0 elsewhere), |t| <= t_max, and that common mask."""
+    n_chan, n = X.shape[0], X.shape[1]
+    Xt = np.zeros((2 * t_max + 1, n, n, 2))
+    common = np.zeros((n, n), np.uint8)
+    rc = _load().orc_delay_modes(n, n_chan, _p(_x2(X)), _p(np.ascontiguousarray(filled, np.uint8)),
+                                 int(t_max), _p(Xt), _p(common))
+    if rc != 0:
+        raise ValueError("delay_modes needs 0 <= 2 t_max < n_chan")
+    return Xt[..., 0] + 1j * Xt[..., 1], common
+
+
+def delay_bin(t: int, tau) -> int:
+    """Delay bin a of a delay index t: tau_a <= |t| < tau_{a+1}, or -1."""
+    for a in range(len(tau) - 1):
+        if tau[a] <= abs(t) < tau[a + 1]:
+            return a
+    return -1
+
+
+def delay_counts(tau, t_max: int) -> np.ndarray:
+    """T1[a][b][c] = number of ordered (t1, t2, t3), |t| <= t_max, t1 + t2 + t3 = 0, with
+    t1, t2, t3 in the delay bins a, b, c (pure-Python enumeration)."""
+    na = len(tau) - 1
+    T1 = np.zeros((na, na, na), np.int64)
+    for t1 in range(-t_max, t_max + 1):
+        for t2 in range(-t_max, t_max + 1):
+            t3 = -(t1 + t2)
+            if abs(t3) > t_max:
+                continue
+            a, b, c = delay_bin(t1, tau), delay_bin(t2, tau), delay_bin(t3, tau)
+            if min(a, b, c) >= 0:
+                T1[a, b, c] += 1
+    return T1
+
+
+def triplets_3d(q: np.ndarray, tau) -> np.ndarray:
+    """Canonical bin triplets u <= v <= w (u = m n_dbins + a) of the 3-D form: the rings
+    (sorted) close a triangle in the 2-D test of `triplets`, and the delay bins close one
+    (their delay count is > 0)."""
+    na = len(tau) - 1
+    T1 = delay_counts(tau, int(tau[-1]) - 1)
+    ring_ok = {tuple(r) for r in np.asarray(triplets(q)).reshape(-1, 3).tolist()}
+    nb3 = (len(q) - 1) * na
+    out = []
+    for u in range(nb3):
+        for v in range(u, nb3):
+            for w in range(v, nb3):
+                if tuple(sorted((u // na, v // na, w // na))) in ring_ok and T1[u % na, v % na, w % na] > 0:
+                    out.append((u, v, w))
+    return np.asarray(out, np.int32).reshape(-1, 3)
+
+
+def triple3d_bruteforce(Xt: np.ndarray, common: np.ndarray, q: np.ndarray, tau, uvw: np.ndarray):
+    """(S complex128 [t], |.|-sum float64 [t], T int64 [t]) over all closed voxel triangles."""
+    t_max = (Xt.shape[0] - 1) // 2
+    n = Xt.shape[1]
+    uvw = np.ascontiguousarray(uvw, np.int32).reshape(-1, 3)
+    nt = len(uvw)
+    S = np.zeros((max(nt, 1), 2))
+    A = np.zeros(max(nt, 1))
+    T = np.zeros(max(nt, 1), np.int64)
+    tau = np.ascontiguousarray(tau, np.int32)
+    xt2 = np.ascontiguousarray(np.stack([Xt.real, Xt.imag], -1))
+    rc = _load().orc_triple3d_bruteforce(n, int(t_max), _p(xt2), _p(np.ascontiguousarray(common, np.uint8)),
+                                         len(q) - 1, _p(np.ascontiguousarray(q, np.int64)), len(tau) - 1,
+                                         _p(tau), nt, _p(uvw), _p(S), _p(A), _p(T))
+    if rc != 0:
+        raise MemoryError("orc_triple3d_bruteforce: allocation failed")
+    return (S[:nt, 0] + 1j * S[:nt, 1]), A[:nt], T[:nt]
+
+
+def counts_3d(common: np.ndarray, q: np.ndarray, tau, uvw: np.ndarray) -> np.ndarray:
+    """T_uvw = T2(rings of u, v, w) x T1(delay bins of u, v, w): the voxel triangles close
+    in g and in t independently and the common mask does not depend on t, so the 3-D count
+    is the 2-D count of `triple_bruteforce` on the common mask times `delay_counts`."""
+    na = len(tau) - 1
+    uvw = np.asarray(uvw, np.int64).reshape(-1, 3)
+    rings = np.sort(uvw // na, axis=1)
+    uniq, inv = np.unique(rings, axis=0, return_inverse=True)
+    n = common.shape[0]
+    _, _, T2 = triple_bruteforce(np.ones((n, n), np.complex128), common, q, uniq.astype(np.int32))
+    T1 = delay_counts(tau, int(tau[-1]) - 1)
+    d = uvw % na
+    return T2[inv.ravel()] * T1[d[:, 0], d[:, 1], d[:, 2]]
+
+
+def _fftn(Z):
+    try:
+        import scipy.fft
+        return scipy.fft.fftn(Z, workers=os.cpu_count() or 1)
+    except ImportError:
+        return np.fft.fftn(Z)
+
+
+def cube_fields(Xt: np.ndarray, common: np.ndarray, q: np.ndarray, tau, N: int, Nz: int):
+    """Real 3-D fields D_u(z, p) = sum over the voxels (g, t) of bin u of
+    Xt(g, t) exp(-2 pi i (t z / N_z + g.p / N)) by numpy's FFT, float64 [n_bins n_dbins,
+    N_z, N, N] (imaginary parts dropped), and the largest |imaginary part| seen."""
+    t_max = (Xt.shape[0] - 1) // 2
+    n = common.shape[0]
+    half = n // 2 - 1
+    gy, gx = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    gy = np.where(gy > n // 2, gy - n, gy)
+    gx = np.where(gx > n // 2, gx - n, gx)
+    r2 = gx.astype(np.int64) ** 2 + gy.astype(np.int64) ** 2
+    na = len(tau) - 1
+    nb = len(q) - 1
+    D = np.zeros((nb * na, Nz, N, N))
+    im = 0.0
+    for m in range(nb):
+        cells = np.nonzero(((np.abs(gx) <= half) & (np.abs(gy) <= half) & (common > 0)
+                            & (r2 >= q[m]) & (r2 < q[m + 1])).ravel())[0]
+        for a in range(na):
+            Z = np.zeros((Nz, N, N), np.complex128)
+            for t in range(-t_max, t_max + 1):
+                if delay_bin(t, tau) != a:
+                    continue
+                Z[t % Nz, gy.ravel()[cells] % N, gx.ravel()[cells] % N] += Xt[t + t_max].ravel()[cells]
+            F = _fftn(Z)
+            im = max(im, float(np.abs(F.imag).max()))
+            D[m * na + a] = F.real
+    return D, im
+
+
+def fft_form_3d(Xt, common, q, tau, uvw, N: int, Nz: int, fields=None, block: int = 65536):
+    """S_uvw = (N^2 N_z)^-1 sum over voxels of D_u D_v D_w (the FFT route of Sec. 2 in three
+    dimensions), the sum over voxels by matrix products as in `fft_form_all` (per middle
+    bin v, rows u, columns w; voxels `block` at a time).  Returns (S, D)."""
+    uvw = np.asarray(uvw, np.int64).reshape(-1, 3)
+    D = cube_fields(Xt, common, q, tau, N, Nz)[0] if fields is None else fields
+    nb3 = D.shape[0]
+    Df = D.reshape(nb3, -1)
+    P = Df.shape[1]
+    vs = np.unique(uvw[:, 1])
+    span = {}
+    for v in vs:
+        sel = np.nonzero(uvw[:, 1] == v)[0]
+        span[v] = (sel, int(uvw[sel, 0].min()), int(uvw[sel, 0].max()) + 1, int(uvw[sel, 2].min()),
+                   int(uvw[sel, 2].max()) + 1)
+    MS = {v: np.zeros((span[v][2] - span[v][1], span[v][4] - span[v][3])) for v in vs}
+    for p0 in range(0, P, block):
+        Db = Df[:, p0:p0 + block]
+        for v in vs:
+            _, u0, u1, w0, w1 = span[v]
+            MS[v] += Db[u0:u1] @ (Db[w0:w1] * Db[v]).T
+    S = np.zeros(len(uvw))
+    for v in vs:
+        sel, u0, _, w0, _ = span[v]
+        S[sel] = MS[v][uvw[sel, 0] - u0, uvw[sel, 2] - w0]
+    return S / (float(N) * N * Nz), D

@@ -20,6 +20,22 @@
  *   estimate      B_ijk = Re S_ijk / (A T_ijk)   (Eq. estimator_t read as the
  *                 average over closed triangles stated after it, Sec. 2).
  *
+ * Multi-frequency (3-D) form, a reading of the generalisation that Sec. 1
+ * and Sec. 5 name as future work (the paper gives no formula for it):
+ *
+ *   channels      every channel c = 0 .. n_chan-1 is gridded on the same uv
+ *                 grid as above (Eq. vg), giving X_c(g) and its filled mask;
+ *   common cells  a cell is used only if it is filled in every channel;
+ *   delay modes   Xt(g, t) = sum_c X_c(g) exp(-2 pi i c t / n_chan) on those
+ *                 cells (the line-of-sight transform along frequency), for
+ *                 integer t with |t| <= t_max, 2 t_max < n_chan;
+ *   bins          voxel (g, t) lies in bin u = m n_dbins + a when g is in
+ *                 ring a_m and tau_a <= |t| < tau_{a+1};
+ *   triple sum    S_uvw = sum over ordered voxel triples, one in each of the
+ *                 bins u, v, w, with g1+g2+g3 = 0 and t1+t2+t3 = 0, of
+ *                 Xt(g1,t1) Xt(g2,t2) Xt(g3,t3); T_uvw = their number;
+ *   estimate      B_uvw = Re S_uvw / (A T_uvw), as in the 2-D form.
+ *
  * The triple sum is done by brute force over pairs of ring cells (the O(N^4)
  * "direct" route that Sec. 2 contrasts with the FFT route); no transform is
  * involved, so the FFT identity the CUDA path relies on is checked, not
@@ -344,4 +360,128 @@ void orc_normalise(int32_t n_trip, const double *S, const int64_t *T, double nor
 {
     for (int32_t t = 0; t < n_trip; ++t)
         B[t] = T[t] > 0 ? S[2 * t] / (norm_A * (double)T[t]) : NAN;
+}
+
+/* ------------------------------------------------------------------------
+ * Multi-frequency (3-D) form.  See the file header for the definitions.
+ * ------------------------------------------------------------------------ */
+
+/* Delay modes of the channel cube.  X: complex [n_chan][n*n][2] (the
+ * per-channel means of orc_mean_grid), filled: [n_chan][n*n].  Outputs:
+ * common[n*n] = 1 where every channel is filled; Xt: complex
+ * [2 t_max + 1][n*n][2], Xt[t + t_max] = sum_c X_c exp(-2 pi i c t / n_chan)
+ * on common cells and 0 elsewhere.  Returns 1 unless 0 <= 2 t_max < n_chan. */
+int orc_delay_modes(int32_t n, int32_t n_chan, const double *X, const uint8_t *filled, int32_t t_max,
+                    double *Xt, uint8_t *common)
+{
+    if (n_chan < 1 || t_max < 0 || 2 * t_max >= n_chan) return 1;
+    const int64_t cells = (int64_t)n * n;
+    const int32_t nt = 2 * t_max + 1;
+    for (int64_t p = 0; p < cells; ++p) {
+        uint8_t all = 1;
+        for (int32_t c = 0; c < n_chan; ++c)
+            if (!filled[(int64_t)c * cells + p]) all = 0;
+        common[p] = all;
+        for (int32_t ti = 0; ti < nt; ++ti) {
+            const int32_t t = ti - t_max;
+            double sr = 0.0, si = 0.0;
+            if (all)
+                for (int32_t c = 0; c < n_chan; ++c) {
+                    /* exp(-2 pi i c t / n_chan), the exponent reduced to [0, n_chan) */
+                    const int64_t e = (((int64_t)c * t) % n_chan + n_chan) % n_chan;
+                    const double ang = -2.0 * M_PI * (double)e / (double)n_chan;
+                    const double wr = cos(ang), wi = sin(ang);
+                    const double xr = X[2 * ((int64_t)c * cells + p)], xi = X[2 * ((int64_t)c * cells + p) + 1];
+                    sr += xr * wr - xi * wi;
+                    si += xr * wi + xi * wr;
+                }
+            Xt[2 * ((int64_t)ti * cells + p)] = sr;
+            Xt[2 * ((int64_t)ti * cells + p) + 1] = si;
+        }
+    }
+    return 0;
+}
+
+/* Delay bin of a delay index t: a with tau_a <= |t| < tau_{a+1}, or -1. */
+static int32_t dbin_of(int32_t t, int32_t n_dbins, const int32_t *tau)
+{
+    const int32_t at = t < 0 ? -t : t;
+    for (int32_t a = 0; a < n_dbins; ++a)
+        if (at >= tau[a] && at < tau[a + 1]) return a;
+    return -1;
+}
+
+typedef struct { int32_t gx, gy, t, u; int64_t p; } voxel;
+
+/* Brute-force 3-D triple sums and counts for a list of bin triplets (u, v, w):
+ * every ordered pair of voxels in the bins is visited once, the third voxel
+ * is (-(g1+g2), -(t1+t2)), and the product is filed under the bins of the
+ * three.  Xt, common as from orc_delay_modes; S: complex [n_trip][2]; absum
+ * (may be NULL): sum of |product|; T: int64 [n_trip]. */
+int orc_triple3d_bruteforce(int32_t n, int32_t t_max, const double *Xt, const uint8_t *common, int32_t n_bins,
+                            const int64_t *q, int32_t n_dbins, const int32_t *tau, int32_t n_trip,
+                            const int32_t *uvw, double *S, double *absum, int64_t *T)
+{
+    const int64_t cells = (int64_t)n * n;
+    ring_cell *c = NULL;
+    const int32_t nc = collect_ring_cells(n, common, n_bins, q, &c);
+    const int32_t nt = 2 * t_max + 1;
+    voxel *vx = (voxel *)malloc(sizeof(voxel) * ((size_t)nc * nt + 1));
+    const int64_t nb3 = (int64_t)n_bins * n_dbins, nb33 = nb3 * nb3 * nb3;
+    double *sd = (double *)calloc((size_t)(2 * nb33), sizeof(double));
+    double *ad = (double *)calloc((size_t)nb33, sizeof(double));
+    int64_t *td = (int64_t *)calloc((size_t)nb33, sizeof(int64_t));
+    if (!vx || !sd || !ad || !td) { free(c); free(vx); free(sd); free(ad); free(td); return 2; }
+    int64_t nv = 0;
+    for (int32_t a = 0; a < nc; ++a)
+        for (int32_t t = -t_max; t <= t_max; ++t) {
+            const int32_t d = dbin_of(t, n_dbins, tau);
+            if (d < 0) continue;
+            vx[nv].gx = c[a].gx; vx[nv].gy = c[a].gy; vx[nv].t = t;
+            vx[nv].u = c[a].m * n_dbins + d;
+            vx[nv].p = c[a].p;
+            ++nv;
+        }
+    for (int64_t a = 0; a < nv; ++a) {
+        const int64_t o1 = (int64_t)(vx[a].t + t_max) * cells + vx[a].p;
+        const double x1r = Xt[2 * o1], x1i = Xt[2 * o1 + 1];
+        for (int64_t b = 0; b < nv; ++b) {
+            const int32_t t3 = -(vx[a].t + vx[b].t);
+            if (t3 < -t_max || t3 > t_max) continue;
+            const int32_t d3 = dbin_of(t3, n_dbins, tau);
+            if (d3 < 0) continue;
+            int64_t p3 = 0;
+            const int32_t m3 = bin_of_cell(n, common, n_bins, q, -(vx[a].gx + vx[b].gx),
+                                           -(vx[a].gy + vx[b].gy), &p3);
+            if (m3 < 0) continue;
+            const int64_t o2 = (int64_t)(vx[b].t + t_max) * cells + vx[b].p;
+            const int64_t o3 = (int64_t)(t3 + t_max) * cells + p3;
+            const double x2r = Xt[2 * o2], x2i = Xt[2 * o2 + 1];
+            const double x3r = Xt[2 * o3], x3i = Xt[2 * o3 + 1];
+            const double pr = x1r * x2r - x1i * x2i, pi = x1r * x2i + x1i * x2r;
+            const double tr = pr * x3r - pi * x3i, ti = pr * x3i + pi * x3r;
+            const int64_t w = (int64_t)m3 * n_dbins + d3;
+            const int64_t idx = ((int64_t)vx[a].u * nb3 + vx[b].u) * nb3 + w;
+            sd[2 * idx] += tr;
+            sd[2 * idx + 1] += ti;
+            ad[idx] += sqrt(tr * tr + ti * ti);
+            td[idx] += 1;
+        }
+    }
+    for (int32_t t = 0; t < n_trip; ++t) {
+        const int64_t u = uvw[3 * t], v = uvw[3 * t + 1], w = uvw[3 * t + 2];
+        if (u < 0 || v < 0 || w < 0 || u >= nb3 || v >= nb3 || w >= nb3) {
+            S[2 * t] = S[2 * t + 1] = 0.0;
+            if (absum) absum[t] = 0.0;
+            T[t] = 0;
+            continue;
+        }
+        const int64_t idx = (u * nb3 + v) * nb3 + w;
+        S[2 * t] = sd[2 * idx];
+        S[2 * t + 1] = sd[2 * idx + 1];
+        if (absum) absum[t] = ad[idx];
+        T[t] = td[idx];
+    }
+    free(c); free(vx); free(sd); free(ad); free(td);
+    return 0;
 }

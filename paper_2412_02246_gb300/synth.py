@@ -317,3 +317,79 @@ def channel_inputs(channel: int, realisation: int = 0, wl: Workload | None = Non
 def vis_as_float2(vis: np.ndarray) -> np.ndarray:
     """complex64 [n] -> float32 [n, 2] (re, im) view used by both implementations."""
     return np.ascontiguousarray(vis.astype(np.complex64)).view(np.float32).reshape(-1, 2)
+
+
+# ------------------------------------------------------------------ multi-frequency cube
+
+
+@dataclass
+class CubeInputs:
+    uv: np.ndarray        # [n_chan, n_vis, 2] float32, wavelengths at each channel's frequency
+    vis: np.ndarray       # [n_chan, n_vis] complex64
+    freqs_mhz: np.ndarray
+    tau: np.ndarray       # delay-bin edges in |t| (int32, ascending)
+    wl: Workload
+
+
+def cube_workload(cfg_id: int) -> Workload:
+    """Multi-frequency cubes for the 3-D form: tiny (5) and MWA-shaped (6).
+
+    tiny: the tiny workload's grid and rings over 8 channels (150-157 MHz),
+    delay bins {0}, {1}, {2, 3}.  MWA-shaped: the MWA-shaped workload's grid,
+    array and rings over 32 channels evenly on 139-169 MHz, delay bins {0},
+    [1, 4), [4, 8), [8, 16).  Baselines are drawn at 154.25 MHz and scaled by
+    nu / 154.25 MHz in every channel.
+    """
+    if cfg_id == 5:
+        return Workload("cube-tiny-64sq-8ch-5k-8lin", 64, 2.0, _lin_edges(25.0, 375.0, 8), map_side=64,
+                        layout="annulus", n_vis=5000, u_min=4.0, u_max=60.0,
+                        extra={"n_chan": 8, "nu_lo_mhz": 150.0, "nu_hi_mhz": 157.0, "nu_ref_mhz": 154.25,
+                               "tau": [0, 1, 2, 4]})
+    if cfg_id == 6:
+        return Workload("cube-mwa-512sq-32ch-975k-20log", 512, 2.3, _log_edges(46.0, 1320.0, 20),
+                        map_side=512, layout="array", n_ant=128, n_time=120, u_min=7.0, u_max=220.0,
+                        extra={"n_chan": 32, "nu_lo_mhz": 139.0, "nu_hi_mhz": 169.0, "nu_ref_mhz": 154.25,
+                               "tau": [0, 1, 4, 8, 16]})
+    raise ValueError(f"unknown cube workload id {cfg_id}")
+
+
+def gaussian_cube(m: int, n_chan: int, rng: np.random.Generator, alpha: float = 2.5) -> np.ndarray:
+    """Real Gaussian field on an m x m x n_chan periodic grid (axis 2 along frequency),
+    P(k) ~ |k|^-alpha with k in grid-index units on all three axes, unit ensemble variance."""
+    kx = np.fft.fftfreq(m) * m
+    kz = np.fft.fftfreq(n_chan) * n_chan
+    kk = np.sqrt(kx[:, None, None] ** 2 + kx[None, :, None] ** 2 + kz[None, None, :] ** 2)
+    p = np.zeros_like(kk)
+    nz = kk > 0
+    p[nz] = kk[nz] ** (-alpha)
+    p *= p.size / p.sum()
+    white = rng.standard_normal((m, m, n_chan))
+    return np.fft.ifftn(np.fft.fftn(white) * np.sqrt(p)).real
+
+
+def cube_inputs(cfg_id: int, realisation: int = 0, wl: Workload | None = None) -> CubeInputs:
+    """Seeded (U, V) of every channel of a multi-frequency cube.
+
+    sky: the quadratic transform of Eq. (mb1) (f = 0.3) of a 3-D Gaussian field,
+    one map per channel; visibilities: each channel's map modes read at that
+    channel's baselines (one set drawn at the reference frequency, scaled by
+    nu / nu_ref), plus 5 % complex Gaussian noise drawn per channel.
+    """
+    wl = cube_workload(cfg_id) if wl is None else wl
+    e = wl.extra
+    freqs = np.linspace(e["nu_lo_mhz"], e["nu_hi_mhz"], e["n_chan"])
+    rb = np.random.Generator(np.random.PCG64(seed_for(cfg_id, 0)))
+    uv0 = make_baselines(wl, rb).astype(np.float64)
+    rs = np.random.Generator(np.random.PCG64(seed_for(cfg_id, 1 + realisation)))
+    cube = quadratic_sky(gaussian_cube(wl.map_side, e["n_chan"], rs, wl.alpha), wl.f_ng)
+    uvs, viss = [], []
+    for c, nu in enumerate(freqs):
+        uv = (uv0 * (nu / e["nu_ref_mhz"])).astype(np.float32)
+        v = bilinear(sky_modes(np.ascontiguousarray(cube[:, :, c])), uv.astype(np.float64) / np.float64(wl.du))
+        rms = np.sqrt(np.mean(np.abs(v) ** 2))
+        s = wl.noise_frac * rms / np.sqrt(2.0)
+        v = v + s * (rs.standard_normal(v.shape) + 1j * rs.standard_normal(v.shape))
+        uvs.append(uv)
+        viss.append(v.astype(np.complex64))
+    return CubeInputs(uv=np.stack(uvs), vis=np.stack(viss), freqs_mhz=freqs,
+                      tau=np.asarray(e["tau"], np.int32), wl=wl)
