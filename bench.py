@@ -605,6 +605,51 @@ def simulator_extras(m, synth, ctx, uv, torch, dev, stream):
             "map": msim, "note": "abs_simulate_vis: MWA tile beam, 0.029 deg pixels, direct DFT"}
 
 
+def cube_extras(m, synth, ctx, torch, dev, stream, steps, peaks):
+    """The multi-frequency (3-D) form on the MWA-shaped cube: 32 channels of 975,360 visibilities
+    (139-169 MHz), 512^2 grid, 20 log l rings x 4 |delay| bins, 18,603 bin triplets, N = 288,
+    N_z = 46; one abs_estimate_3d per call (graph replays; the 500 MB of inputs exceed L2),
+    FP32 and split-BF16, and one eager call of each with the stage profiler."""
+    ci = synth.cube_inputs(6)
+    uv = torch.from_numpy(np.ascontiguousarray(ci.uv)).to(dev)
+    vis = torch.from_numpy(np.ascontiguousarray(ci.vis).view(np.float32).reshape(ci.vis.shape + (2,))).to(dev)
+    out = {"workload": "MWA-shaped cube: 32 channels x 975,360 visibilities (139-169 MHz, baselines scaled by "
+                       "nu / 154.25 MHz), 512^2 uv grid, dU=2.3 lambda, 20 log l rings x |delay| bins {0}, [1,4), "
+                       "[4,8), [8,16): 80 bins, 18,603 bin triplets, N=288, N_z=46 (3.82e6 voxels)"}
+    res = {}
+    for name, prec in (("fp32", m.ABS_FP32), ("split_bf16", m.ABS_SPLIT_BF16)):
+        cfg = m.Config3D.from_cube(ci, precision=prec)
+        nt = len(m.abs_triplets_3d(cfg))
+        B = torch.empty(nt, dtype=torch.float64, device=dev)
+        T = torch.empty(nt, dtype=torch.int64, device=dev)
+        E = torch.empty(cfg.n_bins, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            ctx.abs_estimate_3d(cfg, uv, vis, nt, None, B, T, E)
+        ctx.sync()
+        t = timed_calls(lambda: ctx.abs_estimate_3d(cfg, uv, vis, nt, None, B, T, E), steps, stream, torch, dev)
+        res[name] = (B.cpu().numpy(), T.cpu().numpy())
+        ctx.profile(True)
+        ctx.abs_estimate_3d(cfg, uv, vis, nt, None, B, T, E)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        P3 = 288 * 288 * 46
+        o = {"value": steps / (sum(t) * 1e-3), "unit": UNIT, "ms": sum(t) / steps,
+             "stages_us": {k: round(1e3 * v[0], 1) for k, v in sorted(prof.items())}}
+        if "triple_tc" in prof:
+            ms = prof["triple_tc"][0]
+            useful = 6.0 * nt * P3
+            o["triple_tc"] = {"ms": ms, "useful_bf16_tflops": useful / (ms * 1e9),
+                              "frac_useful_of_measured_bf16": useful / (ms * 1e9) / peaks["bf16_tflops"]}
+        if "triple_fp32" in prof:
+            ms = prof["triple_fp32"][0]
+            o["triple_fp32"] = {"ms": ms, "fp32_tflops": 2.0 * nt * P3 / (ms * 1e9)}
+        out[name] = o
+    out["split_vs_fp32_max_rel_err"] = max_rel_big(res["split_bf16"][0], res["fp32"][0])
+    out["counts_equal"] = bool(np.array_equal(res["split_bf16"][1], res["fp32"][1]))
+    out["split_bf16_over_fp32"] = out["split_bf16"]["value"] / out["fp32"]["value"]
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -765,6 +810,8 @@ def run_ours(args):
     if batch_inputs:
         extras["batched_uneven"] = uneven_extras(m, ctx, batch_inputs, torch, dev, stream, args.steps)
     extras["simulator"] = simulator_extras(m, synth, ctx, uvd[0], torch, dev, stream)
+    if rank == 0 and args.cube:
+        extras["cube3d"] = cube_extras(m, synth, ctx, torch, dev, stream, max(3, args.steps // 2), peaks)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -804,6 +851,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--channels", type=int, default=32, help="channels per step (the workload has 32)")
     ap.add_argument("--batch-items", type=int, default=256, help="items of the uneven batch (0: skip it)")
+    ap.add_argument("--cube", type=int, default=1, help="time the multi-frequency (3-D) form too (0: skip it)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -376,6 +376,65 @@ abs_status abs_inject_alloc_failures(abs_ctx *ctx, int32_t count);
 abs_status abs_tuned_shape(abs_ctx *ctx, const abs_config *cfg, int32_t *set_cols, int32_t *waves,
                            int32_t *measured);
 
+/* ---------------------------------------------------------------------------
+ * Multi-frequency (3-D) form.  The paper restricts itself to one frequency and
+ * names the three-dimensional bispectrum of multi-frequency data as future work
+ * (Sec. 1, Sec. 5), to be reached as the power spectrum was: the angular
+ * statistic first, then a transform along frequency.  It gives no formula; this
+ * is the reading implemented here:
+ *
+ *  - every channel c = 0 .. n_chan-1 is gridded on the same uv grid with the
+ *    per-channel configuration `base` (Eq. vg), giving its weighted means X_c(g);
+ *  - a cell enters only if it is filled in every channel (the common mask);
+ *  - its delay modes are the transform along frequency,
+ *    Xt(g, t) = sum_c X_c(g) exp(-2 pi i c t / n_chan), integer |t| <= t_max;
+ *  - voxel (g, t) lies in bin u = m n_dbins + a when g is in ring a_m and
+ *    delay_edges[a] <= |t| < delay_edges[a + 1];
+ *  - S_uvw is the sum of Xt Xt Xt over ordered voxel triples, one in each of
+ *    the bins u, v, w, with g1 + g2 + g3 = 0 and t1 + t2 + t3 = 0; T_uvw their
+ *    number; B_uvw = Re S_uvw / (A T_uvw), NaN where T = 0.
+ *
+ * On the GPU the sums are taken over an N_z x N x N voxel grid (N_z >= 3 t_max
+ * + 1 and N >= 3 R + 1, so no wrapped triangle enters), and the counts are
+ * exact integers: T_uvw = T2(rings of u, v, w) x T1(delay bins of u, v, w), the
+ * 2-D closed-triangle count on the common mask times the number of closing
+ * delay triples of the bins. */
+#define ABS_MAX_CHAN 4096     /* largest channel count */
+#define ABS_MAX_DELAY 63      /* largest |t| a delay bin may hold */
+
+typedef struct abs_config3d {
+    abs_config base;          /* per-channel uv grid, gridding kernel, rings, n_fft, precision
+                                 (of the triple sums) and norm_A; weight_mode must be
+                                 ABS_W_MEAN_UNITMASK */
+    int32_t n_chan;           /* channels, 1..ABS_MAX_CHAN, evenly spaced in frequency */
+    int32_t n_dbins;          /* delay bins, >= 1, n_bins x n_dbins <= ABS_MAX_BINS */
+    const int32_t *delay_edges; /* host: n_dbins + 1 strictly ascending integers in |t|,
+                                 delay_edges[0] >= 0; t_max = delay_edges[n_dbins] - 1 must
+                                 satisfy 2 t_max < n_chan and t_max <= ABS_MAX_DELAY */
+    int32_t n_z;              /* line-of-sight grid N_z: 0 = 3 t_max + 1, else in
+                                 [3 t_max + 1, 4 ABS_MAX_DELAY + 4] */
+} abs_config3d;
+
+/* Host only: the canonical bin triplets of cfg, u <= v <= w lexicographic, whose rings
+ * (sorted) are in the closing list of abs_triplets(&cfg->base) and whose delay bins hold
+ * a closing delay triple.  Writes min(cap, count) triplets as [t][3] int32 to uvw (may be
+ * NULL) and the count to *n_trip. */
+abs_status abs_triplets_3d(const abs_config3d *cfg, int32_t cap, int32_t *n_trip, int32_t *uvw);
+
+/* Whole multi-frequency estimate: channel cube -> B_uvw.  d_uv, d_vis: [n_chan][n_vis][2]
+ * float32 device (channel c's baselines in wavelengths at its own frequency, and its
+ * visibilities; the same n_vis in every channel).  d_uvw: [n_trip][3] int32 device in
+ * canonical order with bins < n_bins n_dbins, or NULL for the list of abs_triplets_3d
+ * (n_trip must then equal its length).  Outputs (each may be NULL): d_B [n_trip] f64,
+ * d_count [n_trip] int64 (exact T_uvw), d_ellbar [n_bins] f64 (mean l of each ring over
+ * the common mask).  The first call with a set of arguments runs eagerly (sizing the
+ * context's workspaces), the second is captured as a CUDA graph and replayed after that.
+ * Device memory: about 4 (n_bins n_dbins N_z + 2 n_bins (t_max + 1)) N^2 bytes of fields,
+ * plus the split-BF16 operands (8 bytes per bin and voxel) in that precision. */
+abs_status abs_estimate_3d(abs_ctx *ctx, const abs_config3d *cfg, int64_t n_vis, const float *d_uv,
+                           const float *d_vis, int32_t n_trip, const int32_t *d_uvw, double *d_B,
+                           int64_t *d_count, double *d_ellbar);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,11 @@ class abs_config(ctypes.Structure):
                 ("weight_mode", ctypes.c_int32)]
 
 
+class abs_config3d(ctypes.Structure):
+    _fields_ = [("base", abs_config), ("n_chan", ctypes.c_int32), ("n_dbins", ctypes.c_int32),
+                ("delay_edges", ctypes.POINTER(ctypes.c_int32)), ("n_z", ctypes.c_int32)]
+
+
 class abs_item(ctypes.Structure):
     _fields_ = [("cfg", ctypes.POINTER(abs_config)), ("n_vis", ctypes.c_int64), ("d_uv", ctypes.c_void_p),
                 ("d_vis", ctypes.c_void_p), ("n_trip", ctypes.c_int32), ("d_ijk", ctypes.c_void_p),
@@ -101,6 +106,8 @@ def load(path: str | None = None):
         "abs_bana_d": ([P, P, P, P, i32, P, P, ctypes.c_double, P], ctypes.c_int),
         "abs_simulate_vis": ([P, i32, ctypes.c_double, P, i32, ctypes.c_double, i64, P, P], ctypes.c_int),
         "abs_tuned_shape": ([P, P, P, P, P], ctypes.c_int),
+        "abs_triplets_3d": ([P, i32, P, P], ctypes.c_int),
+        "abs_estimate_3d": ([P, P, i64, P, P, i32, P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -156,6 +163,39 @@ class Config:
                     sigma_cells=wl.sigma_cells, radius_cells=wl.radius_cells, precision=prec)
         args.update(kw)
         return cls(**args)
+
+
+@dataclass
+class Config3D:
+    """abs_config3d: the per-channel configuration, the channel count, the delay-bin edges in
+    |t| and the line-of-sight grid N_z (0: 3 t_max + 1)."""
+    base: Config
+    n_chan: int
+    delay_edges: np.ndarray
+    n_z: int = 0
+
+    def __post_init__(self):
+        self.delay_edges = np.ascontiguousarray(self.delay_edges, np.int32)
+        self._c = abs_config3d(self.base._c, int(self.n_chan), len(self.delay_edges) - 1,
+                               self.delay_edges.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), int(self.n_z))
+
+    @property
+    def n_dbins(self) -> int:
+        return len(self.delay_edges) - 1
+
+    @property
+    def n_bins(self) -> int:
+        return self.base.n_bins
+
+    def ref(self):
+        # the base's edges pointer is re-read, so a Config3D stays valid while its base lives
+        self._c.base = self.base._c
+        return ctypes.byref(self._c)
+
+    @classmethod
+    def from_cube(cls, ci, **kw):
+        """From synth.CubeInputs (its workload's grid and rings, its channels and delay bins)."""
+        return cls(Config.from_workload(ci.wl, **kw), int(ci.uv.shape[0]), ci.tau)
 
 
 def _check(st: int, ctx=None, what: str = ""):
@@ -245,6 +285,15 @@ def abs_triplets(cfg: Config) -> np.ndarray:
     out = np.zeros((max(n.value, 1), 3), np.int32)
     _check(load().abs_triplets(cfg.ref(), n.value, ctypes.byref(n), out.ctypes.data_as(ctypes.c_void_p)),
            what="abs_triplets")
+    return out[:n.value]
+
+
+def abs_triplets_3d(cfg: Config3D) -> np.ndarray:
+    n = ctypes.c_int32(0)
+    _check(load().abs_triplets_3d(cfg.ref(), 0, ctypes.byref(n), None), what="abs_triplets_3d")
+    out = np.zeros((max(n.value, 1), 3), np.int32)
+    _check(load().abs_triplets_3d(cfg.ref(), n.value, ctypes.byref(n), out.ctypes.data_as(ctypes.c_void_p)),
+           what="abs_triplets_3d")
     return out[:n.value]
 
 
@@ -403,6 +452,25 @@ class Context:
         nv, puv, pvis, pijk, pB, pT, pE = self._est_ptrs(cfg, uv, vis, 1, n_trip, ijk, B, counts, ellbar)
         _check(load().abs_estimate(self.h, cfg.ref(), nv, puv, pvis, int(n_trip), pijk, pB, pT, pE),
                self.h, "abs_estimate")
+
+    def abs_estimate_3d(self, cfg: Config3D, uv, vis, n_trip, uvw=None, B=None, counts=None, ellbar=None):
+        """Multi-frequency estimate: uv, vis [n_chan][n_vis][2] float32 on the device."""
+        d, nt, nc = self.device, int(n_trip), int(cfg.n_chan)
+        if uv.dim() != 3 or uv.shape[0] != nc or uv.shape[2] != 2:
+            raise ValueError(f"uv: shape {tuple(uv.shape)}, expected ({nc}, n_vis, 2)")
+        nv = int(uv.shape[1])
+        if uvw is not None:
+            puvw, rows = _ijk_rows(uvw, "uvw", device=d)
+            if rows < nt:
+                raise ValueError(f"uvw: {rows} triplets, n_trip = {nt}")
+        else:
+            puvw = None
+        _check(load().abs_estimate_3d(self.h, cfg.ref(), nv, _dev(uv, "f32", 2 * nv * nc, "uv", d),
+                                      _dev(vis, "f32", 2 * nv * nc, "vis", d), nt, puvw,
+                                      _dev(B, "f64", nt, "B", d, optional=True),
+                                      _dev(counts, "i64", nt, "counts", d, optional=True),
+                                      _dev(ellbar, "f64", cfg.n_bins, "ellbar", d, optional=True)),
+               self.h, "abs_estimate_3d")
 
     def abs_estimate_many(self, cfg: Config, uv, vis, n_trip, ijk=None, B=None, counts=None, ellbar=None):
         n_real = int(vis.shape[0])

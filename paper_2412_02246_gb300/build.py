@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libabs.so")
-SOURCES = ["api.cu", "grid.cu", "fft.cu", "counts.cu", "triple.cu", "triple_tc.cu", "results.cu", "simulate.cu"]
+SOURCES = ["api.cu", "grid.cu", "fft.cu", "counts.cu", "triple.cu", "triple_tc.cu", "results.cu", "simulate.cu",
+           "cube.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off",
          "-Xptxas", "-warn-spills"]

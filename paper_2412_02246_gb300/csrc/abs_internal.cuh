@@ -28,6 +28,8 @@ struct Setup {
     std::vector<int> Rm;          // per ring: largest |g_x| of its cells on the grid (-1 empty)
     int R = 0;                    // max over rings
     int N = 0;                    // sky-grid side
+    int64_t P = 0;                // points the triple sums run over: N^2 pixels, or the N_z N^2
+                                  // voxels of the multi-frequency form's triple stage
     std::vector<int> radices;     // N = prod(radices)
     std::vector<int64_t> lat;     // lattice cells per ring (full annulus, on the grid)
     std::vector<int64_t> lat_off; // nb+1 prefix offsets of lat
@@ -53,6 +55,24 @@ struct Setup {
     // known to triple_tc.cu; its deleter frees the device copies)
     std::shared_ptr<void> tc_plan;
     std::string key;              // the configuration's key (setups, tuned shapes)
+};
+
+// The multi-frequency form's setup: the per-channel setup, the triple stage over bins
+// u = m n_dbins + a (ring m, delay bin a) and N_z N^2 points with the canonical bin-triplet
+// list, and its tables (made on the host from an abs_config3d, cached per context).
+struct CubeSetup {
+    const Setup *s2 = nullptr;    // per-channel setup (owned by the context's setups)
+    Setup st;                     // triple stage: nb = n_bins n_dbins, P = N_z N^2, ijk = bin triplets
+    int n_chan = 0, na = 0, t_max = 0, Nz = 0;
+    std::vector<int32_t> tau;     // n_dbins + 1 delay-bin edges in |t|
+    std::vector<int64_t> T1;      // delay counts [na][na][na]
+    int32_t *d_idx2d = nullptr;   // [nb][nb][nb]: index of the sorted ring triple in s2's list, or -1
+    int32_t *d_rm2 = nullptr;     // [2 nb (t_max + 1)]: the ring extent of each delay-transform pair, twice
+    int32_t *d_tau = nullptr;
+    int64_t *d_T1 = nullptr;
+    double2 *d_los_tw = nullptr;  // [n_chan] exp(-2 pi i e / n_chan)
+    float2 *d_ztw = nullptr;      // [t_max + 1][N_z] c_t (cos, sin)(2 pi (t z mod N_z) / N_z), c_0 = 1, else 2
+    ~CubeSetup();
 };
 
 // Host-side validation + derivation.  Returns ABS_OK or an error with text in err.
@@ -112,6 +132,8 @@ struct abs_ctx {
     std::map<std::string, TcShape> tc_shapes;
     std::map<std::string, std::pair<int, int>> fft_shapes;   // lines per CTA: column pass, row pass
     std::vector<abs_ctx *> lanes;
+    // multi-frequency setups by configuration key (they point at entries of setups)
+    std::map<std::string, std::unique_ptr<absk::CubeSetup>> cubes;
     bool owns_stream = false;
     cudaEvent_t ev_lane = nullptr;   // a lane's end, joined by the parent
 };
@@ -176,6 +198,13 @@ abs_status launch_filter_fft_acc(abs_ctx *ctx, const Setup &s, const double *acc
 // The I fields of Eq. iFT_I as printed (ABS_W_PAPER_LITERAL): W_g = 1 / (the
 // cell's mirrored weight sum) on filled cells, from the FP64 accumulators.
 abs_status launch_filter_fft_w(abs_ctx *ctx, const Setup &s, const double *acc, float *d_fields);
+// Multi-frequency form: the ring transforms of the delay modes Xt [t_max + 1][(2R + 1)^2]
+// (packed double-float complex, cells |gx|, |gy| <= R of the setup), one pair p = m (t_max + 1)
+// + t per ring m and delay t >= 0: real fields F [2 p] = FFT of the Hermitian part H1 and
+// F [2 p + 1] = FFT of H2 (Xt(., t) = H1 + i H2), each N x N.  d_rm2 [2 nb (t_max + 1)]:
+// the largest |g_x| of the pair's ring, twice per pair.
+abs_status launch_filter_fft_delay(abs_ctx *ctx, const Setup &s, int t_max, const float4 *d_xt, const int32_t *d_rm2,
+                                   float *d_F);
 // FP64 accumulators [planes][n*n] (re, im, w before the mirror; see grid_acc_planes) of the last
 // launch_grid_accumulate on this context.  A cell received a contribution
 // exactly when its weight sum is > 0 (every footprint weight is a normal,
@@ -229,6 +258,18 @@ abs_status launch_rebin(abs_ctx *ctx, const Setup &s, int32_t n_real, int32_t n_
 abs_status launch_check_triplets(abs_ctx *ctx, const Setup &s, int32_t n_trip,
                                  const int32_t *d_ijk);
 
+// Multi-frequency form: validation of cfg against the per-channel setup s2, the largest delay
+// t_max, the line-of-sight length N_z, the delay counts T1 and the canonical bin triplets
+// (rings closing in s2's list, delay count > 0), u <= v <= w lexicographic; *err is a static
+// message on failure.
+abs_status derive_cube(const abs_config3d *cfg, const Setup &s2, int &t_max, int &Nz, std::vector<int64_t> &T1,
+                       std::vector<int32_t> &uvw, const char **err);
+const CubeSetup *get_cube_setup(abs_ctx *ctx, const abs_config3d *cfg, abs_status &st);
+// The whole multi-frequency estimate on ctx->stream (d_uv, d_vis: [n_chan][n_vis][2]).
+abs_status launch_cube_estimate(abs_ctx *ctx, const CubeSetup &c, int64_t n_vis, const float *d_uv,
+                                const float *d_vis, int32_t n_trip, const int32_t *d_uvw, double *d_B,
+                                int64_t *d_count, double *d_ellbar);
+
 // Brackets the kernel launches of its scope with events when profiling is on.
 struct StageTimer {
     abs_ctx *ctx;
@@ -240,6 +281,12 @@ struct StageTimer {
 
 // --------------------------------------------------------------------------- helpers
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+#define ABS_CHECK(x)                      \
+    do {                                  \
+        const abs_status _st = (x);       \
+        if (_st != ABS_OK) return _st;    \
+    } while (0)
 
 // Lets `kernel` take dynamic shared memory up to the current device's opt-in
 // limit less its static shared memory; false when `bytes` is above that or the

@@ -196,6 +196,7 @@ abs_status make_setup(const abs_config *cfg, Setup &s, std::string &err) {
     }
     s.nb = cfg->n_bins;
     s.radices = radix_plan(s.N);
+    s.P = (int64_t)s.N * s.N;
     // lattice cells per ring on the grid (capacity of the ring lists)
     s.lat.assign(s.nb, 0);
     for (int y = -s.R; y <= s.R; ++y)
@@ -431,11 +432,7 @@ struct DeviceGuard {
 
 using namespace absk;
 
-#define ABS_CHECK(x)                      \
-    do {                                  \
-        const abs_status _st = (x);       \
-        if (_st != ABS_OK) return _st;    \
-    } while (0)
+
 
 extern "C" {
 
@@ -473,6 +470,7 @@ static void release_ctx(abs_ctx *ctx) {
     if (ctx->side) cudaStreamSynchronize(ctx->side);
     drop_graphs(ctx);
     for (auto &kv : ctx->ws) cudaFree(kv.second.p);
+    ctx->cubes.clear();
     for (auto &kv : ctx->setups) free_setup(*kv.second);
     if (!ctx->parent) cudaFree(ctx->d_err);
     if (ctx->side) cudaStreamDestroy(ctx->side);
@@ -676,6 +674,23 @@ abs_status abs_triplets(const abs_config *cfg, int32_t cap, int32_t *n_trip, int
     const int32_t n = (int32_t)(s.ijk.size() / 3);
     *n_trip = n;
     if (ijk) std::memcpy(ijk, s.ijk.data(), sizeof(int32_t) * 3 * std::min(n, cap));
+    return ABS_OK;
+}
+
+abs_status abs_triplets_3d(const abs_config3d *cfg, int32_t cap, int32_t *n_trip, int32_t *uvw) {
+    if (!cfg || !n_trip || cap < 0) return ABS_ERR_INVALID_ARG;
+    if (cfg->n_dbins < 1 || !cfg->delay_edges) return ABS_ERR_INVALID_ARG;
+    Setup s;
+    std::string err;
+    ABS_CHECK(make_setup(&cfg->base, s, err));
+    int t_max = 0, Nz = 0;
+    std::vector<int64_t> T1;
+    std::vector<int32_t> list;
+    const char *msg = "";
+    ABS_CHECK(derive_cube(cfg, s, t_max, Nz, T1, list, &msg));
+    const int32_t n = (int32_t)(list.size() / 3);
+    *n_trip = n;
+    if (uvw) std::memcpy(uvw, list.data(), sizeof(int32_t) * 3 * std::min(n, cap));
     return ABS_OK;
 }
 
@@ -944,6 +959,31 @@ abs_status abs_estimate(abs_ctx *ctx, const abs_config *cfg, int64_t n_vis, cons
                         const float *d_vis, int32_t n_trip, const int32_t *d_ijk, double *d_B,
                         int64_t *d_count, double *d_ellbar) {
     return abs_estimate_many(ctx, cfg, n_vis, d_uv, 1, d_vis, n_trip, d_ijk, d_B, d_count, d_ellbar);
+}
+
+abs_status abs_estimate_3d(abs_ctx *ctx, const abs_config3d *cfg, int64_t n_vis, const float *d_uv,
+                           const float *d_vis, int32_t n_trip, const int32_t *d_uvw, double *d_B,
+                           int64_t *d_count, double *d_ellbar) {
+    if (!ctx) return ABS_ERR_INVALID_ARG;
+    DeviceGuard g(ctx->device);
+    abs_status st;
+    const CubeSetup *c = get_cube_setup(ctx, cfg, st);
+    if (!c) return st;
+    if (n_vis < 0 || n_vis > 0x7fffffffLL) return fail(ctx, ABS_ERR_INVALID_ARG, "n_vis must be in [0, 2^31)");
+    if (n_vis > 0 && (!d_uv || !d_vis)) return fail(ctx, ABS_ERR_INVALID_ARG, "NULL visibility buffer");
+    if (n_trip < 0) return fail(ctx, ABS_ERR_INVALID_ARG, "n_trip < 0");
+    if (!d_uvw) {
+        if (n_trip != (int32_t)(c->st.ijk.size() / 3))
+            return fail(ctx, ABS_ERR_INVALID_ARG, "n_trip must equal the canonical triplet count when d_uvw is NULL");
+        d_uvw = c->st.d_ijk;
+    }
+    char key[320];
+    snprintf(key, sizeof key, "cube|%p|%p|%lld|%p|%p|%d|%p|%p|%p|%p", (const void *)c, (const void *)ctx->stream,
+             (long long)n_vis, (const void *)d_uv, (const void *)d_vis, n_trip, (const void *)d_uvw, (void *)d_B,
+             (void *)d_count, (void *)d_ellbar);
+    return graphed(ctx, key, [&]() {
+        return launch_cube_estimate(ctx, *c, n_vis, d_uv, d_vis, n_trip, d_uvw, d_B, d_count, d_ellbar);
+    });
 }
 
 // A lane of ctx: its own non-blocking streams and events, the parent's device error word.

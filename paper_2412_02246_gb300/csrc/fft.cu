@@ -965,6 +965,83 @@ abs_status run_fft_as(abs_ctx *ctx, const Setup &s, const Src &src, float *d_fie
     return check_launch(ctx, "filter+FFT");
 }
 
+// Multi-frequency form: the ring transforms of the delay modes.  Pair p = m (t_max + 1) + t
+// (ring m, delay t >= 0) transforms Z(g) = Xt(g, t) on the cells of ring m (Xt is zero on
+// cells not filled in every channel), read from the region [t][(2 Rr + 1)^2] of cells
+// |gx|, |gy| <= Rr as packed double-float complex values.  The channel maps are real, so
+// Xt(-g, -t) = conj Xt(g, t): H1 = (Xt(., t) + Xt(., -t)) / 2 and H2 = (Xt(., t) -
+// Xt(., -t)) / 2i are Hermitian on the ring and Z = H1 + i H2.  The row pass therefore
+// gives the real fields F1 = FFT(H1) and F2 = FFT(H2) of the pair in its slots 2p and
+// 2p + 1, and the transforms of Xt(., +-t) are F1 +- i F2.  Same W layout as k_fft_cols.
+template <class A>
+__global__ void __launch_bounds__(FFT_NT) k_fft_cols_delay(RingGeom G, const __grid_constant__ FftPlan P, int CB,
+                                                        const int64_t *__restrict__ q, const int32_t *__restrict__ Rm,
+                                                        int t1, int Rr, const float4 *__restrict__ Xt,
+                                                        const float4 *__restrict__ tw, typename A::E *__restrict__ W) {
+    using E = typename A::E;
+    extern __shared__ float4 sbuf[];
+    const int pair = blockIdx.y;
+    const int m = pair / t1, t = pair - m * t1;
+    const int Rp = Rm[m];
+    const int x0 = (int)blockIdx.x * CB - G.Rmax;
+    if (Rp < 0 || x0 > Rp || x0 + CB - 1 < -Rp) return;
+    E *l0 = (E *)sbuf, *l1 = l0 + (size_t)CB * G.N;
+    for (int i = threadIdx.x; i < CB * G.N; i += blockDim.x) l0[i] = A::zero();
+    __syncthreads();
+    const int span = 2 * Rp + 1, side = 2 * Rr + 1;
+    const int64_t q0 = q[m], q1 = q[m + 1];
+    const float4 *src = Xt + (size_t)t * side * side;
+    for (int e = threadIdx.x; e < CB * span; e += blockDim.x) {
+        const int yy = e / CB, c = e - yy * CB, x = x0 + c, y = yy - Rp;
+        if (x < -Rp || x > Rp) continue;
+        const int64_t r2 = (int64_t)x * x + (int64_t)y * y;
+        if (r2 < q0 || r2 >= q1) continue;
+        l0[(size_t)c * G.N + (y < 0 ? y + G.N : y)] = A::from_cell(src[(size_t)(y + Rr) * side + (x + Rr)]);
+    }
+    E *res = fft_lines<A>(l0, l1, CB, P, tw);
+    for (int e = threadIdx.x; e < CB * G.N; e += blockDim.x) {
+        const int c = e / G.N, x = x0 + c;
+        if (x < -Rp || x > Rp) continue;
+        W[((size_t)pair * (2 * G.Rmax + 1) + (x + G.Rmax)) * G.N + (e - c * G.N)] = res[e];
+    }
+}
+
+template <class A>
+abs_status run_fft_delay(abs_ctx *ctx, const Setup &s, int t_max, const float4 *d_xt, const int32_t *d_rm2,
+                         float *d_F) {
+    using E = typename A::E;
+    const int t1 = t_max + 1;
+    const int npairs = s.nb * t1;
+    if (npairs > 65535) return fail(ctx, ABS_ERR_UNSUPPORTED, "delay transforms: rings x delays above 65535");
+    RingGeom G{s.n, s.half, 2 * npairs, s.N, s.R};
+    const FftPlan P = make_plan(s);
+    const size_t line = sizeof(E) * (size_t)s.N;
+    // lines per CTA of the column pass: the model of fft_launch for this many pairs
+    const int per_sm = std::min(2048 / FFT_NT, 65536 / (FFT_NT * (sizeof(E) == 8 ? 32 : 64)));
+    const int CB = lines_per_cta(line, 2 * s.R + 1, npairs, ctx->sm_count, per_sm);
+    const int RB = 2;
+    const int LS = row_pitch(s.N, s.radices.empty() ? 1 : s.radices[0], RB, sizeof(E));
+    const size_t csm = line * 2 * CB, rsm = row_smem(s, RB, LS, sizeof(E), false);
+    if (csm > 227 * 1024 || rsm > 227 * 1024) return fail(ctx, ABS_ERR_UNSUPPORTED, "FFT lines do not fit shared memory");
+    E *W = (E *)workspace(ctx, "fft.delay", sizeof(E) * (size_t)npairs * (2 * s.R + 1) * s.N);
+    if (!W) return fail(ctx, ABS_ERR_OOM, "delay transform workspace");
+    cudaStream_t st = ctx->stream;
+    const float4 *tw = A::table(s.d_tw, s.N);
+    {
+        StageTimer timer(ctx, "fft_cols_delay");
+        allow_smem(k_fft_cols_delay<A>, csm);
+        k_fft_cols_delay<A><<<dim3((unsigned)cdiv(2 * s.R + 1, CB), npairs), FFT_NT, csm, st>>>(
+            G, P, CB, s.d_q, s.d_Rm, t1, s.R, d_xt, tw, W);
+    }
+    {
+        StageTimer timer(ctx, "fft_rows_delay");
+        allow_smem(k_fft_rows<A, FieldsOut>, rsm);
+        k_fft_rows<A, FieldsOut><<<dim3((unsigned)cdiv(s.N, RB), npairs), RowNT<A>::value, rsm, st>>>(
+            G, P, RB, magic(RB), LS, d_rm2, W, tw, FieldsOut{d_F});
+    }
+    return check_launch(ctx, "delay transforms");
+}
+
 template <class Src>
 abs_status run_fft(abs_ctx *ctx, const Setup &s, const Src &src, float *d_fields, const SplitOut *split = nullptr) {
     if ((int)s.radices.size() > MAXRAD) return fail(ctx, ABS_ERR_UNSUPPORTED, "FFT radix plan too long");
@@ -1006,6 +1083,13 @@ abs_status launch_filter_fft_real(abs_ctx *ctx, const Setup &s, const double *d_
                                   float *d_fields) {
     GridReal src{d_c, d_mask};
     return run_fft(ctx, s, src, d_fields);
+}
+
+abs_status launch_filter_fft_delay(abs_ctx *ctx, const Setup &s, int t_max, const float4 *d_xt, const int32_t *d_rm2,
+                                   float *d_F) {
+    if ((int)s.radices.size() > MAXRAD) return fail(ctx, ABS_ERR_UNSUPPORTED, "FFT radix plan too long");
+    return plain_fp32(s) ? run_fft_delay<ArithF32>(ctx, s, t_max, d_xt, d_rm2, d_F)
+                         : run_fft_delay<ArithDF>(ctx, s, t_max, d_xt, d_rm2, d_F);
 }
 
 }  // namespace absk

@@ -124,10 +124,10 @@ struct TriplePlan {
     size_t smem;
 };
 
-bool triple_plan(int nb, int N, int n_trip, int sms, int64_t max_split, const float *d_fields, TriplePlan &tp) {
+bool triple_plan(int nb, int64_t P, int n_trip, int sms, int64_t max_split, const float *d_fields, TriplePlan &tp) {
     TripleGeom &G = tp.G;
     G.nb = nb;
-    G.P = (int64_t)N * N;
+    G.P = P;
     G.n_trip = n_trip;
     const int ngroups = (int)cdiv(n_trip, 32);
     const int warps = std::min(32, ngroups);
@@ -308,7 +308,7 @@ abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_field
         return launch_normalise(ctx, s, n_trip, d_sum, d_count, d_B);
     }
     TriplePlan tp;
-    if (!triple_plan(s.nb, s.N, n_trip, ctx->sm_count, INT64_MAX, d_fields, tp))
+    if (!triple_plan(s.nb, s.P, n_trip, ctx->sm_count, INT64_MAX, d_fields, tp))
         return fail(ctx, ABS_ERR_UNSUPPORTED, "FP32 triple-sum tiling");
     const int64_t nsplit = tp.nsplit;
     double *partial = (double *)workspace(ctx, "triple.partial", sizeof(double) * nsplit * n_trip);
@@ -322,7 +322,7 @@ abs_status launch_triple_sums(abs_ctx *ctx, const Setup &s, const float *d_field
     if (wait_before_b) cudaStreamWaitEvent(ctx->stream, wait_before_b, 0);
     StageTimer timer(ctx, "triple_reduce");
     k_triple_reduce<<<(int)cdiv(n_trip, 8), 256, 0, ctx->stream>>>(
-        n_trip, (int)nsplit, 1.0 / ((double)s.N * (double)s.N), partial, d_sum, d_count, s.norm_A,
+        n_trip, (int)nsplit, 1.0 / (double)s.P, partial, d_sum, d_count, s.norm_A,
         d_B && d_count ? d_B : nullptr);
     return check_launch(ctx, "triple sums");
 }
@@ -331,7 +331,7 @@ abs_status launch_bana_sums(abs_ctx *ctx, const Setup &s, const float *d_P, cons
                             const int32_t *d_ijk, const int64_t *d_count, double fs, double *d_out) {
     if (n_trip == 0) return ABS_OK;
     TriplePlan tp;   // sized for both field sets in shared memory
-    if (!triple_plan(2 * s.nb, s.N, n_trip, ctx->sm_count, INT64_MAX, d_P, tp))
+    if (!triple_plan(2 * s.nb, s.P, n_trip, ctx->sm_count, INT64_MAX, d_P, tp))
         return fail(ctx, ABS_ERR_UNSUPPORTED, "prediction triple-sum tiling");
     tp.G.nb = s.nb;
     const int64_t nsplit = tp.nsplit;
@@ -344,7 +344,7 @@ abs_status launch_bana_sums(abs_ctx *ctx, const Setup &s, const float *d_P, cons
                                                                                          partial);
     // out = sum / (N^2 A T) with A = 1 / (2 fs)
     k_triple_reduce<<<(int)cdiv(n_trip, 8), 256, 0, ctx->stream>>>(
-        n_trip, (int)nsplit, 1.0 / ((double)s.N * (double)s.N), partial, sum, d_count, 1.0 / (2.0 * fs), d_out);
+        n_trip, (int)nsplit, 1.0 / (double)s.P, partial, sum, d_count, 1.0 / (2.0 * fs), d_out);
     return check_launch(ctx, "prediction sums");
 }
 
@@ -414,7 +414,7 @@ extern "C" abs_status abs_triple_sums_static(const abs_config *cfg, const float 
     // same tiling as launch_triple_sums, with the number of pixel splits capped
     // so that [split][triplet] fits the fixed array
     TriplePlan tp;
-    if (!triple_plan(cfg->n_bins, N, n_trip, sms, std::max<int64_t>(1, cap / n_trip), d_fields, tp))
+    if (!triple_plan(cfg->n_bins, (int64_t)N * N, n_trip, sms, std::max<int64_t>(1, cap / n_trip), d_fields, tp))
         return ABS_ERR_UNSUPPORTED;
     const int64_t nsplit = tp.nsplit;
     if (!allow_smem(k_triple_fp32, tp.smem)) return ABS_ERR_CUDA;

@@ -1009,7 +1009,7 @@ static abs_status tc_run(abs_ctx *ctx, const Setup &s, const TcPlanDev &pd, cons
     {
         StageTimer timer(ctx, e0 ? nullptr : "tc_reduce");
         k_tc_reduce<<<(int)cdiv(G.dense, 256), 256, 0, st>>>(G.dense, (int)ranges, partial, dsum);
-        k_tc_gather<<<(int)cdiv(n_trip, 256), 256, 0, st>>>(n_trip, 1.0 / ((double)s.N * (double)s.N), pd.d_pos,
+        k_tc_gather<<<(int)cdiv(n_trip, 256), 256, 0, st>>>(n_trip, 1.0 / (double)s.P, pd.d_pos,
                                                              dsum, d_sum);
     }
     if (e1) cudaEventRecord(e1, st);   // the autotuner times the kernel with its reduction
@@ -1040,7 +1040,7 @@ static int canonical_nbp(const Setup &s) {
 abs_status tc_split_target(abs_ctx *ctx, const Setup &s, SplitOut &out) {
     const int nbp = canonical_nbp(s);
     if (nbp == 0) return fail(ctx, ABS_ERR_UNSUPPORTED, "split-BF16: no tiling fits the tensor memory");
-    const int64_t P_pad = cdiv((int64_t)s.N * s.N, KC) * KC;
+    const int64_t P_pad = cdiv(s.P, KC) * KC;
     PlaneBufs pl;
     if (!tc_plane_buffers(ctx, nbp, P_pad, pl)) return fail(ctx, ABS_ERR_OOM, "split-BF16 planes");
     out = SplitOut{pl.hi, pl.lo, pl.f32, nbp, P_pad};
@@ -1050,7 +1050,7 @@ abs_status tc_split_target(abs_ctx *ctx, const Setup &s, SplitOut &out) {
 abs_status launch_triple_tc(abs_ctx *ctx, const Setup &s, const float *d_fields, int32_t n_trip,
                             const int32_t *d_ijk, double *d_sum) {
     if (n_trip == 0) return ABS_OK;
-    const int64_t P = (int64_t)s.N * s.N;
+    const int64_t P = s.P;
     const int64_t P_pad = cdiv(P, KC) * KC;
     const bool canonical = d_ijk == s.d_ijk;
     if (!d_fields && !canonical) return fail(ctx, ABS_ERR_INVALID_ARG, "split-BF16: planes without fields need the canonical list");

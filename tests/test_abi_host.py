@@ -113,3 +113,42 @@ def test_binding_rejects_wrong_buffers_before_the_call():
     with pytest.raises(ValueError, match="required"):
         m._dev(None, "f32", 1, "x")
     assert m._dev(None, "f32", 1, "x", optional=True) is None
+
+
+@pytest.mark.parametrize("cfg_id", [5, 6])
+def test_cube_triplets_match_oracle(lib, cfg_id):
+    wl = synth.cube_workload(cfg_id)
+    cfg = absmod.Config3D(absmod.Config.from_workload(wl), wl.extra["n_chan"], wl.extra["tau"])
+    q = oracle.ring_q(wl.ell_edges, wl.du)
+    assert np.array_equal(absmod.abs_triplets_3d(cfg), oracle.triplets_3d(q, wl.extra["tau"]))
+
+
+def test_cube_triplets_random_delay_bins_match_oracle(lib):
+    rng = np.random.default_rng(11)
+    wl = synth.workload(0)
+    q = oracle.ring_q(wl.ell_edges, wl.du)
+    for _ in range(6):
+        n_chan = int(rng.integers(2, 40))
+        t_top = int(rng.integers(1, (n_chan - 1) // 2 + 2))      # delay_edges[-1]: 2 (t_top - 1) < n_chan
+        start = int(rng.integers(0, min(2, t_top)))              # 0, or 1 (drop t = 0) when t_top > 1
+        inner = rng.integers(start + 1, t_top, int(rng.integers(0, 4))).tolist() if t_top > start + 1 else []
+        tau = sorted(set([start, t_top] + inner))
+        cfg = absmod.Config3D(absmod.Config.from_workload(wl), n_chan, tau)
+        assert np.array_equal(absmod.abs_triplets_3d(cfg), oracle.triplets_3d(q, tau)), (n_chan, tau)
+
+
+def test_cube_config_checks(lib):
+    wl = synth.workload(0)
+    base = absmod.Config.from_workload(wl)
+    bad = [
+        absmod.Config3D(base, 8, [0, 2, 1]),       # not ascending
+        absmod.Config3D(base, 8, [0, 1, 5]),       # 2 t_max = 8 >= n_chan
+        absmod.Config3D(base, 0, [0, 1]),          # no channels
+        absmod.Config3D(base, 8, [-1, 1]),         # negative edge
+        absmod.Config3D(base, 8, [0, 1, 4], n_z=9),   # n_z below 3 t_max + 1 = 10
+        absmod.Config3D(absmod.Config.from_workload(wl, weight_mode=absmod.ABS_W_PAPER_LITERAL), 8, [0, 1]),
+    ]
+    for cfg in bad:
+        with pytest.raises(absmod.AbsError):
+            absmod.abs_triplets_3d(cfg)
+    assert len(absmod.abs_triplets_3d(absmod.Config3D(base, 8, [0, 1, 4], n_z=10))) > 0
