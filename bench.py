@@ -628,10 +628,12 @@ def cube_extras(m, synth, ctx, torch, dev, stream, steps, peaks):
         ctx.sync()
         t = timed_calls(lambda: ctx.abs_estimate_3d(cfg, uv, vis, nt, None, B, T, E), steps, stream, torch, dev)
         res[name] = (B.cpu().numpy(), T.cpu().numpy())
+        torch.cuda.nvtx.range_push(f"cube_profile_{name}")
         ctx.profile(True)
         ctx.abs_estimate_3d(cfg, uv, vis, nt, None, B, T, E)
         prof = ctx.profile_read()
         ctx.profile(False)
+        torch.cuda.nvtx.range_pop()
         P3 = 288 * 288 * 46
         o = {"value": steps / (sum(t) * 1e-3), "unit": UNIT, "ms": sum(t) / steps,
              "stages_us": {k: round(1e3 * v[0], 1) for k, v in sorted(prof.items())}}

@@ -70,7 +70,7 @@ struct CubeSetup {
     int32_t *d_rm2 = nullptr;     // [2 nb (t_max + 1)]: the ring extent of each delay-transform pair, twice
     int32_t *d_tau = nullptr;
     int64_t *d_T1 = nullptr;
-    double2 *d_los_tw = nullptr;  // [n_chan] exp(-2 pi i e / n_chan)
+    float4 *d_los_tw = nullptr;   // [n_chan] exp(-2 pi i e / n_chan), double-float (re.hi, im.hi, re.lo, im.lo)
     float2 *d_ztw = nullptr;      // [t_max + 1][N_z] c_t (cos, sin)(2 pi (t z mod N_z) / N_z), c_0 = 1, else 2
     ~CubeSetup();
 };

@@ -8,7 +8,7 @@
 //                 grid (Eq. vg, the 2-D path's plan and gridder);
 //   common cells  a cell enters only if it is filled in every channel;
 //   delay modes   Xt(g, t) = sum_c X_c(g) exp(-2 pi i c t / n_chan) on those
-//                 cells, |t| <= t_max with 2 t_max < n_chan (FP64);
+//                 cells, |t| <= t_max with 2 t_max < n_chan (double-float);
 //   bins          voxel (g, t) lies in bin u = m n_dbins + a when g is in ring
 //                 a_m and tau_a <= |t| < tau_{a+1} (symmetric in t, so every
 //                 3-D field is real);
@@ -20,13 +20,17 @@
 //                 D_u = F1_0 [0 in a] + sum_{t > 0 in a} 2 (F1_t cos + F2_t sin)(2 pi t z / N_z);
 //   sums          S_uvw = (N^2 N_z)^-1 sum over voxels of D_u D_v D_w by the 2-D
 //                 path's triple-sum kernels (FP32 or split-BF16) over N_z N^2
-//                 points: the sum over voxel triangles closed in g and in t, with
-//                 no wrap when N >= 3R + 1 and N_z >= 3 t_max + 1;
+//                 points (on the split-BF16 path with the canonical list the
+//                 line-of-sight pass writes that kernel's split planes itself):
+//                 the sum over voxel triangles closed in g and in t, with no wrap
+//                 when N >= 3R + 1 and N_z >= 3 t_max + 1;
 //   counts        the voxel triangles close in g and t independently and the
 //                 common mask does not depend on t, so T_uvw = T2(rings) x
 //                 T1(delay bins): the 2-D exact counts on the common mask times
 //                 the integer delay count (a table of the binning);
 //   estimate      B_uvw = Re S_uvw / (A T_uvw), NaN where T = 0.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -36,10 +40,11 @@
 namespace absk {
 namespace {
 
-// One channel's weighted means on the region |gx|, |gy| <= Rr (mirror applied,
-// FP64: X = (re_g + re_-g, im_g - im_-g) / (w_g + w_-g) on filled cells), and the
-// count of channels in which each region cell is filled.
-__global__ void k_cube_take(int n, int Rr, int64_t cells, const double *__restrict__ acc, double2 *__restrict__ xc,
+// One channel's weighted means on the region |gx|, |gy| <= Rr (mirror applied, the sums and
+// the quotient X = (re_g + re_-g, im_g - im_-g) / (w_g + w_-g) in FP64 on filled cells), stored
+// as packed double-float complex (re.hi, im.hi, re.lo, im.lo), and the count of channels in
+// which each region cell is filled.
+__global__ void k_cube_take(int n, int Rr, int64_t cells, const double *__restrict__ acc, float4 *__restrict__ xc,
                             int32_t *__restrict__ cnt) {
     const int side = 2 * Rr + 1;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -48,55 +53,105 @@ __global__ void k_cube_take(int n, int Rr, int64_t cells, const double *__restri
     const int64_t cell = (int64_t)(y < 0 ? y + n : y) * n + (x < 0 ? x + n : x);
     const int64_t mcell = (int64_t)(y > 0 ? n - y : -y) * n + (x > 0 ? n - x : -x);
     const double ww = acc[2 * cells + cell] + acc[2 * cells + mcell];
-    double2 v = make_double2(0.0, 0.0);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (ww > 0.0) {
-        v.x = (acc[cell] + acc[mcell]) / ww;
-        v.y = (acc[cells + cell] - acc[cells + mcell]) / ww;
+        const double re = (acc[cell] + acc[mcell]) / ww, im = (acc[cells + cell] - acc[cells + mcell]) / ww;
+        v.x = __double2float_rn(re);
+        v.y = __double2float_rn(im);
+        v.z = __double2float_rn(re - (double)v.x);
+        v.w = __double2float_rn(im - (double)v.y);
         cnt[idx] += 1;
     }
     xc[idx] = v;
 }
 
-// Delay modes t = blockIdx.y of every region cell filled in all n_chan channels (FP64 sums
-// over the channels, twiddle exp(-2 pi i e / n_chan) at e = c t mod n_chan), stored as
-// packed double-float complex (re.hi, im.hi, re.lo, im.lo); zero on the other cells.  The
-// first delay also writes the common filled mask of the n x n grid (region cells only).
-__global__ void k_cube_los(int n, int Rr, int n_chan, const double2 *__restrict__ xc, const int32_t *__restrict__ cnt,
-                           const double2 *__restrict__ tw, float4 *__restrict__ xt, uint8_t *__restrict__ mask) {
+// Double-float arithmetic (a value is hi + lo, two FP32 numbers): Knuth's TwoSum of the high
+// parts with the low parts added, Dekker's product with the FMA remainder, both renormalised.
+struct dfl {
+    float h, l;
+};
+__device__ __forceinline__ dfl dfl_add(dfl a, dfl b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    const float h = __fadd_rn(p, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+
+// Delay modes t = blockIdx.y of every region cell filled in all n_chan channels: the sum over
+// the channels of X_c times exp(-2 pi i e / n_chan), e = c t mod n_chan, in double-float
+// (GB300's FP64 pipe is narrow; about 2^-44 relative per product), stored as packed
+// double-float complex; zero on the other cells.  The first delay also writes the common
+// filled mask of the n x n grid (region cells only).
+__global__ void k_cube_los(int n, int Rr, int n_chan, const float4 *__restrict__ xc, const int32_t *__restrict__ cnt,
+                           const float4 *__restrict__ tw, float4 *__restrict__ xt, uint8_t *__restrict__ mask) {
     const int side = 2 * Rr + 1, side2 = side * side;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= side2) return;
     const int t = blockIdx.y;
     const bool common = cnt[idx] == n_chan;
-    double sr = 0.0, si = 0.0;
+    dfl sr = {0.f, 0.f}, si = {0.f, 0.f};
     if (common) {
         int e = 0;   // c t mod n_chan, advanced by t per channel
         for (int c = 0; c < n_chan; ++c) {
-            const double2 w = __ldg(tw + e), x = xc[(size_t)c * side2 + idx];
-            sr += x.x * w.x - x.y * w.y;
-            si += x.x * w.y + x.y * w.x;
+            const float4 w = __ldg(tw + e), x = xc[(size_t)c * side2 + idx];   // (re.hi, im.hi, re.lo, im.lo)
+            const dfl xr = {x.x, x.z}, xi = {x.y, x.w}, wr = {w.x, w.z}, wi = {w.y, w.w};
+            const dfl ni = dfl_mul(xi, wi);
+            sr = dfl_add(sr, dfl_add(dfl_mul(xr, wr), {-ni.h, -ni.l}));
+            si = dfl_add(si, dfl_add(dfl_mul(xr, wi), dfl_mul(xi, wr)));
             e += t;
             if (e >= n_chan) e -= n_chan;
         }
     }
-    const float rh = __double2float_rn(sr), ih = __double2float_rn(si);
-    xt[(size_t)t * side2 + idx] =
-        make_float4(rh, ih, __double2float_rn(sr - (double)rh), __double2float_rn(si - (double)ih));
+    xt[(size_t)t * side2 + idx] = make_float4(sr.h, si.h, sr.l, si.l);
     if (t == 0) {
         const int y = idx / side - Rr, x = idx - (idx / side) * side - Rr;
         mask[(int64_t)(y < 0 ? y + n : y) * n + (x < 0 ? x + n : x)] = common ? 1 : 0;
     }
 }
 
-// The direct transform along the line of sight: for ring m = blockIdx.y and pixel p,
-// D[(m na + a) N_z + z][p] = sum over t >= 0 in delay bin a of F1_t(p) c_tz + F2_t(p) s_tz,
+// Where k_cube_zexpand puts voxel v of bin u: FP32 fields [u][v], or the split-BF16 kernel's
+// three planes (the layout SplitOut describes: [P_pad / 64][nbp][64], each 64-point row in the
+// 128-byte swizzle of the tensor-core operand, 16-byte units XOR-permuted by u & 7), each value
+// split once into hi = bf16(x) and lo = bf16(x - hi) beside its FP32 copy.
+struct VoxelFields {
+    float *D;
+    int64_t P;
+    __device__ void put(int u, int64_t v, float x) const { D[(size_t)u * P + v] = x; }
+};
+struct VoxelPlanes {
+    SplitOut o;
+    __device__ void put(int u, int64_t v, float x) const {
+        const int w = (int)(v & 63), key = u & 7;
+        const size_t row = ((size_t)(v >> 6) * o.nbp + u) * 64;
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(x, __bfloat162float(h)));   // exact in FP32
+        const size_t ob = row + (size_t)((((w >> 3) ^ key) << 3) | (w & 7));
+        ((__nv_bfloat16 *)o.hi)[ob] = h;
+        ((__nv_bfloat16 *)o.lo)[ob] = l;
+        o.f32[row + (size_t)((((w >> 2) ^ key) << 2) | (w & 3))] = x;
+    }
+};
+
+// The direct transform along the line of sight: for ring m = blockIdx.y and pixel p, voxel
+// z N^2 + p of bin m na + a is the sum over t >= 0 in delay bin a of F1_t(p) c_tz + F2_t(p) s_tz,
 // with (c, s) = (cos, sin)(2 pi t z / N_z) times 1 for t = 0 and 2 for t > 0 (the table
-// ztw [t1][N_z], staged in shared memory).  Eight z a pass, so each F value is loaded once
-// per pass.
+// ztw [t1][N_z], staged in shared memory).  Eight z a pass, so each F value is loaded once per
+// pass.
 constexpr int ZB = 8;
+template <class Out>
 __global__ void __launch_bounds__(256) k_cube_zexpand(int64_t P2, int t1, int na, const int32_t *__restrict__ tau,
                                                      int Nz, const float *__restrict__ F,
-                                                     const float2 *__restrict__ ztw, float *__restrict__ D) {
+                                                     const float2 *__restrict__ ztw, const Out out) {
     extern __shared__ float2 stw[];
     for (int i = threadIdx.x; i < t1 * Nz; i += blockDim.x) stw[i] = ztw[i];
     __syncthreads();
@@ -106,25 +161,25 @@ __global__ void __launch_bounds__(256) k_cube_zexpand(int64_t P2, int t1, int na
     const float *Fm = F + (size_t)2 * m * t1 * P2;
     for (int a = 0; a < na; ++a) {
         const int ta = tau[a], tb = min(tau[a + 1], t1);
-        float *Du = D + ((size_t)(m * na + a) * Nz) * P2;
+        const int u = m * na + a;
         for (int z0 = 0; z0 < Nz; z0 += ZB) {
             float acc[ZB];
 #pragma unroll
-            for (int u = 0; u < ZB; ++u) acc[u] = 0.f;
+            for (int k = 0; k < ZB; ++k) acc[k] = 0.f;
             for (int t = ta; t < tb; ++t) {
                 const float f1 = Fm[(size_t)(2 * t) * P2 + p], f2 = Fm[(size_t)(2 * t + 1) * P2 + p];
                 const float2 *row = stw + (size_t)t * Nz;
 #pragma unroll
-                for (int u = 0; u < ZB; ++u) {
-                    if (z0 + u < Nz) {
-                        const float2 w = row[z0 + u];
-                        acc[u] = fmaf(f1, w.x, fmaf(f2, w.y, acc[u]));
+                for (int k = 0; k < ZB; ++k) {
+                    if (z0 + k < Nz) {
+                        const float2 w = row[z0 + k];
+                        acc[k] = fmaf(f1, w.x, fmaf(f2, w.y, acc[k]));
                     }
                 }
             }
 #pragma unroll
-            for (int u = 0; u < ZB; ++u)
-                if (z0 + u < Nz) Du[(size_t)(z0 + u) * P2 + p] = acc[u];
+            for (int k = 0; k < ZB; ++k)
+                if (z0 + k < Nz) out.put(u, (int64_t)(z0 + k) * P2 + p, acc[k]);
         }
     }
 }
@@ -295,10 +350,12 @@ const CubeSetup *get_cube_setup(abs_ctx *ctx, const abs_config3d *cfg, abs_statu
     std::vector<int32_t> rm2((size_t)2 * nb * t1);
     for (int m = 0; m < nb; ++m)
         for (int d = 0; d < t1; ++d) rm2[2 * ((size_t)m * t1 + d)] = rm2[2 * ((size_t)m * t1 + d) + 1] = s2->Rm[m];
-    std::vector<double2> los(c->n_chan);
+    std::vector<float4> los(c->n_chan);   // exp(-2 pi i e / n_chan) as double-float (re.hi, im.hi, re.lo, im.lo)
     for (int e = 0; e < c->n_chan; ++e) {
         const double a = -2.0 * M_PI * (double)e / (double)c->n_chan;
-        los[e] = make_double2(std::cos(a), std::sin(a));
+        const double cr = std::cos(a), ci = std::sin(a);
+        const float rh = (float)cr, ih = (float)ci;
+        los[e] = make_float4(rh, ih, (float)(cr - (double)rh), (float)(ci - (double)ih));
     }
     std::vector<float2> ztw((size_t)t1 * c->Nz);
     for (int d = 0; d < t1; ++d)
@@ -332,16 +389,21 @@ abs_status launch_cube_estimate(abs_ctx *ctx, const CubeSetup &c, int64_t n_vis,
     const int Rr = s2.R, side = 2 * Rr + 1, side2 = side * side, t1 = c.t_max + 1;
     const int64_t cells = (int64_t)s2.n * s2.n, P2 = (int64_t)s2.N * s2.N;
     const int n_trip2 = (int)(s2.ijk.size() / 3);
-    double2 *xc = (double2 *)workspace(ctx, "cube.xc", sizeof(double2) * (size_t)c.n_chan * side2);
+    float4 *xc = (float4 *)workspace(ctx, "cube.xc", sizeof(float4) * (size_t)c.n_chan * side2);
     int32_t *cnt = (int32_t *)workspace(ctx, "cube.cnt", sizeof(int32_t) * (size_t)side2);
     float4 *xt = (float4 *)workspace(ctx, "cube.xt", sizeof(float4) * (size_t)t1 * side2);
     uint8_t *mask = (uint8_t *)workspace(ctx, "cube.mask", (size_t)cells);
     float *F = (float *)workspace(ctx, "cube.F", sizeof(float) * (size_t)2 * s2.nb * t1 * P2);
-    float *D = (float *)workspace(ctx, "cube.D", sizeof(float) * (size_t)st.nb * st.P);
+    // split-BF16 sums over the canonical list: the line-of-sight transform writes the tensor-core
+    // kernel's planes directly, and no FP32 voxel fields are kept
+    const bool to_planes = st.precision == ABS_SPLIT_BF16 && d_uvw == st.d_ijk && n_trip > 0;
+    SplitOut planes{};
+    if (to_planes) ABS_CHECK(tc_split_target(ctx, st, planes));
+    float *D = to_planes ? nullptr : (float *)workspace(ctx, "cube.D", sizeof(float) * (size_t)st.nb * st.P);
     double *sum = (double *)workspace(ctx, "cube.sum", sizeof(double) * std::max(n_trip, 1));
     int64_t *t2 = (int64_t *)workspace(ctx, "cube.t2", sizeof(int64_t) * std::max(n_trip2, 1));
     int64_t *count = d_count ? d_count : (int64_t *)workspace(ctx, "cube.count", sizeof(int64_t) * std::max(n_trip, 1));
-    if (!xc || !cnt || !xt || !mask || !F || !D || !sum || !t2 || !count)
+    if (!xc || !cnt || !xt || !mask || !F || (!D && !to_planes) || !sum || !t2 || !count)
         return fail(ctx, ABS_ERR_OOM, "multi-frequency workspace");
     cudaStream_t s = ctx->stream;
     if (d_uvw != st.d_ijk) ABS_CHECK(launch_check_triplets(ctx, st, n_trip, d_uvw));
@@ -373,10 +435,19 @@ abs_status launch_cube_estimate(abs_ctx *ctx, const CubeSetup &c, int64_t n_vis,
     ABS_CHECK(launch_filter_fft_delay(ctx, s2, c.t_max, xt, c.d_rm2, F));
     {
         const size_t zsm = sizeof(float2) * (size_t)t1 * c.Nz;
-        if (!allow_smem(k_cube_zexpand, zsm)) return fail(ctx, ABS_ERR_UNSUPPORTED, "line-of-sight twiddles do not fit shared memory");
+        const dim3 grid((unsigned)cdiv(P2, 256), s2.nb);
         StageTimer timer(ctx, "cube_zexpand");
-        k_cube_zexpand<<<dim3((unsigned)cdiv(P2, 256), s2.nb), 256, zsm, s>>>(P2, t1, c.na, c.d_tau, c.Nz, F,
-                                                                            c.d_ztw, D);
+        if (to_planes) {
+            if (!allow_smem(k_cube_zexpand<VoxelPlanes>, zsm))
+                return fail(ctx, ABS_ERR_UNSUPPORTED, "line-of-sight twiddles do not fit shared memory");
+            k_cube_zexpand<VoxelPlanes><<<grid, 256, zsm, s>>>(P2, t1, c.na, c.d_tau, c.Nz, F, c.d_ztw,
+                                                              VoxelPlanes{planes});
+        } else {
+            if (!allow_smem(k_cube_zexpand<VoxelFields>, zsm))
+                return fail(ctx, ABS_ERR_UNSUPPORTED, "line-of-sight twiddles do not fit shared memory");
+            k_cube_zexpand<VoxelFields><<<grid, 256, zsm, s>>>(P2, t1, c.na, c.d_tau, c.Nz, F, c.d_ztw,
+                                                              VoxelFields{D, st.P});
+        }
     }
     ABS_CHECK(check_launch(ctx, "line-of-sight transform"));
     if (n_trip == 0) return ABS_OK;
