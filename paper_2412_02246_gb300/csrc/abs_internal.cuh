@@ -142,6 +142,9 @@ namespace absk {
 
 // Concurrent lanes of abs_estimate_batched (items round-robin over them).
 constexpr int ABS_BATCH_LANES = 4;
+// Creates lanes of ctx (child contexts with their own streams and workspaces, sharing its
+// device error word) until it has K.
+abs_status ensure_lanes(abs_ctx *ctx, int K);
 
 // Device error codes latched into ctx->d_err (first one wins).
 enum : int32_t {

@@ -1006,6 +1006,19 @@ static abs_ctx *make_lane(abs_ctx *ctx) {
     return l;
 }
 
+extern "C++" {
+namespace absk {
+abs_status ensure_lanes(abs_ctx *ctx, int K) {
+    while ((int)ctx->lanes.size() < K) {
+        abs_ctx *l = make_lane(ctx);
+        if (!l) return fail(ctx, ABS_ERR_OOM, "lanes");
+        ctx->lanes.push_back(l);
+    }
+    return ABS_OK;
+}
+}  // namespace absk
+}  // extern "C++"
+
 // The batch driver of abs_estimate_batched and abs_estimate_batched_host.  With
 // host = true the items' uv / vis are host inputs and B / count / ellbar host
 // outputs: each item is staged through its lane's own device buffers (copies in,

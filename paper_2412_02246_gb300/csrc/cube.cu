@@ -42,10 +42,10 @@ namespace {
 
 // One channel's weighted means on the region |gx|, |gy| <= Rr (mirror applied, the sums and
 // the quotient X = (re_g + re_-g, im_g - im_-g) / (w_g + w_-g) in FP64 on filled cells), stored
-// as packed double-float complex (re.hi, im.hi, re.lo, im.lo), and the count of channels in
-// which each region cell is filled.
+// as packed double-float complex (re.hi, im.hi, re.lo, im.lo), and the channel's filled flag of
+// every region cell.
 __global__ void k_cube_take(int n, int Rr, int64_t cells, const double *__restrict__ acc, float4 *__restrict__ xc,
-                            int32_t *__restrict__ cnt) {
+                            uint8_t *__restrict__ filled) {
     const int side = 2 * Rr + 1;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= side * side) return;
@@ -60,9 +60,9 @@ __global__ void k_cube_take(int n, int Rr, int64_t cells, const double *__restri
         v.y = __double2float_rn(im);
         v.z = __double2float_rn(re - (double)v.x);
         v.w = __double2float_rn(im - (double)v.y);
-        cnt[idx] += 1;
     }
     xc[idx] = v;
+    filled[idx] = ww > 0.0 ? 1 : 0;
 }
 
 // Double-float arithmetic (a value is hi + lo, two FP32 numbers): Knuth's TwoSum of the high
@@ -92,13 +92,14 @@ __device__ __forceinline__ dfl dfl_mul(dfl a, dfl b) {
 // (GB300's FP64 pipe is narrow; about 2^-44 relative per product), stored as packed
 // double-float complex; zero on the other cells.  The first delay also writes the common
 // filled mask of the n x n grid (region cells only).
-__global__ void k_cube_los(int n, int Rr, int n_chan, const float4 *__restrict__ xc, const int32_t *__restrict__ cnt,
+__global__ void k_cube_los(int n, int Rr, int n_chan, const float4 *__restrict__ xc, const uint8_t *__restrict__ filled,
                            const float4 *__restrict__ tw, float4 *__restrict__ xt, uint8_t *__restrict__ mask) {
     const int side = 2 * Rr + 1, side2 = side * side;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= side2) return;
     const int t = blockIdx.y;
-    const bool common = cnt[idx] == n_chan;
+    bool common = true;
+    for (int c = 0; c < n_chan; ++c) common = common && filled[(size_t)c * side2 + idx];
     dfl sr = {0.f, 0.f}, si = {0.f, 0.f};
     if (common) {
         int e = 0;   // c t mod n_chan, advanced by t per channel
@@ -390,7 +391,7 @@ abs_status launch_cube_estimate(abs_ctx *ctx, const CubeSetup &c, int64_t n_vis,
     const int64_t cells = (int64_t)s2.n * s2.n, P2 = (int64_t)s2.N * s2.N;
     const int n_trip2 = (int)(s2.ijk.size() / 3);
     float4 *xc = (float4 *)workspace(ctx, "cube.xc", sizeof(float4) * (size_t)c.n_chan * side2);
-    int32_t *cnt = (int32_t *)workspace(ctx, "cube.cnt", sizeof(int32_t) * (size_t)side2);
+    uint8_t *filled = (uint8_t *)workspace(ctx, "cube.filled", (size_t)c.n_chan * side2);
     float4 *xt = (float4 *)workspace(ctx, "cube.xt", sizeof(float4) * (size_t)t1 * side2);
     uint8_t *mask = (uint8_t *)workspace(ctx, "cube.mask", (size_t)cells);
     float *F = (float *)workspace(ctx, "cube.F", sizeof(float) * (size_t)2 * s2.nb * t1 * P2);
@@ -403,26 +404,49 @@ abs_status launch_cube_estimate(abs_ctx *ctx, const CubeSetup &c, int64_t n_vis,
     double *sum = (double *)workspace(ctx, "cube.sum", sizeof(double) * std::max(n_trip, 1));
     int64_t *t2 = (int64_t *)workspace(ctx, "cube.t2", sizeof(int64_t) * std::max(n_trip2, 1));
     int64_t *count = d_count ? d_count : (int64_t *)workspace(ctx, "cube.count", sizeof(int64_t) * std::max(n_trip, 1));
-    if (!xc || !cnt || !xt || !mask || !F || (!D && !to_planes) || !sum || !t2 || !count)
+    if (!xc || !filled || !xt || !mask || !F || (!D && !to_planes) || !sum || !t2 || !count)
         return fail(ctx, ABS_ERR_OOM, "multi-frequency workspace");
     cudaStream_t s = ctx->stream;
     if (d_uvw != st.d_ijk) ABS_CHECK(launch_check_triplets(ctx, st, n_trip, d_uvw));
-    cudaMemsetAsync(cnt, 0, sizeof(int32_t) * (size_t)side2, s);
     cudaMemsetAsync(mask, 0, (size_t)cells, s);
-    // every channel: the 2-D gridding plan and accumulation, then its means on the region
-    for (int ch = 0; ch < c.n_chan; ++ch) {
-        ABS_CHECK(launch_grid_plan(ctx, s2, n_vis, d_uv + (size_t)ch * 2 * n_vis, true));
-        ABS_CHECK(launch_grid_accumulate(ctx, s2, n_vis, d_vis + (size_t)ch * 2 * n_vis, nullptr, nullptr, nullptr));
-        double *acc = nullptr;
-        grid_acc_buffers(ctx, s2, &acc);
-        if (!acc) return fail(ctx, ABS_ERR_OOM, "grid accumulation workspace");
-        StageTimer timer(ctx, "cube_take");
-        k_cube_take<<<(int)cdiv(side2, 256), 256, 0, s>>>(s2.n, Rr, cells, acc, xc + (size_t)ch * side2, cnt);
+    // every channel: the 2-D gridding plan and accumulation, then its means on the region; the
+    // channels run round-robin over the context's lanes (concurrent streams with workspaces of
+    // their own), forked from and joined back to its stream, except while the stage profiler runs
+    // or on the legacy default stream
+    const int K = (ctx->profiling || !s || c.n_chan < 2) ? 1 : std::min(ABS_BATCH_LANES, c.n_chan);
+    if (K > 1) {
+        ABS_CHECK(ensure_lanes(ctx, K));
+        cudaEventRecord(ctx->ev_fork, s);
+        for (int l = 0; l < K; ++l) cudaStreamWaitEvent(ctx->lanes[l]->stream, ctx->ev_fork, 0);
     }
+    abs_status cst = ABS_OK;
+    for (int ch = 0; ch < c.n_chan && cst == ABS_OK; ++ch) {
+        abs_ctx *lc = K > 1 ? ctx->lanes[ch % K] : ctx;
+        cst = launch_grid_plan(lc, s2, n_vis, d_uv + (size_t)ch * 2 * n_vis, true);
+        if (cst == ABS_OK) cst = launch_grid_accumulate(lc, s2, n_vis, d_vis + (size_t)ch * 2 * n_vis, nullptr, nullptr, nullptr);
+        double *acc = nullptr;
+        if (cst == ABS_OK) {
+            grid_acc_buffers(lc, s2, &acc);
+            if (!acc) cst = fail(lc, ABS_ERR_OOM, "grid accumulation workspace");
+        }
+        if (cst == ABS_OK) {
+            StageTimer timer(lc, "cube_take");
+            k_cube_take<<<(int)cdiv(side2, 256), 256, 0, lc->stream>>>(s2.n, Rr, cells, acc, xc + (size_t)ch * side2,
+                                                                       filled + (size_t)ch * side2);
+            cst = check_launch(lc, "channel means");
+        }
+        if (cst != ABS_OK && lc != ctx) ctx->last_error = "channel " + std::to_string(ch) + ": " + lc->last_error;
+    }
+    if (K > 1)   // join: the context's stream waits for every lane
+        for (int l = 0; l < K; ++l) {
+            cudaEventRecord(ctx->lanes[l]->ev_lane, ctx->lanes[l]->stream);
+            cudaStreamWaitEvent(s, ctx->lanes[l]->ev_lane, 0);
+        }
+    if (cst != ABS_OK) return cst;
     {
         StageTimer timer(ctx, "cube_los");
-        k_cube_los<<<dim3((unsigned)cdiv(side2, 128), t1), 128, 0, s>>>(s2.n, Rr, c.n_chan, xc, cnt, c.d_los_tw, xt,
-                                                                       mask);
+        k_cube_los<<<dim3((unsigned)cdiv(side2, 128), t1), 128, 0, s>>>(s2.n, Rr, c.n_chan, xc, filled, c.d_los_tw,
+                                                                       xt, mask);
     }
     ABS_CHECK(check_launch(ctx, "delay modes"));
     // exact counts: 2-D counts on the common mask (and the rings' mean l), times the delay counts
