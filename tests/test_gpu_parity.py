@@ -414,6 +414,13 @@ def test_triple_sums_and_counts(ctx, cfg_id):
     ctx.sync()
     Bn = B.cpu().numpy()
     assert np.array_equal(np.isnan(Bn), np.isnan(est.B))
+    # B = S / (A T) in FP64 (A = 1): the same IEEE quotient of the call's own S and T, and within the
+    # sum tolerance of the oracle's B on every triplet with |B| >= 1e-3 max|B|
+    Sn, Tn = S.cpu().numpy(), T.cpu().numpy()
+    has = Tn > 0
+    assert np.array_equal(Bn[has], Sn[has] / (1.0 * Tn[has].astype(np.float64)))
+    big = has & (np.abs(est.B) >= 1e-3 * np.nanmax(np.abs(est.B)))
+    assert np.max(np.abs(Bn[big] - est.B[big]) / np.abs(est.B[big])) <= SUM_TOL
     assert np.allclose(E.cpu().numpy(), est.ellbar, rtol=1e-12, equal_nan=True)
 
 
