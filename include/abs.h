@@ -427,8 +427,13 @@ abs_status abs_triplets_3d(const abs_config3d *cfg, int32_t cap, int32_t *n_trip
  * canonical order with bins < n_bins n_dbins, or NULL for the list of abs_triplets_3d
  * (n_trip must then equal its length).  Outputs (each may be NULL): d_B [n_trip] f64,
  * d_count [n_trip] int64 (exact T_uvw), d_ellbar [n_bins] f64 (mean l of each ring over
- * the common mask).  The first call with a set of arguments runs eagerly (sizing the
- * context's workspaces), the second is captured as a CUDA graph and replayed after that.
+ * the common mask).  On a non-default stream the channels' gridding runs round-robin over
+ * the context's four lanes (the streams abs_estimate_batched uses, forked from and joined back
+ * to the context's stream), and the first call with a set of arguments runs eagerly (sizing
+ * the workspaces), the second is captured as one CUDA graph and replayed after that; on the
+ * legacy default stream every call runs eagerly on that stream.  A caller-given d_uvw in
+ * split-BF16 precision is read back and planned on every call (one synchronisation; such a
+ * call is not captured).
  * Device memory: about 4 (n_bins n_dbins N_z + 2 n_bins (t_max + 1)) N^2 bytes of fields,
  * plus the split-BF16 operands (8 bytes per bin and voxel) in that precision. */
 abs_status abs_estimate_3d(abs_ctx *ctx, const abs_config3d *cfg, int64_t n_vis, const float *d_uv,
