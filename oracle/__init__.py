@@ -34,7 +34,8 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   one channel reduces to the 2-D brute force; a separable cube x(g) f(c)
   factorises into the 2-D sums times the delay sums of numpy's FFT of f;
   cyclic shifts and reversal of the channel order leave B unchanged;
-  Im S vanishes
+  Im S vanishes; a Gaussian cube gives B = 0 and the quadratic cube the
+  three-dimensional analogue of the discrete Eq. bsana (teeth at 1/2x, 2x)
 * delay_counts / triplets_3d: closed form of the one-bin delay count,
   against the brute-force 3-D counts on a fully filled tiny grid
 * fft_form_3d: against the 3-D brute force (sums to rounding), aliasing

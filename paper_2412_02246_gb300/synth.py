@@ -353,16 +353,22 @@ def cube_workload(cfg_id: int) -> Workload:
     raise ValueError(f"unknown cube workload id {cfg_id}")
 
 
-def gaussian_cube(m: int, n_chan: int, rng: np.random.Generator, alpha: float = 2.5) -> np.ndarray:
-    """Real Gaussian field on an m x m x n_chan periodic grid (axis 2 along frequency),
-    P(k) ~ |k|^-alpha with k in grid-index units on all three axes, unit ensemble variance."""
+def cube_power_model(m: int, n_chan: int, alpha: float = 2.5) -> np.ndarray:
+    """P(k) ~ |k|^-alpha on an m x m x n_chan grid (k in grid-index units on all three axes, FFT
+    order, P(0) = 0), scaled so that (1 / size) sum_k P(k) = 1: the spectrum of `gaussian_cube`."""
     kx = np.fft.fftfreq(m) * m
     kz = np.fft.fftfreq(n_chan) * n_chan
     kk = np.sqrt(kx[:, None, None] ** 2 + kx[None, :, None] ** 2 + kz[None, None, :] ** 2)
     p = np.zeros_like(kk)
     nz = kk > 0
     p[nz] = kk[nz] ** (-alpha)
-    p *= p.size / p.sum()
+    return p * (p.size / p.sum())
+
+
+def gaussian_cube(m: int, n_chan: int, rng: np.random.Generator, alpha: float = 2.5) -> np.ndarray:
+    """Real Gaussian field on an m x m x n_chan periodic grid (axis 2 along frequency) with the
+    spectrum of `cube_power_model`, unit ensemble variance."""
+    p = cube_power_model(m, n_chan, alpha)
     white = rng.standard_normal((m, m, n_chan))
     return np.fft.ifftn(np.fft.fftn(white) * np.sqrt(p)).real
 

@@ -183,3 +183,78 @@ def test_fft_form_3d_matches_bruteforce_and_aliases_when_delays_wrap():
     # onto listed bin triplets
     Sa, _ = oracle.fft_form_3d(Xt, common, q, tau, uvw, N, 2 * t_max + 1)
     assert np.max(np.abs(Sa - S.real) / A) > 1e-6
+
+
+def _cube_closed_form(P, q, tau, uvw, f, V):
+    """First order in f of the quadratic cube's bispectrum (Wick's theorem as in App. B, with sums for
+    integrals, in three dimensions): E[Xt1 Xt2 Xt3] = 2 f V (P1 P2 + P2 P3 + P3 P1) per voxel triangle
+    closed in g and t, with <|Xt(g, t)|^2> = V P(g, t), averaged over the closed triangles of each bin
+    triplet."""
+    M, _, n_chan = P.shape
+    half = M // 2 - 1
+    t_max = tau[-1] - 1
+    na = len(tau) - 1
+    vox = []
+    for gy in range(-half, half + 1):
+        for gx in range(-half, half + 1):
+            r2 = gx * gx + gy * gy
+            if r2 < q[0] or r2 >= q[-1]:
+                continue
+            m = int(np.searchsorted(q, r2, side="right") - 1)
+            for t in range(-t_max, t_max + 1):
+                a = oracle.delay_bin(t, tau)
+                if a >= 0:
+                    vox.append((gx, gy, t, m * na + a))
+    vox = np.array(vox)
+    key = {(int(v[0]), int(v[1]), int(v[2])): int(v[3]) for v in vox}
+    Pv = np.array([P[v[1] % M, v[0] % M, v[2] % n_chan] for v in vox])
+    nb3 = (len(q) - 1) * na
+    acc = np.zeros((nb3, nb3, nb3))
+    cnt = np.zeros((nb3, nb3, nb3))
+    for a in range(len(vox)):
+        third = -(vox[a, :3] + vox[:, :3])
+        u3 = np.array([key.get((int(x), int(y), int(z)), -1) for x, y, z in third])
+        sel = u3 >= 0
+        P3 = np.array([P[y % M, x % M, z % n_chan] for x, y, z in third[sel]])
+        val = Pv[a] * Pv[sel] + Pv[sel] * P3 + P3 * Pv[a]
+        np.add.at(acc, (vox[a, 3], vox[sel, 3], u3[sel]), val)
+        np.add.at(cnt, (vox[a, 3], vox[sel, 3], u3[sel]), 1)
+    out = np.array([acc[u, v, w] / cnt[u, v, w] if cnt[u, v, w] else np.nan for u, v, w in uvw])
+    return 2.0 * f * V * out
+
+
+@pytest.mark.slow
+def test_gaussian_cube_has_zero_mean_and_quadratic_cube_matches_closed_form():
+    """Grid-direct cubes (each channel's map modes taken as its gridded data, every cell filled): a
+    Gaussian cube gives B = 0 within sampling error, and the quadratic cube g + f (g^2 - 1) at f = 0.05
+    gives the three-dimensional analogue of the discrete Eq. bsana."""
+    M, n_chan = 16, 8
+    q = oracle.ring_q(2 * np.pi * np.array([1.5, 3.0, 4.5, 6.5]), 1.0)
+    tau = [0, 1, 2, 4]
+    uvw = oracle.triplets_3d(q, tau)
+    P = synth.cube_power_model(M, n_chan)
+    filled = np.ones((n_chan, M, M), np.uint8)
+    filled[:, M // 2, :] = 0   # the row and column at index M/2 are off the grid
+    filled[:, :, M // 2] = 0
+    R = 1200
+    rng = np.random.default_rng(2025)
+    res = {}
+    for f in (0.0, 0.05):
+        Bs = []
+        for _ in range(R):
+            cube = synth.quadratic_sky(synth.gaussian_cube(M, n_chan, rng), f)
+            X = np.stack([synth.sky_modes(np.ascontiguousarray(cube[:, :, c])) for c in range(n_chan)])
+            Xt, common = oracle.delay_modes(X, filled, tau[-1] - 1)
+            S, _, T = oracle.triple3d_bruteforce(Xt, common, q, tau, uvw)
+            Bs.append(oracle.normalise(S, T))
+        Bs = np.array(Bs)
+        res[f] = (Bs.mean(0), Bs.std(0, ddof=1) / np.sqrt(R))
+    mean0, se0 = res[0.0]
+    assert np.all(np.abs(mean0 / se0) < 5.0)
+    expect = _cube_closed_form(P, q, tau, uvw, 0.05, M * M * n_chan)
+    mean1, se1 = res[0.05]
+    assert np.all(np.abs((mean1 - expect) / se1) < 5.0)
+    # teeth: the signal is detected, and a halved or doubled prediction is rejected
+    assert np.max(np.abs(mean1 / se1)) > 10.0
+    assert np.max(np.abs((mean1 - 0.5 * expect) / se1)) > 5.0
+    assert np.max(np.abs((mean1 - 2.0 * expect) / se1)) > 5.0
