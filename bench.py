@@ -82,7 +82,7 @@ MEASURED_TRAFFIC = {
     "fft_rows": {"bytes": 1250012000, "source": "paper_2412_02246_gb300/csrc/fft.cu",
                  "sha256": "e0c763502d9680073163ddc3c914101553e28b3b6d52983992aa0a07de5173b0"},
     "triple_tc": {"bytes": 1339430000, "source": "paper_2412_02246_gb300/csrc/triple_tc.cu",
-                  "sha256": "aab1f7f3d12c7b43d2dcccfaa54ab1c43670a3c5d0c0c121cf9e486d4fe739fc"},
+                  "sha256": "56ec114d7a18bc151efae201334e7ece346d772bb2221b660021b47bf0ef0815"},
 }
 
 
