@@ -152,3 +152,12 @@ def test_cube_config_checks(lib):
         with pytest.raises(absmod.AbsError):
             absmod.abs_triplets_3d(cfg)
     assert len(absmod.abs_triplets_3d(absmod.Config3D(base, 8, [0, 1, 4], n_z=10))) > 0
+
+
+def test_binding_gives_every_declared_call_a_signature(lib):
+    """Every call the header declares has explicit ctypes argument and result types in the binding
+    (a call without them would be passed guessed C types)."""
+    for n in declared_functions():
+        f = getattr(lib, n)
+        assert f.argtypes is not None, n
+        assert f.restype is not None, n
