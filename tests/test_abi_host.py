@@ -161,3 +161,11 @@ def test_binding_gives_every_declared_call_a_signature(lib):
         f = getattr(lib, n)
         assert f.argtypes is not None, n
         assert f.restype is not None, n
+    # and as many arguments as the declaration has parameters
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "abs.h")).read(), flags=re.S)
+    decls = re.findall(r"^(?:abs_status|const char \*)\s*(abs_\w+)\s*\(([^;]*?)\)\s*;", src, re.M | re.S)
+    assert len(decls) == len(declared_functions())
+    for name, params in decls:
+        params = params.strip()
+        want = 0 if params in ("", "void") else len(params.split(","))
+        assert len(getattr(lib, name).argtypes) == want, (name, want, len(getattr(lib, name).argtypes))
