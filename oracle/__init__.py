@@ -20,7 +20,7 @@ Parity status per function (what pins it, see ``tests/test_oracle_*.py``):
   FFT identity, constant-sky B = s^3, point-source phase closure,
   ring-constant product, rotation/reflection invariance, permutation
   symmetry of counts, Gaussian-sky zero mean, quadratic-sky closed form
-  (discrete Eq. bsana)
+  (discrete Eq. bsana), zero mean under pure gridded visibility noise
 * ellbar: direct closed form on a hand-built mask
 * normalise: closed forms above
 * bana_d (discretely sampled prediction): constant C, a pure-Python
